@@ -1,0 +1,211 @@
+"""FP64 CPU oracle of DE/rand/1/bin (arXiv 2405.16551, Sec. 2 and Sec. 7.3).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product library never imports it, never links it, and shares no
+code with it; it exists to check the CUDA path.
+
+The arithmetic lives in plain C (``de_oracle.c``, ``de_oracle_ode.c``,
+``de_oracle_mlp.c``), compiled with gcc on first use (or by ``build()``) and
+called through ctypes.  This module only marshals numpy arrays.
+
+Parity pins for every function are in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["de_oracle.c", "de_oracle_ode.c", "de_oracle_mlp.c"]
+_LIB_PATH = os.path.join(_HERE, "_build", "libde_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+SPHERE, RASTRIGIN, ROSENBROCK, ACKLEY = 0, 1, 2, 3
+PURPOSE_INIT, PURPOSE_STEP = 1, 2
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C sources into ``_build/libde_oracle.so``."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-o", tmp] + srcs + ["-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        lib.or_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        lib.or_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+        lib.or_draw.restype = ctypes.c_uint32
+        lib.or_map.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+        lib.or_map.restype = ctypes.c_uint32
+        lib.or_u53.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+        lib.or_u53.restype = ctypes.c_double
+        lib.or_cr_threshold.argtypes = [ctypes.c_double]
+        lib.or_cr_threshold.restype = ctypes.c_uint64
+        lib.or_mutant_indices.argtypes = [ctypes.c_uint32] * 5 + [_u32p]
+        lib.or_objective.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
+        lib.or_objective.restype = ctypes.c_double
+        lib.or_eval.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp,
+                                ctypes.c_int64, ctypes.c_int, _dp, _dp, ctypes.c_int]
+        lib.or_init_population.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_uint64, ctypes.c_uint32, _dp]
+        lib.or_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                _dp, _dp, _dp, _dp, _i32p, _i32p, _u32p, _dp, _dp, _dp, _u8p, ctypes.c_int]
+        lib.or_best.argtypes = [ctypes.c_int, _dp]
+        lib.or_best.restype = ctypes.c_int
+        lib.or_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                               ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64,
+                               ctypes.c_double, _dp, _dp, _i64p, _dp, ctypes.c_int]
+        lib.or_run.restype = ctypes.c_int64
+        _bind_extra(lib)
+        _lib = lib
+        return lib
+
+
+def _bind_extra(lib):
+    """Bindings of the ODE and MLP parts (present once their sources exist)."""
+    if hasattr(lib, "or_ode_objective"):
+        lib.or_ode_objective.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double]
+        lib.or_ode_objective.restype = ctypes.c_double
+        lib.or_ode_trajectory.argtypes = [_dp, ctypes.c_int, ctypes.c_double, _dp]
+    if hasattr(lib, "or_mlp_forward"):
+        lib.or_mlp_forward.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp,
+                                       _dp, _dp, _dp]
+        lib.or_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp,
+                                         _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.or_mlp_loss_grad.restype = ctypes.c_double
+
+
+def _p(a, t=_dp):
+    if a is None:
+        return None
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------- RNG
+def philox4x32_10(ctr, key):
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    _load().or_philox4x32_10(_p(c, _u32p), _p(k, _u32p), _p(out, _u32p))
+    return out
+
+
+def draw(seed, purpose, run_id, cand, generation, individual, d):
+    return int(_load().or_draw(seed, purpose, run_id, cand, generation, individual, d))
+
+
+def map_index(u, n):
+    return int(_load().or_map(u, n))
+
+
+def u53(a, b):
+    return float(_load().or_u53(a, b))
+
+
+def cr_threshold(cr):
+    return int(_load().or_cr_threshold(cr))
+
+
+def mutant_indices(w0, w1, w2, i, np_):
+    r = np.zeros(3, dtype=np.uint32)
+    _load().or_mutant_indices(w0, w1, w2, i, np_, _p(r, _u32p))
+    return tuple(int(v) for v in r)
+
+
+# ----------------------------------------------------------------------------- objectives
+def objective(obj, x, o=None, M=None, scale=1.0):
+    """f(x) and the magnitude sum of its terms for one point."""
+    x = _f64(x)
+    d = x.shape[0]
+    o, M = _f64(o), _f64(M)
+    sabs = ctypes.c_double(0.0)
+    f = _load().or_objective(obj, d, _p(o), _p(M), scale, _p(x), ctypes.byref(sabs))
+    return f, sabs.value
+
+
+def evaluate(obj, X, o=None, M=None, scale=1.0, threads=1):
+    """f and magnitude sums for every row of X."""
+    X = _f64(X)
+    n, d = X.shape
+    f = np.zeros(n)
+    sabs = np.zeros(n)
+    _load().or_eval(obj, d, _p(_f64(o)), _p(_f64(M)), scale, _p(X), d, n, _p(f), _p(sabs), threads)
+    return f, sabs
+
+
+# ----------------------------------------------------------------------------- DE
+def init_population(np_, d, lo, hi, seed, run_id=0):
+    X = np.zeros((np_, d))
+    _load().or_init_population(np_, d, lo, hi, seed, run_id, _p(X))
+    return X
+
+
+def step(X, fX, F, CR, lo, hi, obj, o, M, seed, generation, run_id=0, scale=1.0, threads=1):
+    """One synchronous generation; returns a dict with the next population and
+    every intermediate (indices, j_rand, crossover mask, trials, f_trial,
+    magnitude sums, accept flags)."""
+    X = _f64(X)
+    fX = _f64(fX)
+    np_, d = X.shape
+    nw = (d + 31) // 32
+    out = dict(
+        X_next=np.zeros_like(X), f_next=np.zeros(np_), idx=np.zeros((np_, 3), dtype=np.int32),
+        jrand=np.zeros(np_, dtype=np.int32), mask=np.zeros((np_, nw), dtype=np.uint32),
+        trial=np.zeros_like(X), f_trial=np.zeros(np_), sabs_trial=np.zeros(np_),
+        accept=np.zeros(np_, dtype=np.uint8))
+    _load().or_step(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), scale, seed, run_id, generation,
+                    _p(X), _p(fX), _p(out["X_next"]), _p(out["f_next"]), _p(out["idx"], _i32p),
+                    _p(out["jrand"], _i32p), _p(out["mask"], _u32p), _p(out["trial"]), _p(out["f_trial"]),
+                    _p(out["sabs_trial"]), _p(out["accept"], _u8p), threads)
+    return out
+
+
+def best(f):
+    f = _f64(f)
+    return int(_load().or_best(f.shape[0], _p(f)))
+
+
+def run(np_, d, F, CR, lo, hi, obj, o, M, seed, max_generations, max_evals=0, target_error=1e-8,
+        run_id=0, scale=1.0, threads=1, trace=False):
+    """A whole run; returns (X, f, generations, evals, best_trace or None)."""
+    X = np.zeros((np_, d))
+    f = np.zeros(np_)
+    ev = ctypes.c_int64(0)
+    tr = np.full(max_generations + 1, np.nan) if trace else None
+    g = _load().or_run(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), scale, seed, run_id,
+                       max_generations, max_evals, target_error, _p(X), _p(f), ctypes.byref(ev), _p(tr),
+                       threads)
+    return X, f, int(g), int(ev.value), (tr[: g + 1] if trace else None)
