@@ -1,0 +1,320 @@
+"""Throughput of the DE/rand/1/bin generation step on GB300.
+
+Workload (the rotated-shifted Rastrigin configuration): NP = 1024, D = 100,
+F = 0.5, CR = 0.9, bounds [-100, 100]^D, shift o ~ U[-80, 80]^D, M orthogonal
+from the QR of a seeded Gaussian, 3000 generations.  One "step" is one whole
+run of that workload: initialise + evaluate the population, then 3000
+generations of mutation, crossover, repair, rotation + objective and
+selection, with the best-so-far record and stop test after each generation.
+
+Metric: trial evaluations per second (NP x generations per run / time).
+
+* value          device time (CUDA events on the library's stream) summed
+                 over the K timed runs; inputs resident in HBM; L2 flushed
+                 (a 512 MiB write) between runs.
+* e2e            the same runs through the C ABI with host inputs: de_init
+                 from pinned host shift/rotation, de_run, de_get_best back to
+                 host, de_destroy, wall clock.
+* roofline       the dominant kernel's algorithmic work per launch over its
+                 average launch time (events around the generations only).
+* cpu_baseline   the FP64 CPU oracle on a bounded sample of the same
+                 workload, timed on this host's cores.
+
+``--impl reference`` times the oracle itself as the reference arm.
+Multi-GPU (torchrun): every rank runs its own independent replica of the
+workload (run_id = rank), no collective on the data path ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NP, D, F, CR, GENS, SEED = 1024, 100, 0.5, 0.9, 3000, 1
+OBJ_RASTRIGIN = 1
+WORKLOAD = "rotated-shifted Rastrigin NP=1024 D=100 F=0.5 CR=0.9 3000 generations"
+METRIC = "trial evals/sec (DE/rand/1/bin, D=100, NP=1024, rotated-shifted Rastrigin)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16x3", "tf32x3"])
+    p.add_argument("--generations", type=int, default=GENS)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if "Active" in s[4 + k] and "Not" not in s[4 + k]:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------------------------- problem
+def make_problem():
+    from paper_2405_16551_gb300 import problems
+
+    return problems.shift(D, seed=SEED), problems.rotation(D, seed=SEED)
+
+
+def cpu_baseline(o, M, budget_s=12.0):
+    """The FP64 oracle, as it stands, on all host cores (the paper's
+    master-slave form: evaluations spread over a thread pool), on a bounded
+    sample: a first run of a few generations sizes a second run to about
+    budget_s seconds of CPU time."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    oracle.build()
+
+    def timed(gens):
+        t0 = time.perf_counter()
+        _, _, g, _, _ = oracle.run(NP, D, F, CR, -100.0, 100.0, OBJ_RASTRIGIN, o, M, seed=SEED,
+                                   max_generations=gens, target_error=1e-8, threads=cores)
+        return g, time.perf_counter() - t0
+
+    g0, t0 = timed(4)
+    per_gen = max(t0 / max(g0, 1), 1e-4)
+    gens = int(min(GENS, max(4, budget_s / per_gen)))
+    g, dt = timed(gens)
+    return {"value": NP * g / dt, "unit": "trial evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"init + {g} of the {GENS} generations of the same workload (NP={NP}, D={D}), FP64, "
+                      f"OpenMP over individuals for evaluation; {dt:.2f} s"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    o, M = make_problem()
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    sample_gens = 4
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.run(NP, D, F, CR, -100.0, 100.0, OBJ_RASTRIGIN, o, M, seed=SEED, max_generations=sample_gens,
+                   target_error=1e-8, threads=cores)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = NP * sample_gens * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trial evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": f"init + {sample_gens} generations (bounded CPU sample)",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "trial evals/s", "cores": cores, "kind": "oracle",
+                             "sample": f"init + {sample_gens} generations per step, FP64, OpenMP over individuals"},
+            "e2e": {"value": value, "unit": "trial evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- gb300 arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    from paper_2405_16551_gb300 import capi
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prec_name = args.precision
+    if prec_name == "auto":
+        prec_name = os.environ.get("DE_BENCH_PRECISION", "fp64")
+    prec = {"fp64": capi.DE_PREC_FP64, "bf16x3": capi.DE_PREC_BF16X3, "tf32x3": capi.DE_PREC_TF32X3}[prec_name]
+    G = args.generations
+    o, M = make_problem()
+    stream = torch.cuda.current_stream()
+    cfg = capi.make_config(NP, D, f=F, cr=CR, objective=OBJ_RASTRIGIN, shift=o, rot=M, seed=SEED, run_id=rank,
+                           precision=prec, target_error=1e-8, max_generations=G)
+    h = capi.de_init(cfg, stream=stream.cuda_stream)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        capi.de_reset(h)
+        if evs is not None:
+            evs[1].record(stream)
+        capi.de_step(h, G)
+        if evs is not None:
+            evs[2].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        one_step(events[k])
+        flush.zero_()  # evict the population from L2 between runs (outside the events)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[2]) for e in events]
+    gen_ms = [e[1].elapsed_time(e[2]) for e in events]
+    dev_ms = sum(step_ms)
+    gen_total_ms = sum(gen_ms)
+    if dist is not None:
+        t = torch.tensor([dev_ms, gen_total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms, gen_total_ms = t.tolist()
+    best = capi.de_get_best(h)
+    capi.de_destroy(h)
+    trials_per_step = NP * G
+    value = world * trials_per_step * args.steps / (dev_ms / 1e3)
+
+    # e2e through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        o_pin = torch.from_numpy(o).pin_memory()
+        m_pin = torch.from_numpy(np.ascontiguousarray(M)).pin_memory()
+        cfg_e = capi.make_config(NP, D, f=F, cr=CR, objective=OBJ_RASTRIGIN, shift=o_pin.numpy(), rot=m_pin.numpy(),
+                                 seed=SEED, run_id=rank, precision=prec, target_error=1e-8, max_generations=G)
+        times = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            he = capi.de_init(cfg_e, stream=stream.cuda_stream)
+            capi.de_run(he)
+            capi.de_get_best(he)
+            capi.de_destroy(he)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t0)
+            flush.zero_()
+        tot = sum(times)
+        if dist is not None:
+            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = t.item()
+        e2e = {"value": world * trials_per_step * args.steps / tot, "unit": "trial evals/s",
+               "h2d_bytes_per_step": 8 * (D + D * D), "d2h_bytes_per_step": 8 * (D + 1) + 48}
+
+    # roofline of the dominant kernel (the generation kernel(s))
+    avg_gen_us = 1e3 * gen_total_ms / (args.steps * G)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    if prec == capi.DE_PREC_FP64:
+        flops = NP * (2.0 * D * D + 9.0 * D)
+        achieved = flops / (avg_gen_us * 1e-6) / 1e12
+        roof = {"bound": "alu", "kernel": "k_gen_fp64", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25, "traffic": None,
+                "peak_source": "nominal GB300 FP64 rate 1.25 TFLOP/s (a DFMA loop measured 1.20 on this part)"}
+    else:
+        byts = NP * (2 * 8 * D + 16)
+        achieved = byts / (avg_gen_us * 1e-6) / 1e9
+        pk = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "kernel": "generation (trial + fitness kernels)", "achieved": achieved, "peak": pk,
+                "unit": "GB/s", "frac": achieved / pk, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
+    roof["avg_launch_us"] = avg_gen_us
+
+    line = {"metric": METRIC, "value": value, "unit": "trial evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16x3->f32 (+f64 selection band)",
+                                           "tf32x3": "tf32x3->f32 (+f64 selection band)"}[prec_name],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": prec_name, "generations": G,
+                       "l2": "flushed between runs (512 MiB write)", "parallelism": f"replicas x{world}"},
+            "generations_per_s": world * G * args.steps / (dev_ms / 1e3), "best_f_last_run": best["best_f"],
+            "wall_s": t_wall, "e2e": e2e, "roofline": roof, "clocks": clk,
+            "gpu_launches": args.steps * (3 + G * (1 if prec == capi.DE_PREC_FP64 else 2))}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(o, M)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * de.h -- C ABI of the GB300 (sm_103a) DE/rand/1/bin library, libde_gb300.so.
+ *
+ * The method is differential evolution as stated in "GPU Based Differential
+ * Evolution: New Insights and Comparative Study" (arXiv 2405.16551):
+ *   - a population of NP individuals, each a D-dimensional real vector,
+ *     initialised uniformly inside the bounds and evaluated (Sec. 2);
+ *   - per target i, the DE/rand/1 mutant y_i = x_r1 + F (x_r2 - x_r3) with
+ *     r1, r2, r3 mutually distinct and different from i (Sec. 2, Eq. 2);
+ *   - binomial crossover: trial coordinate j is the mutant's when
+ *     rand_j <= CR or j = j_rand, else the target's (Sec. 2, Eq. 3);
+ *   - greedy selection: the trial replaces the target when its objective is
+ *     no worse (Sec. 2, Selection; Sec. 6.2.5);
+ *   - objectives are minimised over [-100, 100]^D after a shift y = x - o and
+ *     a rotation z = M y (Sec. 7.3.1); runs stop at error 1e-8 or at the
+ *     function-evaluation budget (Sec. 7.3.4).
+ *
+ * Conventions (every entry point):
+ *   - The return value is a de_status.  No C++ exception crosses this
+ *     boundary and the library never aborts, traps or exits the process.
+ *     On any status other than DE_OK, de_last_error(h) (or
+ *     de_last_error(NULL) when no handle exists) gives a one-line message.
+ *   - Output pointers are written only when the call returns DE_OK.
+ *   - A handle owns all device memory it allocates.  It issues all of its
+ *     work on the CUDA stream given to de_init / de_init_batch (NULL = the
+ *     legacy default stream).  Calls that return host data synchronise that
+ *     stream; de_step and de_eval only enqueue work.
+ *   - A handle may be used by one host thread at a time.
+ *   - Host arrays are dense row-major; "host" and "device" below say which
+ *     address space a pointer must be in.
+ *   - Population rows are stored on the device with a padded row stride
+ *     (D rounded up to a multiple of 4 doubles); the host-facing calls below
+ *     take and return dense rows of D values.
+ *   - Random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *     the seed, with the counter built from (draw block, individual,
+ *     generation, run_id and purpose), so results do not depend on launch
+ *     shapes and a CPU program can draw the same numbers.
+ */
+#ifndef DE_GB300_H
+#define DE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DE_API __attribute__((visibility("default")))
+#else
+#define DE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DE_OK = 0,
+    DE_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
+    DE_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
+    DE_ERR_OOM = 3,         /* device or host allocation failed */
+    DE_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    DE_ERR_NONFINITE = 5,   /* a non-finite value where a finite one is required */
+    DE_ERR_STATE = 6,       /* the call does not fit the handle's state */
+    DE_ERR_IO = 7,          /* checkpoint file could not be read or written, or is corrupt */
+    DE_ERR_UNSUPPORTED = 8  /* the device or configuration is not supported */
+} de_status;
+
+/* Objectives (Sec. 7.3.1 stand-ins; minimum 0 at x = o):
+ *   SPHERE      sum z_j^2
+ *   RASTRIGIN   sum (z_j^2 - 10 cos(2 pi z_j) + 10)
+ *   ROSENBROCK  sum_{j<D-1} 100 (t_{j+1} - t_j^2)^2 + (t_j - 1)^2,  t = z + 1
+ *   ACKLEY      20 + e - 20 exp(-0.2 sqrt(sum z_j^2 / D)) - exp(sum cos(2 pi z_j) / D)
+ *   ODE         fit of a 10-oscillator damped chain (D = 20) */
+typedef enum {
+    DE_OBJ_SPHERE = 0,
+    DE_OBJ_RASTRIGIN = 1,
+    DE_OBJ_ROSENBROCK = 2,
+    DE_OBJ_ACKLEY = 3,
+    DE_OBJ_ODE = 4
+} de_objective;
+
+/* Arithmetic of the rotation z = M y and of the objective terms.
+ *   FP64     DFMA on CUDA cores, FP64 terms.
+ *   BF16X3   tcgen05 tensor cores: y and M split into bf16 high and low parts,
+ *            z = yh Mh + yh Ml + yl Mh accumulated in FP32 (TMEM); FP32 terms.
+ *   TF32X3   the same with tf32 parts.
+ * In BF16X3/TF32X3 the selection comparison is redone in FP64 when the two
+ * fitness values are within the split-precision tolerance of each other or
+ * below the near-optimum threshold, and the best-so-far record is FP64. */
+typedef enum {
+    DE_PREC_FP64 = 0,
+    DE_PREC_BF16X3 = 1,
+    DE_PREC_TF32X3 = 2
+} de_precision;
+
+typedef enum {
+    DE_STOP_NONE = 0,        /* still running */
+    DE_STOP_TARGET = 1,      /* best f < target_error (f* = 0) */
+    DE_STOP_EVALS = 2,       /* evaluations >= max_evals */
+    DE_STOP_GENERATIONS = 3  /* generations == max_generations */
+} de_stop_reason;
+
+/* One run's configuration.  Ranges are checked by de_init. */
+typedef struct {
+    int32_t np;               /* population size, 4 <= np <= 2^20 (Eq. 2 needs 3 donors besides i) */
+    int32_t d;                /* dimension, 1 <= d <= 4096 (ODE: d == 20) */
+    double f;                 /* differential weight F, 0 <= F <= 2 (Eq. 2) */
+    double cr;                /* crossover rate C_R, 0 <= CR <= 1 (Eq. 3) */
+    double lo, hi;            /* box bounds, finite, lo < hi; the paper's range is [-100, 100] */
+    int32_t objective;        /* de_objective */
+    double scale;             /* y = (x - o) * scale; 1.0 keeps the search range (Sec. 7.3.1) */
+    const double* shift;      /* host, d values of o, or NULL for o = 0; copied by de_init */
+    const double* rot;        /* host, d*d row-major M (z = M y), or NULL for no rotation; copied */
+    uint64_t seed;            /* Philox key */
+    uint32_t run_id;          /* Philox stream id, < 2^20; distinct runs of one seed differ here */
+    int32_t precision;        /* de_precision */
+    double target_error;      /* stop once best f < target_error (Sec. 7.3.4 uses 1e-8); <= 0 disables */
+    int64_t max_evals;        /* stop once evaluations >= max_evals, counting the initial NP; 0 = none */
+    int64_t max_generations;  /* stop after this many generations (de_run); >= 0 */
+    int32_t debug_capture;    /* nonzero: keep indices, masks, trials, f_trial and flags of the last generation */
+} de_config;
+
+/* Result of de_run for one run. */
+typedef struct {
+    double best_f;            /* FP64 fitness of the best individual */
+    int32_t best_index;       /* its index (lowest index on ties) */
+    int32_t stop_reason;      /* de_stop_reason */
+    int64_t generations;      /* generations run so far */
+    int64_t evals;            /* objective evaluations so far, NP (1 + generations) */
+    double seconds;           /* wall time of the de_run call */
+} de_result;
+
+/* Host buffers for de_get_debug, each sized for the run's np and d
+ * (nw = ceil(d / 32)); any pointer may be NULL to skip that field. */
+typedef struct {
+    int32_t* idx;             /* np*3: r1, r2, r3 per target */
+    int32_t* jrand;           /* np */
+    uint32_t* mask;           /* np*nw: bit j%32 of word j/32 set when coordinate j was crossed */
+    double* trial;            /* np*d: trial vectors after bound repair */
+    double* f_trial;          /* np: fitness of each trial (FP64 when the FP64 band re-evaluated it) */
+    uint8_t* accept;          /* np: 1 when the trial replaced the target */
+    uint8_t* fp64_checked;    /* np: 1 when the selection was decided on FP64 fitness values */
+} de_debug;
+
+typedef struct de_handle de_handle;
+
+/* Version string of the library ("de_gb300 <major>.<minor> sm_103a"). */
+DE_API const char* de_version(void);
+
+/* Create a handle for one run: validate cfg, allocate device buffers on the
+ * stream, copy shift and rotation, initialise the population (Sec. 2:
+ * x_ij = lo + (hi - lo) u_ij with u_ij from the INIT stream) and evaluate it.
+ * cuda_stream: a cudaStream_t or NULL.  *out receives the handle.
+ * Errors: DE_ERR_INVALID_ARG (cfg out of range, out == NULL), DE_ERR_OOM,
+ * DE_ERR_CUDA, DE_ERR_UNSUPPORTED (not a compute-capability 10.3 device). */
+DE_API de_status de_init(const de_config* cfg, void* cuda_stream, de_handle** out);
+
+/* Create a handle for nruns independent runs (each with its own np, d,
+ * objective, shift, rotation, seed and run_id) that advance together: one
+ * generation of the handle is one generation of every run that has not
+ * stopped, in a single set of launches.  Runs must share precision.
+ * Errors as de_init; DE_ERR_INVALID_ARG when nruns < 1 or any cfg is invalid. */
+DE_API de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream, de_handle** out);
+
+/* Re-initialise run `run` (or every run when run == -1) as de_init did:
+ * population from the INIT stream, evaluation, counters and best record
+ * reset.  Enqueued on the handle's stream; allocates nothing. */
+DE_API de_status de_reset(de_handle* h, int32_t run);
+
+/* Enqueue `generations` generations (>= 0) on the handle's stream, with no
+ * stop test other than the per-run stop flags the device sets itself.
+ * Generation g builds every trial from the generation g-1 population
+ * (synchronous replacement).  Returns once the work is enqueued. */
+DE_API de_status de_step(de_handle* h, int64_t generations);
+
+/* Run until every run has stopped (target, evaluation budget or
+ * max_generations), checking the stop flags between CUDA-graph launches.
+ * out: host array of nruns results (may be NULL).  Synchronises. */
+DE_API de_status de_run(de_handle* h, de_result* out);
+
+/* Evaluate n rows with run `run`'s objective, shift, rotation and precision.
+ * x_dev: device, n rows of d doubles with row stride ld (>= d) doubles.
+ * f_dev: device, n doubles.  Both caller-owned; enqueued on the stream. */
+DE_API de_status de_eval(de_handle* h, int32_t run, const double* x_dev, int64_t ld, int32_t n, double* f_dev);
+
+/* Copy run `run`'s current population (np*d, host) and fitness (np, host)
+ * out; either pointer may be NULL.  Synchronises. */
+DE_API de_status de_get_population(de_handle* h, int32_t run, double* x_host, double* f_host);
+
+/* Replace run `run`'s population and fitness with host arrays (np*d, np).
+ * f_host may be NULL, in which case the population is evaluated on the
+ * device.  Resets that run's stop flag and recomputes its best record; the
+ * generation counter is kept. */
+DE_API de_status de_set_population(de_handle* h, int32_t run, const double* x_host, const double* f_host);
+
+/* Set the generation counter of run `run` (the next de_step runs g + 1). */
+DE_API de_status de_set_generation(de_handle* h, int32_t run, int64_t generation);
+
+/* Best record of run `run`: best_f (FP64), its index, a copy of its vector
+ * (host, d doubles, may be NULL), and generation/evaluation counters. */
+DE_API de_status de_get_best(de_handle* h, int32_t run, double* best_f, int32_t* best_index, double* best_x,
+                      int64_t* generations, int64_t* evals, int32_t* stop_reason);
+
+/* Copy the last generation's debug capture of run `run` (cfg.debug_capture
+ * must have been set).  Synchronises. */
+DE_API de_status de_get_debug(de_handle* h, int32_t run, const de_debug* out);
+
+/* Number of runs in the handle, and run `run`'s np and d. */
+DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d, int32_t* nruns);
+
+/* Write the full state of every run (population, fitness, counters, best
+ * records, problem data) to `path`, with a CRC32 over the payload; de_load
+ * restores it into a handle created with the same configurations.
+ * Errors: DE_ERR_IO (open/write/read failure, bad magic, CRC mismatch),
+ * DE_ERR_STATE (shapes differ from the handle's). */
+DE_API de_status de_save(de_handle* h, const char* path);
+DE_API de_status de_load(de_handle* h, const char* path);
+
+/* Destroy the handle and free its device memory (h may be NULL). */
+DE_API de_status de_destroy(de_handle* h);
+
+/* Last error message of h (or of the last failed handle-less call when h is
+ * NULL); an empty string after success.  Owned by the library. */
+DE_API const char* de_last_error(de_handle* h);
+
+/* Name of a status code. */
+DE_API const char* de_status_string(de_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DE_GB300_H */

@@ -95,8 +95,15 @@ double or_u53(uint32_t a, uint32_t b)
 /* ------------------------------------------------------------------------- */
 /* Objectives (Sec. 7.3.1): y = (x - o) * scale, z = M y (M row-major D x D, */
 /* NULL means no rotation), then a basic function of z whose minimum 0 is at  */
-/* z = 0, i.e. at x = o.  *sabs receives the sum of the magnitudes of the     */
-/* terms before cancellation, the scale used for fitness tolerances.          */
+/* z = 0, i.e. at x = o.                                                      */
+/*                                                                            */
+/* *sabs receives the scale S of the fitness tolerance tau = rel (|f| + S):  */
+/* the sum of the magnitudes of the terms before cancellation, plus the      */
+/* first-order effect of rounding the inputs of the terms,                   */
+/* sum_j |df/dz_j| (G_j + |z_j|) with G_j = sum_k |M_jk y_k| (the size of    */
+/* the dot product that forms z_j), and for Rosenbrock also |df/dt_j| |t_j|  */
+/* for the rounding of t = z + 1.  A correct evaluation in another summation  */
+/* order differs from this one by a small multiple of eps * S.                */
 /* ------------------------------------------------------------------------- */
 enum { OR_SPHERE = 0, OR_RASTRIGIN = 1, OR_ROSENBROCK = 2, OR_ACKLEY = 3 };
 
@@ -105,28 +112,36 @@ double or_objective(int obj, int d, const double* o, const double* M, double sca
 {
     double* y = (double*)malloc(sizeof(double) * (size_t)d);
     double* z = (double*)malloc(sizeof(double) * (size_t)d);
-    const double two_pi = 2.0 * 3.14159265358979323846;
+    double* G = (double*)malloc(sizeof(double) * (size_t)d);
+    const double pi = 3.14159265358979323846, two_pi = 2.0 * pi;
     double f = 0.0, s = 0.0;
     for (int k = 0; k < d; ++k)
         y[k] = (x[k] - (o ? o[k] : 0.0)) * scale;
     for (int j = 0; j < d; ++j) {
         if (M) {
-            double acc = 0.0;
-            for (int k = 0; k < d; ++k)
+            double acc = 0.0, mag = 0.0;
+            for (int k = 0; k < d; ++k) {
                 acc += M[(size_t)j * d + k] * y[k];
+                mag += fabs(M[(size_t)j * d + k] * y[k]);
+            }
             z[j] = acc;
+            G[j] = mag;
         } else {
             z[j] = y[j];
+            G[j] = fabs(y[j]);
         }
     }
     if (obj == OR_SPHERE) {
         for (int j = 0; j < d; ++j) f += z[j] * z[j];
         s = f;
+        for (int j = 0; j < d; ++j) s += 2.0 * fabs(z[j]) * (G[j] + fabs(z[j]));
     } else if (obj == OR_RASTRIGIN) {
         for (int j = 0; j < d; ++j) {
             double c = cos(two_pi * z[j]);
             f += z[j] * z[j] - 10.0 * c + 10.0;
             s += z[j] * z[j] + 10.0 * fabs(c) + 10.0;
+            double g = 2.0 * fabs(z[j]) + 20.0 * pi * fabs(sin(two_pi * z[j]));
+            s += g * (G[j] + fabs(z[j]));
         }
     } else if (obj == OR_ROSENBROCK) {
         /* evaluated at t = z + 1 so that the minimum sits at z = 0 (x = o) */
@@ -134,8 +149,13 @@ double or_objective(int obj, int d, const double* o, const double* M, double sca
             double t0 = z[j] + 1.0, t1 = z[j + 1] + 1.0;
             double a = t1 - t0 * t0, b = t0 - 1.0;
             f += 100.0 * a * a + b * b;
+            s += 100.0 * a * a + b * b;
+            /* d/dt0 and d/dt1 of this term, times the sizes of t0, t1 and z */
+            double g0 = 400.0 * fabs(a) * fabs(t0) + 2.0 * fabs(b);
+            double g1 = 200.0 * fabs(a);
+            s += g0 * (G[j] + fabs(z[j]) + fabs(t0)) + g1 * (G[j + 1] + fabs(z[j + 1]) + fabs(t1));
+            s += 200.0 * fabs(a) * t0 * t0;
         }
-        s = f;
     } else if (obj == OR_ACKLEY) {
         double s1 = 0.0, s2 = 0.0, s2abs = 0.0;
         for (int j = 0; j < d; ++j) {
@@ -144,16 +164,25 @@ double or_objective(int obj, int d, const double* o, const double* M, double sca
             s2 += c;
             s2abs += fabs(c);
         }
-        double e1 = exp(-0.2 * sqrt(s1 / d));
+        double r = sqrt(s1 / d);
+        double e1 = exp(-0.2 * r);
         double e2 = exp(s2 / d);
         f = 20.0 + exp(1.0) - 20.0 * e1 - e2;
         s = 20.0 + exp(1.0) + 20.0 * e1 + exp(s2abs / d);
+        for (int j = 0; j < d; ++j) {
+            double g = (r > 0.0 ? 4.0 * e1 * fabs(z[j]) / (d * r) : 0.0)
+                     + two_pi / d * fabs(sin(two_pi * z[j])) * e2;
+            s += g * (G[j] + fabs(z[j]));
+        }
+        /* the square root amplifies the rounding of s1 near the optimum */
+        s += (r > 0.0 ? 2.0 * e1 * r : 0.0);
     } else {
         f = NAN;
         s = NAN;
     }
     free(y);
     free(z);
+    free(G);
     if (sabs) *sabs = s;
     return f;
 }

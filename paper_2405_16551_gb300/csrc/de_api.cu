@@ -1,0 +1,874 @@
+// de_api.cu -- the C ABI of include/de.h: handle, device memory, launches,
+// CUDA graphs, autotuning, checkpoints.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <sys/stat.h>
+
+#include "de.h"
+#include "de_common.cuh"
+#include "de_internal.cuh"
+#include "de_kernels.h"
+
+using namespace de;
+
+struct de_handle {
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  int device = 0;
+  int nruns = 0;
+  int prec = DE_PREC_FP64;
+  std::vector<de_config> cfg;
+  std::vector<RunDesc> run;  // host copy of the descriptors
+  RunDesc* d_run = nullptr;
+  int2* d_items = nullptr;  // FP64 generation kernel work list
+  int nitems = 0;
+  int rows = 8;             // rows per tile of the FP64 generation kernel
+  int threads = 256;
+  size_t smem_gen = 0;
+  TcPlan tc;                // split-precision plan (de_tc.cu)
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  RunState* h_state = nullptr;  // pinned mirror of the device states
+  cudaGraphExec_t graph = nullptr;
+  int graph_gens = 0;
+  std::string err;
+};
+
+static thread_local std::string g_err;
+static const char* kVersion = "de_gb300 1.0 sm_103a";
+
+// ---------------------------------------------------------------- helpers
+static de_status fail(de_handle* h, de_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  g_err = msg;
+  return s;
+}
+
+#define DE_CUDA(h, call)                                                                          \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? DE_ERR_OOM : DE_ERR_CUDA,                \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                            \
+  } while (0)
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static de_status validate(const de_config& c, int idx, std::string& why) {
+  char b[256];
+  auto bad = [&](const char* what) {
+    snprintf(b, sizeof b, "config %d: %s", idx, what);
+    why = b;
+    return DE_ERR_INVALID_ARG;
+  };
+  if (c.np < 4 || c.np > (1 << 20)) return bad("np must be in [4, 2^20] (three distinct donors besides the target)");
+  if (c.d < 1 || c.d > 4096) return bad("d must be in [1, 4096]");
+  if (!(c.f >= 0.0 && c.f <= 2.0)) return bad("F must be in [0, 2]");
+  if (!(c.cr >= 0.0 && c.cr <= 1.0)) return bad("CR must be in [0, 1]");
+  if (!std::isfinite(c.lo) || !std::isfinite(c.hi) || !(c.lo < c.hi)) return bad("bounds must be finite with lo < hi");
+  if (c.objective < DE_OBJ_SPHERE || c.objective > DE_OBJ_ACKLEY) return bad("objective out of range");
+  if (!std::isfinite(c.scale) || c.scale == 0.0) return bad("scale must be finite and nonzero");
+  if (c.run_id >= (1u << 20)) return bad("run_id must be < 2^20");
+  if (c.precision < DE_PREC_FP64 || c.precision > DE_PREC_TF32X3) return bad("precision out of range");
+  if (c.max_evals < 0 || c.max_generations < 0) return bad("max_evals and max_generations must be >= 0");
+  if (!std::isfinite(c.target_error) && !(c.target_error < 0)) return bad("target_error must be finite");
+  if (c.shift)
+    for (int j = 0; j < c.d; ++j)
+      if (!std::isfinite(c.shift[j])) return bad("shift has a non-finite entry");
+  if (c.rot)
+    for (size_t k = 0; k < (size_t)c.d * c.d; ++k)
+      if (!std::isfinite(c.rot[k])) return bad("rotation has a non-finite entry");
+  return DE_OK;
+}
+
+// Shared memory of one FP64 generation CTA for `rows` rows of stride dp.
+static size_t gen_smem(int rows, int dp, bool rotate) { return (size_t)(rotate ? 3 : 2) * rows * dp * sizeof(double); }
+
+static de_status build_items(de_handle* h) {
+  std::vector<int2> items;
+  size_t smem = 0;
+  for (int r = 0; r < h->nruns; ++r) {
+    RunDesc& R = h->run[r];
+    int rows = h->rows;
+    while (rows > 1 && gen_smem(rows, R.dp, R.rotate) > 200 * 1024) rows >>= 1;
+    R.rows = rows;
+    R.ntiles = (R.np + rows - 1) / rows;
+    smem = std::max(smem, gen_smem(rows, R.dp, R.rotate));
+    for (int t = 0; t < R.ntiles; ++t) items.push_back(make_int2(r, t));
+  }
+  h->smem_gen = smem;
+  h->nitems = (int)items.size();
+  if (h->d_items) cudaFree(h->d_items);
+  h->d_items = nullptr;
+  DE_CUDA(h, cudaMalloc(&h->d_items, items.size() * sizeof(int2)));
+  DE_CUDA(h, cudaMemcpyAsync(h->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                             h->stream));
+  return DE_OK;
+}
+
+static de_status upload_desc(de_handle* h) {
+  DE_CUDA(h, cudaMemcpyAsync(h->d_run, h->run.data(), h->run.size() * sizeof(RunDesc), cudaMemcpyHostToDevice,
+                             h->stream));
+  return DE_OK;
+}
+
+static void drop_graph(de_handle* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->graph_gens = 0;
+}
+
+// Enqueue one generation of every run (the kernels skip stopped runs).
+static de_status launch_generation(de_handle* h, cudaStream_t s) {
+  if (h->prec == DE_PREC_FP64) {
+    k_gen_fp64_launch(h->d_run, h->d_items, h->nitems, h->threads, h->smem_gen, s);
+  } else {
+    tc_generation_launch(h->tc, h->d_run, s);
+  }
+  DE_CUDA(h, cudaGetLastError());
+  return DE_OK;
+}
+static de_status launch_generation(de_handle* h) { return launch_generation(h, h->stream); }
+
+static de_status enqueue_generations(de_handle* h, int64_t n) {
+  const int kChunk = 64;
+  if (n >= kChunk) {
+    if (!h->graph || h->graph_gens != kChunk) {
+      drop_graph(h);
+      // capture on the handle's private stream (the caller's stream may be the
+      // legacy default stream, which cannot be captured); nothing runs during
+      // capture, and the graph is then launched on the caller's stream
+      if (!h->cap_stream) DE_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      DE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      de_status s = DE_OK;
+      for (int k = 0; k < kChunk && s == DE_OK; ++k) s = launch_generation(h, h->cap_stream);
+      cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+      if (s != DE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e != cudaSuccess) return fail(h, DE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&h->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(h, DE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      h->graph_gens = kChunk;
+    }
+    while (n >= kChunk) {
+      DE_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
+      n -= kChunk;
+    }
+  }
+  for (int64_t k = 0; k < n; ++k) {
+    de_status s = launch_generation(h);
+    if (s != DE_OK) return s;
+  }
+  return DE_OK;
+}
+
+static de_status read_states(de_handle* h) {
+  // the states of all runs are one contiguous block starting at run 0's
+  DE_CUDA(h, cudaMemcpyAsync(h->h_state, h->run[0].st, h->nruns * sizeof(RunState), cudaMemcpyDeviceToHost,
+                             h->stream));
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DE_OK;
+}
+
+static de_status check_device_errors(de_handle* h) {
+  for (int r = 0; r < h->nruns; ++r) {
+    if (h->h_state[r].err & kErrTimeout) return fail(h, DE_ERR_TIMEOUT, "a device-side wait timed out (run " + std::to_string(r) + ")");
+    if (h->h_state[r].err & kErrNonFinite)
+      return fail(h, DE_ERR_NONFINITE, "every fitness of run " + std::to_string(r) + " is NaN");
+  }
+  return DE_OK;
+}
+
+// (Re)initialise run r's population from the INIT stream and evaluate it.
+static de_status init_run(de_handle* h, int r) {
+  RunDesc& R = h->run[r];
+  RunState st{};
+  st.best_idx = -1;
+  st.evals = R.np;  // the initial population counts as NP evaluations
+  DE_CUDA(h, cudaMemcpyAsync(R.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+  DE_CUDA(h, cudaMemsetAsync(R.X[0], 0, (size_t)R.np * R.dp * sizeof(double), h->stream));
+  k_init_population_launch(h->d_run, r, R.np, R.dp, h->stream);
+  k_eval_rows_launch(h->d_run, r, R.X[0], R.dp, R.np, R.dp, R.rotate, R.f[0], R.fx[0], h->stream);
+  k_best_init_launch(h->d_run, r, h->stream);
+  DE_CUDA(h, cudaGetLastError());
+  return DE_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Picks the rows per tile of the FP64 generation kernel by timing candidates
+// on the handle's own problem; results are cached in a text file keyed by
+// the problem shape.  The choice never changes results (tiling does not
+// enter the arithmetic of a trial), only speed.
+static std::string tune_cache_path() {
+  const char* p = getenv("DE_GB300_TUNE_CACHE");
+  if (p && *p) return p;
+  const char* home = getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/de_gb300_tune.txt";
+}
+
+static std::string tune_key(const de_handle* h) {
+  long long sum_np = 0, sum_d = 0;
+  for (auto& R : h->run) {
+    sum_np += R.np;
+    sum_d += (long long)R.np * R.d;
+  }
+  char b[256];
+  snprintf(b, sizeof b, "gen_fp64 runs=%d np0=%d d0=%d obj0=%d rot0=%d sumnp=%lld sumnd=%lld", h->nruns, h->run[0].np,
+           h->run[0].d, h->run[0].obj, h->run[0].rotate, sum_np, sum_d);
+  return b;
+}
+
+static bool tune_lookup(const std::string& key, int& rows) {
+  FILE* f = fopen(tune_cache_path().c_str(), "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (fgets(line, sizeof line, f)) {
+    char* bar = strchr(line, '|');
+    if (!bar) continue;
+    *bar = 0;
+    if (key == line) {
+      rows = atoi(bar + 1);
+      found = rows > 0;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+static void tune_store(const std::string& key, int rows) {
+  std::string p = tune_cache_path();
+  const size_t slash = p.find_last_of('/');
+  if (slash != std::string::npos && slash > 0) mkdir(p.substr(0, slash).c_str(), 0755);
+  FILE* f = fopen(p.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "%s|%d\n", key.c_str(), rows);
+  fclose(f);
+}
+
+static int heuristic_rows(const de_handle* h, int nsm) {
+  long long np_total = 0;
+  for (auto& R : h->run) np_total += R.np;
+  // aim for about two CTAs per SM, at most 16 rows
+  long long want = np_total / (2LL * nsm);
+  int rows = 1;
+  while (rows < 16 && rows * 2 <= want) rows *= 2;
+  return std::max(1, rows);
+}
+
+static de_status autotune_fp64(de_handle* h, int nsm) {
+  const char* env = getenv("DE_GB300_AUTOTUNE");
+  const bool enabled = !(env && env[0] == '0');
+  h->rows = heuristic_rows(h, nsm);
+  if (!enabled) return DE_OK;
+  const std::string key = tune_key(h);
+  int cached = 0;
+  if (tune_lookup(key, cached)) {
+    h->rows = cached;
+    return DE_OK;
+  }
+  // candidates are timed on the freshly initialised problem, which is then
+  // initialised again (initialisation is a pure function of the seed)
+  cudaEvent_t e0, e1;
+  DE_CUDA(h, cudaEventCreate(&e0));
+  DE_CUDA(h, cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int best_rows = h->rows;
+  std::vector<RunDesc> saved = h->run;
+  for (auto& R : h->run) {
+    R.target = 0.0;  // no stop rule while timing
+    R.max_evals = 0;
+    R.max_gens = INT64_MAX / 4;
+  }
+  de_status st_all = DE_OK;
+  for (int rows : {1, 2, 4, 8, 16}) {
+    h->rows = rows;
+    st_all = build_items(h);
+    if (st_all == DE_OK) st_all = upload_desc(h);
+    if (st_all != DE_OK) break;
+    k_configure(h->smem_gen);
+    for (int r = 0; r < h->nruns; ++r) {
+      int32_t zero = 0;
+      DE_CUDA(h, cudaMemcpyAsync(&h->run[r].st->stop, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream));
+    }
+    for (int k = 0; k < 2; ++k) launch_generation(h);
+    DE_CUDA(h, cudaEventRecord(e0, h->stream));
+    const int reps = 5;
+    for (int k = 0; k < reps; ++k) launch_generation(h);
+    DE_CUDA(h, cudaEventRecord(e1, h->stream));
+    DE_CUDA(h, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    DE_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms * 0.97f) {
+      best_ms = ms;
+      best_rows = rows;
+    }
+  }
+  for (int r = 0; r < h->nruns; ++r) {
+    // keep the tile fields, restore the stop rule
+    saved[r].rows = h->run[r].rows;
+    saved[r].ntiles = h->run[r].ntiles;
+  }
+  h->run = saved;
+  if (st_all != DE_OK) return st_all;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->rows = best_rows;
+  tune_store(key, best_rows);
+  return DE_OK;
+}
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* de_version(void) { return kVersion; }
+
+const char* de_status_string(de_status s) {
+  switch (s) {
+    case DE_OK: return "DE_OK";
+    case DE_ERR_INVALID_ARG: return "DE_ERR_INVALID_ARG";
+    case DE_ERR_CUDA: return "DE_ERR_CUDA";
+    case DE_ERR_OOM: return "DE_ERR_OOM";
+    case DE_ERR_TIMEOUT: return "DE_ERR_TIMEOUT";
+    case DE_ERR_NONFINITE: return "DE_ERR_NONFINITE";
+    case DE_ERR_STATE: return "DE_ERR_STATE";
+    case DE_ERR_IO: return "DE_ERR_IO";
+    case DE_ERR_UNSUPPORTED: return "DE_ERR_UNSUPPORTED";
+  }
+  return "DE_ERR_UNKNOWN";
+}
+
+const char* de_last_error(de_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+de_status de_destroy(de_handle* h) {
+  if (!h) return DE_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  tc_plan_free(h->tc);
+  if (h->d_items) cudaFree(h->d_items);
+  if (h->d_run) cudaFree(h->d_run);
+  if (h->arena) cudaFree(h->arena);
+  if (h->h_state) cudaFreeHost(h->h_state);
+  delete h;
+  return DE_OK;
+}
+
+de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream, de_handle** out) {
+  g_err.clear();
+  if (!out) return fail(nullptr, DE_ERR_INVALID_ARG, "out is NULL");
+  if (!cfgs || nruns < 1) return fail(nullptr, DE_ERR_INVALID_ARG, "need at least one config");
+  for (int r = 0; r < nruns; ++r) {
+    std::string why;
+    if (validate(cfgs[r], r, why) != DE_OK) return fail(nullptr, DE_ERR_INVALID_ARG, why);
+    if (cfgs[r].precision != cfgs[0].precision)
+      return fail(nullptr, DE_ERR_INVALID_ARG, "all runs of a batch must share the precision");
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, DE_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return fail(nullptr, DE_ERR_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(nullptr, DE_ERR_UNSUPPORTED, "this library is built for compute capability 10.3 (sm_103a)");
+
+  de_handle* h = new de_handle();
+  h->stream = (cudaStream_t)cuda_stream;
+  h->device = dev;
+  h->nruns = nruns;
+  h->prec = cfgs[0].precision;
+  h->cfg.assign(cfgs, cfgs + nruns);
+  for (auto& c : h->cfg) {
+    c.shift = nullptr;
+    c.rot = nullptr;
+  }
+  h->run.resize(nruns);
+
+  // ---- arena layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = align_up(off, 256);
+    size_t o = off;
+    off += std::max<size_t>(bytes, 1);
+    return o;
+  };
+  struct Offs {
+    size_t X0, X1, f0, f1, fx0, fx1, o, MT, st, bx, part, T, yn;
+    size_t dbg_idx, dbg_jrand, dbg_mask, dbg_trial, dbg_ftrial, dbg_accept, dbg_fp64;
+  };
+  std::vector<Offs> offs(nruns);
+  const size_t states_off = take((size_t)nruns * sizeof(RunState));  // one contiguous block
+  for (int r = 0; r < nruns; ++r) {
+    const de_config& c = cfgs[r];
+    const int dp = (c.d + 3) / 4 * 4;
+    const size_t pop = (size_t)c.np * dp * sizeof(double);
+    Offs& O = offs[r];
+    O.X0 = take(pop);
+    O.X1 = take(pop);
+    O.f0 = take(c.np * sizeof(double));
+    O.f1 = take(c.np * sizeof(double));
+    O.fx0 = take(c.np);
+    O.fx1 = take(c.np);
+    O.o = take(dp * sizeof(double));
+    O.MT = c.rot ? take((size_t)c.d * c.d * sizeof(double)) : 0;
+    O.st = states_off + (size_t)r * sizeof(RunState);
+    O.bx = take(dp * sizeof(double));
+    O.part = take((size_t)c.np * sizeof(BestPartial));
+    const bool split = c.precision != DE_PREC_FP64;
+    O.T = split ? take(pop) : 0;
+    O.yn = split ? take(c.np * sizeof(float)) : 0;
+    if (c.debug_capture) {
+      const int nw = (c.d + 31) / 32;
+      O.dbg_idx = take((size_t)c.np * 3 * sizeof(int32_t));
+      O.dbg_jrand = take((size_t)c.np * sizeof(int32_t));
+      O.dbg_mask = take((size_t)c.np * nw * sizeof(uint32_t));
+      O.dbg_trial = take((size_t)c.np * c.d * sizeof(double));
+      O.dbg_ftrial = take((size_t)c.np * sizeof(double));
+      O.dbg_accept = take((size_t)c.np);
+      O.dbg_fp64 = take((size_t)c.np);
+    }
+  }
+  h->arena_bytes = align_up(off, 256);
+  e = cudaMalloc(&h->arena, h->arena_bytes);
+  if (e != cudaSuccess) {
+    std::string m = std::string("cudaMalloc(") + std::to_string(h->arena_bytes) + "): " + cudaGetErrorString(e);
+    de_destroy(h);
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? DE_ERR_OOM : DE_ERR_CUDA, m);
+  }
+  auto fin = [&](de_status s) {
+    if (s != DE_OK) {
+      std::string m = h->err;
+      de_destroy(h);
+      g_err = m;
+      return s;
+    }
+    *out = h;
+    return DE_OK;
+  };
+#define TRY(x)                      \
+  do {                              \
+    de_status s_ = (x);             \
+    if (s_ != DE_OK) return fin(s_); \
+  } while (0)
+  cudaError_t ce = cudaMallocHost(&h->h_state, nruns * sizeof(RunState));
+  if (ce != cudaSuccess) return fin(fail(h, DE_ERR_OOM, "cudaMallocHost failed"));
+  ce = cudaMalloc(&h->d_run, nruns * sizeof(RunDesc));
+  if (ce != cudaSuccess) return fin(fail(h, DE_ERR_OOM, "cudaMalloc(run table) failed"));
+  ce = cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->stream);
+  if (ce != cudaSuccess) return fin(fail(h, DE_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(ce)));
+
+  std::vector<double> tmp;
+  for (int r = 0; r < nruns; ++r) {
+    const de_config& c = cfgs[r];
+    const Offs& O = offs[r];
+    RunDesc& R = h->run[r];
+    memset(&R, 0, sizeof R);
+    R.np = c.np;
+    R.d = c.d;
+    R.dp = (c.d + 3) / 4 * 4;
+    R.obj = c.objective;
+    R.F = c.f;
+    R.CR = c.cr;
+    R.lo = c.lo;
+    R.hi = c.hi;
+    R.scale = c.scale;
+    R.cr_thr = cr_threshold(c.cr);
+    R.seed = c.seed;
+    R.run_id = c.run_id;
+    R.rotate = c.rot != nullptr;
+    R.target = c.target_error;
+    R.max_evals = c.max_evals;
+    R.max_gens = c.max_generations;
+    R.prec = c.precision;
+    R.nw = (c.d + 31) / 32;
+    char* A = h->arena;
+    R.X[0] = (double*)(A + O.X0);
+    R.X[1] = (double*)(A + O.X1);
+    R.f[0] = (double*)(A + O.f0);
+    R.f[1] = (double*)(A + O.f1);
+    R.fx[0] = (uint8_t*)(A + O.fx0);
+    R.fx[1] = (uint8_t*)(A + O.fx1);
+    R.o = (const double*)(A + O.o);
+    R.MT = R.rotate ? (const double*)(A + O.MT) : nullptr;
+    R.st = (RunState*)(A + O.st);
+    R.best_x = (double*)(A + O.bx);
+    R.part = (BestPartial*)(A + O.part);
+    if (c.precision != DE_PREC_FP64) {
+      R.T = (double*)(A + O.T);
+      R.ynorm = (float*)(A + O.yn);
+    }
+    if (c.debug_capture) {
+      R.dbg_idx = (int32_t*)(A + O.dbg_idx);
+      R.dbg_jrand = (int32_t*)(A + O.dbg_jrand);
+      R.dbg_mask = (uint32_t*)(A + O.dbg_mask);
+      R.dbg_trial = (double*)(A + O.dbg_trial);
+      R.dbg_ftrial = (double*)(A + O.dbg_ftrial);
+      R.dbg_accept = (uint8_t*)(A + O.dbg_accept);
+      R.dbg_fp64 = (uint8_t*)(A + O.dbg_fp64);
+    }
+    if (c.shift) {
+      ce = cudaMemcpyAsync((void*)R.o, c.shift, c.d * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+      if (ce != cudaSuccess) return fin(fail(h, DE_ERR_CUDA, std::string("copy shift: ") + cudaGetErrorString(ce)));
+    }
+    if (c.rot) {
+      tmp.resize((size_t)c.d * c.d);
+      for (int j = 0; j < c.d; ++j)
+        for (int k = 0; k < c.d; ++k) tmp[(size_t)k * c.d + j] = c.rot[(size_t)j * c.d + k];
+      ce = cudaMemcpyAsync((void*)R.MT, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);  // tmp is reused
+      if (ce != cudaSuccess) return fin(fail(h, DE_ERR_CUDA, std::string("copy rotation: ") + cudaGetErrorString(ce)));
+      double rn = 0.0;
+      for (int j = 0; j < c.d; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < c.d; ++k) s += c.rot[(size_t)j * c.d + k] * c.rot[(size_t)j * c.d + k];
+        rn = std::max(rn, std::sqrt(s));
+      }
+      R.rownorm = (float)rn;
+    } else {
+      R.rownorm = 1.0f;
+    }
+  }
+  if (h->prec != DE_PREC_FP64) TRY(tc_plan_build(h->tc, h->run, cfgs, h->prec, h->stream, h->err));
+  TRY(build_items(h));
+  TRY(upload_desc(h));
+  k_configure(h->smem_gen);
+  for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
+  if (h->prec == DE_PREC_FP64) {
+    TRY(autotune_fp64(h, prop.multiProcessorCount));
+    TRY(build_items(h));
+    TRY(upload_desc(h));
+    k_configure(h->smem_gen);
+    for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
+  }
+  ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return fin(fail(h, DE_ERR_CUDA, std::string("init: ") + cudaGetErrorString(ce)));
+#undef TRY
+  return fin(DE_OK);
+}
+
+de_status de_init(const de_config* cfg, void* cuda_stream, de_handle** out) {
+  if (!cfg) return fail(nullptr, DE_ERR_INVALID_ARG, "cfg is NULL");
+  return de_init_batch(cfg, 1, cuda_stream, out);
+}
+
+de_status de_reset(de_handle* h, int32_t run) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (run < -1 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
+  h->err.clear();
+  for (int r = (run < 0 ? 0 : run); r < (run < 0 ? h->nruns : run + 1); ++r) {
+    de_status s = init_run(h, r);
+    if (s != DE_OK) return s;
+  }
+  return DE_OK;
+}
+
+de_status de_step(de_handle* h, int64_t generations) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (generations < 0) return fail(h, DE_ERR_INVALID_ARG, "generations must be >= 0");
+  h->err.clear();
+  return enqueue_generations(h, generations);
+}
+
+de_status de_run(de_handle* h, de_result* out) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  h->err.clear();
+  auto t0 = std::chrono::steady_clock::now();
+  de_status s = read_states(h);
+  if (s != DE_OK) return s;
+  int64_t chunk = 64;
+  for (;;) {
+    bool all = true;
+    int64_t left = 0;
+    for (int r = 0; r < h->nruns; ++r)
+      if (!h->h_state[r].stop) {
+        all = false;
+        left = std::max<int64_t>(left, h->run[r].max_gens - h->h_state[r].gen);
+      }
+    if (all) break;
+    s = enqueue_generations(h, std::max<int64_t>(1, std::min<int64_t>(chunk, left)));
+    if (s != DE_OK) return s;
+    s = read_states(h);
+    if (s != DE_OK) return s;
+    s = check_device_errors(h);
+    if (s != DE_OK) return s;
+    chunk = std::min<int64_t>(chunk * 2, 1024);
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (out)
+    for (int r = 0; r < h->nruns; ++r) {
+      out[r].best_f = h->h_state[r].best_f;
+      out[r].best_index = h->h_state[r].best_idx;
+      out[r].stop_reason = h->h_state[r].stop;
+      out[r].generations = h->h_state[r].gen;
+      out[r].evals = h->h_state[r].evals;
+      out[r].seconds = secs;
+    }
+  return DE_OK;
+}
+
+de_status de_eval(de_handle* h, int32_t run, const double* x_dev, int64_t ld, int32_t n, double* f_dev) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (run < 0 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
+  const RunDesc& R = h->run[run];
+  if (n < 0) return fail(h, DE_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return DE_OK;
+  if (!x_dev || !f_dev) return fail(h, DE_ERR_INVALID_ARG, "x_dev and f_dev must be device pointers");
+  if (ld < R.d) return fail(h, DE_ERR_INVALID_ARG, "ld must be >= d");
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, x_dev) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(h, DE_ERR_INVALID_ARG, "x_dev is not device memory");
+  }
+  if (cudaPointerGetAttributes(&a, f_dev) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(h, DE_ERR_INVALID_ARG, "f_dev is not device memory");
+  }
+  if (h->prec == DE_PREC_FP64) {
+    k_eval_rows_launch(h->d_run, run, x_dev, ld, n, R.dp, R.rotate, f_dev, nullptr, h->stream);
+  } else {
+    de_status s = tc_eval_launch(h->tc, h->d_run, run, R, x_dev, ld, n, f_dev, h->stream, h->err);
+    if (s != DE_OK) return s;
+  }
+  DE_CUDA(h, cudaGetLastError());
+  return DE_OK;
+}
+
+de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d, int32_t* nruns) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (nruns) *nruns = h->nruns;
+  if (run < 0 || run >= h->nruns) return np || d ? fail(h, DE_ERR_INVALID_ARG, "run out of range") : DE_OK;
+  if (np) *np = h->run[run].np;
+  if (d) *d = h->run[run].d;
+  return DE_OK;
+}
+
+de_status de_get_population(de_handle* h, int32_t run, double* x_host, double* f_host) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (run < 0 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
+  de_status s = read_states(h);
+  if (s != DE_OK) return s;
+  const RunDesc& R = h->run[run];
+  const int cur = (int)(h->h_state[run].gen & 1);
+  if (x_host)
+    DE_CUDA(h, cudaMemcpy2DAsync(x_host, R.d * sizeof(double), R.X[cur], R.dp * sizeof(double), R.d * sizeof(double),
+                                 R.np, cudaMemcpyDeviceToHost, h->stream));
+  if (f_host)
+    DE_CUDA(h, cudaMemcpyAsync(f_host, R.f[cur], R.np * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DE_OK;
+}
+
+de_status de_set_population(de_handle* h, int32_t run, const double* x_host, const double* f_host) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (run < 0 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
+  if (!x_host) return fail(h, DE_ERR_INVALID_ARG, "x_host is NULL");
+  const RunDesc& R = h->run[run];
+  for (size_t k = 0; k < (size_t)R.np * R.d; ++k)
+    if (!std::isfinite(x_host[k])) return fail(h, DE_ERR_NONFINITE, "population has a non-finite entry");
+  de_status s = read_states(h);
+  if (s != DE_OK) return s;
+  const int cur = (int)(h->h_state[run].gen & 1);
+  DE_CUDA(h, cudaMemsetAsync(R.X[cur], 0, (size_t)R.np * R.dp * sizeof(double), h->stream));
+  DE_CUDA(h, cudaMemcpy2DAsync(R.X[cur], R.dp * sizeof(double), x_host, R.d * sizeof(double), R.d * sizeof(double),
+                               R.np, cudaMemcpyHostToDevice, h->stream));
+  if (f_host) {
+    DE_CUDA(h, cudaMemcpyAsync(R.f[cur], f_host, R.np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DE_CUDA(h, cudaMemsetAsync(R.fx[cur], 1, R.np, h->stream));
+  } else {
+    k_eval_rows_launch(h->d_run, run, R.X[cur], R.dp, R.np, R.dp, R.rotate, R.f[cur], R.fx[cur], h->stream);
+  }
+  k_best_init_launch(h->d_run, run, h->stream);
+  DE_CUDA(h, cudaGetLastError());
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DE_OK;
+}
+
+de_status de_set_generation(de_handle* h, int32_t run, int64_t generation) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (run < 0 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
+  if (generation < 0 || generation >= (int64_t)UINT32_MAX)
+    return fail(h, DE_ERR_INVALID_ARG, "generation must be in [0, 2^32 - 1)");
+  de_status s = read_states(h);
+  if (s != DE_OK) return s;
+  const RunDesc& R = h->run[run];
+  const int cur = (int)(h->h_state[run].gen & 1), want = (int)(generation & 1);
+  if (cur != want) {
+    DE_CUDA(h, cudaMemcpyAsync(R.X[want], R.X[cur], (size_t)R.np * R.dp * sizeof(double), cudaMemcpyDeviceToDevice,
+                               h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(R.f[want], R.f[cur], R.np * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(R.fx[want], R.fx[cur], R.np, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  DE_CUDA(h, cudaMemcpyAsync(&R.st->gen, &generation, sizeof generation, cudaMemcpyHostToDevice, h->stream));
+  int64_t ev = (int64_t)R.np * (1 + generation);
+  DE_CUDA(h, cudaMemcpyAsync(&R.st->evals, &ev, sizeof ev, cudaMemcpyHostToDevice, h->stream));
+  k_best_init_launch(h->d_run, run, h->stream);
+  DE_CUDA(h, cudaGetLastError());
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DE_OK;
+}
+
+de_status de_get_best(de_handle* h, int32_t run, double* best_f, int32_t* best_index, double* best_x,
+                      int64_t* generations, int64_t* evals, int32_t* stop_reason) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (run < 0 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
+  const RunDesc& R = h->run[run];
+  if (best_x) DE_CUDA(h, cudaMemcpyAsync(best_x, R.best_x, R.d * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  de_status s = read_states(h);
+  if (s != DE_OK) return s;
+  const RunState& st = h->h_state[run];
+  if (best_f) *best_f = st.best_f;
+  if (best_index) *best_index = st.best_idx;
+  if (generations) *generations = st.gen;
+  if (evals) *evals = st.evals;
+  if (stop_reason) *stop_reason = st.stop;
+  return DE_OK;
+}
+
+de_status de_get_debug(de_handle* h, int32_t run, const de_debug* out) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (run < 0 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
+  if (!out) return fail(h, DE_ERR_INVALID_ARG, "out is NULL");
+  const RunDesc& R = h->run[run];
+  if (!R.dbg_trial) return fail(h, DE_ERR_STATE, "debug capture was not enabled for this run");
+  auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (!dst) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream);
+  };
+  DE_CUDA(h, cp(out->idx, R.dbg_idx, (size_t)R.np * 3 * sizeof(int32_t)));
+  DE_CUDA(h, cp(out->jrand, R.dbg_jrand, (size_t)R.np * sizeof(int32_t)));
+  DE_CUDA(h, cp(out->mask, R.dbg_mask, (size_t)R.np * R.nw * sizeof(uint32_t)));
+  DE_CUDA(h, cp(out->trial, R.dbg_trial, (size_t)R.np * R.d * sizeof(double)));
+  DE_CUDA(h, cp(out->f_trial, R.dbg_ftrial, (size_t)R.np * sizeof(double)));
+  DE_CUDA(h, cp(out->accept, R.dbg_accept, (size_t)R.np));
+  DE_CUDA(h, cp(out->fp64_checked, R.dbg_fp64, (size_t)R.np));
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DE_OK;
+}
+
+// ---------------------------------------------------------------- checkpoints
+static uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
+  // reflected CRC-32 (polynomial 0x04C11DB7, reversed form 0xEDB88320), bitwise
+  const uint8_t* p = (const uint8_t*)data;
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) {
+    crc ^= p[i];
+    for (int k = 0; k < 8; ++k) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+  }
+  return ~crc;
+}
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t nruns;
+  uint64_t payload_bytes;
+  uint32_t crc;
+  uint32_t pad;
+};
+
+de_status de_save(de_handle* h, const char* path) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (!path) return fail(h, DE_ERR_INVALID_ARG, "path is NULL");
+  de_status s = read_states(h);
+  if (s != DE_OK) return s;
+  std::vector<char> payload;
+  auto put = [&](const void* p, size_t n) {
+    const char* c = (const char*)p;
+    payload.insert(payload.end(), c, c + n);
+  };
+  for (int r = 0; r < h->nruns; ++r) {
+    const RunDesc& R = h->run[r];
+    const int cur = (int)(h->h_state[r].gen & 1);
+    int32_t shape[3] = {R.np, R.d, R.prec};
+    put(shape, sizeof shape);
+    put(&h->h_state[r], sizeof(RunState));
+    std::vector<double> x((size_t)R.np * R.dp), f(R.np), bx(R.dp);
+    std::vector<uint8_t> fx(R.np);
+    DE_CUDA(h, cudaMemcpyAsync(x.data(), R.X[cur], x.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(f.data(), R.f[cur], f.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(fx.data(), R.fx[cur], fx.size(), cudaMemcpyDeviceToHost, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(bx.data(), R.best_x, bx.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DE_CUDA(h, cudaStreamSynchronize(h->stream));
+    put(x.data(), x.size() * sizeof(double));
+    put(f.data(), f.size() * sizeof(double));
+    put(fx.data(), fx.size());
+    put(bx.data(), bx.size() * sizeof(double));
+  }
+  CkptHeader hd{};
+  memcpy(hd.magic, "DEGB300", 8);
+  hd.version = 1;
+  hd.nruns = h->nruns;
+  hd.payload_bytes = payload.size();
+  hd.crc = crc32_update(0, payload.data(), payload.size());
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return fail(h, DE_ERR_IO, std::string("cannot open ") + path + " for writing");
+  bool ok = fwrite(&hd, sizeof hd, 1, fp) == 1 && fwrite(payload.data(), 1, payload.size(), fp) == payload.size();
+  ok = (fclose(fp) == 0) && ok;
+  if (!ok) return fail(h, DE_ERR_IO, std::string("write failed: ") + path);
+  return DE_OK;
+}
+
+de_status de_load(de_handle* h, const char* path) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (!path) return fail(h, DE_ERR_INVALID_ARG, "path is NULL");
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return fail(h, DE_ERR_IO, std::string("cannot open ") + path);
+  CkptHeader hd{};
+  std::vector<char> payload;
+  bool ok = fread(&hd, sizeof hd, 1, fp) == 1 && memcmp(hd.magic, "DEGB300", 8) == 0 && hd.version == 1 &&
+            hd.payload_bytes < (1ull << 40);
+  if (ok) {
+    payload.resize(hd.payload_bytes);
+    ok = fread(payload.data(), 1, payload.size(), fp) == payload.size();
+  }
+  fclose(fp);
+  if (!ok) return fail(h, DE_ERR_IO, std::string("not a readable checkpoint: ") + path);
+  if (crc32_update(0, payload.data(), payload.size()) != hd.crc) return fail(h, DE_ERR_IO, "checkpoint CRC mismatch");
+  if (hd.nruns != h->nruns) return fail(h, DE_ERR_STATE, "checkpoint has a different number of runs");
+  size_t off = 0;
+  auto get = [&](void* p, size_t n) {
+    if (off + n > payload.size()) return false;
+    memcpy(p, payload.data() + off, n);
+    off += n;
+    return true;
+  };
+  for (int r = 0; r < h->nruns; ++r) {
+    const RunDesc& R = h->run[r];
+    int32_t shape[3];
+    RunState st;
+    if (!get(shape, sizeof shape) || !get(&st, sizeof st)) return fail(h, DE_ERR_IO, "checkpoint truncated");
+    if (shape[0] != R.np || shape[1] != R.d || shape[2] != R.prec)
+      return fail(h, DE_ERR_STATE, "checkpoint shape differs from the handle's");
+    std::vector<double> x((size_t)R.np * R.dp), f(R.np), bx(R.dp);
+    std::vector<uint8_t> fx(R.np);
+    if (!get(x.data(), x.size() * sizeof(double)) || !get(f.data(), f.size() * sizeof(double)) ||
+        !get(fx.data(), fx.size()) || !get(bx.data(), bx.size() * sizeof(double)))
+      return fail(h, DE_ERR_IO, "checkpoint truncated");
+    const int cur = (int)(st.gen & 1);
+    st.ticket = 0;
+    st.ticket2 = 0;
+    DE_CUDA(h, cudaMemcpyAsync(R.X[cur], x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(R.f[cur], f.data(), f.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(R.fx[cur], fx.data(), fx.size(), cudaMemcpyHostToDevice, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(R.best_x, bx.data(), bx.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(R.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+    DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return DE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// de_internal.cuh -- device data layout shared by the kernels and the runtime.
+//
+// HBM layout of one run (all device buffers 256-byte aligned):
+//   X[2]     np x dp doubles, row-major, dp = d rounded up to 4 (32-byte rows);
+//            X[g & 1] is the generation-g population, X[(g + 1) & 1] the next
+//            one (synchronous replacement, double buffered)
+//   f[2]     np doubles, fitness of X[0] / X[1]
+//   fx[2]    np bytes, 1 when f[.] was computed in FP64 (split precisions)
+//   o        dp doubles (shift, zero padded)
+//   MT       d x d doubles, MT[k d + j] = M[j][k] (transposed: a warp reading
+//            consecutive j for one k is one coalesced row)
+//   Bsplit   tensor-core operand copies of M (split precisions only)
+//   state    one RunState (generation, evaluations, best record, stop flag)
+//   best_x   dp doubles
+//   part     one BestPartial per row tile of the generation kernel
+// A batch of runs is a table of RunDesc in device memory plus a flat list of
+// (run, tile) work items; one launch covers every tile of every run.
+#pragma once
+#include <stdint.h>
+
+namespace de {
+
+struct RunState {
+  int64_t gen;         // generations completed
+  int64_t evals;       // objective evaluations, np (1 + gen)
+  double best_f;       // FP64 best fitness
+  int32_t best_idx;    // its index, -1 before the first evaluation
+  int32_t stop;        // de_stop_reason, 0 while running
+  uint32_t ticket;     // CTAs of the current generation that finished
+  int32_t err;         // device-side error bits (kErr*)
+  uint32_t ticket2;    // second ticket (split-precision fitness kernel)
+  int32_t pad;
+};
+
+struct BestPartial {
+  double f;
+  int32_t idx;
+  int32_t pad;
+};
+
+constexpr int32_t kErrTimeout = 1;
+constexpr int32_t kErrNonFinite = 2;
+
+struct RunDesc {
+  // problem
+  int32_t np, d, dp, obj;
+  double F, CR, lo, hi, scale;
+  uint64_t cr_thr;
+  uint64_t seed;
+  uint32_t run_id;
+  int32_t rotate;
+  double target;
+  int64_t max_evals, max_gens;
+  int32_t prec;
+  int32_t nw;  // ceil(d / 32)
+  // buffers
+  double* X[2];
+  double* f[2];
+  uint8_t* fx[2];
+  const double* o;
+  const double* MT;
+  RunState* st;
+  double* best_x;
+  BestPartial* part;
+  int32_t ntiles;     // tiles of the FP64 generation kernel
+  int32_t rows;       // rows per tile of the FP64 generation kernel
+  // split-precision path
+  double* T;          // np x dp trial rows
+  float* ynorm;       // np, |y|_2 of each trial (error bound of the split GEMM)
+  void* A;            // tensor-core A operand, per 128-row tile
+  const void* B;      // tensor-core B operand (M split), one copy
+  int32_t kpad, npad; // padded K (= input dim) and N (= output dim) of the GEMM
+  int32_t ntiles_tc;  // 128-row tiles
+  float rownorm;      // max_j |M_j|_2
+  float band_u;       // unit error of the split product
+  // debug capture (all NULL unless enabled)
+  int32_t* dbg_idx;
+  int32_t* dbg_jrand;
+  uint32_t* dbg_mask;
+  double* dbg_trial;
+  double* dbg_ftrial;
+  uint8_t* dbg_accept;
+  uint8_t* dbg_fp64;
+};
+
+}  // namespace de

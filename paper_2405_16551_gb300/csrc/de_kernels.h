@@ -1,0 +1,39 @@
+// de_kernels.h -- host-side launchers of the kernels (called by de_api.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "de.h"
+#include "de_internal.cuh"
+
+namespace de {
+
+// FP64 path (de_fp64.cu)
+void k_configure(size_t smem_gen);
+void k_gen_fp64_launch(const RunDesc* runs, const int2* items, int nitems, int threads, size_t smem,
+                       cudaStream_t s);
+void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s);
+void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int rotate,
+                        double* f, uint8_t* fx, cudaStream_t s);
+void k_best_init_launch(const RunDesc* runs, int run, cudaStream_t s);
+
+// split-precision tensor-core path (de_tc.cu)
+struct TcPlan {
+  int prec = 0;
+  int nitems_trial = 0;   // warps-per-row work items of the trial kernel
+  int nitems_fit = 0;     // 128-row tiles over all runs
+  int2* d_trial_items = nullptr;
+  int2* d_fit_items = nullptr;
+  void* arena = nullptr;  // operand copies of M and the A tiles
+  size_t smem_fit = 0;
+};
+de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* cfgs, int prec, cudaStream_t s,
+                        std::string& err);
+void tc_plan_free(TcPlan& p);
+void tc_generation_launch(const TcPlan& p, const RunDesc* runs, cudaStream_t s);
+de_status tc_eval_launch(const TcPlan& p, const RunDesc* runs, int run, const RunDesc& R, const double* x, int64_t ld,
+                         int n, double* f, cudaStream_t s, std::string& err);
+
+}  // namespace de
