@@ -207,6 +207,12 @@ DE_API de_status de_get_debug(de_handle* h, int32_t run, const de_debug* out);
 /* Number of runs in the handle, and run `run`'s np and d. */
 DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d, int32_t* nruns);
 
+/* Counters of the split-precision selection of run `run` since de_init:
+ * trials whose comparison (or best-record candidacy) was decided on FP64
+ * re-evaluations, and trials evaluated in total.  Both are 0 in FP64
+ * precision, where every comparison is FP64. */
+DE_API de_status de_get_stats(de_handle* h, int32_t run, int64_t* fp64_reevals, int64_t* trials);
+
 /* Write the full state of every run (population, fitness, counters, best
  * records, problem data) to `path`, with a CRC32 over the payload; de_load
  * restores it into a handle created with the same configurations.

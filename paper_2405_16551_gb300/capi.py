@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
             "de_get_best": ([H, ctypes.c_int32, _dp, _i32p, _dp, _i64p, _i64p, _i32p], ctypes.c_int),
             "de_get_debug": ([H, ctypes.c_int32, ctypes.POINTER(de_debug)], ctypes.c_int),
             "de_get_shape": ([H, ctypes.c_int32, _i32p, _i32p, _i32p], ctypes.c_int),
+            "de_get_stats": ([H, ctypes.c_int32, _i64p, _i64p], ctypes.c_int),
             "de_save": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_load": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_destroy": ([H], ctypes.c_int),
@@ -113,7 +114,7 @@ def load(build_if_missing: bool = True):
 def exported_symbols():
     return ["de_version", "de_status_string", "de_last_error", "de_init", "de_init_batch", "de_reset", "de_step", "de_run",
             "de_eval", "de_get_population", "de_set_population", "de_set_generation", "de_get_best",
-            "de_get_debug", "de_get_shape", "de_save", "de_load", "de_destroy"]
+            "de_get_debug", "de_get_shape", "de_get_stats", "de_save", "de_load", "de_destroy"]
 
 
 def _status_name(s):
@@ -237,6 +238,12 @@ def de_get_debug(h, run: int = 0):
                    _p(out["f_trial"]), _p(out["accept"], _u8p), _p(out["fp64_checked"], _u8p))
     _check(load().de_get_debug(h, run, ctypes.byref(dbg)), h)
     return out
+
+
+def de_get_stats(h, run: int = 0):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().de_get_stats(h, run, ctypes.byref(a), ctypes.byref(b)), h)
+    return dict(fp64_reevals=a.value, trials=b.value)
 
 
 def de_save(h, path: str):

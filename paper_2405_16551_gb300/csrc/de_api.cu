@@ -15,6 +15,7 @@
 
 #include "de.h"
 #include "de_common.cuh"
+#include "de_device.cuh"
 #include "de_internal.cuh"
 #include "de_kernels.h"
 
@@ -29,7 +30,7 @@ struct de_handle {
   std::vector<de_config> cfg;
   std::vector<RunDesc> run;  // host copy of the descriptors
   RunDesc* d_run = nullptr;
-  int2* d_items = nullptr;  // FP64 generation kernel work list
+  int4* d_items = nullptr;  // FP64 generation kernel work list: (run, tile, first row, rows)
   int nitems = 0;
   int rows = 8;             // rows per tile of the FP64 generation kernel
   int threads = 256;
@@ -42,6 +43,11 @@ struct de_handle {
   int graph_gens = 0;
   std::string err;
 };
+
+// Buffer holding the population of generation `gen`: the FP64 kernel writes
+// generation g + 1 into the other buffer; the split-precision kernels update
+// buffer 0 in place.
+static int cur_buf(const de_handle* h, int64_t gen) { return h->prec == DE_PREC_FP64 ? (int)(gen & 1) : 0; }
 
 static thread_local std::string g_err;
 static const char* kVersion = "de_gb300 1.0 sm_103a";
@@ -62,6 +68,8 @@ static de_status fail(de_handle* h, de_status s, const std::string& msg) {
   } while (0)
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+
 
 static de_status validate(const de_config& c, int idx, std::string& why) {
   char b[256];
@@ -90,27 +98,33 @@ static de_status validate(const de_config& c, int idx, std::string& why) {
   return DE_OK;
 }
 
-// Shared memory of one FP64 generation CTA for `rows` rows of stride dp.
-static size_t gen_smem(int rows, int dp, bool rotate) { return (size_t)(rotate ? 3 : 2) * rows * dp * sizeof(double); }
+// Shared memory of one FP64 generation CTA for `rows` rows of stride dp
+// (trial, shifted, rotated and second-term buffers).
+static size_t gen_smem(int rows, int dp) { return (size_t)4 * rows * dp * sizeof(double); }
 
+// Split every run into tiles of at most h->rows targets, of near-equal size.
 static de_status build_items(de_handle* h) {
-  std::vector<int2> items;
+  std::vector<int4> items;
   size_t smem = 0;
   for (int r = 0; r < h->nruns; ++r) {
     RunDesc& R = h->run[r];
-    int rows = h->rows;
-    while (rows > 1 && gen_smem(rows, R.dp, R.rotate) > 200 * 1024) rows >>= 1;
-    R.rows = rows;
-    R.ntiles = (R.np + rows - 1) / rows;
-    smem = std::max(smem, gen_smem(rows, R.dp, R.rotate));
-    for (int t = 0; t < R.ntiles; ++t) items.push_back(make_int2(r, t));
+    int rows = std::max(1, std::min(h->rows, 8));
+    while (rows > 1 && gen_smem(rows, R.dp) > 200 * 1024) --rows;
+    const int nt = (R.np + rows - 1) / rows;
+    R.rows = (R.np + nt - 1) / nt;  // the largest tile after even splitting
+    R.ntiles = nt;
+    smem = std::max(smem, gen_smem(R.rows, R.dp));
+    for (int t = 0; t < nt; ++t) {
+      const int a = (int)((long long)t * R.np / nt), b = (int)((long long)(t + 1) * R.np / nt);
+      items.push_back(make_int4(r, t, a, b - a));
+    }
   }
   h->smem_gen = smem;
   h->nitems = (int)items.size();
   if (h->d_items) cudaFree(h->d_items);
   h->d_items = nullptr;
-  DE_CUDA(h, cudaMalloc(&h->d_items, items.size() * sizeof(int2)));
-  DE_CUDA(h, cudaMemcpyAsync(h->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice,
+  DE_CUDA(h, cudaMalloc(&h->d_items, items.size() * sizeof(int4)));
+  DE_CUDA(h, cudaMemcpyAsync(h->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
                              h->stream));
   return DE_OK;
 }
@@ -226,7 +240,7 @@ static std::string tune_key(const de_handle* h) {
     sum_d += (long long)R.np * R.d;
   }
   char b[256];
-  snprintf(b, sizeof b, "gen_fp64 runs=%d np0=%d d0=%d obj0=%d rot0=%d sumnp=%lld sumnd=%lld", h->nruns, h->run[0].np,
+  snprintf(b, sizeof b, "gen_fp64v2 runs=%d np0=%d d0=%d obj0=%d rot0=%d sumnp=%lld sumnd=%lld", h->nruns, h->run[0].np,
            h->run[0].d, h->run[0].obj, h->run[0].rotate, sum_np, sum_d);
   return b;
 }
@@ -262,11 +276,8 @@ static void tune_store(const std::string& key, int rows) {
 static int heuristic_rows(const de_handle* h, int nsm) {
   long long np_total = 0;
   for (auto& R : h->run) np_total += R.np;
-  // aim for about two CTAs per SM, at most 16 rows
-  long long want = np_total / (2LL * nsm);
-  int rows = 1;
-  while (rows < 16 && rows * 2 <= want) rows *= 2;
-  return std::max(1, rows);
+  // about one CTA per SM, at most 8 rows (one warp per target)
+  return (int)std::max(1LL, std::min(8LL, (np_total + nsm - 1) / nsm));
 }
 
 static de_status autotune_fp64(de_handle* h, int nsm) {
@@ -294,7 +305,7 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
     R.max_gens = INT64_MAX / 4;
   }
   de_status st_all = DE_OK;
-  for (int rows : {1, 2, 4, 8, 16}) {
+  for (int rows : {1, 2, 3, 4, 5, 6, 7, 8}) {
     h->rows = rows;
     st_all = build_items(h);
     if (st_all == DE_OK) st_all = upload_desc(h);
@@ -407,7 +418,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     return o;
   };
   struct Offs {
-    size_t X0, X1, f0, f1, fx0, fx1, o, MT, st, bx, part, T, yn;
+    size_t X0, X1, f0, f1, fx0, fx1, o, MT, Mr, st, part, T;
     size_t dbg_idx, dbg_jrand, dbg_mask, dbg_trial, dbg_ftrial, dbg_accept, dbg_fp64;
   };
   std::vector<Offs> offs(nruns);
@@ -425,12 +436,11 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     O.fx1 = take(c.np);
     O.o = take(dp * sizeof(double));
     O.MT = c.rot ? take((size_t)c.d * c.d * sizeof(double)) : 0;
+    O.Mr = (c.rot && c.precision != DE_PREC_FP64) ? take((size_t)c.d * c.d * sizeof(double)) : 0;
     O.st = states_off + (size_t)r * sizeof(RunState);
-    O.bx = take(dp * sizeof(double));
     O.part = take((size_t)c.np * sizeof(BestPartial));
     const bool split = c.precision != DE_PREC_FP64;
     O.T = split ? take(pop) : 0;
-    O.yn = split ? take(c.np * sizeof(float)) : 0;
     if (c.debug_capture) {
       const int nw = (c.d + 31) / 32;
       O.dbg_idx = take((size_t)c.np * 3 * sizeof(int32_t));
@@ -486,6 +496,9 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     R.lo = c.lo;
     R.hi = c.hi;
     R.scale = c.scale;
+    R.lo_key = ordered_key(c.lo);
+    R.hi_key = ordered_key(c.hi);
+    R.unit_scale = c.scale == 1.0;
     R.cr_thr = cr_threshold(c.cr);
     R.seed = c.seed;
     R.run_id = c.run_id;
@@ -504,12 +517,11 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     R.fx[1] = (uint8_t*)(A + O.fx1);
     R.o = (const double*)(A + O.o);
     R.MT = R.rotate ? (const double*)(A + O.MT) : nullptr;
+    R.Mrow = (R.rotate && c.precision != DE_PREC_FP64) ? (const double*)(A + O.Mr) : nullptr;
     R.st = (RunState*)(A + O.st);
-    R.best_x = (double*)(A + O.bx);
     R.part = (BestPartial*)(A + O.part);
     if (c.precision != DE_PREC_FP64) {
       R.T = (double*)(A + O.T);
-      R.ynorm = (float*)(A + O.yn);
     }
     if (c.debug_capture) {
       R.dbg_idx = (int32_t*)(A + O.dbg_idx);
@@ -529,6 +541,9 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
       for (int j = 0; j < c.d; ++j)
         for (int k = 0; k < c.d; ++k) tmp[(size_t)k * c.d + j] = c.rot[(size_t)j * c.d + k];
       ce = cudaMemcpyAsync((void*)R.MT, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+      if (ce == cudaSuccess && R.Mrow)
+        ce = cudaMemcpyAsync((void*)R.Mrow, c.rot, (size_t)c.d * c.d * sizeof(double), cudaMemcpyHostToDevice,
+                             h->stream);
       if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);  // tmp is reused
       if (ce != cudaSuccess) return fin(fail(h, DE_ERR_CUDA, std::string("copy rotation: ") + cudaGetErrorString(ce)));
       double rn = 0.0;
@@ -662,7 +677,7 @@ de_status de_get_population(de_handle* h, int32_t run, double* x_host, double* f
   de_status s = read_states(h);
   if (s != DE_OK) return s;
   const RunDesc& R = h->run[run];
-  const int cur = (int)(h->h_state[run].gen & 1);
+  const int cur = cur_buf(h, h->h_state[run].gen);
   if (x_host)
     DE_CUDA(h, cudaMemcpy2DAsync(x_host, R.d * sizeof(double), R.X[cur], R.dp * sizeof(double), R.d * sizeof(double),
                                  R.np, cudaMemcpyDeviceToHost, h->stream));
@@ -681,7 +696,7 @@ de_status de_set_population(de_handle* h, int32_t run, const double* x_host, con
     if (!std::isfinite(x_host[k])) return fail(h, DE_ERR_NONFINITE, "population has a non-finite entry");
   de_status s = read_states(h);
   if (s != DE_OK) return s;
-  const int cur = (int)(h->h_state[run].gen & 1);
+  const int cur = cur_buf(h, h->h_state[run].gen);
   DE_CUDA(h, cudaMemsetAsync(R.X[cur], 0, (size_t)R.np * R.dp * sizeof(double), h->stream));
   DE_CUDA(h, cudaMemcpy2DAsync(R.X[cur], R.dp * sizeof(double), x_host, R.d * sizeof(double), R.d * sizeof(double),
                                R.np, cudaMemcpyHostToDevice, h->stream));
@@ -705,7 +720,7 @@ de_status de_set_generation(de_handle* h, int32_t run, int64_t generation) {
   de_status s = read_states(h);
   if (s != DE_OK) return s;
   const RunDesc& R = h->run[run];
-  const int cur = (int)(h->h_state[run].gen & 1), want = (int)(generation & 1);
+  const int cur = cur_buf(h, h->h_state[run].gen), want = cur_buf(h, generation);
   if (cur != want) {
     DE_CUDA(h, cudaMemcpyAsync(R.X[want], R.X[cur], (size_t)R.np * R.dp * sizeof(double), cudaMemcpyDeviceToDevice,
                                h->stream));
@@ -726,10 +741,16 @@ de_status de_get_best(de_handle* h, int32_t run, double* best_f, int32_t* best_i
   if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
   if (run < 0 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
   const RunDesc& R = h->run[run];
-  if (best_x) DE_CUDA(h, cudaMemcpyAsync(best_x, R.best_x, R.d * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   de_status s = read_states(h);
   if (s != DE_OK) return s;
   const RunState& st = h->h_state[run];
+  if (best_x) {
+    // the best individual's vector, read from the current population
+    if (st.best_idx < 0) return fail(h, DE_ERR_NONFINITE, "no finite fitness in the population");
+    const double* row = R.X[cur_buf(h, st.gen)] + (size_t)st.best_idx * R.dp;
+    DE_CUDA(h, cudaMemcpyAsync(best_x, row, R.d * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
   if (best_f) *best_f = st.best_f;
   if (best_index) *best_index = st.best_idx;
   if (generations) *generations = st.gen;
@@ -756,6 +777,19 @@ de_status de_get_debug(de_handle* h, int32_t run, const de_debug* out) {
   DE_CUDA(h, cp(out->accept, R.dbg_accept, (size_t)R.np));
   DE_CUDA(h, cp(out->fp64_checked, R.dbg_fp64, (size_t)R.np));
   DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DE_OK;
+}
+
+de_status de_get_stats(de_handle* h, int32_t run, int64_t* fp64_reevals, int64_t* trials) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (run < 0 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
+  unsigned long long v[2] = {0, 0};
+  if (h->run[run].stats) {
+    DE_CUDA(h, cudaMemcpyAsync(v, h->run[run].stats, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+    DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  if (fp64_reevals) *fp64_reevals = (int64_t)v[0];
+  if (trials) *trials = (int64_t)v[1];
   return DE_OK;
 }
 
@@ -792,25 +826,28 @@ de_status de_save(de_handle* h, const char* path) {
   };
   for (int r = 0; r < h->nruns; ++r) {
     const RunDesc& R = h->run[r];
-    const int cur = (int)(h->h_state[r].gen & 1);
+    const int cur = cur_buf(h, h->h_state[r].gen);
     int32_t shape[3] = {R.np, R.d, R.prec};
     put(shape, sizeof shape);
     put(&h->h_state[r], sizeof(RunState));
-    std::vector<double> x((size_t)R.np * R.dp), f(R.np), bx(R.dp);
+    std::vector<double> x((size_t)R.np * R.dp), f(R.np);
     std::vector<uint8_t> fx(R.np);
     DE_CUDA(h, cudaMemcpyAsync(x.data(), R.X[cur], x.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     DE_CUDA(h, cudaMemcpyAsync(f.data(), R.f[cur], f.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     DE_CUDA(h, cudaMemcpyAsync(fx.data(), R.fx[cur], fx.size(), cudaMemcpyDeviceToHost, h->stream));
-    DE_CUDA(h, cudaMemcpyAsync(bx.data(), R.best_x, bx.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     DE_CUDA(h, cudaStreamSynchronize(h->stream));
     put(x.data(), x.size() * sizeof(double));
     put(f.data(), f.size() * sizeof(double));
     put(fx.data(), fx.size());
-    put(bx.data(), bx.size() * sizeof(double));
+    if (R.tau) {
+      std::vector<float> tau(R.np);
+      DE_CUDA(h, cudaMemcpy(tau.data(), R.tau, tau.size() * sizeof(float), cudaMemcpyDeviceToHost));
+      put(tau.data(), tau.size() * sizeof(float));
+    }
   }
   CkptHeader hd{};
   memcpy(hd.magic, "DEGB300", 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.nruns = h->nruns;
   hd.payload_bytes = payload.size();
   hd.crc = crc32_update(0, payload.data(), payload.size());
@@ -829,7 +866,7 @@ de_status de_load(de_handle* h, const char* path) {
   if (!fp) return fail(h, DE_ERR_IO, std::string("cannot open ") + path);
   CkptHeader hd{};
   std::vector<char> payload;
-  bool ok = fread(&hd, sizeof hd, 1, fp) == 1 && memcmp(hd.magic, "DEGB300", 8) == 0 && hd.version == 1 &&
+  bool ok = fread(&hd, sizeof hd, 1, fp) == 1 && memcmp(hd.magic, "DEGB300", 8) == 0 && hd.version == 2 &&
             hd.payload_bytes < (1ull << 40);
   if (ok) {
     payload.resize(hd.payload_bytes);
@@ -853,18 +890,24 @@ de_status de_load(de_handle* h, const char* path) {
     if (!get(shape, sizeof shape) || !get(&st, sizeof st)) return fail(h, DE_ERR_IO, "checkpoint truncated");
     if (shape[0] != R.np || shape[1] != R.d || shape[2] != R.prec)
       return fail(h, DE_ERR_STATE, "checkpoint shape differs from the handle's");
-    std::vector<double> x((size_t)R.np * R.dp), f(R.np), bx(R.dp);
+    std::vector<double> x((size_t)R.np * R.dp), f(R.np);
     std::vector<uint8_t> fx(R.np);
     if (!get(x.data(), x.size() * sizeof(double)) || !get(f.data(), f.size() * sizeof(double)) ||
-        !get(fx.data(), fx.size()) || !get(bx.data(), bx.size() * sizeof(double)))
+        !get(fx.data(), fx.size()))
       return fail(h, DE_ERR_IO, "checkpoint truncated");
-    const int cur = (int)(st.gen & 1);
+    std::vector<float> tau;
+    if (R.tau) {
+      tau.resize(R.np);
+      if (!get(tau.data(), tau.size() * sizeof(float))) return fail(h, DE_ERR_IO, "checkpoint truncated");
+      DE_CUDA(h, cudaMemcpyAsync(R.tau, tau.data(), tau.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    }
+    const int cur = cur_buf(h, st.gen);
     st.ticket = 0;
-    st.ticket2 = 0;
+    st.band_n = 0;
+    st.band_left = 0;
     DE_CUDA(h, cudaMemcpyAsync(R.X[cur], x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     DE_CUDA(h, cudaMemcpyAsync(R.f[cur], f.data(), f.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     DE_CUDA(h, cudaMemcpyAsync(R.fx[cur], fx.data(), fx.size(), cudaMemcpyHostToDevice, h->stream));
-    DE_CUDA(h, cudaMemcpyAsync(R.best_x, bx.data(), bx.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     DE_CUDA(h, cudaMemcpyAsync(R.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
     DE_CUDA(h, cudaStreamSynchronize(h->stream));
   }

@@ -1,0 +1,387 @@
+// de_device.cuh -- device helpers shared by the FP64 and the tensor-core
+// kernels: objective of a row in FP64, the FP64 rotation of a tile, the
+// best-record reduction, and the construction of one trial vector.
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <string.h>
+
+#include "de_common.cuh"
+#include "de_internal.cuh"
+
+namespace de {
+
+// Programmatic dependent launch: a kernel launched with the programmatic
+// serialization attribute may start while its predecessor finishes; it must
+// wait before touching the predecessor's results.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+// ------------------------------------------------------------------ cos(2 pi z)
+// 2z = k + r with k the nearest integer, found exactly by adding and removing
+// 1.5 * 2^(p-1) (p the significand width); |r| <= 1/2 and r is exact.  Then
+// cos(2 pi z) = (-1)^k cos(pi r), and cos(pi r) is its Taylor series in
+// u = r^2, sum_n (-1)^n pi^(2n) u^n / (2n)!, truncated where the next term is
+// below the format's rounding (u <= 1/4): 7 terms in FP32 (next term 6e-9),
+// 11 terms in FP64 (next term 2e-17).  The FP64 sum is evaluated by Estrin's
+// scheme (dependency depth 5 instead of 10: a dependent FP64 operation costs
+// tens of cycles on this part).
+__host__ __device__ constexpr double cospi_taylor(int n) {
+  double c = 1.0;
+  for (int k = 1; k <= n; ++k) c *= -9.8696044010893586188 / ((2.0 * k - 1.0) * (2.0 * k));  // pi^2
+  return c;
+}
+
+__device__ __forceinline__ double cos2pi_f64(double z) {
+  const double sh = 6755399441055744.0;  // 1.5 * 2^52
+  const double tz = 2.0 * z;
+  const double t1 = __dadd_rn(tz, sh);
+  const double r = __dsub_rn(tz, __dsub_rn(t1, sh));
+  const bool odd = __double_as_longlong(t1) & 1;
+  const double u = r * r, u2 = u * u, u4 = u2 * u2, u8 = u4 * u4;
+  const double p01 = fma(cospi_taylor(1), u, cospi_taylor(0));
+  const double p23 = fma(cospi_taylor(3), u, cospi_taylor(2));
+  const double p45 = fma(cospi_taylor(5), u, cospi_taylor(4));
+  const double p67 = fma(cospi_taylor(7), u, cospi_taylor(6));
+  const double p89 = fma(cospi_taylor(9), u, cospi_taylor(8));
+  const double q0 = fma(p23, u2, p01);
+  const double q1 = fma(p67, u2, p45);
+  const double q2 = fma(cospi_taylor(10), u2, p89);
+  const double c = fma(q2, u8, fma(q1, u4, q0));
+  return odd ? -c : c;
+}
+
+// Same series by Horner's rule: fewer FP64 instructions than Estrin's
+// scheme, for kernels bound by FP64 throughput rather than latency.
+__device__ __forceinline__ double cos2pi_f64_horner(double z) {
+  const double sh = 6755399441055744.0;  // 1.5 * 2^52
+  const double tz = 2.0 * z;
+  const double t1 = __dadd_rn(tz, sh);
+  const double r = __dsub_rn(tz, __dsub_rn(t1, sh));
+  const bool odd = __double_as_longlong(t1) & 1;
+  const double u = r * r;
+  double c = cospi_taylor(10);
+#pragma unroll
+  for (int n = 9; n >= 0; --n) c = fma(c, u, cospi_taylor(n));
+  return odd ? -c : c;
+}
+
+__device__ __forceinline__ float cos2pi_f32(float z) {
+  const float sh = 12582912.0f;  // 1.5 * 2^23
+  const float tz = 2.0f * z;
+  const float t1 = __fadd_rn(tz, sh);
+  const float r = __fsub_rn(tz, __fsub_rn(t1, sh));
+  const bool odd = __float_as_int(t1) & 1;
+  const float u = r * r;
+  float c = (float)cospi_taylor(6);
+  c = fmaf(c, u, (float)cospi_taylor(5));
+  c = fmaf(c, u, (float)cospi_taylor(4));
+  c = fmaf(c, u, (float)cospi_taylor(3));
+  c = fmaf(c, u, (float)cospi_taylor(2));
+  c = fmaf(c, u, (float)cospi_taylor(1));
+  c = fmaf(c, u, 1.0f);
+  return odd ? -c : c;
+}
+
+// Ordering key of a fitness value for the best-record reductions: the
+// integer image of the double (monotone for finite values), NaN last.
+__device__ __forceinline__ long long fit_key(double f) {
+  const long long k = __double_as_longlong(f);
+  if ((k & 0x7FF0000000000000LL) == 0x7FF0000000000000LL && (k & 0x000FFFFFFFFFFFFFLL)) return 0x7FFFFFFFFFFFFFFFLL;
+  return k >= 0 ? k : -(k & 0x7FFFFFFFFFFFFFFFLL);
+}
+
+// ------------------------------------------------------------------ objective
+// Objective of one row held in shared memory (z, length d); the calling warp
+// returns the same value in every lane.  Terms are summed per lane in
+// coordinate order, then across lanes by a fixed xor tree.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double row_objective_fp64(int obj, const double* __restrict__ z, int d, int lane) {
+  double s1 = 0.0, s2 = 0.0;
+  if (obj == kObjSphere) {
+    for (int j = lane; j < d; j += 32) s1 += z[j] * z[j];
+  } else if (obj == kObjRastrigin) {
+    for (int j = lane; j < d; j += 32) {
+      const double zj = z[j];
+      s1 += zj * zj - 10.0 * cos2pi_f64_horner(zj) + 10.0;
+    }
+  } else if (obj == kObjRosenbrock) {
+    for (int j = lane; j + 1 < d; j += 32) {
+      const double t0 = z[j] + 1.0, t1 = z[j + 1] + 1.0;
+      const double a = t1 - t0 * t0, b = t0 - 1.0;
+      s1 += 100.0 * a * a + b * b;
+    }
+  } else if (obj == kObjAckley) {
+    for (int j = lane; j < d; j += 32) {
+      const double zj = z[j];
+      s1 += zj * zj;
+      s2 += cos2pi_f64_horner(zj);
+    }
+  } else {
+    s1 = CUDART_NAN;
+  }
+  s1 = warp_sum(s1);
+  if (obj == kObjAckley) {
+    s2 = warp_sum(s2);
+    const double inv_d = 1.0 / (double)d;
+    return 20.0 + 2.718281828459045 - 20.0 * exp(-0.2 * sqrt(s1 * inv_d)) - exp(s2 * inv_d);
+  }
+  return s1;
+}
+
+// Z[r][j] = sum_k M[j][k] Y[r][k] for the rows of a tile (ROWS rows of stride
+// dp in shared memory).  Thread t owns output columns t, t + blockDim, ...
+template <int ROWS>
+__device__ __forceinline__ void tile_rotate_fp64(const double* __restrict__ MT, const double* __restrict__ Y,
+                                                 double* __restrict__ Z, int d, int dp) {
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    double acc[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) acc[r] = 0.0;
+    const double* mcol = MT + j;
+    int k = 0;
+    for (; k + 4 <= d; k += 4) {
+      const double m0 = __ldg(mcol + (size_t)(k + 0) * d);
+      const double m1 = __ldg(mcol + (size_t)(k + 1) * d);
+      const double m2 = __ldg(mcol + (size_t)(k + 2) * d);
+      const double m3 = __ldg(mcol + (size_t)(k + 3) * d);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const double* y = Y + r * dp + k;
+        acc[r] = fma(m0, y[0], acc[r]);
+        acc[r] = fma(m1, y[1], acc[r]);
+        acc[r] = fma(m2, y[2], acc[r]);
+        acc[r] = fma(m3, y[3], acc[r]);
+      }
+    }
+    for (; k < d; ++k) {
+      const double m = __ldg(mcol + (size_t)k * d);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) acc[r] = fma(m, Y[r * dp + k], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) Z[r * dp + j] = acc[r];
+  }
+}
+
+__device__ __forceinline__ void tile_rotate_dispatch(int rows, const double* MT, const double* Y, double* Z, int d,
+                                                     int dp) {
+  if (rows <= 1) tile_rotate_fp64<1>(MT, Y, Z, d, dp);
+  else if (rows <= 2) tile_rotate_fp64<2>(MT, Y, Z, d, dp);
+  else if (rows <= 4) tile_rotate_fp64<4>(MT, Y, Z, d, dp);
+  else if (rows <= 8) tile_rotate_fp64<8>(MT, Y, Z, d, dp);
+  else tile_rotate_fp64<16>(MT, Y, Z, d, dp);
+}
+
+// ------------------------------------------------------------------ best record
+__device__ __forceinline__ bool better(double fa, int ia, double fb, int ib) {
+  // a beats b: smaller f, or equal f and lower index; NaN never wins
+  // (compared as integer keys: no FP64 instruction on the path)
+  const long long ka = fit_key(fa), kb = fit_key(fb);
+  if (ka == 0x7FFFFFFFFFFFFFFFLL) return false;
+  if (ib < 0 || kb == 0x7FFFFFFFFFFFFFFFLL) return true;
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// Finish a generation of a run: called by the last CTA to arrive.  Reduces
+// the tile partials in order (and, for the split precisions, the rows decided
+// in FP64 this generation, which carry no partial),
+// advances the counters and evaluates the stop rule (Sec. 7.3.4).  The best
+// vector itself is read from the population when a caller asks for it.
+__device__ __forceinline__ void finish_generation(const RunDesc& R, int64_t g, int nparts, const BestPartial* part,
+                                                  const double* Xn, const BandEntry* band = nullptr, int nband = 0,
+                                                  int run = -1, const double* fcur = nullptr) {
+  __shared__ double sf[32];
+  __shared__ int si[32];
+  double bf = CUDART_INF;
+  int bi = -1;
+  for (int t = threadIdx.x; t < nparts; t += blockDim.x) {
+    const double pf = __ldcg(&part[t].f);
+    const int pi = __ldcg(&part[t].idx);
+    if (pi >= 0 && better(pf, pi, bf, bi)) { bf = pf; bi = pi; }
+  }
+  for (int t = threadIdx.x; t < nband; t += blockDim.x) {
+    if (__ldcg(&band[t].run) != run) continue;
+    const int i = __ldcg(&band[t].row);
+    const double fi = __ldcg(&fcur[i]);
+    if (better(fi, i, bf, bi)) { bf = fi; bi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double of = __shfl_xor_sync(0xffffffffu, bf, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (oi >= 0 && better(of, oi, bf, bi)) { bf = of; bi = oi; }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sf[warp] = bf; si[warp] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bf = CUDART_INF;
+    bi = -1;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      if (si[w] >= 0 && better(sf[w], si[w], bf, bi)) { bf = sf[w]; bi = si[w]; }
+    RunState* st = R.st;
+    if (bi >= 0) {
+      st->best_f = bf;
+      st->best_idx = bi;
+    } else {
+      st->err |= kErrNonFinite;
+    }
+    st->gen = g;
+    st->evals += R.np;
+    int stop = 0;
+    if (R.target > 0.0 && st->best_idx >= 0 && st->best_f < R.target) stop = 1;
+    else if (R.max_evals > 0 && st->evals >= R.max_evals) stop = 2;
+    else if (g >= R.max_gens) stop = 3;
+    st->stop = stop;
+    st->ticket = 0;
+    st->band_n = 0;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ trial row
+// Construction of the trial of target i at generation g (Eq. 2 and Eq. 3,
+// with bound repair), split so that the FP64 and the tensor-core trial
+// kernels share it.  A warp handles one target; lane L owns coordinates
+// 128c + 4L .. 128c + 4L + 3 of chunk c.
+// Total order of finite doubles as 64-bit integers (-0 and +0 map to 0), so
+// that the bound tests below run on the integer pipe instead of the slow
+// FP64 pipe; exact for every finite value.
+__host__ __device__ __forceinline__ long long ordered_key(double x) {
+#if defined(__CUDA_ARCH__)
+  const long long k = __double_as_longlong(x);
+#else
+  long long k;
+  memcpy(&k, &x, sizeof k);
+#endif
+  return k >= 0 ? k : -(k & 0x7FFFFFFFFFFFFFFFLL);
+}
+
+__device__ __forceinline__ double repair(double v, double x, const RunDesc& R) {
+  // a coordinate that leaves [lo, hi] goes half way from the target's
+  // coordinate to the violated bound (the paper leaves bounds handling open)
+  const long long kv = ordered_key(v);
+  if (kv < R.lo_key) return __dmul_rn(__dadd_rn(x, R.lo), 0.5);
+  if (kv > R.hi_key) return __dmul_rn(__dadd_rn(x, R.hi), 0.5);
+  return v;
+}
+
+// y = (t - o) s, rounded once per operation as written
+__device__ __forceinline__ double shifted(double t, double o, const RunDesc& R) {
+  const double y = __dsub_rn(t, o);
+  return R.unit_scale ? y : __dmul_rn(y, R.scale);
+}
+
+struct TrialSetup {
+  uint32_t r1, r2, r3, jr;
+};
+
+// Draws 0..3 of the STEP stream: mutant indices (Eq. 2) and j_rand (Eq. 3).
+__device__ __forceinline__ TrialSetup trial_setup(const RunDesc& R, uint32_t i, int64_t g, int lane) {
+  const U32x4 b0 = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, i, 0u);
+  TrialSetup s;
+  mutant_indices(b0.x, b0.y, b0.z, i, (uint32_t)R.np, s.r1, s.r2, s.r3);
+  s.jr = map_to_range(b0.w, (uint32_t)R.d);
+  if (R.dbg_idx && lane == 0) {
+    R.dbg_idx[3 * i + 0] = (int32_t)s.r1;
+    R.dbg_idx[3 * i + 1] = (int32_t)s.r2;
+    R.dbg_idx[3 * i + 2] = (int32_t)s.r3;
+    R.dbg_jrand[i] = (int32_t)s.jr;
+  }
+  return s;
+}
+
+// Coordinates j0 .. j0+3 (j0 < d, j0 % 4 == 0) of the trial; entries at
+// j >= d are 0.  Returns the crossed-coordinate bits (bit m for j0 + m).
+__device__ __forceinline__ uint32_t trial_chunk(const RunDesc& R, const double* __restrict__ X, const TrialSetup& s,
+                                                uint32_t i, int64_t g, int j0, double t[4]) {
+  const int d = R.d;
+  const U32x4 bc = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, i, 1u + (uint32_t)(j0 >> 2));
+  const double* xi = X + (size_t)i * R.dp + j0;
+  const double* x1 = X + (size_t)s.r1 * R.dp + j0;
+  const double* x2 = X + (size_t)s.r2 * R.dp + j0;
+  const double* x3 = X + (size_t)s.r3 * R.dp + j0;
+  const double2 xa = *reinterpret_cast<const double2*>(xi);
+  const double2 xb = *reinterpret_cast<const double2*>(xi + 2);
+  const double2 a1 = *reinterpret_cast<const double2*>(x1);
+  const double2 b1 = *reinterpret_cast<const double2*>(x1 + 2);
+  const double2 a2 = *reinterpret_cast<const double2*>(x2);
+  const double2 b2 = *reinterpret_cast<const double2*>(x2 + 2);
+  const double2 a3 = *reinterpret_cast<const double2*>(x3);
+  const double2 b3 = *reinterpret_cast<const double2*>(x3 + 2);
+  const double tx[4] = {xa.x, xa.y, xb.x, xb.y};
+  const double v1[4] = {a1.x, a1.y, b1.x, b1.y};
+  const double v2[4] = {a2.x, a2.y, b2.x, b2.y};
+  const double v3[4] = {a3.x, a3.y, b3.x, b3.y};
+  const uint32_t u[4] = {bc.x, bc.y, bc.z, bc.w};
+  uint32_t bits = 0;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int j = j0 + m;
+    t[m] = 0.0;
+    if (j < d) {
+      const bool crossed = ((uint32_t)j == s.jr) || ((uint64_t)u[m] <= R.cr_thr);
+      if (crossed) {
+        // Eq. 2: y = x_r1 + F (x_r2 - x_r3), one rounding for the product-sum
+        const double v = __fma_rn(R.F, __dsub_rn(v2[m], v3[m]), v1[m]);
+        t[m] = repair(v, tx[m], R);
+        bits |= 1u << m;
+      } else {
+        t[m] = tx[m];
+      }
+    }
+  }
+  return bits;
+}
+
+// Debug capture of one chunk: trial values and the crossover mask word.
+// Called by every lane of the warp (the mask word is assembled by shuffles).
+__device__ __forceinline__ void trial_debug(const RunDesc& R, uint32_t i, int j0, int lane, uint32_t bits,
+                                            const double t[4]) {
+  const int d = R.d;
+  if (j0 < d) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      if (j0 + m < d) R.dbg_trial[(size_t)i * d + j0 + m] = t[m];
+  }
+  // lanes 8w .. 8w+7 of a chunk cover mask word 4c + w
+  uint32_t word = (j0 < d) ? (bits << (j0 & 31)) : 0u;
+  word |= __shfl_xor_sync(0xffffffffu, word, 1);
+  word |= __shfl_xor_sync(0xffffffffu, word, 2);
+  word |= __shfl_xor_sync(0xffffffffu, word, 4);
+  const int wi = j0 >> 5;
+  if ((lane & 7) == 0 && wi < R.nw) R.dbg_mask[(size_t)i * R.nw + wi] = word;
+}
+
+// FP64 path: build the trial row into T and Y = (T - o) s (rows of length dp).
+__device__ __forceinline__ void build_trial_row(const RunDesc& R, const double* __restrict__ X, uint32_t i,
+                                                int64_t g, int lane, double* __restrict__ Trow,
+                                                double* __restrict__ Yrow) {
+  const TrialSetup s = trial_setup(R, i, g, lane);
+  const bool dbg = R.dbg_trial != nullptr;
+  const int nchunks = (R.d + 127) / 128;
+  for (int c = 0; c < nchunks; ++c) {
+    const int j0 = 128 * c + 4 * lane;
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    uint32_t bits = 0;
+    if (j0 < R.d) {
+      bits = trial_chunk(R, X, s, i, g, j0, t);
+      double y[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) y[m] = (j0 + m < R.d) ? shifted(t[m], R.o[j0 + m], R) : 0.0;
+      *reinterpret_cast<double2*>(Trow + j0) = make_double2(t[0], t[1]);
+      *reinterpret_cast<double2*>(Trow + j0 + 2) = make_double2(t[2], t[3]);
+      *reinterpret_cast<double2*>(Yrow + j0) = make_double2(y[0], y[1]);
+      *reinterpret_cast<double2*>(Yrow + j0 + 2) = make_double2(y[2], y[3]);
+    }
+    if (dbg) trial_debug(R, i, j0, lane, bits, t);
+  }
+}
+
+}  // namespace de

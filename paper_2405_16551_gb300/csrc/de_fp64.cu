@@ -25,96 +25,10 @@
 
 #include "de_common.cuh"
 #include "de_internal.cuh"
+#include "de_device.cuh"
 #include "de_kernels.h"
 
 namespace de {
-
-// ------------------------------------------------------------------ objective
-// Objective of one row held in shared memory (z, length d); the calling warp
-// returns the same value in every lane.  Terms are summed per lane in
-// coordinate order, then across lanes by a fixed xor tree.
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ double row_objective_fp64(int obj, const double* __restrict__ z, int d, int lane) {
-  double s1 = 0.0, s2 = 0.0;
-  if (obj == kObjSphere) {
-    for (int j = lane; j < d; j += 32) s1 += z[j] * z[j];
-  } else if (obj == kObjRastrigin) {
-    for (int j = lane; j < d; j += 32) {
-      const double zj = z[j];
-      s1 += zj * zj - 10.0 * cospi(2.0 * zj) + 10.0;
-    }
-  } else if (obj == kObjRosenbrock) {
-    for (int j = lane; j + 1 < d; j += 32) {
-      const double t0 = z[j] + 1.0, t1 = z[j + 1] + 1.0;
-      const double a = t1 - t0 * t0, b = t0 - 1.0;
-      s1 += 100.0 * a * a + b * b;
-    }
-  } else if (obj == kObjAckley) {
-    for (int j = lane; j < d; j += 32) {
-      const double zj = z[j];
-      s1 += zj * zj;
-      s2 += cospi(2.0 * zj);
-    }
-  } else {
-    s1 = CUDART_NAN;
-  }
-  s1 = warp_sum(s1);
-  if (obj == kObjAckley) {
-    s2 = warp_sum(s2);
-    const double inv_d = 1.0 / (double)d;
-    return 20.0 + 2.718281828459045 - 20.0 * exp(-0.2 * sqrt(s1 * inv_d)) - exp(s2 * inv_d);
-  }
-  return s1;
-}
-
-// Z[r][j] = sum_k M[j][k] Y[r][k] for the rows of a tile (ROWS rows of stride
-// dp in shared memory).  Thread t owns output columns t, t + blockDim, ...
-template <int ROWS>
-__device__ __forceinline__ void tile_rotate_fp64(const double* __restrict__ MT, const double* __restrict__ Y,
-                                                 double* __restrict__ Z, int d, int dp) {
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    double acc[ROWS];
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) acc[r] = 0.0;
-    const double* mcol = MT + j;
-    int k = 0;
-    for (; k + 4 <= d; k += 4) {
-      const double m0 = __ldg(mcol + (size_t)(k + 0) * d);
-      const double m1 = __ldg(mcol + (size_t)(k + 1) * d);
-      const double m2 = __ldg(mcol + (size_t)(k + 2) * d);
-      const double m3 = __ldg(mcol + (size_t)(k + 3) * d);
-#pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        const double* y = Y + r * dp + k;
-        acc[r] = fma(m0, y[0], acc[r]);
-        acc[r] = fma(m1, y[1], acc[r]);
-        acc[r] = fma(m2, y[2], acc[r]);
-        acc[r] = fma(m3, y[3], acc[r]);
-      }
-    }
-    for (; k < d; ++k) {
-      const double m = __ldg(mcol + (size_t)k * d);
-#pragma unroll
-      for (int r = 0; r < ROWS; ++r) acc[r] = fma(m, Y[r * dp + k], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) Z[r * dp + j] = acc[r];
-  }
-}
-
-__device__ __forceinline__ void tile_rotate_dispatch(int rows, const double* MT, const double* Y, double* Z, int d,
-                                                     int dp) {
-  if (rows <= 1) tile_rotate_fp64<1>(MT, Y, Z, d, dp);
-  else if (rows <= 2) tile_rotate_fp64<2>(MT, Y, Z, d, dp);
-  else if (rows <= 4) tile_rotate_fp64<4>(MT, Y, Z, d, dp);
-  else if (rows <= 8) tile_rotate_fp64<8>(MT, Y, Z, d, dp);
-  else tile_rotate_fp64<16>(MT, Y, Z, d, dp);
-}
 
 // ------------------------------------------------------------------ init
 // Parameter j of individual i: x = lo + (hi - lo) u with u from draws 2j, 2j+1
@@ -153,7 +67,7 @@ __global__ void k_eval_rows(const RunDesc* __restrict__ runs, int run, const dou
   for (int e = threadIdx.x; e < rows * dp; e += blockDim.x) {
     const int r = e / dp, j = e % dp;
     double y = 0.0;
-    if (r < nrows && j < d) y = __dmul_rn(__dsub_rn(x[(size_t)(row0 + r) * ld + j], R.o[j]), R.scale);
+    if (r < nrows && j < d) y = shifted(x[(size_t)(row0 + r) * ld + j], R.o[j], R);
     Y[e] = y;
   }
   __syncthreads();
@@ -173,20 +87,13 @@ __global__ void k_eval_rows(const RunDesc* __restrict__ runs, int run, const dou
   }
 }
 
-// ------------------------------------------------------------------ best record
-__device__ __forceinline__ bool better(double fa, int ia, double fb, int ib) {
-  // a beats b: smaller f, or equal f and lower index; NaN never wins
-  if (fa != fa) return false;
-  if (ib < 0 || fb != fb) return true;
-  return fa < fb || (fa == fb && ia < ib);
-}
-
 // Reduce f[0..np) of the current generation into the run's best record and
 // set the stop flag; single CTA per run.  Used after (re)initialisation.
 __global__ void k_best_init(const RunDesc* __restrict__ runs, int run) {
   const RunDesc& R = runs[run];
   RunState* st = R.st;
-  const int cur = (int)(st->gen & 1);
+  // the FP64 path alternates buffers by generation; the split path updates X[0] in place
+  const int cur = R.prec == 0 ? (int)(st->gen & 1) : 0;
   const double* f = R.f[cur];
   __shared__ double sf[32];
   __shared__ int si[32];
@@ -211,7 +118,8 @@ __global__ void k_best_init(const RunDesc* __restrict__ runs, int run) {
     st->best_f = bf;
     st->best_idx = bi;
     st->ticket = 0;
-    st->ticket2 = 0;
+    st->band_n = 0;
+    st->band_left = 0;
     int stop = 0;
     if (R.target > 0.0 && bi >= 0 && bf < R.target) stop = 1;
     else if (R.max_evals > 0 && st->evals >= R.max_evals) stop = 2;
@@ -219,176 +127,53 @@ __global__ void k_best_init(const RunDesc* __restrict__ runs, int run) {
     st->stop = stop;
     if (bi < 0) st->err |= kErrNonFinite;
   }
-  __syncthreads();
-  const int best = st->best_idx;
-  if (best >= 0)
-    for (int j = threadIdx.x; j < R.dp; j += blockDim.x) R.best_x[j] = R.X[cur][(size_t)best * R.dp + j];
-}
-
-// Finish a generation of a run: called by the last CTA to arrive.  Reduces
-// the tile partials in order, copies the best row, advances the counters and
-// evaluates the stop rule (Sec. 7.3.4).
-__device__ void finish_generation(const RunDesc& R, int64_t g, int nparts, const BestPartial* part,
-                                  const double* Xn) {
-  __shared__ double sf[32];
-  __shared__ int si[32];
-  double bf = CUDART_INF;
-  int bi = -1;
-  for (int t = threadIdx.x; t < nparts; t += blockDim.x) {
-    const double pf = __ldcg(&part[t].f);
-    const int pi = __ldcg(&part[t].idx);
-    if (pi >= 0 && better(pf, pi, bf, bi)) { bf = pf; bi = pi; }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double of = __shfl_xor_sync(0xffffffffu, bf, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (oi >= 0 && better(of, oi, bf, bi)) { bf = of; bi = oi; }
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { sf[warp] = bf; si[warp] = bi; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    bf = CUDART_INF;
-    bi = -1;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-      if (si[w] >= 0 && better(sf[w], si[w], bf, bi)) { bf = sf[w]; bi = si[w]; }
-    RunState* st = R.st;
-    if (bi >= 0) {
-      st->best_f = bf;
-      st->best_idx = bi;
-    } else {
-      st->err |= kErrNonFinite;
-    }
-    st->gen = g;
-    st->evals += R.np;
-    int stop = 0;
-    if (R.target > 0.0 && st->best_idx >= 0 && st->best_f < R.target) stop = 1;
-    else if (R.max_evals > 0 && st->evals >= R.max_evals) stop = 2;
-    else if (g >= R.max_gens) stop = 3;
-    st->stop = stop;
-    si[0] = st->best_idx;
-  }
-  __syncthreads();
-  const int best = si[0];
-  if (best >= 0)
-    for (int j = threadIdx.x; j < R.dp; j += blockDim.x) R.best_x[j] = __ldcg(Xn + (size_t)best * R.dp + j);
-  __syncthreads();
-  if (threadIdx.x == 0) R.st->ticket = 0;
-}
-
-// ------------------------------------------------------------------ trial row
-// Build the trial of target i (Eq. 2 and Eq. 3 with bound repair) with one
-// warp; writes T (trial) and Y = (T - o) s rows of length dp.
-__device__ __forceinline__ double repair(double v, double x, double lo, double hi) {
-  // a coordinate that leaves [lo, hi] goes half way from the target's
-  // coordinate to the violated bound (the paper leaves bounds handling open)
-  if (v < lo) return __dmul_rn(__dadd_rn(x, lo), 0.5);
-  if (v > hi) return __dmul_rn(__dadd_rn(x, hi), 0.5);
-  return v;
-}
-
-__device__ __forceinline__ void build_trial_row(const RunDesc& R, const double* __restrict__ X, uint32_t i,
-                                                int64_t g, int lane, double* __restrict__ Trow,
-                                                double* __restrict__ Yrow, float* ynorm2) {
-  const int d = R.d;
-  const U32x4 b0 = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, i, 0u);
-  uint32_t r1, r2, r3;
-  mutant_indices(b0.x, b0.y, b0.z, i, (uint32_t)R.np, r1, r2, r3);
-  const uint32_t jr = map_to_range(b0.w, (uint32_t)d);
-  const double* xi = X + (size_t)i * R.dp;
-  const double* x1 = X + (size_t)r1 * R.dp;
-  const double* x2 = X + (size_t)r2 * R.dp;
-  const double* x3 = X + (size_t)r3 * R.dp;
-  const bool dbg = R.dbg_trial != nullptr;
-  if (dbg && lane == 0) {
-    R.dbg_idx[3 * i + 0] = (int32_t)r1;
-    R.dbg_idx[3 * i + 1] = (int32_t)r2;
-    R.dbg_idx[3 * i + 2] = (int32_t)r3;
-    R.dbg_jrand[i] = (int32_t)jr;
-  }
-  float yn2 = 0.f;
-  const int nchunks = (d + 127) / 128;
-  for (int c = 0; c < nchunks; ++c) {
-    const int j0 = 128 * c + 4 * lane;
-    uint32_t bits = 0;
-    if (j0 < d) {
-      const U32x4 bc = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, i, 1u + (uint32_t)(j0 >> 2));
-      const double2 xa = *reinterpret_cast<const double2*>(xi + j0);
-      const double2 xb = *reinterpret_cast<const double2*>(xi + j0 + 2);
-      const double2 a1 = *reinterpret_cast<const double2*>(x1 + j0);
-      const double2 b1 = *reinterpret_cast<const double2*>(x1 + j0 + 2);
-      const double2 a2 = *reinterpret_cast<const double2*>(x2 + j0);
-      const double2 b2 = *reinterpret_cast<const double2*>(x2 + j0 + 2);
-      const double2 a3 = *reinterpret_cast<const double2*>(x3 + j0);
-      const double2 b3 = *reinterpret_cast<const double2*>(x3 + j0 + 2);
-      const double tx[4] = {xa.x, xa.y, xb.x, xb.y};
-      const double v1[4] = {a1.x, a1.y, b1.x, b1.y};
-      const double v2[4] = {a2.x, a2.y, b2.x, b2.y};
-      const double v3[4] = {a3.x, a3.y, b3.x, b3.y};
-      const uint32_t u[4] = {bc.x, bc.y, bc.z, bc.w};
-      double t[4], y[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int j = j0 + m;
-        t[m] = 0.0;
-        y[m] = 0.0;
-        if (j < d) {
-          const bool crossed = ((uint32_t)j == jr) || ((uint64_t)u[m] <= R.cr_thr);
-          if (crossed) {
-            // Eq. 2: y = x_r1 + F (x_r2 - x_r3), one rounding for the product-sum
-            const double v = __fma_rn(R.F, __dsub_rn(v2[m], v3[m]), v1[m]);
-            t[m] = repair(v, tx[m], R.lo, R.hi);
-            bits |= 1u << m;
-          } else {
-            t[m] = tx[m];
-          }
-          y[m] = __dmul_rn(__dsub_rn(t[m], R.o[j]), R.scale);
-          yn2 += (float)y[m] * (float)y[m];
-        }
-      }
-      *reinterpret_cast<double2*>(Trow + j0) = make_double2(t[0], t[1]);
-      *reinterpret_cast<double2*>(Trow + j0 + 2) = make_double2(t[2], t[3]);
-      if (Yrow) {
-        *reinterpret_cast<double2*>(Yrow + j0) = make_double2(y[0], y[1]);
-        *reinterpret_cast<double2*>(Yrow + j0 + 2) = make_double2(y[2], y[3]);
-      }
-      if (dbg) {
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-          if (j0 + m < d) R.dbg_trial[(size_t)i * d + j0 + m] = t[m];
-      }
-    }
-    if (dbg) {
-      // lanes 8w .. 8w+7 of this chunk cover mask word 4c + w
-      uint32_t word = (j0 < d) ? (bits << (j0 & 31)) : 0u;
-      word |= __shfl_xor_sync(0xffffffffu, word, 1);
-      word |= __shfl_xor_sync(0xffffffffu, word, 2);
-      word |= __shfl_xor_sync(0xffffffffu, word, 4);
-      const int wi = j0 >> 5;
-      if ((lane & 7) == 0 && wi < R.nw) R.dbg_mask[(size_t)i * R.nw + wi] = word;
-    }
-  }
-  if (ynorm2) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) yn2 += __shfl_xor_sync(0xffffffffu, yn2, o);
-    *ynorm2 = yn2;
-  }
 }
 
 // ------------------------------------------------------------------ generation
-// Shared memory: T, Y, Z tiles of rows x dp doubles (Z aliases Y when there
-// is no rotation).
+// Q groups of 32 flattened outputs (row r, coordinate j) of the tile's
+// rotation, one per accumulator chain: z[r][j] = sum_k M^T[k][j] y[r][k].
+template <int Q>
+__device__ __forceinline__ void rotate_groups(const RunDesc& R, const double* __restrict__ Y, double* __restrict__ Z,
+                                              int w0, int stride, int lane, int nout, int dp) {
+  const int d = R.d;
+  int rr[Q], jj[Q];
+  bool ok[Q];
+  double acc[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int e = (w0 + q * stride) * 32 + lane;
+    ok[q] = e < nout;
+    const int ec = ok[q] ? e : nout - 1;
+    rr[q] = ec / d;
+    jj[q] = ec - rr[q] * d;
+    acc[q] = 0.0;
+  }
+  for (int k = 0; k < d; ++k) {
+    const double* mk = R.MT + (size_t)k * d;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = fma(__ldg(mk + jj[q]), Y[rr[q] * dp + k], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    if (ok[q]) Z[rr[q] * dp + jj[q]] = acc[q];
+}
+
+// items: (run, tile, first row, rows); the rows of all runs are spread over
+// about one CTA per SM so that every SM's FP64 pipe gets the same work.
+// Shared memory: T (trials), Y (shifted trials), Z (rotated), W (second term
+// sum of Ackley), each R.rows x dp doubles.
 __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ runs,
-                                                  const int2* __restrict__ items) {
+                                                  const int4* __restrict__ items) {
   extern __shared__ __align__(16) double sm[];
   __shared__ int s_stop, s_last;
   __shared__ long long s_gen;
   __shared__ double s_bf[8];
   __shared__ int s_bi[8];
-  const int2 it = items[blockIdx.x];
+  const int4 it = items[blockIdx.x];
   const RunDesc& R = runs[it.x];
   RunState* st = R.st;
+  pdl_launch_dependents();
+  pdl_wait();
   if (threadIdx.x == 0) {
     s_stop = *(volatile int32_t*)&st->stop;
     s_gen = *(volatile int64_t*)&st->gen;
@@ -401,29 +186,83 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   double* __restrict__ Xn = R.X[nxt];
   const double* __restrict__ fX = R.f[cur];
   double* __restrict__ fn = R.f[nxt];
-  const int d = R.d, dp = R.dp, rows = R.rows;
-  const int row0 = it.y * rows;
-  const int nrows = min(rows, R.np - row0);
+  const int d = R.d, dp = R.dp;
+  const int row0 = it.z, nrows = it.w, rows_max = R.rows;
   double* T = sm;
-  double* Y = T + rows * dp;
-  double* Z = R.rotate ? Y + rows * dp : Y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  double* Y = T + rows_max * dp;
+  double* Z = Y + rows_max * dp;
+  double* W = Z + rows_max * dp;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
 
-  // rows of the tile past the population end contribute zeros to the GEMM
-  for (int e = nrows * dp + threadIdx.x; e < rows * dp; e += blockDim.x) Y[e] = 0.0;
+  // ---- trials (a warp per target)
   for (int rl = warp; rl < nrows; rl += nwarps)
-    build_trial_row(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp, nullptr);
-  __syncthreads();
-  if (R.rotate) tile_rotate_dispatch(rows, R.MT, Y, Z, d, dp);
+    build_trial_row(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp);
   __syncthreads();
 
+  // ---- rotation, flattened over (row, output): output e = 32 w + lane of
+  // warp-group w; a warp takes groups warp, warp + 8, ... and runs up to four
+  // of them at once (independent accumulator chains)
+  const int nout = nrows * d;
+  if (R.rotate) {
+    const int ngroups = (nout + 31) / 32;
+    for (int w0 = warp; w0 < ngroups; w0 += 4 * nwarps) {
+      const int qn = min(4, (ngroups - w0 + nwarps - 1) / nwarps);  // uniform in the warp
+      if (qn == 4) rotate_groups<4>(R, Y, Z, w0, nwarps, lane, nout, dp);
+      else if (qn == 3) rotate_groups<3>(R, Y, Z, w0, nwarps, lane, nout, dp);
+      else if (qn == 2) rotate_groups<2>(R, Y, Z, w0, nwarps, lane, nout, dp);
+      else rotate_groups<1>(R, Y, Z, w0, nwarps, lane, nout, dp);
+    }
+  } else {
+    for (int e = tid; e < nout; e += blockDim.x) {
+      const int r = e / d, j = e - r * d;
+      Z[r * dp + j] = Y[r * dp + j];
+    }
+  }
+  __syncthreads();
+
+  // ---- objective terms, flattened; Y and W receive the per-coordinate terms
+  for (int e = tid; e < nout; e += blockDim.x) {
+    const int r = e / d, j = e - r * d;
+    const double z = Z[r * dp + j];
+    double t1 = 0.0, t2 = 0.0;
+    if (R.obj == kObjSphere) {
+      t1 = z * z;
+    } else if (R.obj == kObjRastrigin) {
+      t1 = z * z - 10.0 * cos2pi_f64_horner(z) + 10.0;
+    } else if (R.obj == kObjAckley) {
+      t1 = z * z;
+      t2 = cos2pi_f64_horner(z);
+    } else if (R.obj == kObjRosenbrock) {
+      if (j + 1 < d) {
+        const double t0 = z + 1.0, tn = Z[r * dp + j + 1] + 1.0;
+        const double a = tn - t0 * t0, b = t0 - 1.0;
+        t1 = 100.0 * a * a + b * b;
+      }
+    } else {
+      t1 = CUDART_NAN;
+    }
+    Y[r * dp + j] = t1;
+    W[r * dp + j] = t2;
+  }
+  __syncthreads();
+
+  // ---- row sums, greedy selection, best partial (a warp per row)
   double bf = CUDART_INF;
   int bi = -1;
   for (int rl = warp; rl < nrows; rl += nwarps) {
     const int i = row0 + rl;
-    const double ft = row_objective_fp64(R.obj, Z + rl * dp, d, lane);
+    double s1 = 0.0, s2 = 0.0;
+    for (int j = lane; j < d; j += 32) {
+      s1 += Y[rl * dp + j];
+      s2 += W[rl * dp + j];
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    const double ft = R.obj == kObjAckley
+                          ? 20.0 + 2.718281828459045 - 20.0 * exp(-0.2 * sqrt(s1 / d)) - exp(s2 / d)
+                          : s1;
     const double fi = fX[i];
-    const bool acc = ft <= fi;  // false for a NaN trial
+    const bool acc = fit_key(ft) <= fit_key(fi) && fit_key(ft) != 0x7FFFFFFFFFFFFFFFLL;  // ft <= fi, NaN never
     const double* src = acc ? (T + rl * dp) : (X + (size_t)i * dp);
     double2* dst = reinterpret_cast<double2*>(Xn + (size_t)i * dp);
     for (int j = lane; j < dp / 2; j += 32) dst[j] = reinterpret_cast<const double2*>(src)[j];
@@ -440,7 +279,7 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   }
   if (lane == 0) { s_bf[warp] = bf; s_bi[warp] = bi; }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     bf = CUDART_INF;
     bi = -1;
     for (int w = 0; w < nwarps; ++w)
@@ -468,9 +307,21 @@ void k_configure(size_t smem_gen) {
   cudaFuncSetAttribute(k_eval_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-void k_gen_fp64_launch(const RunDesc* runs, const int2* items, int nitems, int threads, size_t smem,
+void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
                        cudaStream_t s) {
-  k_gen_fp64<<<nitems, threads, smem, s>>>(runs, items);
+  // programmatic stream serialization: generation g + 1 is scheduled while
+  // generation g drains, and waits (griddepcontrol.wait) before reading it
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nitems);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_gen_fp64, runs, items);
 }
 
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s) {

@@ -11,7 +11,6 @@
 //            consecutive j for one k is one coalesced row)
 //   Bsplit   tensor-core operand copies of M (split precisions only)
 //   state    one RunState (generation, evaluations, best record, stop flag)
-//   best_x   dp doubles
 //   part     one BestPartial per row tile of the generation kernel
 // A batch of runs is a table of RunDesc in device memory plus a flat list of
 // (run, tile) work items; one launch covers every tile of every run.
@@ -28,7 +27,15 @@ struct RunState {
   int32_t stop;        // de_stop_reason, 0 while running
   uint32_t ticket;     // CTAs of the current generation that finished
   int32_t err;         // device-side error bits (kErr*)
-  uint32_t ticket2;    // second ticket (split-precision fitness kernel)
+  int32_t band_n;      // rows of this generation sent to the FP64 band (split precisions)
+  int32_t band_left;   // of those, rows still waiting for their FP64 decision
+};
+
+// One row whose selection is decided in FP64 (split precisions).
+struct BandEntry {
+  int32_t run;
+  int32_t row;
+  int32_t need_target;  // 1 when the target's stored fitness is not FP64
   int32_t pad;
 };
 
@@ -45,6 +52,9 @@ struct RunDesc {
   // problem
   int32_t np, d, dp, obj;
   double F, CR, lo, hi, scale;
+  long long lo_key, hi_key;  // ordered integer keys of lo and hi
+  int32_t unit_scale;        // scale == 1: the shift needs no multiplication
+  int32_t pad0;
   uint64_t cr_thr;
   uint64_t seed;
   uint32_t run_id;
@@ -59,20 +69,34 @@ struct RunDesc {
   uint8_t* fx[2];
   const double* o;
   const double* MT;
+  const double* Mrow;  // d x d, row-major M (z_j = sum_k M[j][k] y_k), split path FP64 band
   RunState* st;
-  double* best_x;
   BestPartial* part;
   int32_t ntiles;     // tiles of the FP64 generation kernel
   int32_t rows;       // rows per tile of the FP64 generation kernel
   // split-precision path
   double* T;          // np x dp trial rows
-  float* ynorm;       // np, |y|_2 of each trial (error bound of the split GEMM)
-  void* A;            // tensor-core A operand, per 128-row tile
-  const void* B;      // tensor-core B operand (M split), one copy
+  float* ynorm;       // ntiles_tc * 128, |y|_2 of each trial (error bound of the split GEMM)
+  float* tau;         // np, error bound of a split-precision f[i] (0 when f[i] is FP64)
+  unsigned long long* stats;  // [0] FP64 re-evaluations, [1] trials evaluated
+  uint8_t* A;         // tensor-core A operand, ntiles_tc tiles of a_tile_bytes
+  const uint8_t* B;   // tensor-core B operand (M split), nn tiles of b_tile_bytes
   int32_t kpad, npad; // padded K (= input dim) and N (= output dim) of the GEMM
   int32_t ntiles_tc;  // 128-row tiles
+  int32_t kc;         // K elements staged per pipeline step
+  int32_t ntn;        // N tile width (columns of one accumulator), <= 256
+  int32_t nn;         // number of N tiles
+  int32_t esz;        // operand element bytes: 2 (bf16) or 4 (tf32)
+  int32_t a_tile_bytes, b_tile_bytes;
+  int32_t nch;        // column chunks of the FP64 band kernel
+  int32_t band_cw;    // columns per chunk (<= 32)
+  BandEntry* band;    // shared list of FP64-decided rows (all runs of the handle)
+  uint32_t* band_cnt; // its length this generation
+  double2* band_part; // per entry: [2 vectors][nch_max] partial sums (s1, s2)
+  uint32_t* band_tk;  // per entry: chunk tickets
+  int32_t nch_max;    // chunks per vector slot in band_part
   float rownorm;      // max_j |M_j|_2
-  float band_u;       // unit error of the split product
+  float band_u;       // unit error of one split product sum, relative to sum_k |M_jk y_k|
   // debug capture (all NULL unless enabled)
   int32_t* dbg_idx;
   int32_t* dbg_jrand;

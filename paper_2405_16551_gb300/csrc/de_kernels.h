@@ -12,7 +12,7 @@ namespace de {
 
 // FP64 path (de_fp64.cu)
 void k_configure(size_t smem_gen);
-void k_gen_fp64_launch(const RunDesc* runs, const int2* items, int nitems, int threads, size_t smem,
+void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
                        cudaStream_t s);
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s);
 void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int rotate,
@@ -26,8 +26,16 @@ struct TcPlan {
   int nitems_fit = 0;     // 128-row tiles over all runs
   int2* d_trial_items = nullptr;
   int2* d_fit_items = nullptr;
-  void* arena = nullptr;  // operand copies of M and the A tiles
+  void* arena = nullptr;  // operand copies of M, the A tiles, |y|, tau, stats
   size_t smem_fit = 0;
+  std::vector<int> fit_offset;  // first fit item of each run
+  BandEntry* d_band = nullptr;  // FP64 band list (all runs)
+  uint32_t* d_band_cnt = nullptr;
+  int nch_max = 1;
+  size_t smem_band = 0;
+  int grid_band = 0;
+  int trial_rows = 8;          // targets (warps) per trial CTA
+  int nruns = 0;
 };
 de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* cfgs, int prec, cudaStream_t s,
                         std::string& err);

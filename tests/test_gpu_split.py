@@ -1,0 +1,120 @@
+"""GPU parity of the split-precision (BF16x3 / TF32x3 tcgen05) path against
+the FP64 CPU oracle.
+
+The trial construction is the FP64 one in every precision, so indices, masks
+and trials must match the oracle bit for bit.  The split-precision fitness
+must stay within the kernel's stated bound; every selection decision must
+equal the oracle's outside the FP64 tolerance band, because comparisons the
+split values cannot decide are redone in FP64.  Through the C ABI only.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_16551_gb300 import capi, problems
+
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-12
+# split-precision fitness tolerance relative to (|f| + S); S as defined by the
+# oracle (term magnitudes plus first-order rounding of their inputs)
+REL_SPLIT = {capi.DE_PREC_BF16X3: 1e-5, capi.DE_PREC_TF32X3: 1e-6}
+PRECS = [capi.DE_PREC_BF16X3, capi.DE_PREC_TF32X3]
+
+
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("obj", [0, 1, 2, 3])
+@pytest.mark.parametrize("d", [10, 100, 130])
+def test_split_eval_within_tolerance(prec, obj, d):
+    torch = _need_gpu()
+    o = problems.shift(d, seed=2)
+    M = problems.rotation(d, seed=2)
+    X = problems.population(700, d, seed=3)
+    X[:200] = o + np.random.default_rng(1).normal(size=(200, d)) * np.logspace(-5, 1, 200)[:, None]
+    cfg = capi.make_config(64, d, objective=obj, shift=o, rot=M, precision=prec, max_generations=1)
+    h = capi.de_init(cfg)
+    try:
+        xd = torch.from_numpy(X).cuda()
+        fd = torch.zeros(len(X), dtype=torch.float64, device="cuda")
+        capi.de_eval(h, 0, xd.data_ptr(), d, len(X), fd.data_ptr())
+        torch.cuda.synchronize()
+    finally:
+        capi.de_destroy(h)
+    f = fd.cpu().numpy()
+    fo, sabs = oracle.evaluate(obj, X, o, M)
+    err = np.abs(f - fo) / (np.abs(fo) + sabs)
+    assert err.max() <= REL_SPLIT[prec], err.max()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize(
+    "np_,d,obj,F,CR",
+    [(1024, 100, 1, 0.5, 0.9), (64, 10, 0, 0.5, 0.9), (300, 37, 2, 0.8, 0.3), (130, 64, 3, 0.5, 1.0),
+     (4, 1, 1, 0.5, 0.9)],
+)
+def test_split_generation_matches_oracle(prec, np_, d, obj, F, CR):
+    _need_gpu()
+    o = problems.shift(d, seed=7)
+    M = problems.rotation(d, seed=7)
+    X = problems.population(np_, d, seed=7)
+    fX, _ = oracle.evaluate(obj, X, o, M)
+    cfg = capi.make_config(np_, d, f=F, cr=CR, objective=obj, shift=o, rot=M, seed=7, precision=prec,
+                           max_generations=10**6, target_error=0.0, debug_capture=True)
+    h = capi.de_init(cfg)
+    try:
+        capi.de_set_population(h, 0, X, fX)
+        capi.de_set_generation(h, 0, 4)
+        capi.de_step(h, 1)
+        g = capi.de_get_debug(h)
+        xn, fn = capi.de_get_population(h)
+        best = capi.de_get_best(h)
+    finally:
+        capi.de_destroy(h)
+    r = oracle.step(X, fX, F, CR, -100, 100, obj, o, M, seed=7, generation=5)
+    assert np.array_equal(g["idx"], r["idx"])
+    assert np.array_equal(g["jrand"], r["jrand"])
+    assert np.array_equal(g["mask"], r["mask"])
+    assert np.array_equal(g["trial"], r["trial"])
+    fp64 = g["fp64_checked"].astype(bool)
+    scale = np.abs(r["f_trial"]) + r["sabs_trial"]
+    tol = np.where(fp64, REL64, REL_SPLIT[prec]) * scale
+    assert np.all(np.abs(g["f_trial"] - r["f_trial"]) <= tol)
+    band = np.abs(r["f_trial"] - fX) <= REL64 * scale
+    assert np.array_equal(g["accept"][~band], r["accept"][~band])
+    acc = g["accept"].astype(bool)
+    assert np.array_equal(xn[acc], r["trial"][acc])
+    assert np.array_equal(xn[~acc], X[~acc])
+    # the best record is an FP64 value of the best individual
+    b = best["best_index"]
+    fo_b, sb = oracle.evaluate(obj, xn[b:b + 1], o, M)
+    assert abs(best["best_f"] - fo_b[0]) <= REL64 * (abs(fo_b[0]) + sb[0])
+    assert abs(best["best_f"] - r["f_next"].min()) <= REL64 * (abs(fo_b[0]) + sb[0])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_split_run_follows_the_fp64_trajectory(prec):
+    """With the FP64 band deciding every comparison the split values cannot,
+    the split-precision run of the small sphere workload takes the same
+    decisions as the FP64 oracle: same population, same stop generation."""
+    _need_gpu()
+    d = 10
+    o = problems.shift(d, seed=1)
+    Xo, fo, go, evo, _ = oracle.run(64, d, 0.5, 0.9, -100, 100, 0, o, None, seed=1, max_generations=1000,
+                                    target_error=1e-8)
+    h = capi.de_init(capi.make_config(64, d, objective=0, shift=o, seed=1, precision=prec, max_generations=1000,
+                                      target_error=1e-8))
+    try:
+        res = capi.de_run(h)[0]
+        x, f = capi.de_get_population(h)
+    finally:
+        capi.de_destroy(h)
+    assert res["generations"] == go and res["evals"] == evo
+    assert np.array_equal(x, Xo)
+    assert res["best_f"] < 1e-8
