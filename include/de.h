@@ -83,9 +83,9 @@ typedef enum {
  *   BF16X3   tcgen05 tensor cores: y and M split into bf16 high and low parts,
  *            z = yh Mh + yh Ml + yl Mh accumulated in FP32 (TMEM); FP32 terms.
  *   TF32X3   the same with tf32 parts.
- * In BF16X3/TF32X3 the selection comparison is redone in FP64 when the two
- * fitness values are within the split-precision tolerance of each other or
- * below the near-optimum threshold, and the best-so-far record is FP64. */
+ * In BF16X3/TF32X3 the selection comparison is redone in FP64 as de_fp64_band
+ * says, and the best-so-far record returned by de_get_best / de_run is the
+ * FP64 fitness of the best individual. */
 typedef enum {
     DE_PREC_FP64 = 0,
     DE_PREC_BF16X3 = 1,
@@ -117,7 +117,25 @@ typedef struct {
     int64_t max_evals;        /* stop once evaluations >= max_evals, counting the initial NP; 0 = none */
     int64_t max_generations;  /* stop after this many generations (de_run); >= 0 */
     int32_t debug_capture;    /* nonzero: keep indices, masks, trials, f_trial and flags of the last generation */
+    int32_t fp64_band;        /* split precisions: de_fp64_band, when a selection is redone in FP64 */
 } de_config;
+
+/* When the split precisions redo a selection comparison in FP64.
+ *   DE_BAND_NEAR (default)  the split values cannot decide it within their
+ *                           error bound and one of the two values is near the
+ *                           optimum (below target_error / (8 u), u the unit
+ *                           error of the split product), or the trial could
+ *                           meet the stop target; elsewhere the split values
+ *                           decide, and a decision may then differ from the
+ *                           FP64 one only inside the split error bound
+ *   DE_BAND_ALL             every comparison the split values cannot decide,
+ *                           and every trial that could become the best: the
+ *                           run takes the FP64 decisions everywhere (up to
+ *                           FP64 rounding) at the cost of more FP64 work */
+typedef enum {
+    DE_BAND_NEAR = 0,
+    DE_BAND_ALL = 1
+} de_fp64_band;
 
 /* Result of de_run for one run. */
 typedef struct {
@@ -195,7 +213,7 @@ DE_API de_status de_set_population(de_handle* h, int32_t run, const double* x_ho
 /* Set the generation counter of run `run` (the next de_step runs g + 1). */
 DE_API de_status de_set_generation(de_handle* h, int32_t run, int64_t generation);
 
-/* Best record of run `run`: best_f (FP64), its index, a copy of its vector
+/* Best record of run `run`: best_f, its index, a copy of its vector
  * (host, d doubles, may be NULL), and generation/evaluation counters. */
 DE_API de_status de_get_best(de_handle* h, int32_t run, double* best_f, int32_t* best_index, double* best_x,
                       int64_t* generations, int64_t* evals, int32_t* stop_reason);
@@ -206,6 +224,17 @@ DE_API de_status de_get_debug(de_handle* h, int32_t run, const de_debug* out);
 
 /* Number of runs in the handle, and run `run`'s np and d. */
 DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d, int32_t* nruns);
+
+/* Which kernel path runs the generations of this handle:
+ *   0  FP64: one fused kernel per generation
+ *   1  split precision, three kernels per generation (trial, tensor-core
+ *      fitness and selection, FP64 band), in CUDA graphs
+ *   2  split precision, one persistent cluster kernel for many generations
+ * cluster_size (may be NULL) receives the CTAs per cluster of path 2, else 0;
+ * each cluster owns 64 or 128 targets.
+ * Path 2 is chosen at de_init for a single run whose clusters all fit on the
+ * device at once; the environment variable DE_GB300_PERSIST=0 disables it. */
+DE_API de_status de_get_plan(de_handle* h, int32_t* kernel_path, int32_t* cluster_size);
 
 /* Counters of the split-precision selection of run `run` since de_init:
  * trials whose comparison (or best-record candidacy) was decided on FP64

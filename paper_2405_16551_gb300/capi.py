@@ -21,6 +21,7 @@ DE_ERR_NONFINITE, DE_ERR_STATE, DE_ERR_IO, DE_ERR_UNSUPPORTED = 5, 6, 7, 8
 DE_OBJ_SPHERE, DE_OBJ_RASTRIGIN, DE_OBJ_ROSENBROCK, DE_OBJ_ACKLEY, DE_OBJ_ODE = 0, 1, 2, 3, 4
 DE_PREC_FP64, DE_PREC_BF16X3, DE_PREC_TF32X3 = 0, 1, 2
 DE_STOP_NONE, DE_STOP_TARGET, DE_STOP_EVALS, DE_STOP_GENERATIONS = 0, 1, 2, 3
+DE_BAND_NEAR, DE_BAND_ALL = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -35,7 +36,7 @@ class de_config(ctypes.Structure):
                 ("scale", ctypes.c_double), ("shift", _dp), ("rot", _dp), ("seed", ctypes.c_uint64),
                 ("run_id", ctypes.c_uint32), ("precision", ctypes.c_int32), ("target_error", ctypes.c_double),
                 ("max_evals", ctypes.c_int64), ("max_generations", ctypes.c_int64),
-                ("debug_capture", ctypes.c_int32)]
+                ("debug_capture", ctypes.c_int32), ("fp64_band", ctypes.c_int32)]
 
 
 class de_result(ctypes.Structure):
@@ -99,6 +100,7 @@ def load(build_if_missing: bool = True):
             "de_get_debug": ([H, ctypes.c_int32, ctypes.POINTER(de_debug)], ctypes.c_int),
             "de_get_shape": ([H, ctypes.c_int32, _i32p, _i32p, _i32p], ctypes.c_int),
             "de_get_stats": ([H, ctypes.c_int32, _i64p, _i64p], ctypes.c_int),
+            "de_get_plan": ([H, _i32p, _i32p], ctypes.c_int),
             "de_save": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_load": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_destroy": ([H], ctypes.c_int),
@@ -114,7 +116,7 @@ def load(build_if_missing: bool = True):
 def exported_symbols():
     return ["de_version", "de_status_string", "de_last_error", "de_init", "de_init_batch", "de_reset", "de_step", "de_run",
             "de_eval", "de_get_population", "de_set_population", "de_set_generation", "de_get_best",
-            "de_get_debug", "de_get_shape", "de_get_stats", "de_save", "de_load", "de_destroy"]
+            "de_get_debug", "de_get_shape", "de_get_stats", "de_get_plan", "de_save", "de_load", "de_destroy"]
 
 
 def _status_name(s):
@@ -141,13 +143,14 @@ def de_version() -> str:
 
 def make_config(np_, d, f=0.5, cr=0.9, lo=-100.0, hi=100.0, objective=DE_OBJ_SPHERE, scale=1.0, shift=None,
                 rot=None, seed=1, run_id=0, precision=DE_PREC_FP64, target_error=1e-8, max_evals=0,
-                max_generations=1000, debug_capture=False):
+                max_generations=1000, debug_capture=False, fp64_band=DE_BAND_NEAR):
     """A de_config; the returned object keeps the shift/rotation arrays alive."""
     c = de_config()
     c.np, c.d, c.f, c.cr, c.lo, c.hi = np_, d, f, cr, lo, hi
     c.objective, c.scale, c.seed, c.run_id, c.precision = objective, scale, seed, run_id, precision
     c.target_error, c.max_evals, c.max_generations = target_error, max_evals, max_generations
     c.debug_capture = 1 if debug_capture else 0
+    c.fp64_band = fp64_band
     keep = []
     if shift is not None:
         s = np.ascontiguousarray(shift, dtype=np.float64)
@@ -244,6 +247,12 @@ def de_get_stats(h, run: int = 0):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(load().de_get_stats(h, run, ctypes.byref(a), ctypes.byref(b)), h)
     return dict(fp64_reevals=a.value, trials=b.value)
+
+
+def de_get_plan(h):
+    p, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().de_get_plan(h, ctypes.byref(p), ctypes.byref(c)), h)
+    return dict(kernel_path=p.value, cluster_size=c.value)
 
 
 def de_save(h, path: str):

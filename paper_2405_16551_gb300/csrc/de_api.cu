@@ -27,6 +27,7 @@ struct de_handle {
   int device = 0;
   int nruns = 0;
   int prec = DE_PREC_FP64;
+  bool dbuf = true;         // generation g in X[g & 1] (FP64 and persistent split paths)
   std::vector<de_config> cfg;
   std::vector<RunDesc> run;  // host copy of the descriptors
   RunDesc* d_run = nullptr;
@@ -47,7 +48,7 @@ struct de_handle {
 // Buffer holding the population of generation `gen`: the FP64 kernel writes
 // generation g + 1 into the other buffer; the split-precision kernels update
 // buffer 0 in place.
-static int cur_buf(const de_handle* h, int64_t gen) { return h->prec == DE_PREC_FP64 ? (int)(gen & 1) : 0; }
+static int cur_buf(const de_handle* h, int64_t gen) { return h->dbuf ? (int)(gen & 1) : 0; }
 
 static thread_local std::string g_err;
 static const char* kVersion = "de_gb300 1.0 sm_103a";
@@ -88,6 +89,7 @@ static de_status validate(const de_config& c, int idx, std::string& why) {
   if (c.run_id >= (1u << 20)) return bad("run_id must be < 2^20");
   if (c.precision < DE_PREC_FP64 || c.precision > DE_PREC_TF32X3) return bad("precision out of range");
   if (c.max_evals < 0 || c.max_generations < 0) return bad("max_evals and max_generations must be >= 0");
+  if (c.fp64_band != DE_BAND_NEAR && c.fp64_band != DE_BAND_ALL) return bad("fp64_band out of range");
   if (!std::isfinite(c.target_error) && !(c.target_error < 0)) return bad("target_error must be finite");
   if (c.shift)
     for (int j = 0; j < c.d; ++j)
@@ -154,6 +156,11 @@ static de_status launch_generation(de_handle* h, cudaStream_t s) {
 static de_status launch_generation(de_handle* h) { return launch_generation(h, h->stream); }
 
 static de_status enqueue_generations(de_handle* h, int64_t n) {
+  if (h->prec != DE_PREC_FP64 && h->tc.persist.ok) {
+    // one persistent launch runs all n generations (or stops early)
+    if (n > 0) DE_CUDA(h, persist_launch(h->tc.persist, h->d_run, h->tc.d_ctl, n, h->stream));
+    return DE_OK;
+  }
   const int kChunk = 64;
   if (n >= kChunk) {
     if (!h->graph || h->graph_gens != kChunk) {
@@ -218,6 +225,30 @@ static de_status init_run(de_handle* h, int r) {
   k_eval_rows_launch(h->d_run, r, R.X[0], R.dp, R.np, R.dp, R.rotate, R.f[0], R.fx[0], h->stream);
   k_best_init_launch(h->d_run, r, h->stream);
   DE_CUDA(h, cudaGetLastError());
+  return DE_OK;
+}
+
+// Split precisions keep some fitness values in split precision; the best
+// record handed to a caller is made FP64 here (the best row is evaluated in
+// FP64 when its stored value is not).
+static de_status exact_best(de_handle* h, int r) {
+  if (h->prec == DE_PREC_FP64) return DE_OK;
+  RunState& st = h->h_state[r];
+  if (st.best_idx < 0) return DE_OK;
+  const RunDesc& R = h->run[r];
+  const int cur = cur_buf(h, st.gen);
+  uint8_t fx = 1;
+  DE_CUDA(h, cudaMemcpyAsync(&fx, R.fx[cur] + st.best_idx, 1, cudaMemcpyDeviceToHost, h->stream));
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (fx) return DE_OK;
+  double* fb = R.f[cur] + st.best_idx;
+  k_eval_rows_launch(h->d_run, r, R.X[cur] + (size_t)st.best_idx * R.dp, R.dp, 1, R.dp, R.rotate, fb,
+                     R.fx[cur] + st.best_idx, h->stream);
+  DE_CUDA(h, cudaGetLastError());
+  DE_CUDA(h, cudaMemcpyAsync(&st.best_f, fb, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  DE_CUDA(h, cudaMemcpyAsync(&R.st->best_f, &st.best_f, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
   return DE_OK;
 }
 
@@ -508,6 +539,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     R.max_gens = c.max_generations;
     R.prec = c.precision;
     R.nw = (c.d + 31) / 32;
+    R.band_all = c.fp64_band == DE_BAND_ALL;
     char* A = h->arena;
     R.X[0] = (double*)(A + O.X0);
     R.X[1] = (double*)(A + O.X1);
@@ -557,7 +589,11 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
       R.rownorm = 1.0f;
     }
   }
-  if (h->prec != DE_PREC_FP64) TRY(tc_plan_build(h->tc, h->run, cfgs, h->prec, h->stream, h->err));
+  if (h->prec != DE_PREC_FP64) {
+    TRY(tc_plan_build(h->tc, h->run, cfgs, h->prec, h->stream, h->err));
+    h->dbuf = h->tc.persist.ok;
+  }
+  for (auto& R : h->run) R.dbuf = h->dbuf ? 1 : 0;
   TRY(build_items(h));
   TRY(upload_desc(h));
   k_configure(h->smem_gen);
@@ -621,6 +657,10 @@ de_status de_run(de_handle* h, de_result* out) {
     s = check_device_errors(h);
     if (s != DE_OK) return s;
     chunk = std::min<int64_t>(chunk * 2, 1024);
+  }
+  for (int r = 0; r < h->nruns && out; ++r) {
+    s = exact_best(h, r);
+    if (s != DE_OK) return s;
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (out)
@@ -743,6 +783,8 @@ de_status de_get_best(de_handle* h, int32_t run, double* best_f, int32_t* best_i
   const RunDesc& R = h->run[run];
   de_status s = read_states(h);
   if (s != DE_OK) return s;
+  s = exact_best(h, run);
+  if (s != DE_OK) return s;
   const RunState& st = h->h_state[run];
   if (best_x) {
     // the best individual's vector, read from the current population
@@ -777,6 +819,14 @@ de_status de_get_debug(de_handle* h, int32_t run, const de_debug* out) {
   DE_CUDA(h, cp(out->accept, R.dbg_accept, (size_t)R.np));
   DE_CUDA(h, cp(out->fp64_checked, R.dbg_fp64, (size_t)R.np));
   DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DE_OK;
+}
+
+de_status de_get_plan(de_handle* h, int32_t* kernel_path, int32_t* cluster_size) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  const bool persist = h->prec != DE_PREC_FP64 && h->tc.persist.ok;
+  if (kernel_path) *kernel_path = h->prec == DE_PREC_FP64 ? 0 : (persist ? 2 : 1);
+  if (cluster_size) *cluster_size = persist ? h->tc.persist.C : 0;
   return DE_OK;
 }
 

@@ -297,29 +297,37 @@ __device__ __forceinline__ TrialSetup trial_setup(const RunDesc& R, uint32_t i, 
   return s;
 }
 
-// Coordinates j0 .. j0+3 (j0 < d, j0 % 4 == 0) of the trial; entries at
-// j >= d are 0.  Returns the crossed-coordinate bits (bit m for j0 + m).
-__device__ __forceinline__ uint32_t trial_chunk(const RunDesc& R, const double* __restrict__ X, const TrialSetup& s,
-                                                uint32_t i, int64_t g, int j0, double t[4]) {
+// Inputs of one 4-coordinate chunk of a trial: the target's and the three
+// donors' coordinates and the chunk's Philox block (rand_j of Eq. 3).
+struct ChunkIn {
+  double xi[4], x1[4], x2[4], x3[4];
+  U32x4 u;
+};
+
+// Issue the loads of chunk j0 (j0 < d, j0 % 4 == 0) and draw its block.
+__device__ __forceinline__ void trial_load(const RunDesc& R, const double* __restrict__ X, const TrialSetup& s,
+                                           uint32_t i, int64_t g, int j0, ChunkIn& c) {
+  c.u = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, i, 1u + (uint32_t)(j0 >> 2));
+  const double* rows[4] = {X + (size_t)i * R.dp + j0, X + (size_t)s.r1 * R.dp + j0, X + (size_t)s.r2 * R.dp + j0,
+                           X + (size_t)s.r3 * R.dp + j0};
+  double* dst[4] = {c.xi, c.x1, c.x2, c.x3};
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const double2 a = *reinterpret_cast<const double2*>(rows[r]);
+    const double2 b = *reinterpret_cast<const double2*>(rows[r] + 2);
+    dst[r][0] = a.x;
+    dst[r][1] = a.y;
+    dst[r][2] = b.x;
+    dst[r][3] = b.y;
+  }
+}
+
+// Coordinates j0 .. j0+3 of the trial from loaded inputs; entries at j >= d
+// are 0.  Returns the crossed-coordinate bits (bit m for j0 + m).
+__device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialSetup& s, int j0, const ChunkIn& c,
+                                                  double t[4]) {
   const int d = R.d;
-  const U32x4 bc = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, i, 1u + (uint32_t)(j0 >> 2));
-  const double* xi = X + (size_t)i * R.dp + j0;
-  const double* x1 = X + (size_t)s.r1 * R.dp + j0;
-  const double* x2 = X + (size_t)s.r2 * R.dp + j0;
-  const double* x3 = X + (size_t)s.r3 * R.dp + j0;
-  const double2 xa = *reinterpret_cast<const double2*>(xi);
-  const double2 xb = *reinterpret_cast<const double2*>(xi + 2);
-  const double2 a1 = *reinterpret_cast<const double2*>(x1);
-  const double2 b1 = *reinterpret_cast<const double2*>(x1 + 2);
-  const double2 a2 = *reinterpret_cast<const double2*>(x2);
-  const double2 b2 = *reinterpret_cast<const double2*>(x2 + 2);
-  const double2 a3 = *reinterpret_cast<const double2*>(x3);
-  const double2 b3 = *reinterpret_cast<const double2*>(x3 + 2);
-  const double tx[4] = {xa.x, xa.y, xb.x, xb.y};
-  const double v1[4] = {a1.x, a1.y, b1.x, b1.y};
-  const double v2[4] = {a2.x, a2.y, b2.x, b2.y};
-  const double v3[4] = {a3.x, a3.y, b3.x, b3.y};
-  const uint32_t u[4] = {bc.x, bc.y, bc.z, bc.w};
+  const uint32_t u[4] = {c.u.x, c.u.y, c.u.z, c.u.w};
   uint32_t bits = 0;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -329,15 +337,24 @@ __device__ __forceinline__ uint32_t trial_chunk(const RunDesc& R, const double* 
       const bool crossed = ((uint32_t)j == s.jr) || ((uint64_t)u[m] <= R.cr_thr);
       if (crossed) {
         // Eq. 2: y = x_r1 + F (x_r2 - x_r3), one rounding for the product-sum
-        const double v = __fma_rn(R.F, __dsub_rn(v2[m], v3[m]), v1[m]);
-        t[m] = repair(v, tx[m], R);
+        const double v = __fma_rn(R.F, __dsub_rn(c.x2[m], c.x3[m]), c.x1[m]);
+        t[m] = repair(v, c.xi[m], R);
         bits |= 1u << m;
       } else {
-        t[m] = tx[m];
+        t[m] = c.xi[m];
       }
     }
   }
   return bits;
+}
+
+// Coordinates j0 .. j0+3 (j0 < d, j0 % 4 == 0) of the trial; entries at
+// j >= d are 0.  Returns the crossed-coordinate bits (bit m for j0 + m).
+__device__ __forceinline__ uint32_t trial_chunk(const RunDesc& R, const double* __restrict__ X, const TrialSetup& s,
+                                                uint32_t i, int64_t g, int j0, double t[4]) {
+  ChunkIn c;
+  trial_load(R, X, s, i, g, j0, c);
+  return trial_compute(R, s, j0, c, t);
 }
 
 // Debug capture of one chunk: trial values and the crossover mask word.

@@ -92,8 +92,9 @@ __global__ void k_eval_rows(const RunDesc* __restrict__ runs, int run, const dou
 __global__ void k_best_init(const RunDesc* __restrict__ runs, int run) {
   const RunDesc& R = runs[run];
   RunState* st = R.st;
-  // the FP64 path alternates buffers by generation; the split path updates X[0] in place
-  const int cur = R.prec == 0 ? (int)(st->gen & 1) : 0;
+  // double-buffered paths alternate buffers by generation; the three-kernel
+  // split path updates X[0] in place
+  const int cur = R.dbuf ? (int)(st->gen & 1) : 0;
   const double* f = R.f[cur];
   __shared__ double sf[32];
   __shared__ int si[32];

@@ -62,7 +62,9 @@ struct RunDesc {
   double target;
   int64_t max_evals, max_gens;
   int32_t prec;
-  int32_t nw;  // ceil(d / 32)
+  int32_t nw;    // ceil(d / 32)
+  int32_t dbuf;  // 1: generation g lives in X[g & 1]; 0: the split kernels update X[0] in place
+  int32_t pad1;
   // buffers
   double* X[2];
   double* f[2];
@@ -97,6 +99,8 @@ struct RunDesc {
   int32_t nch_max;    // chunks per vector slot in band_part
   float rownorm;      // max_j |M_j|_2
   float band_u;       // unit error of one split product sum, relative to sum_k |M_jk y_k|
+  int32_t band_all;   // 1: every undecidable comparison and every possible new best go to FP64
+  float near_thr;     // fitness below which an undecidable comparison goes to FP64
   // debug capture (all NULL unless enabled)
   int32_t* dbg_idx;
   int32_t* dbg_jrand;

@@ -19,6 +19,18 @@ void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t l
                         double* f, uint8_t* fx, cudaStream_t s);
 void k_best_init_launch(const RunDesc* runs, int run, cudaStream_t s);
 
+// persistent cluster path (de_persist.cu)
+struct PersistCtl {
+  unsigned int bar;  // grid barrier arrivals of the current launch
+  int abort;         // set when a bounded wait expired
+  long long gen0;    // generation counter when the launch began
+};
+struct PersistPlan {
+  bool ok = false;
+  int C = 0, ntiles = 0, prec = 0, nch = 1, prows = 128;
+  size_t smem = 0;
+};
+
 // split-precision tensor-core path (de_tc.cu)
 struct TcPlan {
   int prec = 0;
@@ -36,7 +48,13 @@ struct TcPlan {
   int grid_band = 0;
   int trial_rows = 8;          // targets (warps) per trial CTA
   int nruns = 0;
+  PersistPlan persist;         // the persistent cluster kernel, when it applies
+  PersistCtl* d_ctl = nullptr;
 };
+bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec);
+cudaError_t persist_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
+                           cudaStream_t s);
+
 de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* cfgs, int prec, cudaStream_t s,
                         std::string& err);
 void tc_plan_free(TcPlan& p);

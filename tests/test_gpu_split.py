@@ -22,6 +22,24 @@ REL_SPLIT = {capi.DE_PREC_BF16X3: 1e-5, capi.DE_PREC_TF32X3: 1e-6}
 PRECS = [capi.DE_PREC_BF16X3, capi.DE_PREC_TF32X3]
 
 
+@pytest.fixture(params=["persistent", "three-kernel"])
+def split_path(request, monkeypatch):
+    """Run a test on both split-precision kernel paths; the persistent cluster
+    path is chosen at de_init unless DE_GB300_PERSIST=0."""
+    monkeypatch.setenv("DE_GB300_PERSIST", "1" if request.param == "persistent" else "0")
+    return request.param
+
+
+def _check_path(h, split_path):
+    plan = capi.de_get_plan(h)
+    if split_path == "three-kernel":
+        assert plan["kernel_path"] == 1
+    else:
+        assert plan["kernel_path"] in (1, 2)
+        return plan["kernel_path"] == 2
+    return False
+
+
 def _need_gpu():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
@@ -53,22 +71,24 @@ def test_split_eval_within_tolerance(prec, obj, d):
     assert err.max() <= REL_SPLIT[prec], err.max()
 
 
+@pytest.mark.parametrize("band", [capi.DE_BAND_ALL, capi.DE_BAND_NEAR])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize(
     "np_,d,obj,F,CR",
     [(1024, 100, 1, 0.5, 0.9), (64, 10, 0, 0.5, 0.9), (300, 37, 2, 0.8, 0.3), (130, 64, 3, 0.5, 1.0),
      (4, 1, 1, 0.5, 0.9)],
 )
-def test_split_generation_matches_oracle(prec, np_, d, obj, F, CR):
+def test_split_generation_matches_oracle(prec, np_, d, obj, F, CR, split_path, band):
     _need_gpu()
     o = problems.shift(d, seed=7)
     M = problems.rotation(d, seed=7)
     X = problems.population(np_, d, seed=7)
     fX, _ = oracle.evaluate(obj, X, o, M)
     cfg = capi.make_config(np_, d, f=F, cr=CR, objective=obj, shift=o, rot=M, seed=7, precision=prec,
-                           max_generations=10**6, target_error=0.0, debug_capture=True)
+                           max_generations=10**6, target_error=0.0, debug_capture=True, fp64_band=band)
     h = capi.de_init(cfg)
     try:
+        _check_path(h, split_path)
         capi.de_set_population(h, 0, X, fX)
         capi.de_set_generation(h, 0, 4)
         capi.de_step(h, 1)
@@ -86,8 +106,12 @@ def test_split_generation_matches_oracle(prec, np_, d, obj, F, CR):
     scale = np.abs(r["f_trial"]) + r["sabs_trial"]
     tol = np.where(fp64, REL64, REL_SPLIT[prec]) * scale
     assert np.all(np.abs(g["f_trial"] - r["f_trial"]) <= tol)
-    band = np.abs(r["f_trial"] - fX) <= REL64 * scale
-    assert np.array_equal(g["accept"][~band], r["accept"][~band])
+    # with every undecidable comparison in FP64, decisions differ from the
+    # oracle's only inside the FP64 band; with the near-optimum policy, also
+    # inside the split-precision band of the trial (targets here are FP64)
+    rel = REL64 if band == capi.DE_BAND_ALL else REL_SPLIT[prec]
+    inband = np.abs(r["f_trial"] - fX) <= rel * scale
+    assert np.array_equal(g["accept"][~inband], r["accept"][~inband])
     acc = g["accept"].astype(bool)
     assert np.array_equal(xn[acc], r["trial"][acc])
     assert np.array_equal(xn[~acc], X[~acc])
@@ -99,7 +123,7 @@ def test_split_generation_matches_oracle(prec, np_, d, obj, F, CR):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_split_run_follows_the_fp64_trajectory(prec):
+def test_split_run_follows_the_fp64_trajectory(prec, split_path):
     """With the FP64 band deciding every comparison the split values cannot,
     the split-precision run of the small sphere workload takes the same
     decisions as the FP64 oracle: same population, same stop generation."""
@@ -109,8 +133,9 @@ def test_split_run_follows_the_fp64_trajectory(prec):
     Xo, fo, go, evo, _ = oracle.run(64, d, 0.5, 0.9, -100, 100, 0, o, None, seed=1, max_generations=1000,
                                     target_error=1e-8)
     h = capi.de_init(capi.make_config(64, d, objective=0, shift=o, seed=1, precision=prec, max_generations=1000,
-                                      target_error=1e-8))
+                                      target_error=1e-8, fp64_band=capi.DE_BAND_ALL))
     try:
+        _check_path(h, split_path)
         res = capi.de_run(h)[0]
         x, f = capi.de_get_population(h)
     finally:
@@ -118,3 +143,59 @@ def test_split_run_follows_the_fp64_trajectory(prec):
     assert res["generations"] == go and res["evals"] == evo
     assert np.array_equal(x, Xo)
     assert res["best_f"] < 1e-8
+
+
+def test_persistent_path_is_used_for_the_rotated_rastrigin_workload():
+    """NP=1024, D=100 in split precision runs on the persistent cluster kernel."""
+    _need_gpu()
+    d = 100
+    o, M = problems.shift(d, seed=1), problems.rotation(d, seed=1)
+    for prec in PRECS:
+        h = capi.de_init(capi.make_config(1024, d, objective=1, shift=o, rot=M, precision=prec,
+                                          max_generations=10))
+        try:
+            plan = capi.de_get_plan(h)
+        finally:
+            capi.de_destroy(h)
+        assert plan["kernel_path"] == 2 and plan["cluster_size"] == 8, plan
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_split_paths_agree_over_many_generations(prec, monkeypatch):
+    """Both split kernel paths take the FP64 oracle's decisions, so their
+    populations after 200 generations of the rotated Rastrigin workload at
+    NP=300, D=30 are identical."""
+    _need_gpu()
+    d = 30
+    o, M = problems.shift(d, seed=4), problems.rotation(d, seed=4)
+    pops = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("DE_GB300_PERSIST", flag)
+        h = capi.de_init(capi.make_config(300, d, objective=1, shift=o, rot=M, seed=3, precision=prec,
+                                          max_generations=200, target_error=0.0, fp64_band=capi.DE_BAND_ALL))
+        try:
+            capi.de_run(h)
+            pops.append(capi.de_get_population(h))
+        finally:
+            capi.de_destroy(h)
+    assert np.array_equal(pops[0][0], pops[1][0])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_near_policy_reaches_the_target_and_reports_fp64_best(prec):
+    """With the default near-optimum policy the small sphere run still meets
+    the 1e-8 target, and the reported best is the FP64 fitness of the best
+    individual."""
+    _need_gpu()
+    d = 10
+    o = problems.shift(d, seed=1)
+    h = capi.de_init(capi.make_config(64, d, objective=0, shift=o, seed=1, precision=prec, max_generations=1000,
+                                      target_error=1e-8))
+    try:
+        res = capi.de_run(h)[0]
+        b = capi.de_get_best(h)
+    finally:
+        capi.de_destroy(h)
+    assert res["stop_reason"] == capi.DE_STOP_TARGET and res["best_f"] < 1e-8
+    fo, _ = oracle.evaluate(0, b["best_x"][None, :], o, None)
+    assert abs(b["best_f"] - fo[0]) <= 1e-12 * max(abs(fo[0]), 1e-300) + 1e-30
