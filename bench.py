@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--generations", type=int, default=GENS)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     return p.parse_args()
 
 
@@ -175,6 +176,58 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- gb300 arm
+PREC_NAMES = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+DTYPE = {"fp64": "f64", "bf16x3": "bf16x3 products, f32 accumulate, f64 trials and selection band",
+         "tf32x3": "tf32x3 products, f32 accumulate, f64 trials and selection band"}
+
+
+def launches_per_step(plan, G):
+    """Kernels one timed step launches: re-initialisation (population,
+    evaluation, best record) plus the generations."""
+    path = plan["kernel_path"]
+    if path == 0:
+        return 3 + G          # one fused FP64 kernel per generation
+    if path == 1:
+        return 3 + 3 * G      # trial, tensor-core fitness, FP64 band per generation
+    return 3 + 2              # one persistent kernel for all generations, then its close-out kernel
+
+
+def measure(capi, torch, prec_name, G, steps, warmup, rank, flush, stream):
+    """Device-timed steps of one precision form: events around re-initialisation
+    + G generations; L2 flushed between steps outside the events."""
+    o, M = make_problem()
+    cfg = capi.make_config(NP, D, f=F, cr=CR, objective=OBJ_RASTRIGIN, shift=o, rot=M, seed=SEED, run_id=rank,
+                           precision=PREC_NAMES[prec_name], target_error=1e-8, max_generations=G)
+    h = capi.de_init(cfg, stream=stream.cuda_stream)
+    plan = capi.de_get_plan(h)
+
+    def one_step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        capi.de_reset(h)
+        if evs is not None:
+            evs[1].record(stream)
+        capi.de_step(h, G)
+        if evs is not None:
+            evs[2].record(stream)
+
+    for _ in range(warmup):
+        one_step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for k in range(steps):
+        one_step(events[k])
+        flush.zero_()
+    torch.cuda.synchronize()
+    step_ms = [e[0].elapsed_time(e[2]) for e in events]
+    gen_ms = [e[1].elapsed_time(e[2]) for e in events]
+    best = capi.de_get_best(h)
+    stats = capi.de_get_stats(h)
+    capi.de_destroy(h)
+    return dict(dev_ms=sum(step_ms), gen_ms=sum(gen_ms), plan=plan, best_f=best["best_f"], stats=stats)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -195,67 +248,58 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    prec_name = args.precision
-    if prec_name == "auto":
-        prec_name = os.environ.get("DE_BENCH_PRECISION", "fp64")
-    prec = {"fp64": capi.DE_PREC_FP64, "bf16x3": capi.DE_PREC_BF16X3, "tf32x3": capi.DE_PREC_TF32X3}[prec_name]
+    prec_name = args.precision if args.precision != "auto" else os.environ.get("DE_BENCH_PRECISION", "bf16x3")
     G = args.generations
-    o, M = make_problem()
     stream = torch.cuda.current_stream()
-    cfg = capi.make_config(NP, D, f=F, cr=CR, objective=OBJ_RASTRIGIN, shift=o, rot=M, seed=SEED, run_id=rank,
-                           precision=prec, target_error=1e-8, max_generations=G)
-    h = capi.de_init(cfg, stream=stream.cuda_stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def one_step(evs=None):
-        if evs is not None:
-            evs[0].record(stream)
-        capi.de_reset(h)
-        if evs is not None:
-            evs[1].record(stream)
-        capi.de_step(h, G)
-        if evs is not None:
-            evs[2].record(stream)
-
-    for _ in range(args.warmup):
-        one_step()
-        flush.zero_()
-    torch.cuda.synchronize()
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        one_step(events[k])
-        flush.zero_()  # evict the population from L2 between runs (outside the events)
+    head = measure(capi, torch, prec_name, G, args.steps, args.warmup, rank, flush, stream)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    step_ms = [e[0].elapsed_time(e[2]) for e in events]
-    gen_ms = [e[1].elapsed_time(e[2]) for e in events]
-    dev_ms = sum(step_ms)
-    gen_total_ms = sum(gen_ms)
+    dev_ms, gen_ms = head["dev_ms"], head["gen_ms"]
     if dist is not None:
-        t = torch.tensor([dev_ms, gen_total_ms], dtype=torch.float64, device="cuda")
+        t = torch.tensor([dev_ms, gen_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms, gen_total_ms = t.tolist()
-    best = capi.de_get_best(h)
-    capi.de_destroy(h)
+        dev_ms, gen_ms = t.tolist()
     trials_per_step = NP * G
     value = world * trials_per_step * args.steps / (dev_ms / 1e3)
+
+    # the other precision forms on the same device, for the comparison with
+    # the plain FP64 GPU DE (two steps each)
+    forms = {}
+    if not args.no_forms:
+        for name in ("fp64", "bf16x3", "tf32x3"):
+            if name == prec_name:
+                r = head
+                k = args.steps
+            else:
+                r = measure(capi, torch, name, G, 2, 1, rank, flush, stream)
+                k = 2
+            forms[name] = {"trial_evals_per_s": trials_per_step * k / (r["dev_ms"] / 1e3),
+                           "us_per_generation": 1e3 * r["gen_ms"] / (k * G), "kernel_path": r["plan"]["kernel_path"],
+                           "best_f": r["best_f"], "fp64_reevaluations": r["stats"]["fp64_reevals"]}
+        base = forms["fp64"]["trial_evals_per_s"]
+        for name in forms:
+            forms[name]["speedup_vs_fp64_gpu"] = forms[name]["trial_evals_per_s"] / base
 
     # e2e through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
+        o, M = make_problem()
         o_pin = torch.from_numpy(o).pin_memory()
         m_pin = torch.from_numpy(np.ascontiguousarray(M)).pin_memory()
         cfg_e = capi.make_config(NP, D, f=F, cr=CR, objective=OBJ_RASTRIGIN, shift=o_pin.numpy(), rot=m_pin.numpy(),
-                                 seed=SEED, run_id=rank, precision=prec, target_error=1e-8, max_generations=G)
+                                 seed=SEED, run_id=rank, precision=PREC_NAMES[prec_name], target_error=1e-8,
+                                 max_generations=G)
         times = []
         for k in range(args.warmup + args.steps):
             torch.cuda.synchronize()
@@ -276,44 +320,59 @@ def main():
         e2e = {"value": world * trials_per_step * args.steps / tot, "unit": "trial evals/s",
                "h2d_bytes_per_step": 8 * (D + D * D), "d2h_bytes_per_step": 8 * (D + 1) + 48}
 
-    # roofline of the dominant kernel (the generation kernel(s))
-    avg_gen_us = 1e3 * gen_total_ms / (args.steps * G)
+    # roofline of the dominant kernel
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    if prec == capi.DE_PREC_FP64:
+    path = head["plan"]["kernel_path"]
+    avg_gen_us = 1e3 * gen_ms / (args.steps * G)
+    if path == 0:
         flops = NP * (2.0 * D * D + 9.0 * D)
         achieved = flops / (avg_gen_us * 1e-6) / 1e12
         roof = {"bound": "alu", "kernel": "k_gen_fp64", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25, "traffic": None,
                 "peak_source": "nominal GB300 FP64 rate 1.25 TFLOP/s (a DFMA loop measured 1.20 on this part)"}
     else:
+        # algorithmic bytes per trial: read the target row, write the next
+        # generation's row, fitness in and out
         byts = NP * (2 * 8 * D + 16)
-        achieved = byts / (avg_gen_us * 1e-6) / 1e9
+        per_launch = byts * G if path == 2 else byts
+        launch_us = avg_gen_us * G if path == 2 else avg_gen_us
+        achieved = per_launch / (launch_us * 1e-6) / 1e9
         pk = float(peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": "hbm", "kernel": "generation (trial + fitness kernels)", "achieved": achieved, "peak": pk,
-                "unit": "GB/s", "frac": achieved / pk, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
-    roof["avg_launch_us"] = avg_gen_us
+        roof = {"bound": "hbm", "kernel": "k_persist" if path == 2 else "k_trial_split + k_fit_tc + k_band_fp64",
+                "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
+                "traffic": TRAFFIC_PER_LAUNCH.get(("k_persist", G)) if path == 2 else None,
+                "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": launch_us,
+                "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                                else "fallback 6.8 TB/s (of fallback)"),
+                "note": "population of 0.8 MB stays in L2; the generation loop is latency-bound"}
+    roof["avg_generation_us"] = avg_gen_us
 
     line = {"metric": METRIC, "value": value, "unit": "trial evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16x3->f32 (+f64 selection band)",
-                                           "tf32x3": "tf32x3->f32 (+f64 selection band)"}[prec_name],
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": prec_name, "generations": G,
+            "vs_baseline": None, "dtype": DTYPE[prec_name], "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": prec_name, "generations": G, "fp64_band": "near-optimum",
+                       "kernel_path": {0: "fp64 fused", 1: "split three-kernel", 2: "split persistent cluster"}[path],
                        "l2": "flushed between runs (512 MiB write)", "parallelism": f"replicas x{world}"},
-            "generations_per_s": world * G * args.steps / (dev_ms / 1e3), "best_f_last_run": best["best_f"],
-            "wall_s": t_wall, "e2e": e2e, "roofline": roof, "clocks": clk,
-            "gpu_launches": args.steps * (3 + G * (1 if prec == capi.DE_PREC_FP64 else 2))}
+            "generations_per_s": world * G * args.steps / (dev_ms / 1e3), "best_f_last_run": head["best_f"],
+            "forms": forms, "wall_s": t_wall, "e2e": e2e, "roofline": roof, "clocks": clk,
+            "gpu_launches": args.steps * launches_per_step(head["plan"], G)}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(o, M)
+        line["cpu_baseline"] = cpu_baseline(*make_problem())
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# DRAM traffic of one launch of the dominant kernel, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of a 200-generation launch of
+# the BF16x3 persistent kernel on this workload (313,600 + 2,182,144 bytes),
+# scaled to a launch of 3000 generations (traffic grows with generations)
+TRAFFIC_PER_LAUNCH = {("k_persist", 3000): (313600 + 2182144) * 3000 // 200}
 
 
 if __name__ == "__main__":
