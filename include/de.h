@@ -200,6 +200,66 @@ DE_API de_status de_run(de_handle* h, de_result* out);
  * f_dev: device, n doubles.  Both caller-owned; enqueued on the stream. */
 DE_API de_status de_eval(de_handle* h, int32_t run, const double* x_dev, int64_t ld, int32_t n, double* f_dev);
 
+/* ---- evaluation without a handle and without allocation ----------------
+ * The paper has no counterpart to this call; it serves deployment only.
+ *
+ * Evaluates n rows of the shifted, rotated objective in a split precision
+ * (BF16X3 or TF32X3).  The same kernels run as in de_eval on a handle with
+ * the same objective, d, scale, shift, rotation and precision, so the results
+ * are bit-identical.  This call needs no handle and allocates nothing on any
+ * call: no cudaMalloc, cudaFree, pinned host memory or library allocator.
+ * It is for callers that cannot allocate device memory at the point where
+ * they evaluate.  One case is a process whose device memory is already held
+ * by its own caching allocator or fixed arena, where another allocation could
+ * fail or fragment it.  Another is a loop running beside other streams'
+ * work, where cudaFree synchronises the whole device and cudaMalloc may.
+ * (de_init allocates a population arena, operand copies and band lists.)
+ *
+ * Scratch: one 16 MiB array in the library's device memory on each device.
+ * It holds the descriptor, the split copy of M, |y| per row and the
+ * tensor-core operand tiles.  Nothing in it needs to start at zero, because
+ * each call writes every part it uses before reading it.  Rows past n in the
+ * last 128-row tile are computed on but never reach f_dev.
+ *
+ * Limit: the scratch bounds n per call.  A call needs about 1 KiB, plus
+ * 2 e npad kpad bytes for M, plus 256 e kpad + 520 bytes per 128 rows, where:
+ *   e = 2 for BF16X3, 4 for TF32X3;
+ *   kpad = d rounded up to 16;
+ *   npad = kpad for d <= 256, else d rounded up to 256.
+ * The largest n per call (BF16X3 / TF32X3):
+ *   d = 10: 246,400 / 126,976     d = 30: 126,976 / 64,384
+ *   d = 100: 36,992 / 18,432      d = 1000: 3,072 / 1,024
+ * A larger n returns DE_ERR_INVALID_ARG, naming the largest n for that d and
+ * precision, and launches nothing.
+ *
+ * First call: the first call on each device looks up the scratch's address
+ * (cudaGetSymbolAddress), with that device current.  This may also load the
+ * library's device code on that device.  Make that first call before any
+ * stream capture begins.
+ * Concurrency: all calls on one device share the one scratch, so calls must
+ * not overlap.  Issue them on one stream, or order them with events or
+ * synchronisation.  Calls in flight at the same time race on the scratch and
+ * give wrong results, whether they come from two streams, two threads or two
+ * independent users of the library in one process.  Calls are asynchronous
+ * on cuda_stream.
+ *
+ * precision: DE_PREC_BF16X3 or DE_PREC_TF32X3.  DE_PREC_FP64 returns
+ *   DE_ERR_UNSUPPORTED (use de_eval, which needs no scratch for FP64).
+ * objective: DE_OBJ_SPHERE .. DE_OBJ_ACKLEY.  Rosenbrock needs d <= 256.
+ * d: 1..4096.  scale: finite and nonzero (y = (x - o) scale).
+ * shift_dev: device, d doubles, or NULL for o = 0.
+ * rot_dev: device, d*d doubles row-major (z_j = sum_k M[j][k] y_k), or NULL
+ *   for M = I.
+ * x_dev: device, n rows of d doubles with row stride ld (>= d) doubles.
+ * f_dev: device, n doubles.
+ * All device buffers are caller-owned and must be on the current device.
+ * cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
+ * Errors: DE_ERR_INVALID_ARG (arguments, or n beyond the scratch),
+ * DE_ERR_UNSUPPORTED, DE_ERR_CUDA.  The message is in de_last_error(NULL). */
+DE_API de_status de_eval_noalloc(int32_t precision, int32_t objective, int32_t d, double scale,
+                                 const double* shift_dev, const double* rot_dev, const double* x_dev, int64_t ld,
+                                 int32_t n, double* f_dev, void* cuda_stream);
+
 /* Copy run `run`'s current population (np*d, host) and fitness (np, host)
  * out; either pointer may be NULL.  Synchronises. */
 DE_API de_status de_get_population(de_handle* h, int32_t run, double* x_host, double* f_host);

@@ -104,6 +104,9 @@ def load(build_if_missing: bool = True):
             "de_save": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_load": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_destroy": ([H], ctypes.c_int),
+            "de_eval_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                 ctypes.c_void_p], ctypes.c_int),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -116,7 +119,8 @@ def load(build_if_missing: bool = True):
 def exported_symbols():
     return ["de_version", "de_status_string", "de_last_error", "de_init", "de_init_batch", "de_reset", "de_step", "de_run",
             "de_eval", "de_get_population", "de_set_population", "de_set_generation", "de_get_best",
-            "de_get_debug", "de_get_shape", "de_get_stats", "de_get_plan", "de_save", "de_load", "de_destroy"]
+            "de_get_debug", "de_get_shape", "de_get_stats", "de_get_plan", "de_save", "de_load", "de_destroy",
+            "de_eval_noalloc"]
 
 
 def _status_name(s):
@@ -194,6 +198,17 @@ def de_run(h, nruns: int = 1):
 
 def de_eval(h, run: int, x_dev_ptr: int, ld: int, n: int, f_dev_ptr: int):
     _check(load().de_eval(h, run, ctypes.c_void_p(x_dev_ptr), ld, n, ctypes.c_void_p(f_dev_ptr)), h)
+
+
+def de_eval_noalloc(precision: int, objective: int, d: int, scale: float, shift_dev_ptr, rot_dev_ptr, x_dev_ptr: int,
+                    ld: int, n: int, f_dev_ptr: int, stream=None):
+    """Handle-free split-precision evaluation through the library's static
+    scratch (no allocation); pointers are device addresses (ints), shift and
+    rotation may be None."""
+    st = load().de_eval_noalloc(precision, objective, d, scale, ctypes.c_void_p(shift_dev_ptr),
+                                ctypes.c_void_p(rot_dev_ptr), ctypes.c_void_p(x_dev_ptr), ld, n,
+                                ctypes.c_void_p(f_dev_ptr), ctypes.c_void_p(stream))
+    _check(st, None)
 
 
 def de_get_shape(h, run: int = 0):

@@ -964,4 +964,47 @@ de_status de_load(de_handle* h, const char* path) {
   return DE_OK;
 }
 
+de_status de_eval_noalloc(int32_t precision, int32_t objective, int32_t d, double scale, const double* shift_dev,
+                          const double* rot_dev, const double* x_dev, int64_t ld, int32_t n, double* f_dev,
+                          void* cuda_stream) {
+  if (precision == DE_PREC_FP64)
+    return fail(nullptr, DE_ERR_UNSUPPORTED, "de_eval_noalloc: FP64 evaluation uses no scratch; call de_eval");
+  if (precision != DE_PREC_BF16X3 && precision != DE_PREC_TF32X3)
+    return fail(nullptr, DE_ERR_INVALID_ARG, "de_eval_noalloc: precision out of range");
+  if (objective < DE_OBJ_SPHERE || objective > DE_OBJ_ACKLEY)
+    return fail(nullptr, DE_ERR_INVALID_ARG, "de_eval_noalloc: objective out of range");
+  if (d < 1 || d > 4096) return fail(nullptr, DE_ERR_INVALID_ARG, "de_eval_noalloc: d must be in [1, 4096]");
+  if (objective == DE_OBJ_ROSENBROCK && d > 256)
+    return fail(nullptr, DE_ERR_UNSUPPORTED, "de_eval_noalloc: split precision supports Rosenbrock only for d <= 256");
+  if (!std::isfinite(scale) || scale == 0.0)
+    return fail(nullptr, DE_ERR_INVALID_ARG, "de_eval_noalloc: scale must be finite and nonzero");
+  if (n < 0) return fail(nullptr, DE_ERR_INVALID_ARG, "de_eval_noalloc: n must be >= 0");
+  if (n == 0) return DE_OK;
+  if (ld < d) return fail(nullptr, DE_ERR_INVALID_ARG, "de_eval_noalloc: ld must be >= d");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, DE_ERR_CUDA, "de_eval_noalloc: no current CUDA device");
+  }
+  const void* ptrs[4] = {x_dev, f_dev, shift_dev, rot_dev};
+  const char* names[4] = {"x_dev", "f_dev", "shift_dev", "rot_dev"};
+  for (int q = 0; q < 4; ++q) {
+    if (!ptrs[q]) {
+      if (q < 2) return fail(nullptr, DE_ERR_INVALID_ARG, std::string("de_eval_noalloc: ") + names[q] + " is NULL");
+      continue;
+    }
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, ptrs[q]) != cudaSuccess || a.type != cudaMemoryTypeDevice || a.device != dev) {
+      cudaGetLastError();
+      return fail(nullptr, DE_ERR_INVALID_ARG,
+                  std::string("de_eval_noalloc: ") + names[q] + " is not device memory of the current device");
+    }
+  }
+  std::string err;
+  const de_status s = noalloc_eval(precision, objective, d, scale, shift_dev, rot_dev, x_dev, ld, n, f_dev,
+                                   (cudaStream_t)cuda_stream, err);
+  if (s != DE_OK) return fail(nullptr, s, err);
+  return DE_OK;
+}
+
 }  // extern "C"

@@ -61,5 +61,14 @@ void tc_plan_free(TcPlan& p);
 void tc_generation_launch(const TcPlan& p, const RunDesc* runs, cudaStream_t s);
 de_status tc_eval_launch(const TcPlan& p, const RunDesc* runs, int run, const RunDesc& R, const double* x, int64_t ld,
                          int n, double* f, cudaStream_t s, std::string& err);
+// Evaluation of n caller rows with a device descriptor and work list that
+// the caller placed (all tiles of one launch); raises k_fit_tc's dynamic
+// shared-memory limit to `smem` when it is lower, never lowers it.
+de_status tc_eval_rows(const RunDesc* desc, const int2* items, int tiles, int esz, size_t smem, const double* x,
+                       int64_t ld, int n, double* f, cudaStream_t s, std::string& err);
+
+// no-allocation evaluation (de_noalloc.cu)
+de_status noalloc_eval(int prec, int obj, int d, double scale, const double* o, const double* M, const double* x,
+                       int64_t ld, int n, double* f, cudaStream_t s, std::string& err);
 
 }  // namespace de

@@ -935,4 +935,29 @@ de_status tc_eval_launch(const TcPlan& p, const RunDesc* runs, int run, const Ru
   return DE_OK;
 }
 
+de_status tc_eval_rows(const RunDesc* desc, const int2* items, int tiles, int esz, size_t smem, const double* x,
+                       int64_t ld, int n, double* f, cudaStream_t s, std::string& err) {
+  cudaFuncAttributes fa{};
+  cudaError_t e = esz == 2 ? cudaFuncGetAttributes(&fa, k_fit_tc<2>) : cudaFuncGetAttributes(&fa, k_fit_tc<4>);
+  if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < smem) {
+    e = esz == 2 ? cudaFuncSetAttribute(k_fit_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                 : cudaFuncSetAttribute(k_fit_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  if (e == cudaSuccess) {
+    if (esz == 2) {
+      k_prep_rows<2><<<(n + 7) / 8, 256, 0, s>>>(desc, 0, x, ld, n);
+      k_fit_tc<2><<<tiles, kFitThreads, smem, s>>>(desc, items, 1, f, n);
+    } else {
+      k_prep_rows<4><<<(n + 7) / 8, 256, 0, s>>>(desc, 0, x, ld, n);
+      k_fit_tc<4><<<tiles, kFitThreads, smem, s>>>(desc, items, 1, f, n);
+    }
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    err = std::string("split-precision eval: ") + cudaGetErrorString(e);
+    return DE_ERR_CUDA;
+  }
+  return DE_OK;
+}
+
 }  // namespace de

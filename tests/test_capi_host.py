@@ -71,3 +71,31 @@ def test_null_arguments_rejected():
     assert lib.de_step(None, 1) == capi.DE_ERR_INVALID_ARG
     assert lib.de_destroy(None) == capi.DE_OK
     assert b"NULL" in lib.de_last_error(None)
+
+
+@pytest.mark.parametrize(
+    "args,status,msg",
+    [
+        ((7, 1, 10, 1.0), "DE_ERR_INVALID_ARG", "precision"),
+        ((0, 1, 10, 1.0), "DE_ERR_UNSUPPORTED", "FP64"),
+        ((1, 4, 10, 1.0), "DE_ERR_INVALID_ARG", "objective"),
+        ((1, 1, 0, 1.0), "DE_ERR_INVALID_ARG", "d must"),
+        ((2, 1, 4097, 1.0), "DE_ERR_INVALID_ARG", "d must"),
+        ((1, 2, 300, 1.0), "DE_ERR_UNSUPPORTED", "Rosenbrock"),
+        ((1, 1, 10, 0.0), "DE_ERR_INVALID_ARG", "scale"),
+        ((1, 1, 10, float("inf")), "DE_ERR_INVALID_ARG", "scale"),
+    ],
+)
+def test_eval_noalloc_rejects_arguments_on_host(args, status, msg):
+    """de_eval_noalloc checks its scalar arguments before any CUDA call."""
+    lib = capi.load()
+    prec, obj, d, scale = args
+    st = lib.de_eval_noalloc(prec, obj, d, scale, None, None, None, d, 4, None, None)
+    assert lib.de_status_string(st).decode() == status
+    assert msg in lib.de_last_error(None).decode()
+
+
+def test_eval_noalloc_empty_and_negative_n_on_host():
+    lib = capi.load()
+    assert lib.de_eval_noalloc(1, 1, 10, 1.0, None, None, None, 10, 0, None, None) == capi.DE_OK
+    assert lib.de_eval_noalloc(1, 1, 10, 1.0, None, None, None, 10, -1, None, None) == capi.DE_ERR_INVALID_ARG
