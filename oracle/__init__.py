@@ -95,7 +95,11 @@ def _bind_extra(lib):
     if hasattr(lib, "or_ode_objective"):
         lib.or_ode_objective.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double]
         lib.or_ode_objective.restype = ctypes.c_double
+        lib.or_ode_objective_s.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
+        lib.or_ode_objective_s.restype = ctypes.c_double
         lib.or_ode_trajectory.argtypes = [_dp, ctypes.c_int, ctypes.c_double, _dp]
+        lib.or_ode_integrate.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
+        lib.or_ode_params.argtypes = [_dp, _dp, _dp]
     if hasattr(lib, "or_mlp_forward"):
         lib.or_mlp_forward.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp,
                                        _dp, _dp, _dp]
@@ -154,6 +158,40 @@ def objective(obj, x, o=None, M=None, scale=1.0):
     sabs = ctypes.c_double(0.0)
     f = _load().or_objective(obj, d, _p(o), _p(M), scale, _p(x), ctypes.byref(sabs))
     return f, sabs.value
+
+
+# ----------------------------------------------------------------------------- ODE objective
+ODE = 4
+ODE_STEPS, ODE_DT, ODE_N = 2000, 1e-3, 10
+
+
+def ode_params(x):
+    """(k, c) of the oscillator chain from a parameter vector of length 20."""
+    x = _f64(x)
+    k = np.zeros(ODE_N)
+    c = np.zeros(ODE_N)
+    _load().or_ode_params(_p(x), _p(k), _p(c))
+    return k, c
+
+
+def ode_integrate(k, c, steps=ODE_STEPS, dt=ODE_DT):
+    """Positions after every RK4 step (steps x 10) for raw parameters k, c."""
+    out = np.zeros((steps, ODE_N))
+    _load().or_ode_integrate(_p(_f64(k)), _p(_f64(c)), steps, dt, _p(out))
+    return out
+
+
+def ode_trajectory(x, steps=ODE_STEPS, dt=ODE_DT):
+    out = np.zeros((steps, ODE_N))
+    _load().or_ode_trajectory(_p(_f64(x)), steps, dt, _p(out))
+    return out
+
+
+def ode_objective(x, x_hat, steps=ODE_STEPS, dt=ODE_DT):
+    """(f, tolerance scale S) of the ODE fitting objective."""
+    s = ctypes.c_double()
+    f = _load().or_ode_objective_s(_p(_f64(x)), _p(_f64(x_hat)), steps, dt, ctypes.byref(s))
+    return f, s.value
 
 
 def evaluate(obj, X, o=None, M=None, scale=1.0, threads=1):
