@@ -25,11 +25,12 @@
  *     q_hat is the trajectory of the hidden parameter vector x_hat, so that
  *     f(x_hat) = 0.
  *
- * Order of operations (IEEE binary64, round to nearest, no contraction: build
- * with -ffp-contract=off):
- *   a(q, p) = -((k q + c p) + (((q + q) - q_left) - q_right));
- *   stage points q + (dt/2) kq and p + (dt/2) kp, then q + dt kq and p + dt kp;
- *   update q + (dt/6) (((k1 + (k2 + k2)) + (k3 + k3)) + k4), the same for p.
+ * Order of operations (IEEE binary64, round to nearest; the only fused
+ * multiply-adds are the explicit fma() calls: build with -ffp-contract=off):
+ *   a(q, p) = fma(-c, p, fma(-(k + 2), q, q_left + q_right)),
+ *     the same force as above with the two neighbour springs gathered;
+ *   stage points fma(dt/2, kq, q) and fma(dt/2, kp, p), then with dt;
+ *   update fma(dt/6, (k1 + k4) + ((k2 + k3) + (k2 + k3)), q), the same for p.
  * Any correct RK4 in another order differs from this one by rounding only.
  */
 #include <math.h>
@@ -50,14 +51,15 @@ void or_ode_params(const double* x, double* k, double* c)
     }
 }
 
-/* Accelerations of the chain at (q, p). */
+/* Accelerations of the chain at (q, p): -k_i q_i - c_i p_i - (2 q_i - q_{i-1}
+ * - q_{i+1}), gathered as (q_{i-1} + q_{i+1}) - (k_i + 2) q_i - c_i p_i. */
 static void or_ode_accel(const double* k, const double* c, const double* q, const double* p, double* a)
 {
     for (int i = 0; i < OR_ODE_N; ++i) {
         double ql = i > 0 ? q[i - 1] : 0.0;
         double qr = i + 1 < OR_ODE_N ? q[i + 1] : 0.0;
-        double coupling = ((q[i] + q[i]) - ql) - qr;
-        a[i] = -((k[i] * q[i] + c[i] * p[i]) + coupling);
+        double w = fma(-(k[i] + 2.0), q[i], ql + qr);
+        a[i] = fma(-c[i], p[i], w);
     }
 }
 
@@ -80,29 +82,30 @@ void or_ode_integrate(const double* k, const double* c, int steps, double dt, do
         or_ode_accel(k, c, q, p, k1p);
         /* stage 2 at the half step along stage 1 */
         for (int i = 0; i < OR_ODE_N; ++i) {
-            qs[i] = q[i] + hh * k1q[i];
-            ps[i] = p[i] + hh * k1p[i];
+            qs[i] = fma(hh, k1q[i], q[i]);
+            ps[i] = fma(hh, k1p[i], p[i]);
             k2q[i] = ps[i];
         }
         or_ode_accel(k, c, qs, ps, k2p);
         /* stage 3 at the half step along stage 2 */
         for (int i = 0; i < OR_ODE_N; ++i) {
-            qs[i] = q[i] + hh * k2q[i];
-            ps[i] = p[i] + hh * k2p[i];
+            qs[i] = fma(hh, k2q[i], q[i]);
+            ps[i] = fma(hh, k2p[i], p[i]);
             k3q[i] = ps[i];
         }
         or_ode_accel(k, c, qs, ps, k3p);
         /* stage 4 at the full step along stage 3 */
         for (int i = 0; i < OR_ODE_N; ++i) {
-            qs[i] = q[i] + h * k3q[i];
-            ps[i] = p[i] + h * k3p[i];
+            qs[i] = fma(h, k3q[i], q[i]);
+            ps[i] = fma(h, k3p[i], p[i]);
             k4q[i] = ps[i];
         }
         or_ode_accel(k, c, qs, ps, k4p);
         /* weighted update (1, 2, 2, 1) / 6 */
         for (int i = 0; i < OR_ODE_N; ++i) {
-            q[i] = q[i] + h6 * (((k1q[i] + (k2q[i] + k2q[i])) + (k3q[i] + k3q[i])) + k4q[i]);
-            p[i] = p[i] + h6 * (((k1p[i] + (k2p[i] + k2p[i])) + (k3p[i] + k3p[i])) + k4p[i]);
+            double mq = k2q[i] + k3q[i], mp = k2p[i] + k3p[i];
+            q[i] = fma(h6, (k1q[i] + k4q[i]) + (mq + mq), q[i]);
+            p[i] = fma(h6, (k1p[i] + k4p[i]) + (mp + mp), p[i]);
             out[(size_t)s * OR_ODE_N + i] = q[i];
         }
     }
