@@ -69,7 +69,18 @@ typedef enum {
  *   RASTRIGIN   sum (z_j^2 - 10 cos(2 pi z_j) + 10)
  *   ROSENBROCK  sum_{j<D-1} 100 (t_{j+1} - t_j^2)^2 + (t_j - 1)^2,  t = z + 1
  *   ACKLEY      20 + e - 20 exp(-0.2 sqrt(sum z_j^2 / D)) - exp(sum cos(2 pi z_j) / D)
- *   ODE         fit of a 10-oscillator damped chain (D = 20) */
+ *   ODE         fit of a 10-oscillator damped chain (D = 20, FP64, no rotation).
+ *               The paper defines no such problem (it motivates costly
+ *               objectives in its Abstract); the workload is a reading.  Ten
+ *               unit masses in a chain: springs k_i to ground, dampers c_i,
+ *               unit springs between neighbours, walls at both ends, with
+ *               k_i = 0.5 + 4.5 (x_i + 100)/200 and
+ *               c_i = 0.01 + 0.49 (x_{10+i} + 100)/200.
+ *               Integrated by RK4 with dt = 1e-3 for 2000 steps from
+ *               q(0) = e_1, p(0) = 0.
+ *               f = mean over steps and masses of (q - q_o)^2, where q_o is
+ *               the trajectory of the hidden parameter vector, passed as
+ *               the shift o; f(o) = 0 exactly. */
 typedef enum {
     DE_OBJ_SPHERE = 0,
     DE_OBJ_RASTRIGIN = 1,

@@ -84,7 +84,12 @@ static de_status validate(const de_config& c, int idx, std::string& why) {
   if (!(c.f >= 0.0 && c.f <= 2.0)) return bad("F must be in [0, 2]");
   if (!(c.cr >= 0.0 && c.cr <= 1.0)) return bad("CR must be in [0, 1]");
   if (!std::isfinite(c.lo) || !std::isfinite(c.hi) || !(c.lo < c.hi)) return bad("bounds must be finite with lo < hi");
-  if (c.objective < DE_OBJ_SPHERE || c.objective > DE_OBJ_ACKLEY) return bad("objective out of range");
+  if (c.objective < DE_OBJ_SPHERE || c.objective > DE_OBJ_ODE) return bad("objective out of range");
+  if (c.objective == DE_OBJ_ODE) {
+    if (c.d != 20) return bad("the ODE objective has d = 20 (stiffness and damping of 10 oscillators)");
+    if (c.precision != DE_PREC_FP64) return bad("the ODE objective runs in FP64 only");
+    if (c.rot) return bad("the ODE objective takes no rotation");
+  }
   if (!std::isfinite(c.scale) || c.scale == 0.0) return bad("scale must be finite and nonzero");
   if (c.run_id >= (1u << 20)) return bad("run_id must be < 2^20");
   if (c.precision < DE_PREC_FP64 || c.precision > DE_PREC_TF32X3) return bad("precision out of range");
@@ -221,6 +226,7 @@ static de_status init_run(de_handle* h, int r) {
   st.evals = R.np;  // the initial population counts as NP evaluations
   DE_CUDA(h, cudaMemcpyAsync(R.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
   DE_CUDA(h, cudaMemsetAsync(R.X[0], 0, (size_t)R.np * R.dp * sizeof(double), h->stream));
+  if (R.obj == DE_OBJ_ODE) k_ode_reference_launch(h->d_run, r, const_cast<double*>(R.ode_ref), h->stream);
   k_init_population_launch(h->d_run, r, R.np, R.dp, h->stream);
   k_eval_rows_launch(h->d_run, r, R.X[0], R.dp, R.np, R.dp, R.rotate, R.f[0], R.fx[0], h->stream);
   k_best_init_launch(h->d_run, r, h->stream);
@@ -449,7 +455,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     return o;
   };
   struct Offs {
-    size_t X0, X1, f0, f1, fx0, fx1, o, MT, Mr, st, part, T;
+    size_t X0, X1, f0, f1, fx0, fx1, o, MT, Mr, st, part, T, ref;
     size_t dbg_idx, dbg_jrand, dbg_mask, dbg_trial, dbg_ftrial, dbg_accept, dbg_fp64;
   };
   std::vector<Offs> offs(nruns);
@@ -472,6 +478,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     O.part = take((size_t)c.np * sizeof(BestPartial));
     const bool split = c.precision != DE_PREC_FP64;
     O.T = split ? take(pop) : 0;
+    O.ref = c.objective == DE_OBJ_ODE ? take((size_t)kOdeSteps * kOdeN * sizeof(double)) : 0;
     if (c.debug_capture) {
       const int nw = (c.d + 31) / 32;
       O.dbg_idx = take((size_t)c.np * 3 * sizeof(int32_t));
@@ -555,6 +562,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     if (c.precision != DE_PREC_FP64) {
       R.T = (double*)(A + O.T);
     }
+    if (c.objective == DE_OBJ_ODE) R.ode_ref = (const double*)(A + O.ref);
     if (c.debug_capture) {
       R.dbg_idx = (int32_t*)(A + O.dbg_idx);
       R.dbg_jrand = (int32_t*)(A + O.dbg_jrand);

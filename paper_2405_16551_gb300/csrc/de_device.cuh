@@ -101,6 +101,69 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// ------------------------------------------------------------------ ODE objective
+// The expensive objective of the surrogate-assisted workload.  The paper
+// motivates costly objectives (Abstract) but defines none; this one is a
+// reading.  Ten unit masses in a chain: springs k_i to ground, dampers c_i,
+// unit springs between neighbours, walls at both ends.
+//   dq_i/dt = p_i,  dp_i/dt = (q_{i-1} + q_{i+1}) - (k_i + 2) q_i - c_i p_i
+// Parameters from x in [-100, 100]^20:
+//   k_i = 0.5 + 4.5 (x_i + 100) / 200,  c_i = 0.01 + 0.49 (x_{10+i} + 100) / 200.
+// Classical RK4 with dt = 1e-3 for 2000 steps from q(0) = e_1, p(0) = 0.
+// f = mean over steps and masses of (q - q_ref)^2, where q_ref is the
+// trajectory of the hidden parameter vector (the run's shift o).
+// One warp per parameter vector; lane i < 10 carries mass i and its
+// neighbours come by shuffles.  Rounding: one IEEE operation per step of the
+// stated order (explicit __fma_rn / __dadd_rn), so a trajectory is a pure
+// function of x and f(o) = 0 exactly.
+constexpr int kOdeN = 10;
+constexpr int kOdeSteps = 2000;
+constexpr double kOdeDt = 1e-3;
+
+__device__ __forceinline__ double ode_neighbours(double q, int lane) {
+  const double l = __shfl_up_sync(0xffffffffu, q, 1);
+  const double r = __shfl_down_sync(0xffffffffu, q, 1);
+  return __dadd_rn(lane == 0 ? 0.0 : l, lane >= kOdeN - 1 ? 0.0 : r);
+}
+
+// Integrates the chain of x (20 parameters).  Returns this lane's sum of
+// (q - ref)^2 over the steps when ref is not NULL (0 in lanes >= 10); writes
+// the positions to out[step * 10 + lane] when out is not NULL.  All 32 lanes
+// must call it.
+static __device__ __forceinline__ double ode_chain(const double* __restrict__ x, int lane, const double* __restrict__ ref,
+                                         double* __restrict__ out) {
+  const bool on = lane < kOdeN;
+  const int li = on ? lane : 0;
+  const double uk = __ddiv_rn(__dadd_rn(x[li], 100.0), 200.0);
+  const double uc = __ddiv_rn(__dadd_rn(x[kOdeN + li], 100.0), 200.0);
+  const double k = __dadd_rn(0.5, __dmul_rn(4.5, uk));
+  const double c = __dadd_rn(0.01, __dmul_rn(0.49, uc));
+  const double nk2 = -__dadd_rn(k, 2.0), nc = -c;
+  const double h = kOdeDt, hh = kOdeDt * 0.5, h6 = kOdeDt / 6.0;
+  double q = lane == 0 ? 1.0 : 0.0, p = 0.0, acc = 0.0;
+  for (int s = 0; s < kOdeSteps; ++s) {
+    const double rv = (ref && on) ? __ldg(ref + s * kOdeN + lane) : 0.0;
+    const double a1 = __fma_rn(nc, p, __fma_rn(nk2, q, ode_neighbours(q, lane)));
+    const double q2 = __fma_rn(hh, p, q), p2 = __fma_rn(hh, a1, p);
+    const double a2 = __fma_rn(nc, p2, __fma_rn(nk2, q2, ode_neighbours(q2, lane)));
+    const double q3 = __fma_rn(hh, p2, q), p3 = __fma_rn(hh, a2, p);
+    const double a3 = __fma_rn(nc, p3, __fma_rn(nk2, q3, ode_neighbours(q3, lane)));
+    const double q4 = __fma_rn(h, p3, q), p4 = __fma_rn(h, a3, p);
+    const double a4 = __fma_rn(nc, p4, __fma_rn(nk2, q4, ode_neighbours(q4, lane)));
+    const double mq = __dadd_rn(p2, p3), mp = __dadd_rn(a2, a3);
+    q = __fma_rn(h6, __dadd_rn(__dadd_rn(p, p4), __dadd_rn(mq, mq)), q);
+    p = __fma_rn(h6, __dadd_rn(__dadd_rn(a1, a4), __dadd_rn(mp, mp)), p);
+    if (on) {
+      if (ref) {
+        const double r = __dsub_rn(q, rv);
+        acc = __fma_rn(r, r, acc);
+      }
+      if (out) out[s * kOdeN + lane] = q;
+    }
+  }
+  return acc;
+}
+
 __device__ __forceinline__ double row_objective_fp64(int obj, const double* __restrict__ z, int d, int lane) {
   double s1 = 0.0, s2 = 0.0;
   if (obj == kObjSphere) {

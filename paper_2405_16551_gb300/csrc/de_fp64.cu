@@ -3,6 +3,7 @@
 //   k_init_population   Sec. 2 / Sec. 6.2.1: uniform initial population
 //   k_eval_rows         Sec. 7.3.1: z = M((x - o) s), objective of each row
 //   k_best_init         best record, stop flag and counters after (re)initialisation
+//   k_ode_reference     trajectory of the hidden parameters of the ODE objective
 //   k_gen_fp64          one whole generation, fused: mutant indices (Eq. 2),
 //                       mutation (Eq. 2), binomial crossover (Eq. 3), bound
 //                       repair, shift + rotation + objective (Sec. 7.3.1),
@@ -64,6 +65,18 @@ __global__ void k_eval_rows(const RunDesc* __restrict__ runs, int run, const dou
   const int row0 = blockIdx.x * rows;
   const int nrows = min(rows, n - row0);
   if (nrows <= 0) return;
+  if (R.obj == kObjOde) {
+    // a warp integrates one row's chain
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int r = warp; r < nrows; r += nwarps) {
+      const double s = warp_sum(ode_chain(x + (size_t)(row0 + r) * ld, lane, R.ode_ref, nullptr));
+      if (lane == 0) {
+        fout[row0 + r] = s / (double)(kOdeSteps * kOdeN);
+        if (fx_out) fx_out[row0 + r] = 1;
+      }
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < rows * dp; e += blockDim.x) {
     const int r = e / dp, j = e % dp;
     double y = 0.0;
@@ -85,6 +98,12 @@ __global__ void k_eval_rows(const RunDesc* __restrict__ runs, int run, const dou
       if (fx_out) fx_out[row0 + r] = 1;
     }
   }
+}
+
+// Trajectory of the hidden parameter vector o of an ODE run (one warp).
+__global__ void k_ode_reference(const RunDesc* __restrict__ runs, int run, double* __restrict__ ref) {
+  const RunDesc& R = runs[run];
+  ode_chain(R.o, threadIdx.x & 31, nullptr, ref);
 }
 
 // Reduce f[0..np) of the current generation into the run's best record and
@@ -200,10 +219,18 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
     build_trial_row(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp);
   __syncthreads();
 
+  const int nout = nrows * d;
+  if (R.obj == kObjOde) {
+    // ---- ODE objective: a warp integrates one trial's chain; f to W[row][0]
+    for (int rl = warp; rl < nrows; rl += nwarps) {
+      const double s = warp_sum(ode_chain(T + rl * dp, lane, R.ode_ref, nullptr));
+      if (lane == 0) W[rl * dp] = s / (double)(kOdeSteps * kOdeN);
+    }
+    __syncthreads();
+  } else {
   // ---- rotation, flattened over (row, output): output e = 32 w + lane of
   // warp-group w; a warp takes groups warp, warp + 8, ... and runs up to four
   // of them at once (independent accumulator chains)
-  const int nout = nrows * d;
   if (R.rotate) {
     const int ngroups = (nout + 31) / 32;
     for (int w0 = warp; w0 < ngroups; w0 += 4 * nwarps) {
@@ -246,22 +273,26 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
     W[r * dp + j] = t2;
   }
   __syncthreads();
+  }
 
   // ---- row sums, greedy selection, best partial (a warp per row)
   double bf = CUDART_INF;
   int bi = -1;
   for (int rl = warp; rl < nrows; rl += nwarps) {
     const int i = row0 + rl;
-    double s1 = 0.0, s2 = 0.0;
-    for (int j = lane; j < d; j += 32) {
-      s1 += Y[rl * dp + j];
-      s2 += W[rl * dp + j];
+    double ft;
+    if (R.obj == kObjOde) {
+      ft = W[rl * dp];
+    } else {
+      double s1 = 0.0, s2 = 0.0;
+      for (int j = lane; j < d; j += 32) {
+        s1 += Y[rl * dp + j];
+        s2 += W[rl * dp + j];
+      }
+      s1 = warp_sum(s1);
+      s2 = warp_sum(s2);
+      ft = R.obj == kObjAckley ? 20.0 + 2.718281828459045 - 20.0 * exp(-0.2 * sqrt(s1 / d)) - exp(s2 / d) : s1;
     }
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    const double ft = R.obj == kObjAckley
-                          ? 20.0 + 2.718281828459045 - 20.0 * exp(-0.2 * sqrt(s1 / d)) - exp(s2 / d)
-                          : s1;
     const double fi = fX[i];
     const bool acc = fit_key(ft) <= fit_key(fi) && fit_key(ft) != 0x7FFFFFFFFFFFFFFFLL;  // ft <= fi, NaN never
     const double* src = acc ? (T + rl * dp) : (X + (size_t)i * dp);
@@ -342,5 +373,9 @@ void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t l
 }
 
 void k_best_init_launch(const RunDesc* runs, int run, cudaStream_t s) { k_best_init<<<1, 256, 0, s>>>(runs, run); }
+
+void k_ode_reference_launch(const RunDesc* runs, int run, double* ref, cudaStream_t s) {
+  k_ode_reference<<<1, 32, 0, s>>>(runs, run, ref);
+}
 
 }  // namespace de

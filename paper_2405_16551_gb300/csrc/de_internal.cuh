@@ -72,6 +72,7 @@ struct RunDesc {
   const double* o;
   const double* MT;
   const double* Mrow;  // d x d, row-major M (z_j = sum_k M[j][k] y_k), split path FP64 band
+  const double* ode_ref;  // ODE objective: kOdeSteps x 10 positions of the hidden parameter vector o
   RunState* st;
   BestPartial* part;
   int32_t ntiles;     // tiles of the FP64 generation kernel

@@ -18,6 +18,7 @@ void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cuda
 void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int rotate,
                         double* f, uint8_t* fx, cudaStream_t s);
 void k_best_init_launch(const RunDesc* runs, int run, cudaStream_t s);
+void k_ode_reference_launch(const RunDesc* runs, int run, double* ref, cudaStream_t s);
 
 // persistent cluster path (de_persist.cu)
 struct PersistCtl {

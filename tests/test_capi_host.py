@@ -55,6 +55,9 @@ def test_version_and_status_strings():
         (dict(np_=64, d=10, max_generations=-1), "max_"),
         (dict(np_=64, d=2, shift=np.array([0.0, np.inf])), "shift"),
         (dict(np_=64, d=2, rot=np.array([[1.0, 0.0], [np.nan, 1.0]])), "rotation"),
+        (dict(np_=64, d=10, objective=4), "d = 20"),
+        (dict(np_=64, d=20, objective=4, precision=2), "FP64 only"),
+        (dict(np_=64, d=20, objective=4, rot=np.eye(20)), "no rotation"),
     ],
 )
 def test_invalid_config_rejected_on_host(kw, msg):
