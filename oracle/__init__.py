@@ -101,11 +101,11 @@ def _bind_extra(lib):
         lib.or_ode_integrate.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
         lib.or_ode_params.argtypes = [_dp, _dp, _dp]
     if hasattr(lib, "or_mlp_forward"):
-        lib.or_mlp_forward.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp,
-                                       _dp, _dp, _dp]
-        lib.or_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp,
-                                         _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.or_mlp_forward.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int] + [_dp] * 8
+        lib.or_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int] + [_dp] * 14
         lib.or_mlp_loss_grad.restype = ctypes.c_double
+        lib.or_adam.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double]
 
 
 def _p(a, t=_dp):
@@ -192,6 +192,40 @@ def ode_objective(x, x_hat, steps=ODE_STEPS, dt=ODE_DT):
     s = ctypes.c_double()
     f = _load().or_ode_objective_s(_p(_f64(x)), _p(_f64(x_hat)), steps, dt, ctypes.byref(s))
     return f, s.value
+
+
+# ----------------------------------------------------------------------------- surrogate MLP
+MLP_KEYS = ("W1", "b1", "W2", "b2", "w3", "b3")
+
+
+def mlp_forward(params, X):
+    """y for every row of X; params = dict of W1 (nh x nin), b1, W2 (nh x nh), b2, w3, b3."""
+    X = _f64(np.atleast_2d(X))
+    B, nin = X.shape
+    p = {k: _f64(np.atleast_1d(params[k])) for k in MLP_KEYS}
+    nh = p["b1"].shape[0]
+    y = np.zeros(B)
+    _load().or_mlp_forward(B, nin, nh, _p(X), _p(p["W1"]), _p(p["b1"]), _p(p["W2"]), _p(p["b2"]), _p(p["w3"]),
+                           _p(p["b3"]), _p(y))
+    return y
+
+
+def mlp_loss_grad(params, X, t):
+    """(loss, grads) with grads keyed like params."""
+    X = _f64(np.atleast_2d(X))
+    B, nin = X.shape
+    p = {k: _f64(np.atleast_1d(params[k])) for k in MLP_KEYS}
+    g = {k: np.zeros_like(p[k]) for k in MLP_KEYS}
+    loss = _load().or_mlp_loss_grad(B, nin, p["b1"].shape[0], _p(X), _p(_f64(t)), *[_p(p[k]) for k in MLP_KEYS],
+                                    *[_p(g[k]) for k in MLP_KEYS])
+    return loss, g
+
+
+def adam(w, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update in place on float64 arrays w, m, v with gradient g."""
+    for a in (w, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    _load().or_adam(w.size, _p(w), _p(_f64(g)), _p(m), _p(v), step, lr, beta1, beta2, eps)
 
 
 def evaluate(obj, X, o=None, M=None, scale=1.0, threads=1):
