@@ -271,6 +271,45 @@ DE_API de_status de_eval_noalloc(int32_t precision, int32_t objective, int32_t d
                                  const double* shift_dev, const double* rot_dev, const double* x_dev, int64_t ld,
                                  int32_t n, double* f_dev, void* cuda_stream);
 
+/* ---- surrogate network ----------------------------------------------
+ * The paper has no surrogate; it motivates costly objectives in its Abstract.
+ * This network screens candidate trials in the surrogate-assisted workload.
+ *
+ * Architecture: MLP 20 -> 256 -> 256 -> 1 with ReLU, 71,425 parameters.
+ *   h1 = relu(W1 x/100 + b1),  h2 = relu(W2 h1 + b2),  y = w3 . h2 + b3.
+ * Parameter vector (FP32, DE_MLP_PARAMS entries, in this order):
+ *   W1 (256 x 20, row-major), b1 (256), W2 (256 x 256), b2 (256), w3 (256), b3.
+ *
+ * Arithmetic: BF16 operands on the tensor cores (tcgen05) with FP32
+ * accumulation; FP32 epilogues, FP32 master weights, Adam in FP32.
+ * Training minimises the mean squared error over minibatches of 256 rows.
+ * Adam uses beta1 = 0.9, beta2 = 0.999, eps = 1e-8.
+ * Work goes on the stream given to de_mlp_create.  Calls that return host
+ * data synchronise it. */
+#define DE_MLP_PARAMS 71425
+typedef struct de_mlp de_mlp;
+
+/* Allocate the network on the current device.  Weights are He-uniform from
+ * `seed`; biases and Adam moments start at zero. */
+DE_API de_status de_mlp_create(uint64_t seed, void* cuda_stream, de_mlp** out);
+DE_API de_status de_mlp_destroy(de_mlp* m);
+/* Replace the parameters (host, DE_MLP_PARAMS floats) and reset Adam. */
+DE_API de_status de_mlp_set_params(de_mlp* m, const float* params);
+DE_API de_status de_mlp_get_params(de_mlp* m, float* params);
+/* y_dev[i] = network(x_dev row i), for n rows of 20 doubles with stride ld (>= 20). */
+DE_API de_status de_mlp_forward(de_mlp* m, const double* x_dev, int64_t ld, int32_t n, float* y_dev);
+/* Gradient of the loss (1/256) sum (y - t)^2 over rows 0..255 of x_dev,
+ * with targets t_dev (device, 256 floats), without changing the parameters.
+ * grad (host, DE_MLP_PARAMS floats) and loss (host, one float) may be NULL. */
+DE_API de_status de_mlp_grad(de_mlp* m, const double* x_dev, int64_t ld, const float* t_dev, float* grad,
+                             float* loss);
+/* `steps` Adam steps with learning rate lr.  Each minibatch holds 256 rows
+ * drawn uniformly, with replacement, from the n rows of x_dev and t_dev.
+ * The draws come from a Philox stream keyed by the seed and the step count.
+ * *loss (may be NULL) receives the loss of the last minibatch. */
+DE_API de_status de_mlp_train(de_mlp* m, const double* x_dev, int64_t ld, const float* t_dev, int32_t n,
+                              int32_t steps, float lr, float* loss);
+
 /* Copy run `run`'s current population (np*d, host) and fitness (np, host)
  * out; either pointer may be NULL.  Synchronises. */
 DE_API de_status de_get_population(de_handle* h, int32_t run, double* x_host, double* f_host);

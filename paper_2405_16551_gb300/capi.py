@@ -24,6 +24,7 @@ DE_STOP_NONE, DE_STOP_TARGET, DE_STOP_EVALS, DE_STOP_GENERATIONS = 0, 1, 2, 3
 DE_BAND_NEAR, DE_BAND_ALL = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -104,6 +105,14 @@ def load(build_if_missing: bool = True):
             "de_save": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_load": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_destroy": ([H], ctypes.c_int),
+            "de_mlp_create": ([ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
+            "de_mlp_destroy": ([H], ctypes.c_int),
+            "de_mlp_set_params": ([H, _fp], ctypes.c_int),
+            "de_mlp_get_params": ([H, _fp], ctypes.c_int),
+            "de_mlp_forward": ([H, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p], ctypes.c_int),
+            "de_mlp_grad": ([H, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, _fp, _fp], ctypes.c_int),
+            "de_mlp_train": ([H, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                              ctypes.c_float, _fp], ctypes.c_int),
             "de_eval_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                  ctypes.c_void_p], ctypes.c_int),
@@ -120,7 +129,8 @@ def exported_symbols():
     return ["de_version", "de_status_string", "de_last_error", "de_init", "de_init_batch", "de_reset", "de_step", "de_run",
             "de_eval", "de_get_population", "de_set_population", "de_set_generation", "de_get_best",
             "de_get_debug", "de_get_shape", "de_get_stats", "de_get_plan", "de_save", "de_load", "de_destroy",
-            "de_eval_noalloc"]
+            "de_eval_noalloc", "de_mlp_create", "de_mlp_destroy", "de_mlp_set_params", "de_mlp_get_params",
+            "de_mlp_forward", "de_mlp_grad", "de_mlp_train"]
 
 
 def _status_name(s):
@@ -209,6 +219,66 @@ def de_eval_noalloc(precision: int, objective: int, d: int, scale: float, shift_
                                 ctypes.c_void_p(rot_dev_ptr), ctypes.c_void_p(x_dev_ptr), ld, n,
                                 ctypes.c_void_p(f_dev_ptr), ctypes.c_void_p(stream))
     _check(st, None)
+
+
+# ----------------------------------------------------------------------------- surrogate network
+DE_MLP_PARAMS = 71425
+MLP_SHAPES = (("W1", (256, 20)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("w3", (256,)), ("b3", (1,)))
+
+
+def mlp_unpack(p):
+    """Parameter vector -> dict of arrays (float64 copies)."""
+    out, off = {}, 0
+    for k, shp in MLP_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(p[off:off + n], dtype=np.float64).reshape(shp).copy()
+        off += n
+    return out
+
+
+def mlp_pack(d):
+    return np.concatenate([np.asarray(d[k], dtype=np.float32).ravel() for k, _ in MLP_SHAPES])
+
+
+def de_mlp_create(seed=1, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().de_mlp_create(seed, stream, ctypes.byref(h)), None)
+    return h.value
+
+
+def de_mlp_destroy(m):
+    load().de_mlp_destroy(m)
+
+
+def de_mlp_set_params(m, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == DE_MLP_PARAMS
+    _check(load().de_mlp_set_params(m, p.ctypes.data_as(_fp)), None)
+
+
+def de_mlp_get_params(m):
+    p = np.zeros(DE_MLP_PARAMS, dtype=np.float32)
+    _check(load().de_mlp_get_params(m, p.ctypes.data_as(_fp)), None)
+    return p
+
+
+def de_mlp_forward(m, x_dev_ptr: int, ld: int, n: int, y_dev_ptr: int):
+    _check(load().de_mlp_forward(m, ctypes.c_void_p(x_dev_ptr), ld, n, ctypes.c_void_p(y_dev_ptr)), None)
+
+
+def de_mlp_grad(m, x_dev_ptr: int, ld: int, t_dev_ptr: int):
+    g = np.zeros(DE_MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(load().de_mlp_grad(m, ctypes.c_void_p(x_dev_ptr), ld, ctypes.c_void_p(t_dev_ptr), g.ctypes.data_as(_fp),
+                              ctypes.byref(loss)), None)
+    return g, loss.value
+
+
+def de_mlp_train(m, x_dev_ptr: int, ld: int, t_dev_ptr: int, n: int, steps: int, lr: float = 1e-3):
+    loss = ctypes.c_float()
+    _check(load().de_mlp_train(m, ctypes.c_void_p(x_dev_ptr), ld, ctypes.c_void_p(t_dev_ptr), n, steps, lr,
+                               ctypes.byref(loss)), None)
+    return loss.value
 
 
 def de_get_shape(h, run: int = 0):

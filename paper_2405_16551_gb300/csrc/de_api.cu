@@ -51,6 +51,12 @@ struct de_handle {
 static int cur_buf(const de_handle* h, int64_t gen) { return h->dbuf ? (int)(gen & 1) : 0; }
 
 static thread_local std::string g_err;
+
+namespace de {
+// The thread's last error message, as de_last_error(NULL) returns it (for
+// entry points outside this file).
+void set_last_error(const std::string& m) { g_err = m; }
+}  // namespace de
 static const char* kVersion = "de_gb300 1.0 sm_103a";
 
 // ---------------------------------------------------------------- helpers

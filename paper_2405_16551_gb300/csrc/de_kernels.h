@@ -10,6 +10,8 @@
 
 namespace de {
 
+void set_last_error(const std::string& m);
+
 // FP64 path (de_fp64.cu)
 void k_configure(size_t smem_gen);
 void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,

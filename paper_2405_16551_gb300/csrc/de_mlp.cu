@@ -1,0 +1,764 @@
+// de_mlp.cu -- the surrogate network: MLP 20 -> 256 -> 256 -> 1 (ReLU) with
+// BF16 operands on tcgen05 tensor cores, FP32 accumulation in TMEM, FP32
+// master weights and Adam.
+//
+// The paper has no surrogate; this network serves the surrogate-assisted
+// workload: it ranks several candidate trials per target so that only one
+// reaches a costly objective (the paper's Abstract motivates costly
+// objectives).  Input x in [-100, 100]^20 enters as x / 100, with a constant 1
+// in column 20 so that the first bias is column 20 of W1.
+//
+//   k_mlp_pass<false>  rows -> y; one CTA per 128 rows: layer 1 (K = 32) and
+//                   layer 2 (K = 256) as tcgen05 products, ReLU / bias /
+//                   output dot product in the TMEM epilogues
+//   k_mlp_pass<true>   one training step's forward and backward pass for one
+//                   128-row half of a 256-row minibatch: dZ2 = dy w3 relu',
+//                   dH1 = dZ2 W2 on the tensor cores, dZ1 = dH1 relu'; writes
+//                   the transposed operands of the weight gradients
+//   k_mlp_update    weight gradients as products over the batch
+//                   (dW2 = dZ2^T H1 with a ones row for db2, dW1 = dZ1^T A1),
+//                   then Adam on the FP32 masters and the BF16 operand copies
+//
+// Operand layout in shared and global memory: the canonical K-major, no
+// swizzle layout of de_tcgen05.cuh (core matrices of 8 rows x 16 bytes).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <cmath>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "de.h"
+#include "de_common.cuh"
+#include "de_mlp.h"
+#include "de_tcgen05.cuh"
+
+namespace de {
+
+constexpr uint32_t kPurposeSurr = 5u;  // minibatch draws of surrogate training
+
+// ------------------------------------------------------------------ layout helpers
+// Byte offset of bf16 element (row, k) in a K-major tile with RG row groups.
+__device__ __forceinline__ uint32_t toff(int row, int k, int RG) {
+  return (uint32_t)(((((k >> 3) * RG) + (row >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+}
+
+// D (TMEM) = or += A (M = 128, K = 16 ksteps) B^T (N rows); A and B K-major
+// with RGa / RGb row groups.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint32_t a, int rga, uint32_t b, int rgb, int ksteps, int n,
+                                         bool accumulate) {
+  const uint32_t la = (uint32_t)rga * 128u, lb = (uint32_t)rgb * 128u, id = idesc_bf16(n);
+  for (int ks = 0; ks < ksteps; ++ks)
+    mma_split<2>(d, smem_desc(a + (uint32_t)ks * 2u * la, la, 128u), smem_desc(b + (uint32_t)ks * 2u * lb, lb, 128u),
+                 id, (accumulate || ks > 0) ? 1u : 0u);
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat16 lo = __float2bfloat16_rn(a), hi = __float2bfloat16_rn(b);
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void st_bf16(uint8_t* base, uint32_t off, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+}
+
+// 8 consecutive columns (k0 multiple of 8) of row `row` as one 16-byte store.
+__device__ __forceinline__ void st_bf16x8(uint8_t* base, int row, int k0, int RG, const float* v) {
+  uint4 u;
+  u.x = pack_bf16x2(v[0], v[1]);
+  u.y = pack_bf16x2(v[2], v[3]);
+  u.z = pack_bf16x2(v[4], v[5]);
+  u.w = pack_bf16x2(v[6], v[7]);
+  *reinterpret_cast<uint4*>(base + toff(row, k0, RG)) = u;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Row index of minibatch row m at training step `step` (Philox, purpose SURR).
+__device__ __forceinline__ int batch_row(const MlpStepArgs& a, int m) {
+  if (a.sample_n <= 0) return m;  // the first rows, in order
+  const U32x4 w = draw_block(a.seed, kPurposeSurr, 0u, 0u, (uint32_t)a.step, (uint32_t)(m >> 2), 0u);
+  const uint32_t u = word_of(w, m & 3);
+  return (int)((a.sample_base + map_to_range(u, (uint32_t)a.sample_n)) % (uint32_t)a.sample_cap);
+}
+
+// ------------------------------------------------------------------ forward / backward
+// Shared memory of k_mlp_pass (dynamic, 1024-aligned).
+constexpr uint32_t kSBig = 0;                 // 128 KB: W2k; later dZ2 (A) + W2t half 0
+constexpr uint32_t kSH1 = 131072;             // 64 KB: H1 (A operand of layer 2); later W2t half 1
+constexpr uint32_t kSW1 = 196608;             // 16 KB: W1k
+constexpr uint32_t kSA1 = 212992;             // 8 KB: A1 (inputs)
+constexpr uint32_t kMlpSmem = 221184;
+
+// TRAIN = false: forward of n rows of x (row stride ld) to y.
+// TRAIN = true : forward + backward of minibatch half blockIdx.x.
+template <bool TRAIN>
+__global__ void __launch_bounds__(256, 1) k_mlp_pass(MlpDev P, MlpStepArgs a, const double* __restrict__ x,
+                                                     int64_t ld, int n, const float* __restrict__ t,
+                                                     float* __restrict__ yout) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bars[3];  // weights, mma, W2t
+  __shared__ uint32_t s_tmem;
+  __shared__ float s_y[2][kTileM];
+  __shared__ float s_t[kTileM];
+  __shared__ float s_dw3[4][kMlpH];
+  __shared__ float s_red[8][2];
+  __shared__ int s_err;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3, h = warp >> 2;
+  const int m = 32 * q + lane;                 // tile row of this thread in the epilogues
+  const int row0 = blockIdx.x * kTileM;
+  const uint32_t sb = smem_u32(smem);
+  const uint32_t b_w = smem_u32(&bars[0]), b_mma = smem_u32(&bars[1]), b_w2t = smem_u32(&bars[2]);
+
+  if (tid == 0) {
+    for (int k = 0; k < 3; ++k) mbar_init(smem_u32(&bars[k]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_err = 0;
+    mbar_expect_tx(b_w, kMlpW1Bytes + kMlpW2Bytes);
+    bulk_g2s(sb + kSW1, P.w1k, kMlpW1Bytes, b_w);
+    bulk_g2s(sb + kSBig, P.w2k, kMlpW2Bytes, b_w);
+  }
+  if (warp == 0) tmem_alloc(&s_tmem, 512);
+
+  // ---- inputs: A1 row = (x / 100, 1, 0 ...) in bf16; two threads per row
+  {
+    const int r = tid >> 1, half = tid & 1;
+    const int grow = row0 + r;
+    int src = -1;
+    if (TRAIN) src = batch_row(a, grow);
+    else if (grow < n) src = grow;
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int col = 16 * half + c;
+      float val = 0.f;
+      if (src >= 0) {
+        if (col < kMlpIn) val = (float)(x[(size_t)src * ld + col] * 0.01);
+        else if (col == kMlpIn) val = 1.f;
+      }
+      v[c] = val;
+    }
+    st_bf16x8(smem + kSA1, r, 16 * half, 16, v);
+    st_bf16x8(smem + kSA1, r, 16 * half + 8, 16, v + 8);
+    if (TRAIN) {
+      // A1^T (32 x 256 batch, 4 row groups) for the W1 gradient
+#pragma unroll
+      for (int c = 0; c < 16; ++c) st_bf16(P.a1t, toff(16 * half + c, grow, 4), v[c]);
+      if (half == 0) s_t[r] = src >= 0 ? t[src] : 0.f;
+    }
+  }
+  fence_async_smem();
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = s_tmem;
+  const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+
+  // ---- layer 1: Z1 = A1 W1k^T -> TMEM columns [0, 256)
+  if (tid == 0) {
+    if (!mbar_wait(b_w, 0)) s_err = 1;
+    else {
+      tc_after_sync();
+      mma_bf16(tmem, sb + kSA1, 16, sb + kSW1, 32, 2, kMlpH, false);
+    }
+    mma_commit(b_mma);
+  }
+  if (!mbar_wait(b_mma, 0)) s_err = 1;
+  tc_after_sync();
+
+  // ---- epilogue 1: H1 = relu(Z1) to shared memory (A operand of layer 2);
+  // training: its transpose to global memory and the ReLU mask in registers
+  uint32_t mask[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c0 = 128 * h + 32 * j;
+    float v[32];
+    tmem_ld_cols32(tmem + lane_base + (uint32_t)c0, v);
+    uint32_t mk = 0;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      v[e] = fmaxf(v[e], 0.f);
+      mk |= (v[e] > 0.f ? 1u : 0u) << e;
+    }
+    mask[j] = mk;
+#pragma unroll
+    for (int e = 0; e < 32; e += 8) st_bf16x8(smem + kSH1, m, c0 + e, 16, v + e);
+    if (TRAIN) {
+#pragma unroll
+      for (int e = 0; e < 32; ++e) st_bf16(P.h1t, toff(c0 + e, row0 + m, 32), v[e]);
+    }
+  }
+  fence_async_smem();
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+
+  // ---- layer 2: Z2 = H1 W2k^T -> TMEM columns [256, 512)
+  if (tid == 0) {
+    if (!s_err) mma_bf16(tmem + 256, sb + kSH1, 16, sb + kSBig, 32, 16, kMlpH, false);
+    mma_commit(b_mma);
+  }
+  if (!mbar_wait(b_mma, 1)) s_err = 1;
+  tc_after_sync();
+  if (TRAIN && tid == 0) {
+    // W2k and H1 are consumed: stage W2^T (two 128-row halves) for dH1
+    mbar_expect_tx(b_w2t, kMlpW2Bytes);
+    bulk_g2s(sb + kSBig + 65536, P.w2t, kMlpW2Bytes / 2, b_w2t);
+    bulk_g2s(sb + kSH1, P.w2t + kMlpW2Bytes / 2, kMlpW2Bytes / 2, b_w2t);
+  }
+
+  // ---- epilogue 2: y = w3 . relu(Z2 + b2) + b3
+  float yp = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c0 = 128 * h + 32 * j;
+    float v[32];
+    tmem_ld_cols32(tmem + lane_base + 256u + (uint32_t)c0, v);
+#pragma unroll
+    for (int e = 0; e < 32; ++e) yp = fmaf(fmaxf(v[e] + P.b2[c0 + e], 0.f), P.w3[c0 + e], yp);
+  }
+  s_y[h][m] = yp;
+  __syncthreads();
+  const float y = s_y[0][m] + s_y[1][m] + P.b3[0];
+  if (!TRAIN) {
+    if (h == 0 && row0 + m < n) yout[row0 + m] = y;
+  } else {
+    // mean squared error over the 256-row minibatch
+    const float r = y - s_t[m];
+    const float dy = 2.f * r / (float)kMlpBatch;
+    // dZ2 = dy w3 relu'(Z2 + b2): A operand of dH1 (shared) and, transposed,
+    // of dW2 (global); dw3 = sum over rows of H2 dy
+    for (int j = 0; j < 4; ++j) {
+      const int c0 = 128 * h + 32 * j;
+      float v[32], dz[32];
+      tmem_ld_cols32(tmem + lane_base + 256u + (uint32_t)c0, v);
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        const float zb = v[e] + P.b2[c0 + e];
+        const float h2 = fmaxf(zb, 0.f);
+        dz[e] = zb > 0.f ? dy * P.w3[c0 + e] : 0.f;
+        float s = h2 * dy;  // row contribution to dw3[c0 + e]
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) s_dw3[q][c0 + e] = s;
+        st_bf16(P.dz2t + (size_t)((c0 + e) >> 7) * (kMlpW2Bytes / 2), toff((c0 + e) & 127, row0 + m, 16), dz[e]);
+      }
+#pragma unroll
+      for (int e = 0; e < 32; e += 8) st_bf16x8(smem + kSBig, m, c0 + e, 16, dz + e);
+    }
+    // loss and db3 partials of this half
+    float rs = r * r, ds = dy;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rs += __shfl_xor_sync(0xffffffffu, rs, o);
+      ds += __shfl_xor_sync(0xffffffffu, ds, o);
+    }
+    if (lane == 0) {
+      s_red[warp][0] = rs;
+      s_red[warp][1] = ds;
+    }
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid < kMlpH) {
+      // fixed order over the four row quarters
+      P.part[blockIdx.x * kMlpPart + tid] = ((s_dw3[0][tid] + s_dw3[1][tid]) + s_dw3[2][tid]) + s_dw3[3][tid];
+    }
+    if (tid == 0) {
+      // db3 and the squared error from the h = 0 warps (each row once)
+      P.part[blockIdx.x * kMlpPart + kMlpH] = ((s_red[0][1] + s_red[1][1]) + s_red[2][1]) + s_red[3][1];
+      P.part[blockIdx.x * kMlpPart + kMlpH + 1] = ((s_red[0][0] + s_red[1][0]) + s_red[2][0]) + s_red[3][0];
+    }
+
+    // ---- dH1 = dZ2 W2: A = dZ2 (shared), B = W2^T halves -> TMEM [0, 256)
+    if (tid == 0) {
+      if (!mbar_wait(b_w2t, 0)) s_err = 1;
+      else {
+        tc_after_sync();
+        mma_bf16(tmem, sb + kSBig, 16, sb + kSBig + 65536, 16, 16, 128, false);
+        mma_bf16(tmem + 128, sb + kSBig, 16, sb + kSH1, 16, 16, 128, false);
+      }
+      mma_commit(b_mma);
+    }
+    if (!mbar_wait(b_mma, 0)) s_err = 1;
+    tc_after_sync();
+
+    // ---- epilogue 3: dZ1 = dH1 relu'(Z1), transposed to global memory
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c0 = 128 * h + 32 * j;
+      float v[32];
+      tmem_ld_cols32(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        const float g = ((mask[j] >> e) & 1u) ? v[e] : 0.f;
+        st_bf16(P.dz1t + (size_t)((c0 + e) >> 7) * (kMlpW2Bytes / 2), toff((c0 + e) & 127, row0 + m, 16), g);
+      }
+    }
+  }
+  tc_before_sync();
+  __syncthreads();
+  if (s_err && tid == 0) atomicOr(P.err, 1);
+  if (warp == 0) tmem_free(tmem, 512);
+}
+
+// ------------------------------------------------------------------ weight gradients + Adam
+struct AdamArgs {
+  float lr, c1, c2, eps, beta1, beta2;  // c1 = 1 - beta1^t, c2 = 1 - beta2^t
+  float omb1, omb2;                     // 1 - beta1, 1 - beta2 (rounded once from FP64)
+  int apply;                            // 0: write raw gradients to P.grad instead
+};
+
+__device__ __forceinline__ float adam_step(float w, float g, float* m, float* v, const AdamArgs& A) {
+  const float mn = fmaf(A.beta1, *m, A.omb1 * g);
+  const float vn = fmaf(A.beta2, *v, A.omb2 * g * g);
+  *m = mn;
+  *v = vn;
+  return w - A.lr * (mn / A.c1) / (sqrtf(vn / A.c2) + A.eps);
+}
+
+// Blocks 0, 1: rows [128 b, 128 b + 128) of W2 and b2; block 2: W1, b1, w3, b3.
+__global__ void __launch_bounds__(256, 1) k_mlp_update(MlpDev P, AdamArgs A) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_err;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3, h = warp >> 2;
+  const uint32_t sb = smem_u32(smem);
+  const uint32_t b_ld = smem_u32(&bars[0]), b_mma = smem_u32(&bars[1]);
+  const bool w2 = blockIdx.x < 2;
+  const uint32_t ncols = w2 ? 512u : 64u;
+  if (tid == 0) {
+    mbar_init(b_ld, 1);
+    mbar_init(b_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_err = 0;
+    if (w2) {
+      mbar_expect_tx(b_ld, kMlpW2Bytes / 2 + kMlpW2Bytes);
+      bulk_g2s(sb, P.dz2t + (size_t)blockIdx.x * (kMlpW2Bytes / 2), kMlpW2Bytes / 2, b_ld);
+      bulk_g2s(sb + 65536, P.h1t, kMlpW2Bytes, b_ld);
+    } else {
+      mbar_expect_tx(b_ld, kMlpW2Bytes + kMlpA1tBytes);
+      bulk_g2s(sb, P.dz1t, kMlpW2Bytes, b_ld);
+      bulk_g2s(sb + 131072, P.a1t, kMlpA1tBytes, b_ld);
+    }
+  }
+  if (w2) {
+    // a ones row (row 0 of a 16-row operand) so that column 256 of the
+    // product is the sum over the batch, i.e. the gradient of b2
+    for (int e = tid; e < 16 * kMlpBatch; e += blockDim.x) {
+      const int r = e / kMlpBatch, k = e % kMlpBatch;
+      st_bf16(smem + 196608, toff(r, k, 2), r == 0 ? 1.f : 0.f);
+    }
+  }
+  if (warp == 0) tmem_alloc(&s_tmem, ncols);
+  fence_async_smem();
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = s_tmem;
+  if (tid == 0) {
+    if (!mbar_wait(b_ld, 0)) s_err = 1;
+    else {
+      tc_after_sync();
+      if (w2) {
+        mma_bf16(tmem, sb, 16, sb + 65536, 32, 16, kMlpH, false);
+        mma_bf16(tmem + 256, sb, 16, sb + 196608, 2, 16, 16, false);
+      } else {
+        mma_bf16(tmem, sb, 16, sb + 131072, 4, 16, 32, false);
+        mma_bf16(tmem + 32, sb + 65536, 16, sb + 131072, 4, 16, 32, false);
+      }
+    }
+    mma_commit(b_mma);
+  }
+  if (!mbar_wait(b_mma, 0)) s_err = 1;
+  tc_after_sync();
+  const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+
+  if (w2) {
+    const int o = 128 * blockIdx.x + 32 * q + lane;  // output unit of this thread
+    for (int j = 0; j < 4; ++j) {
+      const int c0 = 128 * h + 32 * j;
+      float g[32];
+      tmem_ld_cols32(tmem + lane_base + (uint32_t)c0, g);
+      float wn[32];
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        const size_t k = (size_t)o * kMlpH + c0 + e;
+        if (A.apply) {
+          wn[e] = adam_step(P.W2[k], g[e], P.mW2 + k, P.vW2 + k, A);
+          P.W2[k] = wn[e];
+        } else {
+          P.grad[kMlpOffW2 + k] = g[e];
+          wn[e] = P.W2[k];
+        }
+        // W2^T halves (row = input unit, k = output unit), 16 row groups
+        st_bf16(P.w2t + (size_t)((c0 + e) >> 7) * (kMlpW2Bytes / 2), toff((c0 + e) & 127, o, 16), wn[e]);
+      }
+#pragma unroll
+      for (int e = 0; e < 32; e += 8) st_bf16x8(P.w2k, o, c0 + e, 32, wn + e);
+    }
+    if (h == 0) {
+      const float gb = tmem_ld1(tmem + lane_base + 256u);
+      if (A.apply) P.b2[o] = adam_step(P.b2[o], gb, P.mb2 + o, P.vb2 + o, A);
+      else P.grad[kMlpOffB2 + o] = gb;
+    }
+  } else {
+    // W1 (and b1 in column 20): thread row o of half h
+    const int o = 128 * h + 32 * q + lane;
+    float g[32];
+    tmem_ld_cols32(tmem + lane_base + 32u * (uint32_t)h, g);
+    float wn[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      if (c < kMlpIn) {
+        const size_t k = (size_t)o * kMlpIn + c;
+        if (A.apply) {
+          wn[c] = adam_step(P.W1[k], g[c], P.mW1 + k, P.vW1 + k, A);
+          P.W1[k] = wn[c];
+        } else {
+          P.grad[kMlpOffW1 + k] = g[c];
+          wn[c] = P.W1[k];
+        }
+      } else if (c == kMlpIn) {
+        if (A.apply) {
+          wn[c] = adam_step(P.b1[o], g[c], P.mb1 + o, P.vb1 + o, A);
+          P.b1[o] = wn[c];
+        } else {
+          P.grad[kMlpOffB1 + o] = g[c];
+          wn[c] = P.b1[o];
+        }
+      } else {
+        wn[c] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 32; c += 8) st_bf16x8(P.w1k, o, c, 32, wn + c);
+    // w3 and b3 from the two halves' partial sums, in a fixed order
+    const float gw = P.part[tid] + P.part[kMlpPart + tid];
+    if (A.apply) P.w3[tid] = adam_step(P.w3[tid], gw, P.mw3 + tid, P.vw3 + tid, A);
+    else P.grad[kMlpOffW3 + tid] = gw;
+    if (tid == 0) {
+      const float gb = P.part[kMlpH] + P.part[kMlpPart + kMlpH];
+      if (A.apply) P.b3[0] = adam_step(P.b3[0], gb, P.mb3, P.vb3, A);
+      else P.grad[kMlpOffB3] = gb;
+      P.loss[0] = (P.part[kMlpH + 1] + P.part[kMlpPart + kMlpH + 1]) / (float)kMlpBatch;
+    }
+  }
+  tc_before_sync();
+  __syncthreads();
+  if (s_err && tid == 0) atomicOr(P.err, 1);
+  if (warp == 0) tmem_free(tmem, ncols);
+}
+
+// BF16 operand copies from the FP32 masters (after set-up or a parameter load).
+__global__ void k_mlp_pack(MlpDev P) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (int e = tid; e < kMlpH * 32; e += stride) {
+    const int o = e / 32, c = e % 32;
+    const float v = c < kMlpIn ? P.W1[o * kMlpIn + c] : (c == kMlpIn ? P.b1[o] : 0.f);
+    st_bf16(P.w1k, toff(o, c, 32), v);
+  }
+  for (int e = tid; e < kMlpH * kMlpH; e += stride) {
+    const int o = e / kMlpH, i = e % kMlpH;
+    const float v = P.W2[e];
+    st_bf16(P.w2k, toff(o, i, 32), v);
+    st_bf16(P.w2t + (size_t)(i >> 7) * (kMlpW2Bytes / 2), toff(i & 127, o, 16), v);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+void mlp_configure() {
+  cudaFuncSetAttribute(k_mlp_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
+  cudaFuncSetAttribute(k_mlp_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
+  cudaFuncSetAttribute(k_mlp_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+void mlp_pack_launch(const MlpDev& P, cudaStream_t s) { k_mlp_pack<<<64, 256, 0, s>>>(P); }
+
+void mlp_forward_launch(const MlpDev& P, const double* x, int64_t ld, int n, float* y, cudaStream_t s) {
+  if (n <= 0) return;
+  MlpStepArgs a{};
+  k_mlp_pass<false><<<(n + kTileM - 1) / kTileM, 256, kMlpSmem, s>>>(P, a, x, ld, n, nullptr, y);
+}
+
+void mlp_step_launch(const MlpDev& P, const MlpStepArgs& a, const double* x, int64_t ld, const float* t, float lr,
+                     bool apply, cudaStream_t s) {
+  k_mlp_pass<true><<<kMlpBatch / kTileM, 256, kMlpSmem, s>>>(P, a, x, ld, 0, t, nullptr);
+  AdamArgs A;
+  const double b1 = 0.9, b2 = 0.999;
+  A.lr = lr;
+  A.beta1 = (float)b1;
+  A.beta2 = (float)b2;
+  A.c1 = (float)(1.0 - pow(b1, (double)(a.step + 1)));
+  A.c2 = (float)(1.0 - pow(b2, (double)(a.step + 1)));
+  A.eps = 1e-8f;
+  A.omb1 = (float)(1.0 - b1);
+  A.omb2 = (float)(1.0 - b2);
+  A.apply = apply ? 1 : 0;
+  k_mlp_update<<<3, 256, 200 * 1024, s>>>(P, A);
+}
+
+}  // namespace de
+
+// ------------------------------------------------------------------ C ABI
+struct de_mlp {
+  cudaStream_t stream = nullptr;
+  uint64_t seed = 0;
+  long long step = 0;
+  void* arena = nullptr;
+  de::MlpDev P{};
+  std::string err;
+};
+
+namespace de {
+
+static de_status mlp_fail(de_mlp* m, de_status s, const std::string& msg) {
+  if (m) m->err = msg;
+  set_last_error(msg);
+  return s;
+}
+
+static bool mlp_dev_ptr(const void* p) {
+  cudaPointerAttributes a{};
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice;
+}
+
+static uint64_t mlp_splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// He-uniform weights (bound sqrt(6 / fan_in)), zero biases, from the seed.
+void mlp_init_params(uint64_t seed, float* p) {
+  uint64_t s = seed ^ 0x5EED5EEDull;
+  auto fill = [&](int off, int count, int fan_in) {
+    const double b = sqrt(6.0 / fan_in);
+    for (int e = 0; e < count; ++e) p[off + e] = (float)(-b + 2.0 * b * ((mlp_splitmix(s) >> 11) * 0x1.0p-53));
+  };
+  memset(p, 0, sizeof(float) * kMlpParams);
+  fill(kMlpOffW1, kMlpH * kMlpIn, kMlpIn);
+  fill(kMlpOffW2, kMlpH * kMlpH, kMlpH);
+  fill(kMlpOffW3, kMlpH, kMlpH);
+}
+
+static de_status mlp_upload(de_mlp* m, const float* p) {
+  cudaError_t e = cudaMemcpyAsync(m->P.W1, p, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->P.mW1, 0, sizeof(float) * kMlpParams, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->P.vW1, 0, sizeof(float) * kMlpParams, m->stream);
+  if (e == cudaSuccess) {
+    mlp_pack_launch(m->P, m->stream);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return mlp_fail(m, DE_ERR_CUDA, std::string("surrogate parameters: ") + cudaGetErrorString(e));
+  m->step = 0;
+  return DE_OK;
+}
+
+static de_status mlp_check(de_mlp* m) {
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, m->P.err, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return mlp_fail(m, DE_ERR_CUDA, std::string("surrogate: ") + cudaGetErrorString(e));
+  if (err) return mlp_fail(m, DE_ERR_TIMEOUT, "surrogate: a device-side wait timed out");
+  return DE_OK;
+}
+
+de_status mlp_create(uint64_t seed, cudaStream_t stream, de_mlp** out) {
+  de_mlp* m = new de_mlp();
+  m->stream = stream;
+  m->seed = seed;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 1023) / 1024 * 1024;
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  const size_t pw = take(sizeof(float) * kMlpParams), pm = take(sizeof(float) * kMlpParams),
+               pv = take(sizeof(float) * kMlpParams);
+  const size_t o_w1k = take(kMlpW1Bytes), o_w2k = take(kMlpW2Bytes), o_w2t = take(kMlpW2Bytes);
+  const size_t o_h1t = take(kMlpW2Bytes), o_dz2t = take(kMlpW2Bytes), o_dz1t = take(kMlpW2Bytes);
+  const size_t o_a1t = take(kMlpA1tBytes), o_part = take(sizeof(float) * 2 * kMlpPart);
+  const size_t o_grad = take(sizeof(float) * kMlpParams), o_loss = take(sizeof(float)), o_err = take(sizeof(int));
+  cudaError_t e = cudaMalloc(&m->arena, off);
+  if (e != cudaSuccess) {
+    delete m;
+    return mlp_fail(nullptr, e == cudaErrorMemoryAllocation ? DE_ERR_OOM : DE_ERR_CUDA,
+                    std::string("surrogate arena: ") + cudaGetErrorString(e));
+  }
+  uint8_t* A = (uint8_t*)m->arena;
+  auto views = [&](float* base, float*& W1, float*& b1, float*& W2, float*& b2, float*& w3, float*& b3) {
+    W1 = base + kMlpOffW1;
+    b1 = base + kMlpOffB1;
+    W2 = base + kMlpOffW2;
+    b2 = base + kMlpOffB2;
+    w3 = base + kMlpOffW3;
+    b3 = base + kMlpOffB3;
+  };
+  MlpDev& P = m->P;
+  views((float*)(A + pw), P.W1, P.b1, P.W2, P.b2, P.w3, P.b3);
+  views((float*)(A + pm), P.mW1, P.mb1, P.mW2, P.mb2, P.mw3, P.mb3);
+  views((float*)(A + pv), P.vW1, P.vb1, P.vW2, P.vb2, P.vw3, P.vb3);
+  P.w1k = A + o_w1k;
+  P.w2k = A + o_w2k;
+  P.w2t = A + o_w2t;
+  P.h1t = A + o_h1t;
+  P.dz2t = A + o_dz2t;
+  P.dz1t = A + o_dz1t;
+  P.a1t = A + o_a1t;
+  P.part = (float*)(A + o_part);
+  P.grad = (float*)(A + o_grad);
+  P.loss = (float*)(A + o_loss);
+  P.err = (int*)(A + o_err);
+  mlp_configure();
+  e = cudaMemsetAsync(m->arena, 0, off, stream);
+  if (e != cudaSuccess) {
+    cudaFree(m->arena);
+    delete m;
+    return mlp_fail(nullptr, DE_ERR_CUDA, std::string("surrogate arena: ") + cudaGetErrorString(e));
+  }
+  std::vector<float> p(kMlpParams);
+  mlp_init_params(seed, p.data());
+  const de_status s = mlp_upload(m, p.data());
+  if (s != DE_OK) {
+    const std::string msg = m->err;
+    cudaFree(m->arena);
+    delete m;
+    return mlp_fail(nullptr, s, msg);
+  }
+  *out = m;
+  return DE_OK;
+}
+
+void mlp_destroy(de_mlp* m) {
+  if (!m) return;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  if (m->arena) cudaFree(m->arena);
+  delete m;
+}
+
+const MlpDev& mlp_dev(const de_mlp* m) { return m->P; }
+
+// `steps` Adam steps on minibatches drawn from rows [base, base + n) of a ring
+// of `cap` rows (x: FP64 rows of stride ld, t: FP32 targets, same indexing).
+de_status mlp_train_rows(de_mlp* m, const double* x, int64_t ld, const float* t, int n, int base, int cap, int steps,
+                         float lr) {
+  for (int k = 0; k < steps; ++k) {
+    MlpStepArgs a{m->seed, m->step, n, base, cap};
+    mlp_step_launch(m->P, a, x, ld, t, lr, true, m->stream);
+    ++m->step;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return mlp_fail(m, DE_ERR_CUDA, std::string("surrogate training: ") + cudaGetErrorString(e));
+  return DE_OK;
+}
+
+}  // namespace de
+
+using namespace de;
+
+extern "C" {
+
+de_status de_mlp_create(uint64_t seed, void* cuda_stream, de_mlp** out) {
+  if (!out) return mlp_fail(nullptr, DE_ERR_INVALID_ARG, "out is NULL");
+  return mlp_create(seed, (cudaStream_t)cuda_stream, out);
+}
+
+de_status de_mlp_destroy(de_mlp* m) {
+  mlp_destroy(m);
+  return DE_OK;
+}
+
+de_status de_mlp_set_params(de_mlp* m, const float* params) {
+  if (!m || !params) return mlp_fail(m, DE_ERR_INVALID_ARG, "handle or params is NULL");
+  for (int e = 0; e < kMlpParams; ++e)
+    if (!std::isfinite(params[e])) return mlp_fail(m, DE_ERR_NONFINITE, "params has a non-finite entry");
+  return mlp_upload(m, params);
+}
+
+de_status de_mlp_get_params(de_mlp* m, float* params) {
+  if (!m || !params) return mlp_fail(m, DE_ERR_INVALID_ARG, "handle or params is NULL");
+  cudaError_t e = cudaMemcpyAsync(params, m->P.W1, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return mlp_fail(m, DE_ERR_CUDA, std::string("surrogate parameters: ") + cudaGetErrorString(e));
+  return DE_OK;
+}
+
+de_status de_mlp_forward(de_mlp* m, const double* x_dev, int64_t ld, int32_t n, float* y_dev) {
+  if (!m) return mlp_fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 0 || ld < kMlpIn) return mlp_fail(m, DE_ERR_INVALID_ARG, "need n >= 0 and ld >= 20");
+  if (n == 0) return DE_OK;
+  if (!mlp_dev_ptr(x_dev) || !mlp_dev_ptr(y_dev))
+    return mlp_fail(m, DE_ERR_INVALID_ARG, "x_dev and y_dev must be device memory");
+  mlp_forward_launch(m->P, x_dev, ld, n, y_dev, m->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return mlp_fail(m, DE_ERR_CUDA, std::string("surrogate forward: ") + cudaGetErrorString(e));
+  return DE_OK;
+}
+
+de_status de_mlp_grad(de_mlp* m, const double* x_dev, int64_t ld, const float* t_dev, float* grad, float* loss) {
+  if (!m) return mlp_fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (ld < kMlpIn) return mlp_fail(m, DE_ERR_INVALID_ARG, "ld must be >= 20");
+  if (!mlp_dev_ptr(x_dev) || !mlp_dev_ptr(t_dev))
+    return mlp_fail(m, DE_ERR_INVALID_ARG, "x_dev and t_dev must be device memory");
+  MlpStepArgs a{m->seed, m->step, 0, 0, 1};
+  mlp_step_launch(m->P, a, x_dev, ld, t_dev, 0.f, false, m->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return mlp_fail(m, DE_ERR_CUDA, std::string("surrogate gradient: ") + cudaGetErrorString(e));
+  de_status s = mlp_check(m);
+  if (s != DE_OK) return s;
+  if (grad) e = cudaMemcpyAsync(grad, m->P.grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, m->P.loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return mlp_fail(m, DE_ERR_CUDA, std::string("surrogate gradient: ") + cudaGetErrorString(e));
+  return DE_OK;
+}
+
+de_status de_mlp_train(de_mlp* m, const double* x_dev, int64_t ld, const float* t_dev, int32_t n, int32_t steps,
+                       float lr, float* loss) {
+  if (!m) return mlp_fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (n < 1 || steps < 0 || ld < kMlpIn || !(lr > 0.f) || !std::isfinite(lr))
+    return mlp_fail(m, DE_ERR_INVALID_ARG, "need n >= 1, steps >= 0, ld >= 20 and a finite lr > 0");
+  if (!mlp_dev_ptr(x_dev) || !mlp_dev_ptr(t_dev))
+    return mlp_fail(m, DE_ERR_INVALID_ARG, "x_dev and t_dev must be device memory");
+  de_status s = mlp_train_rows(m, x_dev, ld, t_dev, n, 0, n, steps, lr);
+  if (s != DE_OK) return s;
+  s = mlp_check(m);
+  if (s != DE_OK) return s;
+  if (loss) {
+    cudaError_t e = cudaMemcpyAsync(loss, m->P.loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return mlp_fail(m, DE_ERR_CUDA, std::string("surrogate loss: ") + cudaGetErrorString(e));
+  }
+  return DE_OK;
+}
+
+}  // extern "C"
