@@ -78,6 +78,10 @@ def _load():
                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                 _dp, _dp, _dp, _dp, _i32p, _i32p, _u32p, _dp, _dp, _dp, _u8p, ctypes.c_int]
+        lib.or_step_cand.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                     ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _i32p,
+                                     _dp, _dp, _dp, _dp, _i32p, _i32p, _u32p, _dp, _dp, _dp, _u8p, ctypes.c_int]
         lib.or_best.argtypes = [ctypes.c_int, _dp]
         lib.or_best.restype = ctypes.c_int
         lib.or_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -245,10 +249,11 @@ def init_population(np_, d, lo, hi, seed, run_id=0):
     return X
 
 
-def step(X, fX, F, CR, lo, hi, obj, o, M, seed, generation, run_id=0, scale=1.0, threads=1):
+def step(X, fX, F, CR, lo, hi, obj, o, M, seed, generation, run_id=0, scale=1.0, threads=1, cand=None):
     """One synchronous generation; returns a dict with the next population and
     every intermediate (indices, j_rand, crossover mask, trials, f_trial,
-    magnitude sums, accept flags)."""
+    magnitude sums, accept flags).  cand: per-target candidate stream (None:
+    stream 0, plain DE)."""
     X = _f64(X)
     fX = _f64(fX)
     np_, d = X.shape
@@ -258,8 +263,9 @@ def step(X, fX, F, CR, lo, hi, obj, o, M, seed, generation, run_id=0, scale=1.0,
         jrand=np.zeros(np_, dtype=np.int32), mask=np.zeros((np_, nw), dtype=np.uint32),
         trial=np.zeros_like(X), f_trial=np.zeros(np_), sabs_trial=np.zeros(np_),
         accept=np.zeros(np_, dtype=np.uint8))
-    _load().or_step(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), scale, seed, run_id, generation,
-                    _p(X), _p(fX), _p(out["X_next"]), _p(out["f_next"]), _p(out["idx"], _i32p),
+    cnd = None if cand is None else np.ascontiguousarray(cand, dtype=np.int32)
+    _load().or_step_cand(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), scale, seed, run_id, generation,
+                    _p(cnd, _i32p), _p(X), _p(fX), _p(out["X_next"]), _p(out["f_next"]), _p(out["idx"], _i32p),
                     _p(out["jrand"], _i32p), _p(out["mask"], _u32p), _p(out["trial"]), _p(out["f_trial"]),
                     _p(out["sabs_trial"]), _p(out["accept"], _u8p), threads)
     return out

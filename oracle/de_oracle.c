@@ -278,12 +278,16 @@ uint64_t or_cr_threshold(double cr)
 /* nw = ceil(d/32) (bit j%32 of word j/32), trial[np*d], ftrial[np],          */
 /* sabs_trial[np], accept[np].                                                */
 /* ------------------------------------------------------------------------- */
-void or_step(int np, int d, double F, double CR, double lo, double hi,
-             int obj, const double* o, const double* M, double scale,
-             uint64_t seed, uint32_t run_id, uint32_t generation,
-             const double* X, const double* fX, double* Xn, double* fXn,
-             int32_t* idx, int32_t* jrand_out, uint32_t* mask, double* trial_out,
-             double* ftrial_out, double* sabs_out, uint8_t* accept_out, int threads)
+/* cand (may be NULL = all 0): per target, the candidate stream its trial is
+ * drawn from.  Stream 0 is plain DE/rand/1/bin; streams 1, 2, ... give the
+ * other candidate trials that a surrogate screens (the same Eq. 2 / Eq. 3
+ * construction with independent draws). */
+void or_step_cand(int np, int d, double F, double CR, double lo, double hi,
+                  int obj, const double* o, const double* M, double scale,
+                  uint64_t seed, uint32_t run_id, uint32_t generation, const int32_t* cand,
+                  const double* X, const double* fX, double* Xn, double* fXn,
+                  int32_t* idx, int32_t* jrand_out, uint32_t* mask, double* trial_out,
+                  double* ftrial_out, double* sabs_out, uint8_t* accept_out, int threads)
 {
     const int nw = (d + 31) / 32;
     const uint64_t T = or_cr_threshold(CR);
@@ -293,9 +297,10 @@ void or_step(int np, int d, double F, double CR, double lo, double hi,
 
     /* mutation (Eq. 2), crossover (Eq. 3) and bound repair for every target */
     for (int i = 0; i < np; ++i) {
+        const uint32_t ci = cand ? (uint32_t)cand[i] : 0u;
         uint32_t w[4];
         for (int k = 0; k < 4; ++k)
-            w[k] = or_draw(seed, OR_PURPOSE_STEP, run_id, 0, generation, (uint32_t)i, (uint32_t)k);
+            w[k] = or_draw(seed, OR_PURPOSE_STEP, run_id, ci, generation, (uint32_t)i, (uint32_t)k);
         uint32_t r[3];
         or_mutant_indices(w[0], w[1], w[2], (uint32_t)i, (uint32_t)np, r);
         uint32_t jrand = or_map(w[3], (uint32_t)d);
@@ -307,7 +312,7 @@ void or_step(int np, int d, double F, double CR, double lo, double hi,
         const double* x2 = X + (size_t)r[1] * d;
         const double* x3 = X + (size_t)r[2] * d;
         for (int j = 0; j < d; ++j) {
-            uint32_t u = or_draw(seed, OR_PURPOSE_STEP, run_id, 0, generation, (uint32_t)i, 4u + (uint32_t)j);
+            uint32_t u = or_draw(seed, OR_PURPOSE_STEP, run_id, ci, generation, (uint32_t)i, 4u + (uint32_t)j);
             int crossed = ((uint32_t)j == jrand) || ((uint64_t)u <= T);
             double t;
             if (crossed) {
@@ -344,6 +349,17 @@ void or_step(int np, int d, double F, double CR, double lo, double hi,
     free(trial);
     free(ft);
     free(sa);
+}
+
+void or_step(int np, int d, double F, double CR, double lo, double hi,
+             int obj, const double* o, const double* M, double scale,
+             uint64_t seed, uint32_t run_id, uint32_t generation,
+             const double* X, const double* fX, double* Xn, double* fXn,
+             int32_t* idx, int32_t* jrand_out, uint32_t* mask, double* trial_out,
+             double* ftrial_out, double* sabs_out, uint8_t* accept_out, int threads)
+{
+    or_step_cand(np, d, F, CR, lo, hi, obj, o, M, scale, seed, run_id, generation, NULL, X, fX, Xn, fXn,
+                 idx, jrand_out, mask, trial_out, ftrial_out, sabs_out, accept_out, threads);
 }
 
 /* Best individual: smallest f, lowest index on ties, NaN never best. */

@@ -413,3 +413,22 @@ def test_d2_grid_search_agrees_with_de(obj):
     assert np.max(np.abs(X[b] - x_grid)) < 1e-6
     assert abs(f[b] - f_grid) < 1e-8
     assert np.max(np.abs(X[b] - o)) < 1e-6
+
+
+def test_candidate_streams():
+    """Candidate stream c of target i uses cand = c in the counter: stream 0 is
+    plain DE, other streams give independent trials built the same way."""
+    np_, d = 12, 6
+    X = problems.population(np_, d, seed=21)
+    fX, _ = oracle.evaluate(0, X)
+    plain = oracle.step(X, fX, 0.5, 0.9, -100, 100, 0, None, None, seed=3, generation=4)
+    zero = oracle.step(X, fX, 0.5, 0.9, -100, 100, 0, None, None, seed=3, generation=4, cand=np.zeros(np_))
+    assert np.array_equal(plain["trial"], zero["trial"]) and np.array_equal(plain["idx"], zero["idx"])
+    cand = np.arange(np_) % 5
+    r = oracle.step(X, fX, 0.5, 0.9, -100, 100, 0, None, None, seed=3, generation=4, cand=cand)
+    for i in range(np_):
+        w = [oracle.draw(3, oracle.PURPOSE_STEP, 0, int(cand[i]), 4, i, k) for k in range(4)]
+        assert tuple(r["idx"][i]) == oracle.mutant_indices(w[0], w[1], w[2], i, np_)
+        assert r["jrand"][i] == oracle.map_index(w[3], d)
+    differ = [i for i in range(np_) if cand[i] != 0]
+    assert any(not np.array_equal(r["idx"][i], plain["idx"][i]) for i in differ)
