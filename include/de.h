@@ -129,6 +129,10 @@ typedef struct {
     int64_t max_generations;  /* stop after this many generations (de_run); >= 0 */
     int32_t debug_capture;    /* nonzero: keep indices, masks, trials, f_trial and flags of the last generation */
     int32_t fp64_band;        /* split precisions: de_fp64_band, when a selection is redone in FP64 */
+    int32_t surrogate_k;      /* 0 or 1: plain DE.  2..32: surrogate-assisted generations with this many
+                                 candidate trials per target (FP64, d == 20, one run per handle; see
+                                 de_get_surrogate_stats) */
+    int32_t surrogate_steps;  /* Adam steps per retraining of the surrogate; 0 = 100 */
 } de_config;
 
 /* When the split precisions redo a selection comparison in FP64.
@@ -168,6 +172,8 @@ typedef struct {
     double* f_trial;          /* np: fitness of each trial (FP64 when the FP64 band re-evaluated it) */
     uint8_t* accept;          /* np: 1 when the trial replaced the target */
     uint8_t* fp64_checked;    /* np: 1 when the selection was decided on FP64 fitness values */
+    int32_t* cand;            /* np: candidate stream of the evaluated trial (0 outside surrogate mode);
+                                 surrogate generations do not fill idx, jrand and mask */
 } de_debug;
 
 typedef struct de_handle de_handle;
@@ -309,6 +315,33 @@ DE_API de_status de_mlp_grad(de_mlp* m, const double* x_dev, int64_t ld, const f
  * *loss (may be NULL) receives the loss of the last minibatch. */
 DE_API de_status de_mlp_train(de_mlp* m, const double* x_dev, int64_t ld, const float* t_dev, int32_t n,
                               int32_t steps, float lr, float* loss);
+
+/* ---- surrogate-assisted generations (surrogate_k >= 2) ----------------
+ * The paper has no surrogate.  This mode serves costly objectives, which its
+ * Abstract motivates; every setting below is a choice of this library.
+ *
+ * Per generation, each target draws k candidate trials.  Candidate c uses
+ * the STEP draws with cand = c; candidate 0 is the plain DE/rand/1/bin trial
+ * of Eq. 2 / Eq. 3.  The surrogate network (de_mlp) predicts each
+ * candidate's fitness, and only the candidate with the lowest prediction is
+ * evaluated with the true objective.  Greedy selection then runs as in
+ * plain DE.  Evaluations count true evaluations only.
+ *
+ * Each evaluated trial and its f enter an archive of 200,000 rows.  The
+ * network trains on the most recent 20,000 rows: first after 5 plain
+ * generations, then every 10 generations, with surrogate_steps Adam steps on
+ * standardised log f.
+ * The network is also the judge of its own error: after each generation the
+ * Spearman correlation between its predictions and the true f of the
+ * evaluated trials is measured, and the next generation screens k
+ * candidates only when that correlation is at least 0.3.  Otherwise it
+ * draws a single candidate, which is plain DE.
+ *
+ * Each generation synchronises the stream once, for that decision.
+ * trainings, screened_generations, last_rho and k_now may each be NULL.
+ * Returns DE_ERR_STATE for a handle without a surrogate. */
+DE_API de_status de_get_surrogate_stats(de_handle* h, int64_t* trainings, int64_t* screened_generations,
+                                        double* last_rho, int32_t* k_now);
 
 /* Copy run `run`'s current population (np*d, host) and fitness (np, host)
  * out; either pointer may be NULL.  Synchronises. */

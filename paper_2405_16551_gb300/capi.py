@@ -37,7 +37,8 @@ class de_config(ctypes.Structure):
                 ("scale", ctypes.c_double), ("shift", _dp), ("rot", _dp), ("seed", ctypes.c_uint64),
                 ("run_id", ctypes.c_uint32), ("precision", ctypes.c_int32), ("target_error", ctypes.c_double),
                 ("max_evals", ctypes.c_int64), ("max_generations", ctypes.c_int64),
-                ("debug_capture", ctypes.c_int32), ("fp64_band", ctypes.c_int32)]
+                ("debug_capture", ctypes.c_int32), ("fp64_band", ctypes.c_int32), ("surrogate_k", ctypes.c_int32),
+                ("surrogate_steps", ctypes.c_int32)]
 
 
 class de_result(ctypes.Structure):
@@ -47,7 +48,7 @@ class de_result(ctypes.Structure):
 
 class de_debug(ctypes.Structure):
     _fields_ = [("idx", _i32p), ("jrand", _i32p), ("mask", _u32p), ("trial", _dp), ("f_trial", _dp),
-                ("accept", _u8p), ("fp64_checked", _u8p)]
+                ("accept", _u8p), ("fp64_checked", _u8p), ("cand", _i32p)]
 
 
 class DEError(RuntimeError):
@@ -105,6 +106,7 @@ def load(build_if_missing: bool = True):
             "de_save": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_load": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_destroy": ([H], ctypes.c_int),
+            "de_get_surrogate_stats": ([H, _i64p, _i64p, _dp, _i32p], ctypes.c_int),
             "de_mlp_create": ([ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
             "de_mlp_destroy": ([H], ctypes.c_int),
             "de_mlp_set_params": ([H, _fp], ctypes.c_int),
@@ -130,7 +132,7 @@ def exported_symbols():
             "de_eval", "de_get_population", "de_set_population", "de_set_generation", "de_get_best",
             "de_get_debug", "de_get_shape", "de_get_stats", "de_get_plan", "de_save", "de_load", "de_destroy",
             "de_eval_noalloc", "de_mlp_create", "de_mlp_destroy", "de_mlp_set_params", "de_mlp_get_params",
-            "de_mlp_forward", "de_mlp_grad", "de_mlp_train"]
+            "de_mlp_forward", "de_mlp_grad", "de_mlp_train", "de_get_surrogate_stats"]
 
 
 def _status_name(s):
@@ -157,7 +159,8 @@ def de_version() -> str:
 
 def make_config(np_, d, f=0.5, cr=0.9, lo=-100.0, hi=100.0, objective=DE_OBJ_SPHERE, scale=1.0, shift=None,
                 rot=None, seed=1, run_id=0, precision=DE_PREC_FP64, target_error=1e-8, max_evals=0,
-                max_generations=1000, debug_capture=False, fp64_band=DE_BAND_NEAR):
+                max_generations=1000, debug_capture=False, fp64_band=DE_BAND_NEAR, surrogate_k=0,
+                surrogate_steps=0):
     """A de_config; the returned object keeps the shift/rotation arrays alive."""
     c = de_config()
     c.np, c.d, c.f, c.cr, c.lo, c.hi = np_, d, f, cr, lo, hi
@@ -165,6 +168,7 @@ def make_config(np_, d, f=0.5, cr=0.9, lo=-100.0, hi=100.0, objective=DE_OBJ_SPH
     c.target_error, c.max_evals, c.max_generations = target_error, max_evals, max_generations
     c.debug_capture = 1 if debug_capture else 0
     c.fp64_band = fp64_band
+    c.surrogate_k, c.surrogate_steps = surrogate_k, surrogate_steps
     keep = []
     if shift is not None:
         s = np.ascontiguousarray(shift, dtype=np.float64)
@@ -321,11 +325,19 @@ def de_get_debug(h, run: int = 0):
     nw = (d + 31) // 32
     out = dict(idx=np.zeros((np_, 3), np.int32), jrand=np.zeros(np_, np.int32), mask=np.zeros((np_, nw), np.uint32),
                trial=np.zeros((np_, d)), f_trial=np.zeros(np_), accept=np.zeros(np_, np.uint8),
-               fp64_checked=np.zeros(np_, np.uint8))
+               fp64_checked=np.zeros(np_, np.uint8), cand=np.zeros(np_, np.int32))
     dbg = de_debug(_p(out["idx"], _i32p), _p(out["jrand"], _i32p), _p(out["mask"], _u32p), _p(out["trial"]),
-                   _p(out["f_trial"]), _p(out["accept"], _u8p), _p(out["fp64_checked"], _u8p))
+                   _p(out["f_trial"]), _p(out["accept"], _u8p), _p(out["fp64_checked"], _u8p),
+                   _p(out["cand"], _i32p))
     _check(load().de_get_debug(h, run, ctypes.byref(dbg)), h)
     return out
+
+
+def de_get_surrogate_stats(h):
+    tr, sc, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    rho = ctypes.c_double()
+    _check(load().de_get_surrogate_stats(h, ctypes.byref(tr), ctypes.byref(sc), ctypes.byref(rho), ctypes.byref(k)), h)
+    return dict(trainings=tr.value, screened_generations=sc.value, last_rho=rho.value, k_now=k.value)
 
 
 def de_get_stats(h, run: int = 0):

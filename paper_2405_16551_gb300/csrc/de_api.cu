@@ -18,6 +18,7 @@
 #include "de_device.cuh"
 #include "de_internal.cuh"
 #include "de_kernels.h"
+#include "de_surr.h"
 
 using namespace de;
 
@@ -42,6 +43,7 @@ struct de_handle {
   RunState* h_state = nullptr;  // pinned mirror of the device states
   cudaGraphExec_t graph = nullptr;
   int graph_gens = 0;
+  Surrogate* surr = nullptr;  // surrogate-assisted generations (surrogate_k >= 2)
   std::string err;
 };
 
@@ -101,6 +103,12 @@ static de_status validate(const de_config& c, int idx, std::string& why) {
   if (c.precision < DE_PREC_FP64 || c.precision > DE_PREC_TF32X3) return bad("precision out of range");
   if (c.max_evals < 0 || c.max_generations < 0) return bad("max_evals and max_generations must be >= 0");
   if (c.fp64_band != DE_BAND_NEAR && c.fp64_band != DE_BAND_ALL) return bad("fp64_band out of range");
+  if (c.surrogate_k < 0 || c.surrogate_k > 32) return bad("surrogate_k must be in [0, 32]");
+  if (c.surrogate_steps < 0 || c.surrogate_steps > 100000) return bad("surrogate_steps must be in [0, 100000]");
+  if (c.surrogate_k >= 2) {
+    if (c.precision != DE_PREC_FP64) return bad("surrogate-assisted generations run in FP64 only");
+    if (c.d != 20) return bad("the surrogate network takes d = 20");
+  }
   if (!std::isfinite(c.target_error) && !(c.target_error < 0)) return bad("target_error must be finite");
   if (c.shift)
     for (int j = 0; j < c.d; ++j)
@@ -166,7 +174,20 @@ static de_status launch_generation(de_handle* h, cudaStream_t s) {
 }
 static de_status launch_generation(de_handle* h) { return launch_generation(h, h->stream); }
 
+static de_status read_states(de_handle* h);
+
 static de_status enqueue_generations(de_handle* h, int64_t n) {
+  if (h->surr) {
+    // host-driven: each generation ends with the surrogate's screening decision
+    for (int64_t k = 0; k < n; ++k) {
+      de_status s = read_states(h);
+      if (s != DE_OK) return s;
+      if (h->h_state[0].stop) break;
+      s = surr_generation(*h->surr, h->d_run, h->run[0], h->stream, h->err);
+      if (s != DE_OK) return fail(h, s, h->err);
+    }
+    return DE_OK;
+  }
   if (h->prec != DE_PREC_FP64 && h->tc.persist.ok) {
     // one persistent launch runs all n generations (or stops early)
     if (n > 0) DE_CUDA(h, persist_launch(h->tc.persist, h->d_run, h->tc.d_ctl, n, h->stream));
@@ -411,6 +432,7 @@ de_status de_destroy(de_handle* h) {
   if (!h) return DE_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graph(h);
+  surr_destroy(h->surr);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   tc_plan_free(h->tc);
   if (h->d_items) cudaFree(h->d_items);
@@ -430,6 +452,8 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     if (validate(cfgs[r], r, why) != DE_OK) return fail(nullptr, DE_ERR_INVALID_ARG, why);
     if (cfgs[r].precision != cfgs[0].precision)
       return fail(nullptr, DE_ERR_INVALID_ARG, "all runs of a batch must share the precision");
+    if (cfgs[r].surrogate_k >= 2 && nruns != 1)
+      return fail(nullptr, DE_ERR_INVALID_ARG, "surrogate-assisted generations take one run per handle");
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -462,7 +486,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
   };
   struct Offs {
     size_t X0, X1, f0, f1, fx0, fx1, o, MT, Mr, st, part, T, ref;
-    size_t dbg_idx, dbg_jrand, dbg_mask, dbg_trial, dbg_ftrial, dbg_accept, dbg_fp64;
+    size_t dbg_idx, dbg_jrand, dbg_mask, dbg_trial, dbg_ftrial, dbg_accept, dbg_fp64, dbg_cand;
   };
   std::vector<Offs> offs(nruns);
   const size_t states_off = take((size_t)nruns * sizeof(RunState));  // one contiguous block
@@ -494,6 +518,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
       O.dbg_ftrial = take((size_t)c.np * sizeof(double));
       O.dbg_accept = take((size_t)c.np);
       O.dbg_fp64 = take((size_t)c.np);
+      O.dbg_cand = take((size_t)c.np * sizeof(int32_t));
     }
   }
   h->arena_bytes = align_up(off, 256);
@@ -577,6 +602,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
       R.dbg_ftrial = (double*)(A + O.dbg_ftrial);
       R.dbg_accept = (uint8_t*)(A + O.dbg_accept);
       R.dbg_fp64 = (uint8_t*)(A + O.dbg_fp64);
+      R.dbg_cand = (int32_t*)(A + O.dbg_cand);
     }
     if (c.shift) {
       ce = cudaMemcpyAsync((void*)R.o, c.shift, c.d * sizeof(double), cudaMemcpyHostToDevice, h->stream);
@@ -612,12 +638,17 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
   TRY(upload_desc(h));
   k_configure(h->smem_gen);
   for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
-  if (h->prec == DE_PREC_FP64) {
+  if (h->prec == DE_PREC_FP64 && cfgs[0].surrogate_k < 2) {
     TRY(autotune_fp64(h, prop.multiProcessorCount));
     TRY(build_items(h));
     TRY(upload_desc(h));
     k_configure(h->smem_gen);
     for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
+  }
+  if (cfgs[0].surrogate_k >= 2) {
+    const de_status ss = surr_create(h->surr, cfgs[0].surrogate_k, cfgs[0].surrogate_steps,
+                                     cfgs[0].seed ^ ((uint64_t)cfgs[0].run_id << 32), h->run[0], h->stream, h->err);
+    if (ss != DE_OK) return fin(fail(h, ss, h->err));
   }
   ce = cudaStreamSynchronize(h->stream);
   if (ce != cudaSuccess) return fin(fail(h, DE_ERR_CUDA, std::string("init: ") + cudaGetErrorString(ce)));
@@ -637,6 +668,10 @@ de_status de_reset(de_handle* h, int32_t run) {
   for (int r = (run < 0 ? 0 : run); r < (run < 0 ? h->nruns : run + 1); ++r) {
     de_status s = init_run(h, r);
     if (s != DE_OK) return s;
+  }
+  if (h->surr) {
+    const de_status s = surr_reset(*h->surr, h->stream, h->err);
+    if (s != DE_OK) return fail(h, s, h->err);
   }
   return DE_OK;
 }
@@ -832,7 +867,19 @@ de_status de_get_debug(de_handle* h, int32_t run, const de_debug* out) {
   DE_CUDA(h, cp(out->f_trial, R.dbg_ftrial, (size_t)R.np * sizeof(double)));
   DE_CUDA(h, cp(out->accept, R.dbg_accept, (size_t)R.np));
   DE_CUDA(h, cp(out->fp64_checked, R.dbg_fp64, (size_t)R.np));
+  DE_CUDA(h, cp(out->cand, R.dbg_cand, (size_t)R.np * sizeof(int32_t)));
   DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DE_OK;
+}
+
+de_status de_get_surrogate_stats(de_handle* h, int64_t* trainings, int64_t* screened_generations, double* last_rho,
+                                 int32_t* k_now) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->surr) return fail(h, DE_ERR_STATE, "the handle has no surrogate (surrogate_k < 2)");
+  if (trainings) *trainings = h->surr->trainings;
+  if (screened_generations) *screened_generations = h->surr->screened;
+  if (last_rho) *last_rho = h->surr->last_rho;
+  if (k_now) *k_now = h->surr->k_eff;
   return DE_OK;
 }
 
@@ -881,6 +928,7 @@ struct CkptHeader {
 de_status de_save(de_handle* h, const char* path) {
   if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
   if (!path) return fail(h, DE_ERR_INVALID_ARG, "path is NULL");
+  if (h->surr) return fail(h, DE_ERR_UNSUPPORTED, "checkpoints do not cover the surrogate's archive and network");
   de_status s = read_states(h);
   if (s != DE_OK) return s;
   std::vector<char> payload;
@@ -926,6 +974,7 @@ de_status de_save(de_handle* h, const char* path) {
 de_status de_load(de_handle* h, const char* path) {
   if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
   if (!path) return fail(h, DE_ERR_INVALID_ARG, "path is NULL");
+  if (h->surr) return fail(h, DE_ERR_UNSUPPORTED, "checkpoints do not cover the surrogate's archive and network");
   FILE* fp = fopen(path, "rb");
   if (!fp) return fail(h, DE_ERR_IO, std::string("cannot open ") + path);
   CkptHeader hd{};

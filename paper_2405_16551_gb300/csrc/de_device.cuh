@@ -346,12 +346,15 @@ struct TrialSetup {
 };
 
 // Draws 0..3 of the STEP stream: mutant indices (Eq. 2) and j_rand (Eq. 3).
-__device__ __forceinline__ TrialSetup trial_setup(const RunDesc& R, uint32_t i, int64_t g, int lane) {
-  const U32x4 b0 = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, i, 0u);
+// cand selects the candidate stream (0: plain DE; 1, 2, ...: the extra
+// candidate trials a surrogate screens); record = false skips the debug copy.
+__device__ __forceinline__ TrialSetup trial_setup(const RunDesc& R, uint32_t i, int64_t g, int lane,
+                                                  uint32_t cand = 0u, bool record = true) {
+  const U32x4 b0 = draw_block(R.seed, kPurposeStep, R.run_id, cand, (uint32_t)g, i, 0u);
   TrialSetup s;
   mutant_indices(b0.x, b0.y, b0.z, i, (uint32_t)R.np, s.r1, s.r2, s.r3);
   s.jr = map_to_range(b0.w, (uint32_t)R.d);
-  if (R.dbg_idx && lane == 0) {
+  if (record && R.dbg_idx && lane == 0) {
     R.dbg_idx[3 * i + 0] = (int32_t)s.r1;
     R.dbg_idx[3 * i + 1] = (int32_t)s.r2;
     R.dbg_idx[3 * i + 2] = (int32_t)s.r3;
@@ -369,8 +372,8 @@ struct ChunkIn {
 
 // Issue the loads of chunk j0 (j0 < d, j0 % 4 == 0) and draw its block.
 __device__ __forceinline__ void trial_load(const RunDesc& R, const double* __restrict__ X, const TrialSetup& s,
-                                           uint32_t i, int64_t g, int j0, ChunkIn& c) {
-  c.u = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, i, 1u + (uint32_t)(j0 >> 2));
+                                           uint32_t i, int64_t g, int j0, ChunkIn& c, uint32_t cand = 0u) {
+  c.u = draw_block(R.seed, kPurposeStep, R.run_id, cand, (uint32_t)g, i, 1u + (uint32_t)(j0 >> 2));
   const double* rows[4] = {X + (size_t)i * R.dp + j0, X + (size_t)s.r1 * R.dp + j0, X + (size_t)s.r2 * R.dp + j0,
                            X + (size_t)s.r3 * R.dp + j0};
   double* dst[4] = {c.xi, c.x1, c.x2, c.x3};
@@ -414,9 +417,9 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
 // Coordinates j0 .. j0+3 (j0 < d, j0 % 4 == 0) of the trial; entries at
 // j >= d are 0.  Returns the crossed-coordinate bits (bit m for j0 + m).
 __device__ __forceinline__ uint32_t trial_chunk(const RunDesc& R, const double* __restrict__ X, const TrialSetup& s,
-                                                uint32_t i, int64_t g, int j0, double t[4]) {
+                                                uint32_t i, int64_t g, int j0, double t[4], uint32_t cand = 0u) {
   ChunkIn c;
-  trial_load(R, X, s, i, g, j0, c);
+  trial_load(R, X, s, i, g, j0, c, cand);
   return trial_compute(R, s, j0, c, t);
 }
 

@@ -110,6 +110,7 @@ struct RunDesc {
   double* dbg_ftrial;
   uint8_t* dbg_accept;
   uint8_t* dbg_fp64;
+  int32_t* dbg_cand;  // candidate stream of the evaluated trial (surrogate generations)
 };
 
 }  // namespace de

@@ -658,6 +658,12 @@ de_status mlp_create(uint64_t seed, cudaStream_t stream, de_mlp** out) {
   return DE_OK;
 }
 
+de_status mlp_reset(de_mlp* m) {
+  std::vector<float> p(kMlpParams);
+  mlp_init_params(m->seed, p.data());
+  return mlp_upload(m, p.data());
+}
+
 void mlp_destroy(de_mlp* m) {
   if (!m) return;
   if (m->stream) cudaStreamSynchronize(m->stream);
