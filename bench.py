@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
+    p.add_argument("--workload", default="rastrigin", choices=["rastrigin", "batch512", "ode_surrogate", "stress"],
+                   help="rastrigin: the headline configuration (default); the others measure the batched, "
+                        "surrogate and large-dimension configurations with the same harness")
     return p.parse_args()
 
 
@@ -242,6 +245,11 @@ def main():
     from paper_2405_16551_gb300 import capi
 
     torch.cuda.set_device(local)
+    if args.workload != "rastrigin":
+        line = run_workload(args, capi, torch, rank, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -366,6 +374,112 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- other workloads
+def _timed(torch, stream, flush, steps, warmup, fn):
+    """Device time (ms) of `steps` calls of fn, after `warmup` calls; L2 flushed
+    between calls outside the events."""
+    for _ in range(warmup):
+        fn()
+        flush.zero_()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    return sum(e0.elapsed_time(e1) for e0, e1 in evs)
+
+
+def run_workload(args, capi, torch, rank, world):
+    """The batched (512 uneven runs), surrogate (ODE, k = 8) and stress
+    (NP = 8192, D = 1000) configurations; one JSON line each."""
+    from paper_2405_16551_gb300 import problems
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    steps, warmup = args.steps, args.warmup
+    line = {"n_gpus": world, "steps": steps, "warmup": warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic", "unit": "trial evals/s"}
+    if args.workload == "batch512":
+        G = min(args.generations, 200)
+        shapes = problems.batch_shapes(512, seed=1)
+        forms = {}
+        for name in ("bf16x3", "fp64"):
+            cfgs = []
+            for r, (n, d, obj) in enumerate(shapes):
+                cfgs.append(capi.make_config(n, d, objective=obj, shift=problems.shift(d, seed=1, run_id=r),
+                                             rot=problems.rotation(d, seed=1, run_id=r), seed=1, run_id=r,
+                                             precision=PREC_NAMES[name], target_error=0.0, max_generations=G))
+            h = capi.de_init_batch(cfgs, stream=stream.cuda_stream)
+            ms = _timed(torch, stream, flush, steps, warmup, lambda: (capi.de_reset(h, -1), capi.de_step(h, G)))
+            capi.de_destroy(h)
+            tot = sum(n for n, _, _ in shapes) * G * steps
+            forms[name] = {"trial_evals_per_s": tot / (ms / 1e3), "ms_per_step": ms / steps}
+        # the same runs one handle at a time in plain FP64 (first 16 runs, scaled by their share of the trials)
+        ms_seq, tr_seq = 0.0, 0
+        for r, (n, d, obj) in enumerate(shapes[:16]):
+            c = capi.make_config(n, d, objective=obj, shift=problems.shift(d, seed=1, run_id=r),
+                                 rot=problems.rotation(d, seed=1, run_id=r), seed=1, run_id=r, target_error=0.0,
+                                 max_generations=G)
+            h = capi.de_init(c, stream=stream.cuda_stream)
+            ms_seq += _timed(torch, stream, flush, 1, 1, lambda: (capi.de_reset(h), capi.de_step(h, G)))
+            tr_seq += n * G
+            capi.de_destroy(h)
+        forms["fp64_one_run_at_a_time"] = {"trial_evals_per_s": tr_seq / (ms_seq / 1e3)}
+        for k in forms:
+            forms[k]["speedup_vs_fp64_one_run_at_a_time"] = (forms[k]["trial_evals_per_s"]
+                                                             / forms["fp64_one_run_at_a_time"]["trial_evals_per_s"])
+        line.update(metric="trial evals/sec, 512 independent runs (D in {10,30,50,100}, NP in 50..1000, 4 objectives)",
+                    value=forms["bf16x3"]["trial_evals_per_s"], ms_per_step=forms["bf16x3"]["ms_per_step"],
+                    dtype="bf16x3 products, f32 accumulate, f64 trials and selection band",
+                    config={"workload": f"512-run batch, {G} generations per step, one handle, CUDA graphs",
+                            "l2": "flushed between steps (512 MiB write)"},
+                    forms=forms, gpu_launches=steps * (3 * 512 + 3 * G))
+    elif args.workload == "ode_surrogate":
+        # time and true evaluations to reach f < 1e-8, plain DE vs 8 screened candidates
+        res = {}
+        for k in (0, 8):
+            runs = []
+            for seed in (1, 2, 3):
+                c = capi.make_config(256, 20, objective=4, shift=problems.ode_hidden(seed), seed=seed,
+                                     max_evals=200000, max_generations=10**6, target_error=1e-8, surrogate_k=k)
+                h = capi.de_init(c, stream=stream.cuda_stream)
+                t0 = time.perf_counter()
+                r = capi.de_run(h)[0]
+                runs.append({"seconds": time.perf_counter() - t0, "true_evals": r["evals"],
+                             "generations": r["generations"], "best_f": r["best_f"], "stop": r["stop_reason"]})
+                capi.de_destroy(h)
+            res["plain" if k == 0 else "surrogate_k8"] = runs
+        ev = sum(r["true_evals"] for r in res["plain"])
+        tm = sum(r["seconds"] for r in res["plain"])
+        line.update(metric="true evaluations/sec to f < 1e-8, ODE fit (D=20, NP=256, RK4 2000 steps FP64)",
+                    value=ev / tm, ms_per_step=1e3 * tm / 3, dtype="f64 objective, bf16 surrogate",
+                    config={"workload": "ODE fit, 3 seeds, plain DE and surrogate k = 8, budget 2e5 true evaluations"},
+                    runs=res, gpu_launches=None)
+    else:  # stress
+        G = min(args.generations, 100)
+        n, d = 8192, 1000
+        c = capi.make_config(n, d, objective=1, shift=problems.shift(d, seed=1), rot=problems.rotation(d, seed=1),
+                             seed=1, precision=PREC_NAMES["bf16x3"], target_error=1e-8, max_generations=G)
+        h = capi.de_init(c, stream=stream.cuda_stream)
+        ms = _timed(torch, stream, flush, steps, warmup, lambda: (capi.de_reset(h), capi.de_step(h, G)))
+        plan = capi.de_get_plan(h)
+        capi.de_destroy(h)
+        value = n * G * steps / (ms / 1e3)
+        flops = 3 * 2.0 * n * d * d * G * steps
+        line.update(metric="trial evals/sec, NP=8192 D=1000 rotated-shifted Rastrigin, BF16x3",
+                    value=value, ms_per_step=ms / steps, dtype="bf16x3 products, f32 accumulate",
+                    config={"workload": f"NP=8192 D=1000, {G} generations per step", "kernel_path": plan["kernel_path"],
+                            "l2": "flushed between steps (512 MiB write)"},
+                    tensor_tflops=flops / (ms / 1e3) / 1e12, gpu_launches=steps * (3 + 3 * G))
+    line["clocks"] = clocks.stop()
+    return line
 
 
 # DRAM traffic of one launch of the dominant kernel, from an ncu capture

@@ -49,9 +49,11 @@ def _need_gpu():
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("obj", [0, 1, 2, 3])
-@pytest.mark.parametrize("d", [10, 100, 130])
+@pytest.mark.parametrize("d", [10, 100, 130, 300, 1000])
 def test_split_eval_within_tolerance(prec, obj, d):
     torch = _need_gpu()
+    if obj == 2 and d > 256:
+        pytest.skip("split precision takes Rosenbrock up to d = 256")
     o = problems.shift(d, seed=2)
     M = problems.rotation(d, seed=2)
     X = problems.population(700, d, seed=3)
@@ -76,7 +78,9 @@ def test_split_eval_within_tolerance(prec, obj, d):
 @pytest.mark.parametrize(
     "np_,d,obj,F,CR",
     [(1024, 100, 1, 0.5, 0.9), (64, 10, 0, 0.5, 0.9), (300, 37, 2, 0.8, 0.3), (130, 64, 3, 0.5, 1.0),
-     (4, 1, 1, 0.5, 0.9)],
+     (4, 1, 1, 0.5, 0.9),
+     (256, 1000, 1, 0.5, 0.9),   # the large-dimension workload's D: four N tiles, K staged in chunks
+     (130, 300, 3, 0.5, 0.9)],   # two N tiles, the second ragged
 )
 def test_split_generation_matches_oracle(prec, np_, d, obj, F, CR, split_path, band):
     _need_gpu()
