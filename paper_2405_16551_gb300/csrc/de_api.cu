@@ -406,6 +406,78 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
   return DE_OK;
 }
 
+// Split precisions, three-kernel path: targets per trial CTA and the K chunk
+// of the fitness kernel, timed on the handle's own problem and cached like
+// the FP64 choice (neither changes results).  The persistent cluster kernel
+// takes its geometry from occupancy and is not tuned here.
+static std::string tune_key_split(const de_handle* h) {
+  long long sum_np = 0, sum_d = 0;
+  for (auto& R : h->run) {
+    sum_np += R.np;
+    sum_d += (long long)R.np * R.d;
+  }
+  char b[256];
+  snprintf(b, sizeof b, "split_v1 prec=%d runs=%d np0=%d d0=%d obj0=%d sumnp=%lld sumnd=%lld", h->prec, h->nruns,
+           h->run[0].np, h->run[0].d, h->run[0].obj, sum_np, sum_d);
+  return b;
+}
+
+static de_status autotune_split(de_handle* h) {
+  const char* env = getenv("DE_GB300_AUTOTUNE");
+  if ((env && env[0] == '0') || h->tc.persist.ok) return DE_OK;
+  const std::string key = tune_key_split(h);
+  int code = 0;
+  if (tune_lookup(key, code)) {
+    de_status s = tc_set_geometry(h->tc, h->run, code / 10, code % 10, h->stream, h->err);
+    if (s == DE_OK) s = upload_desc(h);
+    return s;
+  }
+  cudaEvent_t e0, e1;
+  DE_CUDA(h, cudaEventCreate(&e0));
+  DE_CUDA(h, cudaEventCreate(&e1));
+  std::vector<RunDesc> saved = h->run;
+  for (auto& R : h->run) {
+    R.target = 0.0;  // no stop rule while timing
+    R.max_evals = 0;
+    R.max_gens = INT64_MAX / 4;
+  }
+  float best_ms = 1e30f;
+  int best = 0;
+  de_status st_all = DE_OK;
+  for (int tr : {2, 4, 8}) {
+    for (int kd : {1, 2, 4}) {
+      st_all = tc_set_geometry(h->tc, h->run, tr, kd, h->stream, h->err);
+      if (st_all == DE_OK) st_all = upload_desc(h);
+      if (st_all != DE_OK) break;
+      for (int r = 0; r < h->nruns; ++r) {
+        int32_t zero = 0;
+        DE_CUDA(h, cudaMemcpyAsync(&h->run[r].st->stop, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream));
+      }
+      launch_generation(h);
+      DE_CUDA(h, cudaEventRecord(e0, h->stream));
+      for (int k = 0; k < 3; ++k) launch_generation(h);
+      DE_CUDA(h, cudaEventRecord(e1, h->stream));
+      DE_CUDA(h, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      DE_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms * 0.97f) {
+        best_ms = ms;
+        best = tr * 10 + kd;
+      }
+    }
+    if (st_all != DE_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (size_t r = 0; r < saved.size(); ++r) saved[r].kc = h->run[r].kc;
+  h->run = saved;
+  if (st_all != DE_OK) return st_all;
+  de_status s = tc_set_geometry(h->tc, h->run, best / 10, best % 10, h->stream, h->err);
+  if (s == DE_OK) s = upload_desc(h);
+  if (s == DE_OK) tune_store(key, best);
+  return s;
+}
+
 // ---------------------------------------------------------------- C ABI
 extern "C" {
 
@@ -643,6 +715,9 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     TRY(build_items(h));
     TRY(upload_desc(h));
     k_configure(h->smem_gen);
+    for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
+  } else if (h->prec != DE_PREC_FP64 && !h->tc.persist.ok) {
+    TRY(autotune_split(h));
     for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
   }
   if (cfgs[0].surrogate_k >= 2) {

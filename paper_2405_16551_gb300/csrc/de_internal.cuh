@@ -102,6 +102,8 @@ struct RunDesc {
   float band_u;       // unit error of one split product sum, relative to sum_k |M_jk y_k|
   int32_t band_all;   // 1: every undecidable comparison and every possible new best go to FP64
   float near_thr;     // fitness below which an undecidable comparison goes to FP64
+  float* npart;       // several N tiles: per tile, N tile and row the 5 partial epilogue sums
+  uint32_t* nticket;  // several N tiles: CTAs of each row tile that have written their partial sums
   // debug capture (all NULL unless enabled)
   int32_t* dbg_idx;
   int32_t* dbg_jrand;

@@ -50,6 +50,7 @@ struct TcPlan {
   size_t smem_band = 0;
   int grid_band = 0;
   int trial_rows = 8;          // targets (warps) per trial CTA
+  int nsplit = 1;              // N tiles spread over CTAs of the fitness kernel (the largest N-tile count)
   int nruns = 0;
   PersistPlan persist;         // the persistent cluster kernel, when it applies
   PersistCtl* d_ctl = nullptr;
@@ -61,6 +62,10 @@ cudaError_t persist_launch(const PersistPlan& pp, const RunDesc* runs, PersistCt
 de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* cfgs, int prec, cudaStream_t s,
                         std::string& err);
 void tc_plan_free(TcPlan& p);
+// Launch geometry that leaves the results unchanged (autotuner): targets per
+// trial CTA and a divisor of the fitness kernel's default K chunk.
+de_status tc_set_geometry(TcPlan& p, std::vector<RunDesc>& runs, int trial_rows, int kc_div, cudaStream_t s,
+                          std::string& err);
 void tc_generation_launch(const TcPlan& p, const RunDesc* runs, cudaStream_t s);
 de_status tc_eval_launch(const TcPlan& p, const RunDesc* runs, int run, const RunDesc& R, const double* x, int64_t ld,
                          int n, double* f, cudaStream_t s, std::string& err);

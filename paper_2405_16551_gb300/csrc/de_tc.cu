@@ -89,12 +89,16 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
   float yn2 = 0.f;
   const bool dbg = R.dbg_trial != nullptr;
   const int nchunks = (R.kpad + 127) / 128;
+  // the loads of chunk c + 1 are issued before chunk c is computed
+  ChunkIn cur, nxt;
+  if (4 * lane < R.d) trial_load(R, X, s, (uint32_t)i, g, 4 * lane, cur);
   for (int c = 0; c < nchunks; ++c) {
     const int j0 = 128 * c + 4 * lane;
+    if (c + 1 < nchunks && j0 + 128 < R.d) trial_load(R, X, s, (uint32_t)i, g, j0 + 128, nxt);
     double t[4] = {0.0, 0.0, 0.0, 0.0};
     uint32_t bits = 0;
     if (j0 < R.d) {
-      bits = trial_chunk(R, X, s, (uint32_t)i, g, j0, t);
+      bits = trial_compute(R, s, j0, cur, t);
       double* Trow = R.T + (size_t)i * R.dp + j0;
       *reinterpret_cast<double2*>(Trow) = make_double2(t[0], t[1]);
       *reinterpret_cast<double2*>(Trow + 2) = make_double2(t[2], t[3]);
@@ -109,6 +113,7 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
       store_split4<ESZ>(Ahi, a_part, m, j0, y);
     }
     if (dbg) trial_debug(R, (uint32_t)i, j0, lane, bits, t);
+    cur = nxt;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) yn2 += __shfl_xor_sync(0xffffffffu, yn2, o);
@@ -166,6 +171,11 @@ __global__ void __launch_bounds__(kFitThreads, 1)
 
   const int2 it = items[blockIdx.x];
   const RunDesc& R = runs[it.x];  // run descriptors are written once, at set-up
+  // several N tiles: with gridDim.y > 1, CTA (tile, y) computes N tile y only
+  // and the tile's last CTA combines the per-row partial sums in N-tile order
+  if ((int)blockIdx.y >= R.nn) return;  // the grid covers the largest N-tile count of the batch
+  const bool split = gridDim.y > 1 && R.nn > 1;
+  const int nt_lo = split ? (int)blockIdx.y : 0, nt_hi = split ? nt_lo + 1 : R.nn;
   RunState* st = R.st;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pdl_launch_dependents();
@@ -195,7 +205,7 @@ __global__ void __launch_bounds__(kFitThreads, 1)
   // ---- geometry of the K pipeline
   const int kc = R.kc;
   const int nkc = (R.kpad + kc - 1) / kc;
-  const int nseq = R.nn * nkc;
+  const int nseq = (nt_hi - nt_lo) * nkc;
   const uint32_t a_part = (uint32_t)(R.a_tile_bytes / 2);
   const uint32_t b_part = (uint32_t)(R.b_tile_bytes / 2);
   const uint32_t kg_chunk = (uint32_t)(kc * ESZ / 16);  // k-groups per full chunk
@@ -212,7 +222,7 @@ __global__ void __launch_bounds__(kFitThreads, 1)
   auto chunk_len = [&](int kci) { return min(kc, R.kpad - kci * kc); };
   // B half of stage load q (counts the bytes of both halves on the barrier)
   auto issue_load_b = [&](int q) {
-    const int nt = q / nkc, kci = q % nkc, sg = q & 1;
+    const int nt = nt_lo + q / nkc, kci = q % nkc, sg = q & 1;
     const uint32_t kgs = (uint32_t)(chunk_len(kci) * ESZ / 16);
     const uint32_t ab = kgs * 16u * 128u, bb = kgs * bk;
     const uint32_t base = sbase + (uint32_t)sg * stage_bytes;
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(kFitThreads, 1)
 
   int loads_issued = npro, mmas_committed = 0;
   int q = 0;
-  for (int nt = 0; nt < R.nn; ++nt) {
+  for (int nt = nt_lo; nt < nt_hi; ++nt) {
     if (tid == 0 && !s_err) {
       bool ok = true;
       for (int kci = 0; kci < nkc; ++kci, ++q) {
@@ -317,7 +327,7 @@ __global__ void __launch_bounds__(kFitThreads, 1)
     __syncthreads();
     bool have = false;
     if (!s_err) {
-      have = mbar_wait(b_acc, (uint32_t)(nt & 1));
+      have = mbar_wait(b_acc, (uint32_t)((nt - nt_lo) & 1));
       if (!have) atomicOr(&s_err, 1);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -376,9 +386,51 @@ __global__ void __launch_bounds__(kFitThreads, 1)
     s_part[4][m] = acc_.aG;
   }
   __syncthreads();
+  float t1 = 0.f, t2 = 0.f, t3 = 0.f, tS = 0.f, tG = 0.f;
+  if (h == 0) {
+    t1 = acc_.a1 + s_part[0][m];
+    t2 = acc_.a2 + s_part[1][m];
+    t3 = acc_.a3 + s_part[2][m];
+    tS = acc_.aS + s_part[3][m];
+    tG = acc_.aG + s_part[4][m];
+  }
+  if (split) {
+    // partial sums of this N tile -> global; the tile's last CTA adds them up
+    // in N-tile order (the same order whichever CTA finishes last)
+    const size_t pstride = (size_t)5 * kTileM;
+    float* P = R.npart + ((size_t)it.y * R.nn + nt_lo) * pstride;
+    if (h == 0) {
+      P[0 * kTileM + m] = t1;
+      P[1 * kTileM + m] = t2;
+      P[2 * kTileM + m] = t3;
+      P[3 * kTileM + m] = tS;
+      P[4 * kTileM + m] = tG;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t tk = atomicAdd(&R.nticket[it.y], 1u);
+      s_last = (tk == (uint32_t)R.nn - 1u);
+      if (s_last) R.nticket[it.y] = 0u;  // every CTA of this tile has counted itself
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (h == 0) {
+      const float* Q = R.npart + (size_t)it.y * R.nn * pstride;
+      t1 = t2 = t3 = tS = tG = 0.f;
+      for (int k = 0; k < R.nn; ++k, Q += pstride) {
+        t1 += __ldcg(Q + 0 * kTileM + m);
+        t2 += __ldcg(Q + 1 * kTileM + m);
+        t3 += __ldcg(Q + 2 * kTileM + m);
+        tS += __ldcg(Q + 3 * kTileM + m);
+        tG += __ldcg(Q + 4 * kTileM + m);
+      }
+    }
+  }
   if (h == 0 && m < nrows) {
-    const float s1 = acc_.a1 + s_part[0][m], s2 = acc_.a2 + s_part[1][m], s3 = acc_.a3 + s_part[2][m];
-    float S = acc_.aS + s_part[3][m], G = acc_.aG + s_part[4][m];
+    const float s1 = t1, s2 = t2, s3 = t3;
+    float S = tS, G = tG;
     float fs;
     if (obj == kObjAckley) {
       const float r = sqrtf(s1 / (float)d);
@@ -679,6 +731,26 @@ static float host_tf32_rna(float x) {
   return f;
 }
 
+// K chunk of the fitness kernel's pipeline: the whole K in one stage when it
+// fits, else two stages of at most kStageBudget; divided by kc_div (an
+// autotuner choice that leaves the product order, hence the results, alone).
+static int plan_kc(const RunDesc& R, int esz, int kc_div) {
+  int kc;
+  if (kc_div == 1 && (size_t)2 * (kTileM + R.ntn) * R.kpad * esz <= kSingleStageMax) {
+    kc = R.kpad;
+  } else {
+    kc = (int)(kStageBudget / (2 * (kTileM + R.ntn) * esz)) / 16 * 16;
+    kc = std::max(16, std::min(kc, R.kpad));
+    kc = std::max(16, kc / kc_div / 16 * 16);
+  }
+  return kc;
+}
+
+static size_t plan_smem(const RunDesc& R, int esz) {
+  const size_t stage = 2 * (size_t)(R.kc * esz / 16) * 16 * 128 + 2 * (size_t)(R.kc * esz / 16) * (R.ntn / 8) * 128;
+  return (R.kc < R.kpad || R.nn > 1 ? 2 : 1) * stage;
+}
+
 // B operand: N tiles of M's rows (n = output coordinate), each tile two
 // parts (high, low) in the canonical K-major layout with ntn / 8 row groups.
 static void pack_b(const de_config& c, const RunDesc& R, std::vector<uint8_t>& out) {
@@ -713,6 +785,8 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
   const int esz = prec == DE_PREC_BF16X3 ? 2 : 4;
   size_t bytes = 0;
   std::vector<size_t> offA(runs.size()), offB(runs.size()), offY(runs.size()), offT(runs.size()), offS(runs.size());
+  std::vector<size_t> offP(runs.size(), 0), offK(runs.size(), 0);
+  p.nsplit = 1;
   std::vector<int2> trial_items, fit_items;
   size_t smem = 0;
   p.fit_offset.assign(runs.size(), 0);
@@ -727,15 +801,7 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
       err = "split precision supports Rosenbrock only for d <= 256";
       return DE_ERR_UNSUPPORTED;
     }
-    // whole K in one stage when it fits, else two stages of at most kStageBudget
-    int kc;
-    if ((size_t)2 * (kTileM + R.ntn) * R.kpad * esz <= kSingleStageMax) {
-      kc = R.kpad;
-    } else {
-      kc = (int)(kStageBudget / (2 * (kTileM + R.ntn) * esz)) / 16 * 16;
-      kc = std::max(16, std::min(kc, R.kpad));
-    }
-    R.kc = kc;
+    R.kc = plan_kc(R, esz, 1);
     R.ntiles_tc = (R.np + kTileM - 1) / kTileM;
     R.a_tile_bytes = 2 * kTileM * R.kpad * esz;
     R.b_tile_bytes = 2 * R.ntn * R.kpad * esz;
@@ -749,8 +815,7 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
     // near the optimum: where the split bound (about 4 u f) reaches an eighth
     // of the target, comparisons are redone in FP64
     R.near_thr = R.target > 0.0 ? (float)(R.target / (8.0 * R.band_u)) : 0.f;
-    const size_t stage = 2 * (size_t)(kc * esz / 16) * 16 * 128 + 2 * (size_t)(kc * esz / 16) * (R.ntn / 8) * 128;
-    smem = std::max(smem, (kc < R.kpad || R.nn > 1 ? 2 : 1) * stage);
+    smem = std::max(smem, plan_smem(R, esz));
     bytes = round_up(bytes, 1024);
     offA[r] = bytes;
     bytes += (size_t)R.ntiles_tc * R.a_tile_bytes;
@@ -766,6 +831,16 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
     bytes = round_up(bytes, 256);
     offS[r] = bytes;
     bytes += 2 * sizeof(unsigned long long);
+    if (R.nn > 1) {
+      // per-row partial sums of each N tile and the per-tile tickets
+      bytes = round_up(bytes, 256);
+      offP[r] = bytes;
+      bytes += (size_t)R.ntiles_tc * R.nn * 5 * kTileM * sizeof(float);
+      bytes = round_up(bytes, 256);
+      offK[r] = bytes;
+      bytes += (size_t)R.ntiles_tc * sizeof(uint32_t);
+      p.nsplit = std::max(p.nsplit, R.nn);
+    }
 
     p.fit_offset[r] = (int)fit_items.size();
     for (int t = 0; t < R.ntiles_tc; ++t) fit_items.push_back(make_int2((int)r, t));
@@ -826,6 +901,8 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
     R.ynorm = (float*)(base + offY[r]);
     R.tau = (float*)(base + offT[r]);
     R.stats = (unsigned long long*)(base + offS[r]);
+    R.npart = R.nn > 1 ? (float*)(base + offP[r]) : nullptr;
+    R.nticket = R.nn > 1 ? (uint32_t*)(base + offK[r]) : nullptr;
     R.band = (BandEntry*)(base + off_band);
     R.band_cnt = (uint32_t*)(base + off_bcnt);
     R.band_part = (double2*)(base + off_bpart);
@@ -869,6 +946,40 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
   return DE_OK;
 }
 
+de_status tc_set_geometry(TcPlan& p, std::vector<RunDesc>& runs, int trial_rows, int kc_div, cudaStream_t s,
+                          std::string& err) {
+  const int esz = p.prec == DE_PREC_BF16X3 ? 2 : 4;
+  size_t smem = 0;
+  for (auto& R : runs) {
+    R.kc = plan_kc(R, esz, kc_div);
+    smem = std::max(smem, plan_smem(R, esz));
+  }
+  std::vector<int2> items;
+  for (size_t r = 0; r < runs.size(); ++r)
+    for (int gI = 0; gI < (runs[r].np + trial_rows - 1) / trial_rows; ++gI) items.push_back(make_int2((int)r, gI));
+  cudaError_t e = cudaSuccess;
+  if (items.size() != (size_t)p.nitems_trial) {
+    if (p.d_trial_items) cudaFree(p.d_trial_items);
+    p.d_trial_items = nullptr;
+    e = cudaMalloc(&p.d_trial_items, items.size() * sizeof(int2));
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p.d_trial_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    e = esz == 2 ? cudaFuncSetAttribute(k_fit_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                 : cudaFuncSetAttribute(k_fit_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  if (e != cudaSuccess) {
+    err = std::string("split-precision geometry: ") + cudaGetErrorString(e);
+    return DE_ERR_CUDA;
+  }
+  p.nitems_trial = (int)items.size();
+  p.trial_rows = trial_rows;
+  p.smem_fit = smem;
+  return DE_OK;
+}
+
 void tc_plan_free(TcPlan& p) {
   if (p.arena) cudaFree(p.arena);
   if (p.d_trial_items) cudaFree(p.d_trial_items);
@@ -881,10 +992,10 @@ void tc_plan_free(TcPlan& p) {
 // Launch with programmatic stream serialization: the kernel may begin while
 // its predecessor on the stream finishes (it waits with griddepcontrol.wait).
 template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s,
                               Args... args) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
+  cfg.gridDim = grid;
   cfg.blockDim = dim3((unsigned)block);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -899,15 +1010,15 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
 void tc_generation_launch(const TcPlan& p, const RunDesc* runs, cudaStream_t s) {
   const int tb = 32 * p.trial_rows;
   if (p.prec == DE_PREC_BF16X3) {
-    launch_pdl(k_trial_split<2>, p.nitems_trial, tb, 0, s, runs, (const int2*)p.d_trial_items);
-    launch_pdl(k_fit_tc<2>, p.nitems_fit, kFitThreads, p.smem_fit, s, runs, (const int2*)p.d_fit_items, 0,
-               (double*)nullptr, 0);
+    launch_pdl(k_trial_split<2>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
+    launch_pdl(k_fit_tc<2>, dim3(p.nitems_fit, p.nsplit), kFitThreads, p.smem_fit, s, runs,
+               (const int2*)p.d_fit_items, 0, (double*)nullptr, 0);
   } else {
-    launch_pdl(k_trial_split<4>, p.nitems_trial, tb, 0, s, runs, (const int2*)p.d_trial_items);
-    launch_pdl(k_fit_tc<4>, p.nitems_fit, kFitThreads, p.smem_fit, s, runs, (const int2*)p.d_fit_items, 0,
-               (double*)nullptr, 0);
+    launch_pdl(k_trial_split<4>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
+    launch_pdl(k_fit_tc<4>, dim3(p.nitems_fit, p.nsplit), kFitThreads, p.smem_fit, s, runs,
+               (const int2*)p.d_fit_items, 0, (double*)nullptr, 0);
   }
-  launch_pdl(k_band_fp64, p.grid_band, 256, p.smem_band, s, runs, p.nruns, (const BandEntry*)p.d_band,
+  launch_pdl(k_band_fp64, dim3(p.grid_band), 256, p.smem_band, s, runs, p.nruns, (const BandEntry*)p.d_band,
              (const uint32_t*)p.d_band_cnt, p.nch_max);
 }
 

@@ -203,3 +203,33 @@ def test_near_policy_reaches_the_target_and_reports_fp64_best(prec):
     assert res["stop_reason"] == capi.DE_STOP_TARGET and res["best_f"] < 1e-8
     fo, _ = oracle.evaluate(0, b["best_x"][None, :], o, None)
     assert abs(b["best_f"] - fo[0]) <= 1e-12 * max(abs(fo[0]), 1e-300) + 1e-30
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_split_batch_of_mixed_widths_equals_single_runs(prec, monkeypatch):
+    """A batch mixing runs of one and of several N tiles (D = 300 and D = 40)
+    gives each run the population its own handle gives it (single runs on the
+    same three-kernel path)."""
+    _need_gpu()
+    monkeypatch.setenv("DE_GB300_PERSIST", "0")
+    shapes = [(150, 300, 1), (70, 40, 3), (200, 300, 0), (33, 40, 1)]
+    cfgs = []
+    for r, (n, d, obj) in enumerate(shapes):
+        cfgs.append(capi.make_config(n, d, objective=obj, shift=problems.shift(d, seed=9, run_id=r),
+                                     rot=problems.rotation(d, seed=9, run_id=r), seed=9, run_id=r, precision=prec,
+                                     max_generations=12, target_error=0.0))
+    h = capi.de_init_batch(cfgs)
+    try:
+        capi.de_step(h, 12)
+        pops = [capi.de_get_population(h, r) for r in range(len(shapes))]
+    finally:
+        capi.de_destroy(h)
+    for r, c in enumerate(cfgs):
+        hs = capi.de_init(c)
+        try:
+            capi.de_step(hs, 12)
+            xs, fs = capi.de_get_population(hs)
+        finally:
+            capi.de_destroy(hs)
+        assert np.array_equal(pops[r][0], xs), r
+        assert np.array_equal(pops[r][1], fs), r
