@@ -190,10 +190,16 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   __shared__ double s_bf[8];
   __shared__ int s_bi[8];
   const int4 it = items[blockIdx.x];
-  const RunDesc& R = runs[it.x];
-  RunState* st = R.st;
+  // the run descriptor in shared memory: its fields are read in every phase,
+  // after barriers that would force global reloads
+  __shared__ RunDesc sR;
+  for (int q = threadIdx.x; q < (int)(sizeof(RunDesc) / 8); q += blockDim.x)
+    reinterpret_cast<uint64_t*>(&sR)[q] = reinterpret_cast<const uint64_t*>(runs + it.x)[q];
+  const RunDesc& R = sR;
   pdl_launch_dependents();
   pdl_wait();
+  __syncthreads();
+  RunState* st = R.st;
   if (threadIdx.x == 0) {
     s_stop = *(volatile int32_t*)&st->stop;
     s_gen = *(volatile int64_t*)&st->gen;

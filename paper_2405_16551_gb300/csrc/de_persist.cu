@@ -78,15 +78,23 @@ __global__ void __launch_bounds__(256, 1)
   const bool leader = crank == 0;
   const int tile = (int)blockIdx.x / C;
   const int nclusters = (int)gridDim.x / C;
-  const RunDesc& R = runs[run];
-  RunState* st = R.st;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the run descriptor lives in shared memory for the whole launch: its fields
+  // are read in every phase, after barriers that would force global reloads
+  __shared__ RunDesc sR;
+  static_assert(sizeof(RunDesc) % 8 == 0, "descriptor copied in 8-byte words");
+  for (int q = tid; q < (int)(sizeof(RunDesc) / 8); q += blockDim.x)
+    reinterpret_cast<uint64_t*>(&sR)[q] = reinterpret_cast<const uint64_t*>(runs + run)[q];
+  __syncthreads();
+  const RunDesc& R = sR;
+  RunState* st = R.st;
   const int d = R.d, dp = R.dp, np = R.np, obj = R.obj;
-  // prows targets per cluster (64 or 128; rows past prows of the MMA tile stay zero)
+  // prows targets per cluster (a multiple of C, at most 128; rows past prows
+  // of the MMA tile stay zero); CTA r holds rows r rpm .. r rpm + rpm - 1 and
+  // warp w of it rows w and w + 8 of those
   const int kPRows = prows;
   const int row0 = tile * kPRows;
-  const int rpm = kPRows / C;  // rows per CTA
-  const int rpw = rpm / 8;     // rows per warp (1 or 2)
+  const int rpm = kPRows / C;  // rows per CTA, at most 16
 
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_bar[2];
@@ -191,8 +199,16 @@ __global__ void __launch_bounds__(256, 1)
   cluster.sync();
   const uint32_t tmem = leader ? s_tmem : 0u;
 
-  // per-warp registers: trial and target rows of this warp's targets
-  double tr[2][NCH][4], tx[2][NCH][4];
+  // per-warp registers: trial and target rows of this warp's targets, and the
+  // lane's coordinates of the shift
+  double tr[2][NCH][4], tx[2][NCH][4], osh[NCH][4];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = 128 * c + 4 * lane + e;
+      osh[c][e] = j < d ? R.o[j] : 0.0;
+    }
   long long gen = *l_gen;
   int stop = *l_stop;
   double best_prev = *l_best;
@@ -215,7 +231,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
       for (int q = qb; q < qb + QB; ++q) {
         const int i = row0 + crank * rpm + warp + 8 * q;
-        valid[q] = q < rpw && i < np;
+        valid[q] = warp + 8 * q < rpm && i < np;
         if (valid[q]) {
           ts[q] = trial_setup(R, (uint32_t)i, g, lane);
 #pragma unroll
@@ -247,7 +263,7 @@ __global__ void __launch_bounds__(256, 1)
             float y[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              y[e] = (j0 + e < d) ? (float)shifted(t[e], R.o[j0 + e], R) : 0.f;
+              y[e] = (j0 + e < d) ? (float)shifted(t[e], osh[c][e], R) : 0.f;
               yn2 += y[e] * y[e];
             }
             store_split4<ESZ>(lA, a_part, lr, j0, y);
@@ -289,7 +305,7 @@ __global__ void __launch_bounds__(256, 1)
       const int cb = h * half;
       const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
       EpiAcc acc_{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      const bool rows_here = (warp & 3) < kPRows / 32;  // TMEM lanes of this warp hold targets
+      const bool rows_here = (warp & 3) * 32 < kPRows;  // TMEM lanes of this warp hold targets
       if (have && rows_here) {
         for (int c = 0; c < half; c += 32) {
           float v[32];
@@ -393,8 +409,8 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             if (j0 + k >= d) continue;
-            const double yt = shifted(q ? tr[1][c][k] : tr[0][c][k], R.o[j0 + k], R);
-            const double yx = shifted(q ? tx[1][c][k] : tx[0][c][k], R.o[j0 + k], R);
+            const double yt = shifted(q ? tr[1][c][k] : tr[0][c][k], osh[c][k], R);
+            const double yx = shifted(q ? tx[1][c][k] : tx[0][c][k], osh[c][k], R);
             for (int r = 1; r < C; ++r) {
               double* dst = cluster.map_shared_rank(sYm, r);
               dst[(size_t)(2 * e) * dp + j0 + k] = yt;
@@ -537,7 +553,7 @@ __global__ void __launch_bounds__(256, 1)
     cluster.sync();  // final decisions visible
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      if (q >= rpw) break;
+      if (warp + 8 * q >= rpm) break;
       const int lr = crank * rpm + warp + 8 * q;
       const int i = row0 + lr;
       if (i >= np) continue;
@@ -647,49 +663,49 @@ bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
   // one run, one N tile, whole K resident, rows of at most 128 coordinates
   // (the trial and target rows of a warp then stay in registers)
   if (nruns != 1 || R.nn != 1 || R.kc != R.kpad || R.d > 128) return false;
-  for (int prows : {64, 128}) {
+  const int C = kPC;
+  const size_t smem = persist_smem(R, C);
+  if (smem > 220 * 1024) return false;
+  // tiles of 128 rows (fewer clusters meet at the grid barrier, which costs
+  // more than the extra trials per CTA); smaller populations take one tile
+  // of their own size (a multiple of C)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)C);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  auto query = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+  };
+  const cudaError_t e = prec == DE_PREC_BF16X3 ? query(k_persist<2, 1>) : query(k_persist<4, 1>);
+  if (e != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  int prows = std::min(kTileM, (R.np + C - 1) / C * C);
+  if (const char* env = getenv("DE_GB300_PERSIST_ROWS")) {
+    const int v = atoi(env);
+    if (v >= C && v <= kTileM && v % C == 0) prows = std::max(prows, v);
+  }
+  if (prows > kTileM) return false;
   const int ntiles = (R.np + prows - 1) / prows;
-  for (int C : {kPC}) {
-    const size_t smem = persist_smem(R, C);
-    if (smem > 220 * 1024) continue;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(ntiles * C));
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    cudaError_t e;
-    auto query = [&](auto kern) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      return cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
-    };
-    const bool one = true;
-    if (prec == DE_PREC_BF16X3) e = query(k_persist<2, 1>);
-    else e = query(k_persist<4, 1>);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    if (nclusters >= ntiles) {
-      pp.ok = true;
-      pp.C = C;
-      pp.ntiles = ntiles;
-      pp.smem = smem;
-      pp.prec = prec;
-      pp.nch = one ? 1 : 2;
-      pp.prows = prows;
-      return true;
-    }
-  }
-  }
-  return false;
+  if (ntiles > nclusters) return false;
+  pp.ok = true;
+  pp.C = C;
+  pp.ntiles = ntiles;
+  pp.smem = smem;
+  pp.prec = prec;
+  pp.nch = 1;
+  pp.prows = prows;
+  return true;
 }
 
 cudaError_t persist_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
