@@ -242,14 +242,36 @@ __device__ __forceinline__ void tile_rotate_dispatch(int rows, const double* MT,
 }
 
 // ------------------------------------------------------------------ best record
-__device__ __forceinline__ bool better(double fa, int ia, double fb, int ib) {
-  // a beats b: smaller f, or equal f and lower index; NaN never wins
-  // (compared as integer keys: no FP64 instruction on the path)
-  const long long ka = fit_key(fa), kb = fit_key(fb);
-  if (ka == 0x7FFFFFFFFFFFFFFFLL) return false;
-  if (ib < 0 || kb == 0x7FFFFFFFFFFFFFFFLL) return true;
-  return ka < kb || (ka == kb && ia < ib);
-}
+// Running best (f, index) of a reduction.  The ordered integer key of f is
+// computed once per offered value; comparisons and shuffles then use the key
+// (smaller key wins, then the lower index; a NaN, key INT64_MAX, never wins).
+struct Best {
+  double f;
+  long long k;
+  int i;
+  __device__ __forceinline__ void init() {
+    f = CUDART_INF;
+    k = 0x7FFFFFFFFFFFFFFFLL;
+    i = -1;
+  }
+  __device__ __forceinline__ void take(double fo, long long ko, int io) {
+    if (io >= 0 && ko != 0x7FFFFFFFFFFFFFFFLL && (i < 0 || ko < k || (ko == k && io < i))) {
+      f = fo;
+      k = ko;
+      i = io;
+    }
+  }
+  __device__ __forceinline__ void offer(double fo, int io) { take(fo, fit_key(fo), io); }
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double fo = __shfl_xor_sync(0xffffffffu, f, o);
+      const long long ko = __shfl_xor_sync(0xffffffffu, k, o);
+      const int io = __shfl_xor_sync(0xffffffffu, i, o);
+      take(fo, ko, io);
+    }
+  }
+};
 
 // Finish a generation of a run: called by the last CTA to arrive.  Reduces
 // the tile partials in order (and, for the split precisions, the rows decided
@@ -260,34 +282,25 @@ __device__ __forceinline__ void finish_generation(const RunDesc& R, int64_t g, i
                                                   const double* Xn, const BandEntry* band = nullptr, int nband = 0,
                                                   int run = -1, const double* fcur = nullptr) {
   __shared__ double sf[32];
+  __shared__ long long sk[32];
   __shared__ int si[32];
-  double bf = CUDART_INF;
-  int bi = -1;
-  for (int t = threadIdx.x; t < nparts; t += blockDim.x) {
-    const double pf = __ldcg(&part[t].f);
-    const int pi = __ldcg(&part[t].idx);
-    if (pi >= 0 && better(pf, pi, bf, bi)) { bf = pf; bi = pi; }
-  }
+  Best b;
+  b.init();
+  for (int t = threadIdx.x; t < nparts; t += blockDim.x) b.offer(__ldcg(&part[t].f), __ldcg(&part[t].idx));
   for (int t = threadIdx.x; t < nband; t += blockDim.x) {
     if (__ldcg(&band[t].run) != run) continue;
     const int i = __ldcg(&band[t].row);
-    const double fi = __ldcg(&fcur[i]);
-    if (better(fi, i, bf, bi)) { bf = fi; bi = i; }
+    b.offer(__ldcg(&fcur[i]), i);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double of = __shfl_xor_sync(0xffffffffu, bf, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (oi >= 0 && better(of, oi, bf, bi)) { bf = of; bi = oi; }
-  }
+  b.warp_reduce();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { sf[warp] = bf; si[warp] = bi; }
+  if (lane == 0) { sf[warp] = b.f; sk[warp] = b.k; si[warp] = b.i; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    bf = CUDART_INF;
-    bi = -1;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-      if (si[w] >= 0 && better(sf[w], si[w], bf, bi)) { bf = sf[w]; bi = si[w]; }
+    b.init();
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b.take(sf[w], sk[w], si[w]);
+    const double bf = b.f;
+    const int bi = b.i;
     RunState* st = R.st;
     if (bi >= 0) {
       st->best_f = bf;

@@ -116,25 +116,20 @@ __global__ void k_best_init(const RunDesc* __restrict__ runs, int run) {
   const int cur = R.dbuf ? (int)(st->gen & 1) : 0;
   const double* f = R.f[cur];
   __shared__ double sf[32];
+  __shared__ long long sk[32];
   __shared__ int si[32];
-  double bf = CUDART_INF;
-  int bi = -1;
-  for (int i = threadIdx.x; i < R.np; i += blockDim.x)
-    if (better(f[i], i, bf, bi)) { bf = f[i]; bi = i; }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double of = __shfl_xor_sync(0xffffffffu, bf, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (oi >= 0 && better(of, oi, bf, bi)) { bf = of; bi = oi; }
-  }
+  Best b;
+  b.init();
+  for (int i = threadIdx.x; i < R.np; i += blockDim.x) b.offer(f[i], i);
+  b.warp_reduce();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { sf[warp] = bf; si[warp] = bi; }
+  if (lane == 0) { sf[warp] = b.f; sk[warp] = b.k; si[warp] = b.i; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    bf = CUDART_INF;
-    bi = -1;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-      if (si[w] >= 0 && better(sf[w], si[w], bf, bi)) { bf = sf[w]; bi = si[w]; }
+    b.init();
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b.take(sf[w], sk[w], si[w]);
+    const double bf = b.f;
+    const int bi = b.i;
     st->best_f = bf;
     st->best_idx = bi;
     st->ticket = 0;
@@ -188,6 +183,7 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   __shared__ int s_stop, s_last;
   __shared__ long long s_gen;
   __shared__ double s_bf[8];
+  __shared__ long long s_bk[8];
   __shared__ int s_bi[8];
   const int4 it = items[blockIdx.x];
   // the run descriptor in shared memory: its fields are read in every phase,
@@ -282,8 +278,8 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   }
 
   // ---- row sums, greedy selection, best partial (a warp per row)
-  double bf = CUDART_INF;
-  int bi = -1;
+  Best bb;
+  bb.init();
   for (int rl = warp; rl < nrows; rl += nwarps) {
     const int i = row0 + rl;
     double ft;
@@ -313,17 +309,15 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
         R.dbg_fp64[i] = 1;
       }
     }
-    if (better(fnew, i, bf, bi)) { bf = fnew; bi = i; }
+    bb.offer(fnew, i);
   }
-  if (lane == 0) { s_bf[warp] = bf; s_bi[warp] = bi; }
+  if (lane == 0) { s_bf[warp] = bb.f; s_bk[warp] = bb.k; s_bi[warp] = bb.i; }
   __syncthreads();
   if (tid == 0) {
-    bf = CUDART_INF;
-    bi = -1;
-    for (int w = 0; w < nwarps; ++w)
-      if (s_bi[w] >= 0 && better(s_bf[w], s_bi[w], bf, bi)) { bf = s_bf[w]; bi = s_bi[w]; }
-    R.part[it.y].f = bf;
-    R.part[it.y].idx = bi;
+    bb.init();
+    for (int w = 0; w < nwarps; ++w) bb.take(s_bf[w], s_bk[w], s_bi[w]);
+    R.part[it.y].f = bb.f;
+    R.part[it.y].idx = bb.i;
     __threadfence();
     const uint32_t t = atomicAdd(&st->ticket, 1u);
     s_last = (t == (uint32_t)R.ntiles - 1u);

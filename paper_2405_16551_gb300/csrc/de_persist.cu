@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(256, 1)
   __shared__ long long s_gen;
   __shared__ double s_best;
   __shared__ double s_bf[8];
+  __shared__ long long s_bk[8];
   __shared__ int s_bi[8];
   __shared__ unsigned long long s_nband_total;
 
@@ -511,42 +512,30 @@ __global__ void __launch_bounds__(256, 1)
     // ---- 4. leader: best partial and debug; everyone: next-generation rows
     if (leader) {
       __syncthreads();
-      double bf = CUDART_INF;
-      int bi = -1;
+      Best b;
+      b.init();
       if (tid < kPRows && row0 + tid < np) {
-        bf = s_f[tid];
-        bi = row0 + tid;
+        const int i = row0 + tid;
+        b.offer(s_f[tid], i);
         if (R.dbg_ftrial) {
-          R.dbg_ftrial[bi] = s_ft[tid];
-          R.dbg_accept[bi] = s_flag[tid] & 1;
-          R.dbg_fp64[bi] = (s_flag[tid] >> 1) & 1;
+          R.dbg_ftrial[i] = s_ft[tid];
+          R.dbg_accept[i] = s_flag[tid] & 1;
+          R.dbg_fp64[i] = (s_flag[tid] >> 1) & 1;
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double of = __shfl_xor_sync(0xffffffffu, bf, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oi >= 0 && better(of, oi, bf, bi)) {
-          bf = of;
-          bi = oi;
-        }
-      }
+      b.warp_reduce();
       if (lane == 0) {
-        s_bf[warp] = bf;
-        s_bi[warp] = bi;
+        s_bf[warp] = b.f;
+        s_bk[warp] = b.k;
+        s_bi[warp] = b.i;
       }
       __syncthreads();
       if (tid == 0) {
-        bf = CUDART_INF;
-        bi = -1;
-        for (int w = 0; w < 8; ++w)
-          if (s_bi[w] >= 0 && better(s_bf[w], s_bi[w], bf, bi)) {
-            bf = s_bf[w];
-            bi = s_bi[w];
-          }
+        b.init();
+        for (int w = 0; w < 8; ++w) b.take(s_bf[w], s_bk[w], s_bi[w]);
         BestPartial* pp = R.part + (size_t)(g & 1) * nclusters + tile;
-        pp->f = bf;
-        pp->idx = bi;
+        pp->f = b.f;
+        pp->idx = b.i;
         s_nband_total += (unsigned long long)s_nb;  // published once, at the end of the launch
       }
     }
@@ -574,7 +563,7 @@ __global__ void __launch_bounds__(256, 1)
     }
     cluster.sync();  // the cluster's rows are written
 
-    // ---- 5. grid barrier; best record and stop rule
+    // ---- 5. grid barrier; best record and stop rule (thread 0 of each leader)
     if (leader && tid == 0) {
       if (!s_abort) {
         if (!grid_barrier(ctl, (unsigned)(itg + 1) * (unsigned)nclusters)) {
@@ -583,17 +572,12 @@ __global__ void __launch_bounds__(256, 1)
         }
       }
       if (!s_abort) {
-        double bf = CUDART_INF;
-        int bi = -1;
+        Best b;
+        b.init();
         const BestPartial* pp = R.part + (size_t)(g & 1) * nclusters;
-        for (int t = 0; t < nclusters; ++t) {
-          const double pf = __ldcg(&pp[t].f);
-          const int pi = __ldcg(&pp[t].idx);
-          if (pi >= 0 && better(pf, pi, bf, bi)) {
-            bf = pf;
-            bi = pi;
-          }
-        }
+        for (int t = 0; t < nclusters; ++t) b.offer(__ldcg(&pp[t].f), __ldcg(&pp[t].idx));
+        const double bf = b.f;
+        const int bi = b.i;
         const int64_t evals = (int64_t)np * (1 + g);  // the initial population counts as NP evaluations
         int sp = 0;
         if (R.target > 0.0 && bi >= 0 && bf < R.target) sp = 1;

@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(256) k_surr_select(const RunDesc* __restrict__
                                                      const int32_t* __restrict__ csel, double* __restrict__ arch_x,
                                                      double* __restrict__ arch_f, long long head, int cap) {
   __shared__ double s_bf[8];
+  __shared__ long long s_bk[8];
   __shared__ int s_bi[8];
   __shared__ int s_stop, s_last;
   __shared__ long long s_gen;
@@ -107,8 +108,8 @@ __global__ void __launch_bounds__(256) k_surr_select(const RunDesc* __restrict__
   const int64_t g = s_gen + 1;
   const int cur = (int)(s_gen & 1), nxt = cur ^ 1;
   const int dp = R.dp, d = R.d;
-  double bf = CUDART_INF;
-  int bi = -1;
+  Best bb;
+  bb.init();
   const int i = blockIdx.x * 8 + warp;
   if (i < R.np) {
     const double fi = R.f[cur][i], t = ft[i];
@@ -134,26 +135,19 @@ __global__ void __launch_bounds__(256) k_surr_select(const RunDesc* __restrict__
         if (R.dbg_cand) R.dbg_cand[i] = csel[i];
       }
     }
-    if (better(fnew, i, bf, bi)) {
-      bf = fnew;
-      bi = i;
-    }
+    bb.offer(fnew, i);
   }
   if (lane == 0) {
-    s_bf[warp] = bf;
-    s_bi[warp] = bi;
+    s_bf[warp] = bb.f;
+    s_bk[warp] = bb.k;
+    s_bi[warp] = bb.i;
   }
   __syncthreads();
   if (tid == 0) {
-    bf = CUDART_INF;
-    bi = -1;
-    for (int w = 0; w < 8; ++w)
-      if (s_bi[w] >= 0 && better(s_bf[w], s_bi[w], bf, bi)) {
-        bf = s_bf[w];
-        bi = s_bi[w];
-      }
-    R.part[blockIdx.x].f = bf;
-    R.part[blockIdx.x].idx = bi;
+    bb.init();
+    for (int w = 0; w < 8; ++w) bb.take(s_bf[w], s_bk[w], s_bi[w]);
+    R.part[blockIdx.x].f = bb.f;
+    R.part[blockIdx.x].idx = bb.i;
     __threadfence();
     const uint32_t tk = atomicAdd(&st->ticket, 1u);
     s_last = (tk == gridDim.x - 1u);

@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(kFitThreads, 1)
   __shared__ int s_list[kTileM];
   __shared__ int s_acc[kTileM];
   __shared__ double s_bf[8];
+  __shared__ long long s_bk[8];
   __shared__ int s_bi[8];
 
   const int2 it = items[blockIdx.x];
@@ -484,8 +485,8 @@ __global__ void __launch_bounds__(kFitThreads, 1)
   if (mode == 1) return;
 
   // ---- write back fitness, flags, debug; list the accepted rows
-  double bf = CUDART_INF;
-  int bi = -1;
+  Best bb;
+  bb.init();
   if (tid < nrows) {
     const int mm = tid, i = row0 + mm;
     const uint8_t fl = s_flag[mm];
@@ -502,8 +503,7 @@ __global__ void __launch_bounds__(kFitThreads, 1)
         R.dbg_accept[i] = acc ? 1 : 0;
         R.dbg_fp64[i] = 0;
       }
-      bf = s_fnew[mm];
-      bi = i;
+      bb.offer(s_fnew[mm], i);
     }
   }
   if (tid == 0) {
@@ -523,31 +523,19 @@ __global__ void __launch_bounds__(kFitThreads, 1)
     }
   }
   // ---- best partial of the tile, then the last CTA of the run finishes the generation
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double of = __shfl_xor_sync(0xffffffffu, bf, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (oi >= 0 && better(of, oi, bf, bi)) {
-      bf = of;
-      bi = oi;
-    }
-  }
+  bb.warp_reduce();
   if (lane == 0) {
-    s_bf[warp] = bf;
-    s_bi[warp] = bi;
+    s_bf[warp] = bb.f;
+    s_bk[warp] = bb.k;
+    s_bi[warp] = bb.i;
   }
   __syncthreads();
   if (tid == 0) {
-    bf = CUDART_INF;
-    bi = -1;
-    for (int w = 0; w < kFitThreads / 32; ++w)
-      if (s_bi[w] >= 0 && better(s_bf[w], s_bi[w], bf, bi)) {
-        bf = s_bf[w];
-        bi = s_bi[w];
-      }
+    bb.init();
+    for (int w = 0; w < kFitThreads / 32; ++w) bb.take(s_bf[w], s_bk[w], s_bi[w]);
     // the band kernel that follows reduces the partials of every tile
-    R.part[it.y].f = bf;
-    R.part[it.y].idx = bi;
+    R.part[it.y].f = bb.f;
+    R.part[it.y].idx = bb.i;
   }
 }
 
