@@ -189,8 +189,11 @@ static de_status enqueue_generations(de_handle* h, int64_t n) {
     return DE_OK;
   }
   if (h->prec != DE_PREC_FP64 && h->tc.persist.ok) {
-    // one persistent launch runs all n generations (or stops early)
-    if (n > 0) DE_CUDA(h, persist_launch(h->tc.persist, h->d_run, h->tc.d_ctl, n, h->stream));
+    // one persistent launch runs up to 2^20 generations (or stops early); the
+    // launch's grid-barrier count stays below 2^32
+    for (int64_t left = n; left > 0; left -= (int64_t)1 << 20)
+      DE_CUDA(h, persist_launch(h->tc.persist, h->d_run, h->tc.d_ctl, std::min<int64_t>(left, (int64_t)1 << 20),
+                                h->stream));
     return DE_OK;
   }
   const int kChunk = 64;

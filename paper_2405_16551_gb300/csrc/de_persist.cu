@@ -55,10 +55,16 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// Leaders only: arrive and wait until `target` leaders have arrived.
-__device__ bool grid_barrier(PersistCtl* ctl, unsigned target) {
+// Arrival of one CTA at the grid barrier: its writes before the call are
+// released to every CTA that sees the count.
+__device__ __forceinline__ void grid_arrive(PersistCtl* ctl) {
   __threadfence();
   atomicAdd(&ctl->bar, 1u);
+}
+
+// Leaders only: arrive and wait until `target` CTAs have arrived.
+__device__ bool grid_barrier(PersistCtl* ctl, unsigned target) {
+  grid_arrive(ctl);
   for (long long k = 0; k < kGridSpin; ++k) {
     if (ld_acquire_u32(&ctl->bar) >= target) return true;
     if (*(volatile int*)&ctl->abort) return false;
@@ -539,7 +545,9 @@ __global__ void __launch_bounds__(256, 1)
         s_nband_total += (unsigned long long)s_nb;  // published once, at the end of the launch
       }
     }
-    cluster.sync();  // final decisions visible
+    // the FP64 band changes decisions after the last cluster barrier; without
+    // band rows the members already see the final flags
+    if (nb > 0) cluster.sync();  // final decisions visible
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (warp + 8 * q >= rpm) break;
@@ -561,12 +569,15 @@ __global__ void __launch_bounds__(256, 1)
         }
       }
     }
-    cluster.sync();  // the cluster's rows are written
+    // every CTA arrives at the grid barrier once its rows are written; the
+    // leader waits for all of them
+    __syncthreads();
+    if (!leader && tid == 0) grid_arrive(ctl);
 
     // ---- 5. grid barrier; best record and stop rule (thread 0 of each leader)
     if (leader && tid == 0) {
       if (!s_abort) {
-        if (!grid_barrier(ctl, (unsigned)(itg + 1) * (unsigned)nclusters)) {
+        if (!grid_barrier(ctl, (unsigned)(itg + 1) * (unsigned)(nclusters * C))) {
           atomicOr(&st->err, kErrTimeout);
           s_abort = 1;
         }
