@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
-    p.add_argument("--workload", default="rastrigin", choices=["rastrigin", "batch512", "ode_surrogate", "stress"],
+    p.add_argument("--workload", default="rastrigin", choices=["rastrigin", "sphere_small", "batch512", "ode_surrogate", "stress"],
                    help="rastrigin: the headline configuration (default); the others measure the batched, "
                         "surrogate and large-dimension configurations with the same harness")
     return p.parse_args()
@@ -199,7 +199,10 @@ def measure(capi, torch, prec_name, G, steps, warmup, rank, flush, stream):
     """Device-timed steps of one precision form: events around re-initialisation
     + G generations; L2 flushed between steps outside the events."""
     o, M = make_problem()
-    cfg = capi.make_config(NP, D, f=F, cr=CR, objective=OBJ_RASTRIGIN, shift=o, rot=M, seed=SEED, run_id=rank,
+    from paper_2405_16551_gb300 import replicas
+
+    cfg = capi.make_config(NP, D, f=F, cr=CR, objective=OBJ_RASTRIGIN, shift=o, rot=M, seed=SEED,
+                           run_id=replicas.replica_run_id(0, rank),
                            precision=PREC_NAMES[prec_name], target_error=1e-8, max_generations=G)
     h = capi.de_init(cfg, stream=stream.cuda_stream)
     plan = capi.de_get_plan(h)
@@ -242,7 +245,7 @@ def main():
 
     import torch
 
-    from paper_2405_16551_gb300 import capi
+    from paper_2405_16551_gb300 import capi, replicas
 
     torch.cuda.set_device(local)
     if args.workload != "rastrigin":
@@ -273,13 +276,9 @@ def main():
         dist.barrier()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    dev_ms, gen_ms = head["dev_ms"], head["gen_ms"]
-    if dist is not None:
-        t = torch.tensor([dev_ms, gen_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms, gen_ms = t.tolist()
+    dev_ms, gen_ms = replicas.max_over_ranks([head["dev_ms"], head["gen_ms"]], dist, device="cuda")
     trials_per_step = NP * G
-    value = world * trials_per_step * args.steps / (dev_ms / 1e3)
+    value = replicas.job_rate(trials_per_step * args.steps, world, dev_ms / 1e3)
 
     # the other precision forms on the same device, for the comparison with
     # the plain FP64 GPU DE (two steps each)
@@ -306,7 +305,8 @@ def main():
         o_pin = torch.from_numpy(o).pin_memory()
         m_pin = torch.from_numpy(np.ascontiguousarray(M)).pin_memory()
         cfg_e = capi.make_config(NP, D, f=F, cr=CR, objective=OBJ_RASTRIGIN, shift=o_pin.numpy(), rot=m_pin.numpy(),
-                                 seed=SEED, run_id=rank, precision=PREC_NAMES[prec_name], target_error=1e-8,
+                                 seed=SEED, run_id=replicas.replica_run_id(0, rank),
+                                 precision=PREC_NAMES[prec_name], target_error=1e-8,
                                  max_generations=G)
         times = []
         for k in range(args.warmup + args.steps):
@@ -320,12 +320,8 @@ def main():
             if k >= args.warmup:
                 times.append(time.perf_counter() - t0)
             flush.zero_()
-        tot = sum(times)
-        if dist is not None:
-            t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = t.item()
-        e2e = {"value": world * trials_per_step * args.steps / tot, "unit": "trial evals/s",
+        tot = replicas.max_over_ranks([sum(times)], dist, device="cuda")[0]
+        e2e = {"value": replicas.job_rate(trials_per_step * args.steps, world, tot), "unit": "trial evals/s",
                "h2d_bytes_per_step": 8 * (D + D * D), "d2h_bytes_per_step": 8 * (D + 1) + 48}
 
     # roofline of the dominant kernel
@@ -406,7 +402,35 @@ def run_workload(args, capi, torch, rank, world):
     steps, warmup = args.steps, args.warmup
     line = {"n_gpus": world, "steps": steps, "warmup": warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "data": "synthetic", "unit": "trial evals/s"}
-    if args.workload == "batch512":
+    if args.workload == "sphere_small":
+        # the small FP64 sphere run: NP = 64, D = 10, up to 1000 generations, stop at 1e-8
+        o = problems.shift(10, seed=1)
+        c = capi.make_config(64, 10, objective=0, shift=o, seed=1, max_generations=1000, target_error=1e-8)
+        h = capi.de_init(c, stream=stream.cuda_stream)
+        gens = []
+
+        def one():
+            capi.de_reset(h)
+            capi.de_run(h)
+
+        ms = _timed(torch, stream, flush, steps, warmup, one)
+        r = capi.de_get_best(h)
+        capi.de_destroy(h)
+        import oracle
+
+        oracle.build()
+        t0 = time.perf_counter()
+        _, _, go, evo, _ = oracle.run(64, 10, 0.5, 0.9, -100.0, 100.0, 0, o, None, seed=1, max_generations=1000,
+                                      target_error=1e-8)
+        cpu_s = time.perf_counter() - t0
+        line.update(metric="trial evals/sec, NP=64 D=10 shifted sphere FP64, run to 1e-8 (at most 1000 generations)",
+                    value=64 * r["generations"] * steps / (ms / 1e3), ms_per_step=ms / steps, dtype="f64",
+                    config={"workload": "NP=64 D=10 sphere, seed 1, stop at 1e-8", "generations": r["generations"],
+                            "l2": "flushed between steps (512 MiB write)"},
+                    cpu_baseline={"value": 64 * go / cpu_s, "unit": "trial evals/s", "cores": 1, "kind": "oracle",
+                                  "sample": f"the whole run ({go} generations, {evo} evaluations), one thread"},
+                    gpu_launches=None)
+    elif args.workload == "batch512":
         G = min(args.generations, 200)
         shapes = problems.batch_shapes(512, seed=1)
         forms = {}
@@ -484,9 +508,9 @@ def run_workload(args, capi, torch, rank, world):
 
 # DRAM traffic of one launch of the dominant kernel, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a 200-generation launch of
-# the BF16x3 persistent kernel on this workload (313,600 + 2,182,144 bytes),
+# the BF16x3 persistent kernel on this workload (287,232 + 1,915,904 bytes),
 # scaled to a launch of 3000 generations (traffic grows with generations)
-TRAFFIC_PER_LAUNCH = {("k_persist", 3000): (313600 + 2182144) * 3000 // 200}
+TRAFFIC_PER_LAUNCH = {("k_persist", 3000): (287232 + 1915904) * 3000 // 200}
 
 
 if __name__ == "__main__":

@@ -688,7 +688,7 @@ bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
   int prows = std::min(kTileM, (R.np + C - 1) / C * C);
   if (const char* env = getenv("DE_GB300_PERSIST_ROWS")) {
     const int v = atoi(env);
-    if (v >= C && v <= kTileM && v % C == 0) prows = std::max(prows, v);
+    if (v >= C && v <= kTileM && v % C == 0) prows = v;
   }
   if (prows > kTileM) return false;
   const int ntiles = (R.np + prows - 1) / prows;
