@@ -339,15 +339,6 @@ __host__ __device__ __forceinline__ long long ordered_key(double x) {
   return k >= 0 ? k : -(k & 0x7FFFFFFFFFFFFFFFLL);
 }
 
-__device__ __forceinline__ double repair(double v, double x, const RunDesc& R) {
-  // a coordinate that leaves [lo, hi] goes half way from the target's
-  // coordinate to the violated bound (the paper leaves bounds handling open)
-  const long long kv = ordered_key(v);
-  if (kv < R.lo_key) return __dmul_rn(__dadd_rn(x, R.lo), 0.5);
-  if (kv > R.hi_key) return __dmul_rn(__dadd_rn(x, R.hi), 0.5);
-  return v;
-}
-
 // y = (t - o) s, rounded once per operation as written
 __device__ __forceinline__ double shifted(double t, double o, const RunDesc& R) {
   const double y = __dsub_rn(t, o);
@@ -407,7 +398,7 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
                                                   double t[4]) {
   const int d = R.d;
   const uint32_t u[4] = {c.u.x, c.u.y, c.u.z, c.u.w};
-  uint32_t bits = 0;
+  uint32_t bits = 0, oob = 0;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     const int j = j0 + m;
@@ -417,12 +408,25 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
       if (crossed) {
         // Eq. 2: y = x_r1 + F (x_r2 - x_r3), one rounding for the product-sum
         const double v = __fma_rn(R.F, __dsub_rn(c.x2[m], c.x3[m]), c.x1[m]);
-        t[m] = repair(v, c.xi[m], R);
+        t[m] = v;
         bits |= 1u << m;
+        const long long kv = ordered_key(v);
+        if (kv < R.lo_key || kv > R.hi_key) oob |= 1u << m;
       } else {
         t[m] = c.xi[m];
       }
     }
+  }
+  // bound repair: a crossed coordinate outside [lo, hi] goes half way from
+  // the target's coordinate to the violated bound (the paper leaves bounds
+  // handling open); the FP64 work runs only when some lane of the warp needs it
+  if (__any_sync(__activemask(), oob != 0u)) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      if ((oob >> m) & 1u) {
+        const double bound = ordered_key(t[m]) < R.lo_key ? R.lo : R.hi;
+        t[m] = __dmul_rn(__dadd_rn(c.xi[m], bound), 0.5);
+      }
   }
   return bits;
 }
