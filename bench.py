@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
-    p.add_argument("--workload", default="rastrigin", choices=["rastrigin", "sphere_small", "batch512", "ode_surrogate", "stress"],
+    p.add_argument("--workload", default="rastrigin", choices=["rastrigin", "sphere_small", "batch512", "ode_surrogate", "stress", "stress_batch"],
                    help="rastrigin: the headline configuration (default); the others measure the batched, "
                         "surrogate and large-dimension configurations with the same harness")
     return p.parse_args()
@@ -486,6 +486,24 @@ def run_workload(args, capi, torch, rank, world):
                     value=ev / tm, ms_per_step=1e3 * tm / 3, dtype="f64 objective, bf16 surrogate",
                     config={"workload": "ODE fit, 3 seeds, plain DE and surrogate k = 8, budget 2e5 true evaluations"},
                     runs=res, gpu_launches=None)
+    elif args.workload == "stress_batch":
+        # 64 runs of the large-dimension shape in one handle (working set far above L2)
+        G = min(args.generations, 10)
+        n, d, R = 8192, 1000, int(os.environ.get("DE_BENCH_BATCH_RUNS", "64"))
+        cfgs = [capi.make_config(n, d, objective=1, shift=problems.shift(d, seed=1, run_id=r),
+                                 rot=problems.rotation(d, seed=1, run_id=r), seed=1, run_id=r,
+                                 precision=PREC_NAMES["bf16x3"], target_error=0.0, max_generations=G)
+                for r in range(R)]
+        h = capi.de_init_batch(cfgs, stream=stream.cuda_stream)
+        ms = _timed(torch, stream, flush, steps, warmup, lambda: (capi.de_reset(h, -1), capi.de_step(h, G)))
+        capi.de_destroy(h)
+        value = R * n * G * steps / (ms / 1e3)
+        line.update(metric=f"trial evals/sec, {R} runs of NP=8192 D=1000 rotated-shifted Rastrigin, BF16x3",
+                    value=value, ms_per_step=ms / steps, dtype="bf16x3 products, f32 accumulate",
+                    config={"workload": f"{R} x (NP=8192 D=1000), {G} generations per step, one handle",
+                            "l2": f"working set about {R / 4:.0f} GB, far above L2"},
+                    tensor_tflops=3 * 2.0 * R * n * d * d * G * steps / (ms / 1e3) / 1e12,
+                    gpu_launches=steps * (3 * R + 3 * G))
     else:  # stress
         G = min(args.generations, 100)
         n, d = 8192, 1000

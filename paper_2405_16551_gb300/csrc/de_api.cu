@@ -258,7 +258,14 @@ static de_status init_run(de_handle* h, int r) {
   DE_CUDA(h, cudaMemsetAsync(R.X[0], 0, (size_t)R.np * R.dp * sizeof(double), h->stream));
   if (R.obj == DE_OBJ_ODE) k_ode_reference_launch(h->d_run, r, const_cast<double*>(R.ode_ref), h->stream);
   k_init_population_launch(h->d_run, r, R.np, R.dp, h->stream);
-  k_eval_rows_launch(h->d_run, r, R.X[0], R.dp, R.np, R.dp, R.rotate, R.f[0], R.fx[0], h->stream);
+  if (h->prec == DE_PREC_FP64) {
+    k_eval_rows_launch(h->d_run, r, R.X[0], R.dp, R.np, R.dp, R.rotate, R.f[0], R.fx[0], h->stream);
+  } else {
+    // split precisions evaluate the initial population in their own precision
+    // (values with error bounds, like accepted trials); the best record is
+    // made FP64 when a caller reads it
+    tc_init_eval_launch(h->tc, h->d_run, r, R, h->stream);
+  }
   k_best_init_launch(h->d_run, r, h->stream);
   DE_CUDA(h, cudaGetLastError());
   return DE_OK;

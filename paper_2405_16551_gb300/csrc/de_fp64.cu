@@ -136,7 +136,9 @@ __global__ void k_best_init(const RunDesc* __restrict__ runs, int run) {
     st->band_n = 0;
     st->band_left = 0;
     int stop = 0;
-    if (R.target > 0.0 && bi >= 0 && bf < R.target) stop = 1;
+    // the target test takes FP64 values only (a split-precision initial value
+    // below the target leaves the decision to the first generation's FP64 band)
+    if (R.target > 0.0 && bi >= 0 && bf < R.target && R.fx[cur][bi]) stop = 1;
     else if (R.max_evals > 0 && st->evals >= R.max_evals) stop = 2;
     else if (st->gen >= R.max_gens) stop = 3;
     st->stop = stop;

@@ -67,6 +67,9 @@ void tc_plan_free(TcPlan& p);
 de_status tc_set_geometry(TcPlan& p, std::vector<RunDesc>& runs, int trial_rows, int kc_div, cudaStream_t s,
                           std::string& err);
 void tc_generation_launch(const TcPlan& p, const RunDesc* runs, cudaStream_t s);
+// Split-precision evaluation of run `run`'s population X[0] into f[0] (fx = 0,
+// tau set): the initial evaluation of split-precision runs.
+void tc_init_eval_launch(const TcPlan& p, const RunDesc* runs, int run, const RunDesc& R, cudaStream_t s);
 de_status tc_eval_launch(const TcPlan& p, const RunDesc* runs, int run, const RunDesc& R, const double* x, int64_t ld,
                          int n, double* f, cudaStream_t s, std::string& err);
 // Evaluation of n caller rows with a device descriptor and work list that

@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(256) k_prep_rows(const RunDesc* __restrict__ r
 
 // ------------------------------------------------------------------ fitness + selection kernel
 // mode 0: one generation (items = (run, 128-row tile)); mode 1: evaluation of
-// n_eval rows already converted by k_prep_rows, f written to fout.
+// n_eval rows already converted by k_prep_rows, f written to fout; mode 2:
+// the same for the run's own population (n_eval = np), written as the
+// population's split fitness values with their error bounds (f, fx = 0, tau).
 template <int ESZ>
 __global__ void __launch_bounds__(kFitThreads, 1)
     k_fit_tc(const RunDesc* __restrict__ runs, const int2* __restrict__ items, int mode, double* __restrict__ fout,
@@ -449,6 +451,10 @@ __global__ void __launch_bounds__(kFitThreads, 1)
     const float tau = 2.f * R.band_u * G * R.rownorm * pf_yn + (float)d * 0x1.0p-21f * S + 1e-30f;
     if (mode == 1) {
       fout[i] = (double)fs;
+    } else if (mode == 2) {
+      R.f[0][i] = (double)fs;
+      R.fx[0][i] = 0;
+      R.tau[i] = tau;
     } else {
       // decided in FP32; the margins cover the rounding of the FP64 values
       const float fif = (float)pf_fi;
@@ -482,7 +488,7 @@ __global__ void __launch_bounds__(kFitThreads, 1)
     }
   }
   __syncthreads();
-  if (mode == 1) return;
+  if (mode != 0) return;
 
   // ---- write back fitness, flags, debug; list the accepted rows
   Best bb;
@@ -1008,6 +1014,17 @@ void tc_generation_launch(const TcPlan& p, const RunDesc* runs, cudaStream_t s) 
   }
   launch_pdl(k_band_fp64, dim3(p.grid_band), 256, p.smem_band, s, runs, p.nruns, (const BandEntry*)p.d_band,
              (const uint32_t*)p.d_band_cnt, p.nch_max);
+}
+
+void tc_init_eval_launch(const TcPlan& p, const RunDesc* runs, int run, const RunDesc& R, cudaStream_t s) {
+  const int2* items = p.d_fit_items + p.fit_offset[run];
+  if (p.prec == DE_PREC_BF16X3) {
+    k_prep_rows<2><<<(R.np + 7) / 8, 256, 0, s>>>(runs, run, R.X[0], R.dp, R.np);
+    k_fit_tc<2><<<R.ntiles_tc, kFitThreads, p.smem_fit, s>>>(runs, items, 2, (double*)nullptr, R.np);
+  } else {
+    k_prep_rows<4><<<(R.np + 7) / 8, 256, 0, s>>>(runs, run, R.X[0], R.dp, R.np);
+    k_fit_tc<4><<<R.ntiles_tc, kFitThreads, p.smem_fit, s>>>(runs, items, 2, (double*)nullptr, R.np);
+  }
 }
 
 de_status tc_eval_launch(const TcPlan& p, const RunDesc* runs, int run, const RunDesc& R, const double* x, int64_t ld,
