@@ -82,6 +82,16 @@ def _load():
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_double,
                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _i32p,
                                      _dp, _dp, _dp, _dp, _i32p, _i32p, _u32p, _dp, _dp, _dp, _u8p, ctypes.c_int]
+        lib.or_step_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _i32p, ctypes.c_int, ctypes.c_int,
+                                   _dp, _dp, _dp, _dp,
+                                   _dp, _dp, _dp, _dp, _i32p, _i32p, _u32p, _dp, _dp, _dp, _u8p, ctypes.c_int]
+        lib.or_run_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.c_double, _dp, _dp, _dp, _dp, _i64p, _dp, ctypes.c_int]
+        lib.or_run_ex.restype = ctypes.c_int64
         lib.or_best.argtypes = [ctypes.c_int, _dp]
         lib.or_best.restype = ctypes.c_int
         lib.or_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -249,11 +259,18 @@ def init_population(np_, d, lo, hi, seed, run_id=0):
     return X
 
 
-def step(X, fX, F, CR, lo, hi, obj, o, M, seed, generation, run_id=0, scale=1.0, threads=1, cand=None):
+STRATEGIES = {"rand1bin": 0, "best1bin": 1, "rand1exp": 2}
+
+
+def step(X, fX, F, CR, lo, hi, obj, o, M, seed, generation, run_id=0, scale=1.0, threads=1, cand=None,
+         strategy=0, jde=False, jF=None, jCR=None):
     """One synchronous generation; returns a dict with the next population and
-    every intermediate (indices, j_rand, crossover mask, trials, f_trial,
-    magnitude sums, accept flags).  cand: per-target candidate stream (None:
-    stream 0, plain DE)."""
+    every intermediate (indices, j_rand (the crossover start for exp),
+    crossover mask, trials, f_trial, magnitude sums, accept flags).  cand:
+    per-target candidate stream (None: stream 0, plain DE).  strategy: 0
+    rand/1/bin, 1 best/1/bin, 2 rand/1/exp.  jde: per-individual F and CR
+    (jF, jCR of generation g - 1, default all F / CR); the dict then carries
+    F_next and CR_next."""
     X = _f64(X)
     fX = _f64(fX)
     np_, d = X.shape
@@ -264,8 +281,15 @@ def step(X, fX, F, CR, lo, hi, obj, o, M, seed, generation, run_id=0, scale=1.0,
         trial=np.zeros_like(X), f_trial=np.zeros(np_), sabs_trial=np.zeros(np_),
         accept=np.zeros(np_, dtype=np.uint8))
     cnd = None if cand is None else np.ascontiguousarray(cand, dtype=np.int32)
-    _load().or_step_cand(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), scale, seed, run_id, generation,
-                    _p(cnd, _i32p), _p(X), _p(fX), _p(out["X_next"]), _p(out["f_next"]), _p(out["idx"], _i32p),
+    jFa = jCRa = None
+    if jde:
+        jFa = np.full(np_, F) if jF is None else _f64(jF)
+        jCRa = np.full(np_, CR) if jCR is None else _f64(jCR)
+        out["F_next"] = np.zeros(np_)
+        out["CR_next"] = np.zeros(np_)
+    _load().or_step_ex(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), scale, seed, run_id, generation,
+                    _p(cnd, _i32p), int(strategy), 1 if jde else 0, _p(jFa), _p(jCRa),
+                    _p(out.get("F_next")), _p(out.get("CR_next")), _p(X), _p(fX), _p(out["X_next"]), _p(out["f_next"]), _p(out["idx"], _i32p),
                     _p(out["jrand"], _i32p), _p(out["mask"], _u32p), _p(out["trial"]), _p(out["f_trial"]),
                     _p(out["sabs_trial"]), _p(out["accept"], _u8p), threads)
     return out
@@ -277,13 +301,17 @@ def best(f):
 
 
 def run(np_, d, F, CR, lo, hi, obj, o, M, seed, max_generations, max_evals=0, target_error=1e-8,
-        run_id=0, scale=1.0, threads=1, trace=False):
-    """A whole run; returns (X, f, generations, evals, best_trace or None)."""
+        run_id=0, scale=1.0, threads=1, trace=False, strategy=0, jde=False, return_adaptive=False):
+    """A whole run; returns (X, f, generations, evals, best_trace or None),
+    and (F_i, CR_i) after them when return_adaptive (jde)."""
     X = np.zeros((np_, d))
     f = np.zeros(np_)
+    jF = np.zeros(np_)
+    jCR = np.zeros(np_)
     ev = ctypes.c_int64(0)
     tr = np.full(max_generations + 1, np.nan) if trace else None
-    g = _load().or_run(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), scale, seed, run_id,
-                       max_generations, max_evals, target_error, _p(X), _p(f), ctypes.byref(ev), _p(tr),
-                       threads)
-    return X, f, int(g), int(ev.value), (tr[: g + 1] if trace else None)
+    g = _load().or_run_ex(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), scale, seed, run_id, int(strategy),
+                          1 if jde else 0, max_generations, max_evals, target_error, _p(X), _p(f), _p(jF), _p(jCR),
+                          ctypes.byref(ev), _p(tr), threads)
+    res = (X, f, int(g), int(ev.value), (tr[: g + 1] if trace else None))
+    return res + (jF, jCR) if return_adaptive else res

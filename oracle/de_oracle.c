@@ -63,7 +63,7 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
  *   key = (seed low 32 bits, seed high 32 bits)
  *   ctr = (d / 4, individual, generation, run_id << 12 | cand << 4 | purpose)
  *   draw d of a stream is word d % 4 of that block.                         */
-enum { OR_PURPOSE_INIT = 1, OR_PURPOSE_STEP = 2 };
+enum { OR_PURPOSE_INIT = 1, OR_PURPOSE_STEP = 2, OR_PURPOSE_JDE = 6 };
 
 uint32_t or_draw(uint64_t seed, uint32_t purpose, uint32_t run_id, uint32_t cand,
                  uint32_t generation, uint32_t individual, uint32_t d)
@@ -278,22 +278,47 @@ uint64_t or_cr_threshold(double cr)
 /* nw = ceil(d/32) (bit j%32 of word j/32), trial[np*d], ftrial[np],          */
 /* sabs_trial[np], accept[np].                                                */
 /* ------------------------------------------------------------------------- */
-/* cand (may be NULL = all 0): per target, the candidate stream its trial is
- * drawn from.  Stream 0 is plain DE/rand/1/bin; streams 1, 2, ... give the
- * other candidate trials that a surrogate screens (the same Eq. 2 / Eq. 3
- * construction with independent draws). */
-void or_step_cand(int np, int d, double F, double CR, double lo, double hi,
-                  int obj, const double* o, const double* M, double scale,
-                  uint64_t seed, uint32_t run_id, uint32_t generation, const int32_t* cand,
-                  const double* X, const double* fX, double* Xn, double* fXn,
-                  int32_t* idx, int32_t* jrand_out, uint32_t* mask, double* trial_out,
-                  double* ftrial_out, double* sabs_out, uint8_t* accept_out, int threads)
+int or_best(int np, const double* f);
+
+/* Variants of the trial construction (Sec. 2 names them: the base vector
+ * "rand" or "best", "bin" or "exp" crossover; jDE adapts F and CR per
+ * individual).  The formulas are the published ones, restated:
+ *   strategy 0  DE/rand/1/bin   v = x_r1 + F (x_r2 - x_r3), binomial crossover
+ *   strategy 1  DE/best/1/bin   v = x_best + F (x_r1 - x_r2), best = the best
+ *                                individual of generation g-1 (lowest f, then
+ *                                lowest index)
+ *   strategy 2  DE/rand/1/exp   exponential crossover (Storn and Price): from
+ *                                the start n = map(draw 3, D), L = 1 plus the
+ *                                number of leading draws 4, 5, ... with
+ *                                rand <= CR, at most D; coordinates n, n+1,
+ *                                ..., n+L-1 (mod D) cross
+ *   jDE (Brest et al., IEEE TEC 2006): per target, words w0..w3 of the JDE
+ *   stream at (individual, generation); with probability tau = 0.1 each,
+ *     F' = 0.1 + 0.9 u0  (one fma)       when w1 < floor(0.1 2^32),
+ *     CR' = u2                            when w3 < floor(0.1 2^32),
+ *   where u = w / 2^32; otherwise F' = F_i, CR' = CR_i.  The trial uses F'
+ *   and CR'; they replace F_i and CR_i only when the trial is selected.
+ * cand (may be NULL = all 0): per target, the candidate stream its trial is
+ * drawn from.  Stream 0 is plain DE; streams 1, 2, ... give the other
+ * candidate trials that a surrogate screens (the same construction with
+ * independent draws). */
+void or_step_ex(int np, int d, double F, double CR, double lo, double hi,
+                int obj, const double* o, const double* M, double scale,
+                uint64_t seed, uint32_t run_id, uint32_t generation, const int32_t* cand,
+                int strategy, int jde, const double* jF, const double* jCR, double* jFn, double* jCRn,
+                const double* X, const double* fX, double* Xn, double* fXn,
+                int32_t* idx, int32_t* jrand_out, uint32_t* mask, double* trial_out,
+                double* ftrial_out, double* sabs_out, uint8_t* accept_out, int threads)
 {
     const int nw = (d + 31) / 32;
     const uint64_t T = or_cr_threshold(CR);
+    const uint32_t tau_thr = (uint32_t)floor(0.1 * 4294967296.0);
+    const int best = or_best(np, fX);
     double* trial = (double*)malloc(sizeof(double) * (size_t)np * (size_t)d);
     double* ft = (double*)malloc(sizeof(double) * (size_t)np);
     double* sa = (double*)malloc(sizeof(double) * (size_t)np);
+    double* Ft = (double*)malloc(sizeof(double) * (size_t)np);
+    double* CRt = (double*)malloc(sizeof(double) * (size_t)np);
 
     /* mutation (Eq. 2), crossover (Eq. 3) and bound repair for every target */
     for (int i = 0; i < np; ++i) {
@@ -307,17 +332,43 @@ void or_step_cand(int np, int d, double F, double CR, double lo, double hi,
         if (idx) { idx[3 * i] = (int32_t)r[0]; idx[3 * i + 1] = (int32_t)r[1]; idx[3 * i + 2] = (int32_t)r[2]; }
         if (jrand_out) jrand_out[i] = (int32_t)jrand;
         if (mask) for (int k = 0; k < nw; ++k) mask[(size_t)i * nw + k] = 0u;
+        /* control parameters of this trial */
+        double Fi = F, CRi = CR;
+        uint64_t Ti = T;
+        if (jde) {
+            uint32_t a[4];
+            for (int k = 0; k < 4; ++k)
+                a[k] = or_draw(seed, OR_PURPOSE_JDE, run_id, ci, generation, (uint32_t)i, (uint32_t)k);
+            Fi = a[1] < tau_thr ? fma(0.9, (double)a[0] * (1.0 / 4294967296.0), 0.1) : jF[i];
+            CRi = a[3] < tau_thr ? (double)a[2] * (1.0 / 4294967296.0) : jCR[i];
+            Ti = or_cr_threshold(CRi);
+        }
+        Ft[i] = Fi;
+        CRt[i] = CRi;
         const double* xi = X + (size_t)i * d;
-        const double* x1 = X + (size_t)r[0] * d;
-        const double* x2 = X + (size_t)r[1] * d;
-        const double* x3 = X + (size_t)r[2] * d;
+        const double* x1 = strategy == 1 ? X + (size_t)best * d : X + (size_t)r[0] * d;
+        const double* x2 = strategy == 1 ? X + (size_t)r[0] * d : X + (size_t)r[1] * d;
+        const double* x3 = strategy == 1 ? X + (size_t)r[1] * d : X + (size_t)r[2] * d;
+        /* exponential crossover: the length of the crossed block */
+        int L = 0;
+        if (strategy == 2) {
+            L = 1;
+            while (L < d && (uint64_t)or_draw(seed, OR_PURPOSE_STEP, run_id, ci, generation, (uint32_t)i,
+                                              4u + (uint32_t)(L - 1)) <= Ti)
+                ++L;
+        }
         for (int j = 0; j < d; ++j) {
-            uint32_t u = or_draw(seed, OR_PURPOSE_STEP, run_id, ci, generation, (uint32_t)i, 4u + (uint32_t)j);
-            int crossed = ((uint32_t)j == jrand) || ((uint64_t)u <= T);
+            int crossed;
+            if (strategy == 2) {
+                crossed = ((j - (int)jrand + d) % d) < L;
+            } else {
+                uint32_t u = or_draw(seed, OR_PURPOSE_STEP, run_id, ci, generation, (uint32_t)i, 4u + (uint32_t)j);
+                crossed = ((uint32_t)j == jrand) || ((uint64_t)u <= Ti);
+            }
             double t;
             if (crossed) {
-                /* Eq. 2: y_ij = x_r1,j + F (x_r2,j - x_r3,j) */
-                double v = fma(F, x2[j] - x3[j], x1[j]);
+                /* Eq. 2: y_ij = x_base,j + F (x_a,j - x_b,j) */
+                double v = fma(Fi, x2[j] - x3[j], x1[j]);
                 /* bound repair (the paper is silent): a coordinate that leaves
                    [lo, hi] goes half way from the target's coordinate to the
                    violated bound */
@@ -345,10 +396,27 @@ void or_step_cand(int np, int d, double F, double CR, double lo, double hi,
         if (trial_out) memcpy(trial_out + (size_t)i * d, trial + (size_t)i * d, sizeof(double) * (size_t)d);
         if (Xn) memcpy(Xn + (size_t)i * d, acc ? trial + (size_t)i * d : X + (size_t)i * d, sizeof(double) * (size_t)d);
         if (fXn) fXn[i] = acc ? ft[i] : fX[i];
+        if (jde) {
+            if (jFn) jFn[i] = acc ? Ft[i] : jF[i];
+            if (jCRn) jCRn[i] = acc ? CRt[i] : jCR[i];
+        }
     }
     free(trial);
     free(ft);
     free(sa);
+    free(Ft);
+    free(CRt);
+}
+
+void or_step_cand(int np, int d, double F, double CR, double lo, double hi,
+                  int obj, const double* o, const double* M, double scale,
+                  uint64_t seed, uint32_t run_id, uint32_t generation, const int32_t* cand,
+                  const double* X, const double* fX, double* Xn, double* fXn,
+                  int32_t* idx, int32_t* jrand_out, uint32_t* mask, double* trial_out,
+                  double* ftrial_out, double* sabs_out, uint8_t* accept_out, int threads)
+{
+    or_step_ex(np, d, F, CR, lo, hi, obj, o, M, scale, seed, run_id, generation, cand, 0, 0, NULL, NULL, NULL,
+               NULL, X, fX, Xn, fXn, idx, jrand_out, mask, trial_out, ftrial_out, sabs_out, accept_out, threads);
 }
 
 void or_step(int np, int d, double F, double CR, double lo, double hi,
@@ -383,14 +451,20 @@ int or_best(int np, const double* f)
 /* generation, max_generations + 1 entries.                                   */
 /* Returns the number of generations run.                                     */
 /* ------------------------------------------------------------------------- */
-int64_t or_run(int np, int d, double F, double CR, double lo, double hi,
-               int obj, const double* o, const double* M, double scale,
-               uint64_t seed, uint32_t run_id,
-               int64_t max_generations, int64_t max_evals, double target_error,
-               double* X, double* fX, int64_t* evals_out, double* best_trace, int threads)
+int64_t or_run_ex(int np, int d, double F, double CR, double lo, double hi,
+                  int obj, const double* o, const double* M, double scale,
+                  uint64_t seed, uint32_t run_id, int strategy, int jde,
+                  int64_t max_generations, int64_t max_evals, double target_error,
+                  double* X, double* fX, double* jF, double* jCR, int64_t* evals_out, double* best_trace, int threads)
 {
     double* Xn = (double*)malloc(sizeof(double) * (size_t)np * (size_t)d);
     double* fn = (double*)malloc(sizeof(double) * (size_t)np);
+    double* jFn = (double*)malloc(sizeof(double) * (size_t)np);
+    double* jCRn = (double*)malloc(sizeof(double) * (size_t)np);
+    for (int i = 0; i < np && jde; ++i) {
+        jF[i] = F;
+        jCR[i] = CR;
+    }
     or_init_population(np, d, lo, hi, seed, run_id, X);
     or_eval(obj, d, o, M, scale, X, d, np, fX, NULL, threads);
     int64_t evals = np;
@@ -403,15 +477,31 @@ int64_t or_run(int np, int d, double F, double CR, double lo, double hi,
         if (max_evals > 0 && evals >= max_evals) break;
         if (g >= max_generations) break;
         g += 1;
-        or_step(np, d, F, CR, lo, hi, obj, o, M, scale, seed, run_id, (uint32_t)g, X, fX, Xn, fn,
-                NULL, NULL, NULL, NULL, NULL, NULL, NULL, threads);
+        or_step_ex(np, d, F, CR, lo, hi, obj, o, M, scale, seed, run_id, (uint32_t)g, NULL, strategy, jde, jF, jCR,
+                   jFn, jCRn, X, fX, Xn, fn, NULL, NULL, NULL, NULL, NULL, NULL, NULL, threads);
         memcpy(X, Xn, sizeof(double) * (size_t)np * (size_t)d);
         memcpy(fX, fn, sizeof(double) * (size_t)np);
+        if (jde) {
+            memcpy(jF, jFn, sizeof(double) * (size_t)np);
+            memcpy(jCR, jCRn, sizeof(double) * (size_t)np);
+        }
         evals += np;
         if (best_trace) { int bb = or_best(np, fX); best_trace[g] = bb >= 0 ? fX[bb] : NAN; }
     }
     free(Xn);
     free(fn);
+    free(jFn);
+    free(jCRn);
     if (evals_out) *evals_out = evals;
     return g;
+}
+
+int64_t or_run(int np, int d, double F, double CR, double lo, double hi,
+               int obj, const double* o, const double* M, double scale,
+               uint64_t seed, uint32_t run_id,
+               int64_t max_generations, int64_t max_evals, double target_error,
+               double* X, double* fX, int64_t* evals_out, double* best_trace, int threads)
+{
+    return or_run_ex(np, d, F, CR, lo, hi, obj, o, M, scale, seed, run_id, 0, 0, max_generations, max_evals,
+                     target_error, X, fX, NULL, NULL, evals_out, best_trace, threads);
 }
