@@ -133,7 +133,33 @@ typedef struct {
                                  candidate trials per target (FP64, d == 20, one run per handle; see
                                  de_get_surrogate_stats) */
     int32_t surrogate_steps;  /* Adam steps per retraining of the surrogate; 0 = 100 */
+    int32_t strategy;         /* de_strategy: base vector and crossover of the trial (Sec. 2); FP64 only
+                                 for values other than DE_RAND1BIN */
+    int32_t jde;              /* nonzero: jDE self-adaptive F and CR per individual (Sec. 2, the adaptive
+                                 variant); f and cr are the initial values; FP64 only */
 } de_config;
+
+/* Trial-construction strategies (Sec. 2 names the variants by base vector,
+ * number of difference vectors and crossover):
+ *   DE_RAND1BIN  base x_r1, one difference x_r2 - x_r3, binomial crossover (Eq. 2, Eq. 3)
+ *   DE_BEST1BIN  base x_best (the lowest-index best of the current population; row 0 when no
+ *                fitness is finite), difference x_r1 - x_r2 of the first two drawn donors,
+ *                binomial crossover
+ *   DE_RAND1EXP  base x_r1, difference x_r2 - x_r3, exponential crossover: coordinates
+ *                j_rand, j_rand + 1, ... (cyclic) for a block of length L, where L - 1 is the
+ *                number of leading crossover draws rand_0, rand_1, ... at or below the CR
+ *                threshold (at most d - 1); the other coordinates come from the target
+ * jDE (de_config.jde) applies to every strategy: before the trial of target i
+ * is built, with probability 0.1 each (draws 1 and 3 of the JDE stream of
+ * (i, g) below floor(0.1 * 2^32)), F_i becomes 0.1 + 0.9 u_0 and CR_i becomes
+ * u_2 (u_k = draw k / 2^32); otherwise the stored values are used.  The
+ * trial uses F_i and CR_i; the stored values become the trial's when the
+ * trial is accepted. */
+typedef enum {
+    DE_RAND1BIN = 0,
+    DE_BEST1BIN = 1,
+    DE_RAND1EXP = 2
+} de_strategy;
 
 /* When the split precisions redo a selection comparison in FP64.
  *   DE_BAND_NEAR (default)  the split values cannot decide it within their
@@ -355,6 +381,15 @@ DE_API de_status de_set_population(de_handle* h, int32_t run, const double* x_ho
 
 /* Set the generation counter of run `run` (the next de_step runs g + 1). */
 DE_API de_status de_set_generation(de_handle* h, int32_t run, int64_t generation);
+
+/* jDE state of run `run` (cfg.jde set): the per-individual F_i and CR_i of
+ * the current population (np doubles each, host; either may be NULL).
+ * de_init and de_reset set every F_i to cfg.f and every CR_i to cfg.cr;
+ * de_set_population keeps them.  Synchronises.
+ * Errors: DE_ERR_STATE when the run does not use jDE; DE_ERR_INVALID_ARG for
+ * de_set_adaptive values outside F in [0, 2], CR in [0, 1]. */
+DE_API de_status de_get_adaptive(de_handle* h, int32_t run, double* f_host, double* cr_host);
+DE_API de_status de_set_adaptive(de_handle* h, int32_t run, const double* f_host, const double* cr_host);
 
 /* Best record of run `run`: best_f, its index, a copy of its vector
  * (host, d doubles, may be NULL), and generation/evaluation counters. */

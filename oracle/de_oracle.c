@@ -313,7 +313,9 @@ void or_step_ex(int np, int d, double F, double CR, double lo, double hi,
     const int nw = (d + 31) / 32;
     const uint64_t T = or_cr_threshold(CR);
     const uint32_t tau_thr = (uint32_t)floor(0.1 * 4294967296.0);
-    const int best = or_best(np, fX);
+    /* DE/best/1: the lowest-index best; the paper does not cover a population
+       without a finite fitness, where row 0 serves as the base */
+    const int best = or_best(np, fX) < 0 ? 0 : or_best(np, fX);
     double* trial = (double*)malloc(sizeof(double) * (size_t)np * (size_t)d);
     double* ft = (double*)malloc(sizeof(double) * (size_t)np);
     double* sa = (double*)malloc(sizeof(double) * (size_t)np);

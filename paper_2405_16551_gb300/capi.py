@@ -22,6 +22,7 @@ DE_OBJ_SPHERE, DE_OBJ_RASTRIGIN, DE_OBJ_ROSENBROCK, DE_OBJ_ACKLEY, DE_OBJ_ODE = 
 DE_PREC_FP64, DE_PREC_BF16X3, DE_PREC_TF32X3 = 0, 1, 2
 DE_STOP_NONE, DE_STOP_TARGET, DE_STOP_EVALS, DE_STOP_GENERATIONS = 0, 1, 2, 3
 DE_BAND_NEAR, DE_BAND_ALL = 0, 1
+DE_RAND1BIN, DE_BEST1BIN, DE_RAND1EXP = 0, 1, 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -38,7 +39,7 @@ class de_config(ctypes.Structure):
                 ("run_id", ctypes.c_uint32), ("precision", ctypes.c_int32), ("target_error", ctypes.c_double),
                 ("max_evals", ctypes.c_int64), ("max_generations", ctypes.c_int64),
                 ("debug_capture", ctypes.c_int32), ("fp64_band", ctypes.c_int32), ("surrogate_k", ctypes.c_int32),
-                ("surrogate_steps", ctypes.c_int32)]
+                ("surrogate_steps", ctypes.c_int32), ("strategy", ctypes.c_int32), ("jde", ctypes.c_int32)]
 
 
 class de_result(ctypes.Structure):
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = True):
             "de_load": ([H, ctypes.c_char_p], ctypes.c_int),
             "de_destroy": ([H], ctypes.c_int),
             "de_get_surrogate_stats": ([H, _i64p, _i64p, _dp, _i32p], ctypes.c_int),
+            "de_get_adaptive": ([H, ctypes.c_int32, _dp, _dp], ctypes.c_int),
+            "de_set_adaptive": ([H, ctypes.c_int32, _dp, _dp], ctypes.c_int),
             "de_mlp_create": ([ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
             "de_mlp_destroy": ([H], ctypes.c_int),
             "de_mlp_set_params": ([H, _fp], ctypes.c_int),
@@ -132,7 +135,8 @@ def exported_symbols():
             "de_eval", "de_get_population", "de_set_population", "de_set_generation", "de_get_best",
             "de_get_debug", "de_get_shape", "de_get_stats", "de_get_plan", "de_save", "de_load", "de_destroy",
             "de_eval_noalloc", "de_mlp_create", "de_mlp_destroy", "de_mlp_set_params", "de_mlp_get_params",
-            "de_mlp_forward", "de_mlp_grad", "de_mlp_train", "de_get_surrogate_stats"]
+            "de_mlp_forward", "de_mlp_grad", "de_mlp_train", "de_get_surrogate_stats", "de_get_adaptive",
+            "de_set_adaptive"]
 
 
 def _status_name(s):
@@ -160,7 +164,7 @@ def de_version() -> str:
 def make_config(np_, d, f=0.5, cr=0.9, lo=-100.0, hi=100.0, objective=DE_OBJ_SPHERE, scale=1.0, shift=None,
                 rot=None, seed=1, run_id=0, precision=DE_PREC_FP64, target_error=1e-8, max_evals=0,
                 max_generations=1000, debug_capture=False, fp64_band=DE_BAND_NEAR, surrogate_k=0,
-                surrogate_steps=0):
+                surrogate_steps=0, strategy=DE_RAND1BIN, jde=False):
     """A de_config; the returned object keeps the shift/rotation arrays alive."""
     c = de_config()
     c.np, c.d, c.f, c.cr, c.lo, c.hi = np_, d, f, cr, lo, hi
@@ -169,6 +173,7 @@ def make_config(np_, d, f=0.5, cr=0.9, lo=-100.0, hi=100.0, objective=DE_OBJ_SPH
     c.debug_capture = 1 if debug_capture else 0
     c.fp64_band = fp64_band
     c.surrogate_k, c.surrogate_steps = surrogate_k, surrogate_steps
+    c.strategy, c.jde = strategy, 1 if jde else 0
     keep = []
     if shift is not None:
         s = np.ascontiguousarray(shift, dtype=np.float64)
@@ -307,6 +312,22 @@ def de_set_population(h, run: int, x, f=None):
 
 def de_set_generation(h, run: int, generation: int):
     _check(load().de_set_generation(h, run, generation), h)
+
+
+def de_get_adaptive(h, run: int = 0):
+    """jDE parameters (F_i, CR_i) of the current population."""
+    np_, _, _ = de_get_shape(h, run)
+    F = np.empty(np_, dtype=np.float64)
+    CR = np.empty(np_, dtype=np.float64)
+    _check(load().de_get_adaptive(h, run, _p(F), _p(CR)), h)
+    return F, CR
+
+
+def de_set_adaptive(h, run: int, F=None, CR=None):
+    np_, _, _ = de_get_shape(h, run)
+    Fa = None if F is None else np.ascontiguousarray(F, dtype=np.float64).reshape(np_)
+    Ca = None if CR is None else np.ascontiguousarray(CR, dtype=np.float64).reshape(np_)
+    _check(load().de_set_adaptive(h, run, _p(Fa), _p(Ca)), h)
 
 
 def de_get_best(h, run: int = 0):

@@ -44,6 +44,7 @@ struct de_handle {
   cudaGraphExec_t graph = nullptr;
   int graph_gens = 0;
   Surrogate* surr = nullptr;  // surrogate-assisted generations (surrogate_k >= 2)
+  bool variants = false;      // some run uses a strategy variant or jDE
   std::string err;
 };
 
@@ -105,6 +106,7 @@ static de_status validate(const de_config& c, int idx, std::string& why) {
   if (c.fp64_band != DE_BAND_NEAR && c.fp64_band != DE_BAND_ALL) return bad("fp64_band out of range");
   if (c.surrogate_k < 0 || c.surrogate_k > 32) return bad("surrogate_k must be in [0, 32]");
   if (c.surrogate_steps < 0 || c.surrogate_steps > 100000) return bad("surrogate_steps must be in [0, 100000]");
+  if (c.strategy < DE_RAND1BIN || c.strategy > DE_RAND1EXP) return bad("strategy out of range");
   if (c.surrogate_k >= 2) {
     if (c.precision != DE_PREC_FP64) return bad("surrogate-assisted generations run in FP64 only");
     if (c.d != 20) return bad("the surrogate network takes d = 20");
@@ -165,7 +167,7 @@ static void drop_graph(de_handle* h) {
 // Enqueue one generation of every run (the kernels skip stopped runs).
 static de_status launch_generation(de_handle* h, cudaStream_t s) {
   if (h->prec == DE_PREC_FP64) {
-    k_gen_fp64_launch(h->d_run, h->d_items, h->nitems, h->threads, h->smem_gen, s);
+    k_gen_fp64_launch(h->d_run, h->d_items, h->nitems, h->threads, h->smem_gen, h->variants, s);
   } else {
     tc_generation_launch(h->tc, h->d_run, s);
   }
@@ -258,6 +260,7 @@ static de_status init_run(de_handle* h, int r) {
   DE_CUDA(h, cudaMemsetAsync(R.X[0], 0, (size_t)R.np * R.dp * sizeof(double), h->stream));
   if (R.obj == DE_OBJ_ODE) k_ode_reference_launch(h->d_run, r, const_cast<double*>(R.ode_ref), h->stream);
   k_init_population_launch(h->d_run, r, R.np, R.dp, h->stream);
+  if (R.jde) k_jde_init_launch(h->d_run, r, R.np, h->stream);
   if (h->prec == DE_PREC_FP64) {
     k_eval_rows_launch(h->d_run, r, R.X[0], R.dp, R.np, R.dp, R.rotate, R.f[0], R.fx[0], h->stream);
   } else {
@@ -536,6 +539,10 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
       return fail(nullptr, DE_ERR_INVALID_ARG, "all runs of a batch must share the precision");
     if (cfgs[r].surrogate_k >= 2 && nruns != 1)
       return fail(nullptr, DE_ERR_INVALID_ARG, "surrogate-assisted generations take one run per handle");
+    if ((cfgs[r].strategy != DE_RAND1BIN || cfgs[r].jde) &&
+        (cfgs[r].precision != DE_PREC_FP64 || cfgs[r].surrogate_k >= 2))
+      return fail(nullptr, DE_ERR_UNSUPPORTED,
+                  "the best/1/bin and rand/1/exp strategies and jDE run on the FP64 path without a surrogate");
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -551,6 +558,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
   h->device = dev;
   h->nruns = nruns;
   h->prec = cfgs[0].precision;
+  for (int r = 0; r < nruns; ++r) h->variants = h->variants || cfgs[r].strategy != DE_RAND1BIN || cfgs[r].jde;
   h->cfg.assign(cfgs, cfgs + nruns);
   for (auto& c : h->cfg) {
     c.shift = nullptr;
@@ -567,7 +575,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     return o;
   };
   struct Offs {
-    size_t X0, X1, f0, f1, fx0, fx1, o, MT, Mr, st, part, T, ref;
+    size_t X0, X1, f0, f1, fx0, fx1, o, MT, Mr, st, part, T, ref, jF0, jF1, jC0, jC1;
     size_t dbg_idx, dbg_jrand, dbg_mask, dbg_trial, dbg_ftrial, dbg_accept, dbg_fp64, dbg_cand;
   };
   std::vector<Offs> offs(nruns);
@@ -591,6 +599,12 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     const bool split = c.precision != DE_PREC_FP64;
     O.T = split ? take(pop) : 0;
     O.ref = c.objective == DE_OBJ_ODE ? take((size_t)kOdeSteps * kOdeN * sizeof(double)) : 0;
+    if (c.jde) {
+      O.jF0 = take(c.np * sizeof(double));
+      O.jF1 = take(c.np * sizeof(double));
+      O.jC0 = take(c.np * sizeof(double));
+      O.jC1 = take(c.np * sizeof(double));
+    }
     if (c.debug_capture) {
       const int nw = (c.d + 31) / 32;
       O.dbg_idx = take((size_t)c.np * 3 * sizeof(int32_t));
@@ -676,6 +690,14 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
       R.T = (double*)(A + O.T);
     }
     if (c.objective == DE_OBJ_ODE) R.ode_ref = (const double*)(A + O.ref);
+    R.strategy = c.strategy;
+    R.jde = c.jde ? 1 : 0;
+    if (c.jde) {
+      R.jF[0] = (double*)(A + O.jF0);
+      R.jF[1] = (double*)(A + O.jF1);
+      R.jCR[0] = (double*)(A + O.jC0);
+      R.jCR[1] = (double*)(A + O.jC1);
+    }
     if (c.debug_capture) {
       R.dbg_idx = (int32_t*)(A + O.dbg_idx);
       R.dbg_jrand = (int32_t*)(A + O.dbg_jrand);
@@ -900,12 +922,54 @@ de_status de_set_generation(de_handle* h, int32_t run, int64_t generation) {
                                h->stream));
     DE_CUDA(h, cudaMemcpyAsync(R.f[want], R.f[cur], R.np * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     DE_CUDA(h, cudaMemcpyAsync(R.fx[want], R.fx[cur], R.np, cudaMemcpyDeviceToDevice, h->stream));
+    if (R.jde) {
+      DE_CUDA(h, cudaMemcpyAsync(R.jF[want], R.jF[cur], R.np * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      DE_CUDA(h, cudaMemcpyAsync(R.jCR[want], R.jCR[cur], R.np * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 h->stream));
+    }
   }
   DE_CUDA(h, cudaMemcpyAsync(&R.st->gen, &generation, sizeof generation, cudaMemcpyHostToDevice, h->stream));
   int64_t ev = (int64_t)R.np * (1 + generation);
   DE_CUDA(h, cudaMemcpyAsync(&R.st->evals, &ev, sizeof ev, cudaMemcpyHostToDevice, h->stream));
   k_best_init_launch(h->d_run, run, h->stream);
   DE_CUDA(h, cudaGetLastError());
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DE_OK;
+}
+
+de_status de_get_adaptive(de_handle* h, int32_t run, double* f_host, double* cr_host) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (run < 0 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
+  const RunDesc& R = h->run[run];
+  if (!R.jde) return fail(h, DE_ERR_STATE, "the run does not use jDE");
+  de_status s = read_states(h);
+  if (s != DE_OK) return s;
+  const int cur = cur_buf(h, h->h_state[run].gen);
+  if (f_host)
+    DE_CUDA(h, cudaMemcpyAsync(f_host, R.jF[cur], R.np * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (cr_host)
+    DE_CUDA(h, cudaMemcpyAsync(cr_host, R.jCR[cur], R.np * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return DE_OK;
+}
+
+de_status de_set_adaptive(de_handle* h, int32_t run, const double* f_host, const double* cr_host) {
+  if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
+  if (run < 0 || run >= h->nruns) return fail(h, DE_ERR_INVALID_ARG, "run out of range");
+  const RunDesc& R = h->run[run];
+  if (!R.jde) return fail(h, DE_ERR_STATE, "the run does not use jDE");
+  for (int i = 0; i < R.np; ++i) {
+    if (f_host && !(f_host[i] >= 0.0 && f_host[i] <= 2.0)) return fail(h, DE_ERR_INVALID_ARG, "F_i must be in [0, 2]");
+    if (cr_host && !(cr_host[i] >= 0.0 && cr_host[i] <= 1.0))
+      return fail(h, DE_ERR_INVALID_ARG, "CR_i must be in [0, 1]");
+  }
+  de_status s = read_states(h);
+  if (s != DE_OK) return s;
+  const int cur = cur_buf(h, h->h_state[run].gen);
+  if (f_host)
+    DE_CUDA(h, cudaMemcpyAsync(R.jF[cur], f_host, R.np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (cr_host)
+    DE_CUDA(h, cudaMemcpyAsync(R.jCR[cur], cr_host, R.np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   DE_CUDA(h, cudaStreamSynchronize(h->stream));
   return DE_OK;
 }
@@ -1024,7 +1088,7 @@ de_status de_save(de_handle* h, const char* path) {
   for (int r = 0; r < h->nruns; ++r) {
     const RunDesc& R = h->run[r];
     const int cur = cur_buf(h, h->h_state[r].gen);
-    int32_t shape[3] = {R.np, R.d, R.prec};
+    int32_t shape[5] = {R.np, R.d, R.prec, R.strategy, R.jde};
     put(shape, sizeof shape);
     put(&h->h_state[r], sizeof(RunState));
     std::vector<double> x((size_t)R.np * R.dp), f(R.np);
@@ -1041,10 +1105,18 @@ de_status de_save(de_handle* h, const char* path) {
       DE_CUDA(h, cudaMemcpy(tau.data(), R.tau, tau.size() * sizeof(float), cudaMemcpyDeviceToHost));
       put(tau.data(), tau.size() * sizeof(float));
     }
+    if (R.jde) {
+      std::vector<double> a(2 * (size_t)R.np);
+      DE_CUDA(h, cudaMemcpyAsync(a.data(), R.jF[cur], R.np * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      DE_CUDA(h, cudaMemcpyAsync(a.data() + R.np, R.jCR[cur], R.np * sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+      DE_CUDA(h, cudaStreamSynchronize(h->stream));
+      put(a.data(), a.size() * sizeof(double));
+    }
   }
   CkptHeader hd{};
   memcpy(hd.magic, "DEGB300", 8);
-  hd.version = 2;
+  hd.version = 3;
   hd.nruns = h->nruns;
   hd.payload_bytes = payload.size();
   hd.crc = crc32_update(0, payload.data(), payload.size());
@@ -1064,7 +1136,7 @@ de_status de_load(de_handle* h, const char* path) {
   if (!fp) return fail(h, DE_ERR_IO, std::string("cannot open ") + path);
   CkptHeader hd{};
   std::vector<char> payload;
-  bool ok = fread(&hd, sizeof hd, 1, fp) == 1 && memcmp(hd.magic, "DEGB300", 8) == 0 && hd.version == 2 &&
+  bool ok = fread(&hd, sizeof hd, 1, fp) == 1 && memcmp(hd.magic, "DEGB300", 8) == 0 && hd.version == 3 &&
             hd.payload_bytes < (1ull << 40);
   if (ok) {
     payload.resize(hd.payload_bytes);
@@ -1083,10 +1155,10 @@ de_status de_load(de_handle* h, const char* path) {
   };
   for (int r = 0; r < h->nruns; ++r) {
     const RunDesc& R = h->run[r];
-    int32_t shape[3];
+    int32_t shape[5];
     RunState st;
     if (!get(shape, sizeof shape) || !get(&st, sizeof st)) return fail(h, DE_ERR_IO, "checkpoint truncated");
-    if (shape[0] != R.np || shape[1] != R.d || shape[2] != R.prec)
+    if (shape[0] != R.np || shape[1] != R.d || shape[2] != R.prec || shape[3] != R.strategy || shape[4] != R.jde)
       return fail(h, DE_ERR_STATE, "checkpoint shape differs from the handle's");
     std::vector<double> x((size_t)R.np * R.dp), f(R.np);
     std::vector<uint8_t> fx(R.np);
@@ -1099,7 +1171,17 @@ de_status de_load(de_handle* h, const char* path) {
       if (!get(tau.data(), tau.size() * sizeof(float))) return fail(h, DE_ERR_IO, "checkpoint truncated");
       DE_CUDA(h, cudaMemcpyAsync(R.tau, tau.data(), tau.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     }
+    std::vector<double> adapt;
+    if (R.jde) {
+      adapt.resize(2 * (size_t)R.np);
+      if (!get(adapt.data(), adapt.size() * sizeof(double))) return fail(h, DE_ERR_IO, "checkpoint truncated");
+    }
     const int cur = cur_buf(h, st.gen);
+    if (R.jde) {
+      DE_CUDA(h, cudaMemcpyAsync(R.jF[cur], adapt.data(), R.np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      DE_CUDA(h, cudaMemcpyAsync(R.jCR[cur], adapt.data() + R.np, R.np * sizeof(double), cudaMemcpyHostToDevice,
+                                 h->stream));
+    }
     st.ticket = 0;
     st.band_n = 0;
     st.band_left = 0;

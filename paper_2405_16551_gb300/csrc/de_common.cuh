@@ -21,6 +21,7 @@ namespace de {
 
 constexpr uint32_t kPurposeInit = 1u;
 constexpr uint32_t kPurposeStep = 2u;
+constexpr uint32_t kPurposeJde = 6u;  // jDE: draws 0..3 of (i, g) decide F_i and CR_i
 
 constexpr int kObjSphere = 0;
 constexpr int kObjRastrigin = 1;

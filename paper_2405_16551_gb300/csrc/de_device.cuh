@@ -392,10 +392,13 @@ __device__ __forceinline__ void trial_load(const RunDesc& R, const double* __res
   }
 }
 
-// Coordinates j0 .. j0+3 of the trial from loaded inputs; entries at j >= d
-// are 0.  Returns the crossed-coordinate bits (bit m for j0 + m).
+// Coordinates j0 .. j0+3 of the trial from loaded inputs with weight F and
+// crossover threshold thr; entries at j >= d are 0.  L = 0: binomial
+// crossover (Eq. 3); L >= 1: exponential crossover of the cyclic block
+// j_rand .. j_rand + L - 1.  Returns the crossed-coordinate bits (bit m for
+// j0 + m).
 __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialSetup& s, int j0, const ChunkIn& c,
-                                                  double t[4]) {
+                                                  double t[4], double F, uint64_t thr, int L) {
   const int d = R.d;
   const uint32_t u[4] = {c.u.x, c.u.y, c.u.z, c.u.w};
   uint32_t bits = 0, oob = 0;
@@ -404,10 +407,17 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
     const int j = j0 + m;
     t[m] = 0.0;
     if (j < d) {
-      const bool crossed = ((uint32_t)j == s.jr) || ((uint64_t)u[m] <= R.cr_thr);
+      bool crossed;
+      if (L > 0) {
+        int off = j - (int)s.jr;
+        if (off < 0) off += d;
+        crossed = off < L;
+      } else {
+        crossed = ((uint32_t)j == s.jr) || ((uint64_t)u[m] <= thr);
+      }
       if (crossed) {
         // Eq. 2: y = x_r1 + F (x_r2 - x_r3), one rounding for the product-sum
-        const double v = __fma_rn(R.F, __dsub_rn(c.x2[m], c.x3[m]), c.x1[m]);
+        const double v = __fma_rn(F, __dsub_rn(c.x2[m], c.x3[m]), c.x1[m]);
         t[m] = v;
         bits |= 1u << m;
         const long long kv = ordered_key(v);
@@ -431,6 +441,12 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
   return bits;
 }
 
+// DE/rand/1/bin with the run's F and CR.
+__device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialSetup& s, int j0, const ChunkIn& c,
+                                                  double t[4]) {
+  return trial_compute(R, s, j0, c, t, R.F, R.cr_thr, 0);
+}
+
 // Coordinates j0 .. j0+3 (j0 < d, j0 % 4 == 0) of the trial; entries at
 // j >= d are 0.  Returns the crossed-coordinate bits (bit m for j0 + m).
 __device__ __forceinline__ uint32_t trial_chunk(const RunDesc& R, const double* __restrict__ X, const TrialSetup& s,
@@ -438,6 +454,76 @@ __device__ __forceinline__ uint32_t trial_chunk(const RunDesc& R, const double* 
   ChunkIn c;
   trial_load(R, X, s, i, g, j0, c, cand);
   return trial_compute(R, s, j0, c, t);
+}
+
+// ------------------------------------------------------------------ variants
+// Control parameters of one trial under the strategy variants and jDE.
+struct TrialVar {
+  double F;      // weight of the difference vector
+  double CR;     // crossover rate (stored into jCR on acceptance)
+  uint64_t thr;  // floor(CR 2^32): rand_j <= thr crosses coordinate j
+  int L;         // exponential crossover: block length (0: binomial)
+};
+
+// jDE (Brest et al.'s self-adaptation, the adaptive variant of Sec. 2): draws
+// a0..a3 of the JDE stream of (i, g); with probability 0.1 each
+// (a1 resp. a3 below floor(0.1 2^32)) F_i = 0.1 + 0.9 a0 / 2^32 (one
+// rounding) and CR_i = a2 / 2^32, otherwise the stored values.
+__device__ __forceinline__ void jde_params(const RunDesc& R, uint32_t i, int64_t g, const double* __restrict__ jF,
+                                           const double* __restrict__ jCR, double& F, double& CR) {
+  const uint32_t tau = 429496729u;  // floor(0.1 * 2^32)
+  const U32x4 a = draw_block(R.seed, kPurposeJde, R.run_id, 0u, (uint32_t)g, i, 0u);
+  F = a.y < tau ? __fma_rn(0.9, (double)a.x * 0x1p-32, 0.1) : jF[i];
+  CR = a.w < tau ? (double)a.z * 0x1p-32 : jCR[i];
+}
+
+// Exponential crossover length (Sec. 2): L = 1 + the number of leading
+// crossover draws rand_0, rand_1, ... (draw 4 + m of the STEP stream, the
+// ones binomial crossover gives coordinate m) that are <= thr, capped at d.
+// Called by the whole warp; lane q tests draws 128c + 4q .. 128c + 4q + 3.
+__device__ __forceinline__ int exp_length(const RunDesc& R, uint32_t i, int64_t g, int lane, uint64_t thr) {
+  const int d = R.d;
+  for (int m0 = 0; m0 <= d - 2; m0 += 128) {
+    const int mb = m0 + 4 * lane;
+    uint32_t fail = 0;
+    if (mb <= d - 2) {
+      const U32x4 b = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, i, 1u + (uint32_t)(mb >> 2));
+      const uint32_t u[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (mb + q <= d - 2 && (uint64_t)u[q] > thr) fail |= 1u << q;
+    }
+    const uint32_t any = __ballot_sync(0xffffffffu, fail != 0u);
+    if (any) {
+      const int fl = __ffs(any) - 1;
+      const uint32_t fb = __shfl_sync(0xffffffffu, fail, fl);
+      return m0 + 4 * fl + (__ffs(fb) - 1) + 1;
+    }
+  }
+  return d;
+}
+
+// Trial setup under the run's strategy and jDE: records the drawn donors,
+// then for DE/best/1 takes the base from row `best` and the difference from
+// the first two drawn donors.  Called by the whole warp.
+__device__ __forceinline__ TrialSetup trial_setup_var(const RunDesc& R, uint32_t i, int64_t g, int lane, int best,
+                                                      const double* __restrict__ jF, const double* __restrict__ jCR,
+                                                      TrialVar& v) {
+  TrialSetup s = trial_setup(R, i, g, lane);
+  if (R.strategy == 1) {
+    s.r3 = s.r2;
+    s.r2 = s.r1;
+    s.r1 = (uint32_t)best;
+  }
+  v.F = R.F;
+  v.CR = R.CR;
+  v.thr = R.cr_thr;
+  if (R.jde) {
+    jde_params(R, i, g, jF, jCR, v.F, v.CR);
+    v.thr = (uint64_t)floor(__dmul_rn(v.CR, 4294967296.0));
+  }
+  v.L = R.strategy == 2 ? exp_length(R, i, g, lane, v.thr) : 0;
+  return s;
 }
 
 // Debug capture of one chunk: trial values and the crossover mask word.
@@ -460,10 +546,16 @@ __device__ __forceinline__ void trial_debug(const RunDesc& R, uint32_t i, int j0
 }
 
 // FP64 path: build the trial row into T and Y = (T - o) s (rows of length dp).
+// VAR: the run may use a strategy variant or jDE (best: the current best row;
+// jF, jCR: the current jDE parameters).
+template <bool VAR>
 __device__ __forceinline__ void build_trial_row(const RunDesc& R, const double* __restrict__ X, uint32_t i,
                                                 int64_t g, int lane, double* __restrict__ Trow,
-                                                double* __restrict__ Yrow) {
-  const TrialSetup s = trial_setup(R, i, g, lane);
+                                                double* __restrict__ Yrow, int best = 0,
+                                                const double* __restrict__ jF = nullptr,
+                                                const double* __restrict__ jCR = nullptr) {
+  TrialVar v;
+  const TrialSetup s = VAR ? trial_setup_var(R, i, g, lane, best, jF, jCR, v) : trial_setup(R, i, g, lane);
   const bool dbg = R.dbg_trial != nullptr;
   const int nchunks = (R.d + 127) / 128;
   for (int c = 0; c < nchunks; ++c) {
@@ -471,7 +563,13 @@ __device__ __forceinline__ void build_trial_row(const RunDesc& R, const double* 
     double t[4] = {0.0, 0.0, 0.0, 0.0};
     uint32_t bits = 0;
     if (j0 < R.d) {
-      bits = trial_chunk(R, X, s, i, g, j0, t);
+      if (VAR) {
+        ChunkIn ci;
+        trial_load(R, X, s, i, g, j0, ci);
+        bits = trial_compute(R, s, j0, ci, t, v.F, v.thr, v.L);
+      } else {
+        bits = trial_chunk(R, X, s, i, g, j0, t);
+      }
       double y[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) y[m] = (j0 + m < R.d) ? shifted(t[m], R.o[j0 + m], R) : 0.0;

@@ -4,11 +4,13 @@
 //   k_eval_rows         Sec. 7.3.1: z = M((x - o) s), objective of each row
 //   k_best_init         best record, stop flag and counters after (re)initialisation
 //   k_ode_reference     trajectory of the hidden parameters of the ODE objective
+//   k_jde_init          jDE: initial F_i and CR_i
 //   k_gen_fp64          one whole generation, fused: mutant indices (Eq. 2),
 //                       mutation (Eq. 2), binomial crossover (Eq. 3), bound
 //                       repair, shift + rotation + objective (Sec. 7.3.1),
 //                       greedy selection (Sec. 2, Sec. 6.2.5), best-so-far and
-//                       stop test (Sec. 7.3.4)
+//                       stop test (Sec. 7.3.4); also the DE/best/1/bin and
+//                       DE/rand/1/exp strategies and jDE (Sec. 2)
 //
 // One CTA owns a tile of `rows` targets of one run.  A warp builds one trial
 // at a time: lane L holds coordinates 128c + 4L .. 128c + 4L + 3, so a row is
@@ -100,6 +102,16 @@ __global__ void k_eval_rows(const RunDesc* __restrict__ runs, int run, const dou
   }
 }
 
+// jDE: every F_i and CR_i of generation 0 set to the run's F and CR.
+__global__ void k_jde_init(const RunDesc* __restrict__ runs, int run) {
+  const RunDesc& R = runs[run];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < R.np) {
+    R.jF[0][i] = R.F;
+    R.jCR[0][i] = R.CR;
+  }
+}
+
 // Trajectory of the hidden parameter vector o of an ODE run (one warp).
 __global__ void k_ode_reference(const RunDesc* __restrict__ runs, int run, double* __restrict__ ref) {
   const RunDesc& R = runs[run];
@@ -179,10 +191,13 @@ __device__ __forceinline__ void rotate_groups(const RunDesc& R, const double* __
 // about one CTA per SM so that every SM's FP64 pipe gets the same work.
 // Shared memory: T (trials), Y (shifted trials), Z (rotated), W (second term
 // sum of Ackley), each R.rows x dp doubles.
+// VAR: some run of the launch uses a strategy variant or jDE (a separate
+// instance, so that plain DE/rand/1/bin keeps its register allocation).
+template <bool VAR>
 __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ runs,
                                                   const int4* __restrict__ items) {
   extern __shared__ __align__(16) double sm[];
-  __shared__ int s_stop, s_last;
+  __shared__ int s_stop, s_last, s_best;
   __shared__ long long s_gen;
   __shared__ double s_bf[8];
   __shared__ long long s_bk[8];
@@ -201,6 +216,9 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   if (threadIdx.x == 0) {
     s_stop = *(volatile int32_t*)&st->stop;
     s_gen = *(volatile int64_t*)&st->gen;
+    // DE/best/1: the lowest-index best of the current population (row 0
+    // when no fitness is finite)
+    s_best = max(*(volatile int32_t*)&st->best_idx, 0);
   }
   __syncthreads();
   if (s_stop) return;
@@ -219,8 +237,16 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
 
   // ---- trials (a warp per target)
-  for (int rl = warp; rl < nrows; rl += nwarps)
-    build_trial_row(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp);
+  const bool var = VAR && (R.strategy != 0 || R.jde);
+  const double* __restrict__ jFc = VAR && R.jde ? R.jF[cur] : nullptr;
+  const double* __restrict__ jCRc = VAR && R.jde ? R.jCR[cur] : nullptr;
+  if (var) {
+    for (int rl = warp; rl < nrows; rl += nwarps)
+      build_trial_row<true>(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp, s_best, jFc, jCRc);
+  } else {
+    for (int rl = warp; rl < nrows; rl += nwarps)
+      build_trial_row<false>(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp);
+  }
   __syncthreads();
 
   const int nout = nrows * d;
@@ -303,6 +329,13 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
     double2* dst = reinterpret_cast<double2*>(Xn + (size_t)i * dp);
     for (int j = lane; j < dp / 2; j += 32) dst[j] = reinterpret_cast<const double2*>(src)[j];
     const double fnew = acc ? ft : fi;
+    if (VAR && R.jde && lane == 0) {
+      // jDE: an accepted trial passes its F_i and CR_i on
+      double Fi = jFc[i], CRi = jCRc[i];
+      if (acc) jde_params(R, (uint32_t)i, g, jFc, jCRc, Fi, CRi);
+      R.jF[nxt][i] = Fi;
+      R.jCR[nxt][i] = CRi;
+    }
     if (lane == 0) {
       fn[i] = fnew;
       if (R.dbg_ftrial) {
@@ -337,11 +370,14 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
 namespace de {
 
 void k_configure(size_t smem_gen) {
-  cudaFuncSetAttribute(k_gen_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem_gen, 1));
+  cudaFuncSetAttribute(k_gen_fp64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)std::max<size_t>(smem_gen, 1));
+  cudaFuncSetAttribute(k_gen_fp64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)std::max<size_t>(smem_gen, 1));
   cudaFuncSetAttribute(k_eval_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
+void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem, bool var,
                        cudaStream_t s) {
   // programmatic stream serialization: generation g + 1 is scheduled while
   // generation g drains, and waits (griddepcontrol.wait) before reading it
@@ -355,7 +391,8 @@ void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int t
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_gen_fp64, runs, items);
+  if (var) cudaLaunchKernelEx(&cfg, k_gen_fp64<true>, runs, items);
+  else cudaLaunchKernelEx(&cfg, k_gen_fp64<false>, runs, items);
 }
 
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s) {
@@ -375,6 +412,10 @@ void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t l
 }
 
 void k_best_init_launch(const RunDesc* runs, int run, cudaStream_t s) { k_best_init<<<1, 256, 0, s>>>(runs, run); }
+
+void k_jde_init_launch(const RunDesc* runs, int run, int np, cudaStream_t s) {
+  k_jde_init<<<(np + 255) / 256, 256, 0, s>>>(runs, run);
+}
 
 void k_ode_reference_launch(const RunDesc* runs, int run, double* ref, cudaStream_t s) {
   k_ode_reference<<<1, 32, 0, s>>>(runs, run, ref);

@@ -12,6 +12,7 @@
 //   Bsplit   tensor-core operand copies of M (split precisions only)
 //   state    one RunState (generation, evaluations, best record, stop flag)
 //   part     one BestPartial per row tile of the generation kernel
+//   jF, jCR  [2] np doubles each (jDE only), the control parameters of X[0] / X[1]
 // A batch of runs is a table of RunDesc in device memory plus a flat list of
 // (run, tile) work items; one launch covers every tile of every run.
 #pragma once
@@ -65,6 +66,10 @@ struct RunDesc {
   int32_t nw;    // ceil(d / 32)
   int32_t dbuf;  // 1: generation g lives in X[g & 1]; 0: the split kernels update X[0] in place
   int32_t pad1;
+  int32_t strategy;  // de_strategy (FP64 path): 0 rand/1/bin, 1 best/1/bin, 2 rand/1/exp
+  int32_t jde;       // 1: per-individual F and CR in jF / jCR (jDE)
+  double* jF[2];     // jDE: np values of F_i for X[0] / X[1]
+  double* jCR[2];    // jDE: np values of CR_i
   // buffers
   double* X[2];
   double* f[2];

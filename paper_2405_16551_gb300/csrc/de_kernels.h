@@ -14,12 +14,14 @@ void set_last_error(const std::string& m);
 
 // FP64 path (de_fp64.cu)
 void k_configure(size_t smem_gen);
-void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
+// var: some run uses a strategy variant or jDE
+void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem, bool var,
                        cudaStream_t s);
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s);
 void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int rotate,
                         double* f, uint8_t* fx, cudaStream_t s);
 void k_best_init_launch(const RunDesc* runs, int run, cudaStream_t s);
+void k_jde_init_launch(const RunDesc* runs, int run, int np, cudaStream_t s);
 void k_ode_reference_launch(const RunDesc* runs, int run, double* ref, cudaStream_t s);
 
 // persistent cluster path (de_persist.cu)

@@ -58,6 +58,8 @@ def test_version_and_status_strings():
         (dict(np_=64, d=10, objective=4), "d = 20"),
         (dict(np_=64, d=20, objective=4, precision=2), "FP64 only"),
         (dict(np_=64, d=20, objective=4, rot=np.eye(20)), "no rotation"),
+        (dict(np_=64, d=10, strategy=3), "strategy"),
+        (dict(np_=64, d=10, strategy=-1), "strategy"),
     ],
 )
 def test_invalid_config_rejected_on_host(kw, msg):
@@ -66,6 +68,24 @@ def test_invalid_config_rejected_on_host(kw, msg):
         capi.de_init(cfg)
     assert ei.value.status == capi.DE_ERR_INVALID_ARG
     assert msg in str(ei.value)
+
+
+@pytest.mark.parametrize(
+    "kw",
+    [
+        dict(strategy=capi.DE_BEST1BIN, precision=capi.DE_PREC_BF16X3),
+        dict(strategy=capi.DE_RAND1EXP, precision=capi.DE_PREC_TF32X3),
+        dict(jde=True, precision=capi.DE_PREC_BF16X3),
+        dict(jde=True, surrogate_k=4),
+        dict(strategy=capi.DE_BEST1BIN, surrogate_k=8),
+    ],
+)
+def test_variants_outside_the_fp64_path_are_unsupported_on_host(kw):
+    cfg = capi.make_config(64, 20, **kw)
+    with pytest.raises(capi.DEError) as ei:
+        capi.de_init(cfg)
+    assert ei.value.status == capi.DE_ERR_UNSUPPORTED
+    assert "FP64" in str(ei.value)
 
 
 def test_null_arguments_rejected():
