@@ -58,7 +58,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
-    p.add_argument("--workload", default="rastrigin", choices=["rastrigin", "sphere_small", "batch512", "ode_surrogate", "stress", "stress_batch"],
+    p.add_argument("--workload", default="rastrigin",
+                   choices=["rastrigin", "sphere_small", "batch512", "ode_surrogate", "stress", "stress_batch",
+                            "variants"],
                    help="rastrigin: the headline configuration (default); the others measure the batched, "
                         "surrogate and large-dimension configurations with the same harness")
     return p.parse_args()
@@ -486,6 +488,29 @@ def run_workload(args, capi, torch, rank, world):
                     value=ev / tm, ms_per_step=1e3 * tm / 3, dtype="f64 objective, bf16 surrogate",
                     config={"workload": "ODE fit, 3 seeds, plain DE and surrogate k = 8, budget 2e5 true evaluations"},
                     runs=res, gpu_launches=None)
+    elif args.workload == "variants":
+        # the strategy variants and jDE on the FP64 path: rotated Rastrigin
+        # NP = 1024, D = 100, reset + G generations per step, and the best f
+        # each reaches after G generations
+        G = min(args.generations, 1000)
+        n, d = 1024, 100
+        o, M = problems.shift(d, seed=1), problems.rotation(d, seed=1)
+        forms = {}
+        for name, st, jde in (("rand1bin", 0, False), ("best1bin", 1, False), ("rand1exp", 2, False),
+                              ("jde_rand1bin", 0, True), ("jde_rand1exp", 2, True)):
+            c = capi.make_config(n, d, objective=1, shift=o, rot=M, seed=1, target_error=0.0, max_generations=G,
+                                 strategy=st, jde=jde)
+            h = capi.de_init(c, stream=stream.cuda_stream)
+            ms = _timed(torch, stream, flush, steps, warmup, lambda: (capi.de_reset(h), capi.de_step(h, G)))
+            b = capi.de_get_best(h)
+            capi.de_destroy(h)
+            forms[name] = {"trial_evals_per_s": n * G * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                           "us_per_generation": 1e3 * ms / steps / G, "best_f_after": b["best_f"]}
+        line.update(metric="trial evals/sec, NP=1024 D=100 rotated-shifted Rastrigin FP64, per DE variant",
+                    value=forms["jde_rand1bin"]["trial_evals_per_s"], ms_per_step=forms["jde_rand1bin"]["ms_per_step"],
+                    dtype="f64", config={"workload": f"NP=1024 D=100 Rastrigin, {G} generations per step, FP64",
+                                         "l2": "flushed between steps (512 MiB write)"},
+                    forms=forms, gpu_launches=steps * 5 * (3 + G))
     elif args.workload == "stress_batch":
         # 64 runs of the large-dimension shape in one handle (working set far above L2)
         G = min(args.generations, 10)
