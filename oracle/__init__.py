@@ -6,7 +6,7 @@ package.  The product library never imports it, never links it, and shares no
 code with it; it exists to check the CUDA path.
 
 The arithmetic lives in plain C (``de_oracle.c``, ``de_oracle_ode.c``,
-``de_oracle_mlp.c``), compiled with gcc on first use (or by ``build()``) and
+``de_oracle_mlp.c``, ``de_oracle_suite.c``), compiled with gcc on first use (or by ``build()``) and
 called through ctypes.  This module only marshals numpy arrays.
 
 Parity pins for every function are in ``tests/test_oracle_*.py``.
@@ -21,7 +21,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["de_oracle.c", "de_oracle_ode.c", "de_oracle_mlp.c"]
+_SOURCES = ["de_oracle.c", "de_oracle_ode.c", "de_oracle_mlp.c", "de_oracle_suite.c"]
 _LIB_PATH = os.path.join(_HERE, "_build", "libde_oracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -72,6 +72,18 @@ def _load():
         lib.or_objective.restype = ctypes.c_double
         lib.or_eval.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp,
                                 ctypes.c_int64, ctypes.c_int, _dp, _dp, ctypes.c_int]
+        lib.or_eval_p.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _i32p, _dp,
+                                  ctypes.c_int64, ctypes.c_int, _dp, _dp, ctypes.c_int]
+        lib.or_objective_p.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _i32p, _dp, _dp]
+        lib.or_objective_p.restype = ctypes.c_double
+        lib.or_basic.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        lib.or_basic.restype = ctypes.c_double
+        lib.or_domain_scale.argtypes = [ctypes.c_int]
+        lib.or_domain_scale.restype = ctypes.c_double
+        lib.or_hybrid_segments.argtypes = [ctypes.c_int, ctypes.c_int, _i32p]
+        lib.or_hybrid_segments.restype = ctypes.c_int
+        lib.or_suite_components.argtypes = [ctypes.c_int]
+        lib.or_suite_components.restype = ctypes.c_int
         lib.or_init_population.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_uint64, ctypes.c_uint32, _dp]
         lib.or_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -83,12 +95,12 @@ def _load():
                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _i32p,
                                      _dp, _dp, _dp, _dp, _i32p, _i32p, _u32p, _dp, _dp, _dp, _u8p, ctypes.c_int]
         lib.or_step_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, _i32p, ctypes.c_double,
                                    ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _i32p, ctypes.c_int, ctypes.c_int,
                                    _dp, _dp, _dp, _dp,
                                    _dp, _dp, _dp, _dp, _i32p, _i32p, _u32p, _dp, _dp, _dp, _u8p, ctypes.c_int]
         lib.or_run_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, _i32p, ctypes.c_double,
                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                   ctypes.c_int64, ctypes.c_double, _dp, _dp, _dp, _dp, _i64p, _dp, ctypes.c_int]
         lib.or_run_ex.restype = ctypes.c_int64
@@ -132,6 +144,10 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _i32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
+
+
 # ----------------------------------------------------------------------------- RNG
 def philox4x32_10(ctr, key):
     c = np.asarray(ctr, dtype=np.uint32).copy()
@@ -164,14 +180,44 @@ def mutant_indices(w0, w1, w2, i, np_):
 
 
 # ----------------------------------------------------------------------------- objectives
-def objective(obj, x, o=None, M=None, scale=1.0):
+def objective(obj, x, o=None, M=None, scale=1.0, perm=None):
     """f(x) and the magnitude sum of its terms for one point."""
     x = _f64(x)
     d = x.shape[0]
     o, M = _f64(o), _f64(M)
     sabs = ctypes.c_double(0.0)
-    f = _load().or_objective(obj, d, _p(o), _p(M), scale, _p(x), ctypes.byref(sabs))
+    f = _load().or_objective_p(obj, d, _p(o), _p(M), scale, _p(_i32(perm), _i32p), _p(x), ctypes.byref(sabs))
     return f, sabs.value
+
+
+# ----------------------------------------------------------------------------- benchmark suite (Table 2)
+ZAKHAROV, SCHWEFEL, BENT_CIGAR, HGBAT, SCHAFFER_F6, KATSUURA, HAPPYCAT = 5, 6, 7, 8, 9, 10, 11
+GRIEWANK_ROSENBROCK, ELLIPTIC, GRIEWANK = 12, 13, 14
+HYBRID1, HYBRID2, HYBRID3, COMPOSITION1, COMPOSITION2, COMPOSITION3 = 15, 16, 17, 18, 19, 20
+
+
+def basic(fn, z, e=None):
+    """(g(z), tolerance scale) of basic function fn on the vector z."""
+    z = _f64(np.atleast_1d(z))
+    s = ctypes.c_double()
+    f = _load().or_basic(fn, z.shape[0], _p(z), _p(_f64(e)), ctypes.byref(s))
+    return f, s.value
+
+
+def domain_scale(fn):
+    return float(_load().or_domain_scale(fn))
+
+
+def hybrid_segments(obj, d):
+    """Start of every part of a hybrid function's split of d coordinates
+    (m + 1 entries), or None when some part would be empty."""
+    st = np.zeros(6, dtype=np.int32)
+    m = _load().or_hybrid_segments(obj, d, _p(st, _i32p))
+    return None if m == 0 else st[: m + 1].copy()
+
+
+def suite_components(obj):
+    return int(_load().or_suite_components(obj))
 
 
 # ----------------------------------------------------------------------------- ODE objective
@@ -242,13 +288,14 @@ def adam(w, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     _load().or_adam(w.size, _p(w), _p(_f64(g)), _p(m), _p(v), step, lr, beta1, beta2, eps)
 
 
-def evaluate(obj, X, o=None, M=None, scale=1.0, threads=1):
+def evaluate(obj, X, o=None, M=None, scale=1.0, threads=1, perm=None):
     """f and magnitude sums for every row of X."""
     X = _f64(X)
     n, d = X.shape
     f = np.zeros(n)
     sabs = np.zeros(n)
-    _load().or_eval(obj, d, _p(_f64(o)), _p(_f64(M)), scale, _p(X), d, n, _p(f), _p(sabs), threads)
+    _load().or_eval_p(obj, d, _p(_f64(o)), _p(_f64(M)), scale, _p(_i32(perm), _i32p), _p(X), d, n, _p(f), _p(sabs),
+                      threads)
     return f, sabs
 
 
@@ -263,7 +310,7 @@ STRATEGIES = {"rand1bin": 0, "best1bin": 1, "rand1exp": 2}
 
 
 def step(X, fX, F, CR, lo, hi, obj, o, M, seed, generation, run_id=0, scale=1.0, threads=1, cand=None,
-         strategy=0, jde=False, jF=None, jCR=None):
+         strategy=0, jde=False, jF=None, jCR=None, perm=None):
     """One synchronous generation; returns a dict with the next population and
     every intermediate (indices, j_rand (the crossover start for exp),
     crossover mask, trials, f_trial, magnitude sums, accept flags).  cand:
@@ -287,7 +334,8 @@ def step(X, fX, F, CR, lo, hi, obj, o, M, seed, generation, run_id=0, scale=1.0,
         jCRa = np.full(np_, CR) if jCR is None else _f64(jCR)
         out["F_next"] = np.zeros(np_)
         out["CR_next"] = np.zeros(np_)
-    _load().or_step_ex(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), scale, seed, run_id, generation,
+    _load().or_step_ex(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), _p(_i32(perm), _i32p), scale, seed,
+                    run_id, generation,
                     _p(cnd, _i32p), int(strategy), 1 if jde else 0, _p(jFa), _p(jCRa),
                     _p(out.get("F_next")), _p(out.get("CR_next")), _p(X), _p(fX), _p(out["X_next"]), _p(out["f_next"]), _p(out["idx"], _i32p),
                     _p(out["jrand"], _i32p), _p(out["mask"], _u32p), _p(out["trial"]), _p(out["f_trial"]),
@@ -301,7 +349,7 @@ def best(f):
 
 
 def run(np_, d, F, CR, lo, hi, obj, o, M, seed, max_generations, max_evals=0, target_error=1e-8,
-        run_id=0, scale=1.0, threads=1, trace=False, strategy=0, jde=False, return_adaptive=False):
+        run_id=0, scale=1.0, threads=1, trace=False, strategy=0, jde=False, return_adaptive=False, perm=None):
     """A whole run; returns (X, f, generations, evals, best_trace or None),
     and (F_i, CR_i) after them when return_adaptive (jde)."""
     X = np.zeros((np_, d))
@@ -310,7 +358,8 @@ def run(np_, d, F, CR, lo, hi, obj, o, M, seed, max_generations, max_evals=0, ta
     jCR = np.zeros(np_)
     ev = ctypes.c_int64(0)
     tr = np.full(max_generations + 1, np.nan) if trace else None
-    g = _load().or_run_ex(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), scale, seed, run_id, int(strategy),
+    g = _load().or_run_ex(np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)), _p(_i32(perm), _i32p), scale, seed,
+                          run_id, int(strategy),
                           1 if jde else 0, max_generations, max_evals, target_error, _p(X), _p(f), _p(jF), _p(jCR),
                           ctypes.byref(ev), _p(tr), threads)
     res = (X, f, int(g), int(ev.value), (tr[: g + 1] if trace else None))

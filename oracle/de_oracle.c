@@ -111,9 +111,15 @@ enum { OR_SPHERE = 0, OR_RASTRIGIN = 1, OR_ROSENBROCK = 2, OR_ACKLEY = 3, OR_ODE
  * vector, d must be 20, M and scale do not apply. */
 double or_ode_objective_s(const double* x, const double* x_hat, int steps, double dt, double* sabs);
 
-double or_objective(int obj, int d, const double* o, const double* M, double scale,
-                    const double* x, double* sabs)
+/* The benchmark suite's objectives 5..20 (de_oracle_suite.c). */
+double or_suite_objective(int obj, int d, const double* o, const double* M, double scale, const int32_t* perm,
+                          const double* x, double* sabs);
+
+/* perm: the hybrid functions' permutation (d indices), NULL elsewhere. */
+double or_objective_p(int obj, int d, const double* o, const double* M, double scale, const int32_t* perm,
+                      const double* x, double* sabs)
 {
+    if (obj >= 5 && obj <= 20) return or_suite_objective(obj, d, o, M, scale, perm, x, sabs);
     if (obj == OR_ODE) {
         static const double zero[20] = {0};
         if (d != 20) {
@@ -199,9 +205,15 @@ double or_objective(int obj, int d, const double* o, const double* M, double sca
     return f;
 }
 
+double or_objective(int obj, int d, const double* o, const double* M, double scale,
+                    const double* x, double* sabs)
+{
+    return or_objective_p(obj, d, o, M, scale, NULL, x, sabs);
+}
+
 /* n rows of x (row stride ld) -> f[n] (and sabs[n] if not NULL). */
-void or_eval(int obj, int d, const double* o, const double* M, double scale,
-             const double* x, int64_t ld, int n, double* f, double* sabs, int threads)
+void or_eval_p(int obj, int d, const double* o, const double* M, double scale, const int32_t* perm,
+               const double* x, int64_t ld, int n, double* f, double* sabs, int threads)
 {
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(threads > 0 ? threads : 1) schedule(static)
@@ -210,9 +222,15 @@ void or_eval(int obj, int d, const double* o, const double* M, double scale,
 #endif
     for (int i = 0; i < n; ++i) {
         double sa;
-        f[i] = or_objective(obj, d, o, M, scale, x + (size_t)i * (size_t)ld, &sa);
+        f[i] = or_objective_p(obj, d, o, M, scale, perm, x + (size_t)i * (size_t)ld, &sa);
         if (sabs) sabs[i] = sa;
     }
+}
+
+void or_eval(int obj, int d, const double* o, const double* M, double scale,
+             const double* x, int64_t ld, int n, double* f, double* sabs, int threads)
+{
+    or_eval_p(obj, d, o, M, scale, NULL, x, ld, n, f, sabs, threads);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -303,7 +321,7 @@ int or_best(int np, const double* f);
  * candidate trials that a surrogate screens (the same construction with
  * independent draws). */
 void or_step_ex(int np, int d, double F, double CR, double lo, double hi,
-                int obj, const double* o, const double* M, double scale,
+                int obj, const double* o, const double* M, const int32_t* perm, double scale,
                 uint64_t seed, uint32_t run_id, uint32_t generation, const int32_t* cand,
                 int strategy, int jde, const double* jF, const double* jCR, double* jFn, double* jCRn,
                 const double* X, const double* fX, double* Xn, double* fXn,
@@ -386,7 +404,7 @@ void or_step_ex(int np, int d, double F, double CR, double lo, double hi,
     }
 
     /* evaluate the trial population (Sec. 7.3.1) */
-    or_eval(obj, d, o, M, scale, trial, d, np, ft, sa, threads);
+    or_eval_p(obj, d, o, M, scale, perm, trial, d, np, ft, sa, threads);
 
     /* greedy selection: the trial replaces the target when it is no worse
        (ties go to the trial); a NaN trial never replaces */
@@ -417,7 +435,7 @@ void or_step_cand(int np, int d, double F, double CR, double lo, double hi,
                   int32_t* idx, int32_t* jrand_out, uint32_t* mask, double* trial_out,
                   double* ftrial_out, double* sabs_out, uint8_t* accept_out, int threads)
 {
-    or_step_ex(np, d, F, CR, lo, hi, obj, o, M, scale, seed, run_id, generation, cand, 0, 0, NULL, NULL, NULL,
+    or_step_ex(np, d, F, CR, lo, hi, obj, o, M, NULL, scale, seed, run_id, generation, cand, 0, 0, NULL, NULL, NULL,
                NULL, X, fX, Xn, fXn, idx, jrand_out, mask, trial_out, ftrial_out, sabs_out, accept_out, threads);
 }
 
@@ -454,7 +472,7 @@ int or_best(int np, const double* f)
 /* Returns the number of generations run.                                     */
 /* ------------------------------------------------------------------------- */
 int64_t or_run_ex(int np, int d, double F, double CR, double lo, double hi,
-                  int obj, const double* o, const double* M, double scale,
+                  int obj, const double* o, const double* M, const int32_t* perm, double scale,
                   uint64_t seed, uint32_t run_id, int strategy, int jde,
                   int64_t max_generations, int64_t max_evals, double target_error,
                   double* X, double* fX, double* jF, double* jCR, int64_t* evals_out, double* best_trace, int threads)
@@ -468,7 +486,7 @@ int64_t or_run_ex(int np, int d, double F, double CR, double lo, double hi,
         jCR[i] = CR;
     }
     or_init_population(np, d, lo, hi, seed, run_id, X);
-    or_eval(obj, d, o, M, scale, X, d, np, fX, NULL, threads);
+    or_eval_p(obj, d, o, M, scale, perm, X, d, np, fX, NULL, threads);
     int64_t evals = np;
     int64_t g = 0;
     int b = or_best(np, fX);
@@ -479,7 +497,7 @@ int64_t or_run_ex(int np, int d, double F, double CR, double lo, double hi,
         if (max_evals > 0 && evals >= max_evals) break;
         if (g >= max_generations) break;
         g += 1;
-        or_step_ex(np, d, F, CR, lo, hi, obj, o, M, scale, seed, run_id, (uint32_t)g, NULL, strategy, jde, jF, jCR,
+        or_step_ex(np, d, F, CR, lo, hi, obj, o, M, perm, scale, seed, run_id, (uint32_t)g, NULL, strategy, jde, jF, jCR,
                    jFn, jCRn, X, fX, Xn, fn, NULL, NULL, NULL, NULL, NULL, NULL, NULL, threads);
         memcpy(X, Xn, sizeof(double) * (size_t)np * (size_t)d);
         memcpy(fX, fn, sizeof(double) * (size_t)np);
@@ -504,6 +522,6 @@ int64_t or_run(int np, int d, double F, double CR, double lo, double hi,
                int64_t max_generations, int64_t max_evals, double target_error,
                double* X, double* fX, int64_t* evals_out, double* best_trace, int threads)
 {
-    return or_run_ex(np, d, F, CR, lo, hi, obj, o, M, scale, seed, run_id, 0, 0, max_generations, max_evals,
+    return or_run_ex(np, d, F, CR, lo, hi, obj, o, M, NULL, scale, seed, run_id, 0, 0, max_generations, max_evals,
                      target_error, X, fX, NULL, NULL, evals_out, best_trace, threads);
 }
