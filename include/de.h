@@ -80,13 +80,71 @@ typedef enum {
  *               q(0) = e_1, p(0) = 0.
  *               f = mean over steps and masses of (q - q_o)^2, where q_o is
  *               the trajectory of the hidden parameter vector, passed as
- *               the shift o; f(o) = 0 exactly. */
+ *               the shift o; f(o) = 0 exactly.
+ *
+ * The benchmark the paper proposes for GPU DEs (Sec. 7.3, Table 2; FP64
+ * only).  Basic functions of z (same shift / scale / rotation as above; each
+ * is 0 at z = 0; n the dimension, i = 1..n):
+ *   ZAKHAROV    sum z_i^2 + (sum 0.5 i z_i)^2 + (sum 0.5 i z_i)^4
+ *   SCHWEFEL    modified Schwefel: 418.9828872724338 n - sum g(z_i + 420.9687462275036),
+ *               g(t) = t sin sqrt|t| on [-500, 500]; beyond, with m = fmod(|t|, 500),
+ *               g = +-(500 - m) sin sqrt(500 - m) - (|t| - 500)^2 / (10^4 n)
+ *   BENT_CIGAR  z_1^2 + 10^6 sum_{i>=2} z_i^2
+ *   HGBAT       |a^2 - b^2|^(1/2) + (0.5 a + b)/n + 0.5,  a = sum x_i^2, b = sum x_i, x = z - 1
+ *   SCHAFFER_F6 expanded: sum over the cyclic pairs (z_i, z_{i+1}) of
+ *               0.5 + (sin^2 sqrt(s) - 0.5) / (1 + 0.001 s)^2, s = u^2 + v^2
+ *   KATSUURA    (10/n^2) prod_i (1 + i sum_{j=1}^{32} |2^j z_i - round(2^j z_i)| / 2^j)^(10/n^1.2) - 10/n^2
+ *   HAPPYCAT    |a - n|^(1/4) + (0.5 a + b)/n + 0.5 (a, b as HGBAT)
+ *   GRIEWANK_ROSENBROCK  expanded: sum over the cyclic pairs of G(100 (u^2 - v)^2 + (u - 1)^2),
+ *               (u, v) = (z_i + 1, z_{i+1} + 1), G(r) = r^2/4000 - cos r + 1
+ *   ELLIPTIC    sum (10^6)^((i-1)/(n-1)) z_i^2
+ *   GRIEWANK    sum z_i^2 / 4000 - prod cos(z_i / sqrt i) + 1
+ * Hybrid functions (Sec. 7.3.2): z = M ((x - o) scale) is permuted by
+ * de_config.perm (NULL: identity) and split into parts of ceil(p_k d)
+ * coordinates (the last part takes the rest); part k, multiplied by its
+ * function's domain scale, is evaluated by that function as an
+ * n_k-dimensional one, and f is the sum.
+ *   HYBRID1  Bent Cigar, HGBat, Rastrigin;                   p = 0.3, 0.3, 0.4
+ *   HYBRID2  Schaffer F6, HGBat, Rosenbrock, Schwefel;       p = 0.2, 0.2, 0.3, 0.3
+ *   HYBRID3  Katsuura, HappyCat, Griewank-Rosenbrock, Schwefel, Ackley; p = 0.3, 0.2, 0.2, 0.1, 0.2
+ * Composition functions (Sec. 7.3.3): n components, each with its own shift
+ * o_c and rotation M_c (de_config.shift holds n*d values, de_config.rot n
+ * row-major d*d matrices):
+ *   f = sum_c omega_c (lambda_c g_c(M_c ((x - o_c) s_c)) + bias_c),
+ *   omega_c = w_c / sum w,  w_c = exp(-D_c / (2 d sigma_c^2)) / sqrt(D_c),  D_c = |x - o_c|^2
+ * (omega_c = 1 for the first c with x = o_c).  s_c is the component's domain
+ * scale; de_config.scale must be 1.
+ *   COMPOSITION1  Rastrigin, Griewank, Schwefel; sigma 10, 20, 30; lambda 1, 10, 1; bias 0, 100, 200
+ *   COMPOSITION2  Ackley, Elliptic, Griewank, Rastrigin; sigma 10, 20, 30, 40;
+ *                 lambda 10, 1e-6, 10, 1; bias 0, 100, 200, 300
+ *   COMPOSITION3  Schaffer F6, Schwefel, Griewank, Rosenbrock, Rastrigin; sigma 10, 20, 20, 30, 40;
+ *                 lambda 0.005, 1, 10, 1, 10; bias 0, 100, 200, 300, 400
+ * Domain scales inside hybrid and composition functions: Rastrigin 5.12/100,
+ * Rosenbrock 2.048/100, Schwefel 1000/100, Griewank 600/100, HGBat,
+ * HappyCat, Katsuura and Griewank-Rosenbrock 5/100, the others 1.  The
+ * stand-alone basic functions take de_config.scale instead. */
 typedef enum {
     DE_OBJ_SPHERE = 0,
     DE_OBJ_RASTRIGIN = 1,
     DE_OBJ_ROSENBROCK = 2,
     DE_OBJ_ACKLEY = 3,
-    DE_OBJ_ODE = 4
+    DE_OBJ_ODE = 4,
+    DE_OBJ_ZAKHAROV = 5,
+    DE_OBJ_SCHWEFEL = 6,
+    DE_OBJ_BENT_CIGAR = 7,
+    DE_OBJ_HGBAT = 8,
+    DE_OBJ_SCHAFFER_F6 = 9,
+    DE_OBJ_KATSUURA = 10,
+    DE_OBJ_HAPPYCAT = 11,
+    DE_OBJ_GRIEWANK_ROSENBROCK = 12,
+    DE_OBJ_ELLIPTIC = 13,
+    DE_OBJ_GRIEWANK = 14,
+    DE_OBJ_HYBRID1 = 15,
+    DE_OBJ_HYBRID2 = 16,
+    DE_OBJ_HYBRID3 = 17,
+    DE_OBJ_COMPOSITION1 = 18,
+    DE_OBJ_COMPOSITION2 = 19,
+    DE_OBJ_COMPOSITION3 = 20
 } de_objective;
 
 /* Arithmetic of the rotation z = M y and of the objective terms.
@@ -119,8 +177,10 @@ typedef struct {
     double lo, hi;            /* box bounds, finite, lo < hi; the paper's range is [-100, 100] */
     int32_t objective;        /* de_objective */
     double scale;             /* y = (x - o) * scale; 1.0 keeps the search range (Sec. 7.3.1) */
-    const double* shift;      /* host, d values of o, or NULL for o = 0; copied by de_init */
-    const double* rot;        /* host, d*d row-major M (z = M y), or NULL for no rotation; copied */
+    const double* shift;      /* host, d values of o (composition functions: n*d, one row per
+                                 component), or NULL for o = 0; copied by de_init */
+    const double* rot;        /* host, d*d row-major M (z = M y; composition functions: n such
+                                 matrices), or NULL for no rotation; copied */
     uint64_t seed;            /* Philox key */
     uint32_t run_id;          /* Philox stream id, < 2^20; distinct runs of one seed differ here */
     int32_t precision;        /* de_precision */
@@ -137,6 +197,9 @@ typedef struct {
                                  for values other than DE_RAND1BIN */
     int32_t jde;              /* nonzero: jDE self-adaptive F and CR per individual (Sec. 2, the adaptive
                                  variant); f and cr are the initial values; FP64 only */
+    const int32_t* perm;      /* host, d indices: the permutation of a hybrid function (position k of the
+                                 permuted vector is z[perm[k]]), or NULL for the identity; must be NULL
+                                 for other objectives; copied by de_init */
 } de_config;
 
 /* Trial-construction strategies (Sec. 2 names the variants by base vector,

@@ -19,6 +19,10 @@ from . import build as _build
 DE_OK, DE_ERR_INVALID_ARG, DE_ERR_CUDA, DE_ERR_OOM, DE_ERR_TIMEOUT = 0, 1, 2, 3, 4
 DE_ERR_NONFINITE, DE_ERR_STATE, DE_ERR_IO, DE_ERR_UNSUPPORTED = 5, 6, 7, 8
 DE_OBJ_SPHERE, DE_OBJ_RASTRIGIN, DE_OBJ_ROSENBROCK, DE_OBJ_ACKLEY, DE_OBJ_ODE = 0, 1, 2, 3, 4
+DE_OBJ_ZAKHAROV, DE_OBJ_SCHWEFEL, DE_OBJ_BENT_CIGAR, DE_OBJ_HGBAT, DE_OBJ_SCHAFFER_F6 = 5, 6, 7, 8, 9
+DE_OBJ_KATSUURA, DE_OBJ_HAPPYCAT, DE_OBJ_GRIEWANK_ROSENBROCK, DE_OBJ_ELLIPTIC, DE_OBJ_GRIEWANK = 10, 11, 12, 13, 14
+DE_OBJ_HYBRID1, DE_OBJ_HYBRID2, DE_OBJ_HYBRID3 = 15, 16, 17
+DE_OBJ_COMPOSITION1, DE_OBJ_COMPOSITION2, DE_OBJ_COMPOSITION3 = 18, 19, 20
 DE_PREC_FP64, DE_PREC_BF16X3, DE_PREC_TF32X3 = 0, 1, 2
 DE_STOP_NONE, DE_STOP_TARGET, DE_STOP_EVALS, DE_STOP_GENERATIONS = 0, 1, 2, 3
 DE_BAND_NEAR, DE_BAND_ALL = 0, 1
@@ -39,7 +43,8 @@ class de_config(ctypes.Structure):
                 ("run_id", ctypes.c_uint32), ("precision", ctypes.c_int32), ("target_error", ctypes.c_double),
                 ("max_evals", ctypes.c_int64), ("max_generations", ctypes.c_int64),
                 ("debug_capture", ctypes.c_int32), ("fp64_band", ctypes.c_int32), ("surrogate_k", ctypes.c_int32),
-                ("surrogate_steps", ctypes.c_int32), ("strategy", ctypes.c_int32), ("jde", ctypes.c_int32)]
+                ("surrogate_steps", ctypes.c_int32), ("strategy", ctypes.c_int32), ("jde", ctypes.c_int32),
+                ("perm", _i32p)]
 
 
 class de_result(ctypes.Structure):
@@ -164,7 +169,7 @@ def de_version() -> str:
 def make_config(np_, d, f=0.5, cr=0.9, lo=-100.0, hi=100.0, objective=DE_OBJ_SPHERE, scale=1.0, shift=None,
                 rot=None, seed=1, run_id=0, precision=DE_PREC_FP64, target_error=1e-8, max_evals=0,
                 max_generations=1000, debug_capture=False, fp64_band=DE_BAND_NEAR, surrogate_k=0,
-                surrogate_steps=0, strategy=DE_RAND1BIN, jde=False):
+                surrogate_steps=0, strategy=DE_RAND1BIN, jde=False, perm=None):
     """A de_config; the returned object keeps the shift/rotation arrays alive."""
     c = de_config()
     c.np, c.d, c.f, c.cr, c.lo, c.hi = np_, d, f, cr, lo, hi
@@ -183,6 +188,10 @@ def make_config(np_, d, f=0.5, cr=0.9, lo=-100.0, hi=100.0, objective=DE_OBJ_SPH
         m = np.ascontiguousarray(rot, dtype=np.float64)
         keep.append(m)
         c.rot = _p(m)
+    if perm is not None:
+        pm = np.ascontiguousarray(perm, dtype=np.int32)
+        keep.append(pm)
+        c.perm = _p(pm, _i32p)
     c._keep = keep
     return c
 

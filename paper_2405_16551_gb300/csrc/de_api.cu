@@ -45,6 +45,7 @@ struct de_handle {
   int graph_gens = 0;
   Surrogate* surr = nullptr;  // surrogate-assisted generations (surrogate_k >= 2)
   bool variants = false;      // some run uses a strategy variant or jDE
+  bool suite = false;         // some run uses an objective of the proposed benchmark (5..20)
   std::string err;
 };
 
@@ -81,6 +82,78 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 
 
+// ---------------------------------------------------------------- benchmark suite
+// Functions of the proposed benchmark (Table 2) built from several basic
+// functions: hybrid parts (share of the coordinates in percent) or
+// composition components (sigma, lambda, bias).
+struct SuiteSpec {
+  int kind;  // 0 basic, 1 hybrid, 2 composition
+  int n;
+  int fn[5];
+  int pct[5];
+  double sigma[5], lambda[5], bias[5];
+};
+
+static SuiteSpec suite_spec(int obj) {
+  switch (obj) {
+    case DE_OBJ_HYBRID1:
+      return {1, 3, {DE_OBJ_BENT_CIGAR, DE_OBJ_HGBAT, DE_OBJ_RASTRIGIN}, {30, 30, 40}, {}, {}, {}};
+    case DE_OBJ_HYBRID2:
+      return {1, 4, {DE_OBJ_SCHAFFER_F6, DE_OBJ_HGBAT, DE_OBJ_ROSENBROCK, DE_OBJ_SCHWEFEL}, {20, 20, 30, 30}, {}, {}, {}};
+    case DE_OBJ_HYBRID3:
+      return {1, 5,
+              {DE_OBJ_KATSUURA, DE_OBJ_HAPPYCAT, DE_OBJ_GRIEWANK_ROSENBROCK, DE_OBJ_SCHWEFEL, DE_OBJ_ACKLEY},
+              {30, 20, 20, 10, 20}, {}, {}, {}};
+    case DE_OBJ_COMPOSITION1:
+      return {2, 3, {DE_OBJ_RASTRIGIN, DE_OBJ_GRIEWANK, DE_OBJ_SCHWEFEL}, {}, {10, 20, 30}, {1, 10, 1}, {0, 100, 200}};
+    case DE_OBJ_COMPOSITION2:
+      return {2, 4, {DE_OBJ_ACKLEY, DE_OBJ_ELLIPTIC, DE_OBJ_GRIEWANK, DE_OBJ_RASTRIGIN}, {}, {10, 20, 30, 40},
+              {10, 1e-6, 10, 1}, {0, 100, 200, 300}};
+    case DE_OBJ_COMPOSITION3:
+      return {2, 5, {DE_OBJ_SCHAFFER_F6, DE_OBJ_SCHWEFEL, DE_OBJ_GRIEWANK, DE_OBJ_ROSENBROCK, DE_OBJ_RASTRIGIN}, {},
+              {10, 20, 20, 30, 40}, {0.005, 1, 10, 1, 10}, {0, 100, 200, 300, 400}};
+    default:
+      return {0, 1, {obj}, {100}, {}, {}, {}};
+  }
+}
+
+// [-100, 100] mapped onto a basic function's customary domain inside hybrid
+// and composition functions
+static double suite_domain_scale(int fn) {
+  switch (fn) {
+    case DE_OBJ_RASTRIGIN: return 5.12 / 100.0;
+    case DE_OBJ_ROSENBROCK: return 2.048 / 100.0;
+    case DE_OBJ_SCHWEFEL: return 1000.0 / 100.0;
+    case DE_OBJ_GRIEWANK: return 600.0 / 100.0;
+    case DE_OBJ_HGBAT:
+    case DE_OBJ_HAPPYCAT:
+    case DE_OBJ_KATSUURA:
+    case DE_OBJ_GRIEWANK_ROSENBROCK: return 5.0 / 100.0;
+    default: return 1.0;
+  }
+}
+
+// Hybrid split: parts 0..n-2 take ceil(p d) coordinates (integer arithmetic
+// on the percentages), the last the rest; false when a part would be empty.
+static bool suite_segments(const SuiteSpec& sp, int d, int32_t seg[6]) {
+  seg[0] = 0;
+  int used = 0;
+  for (int q = 0; q + 1 < sp.n; ++q) {
+    used += (sp.pct[q] * d + 99) / 100;
+    seg[q + 1] = used;
+  }
+  seg[sp.n] = d;
+  for (int q = 0; q < sp.n; ++q)
+    if (seg[q + 1] - seg[q] < 1) return false;
+  return true;
+}
+
+// (shift, rotation) pairs a config carries: n for a composition function
+static int suite_pairs(int obj) {
+  const SuiteSpec sp = suite_spec(obj);
+  return sp.kind == 2 ? sp.n : 1;
+}
+
 static de_status validate(const de_config& c, int idx, std::string& why) {
   char b[256];
   auto bad = [&](const char* what) {
@@ -93,7 +166,23 @@ static de_status validate(const de_config& c, int idx, std::string& why) {
   if (!(c.f >= 0.0 && c.f <= 2.0)) return bad("F must be in [0, 2]");
   if (!(c.cr >= 0.0 && c.cr <= 1.0)) return bad("CR must be in [0, 1]");
   if (!std::isfinite(c.lo) || !std::isfinite(c.hi) || !(c.lo < c.hi)) return bad("bounds must be finite with lo < hi");
-  if (c.objective < DE_OBJ_SPHERE || c.objective > DE_OBJ_ODE) return bad("objective out of range");
+  if (c.objective < DE_OBJ_SPHERE || c.objective > DE_OBJ_COMPOSITION3) return bad("objective out of range");
+  if (c.objective >= DE_OBJ_ZAKHAROV) {
+    if (c.precision != DE_PREC_FP64) return bad("the benchmark suite's objectives run in FP64 only");
+    const SuiteSpec sp = suite_spec(c.objective);
+    int32_t seg[6];
+    if (sp.kind == 1 && !suite_segments(sp, c.d, seg)) return bad("d is too small for this hybrid function's parts");
+    if (sp.kind == 2 && c.scale != 1.0)
+      return bad("composition functions take scale 1 (each component has its own domain scale)");
+  }
+  if (c.perm) {
+    if (suite_spec(c.objective).kind != 1) return bad("perm applies to the hybrid functions only");
+    std::vector<char> seen(c.d, 0);
+    for (int j = 0; j < c.d; ++j) {
+      if (c.perm[j] < 0 || c.perm[j] >= c.d || seen[c.perm[j]]) return bad("perm is not a permutation of 0..d-1");
+      seen[c.perm[j]] = 1;
+    }
+  }
   if (c.objective == DE_OBJ_ODE) {
     if (c.d != 20) return bad("the ODE objective has d = 20 (stiffness and damping of 10 oscillators)");
     if (c.precision != DE_PREC_FP64) return bad("the ODE objective runs in FP64 only");
@@ -112,11 +201,12 @@ static de_status validate(const de_config& c, int idx, std::string& why) {
     if (c.d != 20) return bad("the surrogate network takes d = 20");
   }
   if (!std::isfinite(c.target_error) && !(c.target_error < 0)) return bad("target_error must be finite");
+  const int pairs = (c.objective >= DE_OBJ_SPHERE && c.objective <= DE_OBJ_COMPOSITION3) ? suite_pairs(c.objective) : 1;
   if (c.shift)
-    for (int j = 0; j < c.d; ++j)
+    for (size_t j = 0; j < (size_t)pairs * c.d; ++j)
       if (!std::isfinite(c.shift[j])) return bad("shift has a non-finite entry");
   if (c.rot)
-    for (size_t k = 0; k < (size_t)c.d * c.d; ++k)
+    for (size_t k = 0; k < (size_t)pairs * c.d * c.d; ++k)
       if (!std::isfinite(c.rot[k])) return bad("rotation has a non-finite entry");
   return DE_OK;
 }
@@ -167,7 +257,7 @@ static void drop_graph(de_handle* h) {
 // Enqueue one generation of every run (the kernels skip stopped runs).
 static de_status launch_generation(de_handle* h, cudaStream_t s) {
   if (h->prec == DE_PREC_FP64) {
-    k_gen_fp64_launch(h->d_run, h->d_items, h->nitems, h->threads, h->smem_gen, h->variants, s);
+    k_gen_fp64_launch(h->d_run, h->d_items, h->nitems, h->threads, h->smem_gen, h->variants, h->suite, s);
   } else {
     tc_generation_launch(h->tc, h->d_run, s);
   }
@@ -558,11 +648,15 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
   h->device = dev;
   h->nruns = nruns;
   h->prec = cfgs[0].precision;
-  for (int r = 0; r < nruns; ++r) h->variants = h->variants || cfgs[r].strategy != DE_RAND1BIN || cfgs[r].jde;
+  for (int r = 0; r < nruns; ++r) {
+    h->variants = h->variants || cfgs[r].strategy != DE_RAND1BIN || cfgs[r].jde;
+    h->suite = h->suite || cfgs[r].objective >= DE_OBJ_ZAKHAROV;
+  }
   h->cfg.assign(cfgs, cfgs + nruns);
   for (auto& c : h->cfg) {
     c.shift = nullptr;
     c.rot = nullptr;
+    c.perm = nullptr;
   }
   h->run.resize(nruns);
 
@@ -575,7 +669,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     return o;
   };
   struct Offs {
-    size_t X0, X1, f0, f1, fx0, fx1, o, MT, Mr, st, part, T, ref, jF0, jF1, jC0, jC1;
+    size_t X0, X1, f0, f1, fx0, fx1, o, MT, Mr, st, part, T, ref, jF0, jF1, jC0, jC1, perm;
     size_t dbg_idx, dbg_jrand, dbg_mask, dbg_trial, dbg_ftrial, dbg_accept, dbg_fp64, dbg_cand;
   };
   std::vector<Offs> offs(nruns);
@@ -591,8 +685,10 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     O.f1 = take(c.np * sizeof(double));
     O.fx0 = take(c.np);
     O.fx1 = take(c.np);
-    O.o = take(dp * sizeof(double));
-    O.MT = c.rot ? take((size_t)c.d * c.d * sizeof(double)) : 0;
+    const int pairs = suite_pairs(c.objective);
+    O.o = take((size_t)pairs * dp * sizeof(double));
+    O.MT = c.rot ? take((size_t)pairs * c.d * c.d * sizeof(double)) : 0;
+    O.perm = suite_spec(c.objective).kind == 1 ? take((size_t)c.d * sizeof(int32_t)) : 0;
     O.Mr = (c.rot && c.precision != DE_PREC_FP64) ? take((size_t)c.d * c.d * sizeof(double)) : 0;
     O.st = states_off + (size_t)r * sizeof(RunState);
     O.part = take((size_t)c.np * sizeof(BestPartial));
@@ -692,6 +788,21 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     if (c.objective == DE_OBJ_ODE) R.ode_ref = (const double*)(A + O.ref);
     R.strategy = c.strategy;
     R.jde = c.jde ? 1 : 0;
+    {
+      const SuiteSpec sp = suite_spec(c.objective);
+      R.nc = sp.n;
+      for (int q = 0; q < sp.n; ++q) {
+        R.sfn[q] = sp.fn[q];
+        R.sscale[q] = suite_domain_scale(sp.fn[q]);
+        R.ssigma[q] = sp.sigma[q];
+        R.slambda[q] = sp.lambda[q];
+        R.sbias[q] = sp.bias[q];
+      }
+      if (sp.kind == 1) {
+        suite_segments(sp, c.d, R.seg);
+        R.perm = (const int32_t*)(A + O.perm);
+      }
+    }
     if (c.jde) {
       R.jF[0] = (double*)(A + O.jF0);
       R.jF[1] = (double*)(A + O.jF1);
@@ -708,14 +819,28 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
       R.dbg_fp64 = (uint8_t*)(A + O.dbg_fp64);
       R.dbg_cand = (int32_t*)(A + O.dbg_cand);
     }
+    const int pairs = suite_pairs(c.objective);
     if (c.shift) {
-      ce = cudaMemcpyAsync((void*)R.o, c.shift, c.d * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+      ce = cudaMemcpy2DAsync((void*)R.o, R.dp * sizeof(double), c.shift, c.d * sizeof(double), c.d * sizeof(double),
+                             pairs, cudaMemcpyHostToDevice, h->stream);
       if (ce != cudaSuccess) return fin(fail(h, DE_ERR_CUDA, std::string("copy shift: ") + cudaGetErrorString(ce)));
     }
+    if (R.perm) {
+      std::vector<int32_t> pm(c.d);
+      for (int j = 0; j < c.d; ++j) pm[j] = c.perm ? c.perm[j] : j;
+      ce = cudaMemcpyAsync((void*)R.perm, pm.data(), c.d * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);  // pm goes out of scope
+      if (ce != cudaSuccess) return fin(fail(h, DE_ERR_CUDA, std::string("copy perm: ") + cudaGetErrorString(ce)));
+    }
     if (c.rot) {
-      tmp.resize((size_t)c.d * c.d);
-      for (int j = 0; j < c.d; ++j)
-        for (int k = 0; k < c.d; ++k) tmp[(size_t)k * c.d + j] = c.rot[(size_t)j * c.d + k];
+      // every component's M, transposed
+      tmp.resize((size_t)pairs * c.d * c.d);
+      for (int q = 0; q < pairs; ++q) {
+        const double* Mq = c.rot + (size_t)q * c.d * c.d;
+        double* Tq = tmp.data() + (size_t)q * c.d * c.d;
+        for (int j = 0; j < c.d; ++j)
+          for (int k = 0; k < c.d; ++k) Tq[(size_t)k * c.d + j] = Mq[(size_t)j * c.d + k];
+      }
       ce = cudaMemcpyAsync((void*)R.MT, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
       if (ce == cudaSuccess && R.Mrow)
         ce = cudaMemcpyAsync((void*)R.Mrow, c.rot, (size_t)c.d * c.d * sizeof(double), cudaMemcpyHostToDevice,

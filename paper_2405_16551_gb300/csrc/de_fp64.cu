@@ -30,6 +30,7 @@
 #include "de_internal.cuh"
 #include "de_device.cuh"
 #include "de_kernels.h"
+#include "de_suite.cuh"
 
 namespace de {
 
@@ -67,6 +68,17 @@ __global__ void k_eval_rows(const RunDesc* __restrict__ runs, int run, const dou
   const int row0 = blockIdx.x * rows;
   const int nrows = min(rows, n - row0);
   if (nrows <= 0) return;
+  if (suite_objective(R.obj)) {
+    // the proposed benchmark's functions (Sec. 7.3, Table 2)
+    __shared__ double s_f[kSuiteMaxRows];
+    __shared__ double s_comp[kSuiteMaxRows][10];
+    suite_tile(R, x + (size_t)row0 * ld, ld, nrows, Y, Z, s_f, s_comp);
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+      fout[row0 + r] = s_f[r];
+      if (fx_out) fx_out[row0 + r] = 1;
+    }
+    return;
+  }
   if (R.obj == kObjOde) {
     // a warp integrates one row's chain
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -191,9 +203,10 @@ __device__ __forceinline__ void rotate_groups(const RunDesc& R, const double* __
 // about one CTA per SM so that every SM's FP64 pipe gets the same work.
 // Shared memory: T (trials), Y (shifted trials), Z (rotated), W (second term
 // sum of Ackley), each R.rows x dp doubles.
-// VAR: some run of the launch uses a strategy variant or jDE (a separate
-// instance, so that plain DE/rand/1/bin keeps its register allocation).
-template <bool VAR>
+// VAR: some run of the launch uses a strategy variant or jDE; SUITE: some
+// run uses a function of the proposed benchmark (objectives 5..20).  Separate
+// instances, so that plain DE/rand/1/bin keeps its register allocation.
+template <bool VAR, bool SUITE>
 __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ runs,
                                                   const int4* __restrict__ items) {
   extern __shared__ __align__(16) double sm[];
@@ -250,7 +263,13 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   __syncthreads();
 
   const int nout = nrows * d;
-  if (R.obj == kObjOde) {
+  __shared__ double s_fsuite[kSuiteMaxRows];
+  __shared__ double s_comp[kSuiteMaxRows][10];
+  const bool suite = SUITE && suite_objective(R.obj);
+  if (suite) {
+    // ---- the proposed benchmark's functions (Sec. 7.3, Table 2)
+    suite_tile(R, T, dp, nrows, Y, Z, s_fsuite, s_comp);
+  } else if (R.obj == kObjOde) {
     // ---- ODE objective: a warp integrates one trial's chain; f to W[row][0]
     for (int rl = warp; rl < nrows; rl += nwarps) {
       const double s = warp_sum(ode_chain(T + rl * dp, lane, R.ode_ref, nullptr));
@@ -311,7 +330,9 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   for (int rl = warp; rl < nrows; rl += nwarps) {
     const int i = row0 + rl;
     double ft;
-    if (R.obj == kObjOde) {
+    if (suite) {
+      ft = s_fsuite[rl];
+    } else if (R.obj == kObjOde) {
       ft = W[rl * dp];
     } else {
       double s1 = 0.0, s2 = 0.0;
@@ -370,15 +391,16 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
 namespace de {
 
 void k_configure(size_t smem_gen) {
-  cudaFuncSetAttribute(k_gen_fp64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)std::max<size_t>(smem_gen, 1));
-  cudaFuncSetAttribute(k_gen_fp64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)std::max<size_t>(smem_gen, 1));
+  const int smem = (int)std::max<size_t>(smem_gen, 1);
+  cudaFuncSetAttribute(k_gen_fp64<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_eval_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem, bool var,
-                       cudaStream_t s) {
+                       bool suite, cudaStream_t s) {
   // programmatic stream serialization: generation g + 1 is scheduled while
   // generation g drains, and waits (griddepcontrol.wait) before reading it
   cudaLaunchConfig_t cfg = {};
@@ -391,8 +413,10 @@ void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int t
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (var) cudaLaunchKernelEx(&cfg, k_gen_fp64<true>, runs, items);
-  else cudaLaunchKernelEx(&cfg, k_gen_fp64<false>, runs, items);
+  if (var && suite) cudaLaunchKernelEx(&cfg, k_gen_fp64<true, true>, runs, items);
+  else if (var) cudaLaunchKernelEx(&cfg, k_gen_fp64<true, false>, runs, items);
+  else if (suite) cudaLaunchKernelEx(&cfg, k_gen_fp64<false, true>, runs, items);
+  else cudaLaunchKernelEx(&cfg, k_gen_fp64<false, false>, runs, items);
 }
 
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s) {

@@ -6,9 +6,11 @@
 //            one (synchronous replacement, double buffered)
 //   f[2]     np doubles, fitness of X[0] / X[1]
 //   fx[2]    np bytes, 1 when f[.] was computed in FP64 (split precisions)
-//   o        dp doubles (shift, zero padded)
+//   o        dp doubles (shift, zero padded); nc x dp for a composition function
 //   MT       d x d doubles, MT[k d + j] = M[j][k] (transposed: a warp reading
-//            consecutive j for one k is one coalesced row)
+//            consecutive j for one k is one coalesced row); nc of them for a
+//            composition function
+//   perm     d int32 (hybrid functions)
 //   Bsplit   tensor-core operand copies of M (split precisions only)
 //   state    one RunState (generation, evaluations, best record, stop flag)
 //   part     one BestPartial per row tile of the generation kernel
@@ -70,6 +72,14 @@ struct RunDesc {
   int32_t jde;       // 1: per-individual F and CR in jF / jCR (jDE)
   double* jF[2];     // jDE: np values of F_i for X[0] / X[1]
   double* jCR[2];    // jDE: np values of CR_i
+  // benchmark suite (objectives 5..20, FP64 path): parts of a hybrid
+  // function or components of a composition function
+  int32_t nc;              // parts / components (1 for a basic function)
+  int32_t sfn[5];          // basic function of each
+  int32_t seg[6];          // hybrid: first permuted position of each part, seg[nc] = d
+  double sscale[5];        // domain scale of each
+  double slambda[5], ssigma[5], sbias[5];  // composition: height, coverage, bias
+  const int32_t* perm;     // hybrid: d positions of the permutation
   // buffers
   double* X[2];
   double* f[2];

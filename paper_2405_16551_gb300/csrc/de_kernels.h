@@ -14,9 +14,10 @@ void set_last_error(const std::string& m);
 
 // FP64 path (de_fp64.cu)
 void k_configure(size_t smem_gen);
-// var: some run uses a strategy variant or jDE
+// var: some run uses a strategy variant or jDE; suite: some run uses an
+// objective of the proposed benchmark (5..20)
 void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem, bool var,
-                       cudaStream_t s);
+                       bool suite, cudaStream_t s);
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s);
 void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int rotate,
                         double* f, uint8_t* fx, cudaStream_t s);

@@ -1,0 +1,276 @@
+// de_suite.cuh -- the benchmark the paper proposes for GPU DEs (Sec. 7.3,
+// Table 2) on the FP64 path: its basic functions on a warp, the hybrid
+// functions (Sec. 7.3.2: one shift, one rotation, a permutation, parts
+// evaluated by different basic functions) and the composition functions
+// (Sec. 7.3.3: n shifted and rotated basic functions mixed by distance
+// weights).
+//
+// Every basic function g has g = 0 at z = 0 (with the offsets written next to
+// it).  The definitions are the published CEC'14 / CEC'17 ones the paper
+// names; the shift, rotation and permutation data are the run's.
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "de_common.cuh"
+#include "de_device.cuh"
+#include "de_internal.cuh"
+
+namespace de {
+
+constexpr int kObjZakharov = 5, kObjSchwefel = 6, kObjBentCigar = 7, kObjHGBat = 8, kObjSchafferF6 = 9;
+constexpr int kObjKatsuura = 10, kObjHappyCat = 11, kObjGriewankRosenbrock = 12, kObjElliptic = 13;
+constexpr int kObjGriewank = 14, kObjHybrid1 = 15, kObjHybrid3 = 17, kObjComposition1 = 18;
+constexpr int kObjComposition3 = 20;
+
+__device__ __forceinline__ bool suite_objective(int obj) { return obj >= kObjZakharov && obj <= kObjComposition3; }
+
+__device__ __forceinline__ double warp_prod(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// modified Schwefel term of t = z + 420.9687462275036: t sin sqrt|t| inside
+// [-500, 500]; outside, the value folded back with fmod plus the penalty
+// (t -+ 500)^2 / (10^4 n)
+__device__ __forceinline__ double schwefel_term(double t, int n) {
+  if (t > 500.0) {
+    const double m = fmod(t, 500.0);
+    return (500.0 - m) * sin(sqrt(500.0 - m)) - (t - 500.0) * (t - 500.0) / (10000.0 * n);
+  }
+  if (t < -500.0) {
+    const double m = fmod(-t, 500.0);
+    return (m - 500.0) * sin(sqrt(500.0 - m)) - (t + 500.0) * (t + 500.0) / (10000.0 * n);
+  }
+  return t * sin(sqrt(fabs(t)));
+}
+
+// g of basic function fn on the n-vector w_l = sc * z[src(l)], src(l) =
+// idx[base + l] (idx != NULL: a hybrid part) or base + l; position i = l + 1.
+// Called by a whole warp; every lane returns g.
+static __device__ __noinline__ double basic_fn_warp(int fn, const double* __restrict__ z, const int32_t* __restrict__ idx, int base,
+                                int n, double sc, int lane) {
+  auto W = [&](int l) { return sc * z[idx ? idx[base + l] : base + l]; };
+  double s1 = 0.0, s2 = 0.0, p = 1.0;
+  const double kex = fn == kObjKatsuura ? 10.0 / pow((double)n, 1.2) : 0.0;
+  for (int l = lane; l < n; l += 32) {
+    const double w = W(l);
+    switch (fn) {
+      case kObjSphere: s1 += w * w; break;
+      case kObjRastrigin: s1 += w * w - 10.0 * cos2pi_f64_horner(w) + 10.0; break;
+      case kObjRosenbrock:
+        if (l + 1 < n) {
+          const double t0 = w + 1.0, t1 = W(l + 1) + 1.0;
+          const double a = t1 - t0 * t0, b = t0 - 1.0;
+          s1 += 100.0 * a * a + b * b;
+        }
+        break;
+      case kObjAckley:
+        s1 += w * w;
+        s2 += cos2pi_f64_horner(w);
+        break;
+      case kObjZakharov:
+        // sum w^2 + (sum 0.5 i w_i)^2 + (sum 0.5 i w_i)^4
+        s1 += w * w;
+        s2 += 0.5 * (double)(l + 1) * w;
+        break;
+      case kObjSchwefel: s1 += schwefel_term(w + 420.9687462275036, n); break;
+      case kObjBentCigar: s1 += (l == 0 ? 1.0 : 1e6) * (w * w); break;
+      case kObjHGBat:
+      case kObjHappyCat: {
+        const double x = w - 1.0;  // minimum at w = 0
+        s1 += x * x;
+        s2 += x;
+        break;
+      }
+      case kObjSchafferF6: {
+        // pair (w_l, w_{l+1}), cyclic
+        const double v = W(l + 1 < n ? l + 1 : 0);
+        const double s = w * w + v * v;
+        const double sn = sin(sqrt(s));
+        const double den = 1.0 + 0.001 * s;
+        s1 += 0.5 + (sn * sn - 0.5) / (den * den);
+        break;
+      }
+      case kObjKatsuura: {
+        // 1 + i sum_{j=1}^{32} |2^j w - nearest integer| / 2^j, to the power 10 / n^1.2;
+        // 2^j w, its rounding and the difference are exact
+        double s = 0.0, p2 = 1.0;
+        for (int j = 1; j <= 32; ++j) {
+          p2 *= 2.0;
+          const double v = p2 * w;
+          s += fabs(v - rint(v)) / p2;
+        }
+        p *= pow(1.0 + (double)(l + 1) * s, kex);
+        break;
+      }
+      case kObjGriewankRosenbrock: {
+        // Griewank's 1-D term of Rosenbrock's 2-D term of the cyclic pair, at t = w + 1
+        const double u = w + 1.0, v = W(l + 1 < n ? l + 1 : 0) + 1.0;
+        const double a = u * u - v, b = u - 1.0;
+        const double r = 100.0 * a * a + b * b;
+        s1 += r * r / 4000.0 - cos(r) + 1.0;
+        break;
+      }
+      case kObjElliptic: {
+        const double c = n > 1 ? pow(1e6, (double)l / (double)(n - 1)) : 1.0;
+        s1 += c * (w * w);
+        break;
+      }
+      case kObjGriewank:
+        s1 += w * w / 4000.0;
+        p *= cos(w / sqrt((double)(l + 1)));
+        break;
+      default: s1 = CUDART_NAN;
+    }
+  }
+  s1 = warp_sum(s1);
+  switch (fn) {
+    case kObjAckley: {
+      s2 = warp_sum(s2);
+      return 20.0 + 2.718281828459045 - 20.0 * exp(-0.2 * sqrt(s1 / n)) - exp(s2 / n);
+    }
+    case kObjZakharov: {
+      s2 = warp_sum(s2);
+      const double b2 = s2 * s2;
+      return s1 + b2 + b2 * b2;
+    }
+    case kObjSchwefel: return 418.9828872724338 * n - s1;
+    case kObjHGBat: {
+      // |a^2 - b^2|^(1/2) + (0.5 a + b) / n + 0.5, a = sum x^2, b = sum x
+      s2 = warp_sum(s2);
+      return sqrt(fabs(s1 * s1 - s2 * s2)) + (0.5 * s1 + s2) / n + 0.5;
+    }
+    case kObjHappyCat: {
+      // |a - n|^(1/4) + (0.5 a + b) / n + 0.5
+      s2 = warp_sum(s2);
+      return pow(fabs(s1 - n), 0.25) + (0.5 * s1 + s2) / n + 0.5;
+    }
+    case kObjKatsuura: {
+      p = warp_prod(p);
+      const double c = 10.0 / ((double)n * n);
+      return c * p - c;
+    }
+    case kObjGriewank: {
+      p = warp_prod(p);
+      return s1 - p + 1.0;
+    }
+    default: return s1;
+  }
+}
+
+// Rotation of a tile with a given transposed matrix: Z[r][j] = sum_k MT[k][j]
+// Y[r][k], flattened over (row, output); a thread runs four outputs as
+// independent accumulator chains (consecutive threads read consecutive j of
+// one row of MT).
+__device__ __forceinline__ void suite_rotate(const double* __restrict__ MT, const double* __restrict__ Y,
+                                             double* __restrict__ Z, int nrows, int d, int dp) {
+  const int nout = nrows * d;
+  const int step = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < nout; e0 += 4 * step) {
+    int rr[4], jj[4];
+    double acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = min(e0 + q * step, nout - 1);
+      rr[q] = e / d;
+      jj[q] = e - rr[q] * d;
+      acc[q] = 0.0;
+    }
+    for (int k = 0; k < d; ++k) {
+      const double* mk = MT + (size_t)k * d;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fma(__ldg(mk + jj[q]), Y[rr[q] * dp + k], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (e0 + q * step < nout) Z[rr[q] * dp + jj[q]] = acc[q];
+  }
+}
+
+// Objective of the suite for nrows rows of src (row stride ld, in shared or
+// global memory); the whole CTA calls it.  Y, Z: nrows x dp shared buffers;
+// f[r] receives row r's value; comp: per row, the composition's g_c and
+// D_c (kSuiteMaxRows x 10).
+//   basic (5..14):  g(M ((x - o) s)), s the run's scale
+//   hybrid:         z = M ((x - o) s), part p = the positions seg_p ..
+//                   seg_{p+1} - 1 of the permuted z, scaled by the part's
+//                   domain scale and evaluated as an n_p-dimensional function
+//   composition:    sum_c omega_c (lambda_c g_c(M_c ((x - o_c) s_c)) + bias_c)
+//                   with omega_c = w_c / sum w, w_c = exp(-D_c / (2 d
+//                   sigma_c^2)) / sqrt(D_c), D_c = |x - o_c|^2, normalised in
+//                   logarithms; at x = o_c the weight is 1 for the first such c.
+constexpr int kSuiteMaxRows = 8;
+
+static __device__ __noinline__ void suite_tile(const RunDesc& R, const double* src, int64_t ld, int nrows, double* __restrict__ Y,
+                           double* __restrict__ Z, double* __restrict__ f, double (*comp)[10]) {
+  const int d = R.d, dp = R.dp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const bool is_comp = R.obj >= kObjComposition1;
+  const bool is_hyb = R.obj >= kObjHybrid1 && R.obj <= kObjHybrid3;
+  const int nc = is_comp ? R.nc : 1;
+  for (int c = 0; c < nc; ++c) {
+    const double* oc = R.o + (size_t)c * dp;
+    const double s = is_comp ? R.sscale[c] : R.scale;
+    for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) {
+      const int r = e / dp, j = e - r * dp;
+      double y = 0.0;
+      if (j < d) y = __dmul_rn(__dsub_rn(src[(size_t)r * ld + j], oc[j]), s);
+      Y[e] = y;
+    }
+    __syncthreads();
+    if (R.rotate) suite_rotate(R.MT + (size_t)c * d * d, Y, Z, nrows, d, dp);
+    else
+      for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) Z[e] = Y[e];
+    __syncthreads();
+    for (int r = warp; r < nrows; r += nwarps) {
+      const double* zr = Z + r * dp;
+      if (is_comp) {
+        const double g = basic_fn_warp(R.sfn[c], zr, nullptr, 0, d, 1.0, lane);
+        double dd = 0.0;
+        for (int j = lane; j < d; j += 32) {
+          const double t = __dsub_rn(src[(size_t)r * ld + j], oc[j]);
+          dd += t * t;
+        }
+        dd = warp_sum(dd);
+        if (lane == 0) {
+          comp[r][c] = g;
+          comp[r][5 + c] = dd;
+        }
+      } else if (is_hyb) {
+        double g = 0.0;
+        for (int q = 0; q < R.nc; ++q)
+          g += basic_fn_warp(R.sfn[q], zr, R.perm, R.seg[q], R.seg[q + 1] - R.seg[q], R.sscale[q], lane);
+        if (lane == 0) f[r] = g;
+      } else {
+        const double g = basic_fn_warp(R.obj, zr, nullptr, 0, d, 1.0, lane);
+        if (lane == 0) f[r] = g;
+      }
+    }
+    __syncthreads();
+  }
+  if (is_comp) {
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+      int hit = -1;
+      for (int c = 0; c < nc; ++c)
+        if (comp[r][5 + c] == 0.0 && hit < 0) hit = c;
+      double om[5], m = -CUDART_INF, sum = 0.0;
+      for (int c = 0; c < nc; ++c) {
+        const double D = comp[r][5 + c];
+        om[c] = -0.5 * log(D) - D / (2.0 * d * R.ssigma[c] * R.ssigma[c]);
+        m = fmax(m, om[c]);
+      }
+      for (int c = 0; c < nc; ++c) {
+        om[c] = hit >= 0 ? (c == hit ? 1.0 : 0.0) : exp(om[c] - m);
+        sum += om[c];
+      }
+      double acc = 0.0;
+      for (int c = 0; c < nc; ++c) acc += om[c] / sum * (R.slambda[c] * comp[r][c] + R.sbias[c]);
+      f[r] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace de

@@ -48,7 +48,7 @@ def test_version_and_status_strings():
         (dict(np_=64, d=10, cr=1.5), "CR must"),
         (dict(np_=64, d=10, lo=1.0, hi=1.0), "bounds"),
         (dict(np_=64, d=10, lo=float("nan")), "bounds"),
-        (dict(np_=64, d=10, objective=9), "objective"),
+        (dict(np_=64, d=10, objective=99), "objective"),
         (dict(np_=64, d=10, scale=0.0), "scale"),
         (dict(np_=64, d=10, run_id=1 << 20), "run_id"),
         (dict(np_=64, d=10, precision=7), "precision"),
@@ -59,6 +59,15 @@ def test_version_and_status_strings():
         (dict(np_=64, d=20, objective=4, precision=2), "FP64 only"),
         (dict(np_=64, d=20, objective=4, rot=np.eye(20)), "no rotation"),
         (dict(np_=64, d=10, strategy=3), "strategy"),
+        (dict(np_=64, d=10, objective=21), "objective"),
+        (dict(np_=64, d=10, objective=5, precision=1), "FP64 only"),
+        (dict(np_=64, d=10, objective=18, precision=2), "FP64 only"),
+        (dict(np_=64, d=6, objective=17), "too small"),
+        (dict(np_=64, d=10, objective=18, scale=0.5), "scale 1"),
+        (dict(np_=64, d=4, objective=1, perm=np.arange(4)), "hybrid functions only"),
+        (dict(np_=64, d=10, objective=15, perm=np.array([0, 1, 1, 3, 4, 5, 6, 7, 8, 9])), "permutation"),
+        (dict(np_=64, d=10, objective=15, perm=np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 10])), "permutation"),
+        (dict(np_=64, d=2, objective=19, shift=np.array([0.0, 1.0, np.nan, 0, 0, 0, 0, 0])), "shift"),
         (dict(np_=64, d=10, strategy=-1), "strategy"),
     ],
 )
