@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     p.add_argument("--workload", default="rastrigin",
                    choices=["rastrigin", "sphere_small", "batch512", "ode_surrogate", "stress", "stress_batch",
-                            "variants"],
+                            "variants", "suite"],
                    help="rastrigin: the headline configuration (default); the others measure the batched, "
                         "surrogate and large-dimension configurations with the same harness")
     return p.parse_args()
@@ -511,6 +511,52 @@ def run_workload(args, capi, torch, rank, world):
                     dtype="f64", config={"workload": f"NP=1024 D=100 Rastrigin, {G} generations per step, FP64",
                                          "l2": "flushed between steps (512 MiB write)"},
                     forms=forms, gpu_launches=steps * 5 * (3 + G))
+    elif args.workload == "suite":
+        # the proposed 100-D benchmark (F01-F10) in the configuration of the
+        # paper's timing study: DE/rand/1/bin, NP = 250, F = 0.5, CR = 0.3,
+        # 1e7 evaluations per trial, FP64; trials batched in one handle.  Then
+        # the protocol's rank-sum score of that configuration against jDE
+        # (NP = 250) on the same trials' data.
+        from paper_2405_16551_gb300 import protocol
+
+        ntr = int(os.environ.get("DE_BENCH_SUITE_TRIALS", "30"))
+        budget = int(float(os.environ.get("DE_BENCH_SUITE_BUDGET", "1e7")))
+        d = 100
+        paper_ide = [0.63, 0.61, 0.60, 0.66, 0.70, 0.78, 1.05, 1.28, 1.55, 1.85]
+        algs = [protocol.Algorithm("rand1bin_np250_cr0.3", 250, f=0.5, cr=0.3),
+                protocol.Algorithm("jde_np250", 250, f=0.5, cr=0.9, jde=True)]
+        forms, per_fn, tot_ev, tot_s = {}, {}, 0, 0.0
+        for k in range(1, 11):
+            obj = problems.SUITE[k]
+            data = problems.suite(obj, d, seed=1)
+            # one trial alone (latency)
+            t1 = protocol.run_trials(capi, algs[0], obj, d, data, 1, budget, stream=stream.cuda_stream,
+                                     synchronize=torch.cuda.synchronize)[0]
+            per_fn[f"F{k:02d}"] = {}
+            row = {"objective": obj, "one_trial_s": t1.seconds, "one_trial_evals": t1.evals,
+                   "paper_all_gpu_ide_s_rtx3080": paper_ide[k - 1]}
+            for a in algs:
+                tr = protocol.run_trials(capi, a, obj, d, data, ntr, budget, stream=stream.cuda_stream,
+                                         synchronize=torch.cuda.synchronize)
+                per_fn[f"F{k:02d}"][a.name] = tr
+                secs = max(t.seconds for t in tr)
+                ev = sum(t.evals for t in tr)
+                row[a.name] = {"batch_s": secs, "per_trial_s": secs / ntr, "trial_evals_per_s": ev / secs,
+                               "median_error": float(np.median([t.error for t in tr])),
+                               "solved": sum(t.error < protocol.TARGET for t in tr)}
+                if a is algs[0]:
+                    tot_ev += ev
+                    tot_s += secs
+            forms[f"F{k:02d}"] = row
+        total = protocol.benchmark_scores(per_fn)
+        line.update(metric=f"trial evals/sec over the 100-D proposed benchmark F01-F10 (NP=250, CR=0.3, "
+                           f"{budget:.0e} evaluations per trial, {ntr} trials batched), FP64",
+                    value=tot_ev / tot_s, ms_per_step=1e3 * tot_s / 10, dtype="f64",
+                    config={"workload": f"F01-F10, D=100, NP=250, F=0.5, CR=0.3, budget {budget:.0e}, {ntr} trials "
+                                        "per function in one handle", "l2": "working set in L2 (a few MB)"},
+                    forms=forms, protocol={"scores": total, "ranking": protocol.final_ranking(total),
+                                           "algorithms": [a.name for a in algs]},
+                    gpu_launches=None)
     elif args.workload == "stress_batch":
         # 64 runs of the large-dimension shape in one handle (working set far above L2)
         G = min(args.generations, 10)

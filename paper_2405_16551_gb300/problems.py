@@ -91,12 +91,14 @@ def permutation(d: int, seed: int = 1, run_id: int = 0) -> np.ndarray:
 
 
 def suite(objective: int, d: int, seed: int = 1) -> dict:
-    """Shift (n x d), rotation (n x d x d) and permutation (d) of one function of
-    the proposed benchmark; n = 1 except for the composition functions.  For
-    n = 1 the shift is a vector and the rotation a matrix."""
+    """Shift (n x d), rotation (n x d x d) and permutation (d; hybrid functions
+    only, else None) of one function of the proposed benchmark; n = 1 except
+    for the composition functions.  For n = 1 the shift is a vector and the
+    rotation a matrix."""
     n = _COMPONENTS.get(objective, 1)
     o = np.stack([shift(d, seed=seed, run_id=c) for c in range(n)])
     M = np.stack([rotation(d, seed=seed, run_id=c) for c in range(n)])
     if n == 1:
         o, M = o[0], M[0]
-    return {"shift": o, "rot": M, "perm": permutation(d, seed=seed), "scale": SUITE_SCALE.get(objective, 1.0)}
+    perm = permutation(d, seed=seed) if objective in (HYBRID1, HYBRID2, HYBRID3) else None
+    return {"shift": o, "rot": M, "perm": perm, "scale": SUITE_SCALE.get(objective, 1.0)}

@@ -25,7 +25,7 @@ def _need_gpu():
 
 def _data(obj, d, seed, rotate=True):
     s = problems.suite(obj, d, seed=seed)
-    perm = s["perm"] if obj in HYBRID else None
+    perm = s["perm"]
     scale = 1.0 if obj in HYBRID + COMPOSITION else 0.05
     return s["shift"], (s["rot"] if rotate else None), perm, scale
 
