@@ -6,7 +6,7 @@ package.  The product library never imports it, never links it, and shares no
 code with it; it exists to check the CUDA path.
 
 The arithmetic lives in plain C (``de_oracle.c``, ``de_oracle_ode.c``,
-``de_oracle_mlp.c``, ``de_oracle_suite.c``), compiled with gcc on first use (or by ``build()``) and
+``de_oracle_mlp.c``, ``de_oracle_suite.c``, ``de_oracle_islands.c``), compiled with gcc on first use (or by ``build()``) and
 called through ctypes.  This module only marshals numpy arrays.
 
 Parity pins for every function are in ``tests/test_oracle_*.py``.
@@ -21,7 +21,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["de_oracle.c", "de_oracle_ode.c", "de_oracle_mlp.c", "de_oracle_suite.c"]
+_SOURCES = ["de_oracle.c", "de_oracle_ode.c", "de_oracle_mlp.c", "de_oracle_suite.c", "de_oracle_islands.c"]
 _LIB_PATH = os.path.join(_HERE, "_build", "libde_oracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -84,6 +84,13 @@ def _load():
         lib.or_hybrid_segments.restype = ctypes.c_int
         lib.or_suite_components.argtypes = [ctypes.c_int]
         lib.or_suite_components.restype = ctypes.c_int
+        lib.or_island_ranked.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _i32p]
+        lib.or_run_islands.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, _dp, _dp, _i32p, ctypes.c_double, ctypes.c_uint64,
+                                       ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_double, _dp, _dp, _dp, _dp, _i64p, ctypes.c_int]
+        lib.or_run_islands.restype = ctypes.c_int64
         lib.or_init_population.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_uint64, ctypes.c_uint32, _dp]
         lib.or_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -364,3 +371,28 @@ def run(np_, d, F, CR, lo, hi, obj, o, M, seed, max_generations, max_evals=0, ta
                           ctypes.byref(ev), _p(tr), threads)
     res = (X, f, int(g), int(ev.value), (tr[: g + 1] if trace else None))
     return res + (jF, jCR) if return_adaptive else res
+
+
+# ----------------------------------------------------------------------------- island model
+def island_ranked(f, n, worst=False):
+    """The n best (or worst) indices of f in the island model's order."""
+    f = _f64(f)
+    out = np.zeros(n, dtype=np.int32)
+    _load().or_island_ranked(f.shape[0], _p(f), n, 1 if worst else 0, _p(out, _i32p))
+    return out
+
+
+def run_islands(m, interval, nmig, np_, d, F, CR, lo, hi, obj, o, M, seed, max_generations, max_evals=0,
+                target_error=1e-8, run_id=0, scale=1.0, perm=None, strategy=0, jde=False, threads=1):
+    """The island model: returns (X [m, np, d], f [m, np], generations,
+    evaluations of one island, F_i [m, np], CR_i [m, np])."""
+    X = np.zeros((m, np_, d))
+    f = np.zeros((m, np_))
+    jF = np.zeros((m, np_))
+    jCR = np.zeros((m, np_))
+    ev = ctypes.c_int64(0)
+    g = _load().or_run_islands(m, interval, nmig, np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)),
+                               _p(_i32(perm), _i32p), scale, seed, run_id, int(strategy), 1 if jde else 0,
+                               max_generations, max_evals, target_error, _p(X), _p(f), _p(jF), _p(jCR),
+                               ctypes.byref(ev), threads)
+    return X, f, int(g), int(ev.value), jF, jCR
