@@ -285,6 +285,26 @@ DE_API de_status de_init(const de_config* cfg, void* cuda_stream, de_handle** ou
  * Errors as de_init; DE_ERR_INVALID_ARG when nruns < 1 or any cfg is invalid. */
 DE_API de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream, de_handle** out);
 
+/* The island model (Sec. 3.2; on the GPU, the multi-population model of
+ * Sec. 5.4, which the paper leaves to future work for DE): nislands copies
+ * of *cfg, island k with run_id = cfg->run_id + k, evolve as the runs of one
+ * batch.  Synchronous migration on a ring after every generation g with
+ * g % interval == 0: the `migrants` best individuals of island k (ascending
+ * f, lower index first, NaN last) replace the `migrants` worst of island
+ * (k + 1) % nislands (descending f, NaN first, higher index first), the q-th
+ * best into the q-th worst, all taken before any is written; a migrant keeps
+ * its fitness (and its jDE parameters).  The model stops as a whole: when any
+ * island's best is below target_error every island stops with reason
+ * DE_STOP_TARGET; the evaluation and generation limits apply per island
+ * (the islands advance together).  Results come per island from de_run
+ * (nruns = nislands) and de_get_best.
+ * Errors: DE_ERR_INVALID_ARG (nislands outside [2, 4096], interval < 1,
+ * migrants outside [1, min(32, np / 2)], run_id + nislands > 2^20, or cfg
+ * invalid), DE_ERR_UNSUPPORTED (split precision or a surrogate), DE_ERR_OOM,
+ * DE_ERR_CUDA. */
+DE_API de_status de_init_islands(const de_config* cfg, int32_t nislands, int32_t interval, int32_t migrants,
+                                 void* cuda_stream, de_handle** out);
+
 /* Re-initialise run `run` (or every run when run == -1) as de_init did:
  * population from the INIT stream, evaluation, counters and best record
  * reset.  Enqueued on the handle's stream; allocates nothing. */

@@ -114,6 +114,8 @@ def load(build_if_missing: bool = True):
             "de_destroy": ([H], ctypes.c_int),
             "de_get_surrogate_stats": ([H, _i64p, _i64p, _dp, _i32p], ctypes.c_int),
             "de_get_adaptive": ([H, ctypes.c_int32, _dp, _dp], ctypes.c_int),
+            "de_init_islands": ([ctypes.POINTER(de_config), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                 ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
             "de_set_adaptive": ([H, ctypes.c_int32, _dp, _dp], ctypes.c_int),
             "de_mlp_create": ([ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
             "de_mlp_destroy": ([H], ctypes.c_int),
@@ -141,7 +143,7 @@ def exported_symbols():
             "de_get_debug", "de_get_shape", "de_get_stats", "de_get_plan", "de_save", "de_load", "de_destroy",
             "de_eval_noalloc", "de_mlp_create", "de_mlp_destroy", "de_mlp_set_params", "de_mlp_get_params",
             "de_mlp_forward", "de_mlp_grad", "de_mlp_train", "de_get_surrogate_stats", "de_get_adaptive",
-            "de_set_adaptive"]
+            "de_set_adaptive", "de_init_islands"]
 
 
 def _status_name(s):
@@ -321,6 +323,15 @@ def de_set_population(h, run: int, x, f=None):
 
 def de_set_generation(h, run: int, generation: int):
     _check(load().de_set_generation(h, run, generation), h)
+
+
+def de_init_islands(cfg, nislands: int, interval: int, migrants: int, stream=None):
+    """The island model: nislands copies of cfg (run_id + k) with ring
+    migration every `interval` generations; returns the handle."""
+    h = ctypes.c_void_p()
+    _check(load().de_init_islands(ctypes.byref(cfg), nislands, interval, migrants, ctypes.c_void_p(stream or 0),
+                                  ctypes.byref(h)), None)
+    return h.value
 
 
 def de_get_adaptive(h, run: int = 0):

@@ -46,6 +46,12 @@ struct de_handle {
   Surrogate* surr = nullptr;  // surrogate-assisted generations (surrogate_k >= 2)
   bool variants = false;      // some run uses a strategy variant or jDE
   bool suite = false;         // some run uses an objective of the proposed benchmark (5..20)
+  // island model (de_init_islands): the runs are islands on a migration ring
+  bool islands = false;
+  IslandCtl* d_isl = nullptr;
+  IslandStage stage{};
+  void* isl_mem = nullptr;
+  IslandCtl isl{};
   std::string err;
 };
 
@@ -254,10 +260,22 @@ static void drop_graph(de_handle* h) {
   h->graph_gens = 0;
 }
 
+// Island model: forget the last migration and apply the model's group stop
+// to the current state (after (re)initialisation or a population change).
+static de_status islands_resync(de_handle* h) {
+  if (!h->islands) return DE_OK;
+  h->isl.mig_gen = -1;
+  DE_CUDA(h, cudaMemcpyAsync(h->d_isl, &h->isl, sizeof(IslandCtl), cudaMemcpyHostToDevice, h->stream));
+  k_island_launch(h->d_run, h->d_isl, h->stage, h->nruns, false, h->stream);
+  DE_CUDA(h, cudaGetLastError());
+  return DE_OK;
+}
+
 // Enqueue one generation of every run (the kernels skip stopped runs).
 static de_status launch_generation(de_handle* h, cudaStream_t s) {
   if (h->prec == DE_PREC_FP64) {
     k_gen_fp64_launch(h->d_run, h->d_items, h->nitems, h->threads, h->smem_gen, h->variants, h->suite, s);
+    if (h->islands) k_island_launch(h->d_run, h->d_isl, h->stage, h->nruns, true, s);
   } else {
     tc_generation_launch(h->tc, h->d_run, s);
   }
@@ -612,6 +630,7 @@ de_status de_destroy(de_handle* h) {
   tc_plan_free(h->tc);
   if (h->d_items) cudaFree(h->d_items);
   if (h->d_run) cudaFree(h->d_run);
+  if (h->isl_mem) cudaFree(h->isl_mem);
   if (h->arena) cudaFree(h->arena);
   if (h->h_state) cudaFreeHost(h->h_state);
   delete h;
@@ -905,6 +924,64 @@ de_status de_reset(de_handle* h, int32_t run) {
     const de_status s = surr_reset(*h->surr, h->stream, h->err);
     if (s != DE_OK) return fail(h, s, h->err);
   }
+  return islands_resync(h);
+}
+
+de_status de_init_islands(const de_config* cfg, int32_t nislands, int32_t interval, int32_t migrants,
+                          void* cuda_stream, de_handle** out) {
+  g_err.clear();
+  if (!cfg || !out) return fail(nullptr, DE_ERR_INVALID_ARG, "cfg or out is NULL");
+  if (nislands < 2 || nislands > 4096) return fail(nullptr, DE_ERR_INVALID_ARG, "nislands must be in [2, 4096]");
+  if (interval < 1) return fail(nullptr, DE_ERR_INVALID_ARG, "interval must be >= 1");
+  if (migrants < 1 || migrants > kIslandMaxMigrants || 2 * migrants > cfg->np)
+    return fail(nullptr, DE_ERR_INVALID_ARG, "migrants must be in [1, min(32, np / 2)]");
+  if ((uint64_t)cfg->run_id + (uint64_t)nislands > (1u << 20))
+    return fail(nullptr, DE_ERR_INVALID_ARG, "run_id + nislands must be <= 2^20");
+  if (cfg->precision != DE_PREC_FP64 || cfg->surrogate_k >= 2)
+    return fail(nullptr, DE_ERR_UNSUPPORTED, "the island model runs on the FP64 path without a surrogate");
+  std::vector<de_config> cfgs(nislands, *cfg);
+  for (int k = 0; k < nislands; ++k) cfgs[k].run_id = cfg->run_id + (uint32_t)k;
+  de_handle* h = nullptr;
+  de_status st = de_init_batch(cfgs.data(), nislands, cuda_stream, &h);
+  if (st != DE_OK) return st;
+  const int dp = h->run[0].dp;
+  const size_t n = (size_t)nislands * migrants;
+  const size_t bytes = n * (dp * sizeof(double) + 3 * sizeof(double) + sizeof(int32_t) + 1) + 1024;
+  cudaError_t e = cudaMalloc(&h->isl_mem, bytes + sizeof(IslandCtl));
+  if (e != cudaSuccess) {
+    de_destroy(h);
+    return fail(nullptr, DE_ERR_OOM, "cudaMalloc(island staging) failed");
+  }
+  char* p = (char*)h->isl_mem;
+  h->d_isl = (IslandCtl*)p;
+  p += 256;
+  h->stage.x = (double*)p;
+  p += n * dp * sizeof(double);
+  h->stage.f = (double*)p;
+  p += n * sizeof(double);
+  h->stage.F = (double*)p;
+  p += n * sizeof(double);
+  h->stage.CR = (double*)p;
+  p += n * sizeof(double);
+  h->stage.widx = (int32_t*)p;
+  p += n * sizeof(int32_t);
+  h->stage.fx = (uint8_t*)p;
+  h->stage.dp = dp;
+  h->isl = IslandCtl{nislands, interval, migrants, 0, -1};
+  h->islands = true;
+  drop_graph(h);
+  st = islands_resync(h);
+  if (st == DE_OK) {
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) st = fail(h, DE_ERR_CUDA, std::string("islands: ") + cudaGetErrorString(e));
+  }
+  if (st != DE_OK) {
+    std::string m = h->err;
+    de_destroy(h);
+    g_err = m;
+    return st;
+  }
+  *out = h;
   return DE_OK;
 }
 
@@ -1029,6 +1106,8 @@ de_status de_set_population(de_handle* h, int32_t run, const double* x_host, con
   }
   k_best_init_launch(h->d_run, run, h->stream);
   DE_CUDA(h, cudaGetLastError());
+  s = islands_resync(h);
+  if (s != DE_OK) return s;
   DE_CUDA(h, cudaStreamSynchronize(h->stream));
   return DE_OK;
 }
@@ -1058,6 +1137,8 @@ de_status de_set_generation(de_handle* h, int32_t run, int64_t generation) {
   DE_CUDA(h, cudaMemcpyAsync(&R.st->evals, &ev, sizeof ev, cudaMemcpyHostToDevice, h->stream));
   k_best_init_launch(h->d_run, run, h->stream);
   DE_CUDA(h, cudaGetLastError());
+  s = islands_resync(h);
+  if (s != DE_OK) return s;
   DE_CUDA(h, cudaStreamSynchronize(h->stream));
   return DE_OK;
 }
@@ -1316,6 +1397,9 @@ de_status de_load(de_handle* h, const char* path) {
     DE_CUDA(h, cudaMemcpyAsync(R.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
     DE_CUDA(h, cudaStreamSynchronize(h->stream));
   }
+  const de_status s = islands_resync(h);
+  if (s != DE_OK) return s;
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
   return DE_OK;
 }
 

@@ -1,0 +1,199 @@
+// de_islands.cu -- the island (multi-population) model of DE (Sec. 3.2; on
+// the GPU the multi-population model of Sec. 5.4): the runs of a batch are
+// islands that evolve independently and exchange migrants on a ring.
+//
+// Synchronous migration (Sec. 5.4: the generation kernels end and a
+// migration kernel runs), after every generation g with g % interval == 0:
+//   k_island_select  one CTA per island: the island's nmig best individuals
+//                    (ascending f, lower index first, NaN last) are copied
+//                    to a staging area, and its nmig worst slots (descending
+//                    f, NaN first, higher index first) are recorded;
+//   k_island_apply   one CTA per island: island k writes island k-1's
+//                    migrants (ring) into its worst slots (the q-th best
+//                    into the q-th worst), with their fitness (and jDE
+//                    parameters), then recomputes its best record;
+//   k_island_group   one CTA: the model stops as a whole once any island's
+//                    best is below the target (every island gets stop
+//                    reason "target"), and the migration is marked done.
+// Staging between two kernels makes the exchange independent of the order in
+// which CTAs run: every migrant is read before any island is written.  The
+// three kernels run after every generation and return at once when no
+// migration is due, so a CUDA graph of generations can hold them.
+#include <cuda_runtime.h>
+
+#include "de_common.cuh"
+#include "de_device.cuh"
+#include "de_internal.cuh"
+#include "de_kernels.h"
+
+namespace de {
+
+// a migration is due after generation gen
+__device__ __forceinline__ bool island_due(const IslandCtl* ctl, int64_t gen) {
+  return ctl->interval > 0 && gen > 0 && gen % ctl->interval == 0 && gen > ctl->mig_gen;
+}
+
+// CTA-wide arg-extremum of (key, index) over i in [0, np) minus the `ntaken`
+// indices already chosen; worst = largest (key, index), else smallest.
+__device__ int island_pick(const double* __restrict__ f, int np, const int* taken, int ntaken, bool worst) {
+  __shared__ long long sk[32];
+  __shared__ int si[32];
+  long long bk = worst ? (long long)0x8000000000000000LL : 0x7FFFFFFFFFFFFFFFLL;
+  int bi = -1;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    bool t = false;
+    for (int q = 0; q < ntaken; ++q) t |= taken[q] == i;
+    if (t) continue;
+    const long long k = fit_key(f[i]);
+    const bool take = bi < 0 || (worst ? (k > bk || (k == bk && i > bi)) : (k < bk || (k == bk && i < bi)));
+    if (take) {
+      bk = k;
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    const bool take = oi >= 0 && (bi < 0 || (worst ? (ok > bk || (ok == bk && oi > bi)) : (ok < bk || (ok == bk && oi < bi))));
+    if (take) {
+      bk = ok;
+      bi = oi;
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sk[warp] = bk;
+    si[warp] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      const long long ok = sk[w];
+      const int oi = si[w];
+      const bool take = oi >= 0 && (bi < 0 || (worst ? (ok > bk || (ok == bk && oi > bi)) : (ok < bk || (ok == bk && oi < bi))));
+      if (take) {
+        bk = ok;
+        bi = oi;
+      }
+    }
+    si[0] = bi;
+  }
+  __syncthreads();
+  const int r = si[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_island_select(const RunDesc* __restrict__ runs, const IslandCtl* ctl,
+                                                       IslandStage stage) {
+  const int k = blockIdx.x;
+  const RunDesc& R = runs[k];
+  const int64_t gen = *(volatile int64_t*)&R.st->gen;
+  if (!island_due(ctl, gen)) return;
+  const int cur = (int)(gen & 1), nmig = ctl->nmig;
+  const double* f = R.f[cur];
+  __shared__ int best[kIslandMaxMigrants], worst[kIslandMaxMigrants];
+  for (int q = 0; q < nmig; ++q) {
+    const int b = island_pick(f, R.np, best, q, false);
+    if (threadIdx.x == 0) best[q] = b;
+    __syncthreads();
+  }
+  for (int q = 0; q < nmig; ++q) {
+    const int w = island_pick(f, R.np, worst, q, true);
+    if (threadIdx.x == 0) worst[q] = w;
+    __syncthreads();
+  }
+  for (int q = 0; q < nmig; ++q) {
+    const size_t s = (size_t)k * nmig + q;
+    const double* src = R.X[cur] + (size_t)best[q] * R.dp;
+    for (int j = threadIdx.x; j < R.dp; j += blockDim.x) stage.x[s * stage.dp + j] = src[j];
+    if (threadIdx.x == 0) {
+      stage.f[s] = f[best[q]];
+      stage.fx[s] = R.fx[cur][best[q]];
+      if (R.jde) {
+        stage.F[s] = R.jF[cur][best[q]];
+        stage.CR[s] = R.jCR[cur][best[q]];
+      }
+      stage.widx[s] = worst[q];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_island_apply(const RunDesc* __restrict__ runs, const IslandCtl* ctl,
+                                                      IslandStage stage) {
+  const int k = blockIdx.x, m = ctl->m;
+  const RunDesc& R = runs[k];
+  const int64_t gen = *(volatile int64_t*)&R.st->gen;
+  if (!island_due(ctl, gen)) return;
+  const int cur = (int)(gen & 1), nmig = ctl->nmig;
+  const int from = (k + m - 1) % m;
+  for (int q = 0; q < nmig; ++q) {
+    const size_t s = (size_t)from * nmig + q;
+    const int w = stage.widx[(size_t)k * nmig + q];
+    double* dst = R.X[cur] + (size_t)w * R.dp;
+    for (int j = threadIdx.x; j < R.dp; j += blockDim.x) dst[j] = stage.x[s * stage.dp + j];
+    if (threadIdx.x == 0) {
+      R.f[cur][w] = stage.f[s];
+      R.fx[cur][w] = stage.fx[s];
+      if (R.jde) {
+        R.jF[cur][w] = stage.F[s];
+        R.jCR[cur][w] = stage.CR[s];
+      }
+    }
+  }
+  __syncthreads();
+  // the island's best record after the exchange
+  __shared__ double sf[32];
+  __shared__ long long sk[32];
+  __shared__ int si[32];
+  Best b;
+  b.init();
+  for (int i = threadIdx.x; i < R.np; i += blockDim.x) b.offer(R.f[cur][i], i);
+  b.warp_reduce();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sf[warp] = b.f;
+    sk[warp] = b.k;
+    si[warp] = b.i;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    b.init();
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b.take(sf[w], sk[w], si[w]);
+    if (b.i >= 0) {
+      R.st->best_f = b.f;
+      R.st->best_idx = b.i;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_island_group(const RunDesc* __restrict__ runs, IslandCtl* ctl) {
+  const int m = ctl->m;
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    const RunDesc& R = runs[k];
+    const RunState* st = R.st;
+    if (st->stop == 1 || (R.target > 0.0 && st->best_idx >= 0 && st->best_f < R.target)) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (any)
+    for (int k = threadIdx.x; k < m; k += blockDim.x) runs[k].st->stop = 1;
+  if (threadIdx.x == 0) {
+    const int64_t gen = runs[0].st->gen;
+    if (island_due(ctl, gen)) ctl->mig_gen = gen;
+  }
+}
+
+void k_island_launch(const RunDesc* runs, IslandCtl* ctl, const IslandStage& stage, int m, bool migrate,
+                     cudaStream_t s) {
+  if (migrate) {
+    k_island_select<<<m, 256, 0, s>>>(runs, ctl, stage);
+    k_island_apply<<<m, 256, 0, s>>>(runs, ctl, stage);
+  }
+  k_island_group<<<1, 256, 0, s>>>(runs, ctl);
+}
+
+}  // namespace de

@@ -25,6 +25,28 @@ void k_best_init_launch(const RunDesc* runs, int run, cudaStream_t s);
 void k_jde_init_launch(const RunDesc* runs, int run, int np, cudaStream_t s);
 void k_ode_reference_launch(const RunDesc* runs, int run, double* ref, cudaStream_t s);
 
+// island model (de_islands.cu)
+constexpr int kIslandMaxMigrants = 32;
+struct IslandCtl {
+  int32_t m;         // islands (the runs of the handle)
+  int32_t interval;  // generations between migrations
+  int32_t nmig;      // migrants per island and migration
+  int32_t pad;
+  int64_t mig_gen;   // generation of the last migration (-1: none)
+};
+struct IslandStage {  // m x nmig migrants between the select and apply kernels
+  double* x;          // rows of dp doubles
+  double* f;
+  uint8_t* fx;
+  double* F;          // jDE parameters
+  double* CR;
+  int32_t* widx;      // the receiving island's worst slots
+  int32_t dp;
+};
+// migrate: also run the exchange kernels (else only the group stop test)
+void k_island_launch(const RunDesc* runs, IslandCtl* ctl, const IslandStage& stage, int m, bool migrate,
+                     cudaStream_t s);
+
 // persistent cluster path (de_persist.cu)
 struct PersistCtl {
   unsigned int bar;  // grid barrier arrivals of the current launch

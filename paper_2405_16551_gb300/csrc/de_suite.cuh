@@ -160,32 +160,20 @@ static __device__ __noinline__ double basic_fn_warp(int fn, const double* __rest
   }
 }
 
-// Rotation of a tile with a given transposed matrix: Z[r][j] = sum_k MT[k][j]
-// Y[r][k], flattened over (row, output); a thread runs four outputs as
-// independent accumulator chains (consecutive threads read consecutive j of
-// one row of MT).
+// Rotation of the tile's nrows rows with a given transposed matrix: thread
+// t owns output columns t, t + blockDim, ... and runs one accumulator chain
+// per row (each MT element loaded once serves every row of the tile).
 __device__ __forceinline__ void suite_rotate(const double* __restrict__ MT, const double* __restrict__ Y,
                                              double* __restrict__ Z, int nrows, int d, int dp) {
-  const int nout = nrows * d;
-  const int step = blockDim.x;
-  for (int e0 = threadIdx.x; e0 < nout; e0 += 4 * step) {
-    int rr[4], jj[4];
-    double acc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = min(e0 + q * step, nout - 1);
-      rr[q] = e / d;
-      jj[q] = e - rr[q] * d;
-      acc[q] = 0.0;
-    }
-    for (int k = 0; k < d; ++k) {
-      const double* mk = MT + (size_t)k * d;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fma(__ldg(mk + jj[q]), Y[rr[q] * dp + k], acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (e0 + q * step < nout) Z[rr[q] * dp + jj[q]] = acc[q];
+  switch (nrows) {
+    case 1: tile_rotate_fp64<1>(MT, Y, Z, d, dp); break;
+    case 2: tile_rotate_fp64<2>(MT, Y, Z, d, dp); break;
+    case 3: tile_rotate_fp64<3>(MT, Y, Z, d, dp); break;
+    case 4: tile_rotate_fp64<4>(MT, Y, Z, d, dp); break;
+    case 5: tile_rotate_fp64<5>(MT, Y, Z, d, dp); break;
+    case 6: tile_rotate_fp64<6>(MT, Y, Z, d, dp); break;
+    case 7: tile_rotate_fp64<7>(MT, Y, Z, d, dp); break;
+    default: tile_rotate_fp64<8>(MT, Y, Z, d, dp); break;
   }
 }
 

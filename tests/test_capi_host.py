@@ -131,3 +131,32 @@ def test_eval_noalloc_empty_and_negative_n_on_host():
     lib = capi.load()
     assert lib.de_eval_noalloc(1, 1, 10, 1.0, None, None, None, 10, 0, None, None) == capi.DE_OK
     assert lib.de_eval_noalloc(1, 1, 10, 1.0, None, None, None, 10, -1, None, None) == capi.DE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize(
+    "args,status",
+    [
+        ((1, 5, 1), "DE_ERR_INVALID_ARG"),      # one island
+        ((4, 0, 1), "DE_ERR_INVALID_ARG"),      # no interval
+        ((4, 5, 0), "DE_ERR_INVALID_ARG"),      # no migrants
+        ((4, 5, 33), "DE_ERR_INVALID_ARG"),     # above 32
+        ((4, 5, 40), "DE_ERR_INVALID_ARG"),     # above np / 2
+    ],
+)
+def test_island_arguments_rejected_on_host(args, status):
+    cfg = capi.make_config(64, 10)
+    with pytest.raises(capi.DEError) as ei:
+        capi.de_init_islands(cfg, *args)
+    assert status in str(ei.value)
+
+
+def test_islands_outside_the_fp64_path_are_unsupported_on_host():
+    for kw in (dict(precision=capi.DE_PREC_BF16X3), dict(surrogate_k=4)):
+        cfg = capi.make_config(64, 20, **kw)
+        with pytest.raises(capi.DEError) as ei:
+            capi.de_init_islands(cfg, 4, 5, 1)
+        assert ei.value.status == capi.DE_ERR_UNSUPPORTED
+    cfg = capi.make_config(64, 20, run_id=(1 << 20) - 2)
+    with pytest.raises(capi.DEError) as ei:
+        capi.de_init_islands(cfg, 4, 5, 1)
+    assert ei.value.status == capi.DE_ERR_INVALID_ARG
