@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     p.add_argument("--workload", default="rastrigin",
                    choices=["rastrigin", "sphere_small", "batch512", "ode_surrogate", "stress", "stress_batch",
-                            "variants", "suite"],
+                            "variants", "suite", "islands"],
                    help="rastrigin: the headline configuration (default); the others measure the batched, "
                         "surrogate and large-dimension configurations with the same harness")
     return p.parse_args()
@@ -557,6 +557,47 @@ def run_workload(args, capi, torch, rank, world):
                     forms=forms, protocol={"scores": total, "ranking": protocol.final_ranking(total),
                                            "algorithms": [a.name for a in algs]},
                     gpu_launches=None)
+    elif args.workload == "islands":
+        # the island model against one population of the same total size and
+        # against the same islands without migration, on the 30-D rotated
+        # Rastrigin function of the proposed benchmark (F03), at equal
+        # generations and evaluations
+        m, npi, d, G = 16, 64, 30, int(os.environ.get("DE_BENCH_ISLAND_GENS", "3000"))
+        obj = problems.SUITE[3]
+        data = problems.suite(obj, d, seed=1)
+        forms = {}
+        for name, kind in (("islands_ring_k20_m2", "ring"), ("islands_no_migration", "none"),
+                           ("one_population_np1024", "single")):
+            bests, secs = [], []
+            for seed in (1, 2, 3):
+                c = capi.make_config(npi if kind != "single" else m * npi, d, objective=obj, shift=data["shift"],
+                                     rot=data["rot"], scale=data["scale"], seed=seed, max_generations=G,
+                                     target_error=0.0)
+                if kind == "single":
+                    h = capi.de_init(c, stream=stream.cuda_stream)
+                    nr = 1
+                else:
+                    h = capi.de_init_islands(c, m, 20 if kind == "ring" else 1 << 30, 2, stream=stream.cuda_stream)
+                    nr = m
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = capi.de_run(h, nr)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                secs.append(e0.elapsed_time(e1) / 1e3)
+                bests.append(min(r["best_f"] for r in res))
+                capi.de_destroy(h)
+            forms[name] = {"best_f_per_seed": bests, "median_best_f": float(np.median(bests)),
+                           "seconds_per_run": float(np.mean(secs)),
+                           "trial_evals_per_s": m * npi * G / float(np.mean(secs))}
+        line.update(metric=f"trial evals/sec, island model (16 x NP=64, ring migration every 20 generations, "
+                           f"2 migrants) on the 30-D rotated Rastrigin function F03, FP64",
+                    value=forms["islands_ring_k20_m2"]["trial_evals_per_s"],
+                    ms_per_step=1e3 * forms["islands_ring_k20_m2"]["seconds_per_run"], dtype="f64",
+                    config={"workload": f"F03 D=30, {G} generations, 3 seeds; islands vs no migration vs one "
+                                        "population of 1024", "l2": "working set in L2"},
+                    forms=forms, gpu_launches=None)
     elif args.workload == "stress_batch":
         # 64 runs of the large-dimension shape in one handle (working set far above L2)
         G = min(args.generations, 10)
