@@ -375,7 +375,10 @@ struct ChunkIn {
 };
 
 // Issue the loads of chunk j0 (j0 < d, j0 % 4 == 0) and draw its block.
-__device__ __forceinline__ void trial_load(const RunDesc& R, const double* __restrict__ X, const TrialSetup& s,
+// The rows are read at L2 (ld.global.cg): the persistent kernels read, in
+// generation g, population rows other CTAs wrote in generation g - 1, so the
+// loads must not come from a non-coherent per-SM cache.
+__device__ __forceinline__ void trial_load(const RunDesc& R, const double* X, const TrialSetup& s,
                                            uint32_t i, int64_t g, int j0, ChunkIn& c, uint32_t cand = 0u) {
   c.u = draw_block(R.seed, kPurposeStep, R.run_id, cand, (uint32_t)g, i, 1u + (uint32_t)(j0 >> 2));
   const double* rows[4] = {X + (size_t)i * R.dp + j0, X + (size_t)s.r1 * R.dp + j0, X + (size_t)s.r2 * R.dp + j0,
@@ -383,8 +386,8 @@ __device__ __forceinline__ void trial_load(const RunDesc& R, const double* __res
   double* dst[4] = {c.xi, c.x1, c.x2, c.x3};
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const double2 a = *reinterpret_cast<const double2*>(rows[r]);
-    const double2 b = *reinterpret_cast<const double2*>(rows[r] + 2);
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(rows[r]));
+    const double2 b = __ldcg(reinterpret_cast<const double2*>(rows[r] + 2));
     dst[r][0] = a.x;
     dst[r][1] = a.y;
     dst[r][2] = b.x;
