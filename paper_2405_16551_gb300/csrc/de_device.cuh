@@ -472,12 +472,12 @@ struct TrialVar {
 // a0..a3 of the JDE stream of (i, g); with probability 0.1 each
 // (a1 resp. a3 below floor(0.1 2^32)) F_i = 0.1 + 0.9 a0 / 2^32 (one
 // rounding) and CR_i = a2 / 2^32, otherwise the stored values.
-__device__ __forceinline__ void jde_params(const RunDesc& R, uint32_t i, int64_t g, const double* __restrict__ jF,
-                                           const double* __restrict__ jCR, double& F, double& CR) {
+__device__ __forceinline__ void jde_params(const RunDesc& R, uint32_t i, int64_t g, const double* jF,
+                                           const double* jCR, double& F, double& CR) {
   const uint32_t tau = 429496729u;  // floor(0.1 * 2^32)
   const U32x4 a = draw_block(R.seed, kPurposeJde, R.run_id, 0u, (uint32_t)g, i, 0u);
-  F = a.y < tau ? __fma_rn(0.9, (double)a.x * 0x1p-32, 0.1) : jF[i];
-  CR = a.w < tau ? (double)a.z * 0x1p-32 : jCR[i];
+  F = a.y < tau ? __fma_rn(0.9, (double)a.x * 0x1p-32, 0.1) : __ldcg(jF + i);
+  CR = a.w < tau ? (double)a.z * 0x1p-32 : __ldcg(jCR + i);
 }
 
 // Exponential crossover length (Sec. 2): L = 1 + the number of leading
@@ -510,8 +510,7 @@ __device__ __forceinline__ int exp_length(const RunDesc& R, uint32_t i, int64_t 
 // then for DE/best/1 takes the base from row `best` and the difference from
 // the first two drawn donors.  Called by the whole warp.
 __device__ __forceinline__ TrialSetup trial_setup_var(const RunDesc& R, uint32_t i, int64_t g, int lane, int best,
-                                                      const double* __restrict__ jF, const double* __restrict__ jCR,
-                                                      TrialVar& v) {
+                                                      const double* jF, const double* jCR, TrialVar& v) {
   TrialSetup s = trial_setup(R, i, g, lane);
   if (R.strategy == 1) {
     s.r3 = s.r2;
@@ -552,11 +551,10 @@ __device__ __forceinline__ void trial_debug(const RunDesc& R, uint32_t i, int j0
 // VAR: the run may use a strategy variant or jDE (best: the current best row;
 // jF, jCR: the current jDE parameters).
 template <bool VAR>
-__device__ __forceinline__ void build_trial_row(const RunDesc& R, const double* __restrict__ X, uint32_t i,
+__device__ __forceinline__ void build_trial_row(const RunDesc& R, const double* X, uint32_t i,
                                                 int64_t g, int lane, double* __restrict__ Trow,
                                                 double* __restrict__ Yrow, int best = 0,
-                                                const double* __restrict__ jF = nullptr,
-                                                const double* __restrict__ jCR = nullptr) {
+                                                const double* jF = nullptr, const double* jCR = nullptr) {
   TrialVar v;
   const TrialSetup s = VAR ? trial_setup_var(R, i, g, lane, best, jF, jCR, v) : trial_setup(R, i, g, lane);
   const bool dbg = R.dbg_trial != nullptr;

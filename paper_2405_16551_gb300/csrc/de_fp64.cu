@@ -199,50 +199,24 @@ __device__ __forceinline__ void rotate_groups(const RunDesc& R, const double* __
     if (ok[q]) Z[rr[q] * dp + jj[q]] = acc[q];
 }
 
-// items: (run, tile, first row, rows); the rows of all runs are spread over
-// about one CTA per SM so that every SM's FP64 pipe gets the same work.
-// Shared memory: T (trials), Y (shifted trials), Z (rotated), W (second term
-// sum of Ackley), each R.rows x dp doubles.
-// VAR: some run of the launch uses a strategy variant or jDE; SUITE: some
-// run uses a function of the proposed benchmark (objectives 5..20).  Separate
-// instances, so that plain DE/rand/1/bin keeps its register allocation.
+// One tile of generation g: the trials of targets row0 .. row0 + nrows - 1
+// (a warp per target), their fitness, and greedy selection into the other
+// population buffer.  Shared memory sm: T (trials), Y (shifted trials), Z
+// (rotated), W (second term sum of Ackley), each rows_max x dp doubles.
+// best: the current population's best row (DE/best/1).  Returns the calling
+// warp's best (f, index) over the tile's new population rows (the same in
+// every lane).  Population rows, fitness and jDE parameters of generation
+// g - 1 are read at L2.
+// VAR / SUITE: strategy variants and jDE / the benchmark suite's objectives.
 template <bool VAR, bool SUITE>
-__global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ runs,
-                                                  const int4* __restrict__ items) {
-  extern __shared__ __align__(16) double sm[];
-  __shared__ int s_stop, s_last, s_best;
-  __shared__ long long s_gen;
-  __shared__ double s_bf[8];
-  __shared__ long long s_bk[8];
-  __shared__ int s_bi[8];
-  const int4 it = items[blockIdx.x];
-  // the run descriptor in shared memory: its fields are read in every phase,
-  // after barriers that would force global reloads
-  __shared__ RunDesc sR;
-  for (int q = threadIdx.x; q < (int)(sizeof(RunDesc) / 8); q += blockDim.x)
-    reinterpret_cast<uint64_t*>(&sR)[q] = reinterpret_cast<const uint64_t*>(runs + it.x)[q];
-  const RunDesc& R = sR;
-  pdl_launch_dependents();
-  pdl_wait();
-  __syncthreads();
-  RunState* st = R.st;
-  if (threadIdx.x == 0) {
-    s_stop = *(volatile int32_t*)&st->stop;
-    s_gen = *(volatile int64_t*)&st->gen;
-    // DE/best/1: the lowest-index best of the current population (row 0
-    // when no fitness is finite)
-    s_best = max(*(volatile int32_t*)&st->best_idx, 0);
-  }
-  __syncthreads();
-  if (s_stop) return;
-  const int64_t g = s_gen + 1;
-  const int cur = (int)(s_gen & 1), nxt = cur ^ 1;
-  const double* __restrict__ X = R.X[cur];
+__device__ __forceinline__ Best gen_tile(const RunDesc& R, int64_t g, int row0, int nrows, int rows_max, int best,
+                                         double* sm, double* s_fsuite, double (*s_comp)[10]) {
+  const int cur = (int)((g - 1) & 1), nxt = cur ^ 1;
+  const double* X = R.X[cur];
   double* __restrict__ Xn = R.X[nxt];
-  const double* __restrict__ fX = R.f[cur];
+  const double* fX = R.f[cur];
   double* __restrict__ fn = R.f[nxt];
   const int d = R.d, dp = R.dp;
-  const int row0 = it.z, nrows = it.w, rows_max = R.rows;
   double* T = sm;
   double* Y = T + rows_max * dp;
   double* Z = Y + rows_max * dp;
@@ -251,11 +225,11 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
 
   // ---- trials (a warp per target)
   const bool var = VAR && (R.strategy != 0 || R.jde);
-  const double* __restrict__ jFc = VAR && R.jde ? R.jF[cur] : nullptr;
-  const double* __restrict__ jCRc = VAR && R.jde ? R.jCR[cur] : nullptr;
+  const double* jFc = VAR && R.jde ? R.jF[cur] : nullptr;
+  const double* jCRc = VAR && R.jde ? R.jCR[cur] : nullptr;
   if (var) {
     for (int rl = warp; rl < nrows; rl += nwarps)
-      build_trial_row<true>(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp, s_best, jFc, jCRc);
+      build_trial_row<true>(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp, best, jFc, jCRc);
   } else {
     for (int rl = warp; rl < nrows; rl += nwarps)
       build_trial_row<false>(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp);
@@ -263,8 +237,6 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   __syncthreads();
 
   const int nout = nrows * d;
-  __shared__ double s_fsuite[kSuiteMaxRows];
-  __shared__ double s_comp[kSuiteMaxRows][10];
   const bool suite = SUITE && suite_objective(R.obj);
   if (suite) {
     // ---- the proposed benchmark's functions (Sec. 7.3, Table 2)
@@ -277,51 +249,51 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
     }
     __syncthreads();
   } else {
-  // ---- rotation, flattened over (row, output): output e = 32 w + lane of
-  // warp-group w; a warp takes groups warp, warp + 8, ... and runs up to four
-  // of them at once (independent accumulator chains)
-  if (R.rotate) {
-    const int ngroups = (nout + 31) / 32;
-    for (int w0 = warp; w0 < ngroups; w0 += 4 * nwarps) {
-      const int qn = min(4, (ngroups - w0 + nwarps - 1) / nwarps);  // uniform in the warp
-      if (qn == 4) rotate_groups<4>(R, Y, Z, w0, nwarps, lane, nout, dp);
-      else if (qn == 3) rotate_groups<3>(R, Y, Z, w0, nwarps, lane, nout, dp);
-      else if (qn == 2) rotate_groups<2>(R, Y, Z, w0, nwarps, lane, nout, dp);
-      else rotate_groups<1>(R, Y, Z, w0, nwarps, lane, nout, dp);
-    }
-  } else {
-    for (int e = tid; e < nout; e += blockDim.x) {
-      const int r = e / d, j = e - r * d;
-      Z[r * dp + j] = Y[r * dp + j];
-    }
-  }
-  __syncthreads();
-
-  // ---- objective terms, flattened; Y and W receive the per-coordinate terms
-  for (int e = tid; e < nout; e += blockDim.x) {
-    const int r = e / d, j = e - r * d;
-    const double z = Z[r * dp + j];
-    double t1 = 0.0, t2 = 0.0;
-    if (R.obj == kObjSphere) {
-      t1 = z * z;
-    } else if (R.obj == kObjRastrigin) {
-      t1 = z * z - 10.0 * cos2pi_f64_horner(z) + 10.0;
-    } else if (R.obj == kObjAckley) {
-      t1 = z * z;
-      t2 = cos2pi_f64_horner(z);
-    } else if (R.obj == kObjRosenbrock) {
-      if (j + 1 < d) {
-        const double t0 = z + 1.0, tn = Z[r * dp + j + 1] + 1.0;
-        const double a = tn - t0 * t0, b = t0 - 1.0;
-        t1 = 100.0 * a * a + b * b;
+    // ---- rotation, flattened over (row, output): output e = 32 w + lane of
+    // warp-group w; a warp takes groups warp, warp + 8, ... and runs up to four
+    // of them at once (independent accumulator chains)
+    if (R.rotate) {
+      const int ngroups = (nout + 31) / 32;
+      for (int w0 = warp; w0 < ngroups; w0 += 4 * nwarps) {
+        const int qn = min(4, (ngroups - w0 + nwarps - 1) / nwarps);  // uniform in the warp
+        if (qn == 4) rotate_groups<4>(R, Y, Z, w0, nwarps, lane, nout, dp);
+        else if (qn == 3) rotate_groups<3>(R, Y, Z, w0, nwarps, lane, nout, dp);
+        else if (qn == 2) rotate_groups<2>(R, Y, Z, w0, nwarps, lane, nout, dp);
+        else rotate_groups<1>(R, Y, Z, w0, nwarps, lane, nout, dp);
       }
     } else {
-      t1 = CUDART_NAN;
+      for (int e = tid; e < nout; e += blockDim.x) {
+        const int r = e / d, j = e - r * d;
+        Z[r * dp + j] = Y[r * dp + j];
+      }
     }
-    Y[r * dp + j] = t1;
-    W[r * dp + j] = t2;
-  }
-  __syncthreads();
+    __syncthreads();
+
+    // ---- objective terms, flattened; Y and W receive the per-coordinate terms
+    for (int e = tid; e < nout; e += blockDim.x) {
+      const int r = e / d, j = e - r * d;
+      const double z = Z[r * dp + j];
+      double t1 = 0.0, t2 = 0.0;
+      if (R.obj == kObjSphere) {
+        t1 = z * z;
+      } else if (R.obj == kObjRastrigin) {
+        t1 = z * z - 10.0 * cos2pi_f64_horner(z) + 10.0;
+      } else if (R.obj == kObjAckley) {
+        t1 = z * z;
+        t2 = cos2pi_f64_horner(z);
+      } else if (R.obj == kObjRosenbrock) {
+        if (j + 1 < d) {
+          const double t0 = z + 1.0, tn = Z[r * dp + j + 1] + 1.0;
+          const double a = tn - t0 * t0, b = t0 - 1.0;
+          t1 = 100.0 * a * a + b * b;
+        }
+      } else {
+        t1 = CUDART_NAN;
+      }
+      Y[r * dp + j] = t1;
+      W[r * dp + j] = t2;
+    }
+    __syncthreads();
   }
 
   // ---- row sums, greedy selection, best partial (a warp per row)
@@ -344,15 +316,20 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
       s2 = warp_sum(s2);
       ft = R.obj == kObjAckley ? 20.0 + 2.718281828459045 - 20.0 * exp(-0.2 * sqrt(s1 / d)) - exp(s2 / d) : s1;
     }
-    const double fi = fX[i];
+    const double fi = __ldcg(fX + i);
     const bool acc = fit_key(ft) <= fit_key(fi) && fit_key(ft) != 0x7FFFFFFFFFFFFFFFLL;  // ft <= fi, NaN never
-    const double* src = acc ? (T + rl * dp) : (X + (size_t)i * dp);
     double2* dst = reinterpret_cast<double2*>(Xn + (size_t)i * dp);
-    for (int j = lane; j < dp / 2; j += 32) dst[j] = reinterpret_cast<const double2*>(src)[j];
+    if (acc) {
+      const double2* src = reinterpret_cast<const double2*>(T + rl * dp);
+      for (int j = lane; j < dp / 2; j += 32) dst[j] = src[j];
+    } else {
+      const double2* src = reinterpret_cast<const double2*>(X + (size_t)i * dp);
+      for (int j = lane; j < dp / 2; j += 32) dst[j] = __ldcg(src + j);
+    }
     const double fnew = acc ? ft : fi;
     if (VAR && R.jde && lane == 0) {
       // jDE: an accepted trial passes its F_i and CR_i on
-      double Fi = jFc[i], CRi = jCRc[i];
+      double Fi = __ldcg(jFc + i), CRi = __ldcg(jCRc + i);
       if (acc) jde_params(R, (uint32_t)i, g, jFc, jCRc, Fi, CRi);
       R.jF[nxt][i] = Fi;
       R.jCR[nxt][i] = CRi;
@@ -367,6 +344,52 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
     }
     bb.offer(fnew, i);
   }
+  return bb;
+}
+
+// Copy of a run descriptor into shared memory (its fields are read in every
+// phase, after barriers that would force global reloads).
+__device__ __forceinline__ void load_desc(RunDesc& sR, const RunDesc* src) {
+  for (int q = threadIdx.x; q < (int)(sizeof(RunDesc) / 8); q += blockDim.x)
+    reinterpret_cast<uint64_t*>(&sR)[q] = reinterpret_cast<const uint64_t*>(src)[q];
+}
+
+// items: (run, tile, first row, rows); the rows of all runs are spread over
+// about one CTA per SM so that every SM's FP64 pipe gets the same work.
+// VAR: some run of the launch uses a strategy variant or jDE; SUITE: some
+// run uses a function of the proposed benchmark (objectives 5..20).  Separate
+// instances, so that plain DE/rand/1/bin keeps its register allocation.
+template <bool VAR, bool SUITE>
+__global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ runs,
+                                                  const int4* __restrict__ items) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int s_stop, s_last, s_best;
+  __shared__ long long s_gen;
+  __shared__ double s_bf[8];
+  __shared__ long long s_bk[8];
+  __shared__ int s_bi[8];
+  __shared__ double s_fsuite[kSuiteMaxRows];
+  __shared__ double s_comp[kSuiteMaxRows][10];
+  const int4 it = items[blockIdx.x];
+  __shared__ RunDesc sR;
+  load_desc(sR, runs + it.x);
+  const RunDesc& R = sR;
+  pdl_launch_dependents();
+  pdl_wait();
+  __syncthreads();
+  RunState* st = R.st;
+  if (threadIdx.x == 0) {
+    s_stop = *(volatile int32_t*)&st->stop;
+    s_gen = *(volatile int64_t*)&st->gen;
+    // DE/best/1: the lowest-index best of the current population (row 0
+    // when no fitness is finite)
+    s_best = max(*(volatile int32_t*)&st->best_idx, 0);
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const int64_t g = s_gen + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+  Best bb = gen_tile<VAR, SUITE>(R, g, it.z, it.w, R.rows, s_best, sm, s_fsuite, s_comp);
   if (lane == 0) { s_bf[warp] = bb.f; s_bk[warp] = bb.k; s_bi[warp] = bb.i; }
   __syncthreads();
   if (tid == 0) {
@@ -381,7 +404,7 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   __syncthreads();
   if (s_last) {
     __threadfence();
-    finish_generation(R, g, R.ntiles, R.part, Xn);
+    finish_generation(R, g, R.ntiles, R.part, R.X[g & 1]);
   }
 }
 
