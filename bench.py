@@ -496,21 +496,23 @@ def run_workload(args, capi, torch, rank, world):
         n, d = 1024, 100
         o, M = problems.shift(d, seed=1), problems.rotation(d, seed=1)
         forms = {}
-        for name, st, jde in (("rand1bin", 0, False), ("best1bin", 1, False), ("rand1exp", 2, False),
-                              ("jde_rand1bin", 0, True), ("jde_rand1exp", 2, True)):
+        for name, st, jde, prec in (("rand1bin", 0, False, 0), ("best1bin", 1, False, 0), ("rand1exp", 2, False, 0),
+                                    ("jde_rand1bin", 0, True, 0), ("jde_rand1exp", 2, True, 0),
+                                    ("bf16x3_rand1bin", 0, False, 1), ("bf16x3_jde_rand1bin", 0, True, 1),
+                                    ("bf16x3_jde_rand1exp", 2, True, 1)):
             c = capi.make_config(n, d, objective=1, shift=o, rot=M, seed=1, target_error=0.0, max_generations=G,
-                                 strategy=st, jde=jde)
+                                 strategy=st, jde=jde, precision=prec)
             h = capi.de_init(c, stream=stream.cuda_stream)
             ms = _timed(torch, stream, flush, steps, warmup, lambda: (capi.de_reset(h), capi.de_step(h, G)))
             b = capi.de_get_best(h)
             capi.de_destroy(h)
             forms[name] = {"trial_evals_per_s": n * G * steps / (ms / 1e3), "ms_per_step": ms / steps,
                            "us_per_generation": 1e3 * ms / steps / G, "best_f_after": b["best_f"]}
-        line.update(metric="trial evals/sec, NP=1024 D=100 rotated-shifted Rastrigin FP64, per DE variant",
+        line.update(metric="trial evals/sec, NP=1024 D=100 rotated-shifted Rastrigin, jDE (FP64), per DE variant",
                     value=forms["jde_rand1bin"]["trial_evals_per_s"], ms_per_step=forms["jde_rand1bin"]["ms_per_step"],
-                    dtype="f64", config={"workload": f"NP=1024 D=100 Rastrigin, {G} generations per step, FP64",
+                    dtype="f64", config={"workload": f"NP=1024 D=100 Rastrigin, {G} generations per step, FP64 and BF16x3 forms",
                                          "l2": "flushed between steps (512 MiB write)"},
-                    forms=forms, gpu_launches=steps * 5 * (3 + G))
+                    forms=forms, gpu_launches=None)
     elif args.workload == "suite":
         # the proposed 100-D benchmark (F01-F10) in the configuration of the
         # paper's timing study: DE/rand/1/bin, NP = 250, F = 0.5, CR = 0.3,

@@ -193,10 +193,10 @@ typedef struct {
                                  candidate trials per target (FP64, d == 20, one run per handle; see
                                  de_get_surrogate_stats) */
     int32_t surrogate_steps;  /* Adam steps per retraining of the surrogate; 0 = 100 */
-    int32_t strategy;         /* de_strategy: base vector and crossover of the trial (Sec. 2); FP64 only
-                                 for values other than DE_RAND1BIN */
+    int32_t strategy;         /* de_strategy: base vector and crossover of the trial (Sec. 2); not with a
+                                 surrogate */
     int32_t jde;              /* nonzero: jDE self-adaptive F and CR per individual (Sec. 2, the adaptive
-                                 variant); f and cr are the initial values; FP64 only */
+                                 variant); f and cr are the initial values; not with a surrogate */
     const int32_t* perm;      /* host, d indices: the permutation of a hybrid function (position k of the
                                  permuted vector is z[perm[k]]), or NULL for the identity; must be NULL
                                  for other objectives; copied by de_init */

@@ -648,10 +648,9 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
       return fail(nullptr, DE_ERR_INVALID_ARG, "all runs of a batch must share the precision");
     if (cfgs[r].surrogate_k >= 2 && nruns != 1)
       return fail(nullptr, DE_ERR_INVALID_ARG, "surrogate-assisted generations take one run per handle");
-    if ((cfgs[r].strategy != DE_RAND1BIN || cfgs[r].jde) &&
-        (cfgs[r].precision != DE_PREC_FP64 || cfgs[r].surrogate_k >= 2))
+    if ((cfgs[r].strategy != DE_RAND1BIN || cfgs[r].jde) && cfgs[r].surrogate_k >= 2)
       return fail(nullptr, DE_ERR_UNSUPPORTED,
-                  "the best/1/bin and rand/1/exp strategies and jDE run on the FP64 path without a surrogate");
+                  "the best/1/bin and rand/1/exp strategies and jDE run without a surrogate");
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -56,6 +56,7 @@ struct PersistCtl {
 struct PersistPlan {
   bool ok = false;
   int C = 0, ntiles = 0, prec = 0, nch = 1, prows = 128;
+  bool var = false;  // the run uses a strategy variant or jDE
   size_t smem = 0;
 };
 
@@ -77,6 +78,7 @@ struct TcPlan {
   int trial_rows = 8;          // targets (warps) per trial CTA
   int nsplit = 1;              // N tiles spread over CTAs of the fitness kernel (the largest N-tile count)
   int nruns = 0;
+  bool var = false;            // some run uses a strategy variant or jDE
   PersistPlan persist;         // the persistent cluster kernel, when it applies
   PersistCtl* d_ctl = nullptr;
 };

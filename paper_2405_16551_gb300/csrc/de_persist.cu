@@ -74,8 +74,10 @@ __device__ bool grid_barrier(PersistCtl* ctl, unsigned target) {
   return false;
 }
 
-// NCH: 128-coordinate chunks per row (1 for d <= 128, 2 for d <= 256)
-template <int ESZ, int NCH>
+// NCH: 128-coordinate chunks per row (1 for d <= 128, 2 for d <= 256);
+// VAR: the run uses a strategy variant or jDE (a separate instance, so that
+// plain DE/rand/1/bin keeps its register allocation)
+template <int ESZ, int NCH, bool VAR>
 __global__ void __launch_bounds__(256, 1)
     k_persist(const RunDesc* __restrict__ runs, int run, PersistCtl* ctl, long long gens, int prows) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(256, 1)
   __shared__ int s_blist[kTileM];
   __shared__ float s_part[5][kTileM];
   __shared__ double s_bpart[2 * kPBandMax][kPMaxC][2];
-  __shared__ int s_nb, s_stop, s_abort;
+  __shared__ int s_nb, s_stop, s_abort, s_bidx;
   __shared__ long long s_gen;
   __shared__ double s_best;
   __shared__ double s_bf[8];
@@ -145,6 +147,7 @@ __global__ void __launch_bounds__(256, 1)
   int* l_stop = cluster.map_shared_rank(&s_stop, 0);
   int* l_abort = cluster.map_shared_rank(&s_abort, 0);
   double* l_best = cluster.map_shared_rank(&s_best, 0);
+  int* l_bidx = cluster.map_shared_rank(&s_bidx, 0);
   long long* l_gen = cluster.map_shared_rank(&s_gen, 0);
 
   const uint32_t bar_b = smem_u32(&s_bar[0]), bar_mma = smem_u32(&s_bar[1]);
@@ -163,6 +166,7 @@ __global__ void __launch_bounds__(256, 1)
       s_gen = *(volatile int64_t*)&st->gen;
       s_stop = *(volatile int32_t*)&st->stop;
       s_best = *(volatile double*)&st->best_f;
+      s_bidx = max(*(volatile int32_t*)&st->best_idx, 0);  // DE/best/1 base (row 0 when none is finite)
       s_abort = 0;
       s_nband_total = 0;
       if (blockIdx.x == 0) ctl->gen0 = s_gen;  // generation counter at launch, for the trial count
@@ -219,6 +223,7 @@ __global__ void __launch_bounds__(256, 1)
   long long gen = *l_gen;
   int stop = *l_stop;
   double best_prev = *l_best;
+  int best_idx = *l_bidx;
   bool abort = *l_abort != 0;
 
   for (long long itg = 0; itg < gens && !stop && !abort; ++itg) {
@@ -226,6 +231,8 @@ __global__ void __launch_bounds__(256, 1)
     const int cur = (int)(gen & 1), nxt = cur ^ 1;
     const double* __restrict__ X = R.X[cur];
     double* __restrict__ Xn = R.X[nxt];
+    const double* jFc = VAR && R.jde ? R.jF[cur] : nullptr;
+    const double* jCRc = VAR && R.jde ? R.jCR[cur] : nullptr;
 
     // ---- 1. trials of this CTA's rows -> registers and the leader's operand tile;
     // all loads of the warp's rows are issued before any of them is used
@@ -234,13 +241,15 @@ __global__ void __launch_bounds__(256, 1)
     for (int qb = 0; qb < 2; qb += QB) {
       TrialSetup ts[2];
       ChunkIn cin[2][NCH];
+      TrialVar tv[2];
       bool valid[2] = {false, false};
 #pragma unroll
       for (int q = qb; q < qb + QB; ++q) {
         const int i = row0 + crank * rpm + warp + 8 * q;
         valid[q] = warp + 8 * q < rpm && i < np;
         if (valid[q]) {
-          ts[q] = trial_setup(R, (uint32_t)i, g, lane);
+          if constexpr (VAR) ts[q] = trial_setup_var(R, (uint32_t)i, g, lane, best_idx, jFc, jCRc, tv[q]);
+          else ts[q] = trial_setup(R, (uint32_t)i, g, lane);
 #pragma unroll
           for (int c = 0; c < NCH; ++c) {
             const int j0 = 128 * c + 4 * lane;
@@ -260,7 +269,8 @@ __global__ void __launch_bounds__(256, 1)
           double t[4] = {0.0, 0.0, 0.0, 0.0};
           uint32_t bits = 0;
           if (j0 < d) {
-            bits = trial_compute(R, ts[q], j0, cin[q][c], t);
+            if constexpr (VAR) bits = trial_compute(R, ts[q], j0, cin[q][c], t, tv[q].F, tv[q].thr, tv[q].L);
+            else bits = trial_compute(R, ts[q], j0, cin[q][c], t);
 #pragma unroll
             for (int e = 0; e < 4; ++e) tx[q][c][e] = cin[q][c].xi[e];
           }
@@ -555,6 +565,13 @@ __global__ void __launch_bounds__(256, 1)
       const int i = row0 + lr;
       if (i >= np) continue;
       const bool acc = l_flag[lr] & 1;
+      if (VAR && R.jde && lane == 0) {
+        // jDE: an accepted trial passes its F_i and CR_i on
+        double Fi = __ldcg(jFc + i), CRi = __ldcg(jCRc + i);
+        if (acc) jde_params(R, (uint32_t)i, g, jFc, jCRc, Fi, CRi);
+        R.jF[nxt][i] = Fi;
+        R.jCR[nxt][i] = CRi;
+      }
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
         const int j0 = 128 * c + 4 * lane;
@@ -596,6 +613,7 @@ __global__ void __launch_bounds__(256, 1)
         else if (g >= R.max_gens) sp = 3;
         s_stop = sp;
         s_best = bf;
+        if (bi >= 0) s_bidx = bi;
         s_gen = g;
         if (tile == 0) {
           // one writer of the run state; evals are published at the end
@@ -610,6 +628,7 @@ __global__ void __launch_bounds__(256, 1)
     gen = *l_gen;
     stop = *l_stop;
     best_prev = *l_best;
+    best_idx = *l_bidx;
     abort = *l_abort != 0;
   }
 
@@ -680,7 +699,9 @@ bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
   };
-  const cudaError_t e = prec == DE_PREC_BF16X3 ? query(k_persist<2, 1>) : query(k_persist<4, 1>);
+  const bool var = R.strategy != 0 || R.jde;
+  const cudaError_t e = prec == DE_PREC_BF16X3 ? (var ? query(k_persist<2, 1, true>) : query(k_persist<2, 1, false>))
+                                               : (var ? query(k_persist<4, 1, true>) : query(k_persist<4, 1, false>));
   if (e != cudaSuccess || nclusters < 1) {
     cudaGetLastError();
     return false;
@@ -700,6 +721,7 @@ bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
   pp.prec = prec;
   pp.nch = 1;
   pp.prows = prows;
+  pp.var = var;
   return true;
 }
 
@@ -719,8 +741,13 @@ cudaError_t persist_launch(const PersistPlan& pp, const RunDesc* runs, PersistCt
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (pp.prec == DE_PREC_BF16X3) e = cudaLaunchKernelEx(&cfg, k_persist<2, 1>, runs, 0, ctl, gens, pp.prows);
-  else e = cudaLaunchKernelEx(&cfg, k_persist<4, 1>, runs, 0, ctl, gens, pp.prows);
+  if (pp.prec == DE_PREC_BF16X3) {
+    if (pp.var) e = cudaLaunchKernelEx(&cfg, k_persist<2, 1, true>, runs, 0, ctl, gens, pp.prows);
+    else e = cudaLaunchKernelEx(&cfg, k_persist<2, 1, false>, runs, 0, ctl, gens, pp.prows);
+  } else {
+    if (pp.var) e = cudaLaunchKernelEx(&cfg, k_persist<4, 1, true>, runs, 0, ctl, gens, pp.prows);
+    else e = cudaLaunchKernelEx(&cfg, k_persist<4, 1, false>, runs, 0, ctl, gens, pp.prows);
+  }
   if (e != cudaSuccess) return e;
   k_persist_close<<<1, 1, 0, s>>>(runs, 0, ctl);
   return cudaGetLastError();

@@ -61,9 +61,10 @@ namespace de {
 // ------------------------------------------------------------------ trial kernel
 // items: (run, group of blockDim / 32 targets); warp w of the CTA takes
 // target group * (blockDim / 32) + w.
-template <int ESZ>
+// VAR: some run uses a strategy variant or jDE (a separate instance).
+template <int ESZ, bool VAR>
 __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__ runs, const int2* __restrict__ items) {
-  __shared__ int s_stop;
+  __shared__ int s_stop, s_best;
   __shared__ long long s_gen;
   const int2 it = items[blockIdx.x];
   const RunDesc& R = runs[it.x];
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
   if (threadIdx.x == 0) {
     s_stop = *(volatile int32_t*)&R.st->stop;
     s_gen = *(volatile int64_t*)&R.st->gen;
+    s_best = max(*(volatile int32_t*)&R.st->best_idx, 0);  // DE/best/1 base (row 0 when none is finite)
   }
   __syncthreads();
   if (s_stop) return;
@@ -82,7 +84,11 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
   const int i = it.y * (int)(blockDim.x >> 5) + warp;
   if (i >= R.np) return;
   const double* X = R.X[0];
-  const TrialSetup s = trial_setup(R, (uint32_t)i, g, lane);
+  TrialVar v;
+  TrialSetup s;
+  if constexpr (VAR) s = trial_setup_var(R, (uint32_t)i, g, lane, s_best, R.jde ? R.jF[0] : nullptr,
+                                         R.jde ? R.jCR[0] : nullptr, v);
+  else s = trial_setup(R, (uint32_t)i, g, lane);
   uint8_t* Ahi = R.A + (size_t)(i >> 7) * R.a_tile_bytes;
   const uint32_t a_part = (uint32_t)(R.a_tile_bytes / 2);
   const int m = i & 127;
@@ -98,7 +104,8 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
     double t[4] = {0.0, 0.0, 0.0, 0.0};
     uint32_t bits = 0;
     if (j0 < R.d) {
-      bits = trial_compute(R, s, j0, cur, t);
+      if constexpr (VAR) bits = trial_compute(R, s, j0, cur, t, v.F, v.thr, v.L);
+      else bits = trial_compute(R, s, j0, cur, t);
       double* Trow = R.T + (size_t)i * R.dp + j0;
       *reinterpret_cast<double2*>(Trow) = make_double2(t[0], t[1]);
       *reinterpret_cast<double2*>(Trow + 2) = make_double2(t[2], t[3]);
@@ -503,6 +510,13 @@ __global__ void __launch_bounds__(kFitThreads, 1)
         R.fx[0][i] = 0;
         R.tau[i] = s_taunew[mm];
         s_acc[atomicAdd(&s_nacc, 1)] = mm;
+        if (R.jde) {
+          // jDE: the accepted trial's F_i and CR_i replace the target's (in place)
+          double Fi, CRi;
+          jde_params(R, (uint32_t)i, s_gen + 1, R.jF[0], R.jCR[0], Fi, CRi);
+          R.jF[0][i] = Fi;
+          R.jCR[0][i] = CRi;
+        }
       }
       if (R.dbg_ftrial) {
         R.dbg_ftrial[i] = s_ftrial[mm];
@@ -665,6 +679,13 @@ __global__ void __launch_bounds__(256) k_band_fp64(const RunDesc* __restrict__ r
           R.f[0][i] = acc ? ft : fi;
           R.fx[0][i] = 1;
           R.tau[i] = 0.f;
+          if (acc && R.jde) {
+            // jDE: the accepted trial's F_i and CR_i replace the target's (in place)
+            double Fi, CRi;
+            jde_params(R, (uint32_t)i, *(volatile int64_t*)&R.st->gen + 1, R.jF[0], R.jCR[0], Fi, CRi);
+            R.jF[0][i] = Fi;
+            R.jCR[0][i] = CRi;
+          }
           if (R.dbg_ftrial) {
             R.dbg_ftrial[i] = ft;
             R.dbg_accept[i] = acc ? 1 : 0;
@@ -776,6 +797,8 @@ static void pack_b(const de_config& c, const RunDesc& R, std::vector<uint8_t>& o
 de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* cfgs, int prec, cudaStream_t s,
                         std::string& err) {
   p.prec = prec;
+  p.var = false;
+  for (const auto& R : runs) p.var = p.var || R.strategy != 0 || R.jde;
   const int esz = prec == DE_PREC_BF16X3 ? 2 : 4;
   size_t bytes = 0;
   std::vector<size_t> offA(runs.size()), offB(runs.size()), offY(runs.size()), offT(runs.size()), offS(runs.size());
@@ -1004,11 +1027,13 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int block, si
 void tc_generation_launch(const TcPlan& p, const RunDesc* runs, cudaStream_t s) {
   const int tb = 32 * p.trial_rows;
   if (p.prec == DE_PREC_BF16X3) {
-    launch_pdl(k_trial_split<2>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
+    if (p.var) launch_pdl(k_trial_split<2, true>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
+    else launch_pdl(k_trial_split<2, false>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
     launch_pdl(k_fit_tc<2>, dim3(p.nitems_fit, p.nsplit), kFitThreads, p.smem_fit, s, runs,
                (const int2*)p.d_fit_items, 0, (double*)nullptr, 0);
   } else {
-    launch_pdl(k_trial_split<4>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
+    if (p.var) launch_pdl(k_trial_split<4, true>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
+    else launch_pdl(k_trial_split<4, false>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
     launch_pdl(k_fit_tc<4>, dim3(p.nitems_fit, p.nsplit), kFitThreads, p.smem_fit, s, runs,
                (const int2*)p.d_fit_items, 0, (double*)nullptr, 0);
   }

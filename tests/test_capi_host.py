@@ -82,19 +82,16 @@ def test_invalid_config_rejected_on_host(kw, msg):
 @pytest.mark.parametrize(
     "kw",
     [
-        dict(strategy=capi.DE_BEST1BIN, precision=capi.DE_PREC_BF16X3),
-        dict(strategy=capi.DE_RAND1EXP, precision=capi.DE_PREC_TF32X3),
-        dict(jde=True, precision=capi.DE_PREC_BF16X3),
         dict(jde=True, surrogate_k=4),
         dict(strategy=capi.DE_BEST1BIN, surrogate_k=8),
     ],
 )
-def test_variants_outside_the_fp64_path_are_unsupported_on_host(kw):
+def test_variants_with_a_surrogate_are_unsupported_on_host(kw):
     cfg = capi.make_config(64, 20, **kw)
     with pytest.raises(capi.DEError) as ei:
         capi.de_init(cfg)
     assert ei.value.status == capi.DE_ERR_UNSUPPORTED
-    assert "FP64" in str(ei.value)
+    assert "surrogate" in str(ei.value)
 
 
 def test_null_arguments_rejected():

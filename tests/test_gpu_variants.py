@@ -227,3 +227,109 @@ def test_adaptive_getters_reject_plain_runs_and_bad_values():
         assert ei.value.status == capi.DE_ERR_INVALID_ARG
     finally:
         capi.de_destroy(h)
+
+
+# ------------------------------------------------------------------ split precisions
+REL_SPLIT = {capi.DE_PREC_BF16X3: 1e-5, capi.DE_PREC_TF32X3: 1e-6}
+
+
+@pytest.fixture(params=["persistent", "three-kernel"])
+def split_path(request, monkeypatch):
+    monkeypatch.setenv("DE_GB300_PERSIST", "1" if request.param == "persistent" else "0")
+    return request.param
+
+
+@pytest.mark.parametrize("prec", [capi.DE_PREC_BF16X3, capi.DE_PREC_TF32X3])
+@pytest.mark.parametrize("strategy,jde", [(capi.DE_BEST1BIN, False), (capi.DE_RAND1EXP, False),
+                                          (capi.DE_RAND1BIN, True), (capi.DE_RAND1EXP, True),
+                                          (capi.DE_BEST1BIN, True)])
+@pytest.mark.parametrize("np_,d,obj", [(256, 100, 1), (70, 37, 3), (1024, 100, 1)])
+def test_split_variants_one_generation_match_oracle(prec, strategy, jde, np_, d, obj, split_path):
+    _need_gpu()
+    o, M = problems.shift(d, seed=21), problems.rotation(d, seed=21)
+    X = problems.population(np_, d, seed=21)
+    fX, _ = oracle.evaluate(obj, X, o, M)
+    rng = np.random.default_rng(21)
+    jF = 0.1 + 0.9 * rng.random(np_) if jde else None
+    jCR = rng.random(np_) if jde else None
+    cfg = capi.make_config(np_, d, objective=obj, shift=o, rot=M, seed=21, precision=prec, max_generations=10**6,
+                           target_error=0.0, debug_capture=True, fp64_band=capi.DE_BAND_ALL, strategy=strategy,
+                           jde=jde)
+    h = capi.de_init(cfg)
+    try:
+        plan = capi.de_get_plan(h)["kernel_path"]
+        assert plan == (1 if split_path == "three-kernel" else plan)
+        capi.de_set_population(h, 0, X, fX)
+        capi.de_set_generation(h, 0, 8)
+        if jde:
+            capi.de_set_adaptive(h, 0, jF, jCR)
+        capi.de_step(h, 1)
+        g = capi.de_get_debug(h)
+        xn, fn = capi.de_get_population(h)
+        ad = capi.de_get_adaptive(h) if jde else None
+    finally:
+        capi.de_destroy(h)
+    r = oracle.step(X, fX, 0.5, 0.9, -100, 100, obj, o, M, seed=21, generation=9, strategy=strategy, jde=jde,
+                    jF=jF, jCR=jCR)
+    assert np.array_equal(g["idx"], r["idx"]) and np.array_equal(g["jrand"], r["jrand"])
+    assert np.array_equal(g["mask"], r["mask"]) and np.array_equal(g["trial"], r["trial"])
+    fp64 = g["fp64_checked"].astype(bool)
+    scale = np.abs(r["f_trial"]) + r["sabs_trial"]
+    assert np.all(np.abs(g["f_trial"] - r["f_trial"]) <= np.where(fp64, REL64, REL_SPLIT[prec]) * scale)
+    inband = np.abs(r["f_trial"] - fX) <= REL64 * scale
+    assert np.array_equal(g["accept"][~inband], r["accept"][~inband])
+    acc = g["accept"].astype(bool)
+    assert np.array_equal(xn[acc], r["trial"][acc]) and np.array_equal(xn[~acc], X[~acc])
+    if jde:
+        same = g["accept"] == r["accept"]
+        assert np.array_equal(ad[0][same], r["F_next"][same]) and np.array_equal(ad[1][same], r["CR_next"][same])
+
+
+@pytest.mark.parametrize("strategy,jde", [(capi.DE_BEST1BIN, False), (capi.DE_RAND1EXP, True)])
+def test_split_variant_paths_agree_over_many_generations(strategy, jde, monkeypatch):
+    """With every undecidable comparison in FP64 both split kernel paths take
+    the same decisions: identical populations and jDE parameters after 150
+    generations."""
+    _need_gpu()
+    d = 30
+    o, M = problems.shift(d, seed=4), problems.rotation(d, seed=4)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("DE_GB300_PERSIST", flag)
+        h = capi.de_init(capi.make_config(300, d, objective=1, shift=o, rot=M, seed=3, precision=capi.DE_PREC_BF16X3,
+                                          max_generations=150, target_error=0.0, fp64_band=capi.DE_BAND_ALL,
+                                          strategy=strategy, jde=jde))
+        try:
+            capi.de_run(h)
+            out.append((capi.de_get_population(h), capi.de_get_adaptive(h) if jde else None))
+        finally:
+            capi.de_destroy(h)
+    assert np.array_equal(out[0][0][0], out[1][0][0])
+    if jde:
+        assert np.array_equal(out[0][1][0], out[1][1][0]) and np.array_equal(out[0][1][1], out[1][1][1])
+
+
+def test_split_batch_with_variants_equals_single_runs(monkeypatch):
+    _need_gpu()
+    monkeypatch.setenv("DE_GB300_PERSIST", "0")
+    specs = [(64, 10, 0, 1, False), (100, 30, 1, 2, True), (57, 50, 3, 0, True)]
+    cfgs = []
+    for r, (np_, d, obj, st, jde) in enumerate(specs):
+        o, M = problems.shift(d, seed=60 + r), problems.rotation(d, seed=60 + r)
+        cfgs.append(capi.make_config(np_, d, objective=obj, shift=o, rot=M, seed=1, run_id=r, max_generations=25,
+                                     target_error=0.0, precision=capi.DE_PREC_BF16X3, fp64_band=capi.DE_BAND_ALL,
+                                     strategy=st, jde=jde))
+    hb = capi.de_init_batch(cfgs)
+    try:
+        capi.de_run(hb, len(cfgs))
+        batch = [capi.de_get_population(hb, r) for r in range(len(cfgs))]
+    finally:
+        capi.de_destroy(hb)
+    for r, c in enumerate(cfgs):
+        h = capi.de_init(c)
+        try:
+            capi.de_run(h)
+            x, f = capi.de_get_population(h)
+        finally:
+            capi.de_destroy(h)
+        assert np.array_equal(x, batch[r][0])
