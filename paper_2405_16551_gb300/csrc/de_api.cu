@@ -538,7 +538,7 @@ static std::string tune_key_split(const de_handle* h) {
     sum_d += (long long)R.np * R.d;
   }
   char b[256];
-  snprintf(b, sizeof b, "split_v1 prec=%d runs=%d np0=%d d0=%d obj0=%d sumnp=%lld sumnd=%lld", h->prec, h->nruns,
+  snprintf(b, sizeof b, "split_v2 prec=%d runs=%d np0=%d d0=%d obj0=%d sumnp=%lld sumnd=%lld", h->prec, h->nruns,
            h->run[0].np, h->run[0].d, h->run[0].obj, sum_np, sum_d);
   return b;
 }
@@ -547,9 +547,10 @@ static de_status autotune_split(de_handle* h) {
   const char* env = getenv("DE_GB300_AUTOTUNE");
   if ((env && env[0] == '0') || h->tc.persist.ok) return DE_OK;
   const std::string key = tune_key_split(h);
+  // cached value: 100 x targets per trial CTA + 10 x K-chunk divisor + pipeline stages
   int code = 0;
   if (tune_lookup(key, code)) {
-    de_status s = tc_set_geometry(h->tc, h->run, code / 10, code % 10, h->stream, h->err);
+    de_status s = tc_set_geometry(h->tc, h->run, code / 100, (code / 10) % 10, code % 10, h->stream, h->err);
     if (s == DE_OK) s = upload_desc(h);
     return s;
   }
@@ -566,8 +567,9 @@ static de_status autotune_split(de_handle* h) {
   int best = 0;
   de_status st_all = DE_OK;
   for (int tr : {2, 4, 8}) {
-    for (int kd : {1, 2, 4}) {
-      st_all = tc_set_geometry(h->tc, h->run, tr, kd, h->stream, h->err);
+    for (int kd : {1, 2, 4})
+      for (int ns : {2, 4}) {
+      st_all = tc_set_geometry(h->tc, h->run, tr, kd, ns, h->stream, h->err);
       if (st_all == DE_OK) st_all = upload_desc(h);
       if (st_all != DE_OK) break;
       for (int r = 0; r < h->nruns; ++r) {
@@ -583,17 +585,20 @@ static de_status autotune_split(de_handle* h) {
       DE_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best_ms * 0.97f) {
         best_ms = ms;
-        best = tr * 10 + kd;
+        best = tr * 100 + kd * 10 + ns;
       }
-    }
+      }
     if (st_all != DE_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (size_t r = 0; r < saved.size(); ++r) saved[r].kc = h->run[r].kc;
+  for (size_t r = 0; r < saved.size(); ++r) {
+    saved[r].kc = h->run[r].kc;
+    saved[r].nstage = h->run[r].nstage;
+  }
   h->run = saved;
   if (st_all != DE_OK) return st_all;
-  de_status s = tc_set_geometry(h->tc, h->run, best / 10, best % 10, h->stream, h->err);
+  de_status s = tc_set_geometry(h->tc, h->run, best / 100, (best / 10) % 10, best % 10, h->stream, h->err);
   if (s == DE_OK) s = upload_desc(h);
   if (s == DE_OK) tune_store(key, best);
   return s;

@@ -90,9 +90,10 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
                         std::string& err);
 void tc_plan_free(TcPlan& p);
 // Launch geometry that leaves the results unchanged (autotuner): targets per
-// trial CTA and a divisor of the fitness kernel's default K chunk.
-de_status tc_set_geometry(TcPlan& p, std::vector<RunDesc>& runs, int trial_rows, int kc_div, cudaStream_t s,
-                          std::string& err);
+// trial CTA, a divisor of the fitness kernel's default K chunk, and the
+// stages of its K pipeline.
+de_status tc_set_geometry(TcPlan& p, std::vector<RunDesc>& runs, int trial_rows, int kc_div, int stages,
+                          cudaStream_t s, std::string& err);
 void tc_generation_launch(const TcPlan& p, const RunDesc* runs, cudaStream_t s);
 // Split-precision evaluation of run `run`'s population X[0] into f[0] (fx = 0,
 // tau set): the initial evaluation of split-precision runs.

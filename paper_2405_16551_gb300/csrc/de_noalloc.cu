@@ -194,6 +194,7 @@ de_status noalloc_eval(int prec, int obj, int d, double scale, const double* o, 
   R.npad = npad;
   R.ntiles_tc = (int)tiles;
   R.kc = kc;
+  R.nstage = kc < kpad || nn > 1 ? 2 : 1;
   R.ntn = ntn;
   R.nn = nn;
   R.esz = esz;

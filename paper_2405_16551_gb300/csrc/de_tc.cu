@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kFitThreads, 1)
     k_fit_tc(const RunDesc* __restrict__ runs, const int2* __restrict__ items, int mode, double* __restrict__ fout,
              int n_eval) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[5];  // full[2], done[2], acc
+  __shared__ __align__(8) uint64_t bars[2 * kMaxStages + 1];  // full[S], done[S], acc
   __shared__ uint32_t s_tmem;
   __shared__ int s_stop, s_err, s_nlist, s_nacc, s_last;
   __shared__ long long s_gen;
@@ -192,10 +192,14 @@ __global__ void __launch_bounds__(kFitThreads, 1)
 
   // ---- set-up that does not depend on the previous kernel: barriers, tensor
   // memory, and the constant B operand of the first pipeline stages
-  const uint32_t b_full0 = smem_u32(&bars[0]), b_full1 = smem_u32(&bars[1]);
-  const uint32_t b_done0 = smem_u32(&bars[2]), b_done1 = smem_u32(&bars[3]), b_acc = smem_u32(&bars[4]);
+  // S-stage K pipeline: stage s is filled when full[s] completes and free
+  // again when done[s] (the commit of its products) completes
+  const int S = R.nstage;
+  auto full_bar = [&](int sg) { return smem_u32(&bars[sg]); };
+  auto done_bar = [&](int sg) { return smem_u32(&bars[kMaxStages + sg]); };
+  const uint32_t b_acc = smem_u32(&bars[2 * kMaxStages]);
   if (tid == 0) {
-    for (int k = 0; k < 5; ++k) mbar_init(smem_u32(&bars[k]), 1);
+    for (int k = 0; k < 2 * kMaxStages + 1; ++k) mbar_init(smem_u32(&bars[k]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_err = 0;
     s_nlist = 0;
@@ -232,11 +236,11 @@ __global__ void __launch_bounds__(kFitThreads, 1)
   auto chunk_len = [&](int kci) { return min(kc, R.kpad - kci * kc); };
   // B half of stage load q (counts the bytes of both halves on the barrier)
   auto issue_load_b = [&](int q) {
-    const int nt = nt_lo + q / nkc, kci = q % nkc, sg = q & 1;
+    const int nt = nt_lo + q / nkc, kci = q % nkc, sg = q % S;
     const uint32_t kgs = (uint32_t)(chunk_len(kci) * ESZ / 16);
     const uint32_t ab = kgs * 16u * 128u, bb = kgs * bk;
     const uint32_t base = sbase + (uint32_t)sg * stage_bytes;
-    const uint32_t bar = sg ? b_full1 : b_full0;
+    const uint32_t bar = full_bar(sg);
     mbar_expect_tx(bar, 2 * ab + 2 * bb);
     const size_t b_off = (size_t)kci * b_chunk;
     const uint8_t* Bt = R.B + (size_t)nt * R.b_tile_bytes;
@@ -244,16 +248,16 @@ __global__ void __launch_bounds__(kFitThreads, 1)
     bulk_g2s(base + 2 * a_chunk + b_chunk, Bt + b_part + b_off, bb, bar);
   };
   auto issue_load_a = [&](int q) {
-    const int kci = q % nkc, sg = q & 1;
+    const int kci = q % nkc, sg = q % S;
     const uint32_t kgs = (uint32_t)(chunk_len(kci) * ESZ / 16);
     const uint32_t ab = kgs * 16u * 128u;
     const uint32_t base = sbase + (uint32_t)sg * stage_bytes;
-    const uint32_t bar = sg ? b_full1 : b_full0;
+    const uint32_t bar = full_bar(sg);
     const size_t a_off = (size_t)kci * a_chunk;
     bulk_g2s(base, Atile + a_off, ab, bar);
     bulk_g2s(base + a_chunk, Atile + a_part + a_off, ab, bar);
   };
-  const int npro = min(nseq, 2);
+  const int npro = min(nseq, S);
   if (tid == 0)
     for (int q = 0; q < npro; ++q) issue_load_b(q);
 
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(kFitThreads, 1)
   if (s_stop) {
     // the run has stopped: let the prologue copies land, free TMEM, leave
     if (tid == 0)
-      for (int q = 0; q < npro; ++q) mbar_wait(q ? b_full1 : b_full0, 0u);
+      for (int q = 0; q < npro; ++q) mbar_wait(full_bar(q), 0u);
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
     return;
@@ -305,8 +309,8 @@ __global__ void __launch_bounds__(kFitThreads, 1)
     if (tid == 0 && !s_err) {
       bool ok = true;
       for (int kci = 0; kci < nkc; ++kci, ++q) {
-        const int sg = q & 1;
-        ok = mbar_wait(sg ? b_full1 : b_full0, (uint32_t)((q >> 1) & 1));
+        const int sg = q % S;
+        ok = mbar_wait(full_bar(sg), (uint32_t)((q / S) & 1));
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t base = sbase + (uint32_t)sg * stage_bytes;
@@ -320,14 +324,15 @@ __global__ void __launch_bounds__(kFitThreads, 1)
             mma_split<ESZ>(tmem, smem_desc(a, 2048u, 128u), smem_desc(b, bk, 128u), idesc, accum);
           }
         }
-        mma_commit(sg ? b_done1 : b_done0);
+        mma_commit(done_bar(sg));
         ++mmas_committed;
-        if (q >= 1 && q + 1 < nseq) {
+        // refill the stage of chunk q - 1 (its products done) with chunk q - 1 + S
+        if (q >= 1 && q - 1 + S < nseq) {
           const int pq = q - 1;
-          ok = mbar_wait((pq & 1) ? b_done1 : b_done0, (uint32_t)((pq >> 1) & 1));
+          ok = mbar_wait(done_bar(pq % S), (uint32_t)((pq / S) & 1));
           if (!ok) break;
-          issue_load_b(q + 1);
-          issue_load_a(q + 1);
+          issue_load_b(pq + S);
+          issue_load_a(pq + S);
           ++loads_issued;
         }
       }
@@ -378,8 +383,8 @@ __global__ void __launch_bounds__(kFitThreads, 1)
   if (s_err) {
     if (tid == 0) {
       atomicOr(&st->err, kErrTimeout);
-      for (int k = 0; k < loads_issued; ++k) mbar_wait((k & 1) ? b_full1 : b_full0, (uint32_t)((k >> 1) & 1));
-      for (int k = 0; k < mmas_committed; ++k) mbar_wait((k & 1) ? b_done1 : b_done0, (uint32_t)((k >> 1) & 1));
+      for (int k = 0; k < loads_issued; ++k) mbar_wait(full_bar(k % S), (uint32_t)((k / S) & 1));
+      for (int k = 0; k < mmas_committed; ++k) mbar_wait(done_bar(k % S), (uint32_t)((k / S) & 1));
     }
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
@@ -761,9 +766,19 @@ static int plan_kc(const RunDesc& R, int esz, int kc_div) {
   return kc;
 }
 
+// Stages of the K pipeline: one when the whole K of one N tile is one chunk,
+// else `stages` (at least 2) as far as kFitSmemMax allows.
+static int plan_stages(const RunDesc& R, int esz, int stages) {
+  if (R.kc >= R.kpad && R.nn == 1) return 1;
+  const size_t stage = 2 * (size_t)(R.kc * esz / 16) * 16 * 128 + 2 * (size_t)(R.kc * esz / 16) * (R.ntn / 8) * 128;
+  int S = std::max(2, std::min(stages, kMaxStages));
+  while (S > 2 && (size_t)S * stage > kFitSmemMax) --S;
+  return S;
+}
+
 static size_t plan_smem(const RunDesc& R, int esz) {
   const size_t stage = 2 * (size_t)(R.kc * esz / 16) * 16 * 128 + 2 * (size_t)(R.kc * esz / 16) * (R.ntn / 8) * 128;
-  return (R.kc < R.kpad || R.nn > 1 ? 2 : 1) * stage;
+  return (size_t)R.nstage * stage;
 }
 
 // B operand: N tiles of M's rows (n = output coordinate), each tile two
@@ -819,6 +834,7 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
       return DE_ERR_UNSUPPORTED;
     }
     R.kc = plan_kc(R, esz, 1);
+    R.nstage = plan_stages(R, esz, 2);
     R.ntiles_tc = (R.np + kTileM - 1) / kTileM;
     R.a_tile_bytes = 2 * kTileM * R.kpad * esz;
     R.b_tile_bytes = 2 * R.ntn * R.kpad * esz;
@@ -963,12 +979,13 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
   return DE_OK;
 }
 
-de_status tc_set_geometry(TcPlan& p, std::vector<RunDesc>& runs, int trial_rows, int kc_div, cudaStream_t s,
-                          std::string& err) {
+de_status tc_set_geometry(TcPlan& p, std::vector<RunDesc>& runs, int trial_rows, int kc_div, int stages,
+                          cudaStream_t s, std::string& err) {
   const int esz = p.prec == DE_PREC_BF16X3 ? 2 : 4;
   size_t smem = 0;
   for (auto& R : runs) {
     R.kc = plan_kc(R, esz, kc_div);
+    R.nstage = plan_stages(R, esz, stages);
     smem = std::max(smem, plan_smem(R, esz));
   }
   std::vector<int2> items;

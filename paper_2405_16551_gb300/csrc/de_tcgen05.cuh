@@ -22,6 +22,8 @@ constexpr int kTileM = 128;
 constexpr int kFitThreads = 256;
 constexpr int kStageBudget = 96 * 1024;
 constexpr size_t kSingleStageMax = 216 * 1024;  // dynamic shared memory of one whole-K stage
+constexpr int kMaxStages = 8;                   // stages of the fitness kernel's K pipeline
+constexpr size_t kFitSmemMax = 200 * 1024;      // dynamic shared memory of all stages
 constexpr size_t kBandSmem = 160 * 1024;        // M rows staged by one FP64 band work item
 constexpr long long kWaitLimit = 1LL << 22;
 
