@@ -474,6 +474,14 @@ DE_API de_status de_set_generation(de_handle* h, int32_t run, int64_t generation
 DE_API de_status de_get_adaptive(de_handle* h, int32_t run, double* f_host, double* cr_host);
 DE_API de_status de_set_adaptive(de_handle* h, int32_t run, const double* f_host, const double* cr_host);
 
+/* Self-test (no counterpart in the paper): converts n host doubles to FP32
+ * with the library's integer round-to-nearest-even (the conversion used for
+ * the split-precision operands) and with the GPU's conversion instruction,
+ * and returns how many results differ (NaN equals NaN), or -1 on a CUDA
+ * error or a NULL / negative argument.  Allocates and synchronises the
+ * current device. */
+DE_API int64_t de_selftest_f32_rounding(const double* x_host, int64_t n);
+
 /* Best record of run `run`: best_f, its index, a copy of its vector
  * (host, d doubles, may be NULL), and generation/evaluation counters. */
 DE_API de_status de_get_best(de_handle* h, int32_t run, double* best_f, int32_t* best_index, double* best_x,

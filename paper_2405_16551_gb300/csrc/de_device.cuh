@@ -339,6 +339,24 @@ __host__ __device__ __forceinline__ long long ordered_key(double x) {
   return k >= 0 ? k : -(k & 0x7FFFFFFFFFFFFFFFLL);
 }
 
+// FP64 -> FP32 rounding to nearest, ties to even, on the integer pipe (the
+// conversion instruction occupies the FP64 pipe, which bounds the trial
+// kernels on this part): the 29 dropped significand bits decide the
+// increment, whose carry runs into the exponent field (and to infinity past
+// the largest float).  Zero, subnormal, infinite and NaN inputs and results
+// below the normal float range take the hardware conversion.
+__device__ __forceinline__ float to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  if (e < 1 || e > 254) return (float)x;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+  const unsigned int mant = (unsigned int)(m >> 29);
+  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFULL);
+  unsigned int r = ((unsigned int)(b >> 63) << 31) | ((unsigned int)e << 23) | mant;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) r += 1u;
+  return __uint_as_float(r);
+}
+
 // y = (t - o) s, rounded once per operation as written
 __device__ __forceinline__ double shifted(double t, double o, const RunDesc& R) {
   const double y = __dsub_rn(t, o);

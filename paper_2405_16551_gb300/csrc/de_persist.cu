@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256, 1)
             float y[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              y[e] = (j0 + e < d) ? (float)shifted(t[e], osh[c][e], R) : 0.f;
+              y[e] = (j0 + e < d) ? to_f32_rn(shifted(t[e], osh[c][e], R)) : 0.f;
               yn2 += y[e] * y[e];
             }
             store_split4<ESZ>(lA, a_part, lr, j0, y);

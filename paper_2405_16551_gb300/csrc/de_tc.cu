@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
       float y[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        y[q] = (j0 + q < R.d) ? (float)shifted(t[q], R.o[j0 + q], R) : 0.f;
+        y[q] = (j0 + q < R.d) ? to_f32_rn(shifted(t[q], R.o[j0 + q], R)) : 0.f;
         yn2 += y[q] * y[q];
       }
       store_split4<ESZ>(Ahi, a_part, m, j0, y);
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) k_prep_rows(const RunDesc* __restrict__ r
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = j0 + q;
-      y[q] = (j < R.d) ? (float)shifted(x[(size_t)i * ld + j], R.o[j], R) : 0.f;
+      y[q] = (j < R.d) ? to_f32_rn(shifted(x[(size_t)i * ld + j], R.o[j], R)) : 0.f;
       yn2 += y[q] * y[q];
     }
     store_split4<ESZ>(Ahi, a_part, i & 127, j0, y);

@@ -233,3 +233,23 @@ def test_split_batch_of_mixed_widths_equals_single_runs(prec, monkeypatch):
             capi.de_destroy(hs)
         assert np.array_equal(pops[r][0], xs), r
         assert np.array_equal(pops[r][1], fs), r
+
+
+def test_integer_fp32_rounding_equals_the_hardware_conversion():
+    """The split operands are rounded to FP32 by integer operations; they must
+    equal the GPU's round-to-nearest conversion bit for bit, ties included."""
+    _need_gpu()
+    rng = np.random.default_rng(5)
+    bits = rng.integers(0, 2 ** 63, size=500_000, dtype=np.int64).astype(np.uint64)
+    bits |= rng.integers(0, 2, size=bits.size).astype(np.uint64) << np.uint64(63)
+    x = bits.view(np.float64)
+    # values in the float range, exact halfway cases (both parities), the range edges
+    f = rng.standard_normal(200_000).astype(np.float32) * np.float32(1e3)
+    fb = f.view(np.uint32).astype(np.uint64)
+    up = (fb + 1).astype(np.uint32).view(np.float32).astype(np.float64)
+    ties = (f.astype(np.float64) + up) / 2
+    edges = np.array([3.4028234663852886e38, 3.4028235677973366e38, 3.402823567797337e38, 1.1754943508222875e-38,
+                      1.1754942106924411e-38, -1.1754943508222875e-38, 0.0, -0.0, np.inf, -np.inf, np.nan, 1e-320,
+                      5e-324, 1e300, -1e300, 0.1, 1 / 3], dtype=np.float64)
+    for arr in (x, ties, rng.uniform(-200, 200, 300_000), edges):
+        assert capi.de_selftest_f32_rounding(arr) == 0
