@@ -502,34 +502,46 @@ __device__ __forceinline__ void jde_params(const RunDesc& R, uint32_t i, int64_t
 // crossover draws rand_0, rand_1, ... (draw 4 + m of the STEP stream, the
 // ones binomial crossover gives coordinate m) that are <= thr, capped at d.
 // Called by the whole warp; lane q tests draws 128c + 4q .. 128c + 4q + 3.
-__device__ __forceinline__ int exp_length(const RunDesc& R, uint32_t i, int64_t g, int lane, uint64_t thr) {
+// The warp may hold several targets: lpt lanes per target (a power of two,
+// aligned segments), the lane's position in its segment is lane % lpt, and
+// the segment's draws are tested 4 lpt at a time.  Every lane runs the same
+// number of rounds (d is the run's), so the ballots stay warp-wide.
+__device__ __forceinline__ int exp_length(const RunDesc& R, uint32_t i, int64_t g, int lane, uint64_t thr,
+                                          int lpt = 32) {
   const int d = R.d;
-  for (int m0 = 0; m0 <= d - 2; m0 += 128) {
-    const int mb = m0 + 4 * lane;
+  const int sub = lane & (lpt - 1), base = lane - sub;
+  const uint32_t seg = lpt == 32 ? 0xffffffffu : (((1u << lpt) - 1u) << base);
+  int L = d;
+  bool found = false;
+  for (int m0 = 0; m0 <= d - 2; m0 += 4 * lpt) {
+    const int mb = m0 + 4 * sub;
     uint32_t fail = 0;
-    if (mb <= d - 2) {
+    if (mb <= d - 2 && !found) {
       const U32x4 b = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, i, 1u + (uint32_t)(mb >> 2));
       const uint32_t u[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (mb + q <= d - 2 && (uint64_t)u[q] > thr) fail |= 1u << q;
     }
-    const uint32_t any = __ballot_sync(0xffffffffu, fail != 0u);
-    if (any) {
-      const int fl = __ffs(any) - 1;
-      const uint32_t fb = __shfl_sync(0xffffffffu, fail, fl);
-      return m0 + 4 * fl + (__ffs(fb) - 1) + 1;
+    const uint32_t any = __ballot_sync(0xffffffffu, fail != 0u) & seg;
+    const int fl = any ? __ffs(any) - 1 : lane;
+    const uint32_t fb = __shfl_sync(0xffffffffu, fail, fl);
+    if (any && !found) {
+      L = m0 + 4 * (fl - base) + (__ffs(fb) - 1) + 1;
+      found = true;
     }
+    if (lpt == 32 && found) break;  // the whole warp is one target: a uniform exit
   }
-  return d;
+  return L;
 }
 
 // Trial setup under the run's strategy and jDE: records the drawn donors,
 // then for DE/best/1 takes the base from row `best` and the difference from
 // the first two drawn donors.  Called by the whole warp.
 __device__ __forceinline__ TrialSetup trial_setup_var(const RunDesc& R, uint32_t i, int64_t g, int lane, int best,
-                                                      const double* jF, const double* jCR, TrialVar& v) {
-  TrialSetup s = trial_setup(R, i, g, lane);
+                                                      const double* jF, const double* jCR, TrialVar& v,
+                                                      int lpt = 32, bool record = true) {
+  TrialSetup s = trial_setup(R, i, g, lane & (lpt - 1), 0u, record);
   if (R.strategy == 1) {
     s.r3 = s.r2;
     s.r2 = s.r1;
@@ -542,27 +554,28 @@ __device__ __forceinline__ TrialSetup trial_setup_var(const RunDesc& R, uint32_t
     jde_params(R, i, g, jF, jCR, v.F, v.CR);
     v.thr = (uint64_t)floor(__dmul_rn(v.CR, 4294967296.0));
   }
-  v.L = R.strategy == 2 ? exp_length(R, i, g, lane, v.thr) : 0;
+  v.L = R.strategy == 2 ? exp_length(R, i, g, lane, v.thr, lpt) : 0;
   return s;
 }
 
 // Debug capture of one chunk: trial values and the crossover mask word.
-// Called by every lane of the warp (the mask word is assembled by shuffles).
+// Called by every lane of the warp (the mask word is assembled by shuffles
+// within each target's lpt lanes); `valid` lanes write.
 __device__ __forceinline__ void trial_debug(const RunDesc& R, uint32_t i, int j0, int lane, uint32_t bits,
-                                            const double t[4]) {
+                                            const double t[4], int lpt = 32, bool valid = true) {
   const int d = R.d;
-  if (j0 < d) {
+  if (valid && j0 < d) {
 #pragma unroll
     for (int m = 0; m < 4; ++m)
       if (j0 + m < d) R.dbg_trial[(size_t)i * d + j0 + m] = t[m];
   }
-  // lanes 8w .. 8w+7 of a chunk cover mask word 4c + w
+  // lanes 8w .. 8w+7 of a target's chunk cover mask word 4c + w
   uint32_t word = (j0 < d) ? (bits << (j0 & 31)) : 0u;
-  word |= __shfl_xor_sync(0xffffffffu, word, 1);
-  word |= __shfl_xor_sync(0xffffffffu, word, 2);
-  word |= __shfl_xor_sync(0xffffffffu, word, 4);
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1)
+    if (o < lpt) word |= __shfl_xor_sync(0xffffffffu, word, o);
   const int wi = j0 >> 5;
-  if ((lane & 7) == 0 && wi < R.nw) R.dbg_mask[(size_t)i * R.nw + wi] = word;
+  if (valid && (lane & 7 & (lpt - 1)) == 0 && wi < R.nw) R.dbg_mask[(size_t)i * R.nw + wi] = word;
 }
 
 // FP64 path: build the trial row into T and Y = (T - o) s (rows of length dp).

@@ -103,7 +103,7 @@ struct RunDesc {
   int32_t ntiles_tc;  // 128-row tiles
   int32_t kc;         // K elements staged per pipeline step
   int32_t nstage;     // stages of the fitness kernel's K pipeline (1: whole K resident)
-  int32_t pad3;
+  int32_t lpt;        // lanes per target in the split trial kernel (power of two, <= 32)
   int32_t ntn;        // N tile width (columns of one accumulator), <= 256
   int32_t nn;         // number of N tiles
   int32_t esz;        // operand element bytes: 2 (bf16) or 4 (tf32)

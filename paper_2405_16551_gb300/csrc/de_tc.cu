@@ -59,8 +59,10 @@
 namespace de {
 
 // ------------------------------------------------------------------ trial kernel
-// items: (run, group of blockDim / 32 targets); warp w of the CTA takes
-// target group * (blockDim / 32) + w.
+// items: (run, group); a warp holds 32 / R.lpt targets, R.lpt lanes each
+// (lane L: coordinates 4 (L % lpt) .. + 3 of each 4 lpt-wide chunk), so that
+// short rows do not leave most lanes of the FP64 instructions idle; warp w of
+// the CTA takes targets (group * warps + w) * (32 / lpt) + L / lpt.
 // VAR: some run uses a strategy variant or jDE (a separate instance).
 template <int ESZ, bool VAR>
 __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__ runs, const int2* __restrict__ items) {
@@ -81,34 +83,41 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
   if (s_stop) return;
   const int64_t g = s_gen + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = it.y * (int)(blockDim.x >> 5) + warp;
-  if (i >= R.np) return;
+  const int lpt = R.lpt, sub = lane & (lpt - 1);
+  const int i0 = (it.y * (int)(blockDim.x >> 5) + warp) * (32 / lpt);
+  if (i0 >= R.np) return;  // the whole warp
+  const int iraw = i0 + lane / lpt;
+  const bool valid = iraw < R.np;
+  const int i = valid ? iraw : R.np - 1;  // idle segments repeat a valid target without writing
   const double* X = R.X[0];
   TrialVar v;
   TrialSetup s;
   if constexpr (VAR) s = trial_setup_var(R, (uint32_t)i, g, lane, s_best, R.jde ? R.jF[0] : nullptr,
-                                         R.jde ? R.jCR[0] : nullptr, v);
-  else s = trial_setup(R, (uint32_t)i, g, lane);
+                                         R.jde ? R.jCR[0] : nullptr, v, lpt, valid);
+  else s = trial_setup(R, (uint32_t)i, g, sub, 0u, valid);
   uint8_t* Ahi = R.A + (size_t)(i >> 7) * R.a_tile_bytes;
   const uint32_t a_part = (uint32_t)(R.a_tile_bytes / 2);
   const int m = i & 127;
   float yn2 = 0.f;
   const bool dbg = R.dbg_trial != nullptr;
-  const int nchunks = (R.kpad + 127) / 128;
+  const int cw = 4 * lpt;  // coordinates per chunk
+  const int nchunks = (R.kpad + cw - 1) / cw;
   // the loads of chunk c + 1 are issued before chunk c is computed
   ChunkIn cur, nxt;
-  if (4 * lane < R.d) trial_load(R, X, s, (uint32_t)i, g, 4 * lane, cur);
+  if (4 * sub < R.d) trial_load(R, X, s, (uint32_t)i, g, 4 * sub, cur);
   for (int c = 0; c < nchunks; ++c) {
-    const int j0 = 128 * c + 4 * lane;
-    if (c + 1 < nchunks && j0 + 128 < R.d) trial_load(R, X, s, (uint32_t)i, g, j0 + 128, nxt);
+    const int j0 = cw * c + 4 * sub;
+    if (c + 1 < nchunks && j0 + cw < R.d) trial_load(R, X, s, (uint32_t)i, g, j0 + cw, nxt);
     double t[4] = {0.0, 0.0, 0.0, 0.0};
     uint32_t bits = 0;
     if (j0 < R.d) {
       if constexpr (VAR) bits = trial_compute(R, s, j0, cur, t, v.F, v.thr, v.L);
       else bits = trial_compute(R, s, j0, cur, t);
-      double* Trow = R.T + (size_t)i * R.dp + j0;
-      *reinterpret_cast<double2*>(Trow) = make_double2(t[0], t[1]);
-      *reinterpret_cast<double2*>(Trow + 2) = make_double2(t[2], t[3]);
+      if (valid) {
+        double* Trow = R.T + (size_t)i * R.dp + j0;
+        *reinterpret_cast<double2*>(Trow) = make_double2(t[0], t[1]);
+        *reinterpret_cast<double2*>(Trow + 2) = make_double2(t[2], t[3]);
+      }
     }
     if (j0 < R.kpad) {
       float y[4];
@@ -117,14 +126,13 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
         y[q] = (j0 + q < R.d) ? to_f32_rn(shifted(t[q], R.o[j0 + q], R)) : 0.f;
         yn2 += y[q] * y[q];
       }
-      store_split4<ESZ>(Ahi, a_part, m, j0, y);
+      if (valid) store_split4<ESZ>(Ahi, a_part, m, j0, y);
     }
-    if (dbg) trial_debug(R, (uint32_t)i, j0, lane, bits, t);
+    if (dbg) trial_debug(R, (uint32_t)i, j0, lane, bits, t, lpt, valid);
     cur = nxt;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) yn2 += __shfl_xor_sync(0xffffffffu, yn2, o);
-  if (lane == 0) R.ynorm[i] = sqrtf(yn2);
+  for (int o = lpt >> 1; o > 0; o >>= 1) yn2 += __shfl_xor_sync(0xffffffffu, yn2, o);
+  if (valid && sub == 0) R.ynorm[i] = sqrtf(yn2);
 }
 
 // Rows of caller memory -> A operand tiles and |y| (evaluation mode).
@@ -766,6 +774,13 @@ static int plan_kc(const RunDesc& R, int esz, int kc_div) {
   return kc;
 }
 
+// Work items of the trial kernel for one run: CTAs of `warps` warps, each
+// warp 32 / lpt targets.
+static int trial_groups(const RunDesc& R, int warps) {
+  const int per = warps * (32 / R.lpt);
+  return (R.np + per - 1) / per;
+}
+
 // Stages of the K pipeline: one when the whole K of one N tile is one chunk,
 // else `stages` (at least 2) as far as kFitSmemMax allows.
 static int plan_stages(const RunDesc& R, int esz, int stages) {
@@ -826,6 +841,10 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
     RunDesc& R = runs[r];
     R.esz = esz;
     R.kpad = (int)round_up(R.d, 16);
+    // lanes per target of the trial kernel: the fewest lanes (a power of two)
+    // whose 4 coordinates each cover the padded row, at most a warp
+    R.lpt = 1;
+    while (R.lpt < 32 && 4 * R.lpt < R.kpad) R.lpt *= 2;
     R.ntn = R.d <= 256 ? (int)round_up(R.d, 16) : 256;
     R.nn = (R.d + R.ntn - 1) / R.ntn;
     R.npad = R.nn * R.ntn;
@@ -889,7 +908,7 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
     for (auto& R : runs) tot += R.np;
     p.trial_rows = (int)std::max(1LL, std::min(8LL, (tot + nsm - 1) / nsm));
     for (size_t r = 0; r < runs.size(); ++r)
-      for (int gI = 0; gI < (runs[r].np + p.trial_rows - 1) / p.trial_rows; ++gI)
+      for (int gI = 0; gI < trial_groups(runs[r], p.trial_rows); ++gI)
         trial_items.push_back(make_int2((int)r, gI));
   }
   // FP64 band list shared by all runs of the handle
@@ -990,7 +1009,7 @@ de_status tc_set_geometry(TcPlan& p, std::vector<RunDesc>& runs, int trial_rows,
   }
   std::vector<int2> items;
   for (size_t r = 0; r < runs.size(); ++r)
-    for (int gI = 0; gI < (runs[r].np + trial_rows - 1) / trial_rows; ++gI) items.push_back(make_int2((int)r, gI));
+    for (int gI = 0; gI < trial_groups(runs[r], trial_rows); ++gI) items.push_back(make_int2((int)r, gI));
   cudaError_t e = cudaSuccess;
   if (items.size() != (size_t)p.nitems_trial) {
     if (p.d_trial_items) cudaFree(p.d_trial_items);
