@@ -219,7 +219,11 @@ static de_status validate(const de_config& c, int idx, std::string& why) {
 
 // Shared memory of one FP64 generation CTA for `rows` rows of stride dp
 // (trial, shifted, rotated and second-term buffers).
-static size_t gen_smem(int rows, int dp) { return (size_t)4 * rows * dp * sizeof(double); }
+// A composition function's tile keeps every component's shifted and rotated
+// rows: trials plus 2 ncomp buffers.
+static size_t gen_smem(int rows, int dp, int ncomp = 1) {
+  return (size_t)std::max(4, 1 + 2 * ncomp) * rows * dp * sizeof(double);
+}
 
 // Split every run into tiles of at most h->rows targets, of near-equal size.
 static de_status build_items(de_handle* h) {
@@ -228,11 +232,11 @@ static de_status build_items(de_handle* h) {
   for (int r = 0; r < h->nruns; ++r) {
     RunDesc& R = h->run[r];
     int rows = std::max(1, std::min(h->rows, 8));
-    while (rows > 1 && gen_smem(rows, R.dp) > 200 * 1024) --rows;
+    while (rows > 1 && gen_smem(rows, R.dp, suite_comps(R)) > 200 * 1024) --rows;
     const int nt = (R.np + rows - 1) / rows;
     R.rows = (R.np + nt - 1) / nt;  // the largest tile after even splitting
     R.ntiles = nt;
-    smem = std::max(smem, gen_smem(R.rows, R.dp));
+    smem = std::max(smem, gen_smem(R.rows, R.dp, suite_comps(R)));
     for (int t = 0; t < nt; ++t) {
       const int a = (int)((long long)t * R.np / nt), b = (int)((long long)(t + 1) * R.np / nt);
       items.push_back(make_int4(r, t, a, b - a));
@@ -370,7 +374,7 @@ static de_status init_run(de_handle* h, int r) {
   k_init_population_launch(h->d_run, r, R.np, R.dp, h->stream);
   if (R.jde) k_jde_init_launch(h->d_run, r, R.np, h->stream);
   if (h->prec == DE_PREC_FP64) {
-    k_eval_rows_launch(h->d_run, r, R.X[0], R.dp, R.np, R.dp, R.rotate, R.f[0], R.fx[0], h->stream);
+    k_eval_rows_launch(h->d_run, r, R.X[0], R.dp, R.np, R.dp, suite_comps(R), R.f[0], R.fx[0], h->stream);
   } else {
     // split precisions evaluate the initial population in their own precision
     // (values with error bounds, like accepted trials); the best record is
@@ -396,7 +400,7 @@ static de_status exact_best(de_handle* h, int r) {
   DE_CUDA(h, cudaStreamSynchronize(h->stream));
   if (fx) return DE_OK;
   double* fb = R.f[cur] + st.best_idx;
-  k_eval_rows_launch(h->d_run, r, R.X[cur] + (size_t)st.best_idx * R.dp, R.dp, 1, R.dp, R.rotate, fb,
+  k_eval_rows_launch(h->d_run, r, R.X[cur] + (size_t)st.best_idx * R.dp, R.dp, 1, R.dp, suite_comps(R), fb,
                      R.fx[cur] + st.best_idx, h->stream);
   DE_CUDA(h, cudaGetLastError());
   DE_CUDA(h, cudaMemcpyAsync(&st.best_f, fb, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1055,7 +1059,7 @@ de_status de_eval(de_handle* h, int32_t run, const double* x_dev, int64_t ld, in
     return fail(h, DE_ERR_INVALID_ARG, "f_dev is not device memory");
   }
   if (h->prec == DE_PREC_FP64) {
-    k_eval_rows_launch(h->d_run, run, x_dev, ld, n, R.dp, R.rotate, f_dev, nullptr, h->stream);
+    k_eval_rows_launch(h->d_run, run, x_dev, ld, n, R.dp, suite_comps(R), f_dev, nullptr, h->stream);
   } else {
     de_status s = tc_eval_launch(h->tc, h->d_run, run, R, x_dev, ld, n, f_dev, h->stream, h->err);
     if (s != DE_OK) return s;
@@ -1106,7 +1110,7 @@ de_status de_set_population(de_handle* h, int32_t run, const double* x_host, con
     DE_CUDA(h, cudaMemcpyAsync(R.f[cur], f_host, R.np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     DE_CUDA(h, cudaMemsetAsync(R.fx[cur], 1, R.np, h->stream));
   } else {
-    k_eval_rows_launch(h->d_run, run, R.X[cur], R.dp, R.np, R.dp, R.rotate, R.f[cur], R.fx[cur], h->stream);
+    k_eval_rows_launch(h->d_run, run, R.X[cur], R.dp, R.np, R.dp, suite_comps(R), R.f[cur], R.fx[cur], h->stream);
   }
   k_best_init_launch(h->d_run, run, h->stream);
   DE_CUDA(h, cudaGetLastError());

@@ -63,8 +63,10 @@ __global__ void k_eval_rows(const RunDesc* __restrict__ runs, int run, const dou
   extern __shared__ __align__(16) double sm[];
   const RunDesc& R = runs[run];
   const int d = R.d, dp = R.dp;
+  // a composition function keeps every component's rows at once
+  const int ncomp = R.obj >= kObjComposition1 ? R.nc : 1;
   double* Y = sm;
-  double* Z = Y + rows * dp;
+  double* Z = Y + ncomp * rows * dp;
   const int row0 = blockIdx.x * rows;
   const int nrows = min(rows, n - row0);
   if (nrows <= 0) return;
@@ -240,7 +242,8 @@ __device__ __forceinline__ Best gen_tile(const RunDesc& R, int64_t g, int row0, 
   const bool suite = SUITE && suite_objective(R.obj);
   if (suite) {
     // ---- the proposed benchmark's functions (Sec. 7.3, Table 2)
-    suite_tile(R, T, dp, nrows, Y, Z, s_fsuite, s_comp);
+    const int ncomp = R.obj >= kObjComposition1 ? R.nc : 1;  // Y and Z hold every component of the tile
+    suite_tile(R, T, dp, nrows, Y, Y + (size_t)ncomp * rows_max * dp, s_fsuite, s_comp);
   } else if (R.obj == kObjOde) {
     // ---- ODE objective: a warp integrates one trial's chain; f to W[row][0]
     for (int rl = warp; rl < nrows; rl += nwarps) {
@@ -449,12 +452,11 @@ void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cuda
   k_init_population<<<blocks, threads, 0, s>>>(runs, run);
 }
 
-void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int rotate,
+void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int ncomp,
                         double* f, uint8_t* fx, cudaStream_t s) {
   int rows = 8;
-  while (rows > 1 && (size_t)2 * rows * dp * sizeof(double) > 200 * 1024) rows >>= 1;
-  (void)rotate;
-  const size_t smem = (size_t)2 * rows * dp * sizeof(double);
+  while (rows > 1 && (size_t)2 * ncomp * rows * dp * sizeof(double) > 200 * 1024) rows >>= 1;
+  const size_t smem = (size_t)2 * ncomp * rows * dp * sizeof(double);
   k_eval_rows<<<(n + rows - 1) / rows, 256, smem, s>>>(runs, run, x, ld, n, rows, f, fx);
 }
 

@@ -19,8 +19,10 @@ void k_configure(size_t smem_gen);
 void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem, bool var,
                        bool suite, cudaStream_t s);
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s);
-void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int rotate,
+// ncomp: row buffers per row (the components of a composition function, else 1)
+void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int ncomp,
                         double* f, uint8_t* fx, cudaStream_t s);
+inline int suite_comps(const RunDesc& R) { return R.obj >= DE_OBJ_COMPOSITION1 ? R.nc : 1; }
 void k_best_init_launch(const RunDesc* runs, int run, cudaStream_t s);
 void k_jde_init_launch(const RunDesc* runs, int run, int np, cudaStream_t s);
 void k_ode_reference_launch(const RunDesc* runs, int run, double* ref, cudaStream_t s);

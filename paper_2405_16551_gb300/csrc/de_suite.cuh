@@ -177,8 +177,50 @@ __device__ __forceinline__ void suite_rotate(const double* __restrict__ MT, cons
   }
 }
 
+// Rotation of every component of a composition function at once:
+// Z_c[r][j] = sum_k MT_c[k][j] Y_c[r][k] for c < nc, with Y_c and Z_c the
+// c-th blocks of ROWS x dp rows.  Thread t owns (component, column) pairs
+// t, t + blockDim, ... and runs one accumulator chain per row, as
+// tile_rotate_fp64 does for one matrix (the same sums in the same order).
+template <int ROWS>
+__device__ __forceinline__ void comp_rotate(const double* __restrict__ MT, const double* __restrict__ Y,
+                                            double* __restrict__ Z, int nc, int d, int dp) {
+  const size_t blk = (size_t)ROWS * dp;
+  for (int cj = threadIdx.x; cj < nc * d; cj += blockDim.x) {
+    const int c = cj / d, j = cj - c * d;
+    const double* mcol = MT + (size_t)c * d * d + j;
+    const double* Yc = Y + c * blk;
+    double acc[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) acc[r] = 0.0;
+    int k = 0;
+    for (; k + 4 <= d; k += 4) {
+      const double m0 = __ldg(mcol + (size_t)(k + 0) * d);
+      const double m1 = __ldg(mcol + (size_t)(k + 1) * d);
+      const double m2 = __ldg(mcol + (size_t)(k + 2) * d);
+      const double m3 = __ldg(mcol + (size_t)(k + 3) * d);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const double* y = Yc + r * dp + k;
+        acc[r] = fma(m0, y[0], acc[r]);
+        acc[r] = fma(m1, y[1], acc[r]);
+        acc[r] = fma(m2, y[2], acc[r]);
+        acc[r] = fma(m3, y[3], acc[r]);
+      }
+    }
+    for (; k < d; ++k) {
+      const double m = __ldg(mcol + (size_t)k * d);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) acc[r] = fma(m, Yc[r * dp + k], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) Z[c * blk + r * dp + j] = acc[r];
+  }
+}
+
 // Objective of the suite for nrows rows of src (row stride ld, in shared or
-// global memory); the whole CTA calls it.  Y, Z: nrows x dp shared buffers;
+// global memory); the whole CTA calls it.  Y, Z: shared buffers of
+// nrows x dp doubles, nc times that for a composition function;
 // f[r] receives row r's value; comp: per row, the composition's g_c and
 // D_c (kSuiteMaxRows x 10).
 //   basic (5..14):  g(M ((x - o) s)), s the run's scale
@@ -191,54 +233,56 @@ __device__ __forceinline__ void suite_rotate(const double* __restrict__ MT, cons
 //                   logarithms; at x = o_c the weight is 1 for the first such c.
 constexpr int kSuiteMaxRows = 8;
 
-static __device__ __noinline__ void suite_tile(const RunDesc& R, const double* src, int64_t ld, int nrows, double* __restrict__ Y,
-                           double* __restrict__ Z, double* __restrict__ f, double (*comp)[10]) {
+static __device__ __noinline__ void suite_tile(const RunDesc& R, const double* src, int64_t ld, int nrows,
+                                              double* __restrict__ Y, double* __restrict__ Z, double* __restrict__ f,
+                                              double (*comp)[10]) {
   const int d = R.d, dp = R.dp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const bool is_comp = R.obj >= kObjComposition1;
   const bool is_hyb = R.obj >= kObjHybrid1 && R.obj <= kObjHybrid3;
-  const int nc = is_comp ? R.nc : 1;
-  for (int c = 0; c < nc; ++c) {
-    const double* oc = R.o + (size_t)c * dp;
-    const double s = is_comp ? R.sscale[c] : R.scale;
-    for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) {
-      const int r = e / dp, j = e - r * dp;
+  if (is_comp) {
+    // every component at once: Y_c = (x - o_c) s_c, Z_c = M_c Y_c (blocks of
+    // nrows x dp), then g_c and D_c = |x - o_c|^2 for every (row, component)
+    const int nc = R.nc;
+    const int blk = nrows * dp;
+    for (int e = threadIdx.x; e < nc * blk; e += blockDim.x) {
+      const int c = e / blk, rem = e - c * blk, r = rem / dp, j = rem - r * dp;
       double y = 0.0;
-      if (j < d) y = __dmul_rn(__dsub_rn(src[(size_t)r * ld + j], oc[j]), s);
+      if (j < d) y = __dmul_rn(__dsub_rn(src[(size_t)r * ld + j], R.o[(size_t)c * dp + j]), R.sscale[c]);
       Y[e] = y;
     }
     __syncthreads();
-    if (R.rotate) suite_rotate(R.MT + (size_t)c * d * d, Y, Z, nrows, d, dp);
-    else
-      for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) Z[e] = Y[e];
+    if (R.rotate) {
+      switch (nrows) {
+        case 1: comp_rotate<1>(R.MT, Y, Z, nc, d, dp); break;
+        case 2: comp_rotate<2>(R.MT, Y, Z, nc, d, dp); break;
+        case 3: comp_rotate<3>(R.MT, Y, Z, nc, d, dp); break;
+        case 4: comp_rotate<4>(R.MT, Y, Z, nc, d, dp); break;
+        case 5: comp_rotate<5>(R.MT, Y, Z, nc, d, dp); break;
+        case 6: comp_rotate<6>(R.MT, Y, Z, nc, d, dp); break;
+        case 7: comp_rotate<7>(R.MT, Y, Z, nc, d, dp); break;
+        default: comp_rotate<8>(R.MT, Y, Z, nc, d, dp); break;
+      }
+    } else {
+      for (int e = threadIdx.x; e < nc * blk; e += blockDim.x) Z[e] = Y[e];
+    }
     __syncthreads();
-    for (int r = warp; r < nrows; r += nwarps) {
-      const double* zr = Z + r * dp;
-      if (is_comp) {
-        const double g = basic_fn_warp(R.sfn[c], zr, nullptr, 0, d, 1.0, lane);
-        double dd = 0.0;
-        for (int j = lane; j < d; j += 32) {
-          const double t = __dsub_rn(src[(size_t)r * ld + j], oc[j]);
-          dd += t * t;
-        }
-        dd = warp_sum(dd);
-        if (lane == 0) {
-          comp[r][c] = g;
-          comp[r][5 + c] = dd;
-        }
-      } else if (is_hyb) {
-        double g = 0.0;
-        for (int q = 0; q < R.nc; ++q)
-          g += basic_fn_warp(R.sfn[q], zr, R.perm, R.seg[q], R.seg[q + 1] - R.seg[q], R.sscale[q], lane);
-        if (lane == 0) f[r] = g;
-      } else {
-        const double g = basic_fn_warp(R.obj, zr, nullptr, 0, d, 1.0, lane);
-        if (lane == 0) f[r] = g;
+    for (int p = warp; p < nc * nrows; p += nwarps) {
+      const int c = p / nrows, r = p - c * nrows;
+      const double g = basic_fn_warp(R.sfn[c], Z + (size_t)c * blk + r * dp, nullptr, 0, d, 1.0, lane);
+      const double* oc = R.o + (size_t)c * dp;
+      double dd = 0.0;
+      for (int j = lane; j < d; j += 32) {
+        const double t = __dsub_rn(src[(size_t)r * ld + j], oc[j]);
+        dd += t * t;
+      }
+      dd = warp_sum(dd);
+      if (lane == 0) {
+        comp[r][c] = g;
+        comp[r][5 + c] = dd;
       }
     }
     __syncthreads();
-  }
-  if (is_comp) {
     for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
       int hit = -1;
       for (int c = 0; c < nc; ++c)
@@ -258,7 +302,32 @@ static __device__ __noinline__ void suite_tile(const RunDesc& R, const double* s
       f[r] = acc;
     }
     __syncthreads();
+    return;
   }
+  // basic and hybrid functions: one shift and one rotation
+  for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) {
+    const int r = e / dp, j = e - r * dp;
+    double y = 0.0;
+    if (j < d) y = __dmul_rn(__dsub_rn(src[(size_t)r * ld + j], R.o[j]), R.scale);
+    Y[e] = y;
+  }
+  __syncthreads();
+  if (R.rotate) suite_rotate(R.MT, Y, Z, nrows, d, dp);
+  else
+    for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) Z[e] = Y[e];
+  __syncthreads();
+  for (int r = warp; r < nrows; r += nwarps) {
+    const double* zr = Z + r * dp;
+    double g = 0.0;
+    if (is_hyb) {
+      for (int q = 0; q < R.nc; ++q)
+        g += basic_fn_warp(R.sfn[q], zr, R.perm, R.seg[q], R.seg[q + 1] - R.seg[q], R.sscale[q], lane);
+    } else {
+      g = basic_fn_warp(R.obj, zr, nullptr, 0, d, 1.0, lane);
+    }
+    if (lane == 0) f[r] = g;
+  }
+  __syncthreads();
 }
 
 }  // namespace de
