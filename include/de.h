@@ -440,7 +440,7 @@ DE_API de_status de_mlp_train(de_mlp* m, const double* x_dev, int64_t ld, const 
  * network trains on the most recent 20,000 rows: first after 5 plain
  * generations, then every 10 generations, with surrogate_steps Adam steps on
  * standardised log f.
- * The network is also the judge of its own error: after each generation the
+ * The network's measured error decides whether it screens: after each generation the
  * Spearman correlation between its predictions and the true f of the
  * evaluated trials is measured, and the next generation screens k
  * candidates only when that correlation is at least 0.3.  Otherwise it
