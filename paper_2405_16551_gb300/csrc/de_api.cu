@@ -46,6 +46,8 @@ struct de_handle {
   Surrogate* surr = nullptr;  // surrogate-assisted generations (surrogate_k >= 2)
   bool variants = false;      // some run uses a strategy variant or jDE
   bool suite = false;         // some run uses an objective of the proposed benchmark (5..20)
+  bool fp64_persist = false;  // FP64, one run: every generation of a call in one cooperative launch
+  PersistCtl* d_ctl64 = nullptr;
   // island model (de_init_islands): the runs are islands on a migration ring
   bool islands = false;
   IslandCtl* d_isl = nullptr;
@@ -302,6 +304,14 @@ static de_status enqueue_generations(de_handle* h, int64_t n) {
     }
     return DE_OK;
   }
+  if (h->fp64_persist) {
+    // one cooperative launch runs up to 2^20 generations (or stops early)
+    for (int64_t left = n; left > 0; left -= (int64_t)1 << 20)
+      DE_CUDA(h, k_gen_fp64_persist_launch(h->d_run, h->d_items, h->nitems, h->threads, h->smem_gen, h->variants,
+                                           h->suite, h->d_ctl64, std::min<int64_t>(left, (int64_t)1 << 20),
+                                           h->stream));
+    return DE_OK;
+  }
   if (h->prec != DE_PREC_FP64 && h->tc.persist.ok) {
     // one persistent launch runs up to 2^20 generations (or stops early); the
     // launch's grid-barrier count stays below 2^32
@@ -429,7 +439,7 @@ static std::string tune_key(const de_handle* h) {
     sum_d += (long long)R.np * R.d;
   }
   char b[256];
-  snprintf(b, sizeof b, "gen_fp64v2 runs=%d np0=%d d0=%d obj0=%d rot0=%d sumnp=%lld sumnd=%lld", h->nruns, h->run[0].np,
+  snprintf(b, sizeof b, "gen_fp64v3 runs=%d np0=%d d0=%d obj0=%d rot0=%d sumnp=%lld sumnd=%lld", h->nruns, h->run[0].np,
            h->run[0].d, h->run[0].obj, h->run[0].rotate, sum_np, sum_d);
   return b;
 }
@@ -469,6 +479,16 @@ static int heuristic_rows(const de_handle* h, int nsm) {
   return (int)std::max(1LL, std::min(8LL, (np_total + nsm - 1) / nsm));
 }
 
+// The cooperative persistent FP64 kernel applies to a single run without a
+// surrogate or islands whose tiles all fit on the device at once
+// (DE_GB300_FP64_PERSIST=0 disables it, =1 forces it where it applies).
+static bool fp64_persist_ok(const de_handle* h) {
+  if (h->prec != DE_PREC_FP64 || h->nruns != 1 || h->surr || h->islands || !h->d_ctl64) return false;
+  if (const char* e = getenv("DE_GB300_FP64_PERSIST"))
+    if (e[0] == '0') return false;
+  return h->nitems <= k_gen_fp64_persist_capacity(h->threads, h->smem_gen, h->variants, h->suite);
+}
+
 static de_status autotune_fp64(de_handle* h, int nsm) {
   const char* env = getenv("DE_GB300_AUTOTUNE");
   const bool enabled = !(env && env[0] == '0');
@@ -477,7 +497,9 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
   const std::string key = tune_key(h);
   int cached = 0;
   if (tune_lookup(key, cached)) {
-    h->rows = cached;
+    // value: rows per tile, plus 100 when the cooperative persistent kernel won
+    h->rows = cached % 100;
+    h->fp64_persist = cached >= 100 && fp64_persist_ok(h);
     return DE_OK;
   }
   // candidates are timed on the freshly initialised problem, which is then
@@ -487,6 +509,7 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
   DE_CUDA(h, cudaEventCreate(&e1));
   float best_ms = 1e30f;
   int best_rows = h->rows;
+  bool best_persist = false;
   std::vector<RunDesc> saved = h->run;
   for (auto& R : h->run) {
     R.target = 0.0;  // no stop rule while timing
@@ -515,6 +538,30 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
     if (ms < best_ms * 0.97f) {
       best_ms = ms;
       best_rows = rows;
+      best_persist = false;
+    }
+    // the same tiles in one cooperative launch
+    if (fp64_persist_ok(h)) {
+      for (int r = 0; r < h->nruns; ++r) {
+        int32_t zero = 0;
+        DE_CUDA(h, cudaMemcpyAsync(&h->run[r].st->stop, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream));
+      }
+      h->fp64_persist = true;
+      st_all = enqueue_generations(h, 2);
+      if (st_all == DE_OK) {
+        DE_CUDA(h, cudaEventRecord(e0, h->stream));
+        st_all = enqueue_generations(h, reps);
+        DE_CUDA(h, cudaEventRecord(e1, h->stream));
+        DE_CUDA(h, cudaEventSynchronize(e1));
+        DE_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+      }
+      h->fp64_persist = false;
+      if (st_all != DE_OK) break;
+      if (ms < best_ms * 0.97f) {
+        best_ms = ms;
+        best_rows = rows;
+        best_persist = true;
+      }
     }
   }
   for (int r = 0; r < h->nruns; ++r) {
@@ -527,7 +574,8 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->rows = best_rows;
-  tune_store(key, best_rows);
+  h->fp64_persist = best_persist;
+  tune_store(key, best_rows + (best_persist ? 100 : 0));
   return DE_OK;
 }
 
@@ -639,6 +687,7 @@ de_status de_destroy(de_handle* h) {
   tc_plan_free(h->tc);
   if (h->d_items) cudaFree(h->d_items);
   if (h->d_run) cudaFree(h->d_run);
+  if (h->d_ctl64) cudaFree(h->d_ctl64);
   if (h->isl_mem) cudaFree(h->isl_mem);
   if (h->arena) cudaFree(h->arena);
   if (h->h_state) cudaFreeHost(h->h_state);
@@ -718,7 +767,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     O.perm = suite_spec(c.objective).kind == 1 ? take((size_t)c.d * sizeof(int32_t)) : 0;
     O.Mr = (c.rot && c.precision != DE_PREC_FP64) ? take((size_t)c.d * c.d * sizeof(double)) : 0;
     O.st = states_off + (size_t)r * sizeof(RunState);
-    O.part = take((size_t)c.np * sizeof(BestPartial));
+    O.part = take((size_t)2 * c.np * sizeof(BestPartial));  // double buffered by generation parity
     const bool split = c.precision != DE_PREC_FP64;
     O.T = split ? take(pop) : 0;
     O.ref = c.objective == DE_OBJ_ODE ? take((size_t)kOdeSteps * kOdeN * sizeof(double)) : 0;
@@ -895,10 +944,17 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
   k_configure(h->smem_gen);
   for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
   if (h->prec == DE_PREC_FP64 && cfgs[0].surrogate_k < 2) {
+    if (nruns == 1) {
+      ce = cudaMalloc(&h->d_ctl64, sizeof(PersistCtl));
+      if (ce != cudaSuccess) return fin(fail(h, DE_ERR_OOM, "cudaMalloc(persistent control) failed"));
+    }
     TRY(autotune_fp64(h, prop.multiProcessorCount));
     TRY(build_items(h));
     TRY(upload_desc(h));
     k_configure(h->smem_gen);
+    if (const char* e = getenv("DE_GB300_FP64_PERSIST"))
+      if (e[0] == '1') h->fp64_persist = true;  // forced on where it applies
+    if (h->fp64_persist && !fp64_persist_ok(h)) h->fp64_persist = false;
     for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
   } else if (h->prec != DE_PREC_FP64 && !h->tc.persist.ok) {
     TRY(autotune_split(h));
@@ -977,6 +1033,7 @@ de_status de_init_islands(const de_config* cfg, int32_t nislands, int32_t interv
   h->stage.dp = dp;
   h->isl = IslandCtl{nislands, interval, migrants, 0, -1};
   h->islands = true;
+  h->fp64_persist = false;  // migration runs between generations
   drop_graph(h);
   st = islands_resync(h);
   if (st == DE_OK) {
@@ -1016,7 +1073,9 @@ de_status de_run(de_handle* h, de_result* out) {
         left = std::max<int64_t>(left, h->run[r].max_gens - h->h_state[r].gen);
       }
     if (all) break;
-    s = enqueue_generations(h, std::max<int64_t>(1, std::min<int64_t>(chunk, left)));
+    // the persistent kernels stop the run themselves: one launch
+    const bool persistent = h->fp64_persist || (h->prec != DE_PREC_FP64 && h->tc.persist.ok);
+    s = enqueue_generations(h, std::max<int64_t>(1, persistent ? left : std::min<int64_t>(chunk, left)));
     if (s != DE_OK) return s;
     s = read_states(h);
     if (s != DE_OK) return s;
@@ -1249,7 +1308,7 @@ de_status de_get_surrogate_stats(de_handle* h, int64_t* trainings, int64_t* scre
 de_status de_get_plan(de_handle* h, int32_t* kernel_path, int32_t* cluster_size) {
   if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
   const bool persist = h->prec != DE_PREC_FP64 && h->tc.persist.ok;
-  if (kernel_path) *kernel_path = h->prec == DE_PREC_FP64 ? 0 : (persist ? 2 : 1);
+  if (kernel_path) *kernel_path = h->prec == DE_PREC_FP64 ? (h->fp64_persist ? 3 : 0) : (persist ? 2 : 1);
   if (cluster_size) *cluster_size = persist ? h->tc.persist.C : 0;
   return DE_OK;
 }

@@ -411,6 +411,123 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   }
 }
 
+// The generation loop of a single FP64 run in one cooperative launch: CTA t
+// owns item t's targets for every generation; after its tile it arrives at a
+// grid barrier (bounded spin on a global counter), then every CTA reduces
+// the tiles' best partials (double buffered by generation parity) itself, in
+// tile order, so that all of them take the same best record and stop
+// decision; tile 0 publishes the run state.  Population rows written by
+// other CTAs in generation g - 1 are read at L2 (gen_tile).
+constexpr long long kFp64Spin = 1LL << 22;
+
+template <bool VAR, bool SUITE>
+__global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restrict__ runs,
+                                                          const int4* __restrict__ items, PersistCtl* ctl,
+                                                          long long gens) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int s_stop, s_best, s_abort;
+  __shared__ long long s_gen, s_evals;
+  __shared__ double s_bestf;
+  __shared__ double s_bf[8];
+  __shared__ long long s_bk[8];
+  __shared__ int s_bi[8];
+  __shared__ double s_fsuite[kSuiteMaxRows];
+  __shared__ double s_comp[kSuiteMaxRows][10];
+  const int4 it = items[blockIdx.x];
+  __shared__ RunDesc sR;
+  load_desc(sR, runs + it.x);
+  __syncthreads();
+  const RunDesc& R = sR;
+  RunState* st = R.st;
+  const int nct = (int)gridDim.x;
+  if (threadIdx.x == 0) {
+    s_stop = st->stop;
+    s_gen = st->gen;
+    s_evals = st->evals;
+    s_bestf = st->best_f;
+    s_best = st->best_idx;
+    s_abort = 0;
+    if (blockIdx.x == 0) ctl->gen0 = s_gen;
+  }
+  __syncthreads();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+  for (long long itg = 0; itg < gens && !s_stop && !s_abort; ++itg) {
+    const int64_t g = s_gen + 1;
+    Best bb = gen_tile<VAR, SUITE>(R, g, it.z, it.w, R.rows, max(s_best, 0), sm, s_fsuite, s_comp);
+    if (lane == 0) { s_bf[warp] = bb.f; s_bk[warp] = bb.k; s_bi[warp] = bb.i; }
+    __syncthreads();
+    if (tid == 0) {
+      bb.init();
+      for (int w = 0; w < nwarps; ++w) bb.take(s_bf[w], s_bk[w], s_bi[w]);
+      BestPartial* pp = R.part + (size_t)(g & 1) * nct + it.y;
+      pp->f = bb.f;
+      pp->idx = bb.i;
+      // arrive, then wait for every CTA of this generation
+      __threadfence();
+      atomicAdd(&ctl->bar, 1u);
+      const unsigned target = (unsigned)(itg + 1) * (unsigned)nct;
+      bool ok = false;
+      for (long long k = 0; k < kFp64Spin; ++k) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->bar) : "memory");
+        if (v >= target) {
+          ok = true;
+          break;
+        }
+        if (*(volatile int*)&ctl->abort) break;
+        __nanosleep(32);
+      }
+      if (!ok) {
+        atomicExch(&ctl->abort, 1);
+        atomicOr(&st->err, kErrTimeout);
+        s_abort = 1;
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    // the best record and the stop rule of generation g, the same in every
+    // CTA: the whole CTA reduces the tiles' partials
+    {
+      Best b;
+      b.init();
+      const BestPartial* q = R.part + (size_t)(g & 1) * nct;
+      for (int t = tid; t < nct; t += blockDim.x) b.offer(__ldcg(&q[t].f), __ldcg(&q[t].idx));
+      b.warp_reduce();
+      if (lane == 0) { s_bf[warp] = b.f; s_bk[warp] = b.k; s_bi[warp] = b.i; }
+      __syncthreads();
+      if (tid == 0) {
+        b.init();
+        for (int w = 0; w < nwarps; ++w) b.take(s_bf[w], s_bk[w], s_bi[w]);
+        const bool have = b.i >= 0;
+        if (have) {
+          s_bestf = b.f;
+          s_best = b.i;
+        }
+        const int64_t evals = s_evals + R.np;
+        int stop = 0;
+        if (R.target > 0.0 && s_best >= 0 && s_bestf < R.target) stop = 1;
+        else if (R.max_evals > 0 && evals >= R.max_evals) stop = 2;
+        else if (g >= R.max_gens) stop = 3;
+        s_evals = evals;
+        s_stop = stop;
+        s_gen = g;
+        if (blockIdx.x == 0) {
+          if (have) {
+            st->best_f = b.f;
+            st->best_idx = b.i;
+          } else {
+            st->err |= kErrNonFinite;
+          }
+          st->gen = g;
+          st->evals = evals;
+          st->stop = stop;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace de
 
 // ------------------------------------------------------------------ launchers
@@ -422,7 +539,39 @@ void k_configure(size_t smem_gen) {
   cudaFuncSetAttribute(k_gen_fp64<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_gen_fp64<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_gen_fp64<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64_persist<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64_persist<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64_persist<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64_persist<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_eval_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
+                                      bool var, bool suite, PersistCtl* ctl, long long gens, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&runs, (void*)&items, (void*)&ctl, (void*)&gens};
+  const dim3 grid((unsigned)nitems), block((unsigned)threads);
+  if (var && suite) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<true, true>, grid, block, args, smem, s);
+  else if (var) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<true, false>, grid, block, args, smem, s);
+  else if (suite) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<false, true>, grid, block, args, smem, s);
+  else e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<false, false>, grid, block, args, smem, s);
+  return e;
+}
+
+int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite) {
+  int per_sm = 0, dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const void* f = var && suite ? (const void*)k_gen_fp64_persist<true, true>
+                  : var        ? (const void*)k_gen_fp64_persist<true, false>
+                  : suite      ? (const void*)k_gen_fp64_persist<false, true>
+                               : (const void*)k_gen_fp64_persist<false, false>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * nsm;
 }
 
 void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem, bool var,

@@ -12,12 +12,23 @@ namespace de {
 
 void set_last_error(const std::string& m);
 
+// grid-barrier state of a persistent launch
+struct PersistCtl {
+  unsigned int bar;  // grid barrier arrivals of the current launch
+  int abort;         // set when a bounded wait expired
+  long long gen0;    // generation counter when the launch began
+};
 // FP64 path (de_fp64.cu)
 void k_configure(size_t smem_gen);
 // var: some run uses a strategy variant or jDE; suite: some run uses an
 // objective of the proposed benchmark (5..20)
 void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem, bool var,
                        bool suite, cudaStream_t s);
+// the generation loop of one FP64 run in one cooperative launch (every item
+// co-resident: nitems <= k_gen_fp64_persist_capacity)
+cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
+                                      bool var, bool suite, PersistCtl* ctl, long long gens, cudaStream_t s);
+int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite);
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s);
 // ncomp: row buffers per row (the components of a composition function, else 1)
 void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int ncomp,
@@ -50,11 +61,6 @@ void k_island_launch(const RunDesc* runs, IslandCtl* ctl, const IslandStage& sta
                      cudaStream_t s);
 
 // persistent cluster path (de_persist.cu)
-struct PersistCtl {
-  unsigned int bar;  // grid barrier arrivals of the current launch
-  int abort;         // set when a bounded wait expired
-  long long gen0;    // generation counter when the launch began
-};
 struct PersistPlan {
   bool ok = false;
   int C = 0, ntiles = 0, prec = 0, nch = 1, prows = 128;

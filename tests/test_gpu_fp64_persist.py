@@ -1,0 +1,110 @@
+"""The FP64 cooperative persistent kernel (kernel path 3: every generation of
+a single run in one launch, a grid barrier between generations) computes
+exactly what the one-kernel-per-generation path computes, and follows the
+CPU oracle; through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_16551_gb300 import capi, problems
+
+pytestmark = pytest.mark.gpu
+
+
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _cfgs():
+    s = problems.suite(18, 10, seed=4)
+    return [
+        capi.make_config(64, 10, objective=0, shift=problems.shift(10, seed=1), seed=1, max_generations=10**6,
+                         target_error=0.0),
+        capi.make_config(250, 100, f=0.5, cr=0.3, objective=1, shift=problems.shift(100, seed=2),
+                         rot=problems.rotation(100, seed=2), seed=2, max_generations=10**6, target_error=0.0),
+        capi.make_config(100, 30, objective=3, shift=problems.shift(30, seed=3), rot=problems.rotation(30, seed=3),
+                         seed=3, max_generations=10**6, target_error=0.0, strategy=capi.DE_RAND1EXP, jde=True),
+        capi.make_config(48, 10, objective=18, shift=s["shift"], rot=s["rot"], perm=s["perm"], scale=s["scale"],
+                         seed=4, max_generations=10**6, target_error=0.0, strategy=capi.DE_BEST1BIN),
+        capi.make_config(16, 20, objective=4, shift=problems.ode_hidden(5), seed=5, max_generations=10**6,
+                         target_error=0.0),
+    ]
+
+
+def _run(monkeypatch, persist, cfg, G):
+    monkeypatch.setenv("DE_GB300_FP64_PERSIST", "1" if persist else "0")
+    h = capi.de_init(cfg)
+    try:
+        plan = capi.de_get_plan(h)["kernel_path"]
+        capi.de_step(h, G)
+        x, f = capi.de_get_population(h)
+        b = capi.de_get_best(h)
+        ad = capi.de_get_adaptive(h) if cfg.jde else None
+    finally:
+        capi.de_destroy(h)
+    assert plan == (3 if persist else 0)
+    return x, f, b, ad
+
+
+@pytest.mark.parametrize("k", range(5))
+def test_persistent_fp64_equals_the_per_generation_kernel(k, monkeypatch):
+    _need_gpu()
+    G = 120
+    xa, fa, ba, ada = _run(monkeypatch, True, _cfgs()[k], G)
+    xb, fb, bb, adb = _run(monkeypatch, False, _cfgs()[k], G)
+    assert np.array_equal(xa, xb) and np.array_equal(fa, fb)
+    for key in ("generations", "evals", "best_index", "best_f", "stop_reason"):
+        assert ba[key] == bb[key], key
+    assert ba["generations"] == G
+    if ada is not None:
+        assert np.array_equal(ada[0], adb[0]) and np.array_equal(ada[1], adb[1])
+
+
+def test_persistent_fp64_runs_the_small_sphere_like_the_oracle(monkeypatch):
+    _need_gpu()
+    monkeypatch.setenv("DE_GB300_FP64_PERSIST", "1")
+    d = 10
+    o = problems.shift(d, seed=1)
+    Xo, fo, go, evo, _ = oracle.run(64, d, 0.5, 0.9, -100, 100, 0, o, None, seed=1, max_generations=1000,
+                                    target_error=1e-8)
+    h = capi.de_init(capi.make_config(64, d, objective=0, shift=o, seed=1, max_generations=1000, target_error=1e-8))
+    try:
+        assert capi.de_get_plan(h)["kernel_path"] == 3
+        res = capi.de_run(h)[0]
+        x, f = capi.de_get_population(h)
+    finally:
+        capi.de_destroy(h)
+    assert res["generations"] == go and res["evals"] == evo and res["stop_reason"] == capi.DE_STOP_TARGET
+    assert np.array_equal(x, Xo)
+    assert np.allclose(f, fo, rtol=1e-12, atol=0)
+
+
+def test_persistent_fp64_one_generation_matches_oracle(monkeypatch):
+    _need_gpu()
+    monkeypatch.setenv("DE_GB300_FP64_PERSIST", "1")
+    np_, d, obj = 300, 37, 2
+    o, M = problems.shift(d, seed=8), problems.rotation(d, seed=8)
+    X = problems.population(np_, d, seed=8)
+    fX, _ = oracle.evaluate(obj, X, o, M)
+    h = capi.de_init(capi.make_config(np_, d, objective=obj, shift=o, rot=M, seed=9, max_generations=100,
+                                      target_error=0.0, debug_capture=True))
+    try:
+        assert capi.de_get_plan(h)["kernel_path"] == 3
+        capi.de_set_population(h, 0, X, fX)
+        capi.de_set_generation(h, 0, 4)
+        capi.de_step(h, 1)
+        g = capi.de_get_debug(h)
+        best = capi.de_get_best(h)
+    finally:
+        capi.de_destroy(h)
+    r = oracle.step(X, fX, 0.5, 0.9, -100, 100, obj, o, M, seed=9, generation=5)
+    assert np.array_equal(g["idx"], r["idx"]) and np.array_equal(g["mask"], r["mask"])
+    assert np.array_equal(g["trial"], r["trial"])
+    tol = 1e-12 * (np.abs(r["f_trial"]) + r["sabs_trial"])
+    assert np.all(np.abs(g["f_trial"] - r["f_trial"]) <= tol)
+    band = np.abs(r["f_trial"] - fX) <= tol
+    assert np.array_equal(g["accept"][~band], r["accept"][~band])
+    assert best["generations"] == 5 and best["evals"] == np_ * 6
