@@ -499,11 +499,12 @@ DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d
  *   1  split precision, three kernels per generation (trial, tensor-core
  *      fitness and selection, FP64 band), in CUDA graphs
  *   2  split precision, one persistent cluster kernel for many generations
- *   3  FP64, one cooperative persistent kernel for many generations of a
- *      single run (grid barrier between generations; the same numbers as
- *      path 0); the FP64 autotuner chooses it over path 0 when it times
- *      faster on the handle's problem; DE_GB300_FP64_PERSIST=0 / 1 forces it
- *      off / on (where it applies)
+ *   3  FP64, one cooperative persistent kernel for many generations of
+ *      every run of the handle (grid barrier between generations; the same
+ *      numbers as path 0; not with islands or a surrogate, and only when
+ *      every tile fits on the device at once); the FP64 autotuner chooses it
+ *      over path 0 when it times faster on the handle's problem;
+ *      DE_GB300_FP64_PERSIST=0 / 1 forces it off / on (where it applies)
  * cluster_size (may be NULL) receives the CTAs per cluster of path 2, else 0;
  * each cluster owns 64 or 128 targets.
  * Path 2 is chosen at de_init for a single run whose clusters all fit on the

@@ -307,9 +307,9 @@ static de_status enqueue_generations(de_handle* h, int64_t n) {
   if (h->fp64_persist) {
     // one cooperative launch runs up to 2^20 generations (or stops early)
     for (int64_t left = n; left > 0; left -= (int64_t)1 << 20)
-      DE_CUDA(h, k_gen_fp64_persist_launch(h->d_run, h->d_items, h->nitems, h->threads, h->smem_gen, h->variants,
-                                           h->suite, h->d_ctl64, std::min<int64_t>(left, (int64_t)1 << 20),
-                                           h->stream));
+      DE_CUDA(h, k_gen_fp64_persist_launch(h->d_run, h->d_items, h->nitems, h->nruns, h->threads, h->smem_gen,
+                                           h->variants, h->suite, h->d_ctl64,
+                                           std::min<int64_t>(left, (int64_t)1 << 20), h->stream));
     return DE_OK;
   }
   if (h->prec != DE_PREC_FP64 && h->tc.persist.ok) {
@@ -479,11 +479,12 @@ static int heuristic_rows(const de_handle* h, int nsm) {
   return (int)std::max(1LL, std::min(8LL, (np_total + nsm - 1) / nsm));
 }
 
-// The cooperative persistent FP64 kernel applies to a single run without a
-// surrogate or islands whose tiles all fit on the device at once
-// (DE_GB300_FP64_PERSIST=0 disables it, =1 forces it where it applies).
+// The cooperative persistent FP64 kernel applies to runs without a surrogate
+// or islands whose tiles all fit on the device at once (the grid barrier's
+// count, tiles x 2^20 generations per launch, stays below 2^32);
+// DE_GB300_FP64_PERSIST=0 disables it, =1 forces it where it applies.
 static bool fp64_persist_ok(const de_handle* h) {
-  if (h->prec != DE_PREC_FP64 || h->nruns != 1 || h->surr || h->islands || !h->d_ctl64) return false;
+  if (h->prec != DE_PREC_FP64 || h->surr || h->islands || !h->d_ctl64 || h->nitems >= 4096) return false;
   if (const char* e = getenv("DE_GB300_FP64_PERSIST"))
     if (e[0] == '0') return false;
   return h->nitems <= k_gen_fp64_persist_capacity(h->threads, h->smem_gen, h->variants, h->suite);
@@ -944,10 +945,8 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
   k_configure(h->smem_gen);
   for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
   if (h->prec == DE_PREC_FP64 && cfgs[0].surrogate_k < 2) {
-    if (nruns == 1) {
-      ce = cudaMalloc(&h->d_ctl64, sizeof(PersistCtl));
-      if (ce != cudaSuccess) return fin(fail(h, DE_ERR_OOM, "cudaMalloc(persistent control) failed"));
-    }
+    ce = cudaMalloc(&h->d_ctl64, sizeof(PersistCtl));
+    if (ce != cudaSuccess) return fin(fail(h, DE_ERR_OOM, "cudaMalloc(persistent control) failed"));
     TRY(autotune_fp64(h, prop.multiProcessorCount));
     TRY(build_items(h));
     TRY(upload_desc(h));

@@ -411,21 +411,31 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
   }
 }
 
-// The generation loop of a single FP64 run in one cooperative launch: CTA t
-// owns item t's targets for every generation; after its tile it arrives at a
-// grid barrier (bounded spin on a global counter), then every CTA reduces
-// the tiles' best partials (double buffered by generation parity) itself, in
-// tile order, so that all of them take the same best record and stop
-// decision; tile 0 publishes the run state.  Population rows written by
-// other CTAs in generation g - 1 are read at L2 (gen_tile).
+// The generation loop of FP64 runs in one cooperative launch: CTA t owns
+// item t's targets for every generation; after its tile it arrives at a grid
+// barrier (bounded spin on a global counter), then every CTA of a run reduces
+// that run's tile partials (double buffered by generation parity) itself, so
+// that all of them take the same best record and stop decision; the run's
+// tile 0 publishes the run state.  Population rows written by other CTAs in
+// generation g - 1 are read at L2 (gen_tile).
+//
+// The CTAs of a stopped run keep arriving at the barrier until every run has
+// stopped.  A run that stops at iteration k is counted (by its tile 0) in
+// ctl->stopped[k % 3]; every CTA reads that slot after barrier k + 1, when
+// it is complete and no longer written, so all CTAs see the same count and
+// leave at the same iteration; CTA 0 clears slot (k + 1) % 3 after barrier k
+// (every CTA read it after barrier k - 1; it is next written after barrier
+// k + 1).  Runs stopped before the launch are counted in
+// slot 2 (iteration -1).  With one run every CTA takes the stop decision
+// itself and the launch ends at once.
 constexpr long long kFp64Spin = 1LL << 22;
 
 template <bool VAR, bool SUITE>
 __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restrict__ runs,
-                                                          const int4* __restrict__ items, PersistCtl* ctl,
-                                                          long long gens) {
+                                                          const int4* __restrict__ items, int nruns,
+                                                          PersistCtl* ctl, long long gens) {
   extern __shared__ __align__(16) double sm[];
-  __shared__ int s_stop, s_best, s_abort;
+  __shared__ int s_stop, s_best, s_abort, s_done;
   __shared__ long long s_gen, s_evals;
   __shared__ double s_bestf;
   __shared__ double s_bf[8];
@@ -439,7 +449,8 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
   __syncthreads();
   const RunDesc& R = sR;
   RunState* st = R.st;
-  const int nct = (int)gridDim.x;
+  const unsigned nct = gridDim.x;
+  const int ntiles = R.ntiles;
   if (threadIdx.x == 0) {
     s_stop = st->stop;
     s_gen = st->gen;
@@ -447,25 +458,34 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
     s_bestf = st->best_f;
     s_best = st->best_idx;
     s_abort = 0;
+    s_done = 0;
     if (blockIdx.x == 0) ctl->gen0 = s_gen;
+    if (s_stop && it.y == 0 && nruns > 1) atomicAdd(&ctl->stopped[2], 1u);
   }
   __syncthreads();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
-  for (long long itg = 0; itg < gens && !s_stop && !s_abort; ++itg) {
+  if (nruns == 1 && s_stop) return;
+  unsigned nstopped = 0;  // runs known stopped (thread 0)
+  for (long long itg = 0; itg < gens; ++itg) {
+    const bool live = !s_stop;
     const int64_t g = s_gen + 1;
-    Best bb = gen_tile<VAR, SUITE>(R, g, it.z, it.w, R.rows, max(s_best, 0), sm, s_fsuite, s_comp);
-    if (lane == 0) { s_bf[warp] = bb.f; s_bk[warp] = bb.k; s_bi[warp] = bb.i; }
-    __syncthreads();
+    if (live) {
+      Best bb = gen_tile<VAR, SUITE>(R, g, it.z, it.w, R.rows, max(s_best, 0), sm, s_fsuite, s_comp);
+      if (lane == 0) { s_bf[warp] = bb.f; s_bk[warp] = bb.k; s_bi[warp] = bb.i; }
+      __syncthreads();
+      if (tid == 0) {
+        bb.init();
+        for (int w = 0; w < nwarps; ++w) bb.take(s_bf[w], s_bk[w], s_bi[w]);
+        BestPartial* pp = R.part + (size_t)(g & 1) * ntiles + it.y;
+        pp->f = bb.f;
+        pp->idx = bb.i;
+      }
+    }
     if (tid == 0) {
-      bb.init();
-      for (int w = 0; w < nwarps; ++w) bb.take(s_bf[w], s_bk[w], s_bi[w]);
-      BestPartial* pp = R.part + (size_t)(g & 1) * nct + it.y;
-      pp->f = bb.f;
-      pp->idx = bb.i;
-      // arrive, then wait for every CTA of this generation
+      // arrive, then wait for every CTA of this iteration
       __threadfence();
       atomicAdd(&ctl->bar, 1u);
-      const unsigned target = (unsigned)(itg + 1) * (unsigned)nct;
+      const unsigned target = (unsigned)(itg + 1) * nct;
       bool ok = false;
       for (long long k = 0; k < kFp64Spin; ++k) {
         unsigned v;
@@ -481,17 +501,24 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
         atomicExch(&ctl->abort, 1);
         atomicOr(&st->err, kErrTimeout);
         s_abort = 1;
+      } else if (nruns > 1) {
+        // runs stopped at iteration itg - 1 (complete after this barrier)
+        nstopped += __ldcg(&ctl->stopped[(itg + 2) % 3]);
+        // every CTA read slot (itg + 1) % 3 after the previous barrier; it is
+        // next written at iteration itg + 1, after the next barrier
+        if (blockIdx.x == 0) ctl->stopped[(itg + 1) % 3] = 0u;
+        if (nstopped >= (unsigned)nruns) s_done = 1;
       }
     }
     __syncthreads();
-    if (s_abort) break;
-    // the best record and the stop rule of generation g, the same in every
-    // CTA: the whole CTA reduces the tiles' partials
-    {
+    if (s_abort || s_done) break;
+    if (live) {
+      // the best record and the stop rule of generation g, the same in every
+      // CTA of the run: the whole CTA reduces the run's tile partials
       Best b;
       b.init();
-      const BestPartial* q = R.part + (size_t)(g & 1) * nct;
-      for (int t = tid; t < nct; t += blockDim.x) b.offer(__ldcg(&q[t].f), __ldcg(&q[t].idx));
+      const BestPartial* q = R.part + (size_t)(g & 1) * ntiles;
+      for (int t = tid; t < ntiles; t += blockDim.x) b.offer(__ldcg(&q[t].f), __ldcg(&q[t].idx));
       b.warp_reduce();
       if (lane == 0) { s_bf[warp] = b.f; s_bk[warp] = b.k; s_bi[warp] = b.i; }
       __syncthreads();
@@ -511,20 +538,22 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
         s_evals = evals;
         s_stop = stop;
         s_gen = g;
-        if (blockIdx.x == 0) {
+        if (it.y == 0) {
           if (have) {
             st->best_f = b.f;
             st->best_idx = b.i;
           } else {
-            st->err |= kErrNonFinite;
+            atomicOr(&st->err, kErrNonFinite);
           }
           st->gen = g;
           st->evals = evals;
           st->stop = stop;
+          if (stop && nruns > 1) atomicAdd(&ctl->stopped[itg % 3], 1u);
         }
       }
+      __syncthreads();
+      if (nruns == 1 && s_stop) break;
     }
-    __syncthreads();
   }
 }
 
@@ -546,11 +575,12 @@ void k_configure(size_t smem_gen) {
   cudaFuncSetAttribute(k_eval_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
-                                      bool var, bool suite, PersistCtl* ctl, long long gens, cudaStream_t s) {
+cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int nruns, int threads,
+                                      size_t smem, bool var, bool suite, PersistCtl* ctl, long long gens,
+                                      cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
   if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&runs, (void*)&items, (void*)&ctl, (void*)&gens};
+  void* args[] = {(void*)&runs, (void*)&items, (void*)&nruns, (void*)&ctl, (void*)&gens};
   const dim3 grid((unsigned)nitems), block((unsigned)threads);
   if (var && suite) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<true, true>, grid, block, args, smem, s);
   else if (var) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<true, false>, grid, block, args, smem, s);

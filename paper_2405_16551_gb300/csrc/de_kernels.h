@@ -17,6 +17,7 @@ struct PersistCtl {
   unsigned int bar;  // grid barrier arrivals of the current launch
   int abort;         // set when a bounded wait expired
   long long gen0;    // generation counter when the launch began
+  unsigned int stopped[3];  // runs stopped per iteration mod 3 (batched FP64 launch)
 };
 // FP64 path (de_fp64.cu)
 void k_configure(size_t smem_gen);
@@ -24,10 +25,11 @@ void k_configure(size_t smem_gen);
 // objective of the proposed benchmark (5..20)
 void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem, bool var,
                        bool suite, cudaStream_t s);
-// the generation loop of one FP64 run in one cooperative launch (every item
-// co-resident: nitems <= k_gen_fp64_persist_capacity)
-cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
-                                      bool var, bool suite, PersistCtl* ctl, long long gens, cudaStream_t s);
+// the generation loop of FP64 runs in one cooperative launch (every item
+// co-resident: nitems <= k_gen_fp64_persist_capacity; gens <= 2^20)
+cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int nruns, int threads,
+                                      size_t smem, bool var, bool suite, PersistCtl* ctl, long long gens,
+                                      cudaStream_t s);
 int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite);
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s);
 // ncomp: row buffers per row (the components of a composition function, else 1)

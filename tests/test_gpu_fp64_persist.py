@@ -108,3 +108,81 @@ def test_persistent_fp64_one_generation_matches_oracle(monkeypatch):
     band = np.abs(r["f_trial"] - fX) <= tol
     assert np.array_equal(g["accept"][~band], r["accept"][~band])
     assert best["generations"] == 5 and best["evals"] == np_ * 6
+
+
+def _batch_cfgs():
+    """Uneven runs that stop at different generations: by the target, by the
+    evaluation budget and by the generation limit."""
+    s17 = problems.suite(17, 20, seed=6)
+    return [
+        capi.make_config(32, 5, objective=0, shift=problems.shift(5, seed=1), seed=1, max_generations=400,
+                         target_error=1e-6),
+        capi.make_config(64, 10, objective=0, shift=problems.shift(10, seed=2), seed=2, run_id=1,
+                         max_generations=5000, target_error=1e-8),
+        capi.make_config(40, 17, objective=2, shift=problems.shift(17, seed=3), rot=problems.rotation(17, seed=3),
+                         seed=3, max_evals=40 * 90, max_generations=10**6, target_error=0.0),
+        capi.make_config(24, 20, objective=17, shift=s17["shift"], rot=s17["rot"], perm=s17["perm"],
+                         scale=s17["scale"], seed=6, max_generations=150, target_error=0.0, jde=True),
+        capi.make_config(90, 33, objective=1, shift=problems.shift(33, seed=7), seed=7, max_generations=260,
+                         target_error=0.0, strategy=capi.DE_BEST1BIN),
+    ]
+
+
+def _run_batch(monkeypatch, persist, steps):
+    monkeypatch.setenv("DE_GB300_FP64_PERSIST", "1" if persist else "0")
+    cfgs = _batch_cfgs()
+    h = capi.de_init_batch(cfgs)
+    out = []
+    try:
+        plan = capi.de_get_plan(h)["kernel_path"]
+        for n in steps:
+            if n < 0:
+                capi.de_reset(h, -n - 1)
+            else:
+                capi.de_step(h, n)
+        for r in range(len(cfgs)):
+            x, f = capi.de_get_population(h, r)
+            out.append((x, f, capi.de_get_best(h, r)))
+    finally:
+        capi.de_destroy(h)
+    assert plan == (3 if persist else 0)
+    return out
+
+
+@pytest.mark.parametrize("steps", [[5000], [37, 1, 200, 4000], [100, -2, 60, -5, 3000]])
+def test_persistent_fp64_batch_equals_the_per_generation_kernel(steps, monkeypatch):
+    """Runs stop at different generations (a stopped run's tiles keep meeting
+    the grid barrier until the last run stops); resets of single runs."""
+    _need_gpu()
+    a = _run_batch(monkeypatch, True, steps)
+    b = _run_batch(monkeypatch, False, steps)
+    for r, ((xa, fa, ba), (xb, fb, bb)) in enumerate(zip(a, b)):
+        assert np.array_equal(xa, xb) and np.array_equal(fa, fb), r
+        for key in ("generations", "evals", "best_index", "best_f", "stop_reason"):
+            assert ba[key] == bb[key], (r, key)
+    stops = [x[2]["stop_reason"] for x in a]
+    if steps == [5000]:
+        assert stops[0] == capi.DE_STOP_TARGET and stops[2] == capi.DE_STOP_EVALS
+        assert stops[3] == capi.DE_STOP_GENERATIONS and stops[4] == capi.DE_STOP_GENERATIONS
+
+
+def test_persistent_fp64_batch_runs_like_the_oracle(monkeypatch):
+    _need_gpu()
+    monkeypatch.setenv("DE_GB300_FP64_PERSIST", "1")
+    cfgs = _batch_cfgs()[:3]
+    h = capi.de_init_batch(cfgs)
+    try:
+        assert capi.de_get_plan(h)["kernel_path"] == 3
+        capi.de_step(h, 5000)
+        got = [(capi.de_get_population(h, r), capi.de_get_best(h, r)) for r in range(3)]
+    finally:
+        capi.de_destroy(h)
+    args = [(32, 5, 0, problems.shift(5, seed=1), None, 1, 0, 400, 0, 1e-6),
+            (64, 10, 0, problems.shift(10, seed=2), None, 2, 1, 5000, 0, 1e-8),
+            (40, 17, 2, problems.shift(17, seed=3), problems.rotation(17, seed=3), 3, 0, 10**6, 40 * 90, 0.0)]
+    for (np_, d, obj, o, M, seed, rid, mg, me, te), ((x, f), b) in zip(args, got):
+        Xo, fo, go, evo, _ = oracle.run(np_, d, 0.5, 0.9, -100, 100, obj, o, M, seed=seed, run_id=rid,
+                                        max_generations=mg, max_evals=me, target_error=te)
+        assert b["generations"] == go and b["evals"] == evo
+        assert np.array_equal(x, Xo)
+        assert np.allclose(f, fo, rtol=1e-12, atol=0)
