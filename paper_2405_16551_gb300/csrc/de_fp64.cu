@@ -481,10 +481,14 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
         pp->idx = bb.i;
       }
     }
-    if (tid == 0) {
-      // arrive, then wait for every CTA of this iteration
-      __threadfence();
-      atomicAdd(&ctl->bar, 1u);
+    if (warp == 0) {
+      // arrive, then wait for every CTA of this iteration; the whole warp
+      // polls the counter (one load per poll, no divergent spin)
+      if (lane == 0) {
+        __threadfence();
+        atomicAdd(&ctl->bar, 1u);
+      }
+      __syncwarp();
       const unsigned target = (unsigned)(itg + 1) * nct;
       bool ok = false;
       for (long long k = 0; k < kFp64Spin; ++k) {
@@ -497,17 +501,20 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
         if (*(volatile int*)&ctl->abort) break;
         __nanosleep(32);
       }
-      if (!ok) {
-        atomicExch(&ctl->abort, 1);
-        atomicOr(&st->err, kErrTimeout);
-        s_abort = 1;
-      } else if (nruns > 1) {
-        // runs stopped at iteration itg - 1 (complete after this barrier)
-        nstopped += __ldcg(&ctl->stopped[(itg + 2) % 3]);
-        // every CTA read slot (itg + 1) % 3 after the previous barrier; it is
-        // next written at iteration itg + 1, after the next barrier
-        if (blockIdx.x == 0) ctl->stopped[(itg + 1) % 3] = 0u;
-        if (nstopped >= (unsigned)nruns) s_done = 1;
+      __syncwarp();
+      if (lane == 0) {
+        if (!ok) {
+          atomicExch(&ctl->abort, 1);
+          atomicOr(&st->err, kErrTimeout);
+          s_abort = 1;
+        } else if (nruns > 1) {
+          // runs stopped at iteration itg - 1 (complete after this barrier)
+          nstopped += __ldcg(&ctl->stopped[(itg + 2) % 3]);
+          // every CTA read slot (itg + 1) % 3 after the previous barrier; it is
+          // next written at iteration itg + 1, after the next barrier
+          if (blockIdx.x == 0) ctl->stopped[(itg + 1) % 3] = 0u;
+          if (nstopped >= (unsigned)nruns) s_done = 1;
+        }
       }
     }
     __syncthreads();

@@ -62,9 +62,10 @@ __device__ __forceinline__ void grid_arrive(PersistCtl* ctl) {
   atomicAdd(&ctl->bar, 1u);
 }
 
-// Leaders only: arrive and wait until `target` CTAs have arrived.
-__device__ bool grid_barrier(PersistCtl* ctl, unsigned target) {
-  grid_arrive(ctl);
+// Wait until `target` CTAs have arrived at the grid barrier (called by a
+// whole warp: every lane reads the same counter in the same instruction, so
+// all of them leave the loop together).
+__device__ bool grid_wait(PersistCtl* ctl, unsigned target) {
   for (long long k = 0; k < kGridSpin; ++k) {
     if (ld_acquire_u32(&ctl->bar) >= target) return true;
     if (*(volatile int*)&ctl->abort) return false;
@@ -591,36 +592,44 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     if (!leader && tid == 0) grid_arrive(ctl);
 
-    // ---- 5. grid barrier; best record and stop rule (thread 0 of each leader)
-    if (leader && tid == 0) {
+    // ---- 5. grid barrier (thread 0 of each leader); best record and stop
+    // rule (the leader's warp 0 reduces the clusters' partials)
+    if (leader && warp == 0) {
       if (!s_abort) {
-        if (!grid_barrier(ctl, (unsigned)(itg + 1) * (unsigned)(nclusters * C))) {
+        // the whole warp polls (one load per poll, no divergent spin)
+        if (lane == 0) grid_arrive(ctl);
+        __syncwarp();
+        if (!grid_wait(ctl, (unsigned)(itg + 1) * (unsigned)(nclusters * C)) && lane == 0) {
           atomicOr(&st->err, kErrTimeout);
           s_abort = 1;
         }
+        __syncwarp();
       }
       if (!s_abort) {
         Best b;
         b.init();
         const BestPartial* pp = R.part + (size_t)(g & 1) * nclusters;
-        for (int t = 0; t < nclusters; ++t) b.offer(__ldcg(&pp[t].f), __ldcg(&pp[t].idx));
-        const double bf = b.f;
-        const int bi = b.i;
-        const int64_t evals = (int64_t)np * (1 + g);  // the initial population counts as NP evaluations
-        int sp = 0;
-        if (R.target > 0.0 && bi >= 0 && bf < R.target) sp = 1;
-        else if (R.max_evals > 0 && evals >= R.max_evals) sp = 2;
-        else if (g >= R.max_gens) sp = 3;
-        s_stop = sp;
-        s_best = bf;
-        if (bi >= 0) s_bidx = bi;
-        s_gen = g;
-        if (tile == 0) {
-          // one writer of the run state; evals are published at the end
-          st->best_f = bf;
-          st->best_idx = bi;
-          st->gen = g;
-          st->stop = sp;
+        for (int t = lane; t < nclusters; t += 32) b.offer(__ldcg(&pp[t].f), __ldcg(&pp[t].idx));
+        b.warp_reduce();
+        if (lane == 0) {
+          const double bf = b.f;
+          const int bi = b.i;
+          const int64_t evals = (int64_t)np * (1 + g);  // the initial population counts as NP evaluations
+          int sp = 0;
+          if (R.target > 0.0 && bi >= 0 && bf < R.target) sp = 1;
+          else if (R.max_evals > 0 && evals >= R.max_evals) sp = 2;
+          else if (g >= R.max_gens) sp = 3;
+          s_stop = sp;
+          s_best = bf;
+          if (bi >= 0) s_bidx = bi;
+          s_gen = g;
+          if (tile == 0) {
+            // one writer of the run state; evals are published at the end
+            st->best_f = bf;
+            st->best_idx = bi;
+            st->gen = g;
+            st->stop = sp;
+          }
         }
       }
     }
