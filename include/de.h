@@ -506,7 +506,8 @@ DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d
  *      over path 0 when it times faster on the handle's problem;
  *      DE_GB300_FP64_PERSIST=0 / 1 forces it off / on (where it applies)
  * cluster_size (may be NULL) receives the CTAs per cluster of path 2, else 0;
- * each cluster owns 64 or 128 targets.
+ * each cluster owns up to 128 targets (a multiple of the cluster size, timed
+ * at de_init; DE_GB300_PERSIST_ROWS fixes it).
  * Path 2 is chosen at de_init for a single run whose clusters all fit on the
  * device at once; the environment variable DE_GB300_PERSIST=0 disables it. */
 DE_API de_status de_get_plan(de_handle* h, int32_t* kernel_path, int32_t* cluster_size);

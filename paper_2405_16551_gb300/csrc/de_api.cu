@@ -657,6 +657,72 @@ static de_status autotune_split(de_handle* h) {
   return s;
 }
 
+// Rows per cluster of the persistent cluster kernel: fewer rows give each
+// CTA fewer trials to build but put more clusters at the grid barrier.  Timed
+// on the handle's own problem from 128 rows down (multiples of the cluster
+// size, every tile resident), cached like the other choices; it never changes
+// results.  DE_GB300_PERSIST_ROWS fixes the value instead.
+static std::string tune_key_persist(const de_handle* h) {
+  const RunDesc& R = h->run[0];
+  char b[256];
+  snprintf(b, sizeof b, "persist_v1 prec=%d np=%d d=%d obj=%d rot=%d var=%d", h->prec, R.np, R.d, R.obj, R.rotate,
+           h->tc.persist.var ? 1 : 0);
+  return b;
+}
+
+static de_status autotune_persist(de_handle* h) {
+  const char* env = getenv("DE_GB300_AUTOTUNE");
+  PersistPlan& pp = h->tc.persist;
+  if ((env && env[0] == '0') || !pp.ok || getenv("DE_GB300_PERSIST_ROWS")) return DE_OK;
+  const std::string key = tune_key_persist(h);
+  int cached = 0;
+  if (tune_lookup(key, cached)) {
+    persist_set_rows(pp, h->run[0], cached);
+    return DE_OK;
+  }
+  cudaEvent_t e0, e1;
+  DE_CUDA(h, cudaEventCreate(&e0));
+  DE_CUDA(h, cudaEventCreate(&e1));
+  std::vector<RunDesc> saved = h->run;
+  for (auto& R : h->run) {
+    R.target = 0.0;  // no stop rule while timing
+    R.max_evals = 0;
+    R.max_gens = INT64_MAX / 4;
+  }
+  de_status st_all = upload_desc(h);
+  const int first = pp.prows;
+  float best_ms = 1e30f;
+  int best = first;
+  for (int rows = first; rows >= pp.C && st_all == DE_OK; rows -= pp.C) {
+    if (!persist_set_rows(pp, h->run[0], rows)) continue;
+    int32_t zero = 0;
+    DE_CUDA(h, cudaMemcpyAsync(&h->run[0].st->stop, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream));
+    st_all = enqueue_generations(h, 4);
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2 && st_all == DE_OK; ++rep) {
+      DE_CUDA(h, cudaEventRecord(e0, h->stream));
+      st_all = enqueue_generations(h, 24);
+      DE_CUDA(h, cudaEventRecord(e1, h->stream));
+      DE_CUDA(h, cudaEventSynchronize(e1));
+      float t = 0.f;
+      DE_CUDA(h, cudaEventElapsedTime(&t, e0, e1));
+      ms = std::min(ms, t);
+    }
+    if (st_all == DE_OK && ms < best_ms * 0.98f) {
+      best_ms = ms;
+      best = rows;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->run = saved;
+  persist_set_rows(pp, h->run[0], best);
+  if (st_all != DE_OK) return st_all;
+  const de_status s = upload_desc(h);
+  if (s == DE_OK) tune_store(key, best);
+  return s;
+}
+
 // ---------------------------------------------------------------- C ABI
 extern "C" {
 
@@ -955,9 +1021,17 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
       if (e[0] == '1') h->fp64_persist = true;  // forced on where it applies
     if (h->fp64_persist && !fp64_persist_ok(h)) h->fp64_persist = false;
     for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
-  } else if (h->prec != DE_PREC_FP64 && !h->tc.persist.ok) {
-    TRY(autotune_split(h));
-    for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
+  } else if (h->prec != DE_PREC_FP64) {
+    if (h->tc.persist.ok) TRY(autotune_persist(h));
+    else TRY(autotune_split(h));
+    for (int r = 0; r < nruns; ++r) {
+      TRY(init_run(h, r));
+      // the counters start after the timing generations
+      if (h->run[r].stats) {
+        ce = cudaMemsetAsync(h->run[r].stats, 0, 2 * sizeof(unsigned long long), h->stream);
+        if (ce != cudaSuccess) return fin(fail(h, DE_ERR_CUDA, std::string("init: ") + cudaGetErrorString(ce)));
+      }
+    }
   }
   if (cfgs[0].surrogate_k >= 2) {
     const de_status ss = surr_create(h->surr, cfgs[0].surrogate_k, cfgs[0].surrogate_steps,

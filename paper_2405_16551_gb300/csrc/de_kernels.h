@@ -66,6 +66,7 @@ void k_island_launch(const RunDesc* runs, IslandCtl* ctl, const IslandStage& sta
 struct PersistPlan {
   bool ok = false;
   int C = 0, ntiles = 0, prec = 0, nch = 1, prows = 128;
+  int maxcl = 0;  // clusters that fit on the device at once
   bool var = false;  // the run uses a strategy variant or jDE
   size_t smem = 0;
 };
@@ -93,6 +94,9 @@ struct TcPlan {
   PersistCtl* d_ctl = nullptr;
 };
 bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec);
+// rows per cluster of a planned persistent launch (a multiple of C, at most
+// 128, with every tile resident); false leaves the plan unchanged
+bool persist_set_rows(PersistPlan& pp, const RunDesc& R, int prows);
 cudaError_t persist_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
                            cudaStream_t s);
 

@@ -689,9 +689,9 @@ bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
   const int C = kPC;
   const size_t smem = persist_smem(R, C);
   if (smem > 220 * 1024) return false;
-  // tiles of 128 rows (fewer clusters meet at the grid barrier, which costs
-  // more than the extra trials per CTA); smaller populations take one tile
-  // of their own size (a multiple of C)
+  // first choice: tiles of 128 rows (smaller populations take one tile of
+  // their own size, a multiple of C); the split autotuner then times smaller
+  // tiles (fewer trials per CTA, more clusters at the grid barrier)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)C);
   cfg.blockDim = dim3(256);
@@ -715,22 +715,28 @@ bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
     cudaGetLastError();
     return false;
   }
+  pp.C = C;
+  pp.maxcl = nclusters;
   int prows = std::min(kTileM, (R.np + C - 1) / C * C);
   if (const char* env = getenv("DE_GB300_PERSIST_ROWS")) {
     const int v = atoi(env);
     if (v >= C && v <= kTileM && v % C == 0) prows = v;
   }
-  if (prows > kTileM) return false;
-  const int ntiles = (R.np + prows - 1) / prows;
-  if (ntiles > nclusters) return false;
+  if (!persist_set_rows(pp, R, prows)) return false;
   pp.ok = true;
-  pp.C = C;
-  pp.ntiles = ntiles;
   pp.smem = smem;
   pp.prec = prec;
   pp.nch = 1;
-  pp.prows = prows;
   pp.var = var;
+  return true;
+}
+
+bool persist_set_rows(PersistPlan& pp, const RunDesc& R, int prows) {
+  if (pp.C < 1 || prows < pp.C || prows > kTileM || prows % pp.C != 0) return false;
+  const int ntiles = (R.np + prows - 1) / prows;
+  if (ntiles > pp.maxcl) return false;
+  pp.prows = prows;
+  pp.ntiles = ntiles;
   return true;
 }
 

@@ -185,6 +185,35 @@ def test_split_paths_agree_over_many_generations(prec, monkeypatch):
     assert np.array_equal(pops[0][0], pops[1][0])
 
 
+@pytest.mark.parametrize("rows", ["8", "40", "88", "128"])
+def test_persistent_rows_per_cluster_do_not_change_results(rows, monkeypatch):
+    """The persistent kernel's rows per cluster (tuned at de_init) only change
+    the tiling: the populations, counters and best records after 150
+    generations equal those of the three-kernel path (NP = 120: 1 to 15
+    clusters)."""
+    _need_gpu()
+    d = 40
+    o, M = problems.shift(d, seed=6), problems.rotation(d, seed=6)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("DE_GB300_PERSIST", flag)
+        monkeypatch.setenv("DE_GB300_PERSIST_ROWS", rows)
+        h = capi.de_init(capi.make_config(120, d, objective=3, shift=o, rot=M, seed=5, precision=capi.DE_PREC_BF16X3,
+                                          max_generations=150, target_error=0.0))
+        try:
+            if flag == "1":
+                assert capi.de_get_plan(h)["kernel_path"] == 2
+            capi.de_run(h)
+            x, f = capi.de_get_population(h)
+            out.append((x, f, capi.de_get_best(h), capi.de_get_stats(h)))
+        finally:
+            capi.de_destroy(h)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for key in ("generations", "evals", "best_index", "best_f", "stop_reason"):
+        assert out[0][2][key] == out[1][2][key], key
+    assert out[0][3]["trials"] == out[1][3]["trials"] == 120 * 150  # trials evaluated since de_init
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_near_policy_reaches_the_target_and_reports_fp64_best(prec):
     """With the default near-optimum policy the small sphere run still meets
