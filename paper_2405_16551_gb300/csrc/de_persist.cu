@@ -75,6 +75,23 @@ __device__ bool grid_wait(PersistCtl* ctl, unsigned target) {
   return false;
 }
 
+// Row stride (floats) of the accumulator rows a CTA receives: at least the
+// N extent, and 4 mod 8 so that the leader's 16-byte stores of 32 rows at a
+// time spread over all banks.
+__host__ __device__ inline int persist_zstride(const RunDesc& R) { return R.ntn + ((12 - R.ntn % 8) % 8); }
+
+// Byte offset of those rows in the kernel's dynamic shared memory.  The
+// leader keeps them in its A operand (free once the products are complete;
+// the other CTAs write the next operands only after the generation's last
+// cluster barrier), the other CTAs after their own layout (rows of M, band
+// vectors, reduction scratch).
+__host__ __device__ inline size_t persist_z_offset(const RunDesc& R, int C, bool leader) {
+  if (leader) return (size_t)R.b_tile_bytes;
+  const int cwp = (R.d + C - 2) / (C - 1);
+  const size_t member = ((size_t)(cwp + 1) * R.d + (size_t)2 * kPBandMax * R.dp + 16 * 17 + 17) * sizeof(double);
+  return (member + 15) / 16 * 16;
+}
+
 // NCH: 128-coordinate chunks per row (1 for d <= 128, 2 for d <= 256);
 // VAR: the run uses a strategy variant or jDE (a separate instance, so that
 // plain DE/rand/1/bin keeps its register allocation)
@@ -116,9 +133,8 @@ __global__ void __launch_bounds__(256, 1)
   __shared__ uint8_t s_fx[kTileM];
   __shared__ uint8_t s_flag[kTileM];  // bit 0 accept, bit 1 decided in FP64, bit 2 pending FP64
   __shared__ int s_blist[kTileM];
-  __shared__ float s_part[5][kTileM];
   __shared__ double s_bpart[2 * kPBandMax][kPMaxC][2];
-  __shared__ int s_nb, s_stop, s_abort, s_bidx;
+  __shared__ int s_nb, s_stop, s_abort, s_bidx, s_have;
   __shared__ long long s_gen;
   __shared__ double s_best;
   __shared__ double s_bf[8];
@@ -150,6 +166,15 @@ __global__ void __launch_bounds__(256, 1)
   double* l_best = cluster.map_shared_rank(&s_best, 0);
   int* l_bidx = cluster.map_shared_rank(&s_bidx, 0);
   long long* l_gen = cluster.map_shared_rank(&s_gen, 0);
+  double* l_f = cluster.map_shared_rank(s_f, 0);
+  double* l_ft = cluster.map_shared_rank(s_ft, 0);
+  float* l_tau = cluster.map_shared_rank(s_tau, 0);
+  int* l_have = cluster.map_shared_rank(&s_have, 0);
+  // every CTA: the FP32 accumulator rows of its targets (written by the
+  // leader), after both layouts above
+  const int zs = persist_zstride(R);
+  const size_t zoff_lead = persist_z_offset(R, C, true), zoff_member = persist_z_offset(R, C, false);
+  float* zbuf = reinterpret_cast<float*>(smem + (leader ? zoff_lead : zoff_member));
 
   const uint32_t bar_b = smem_u32(&s_bar[0]), bar_mma = smem_u32(&s_bar[1]);
   const uint32_t ncols = R.ntn <= 32 ? 32u : (R.ntn <= 64 ? 64u : (R.ntn <= 128 ? 128u : 256u));
@@ -177,7 +202,9 @@ __global__ void __launch_bounds__(256, 1)
                    "r"(ncols));
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    // rows of the tile past the population end stay zero in the operand
+    // rows of the tile past the population end start at zero in the operand
+    // (their products are never read; the leader's accumulator rows later
+    // reuse the start of this region)
     for (uint32_t q = tid * 16u; q < 2u * a_part; q += blockDim.x * 16u)
       *reinterpret_cast<uint4*>(sA + q) = make_uint4(0u, 0u, 0u, 0u);
     const int cur0 = (int)(*(volatile int64_t*)&st->gen & 1);
@@ -295,7 +322,8 @@ __global__ void __launch_bounds__(256, 1)
     }
     cluster.sync();  // operands complete
 
-    // ---- 2. leader: split products, FP32 objective, selection
+    // ---- 2. leader: split products; each accumulator row goes to the CTA
+    // that owns the target (distributed shared memory)
     if (leader) {
       if (tid == 0) {
         s_nb = 0;
@@ -318,13 +346,16 @@ __global__ void __launch_bounds__(256, 1)
       const bool have = mbar_wait(bar_mma, (uint32_t)(itg & 1));
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int m = 32 * (warp & 3) + lane;
-      const int h = warp >> 2;
       const int half = R.ntn / 2;
-      const int cb = h * half;
+      const int cb = (warp >> 2) * half;
       const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-      EpiAcc acc_{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const bool rows_here = (warp & 3) * 32 < kPRows;  // TMEM lanes of this warp hold targets
       if (have && rows_here) {
+        const bool mine = m < kPRows && row0 + m < np;
+        const int owner = mine ? m / rpm : 0;
+        float* dst = cluster.map_shared_rank(reinterpret_cast<float*>(smem + (owner == 0 ? zoff_lead : zoff_member)),
+                                             owner) +
+                     (size_t)(m % rpm) * zs + cb;
         for (int c = 0; c < half; c += 32) {
           float v[32];
           const int w = min(32, half - c);
@@ -339,33 +370,45 @@ __global__ void __launch_bounds__(256, 1)
           } else {
             tmem_ld8(ta, v);
           }
-          epi_dispatch(obj, v, w, cb + c, d, c == 0, acc_);
+          if (mine) {
+#pragma unroll
+            for (int e = 0; e < 32; e += 4)
+              if (e < w) *reinterpret_cast<float4*>(dst + c + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+          }
         }
-        if (obj == kObjRosenbrock && h == 0 && half < R.ntn && half < d) {
-          const float t = tmem_ld1(tmem + lane_base + (uint32_t)half) + 1.f;
-          const float a2 = t - acc_.prev_t * acc_.prev_t, b2 = acc_.prev_t - 1.f;
-          acc_.a1 += fmaf(100.f * a2, a2, b2 * b2);
-          acc_.aG += 400.f * fabsf(acc_.prev_t) * fabsf(a2) + 2.f * fabsf(b2) + 200.f * fabsf(a2);
-        }
-      } else if (tid == 0) {
+      } else if (!have && tid == 0) {
         atomicOr(&st->err, kErrTimeout);
         s_abort = 1;
       }
+      if (tid == 0) s_have = have ? 1 : 0;
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      if (h == 1) {
-        s_part[0][m] = acc_.a1;
-        s_part[1][m] = acc_.a2;
-        s_part[2][m] = acc_.a3;
-        s_part[3][m] = acc_.aS;
-        s_part[4][m] = acc_.aG;
+    }
+    cluster.sync();  // accumulator rows delivered
+
+    // ---- 2b. every CTA, for its own targets: the FP32 objective from the
+    // accumulator row (16 threads per row, columns strided, then a fixed xor
+    // tree) and the selection, on the leader's tile state
+    {
+      const int rr = tid >> 4, sub = tid & 15;
+      const int lr = crank * rpm + rr;
+      const int i = row0 + lr;
+      const bool valid = rr < rpm && i < np;
+      const bool have = *l_have != 0;
+      EpiAcc acc_{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (valid && have) epi_strided_dispatch(obj, zbuf + (size_t)rr * zs, sub, d, acc_);
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        acc_.a1 += __shfl_xor_sync(0xffffffffu, acc_.a1, o);
+        acc_.a2 += __shfl_xor_sync(0xffffffffu, acc_.a2, o);
+        acc_.a3 += __shfl_xor_sync(0xffffffffu, acc_.a3, o);
+        acc_.aS += __shfl_xor_sync(0xffffffffu, acc_.aS, o);
+        acc_.aG += __shfl_xor_sync(0xffffffffu, acc_.aG, o);
       }
-      __syncthreads();
-      if (h == 0 && m < kPRows) {
-        const int i = row0 + m;
-        s_flag[m] = 0;
-        if (i < np) {
-          const float s1 = acc_.a1 + s_part[0][m], s2 = acc_.a2 + s_part[1][m], s3 = acc_.a3 + s_part[2][m];
-          float S = acc_.aS + s_part[3][m], G = acc_.aG + s_part[4][m];
+      if (sub == 0 && rr < rpm) {
+        uint8_t flag = 0;
+        if (valid) {
+          const float s1 = acc_.a1, s2 = acc_.a2, s3 = acc_.a3;
+          float S = acc_.aS, G = acc_.aG;
           float fs;
           if (obj == kObjAckley) {
             const float r = sqrtf(s1 / (float)d);
@@ -377,10 +420,10 @@ __global__ void __launch_bounds__(256, 1)
             if (obj != kObjRastrigin) S = s1;
             fs = s1;
           }
-          const float tau = 2.f * R.band_u * G * R.rownorm * s_yn[m] + (float)d * 0x1.0p-21f * S + 1e-30f;
-          const double fi = s_f[m];
+          const float tau = 2.f * R.band_u * G * R.rownorm * l_yn[lr] + (float)d * 0x1.0p-21f * S + 1e-30f;
+          const double fi = l_f[lr];
           const float fif = (float)fi;
-          const float tif = s_fx[m] ? 0.f : s_tau[m];
+          const float tif = l_fx[lr] ? 0.f : l_tau[lr];
           const float mrg = 0x1.0p-22f * fabsf(fif);
           const float bp = (float)best_prev;
           const bool sure_reject = fs - tau > fif + tif + mrg;
@@ -389,21 +432,21 @@ __global__ void __launch_bounds__(256, 1)
           const bool may_be_best = R.band_all && fs - tau <= bp + 0x1.0p-22f * fabsf(bp);
           const bool near = fs - tau <= R.near_thr || fif - tif <= R.near_thr;
           const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f;
-          s_ft[m] = (double)fs;
+          l_ft[lr] = (double)fs;
           if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !have) {
-            s_blist[atomicAdd(&s_nb, 1)] = m;
-            s_flag[m] = 4;
+            l_blist[atomicAdd(l_nb, 1)] = lr;
+            flag = 4;
           } else if (sure_accept || (ambiguous && fs <= fif)) {
             // decided on the split values (an undecidable comparison far from
             // the optimum goes to the smaller split value, ties to the trial)
-            s_flag[m] = 1;
-            s_f[m] = (double)fs;
-            s_fx[m] = 0;
-            s_tau[m] = tau;
+            flag = 1;
+            l_f[lr] = (double)fs;
+            l_fx[lr] = 0;
+            l_tau[lr] = tau;
           }
         }
+        l_flag[lr] = flag;
       }
-      __syncthreads();
     }
     cluster.sync();  // decisions and the band list are visible
 
@@ -676,8 +719,7 @@ __global__ void k_persist_close(const RunDesc* __restrict__ runs, int run, const
 // ------------------------------------------------------------------ host side
 size_t persist_smem(const RunDesc& R, int C) {
   const size_t lead = (size_t)R.a_tile_bytes + R.b_tile_bytes + (size_t)2 * kPBandMax * R.dp * sizeof(double);
-  const int cwp = (R.d + C - 2) / (C - 1);
-  const size_t member = ((size_t)(cwp + 1) * R.d + (size_t)2 * kPBandMax * R.dp + 16 * 17 + 17) * sizeof(double);
+  const size_t member = persist_z_offset(R, C, false) + (size_t)16 * persist_zstride(R) * sizeof(float);
   return std::max(lead, member);
 }
 

@@ -226,4 +226,43 @@ __device__ __forceinline__ void epi_dispatch(int obj, const float* v, int w, int
   else epi_cols<kObjRosenbrock>(v, w, nb, d, first, A);
 }
 
+// The same terms over one accumulator row held in shared memory, the
+// columns j = sub, sub + 16, ... of one of 16 threads (each term in the order
+// of epi_cols; Rosenbrock's term of coordinate j pairs z_j with z_{j+1}).
+template <int OBJ>
+__device__ __forceinline__ void epi_strided(const float* z, int sub, int d, EpiAcc& A) {
+  for (int j = sub; j < d; j += 16) {
+    const float zj = z[j];
+    if constexpr (OBJ == kObjSphere) {
+      A.a1 = fmaf(zj, zj, A.a1);
+      A.aG += 2.f * fabsf(zj);
+    } else if constexpr (OBJ == kObjRastrigin) {
+      const float cz = cos2pi_f32(zj);
+      A.a1 += fmaf(zj, zj, fmaf(-10.f, cz, 10.f));
+      A.aS += fmaf(zj, zj, fmaf(10.f, fabsf(cz), 10.f));
+      A.aG += fmaf(2.f, fabsf(zj), 62.83185307f);
+    } else if constexpr (OBJ == kObjAckley) {
+      const float cz = cos2pi_f32(zj);
+      A.a1 = fmaf(zj, zj, A.a1);
+      A.a2 += cz;
+      A.a3 += fabsf(zj);
+      A.aS += fabsf(cz);
+    } else {  // Rosenbrock at t = z + 1
+      if (j + 1 < d) {
+        const float t = zj + 1.f, tn = z[j + 1] + 1.f;
+        const float aa = tn - t * t, bb = t - 1.f;
+        A.a1 += fmaf(100.f * aa, aa, bb * bb);
+        A.aG += 400.f * fabsf(t) * fabsf(aa) + 2.f * fabsf(bb) + 200.f * fabsf(aa);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void epi_strided_dispatch(int obj, const float* z, int sub, int d, EpiAcc& A) {
+  if (obj == kObjSphere) epi_strided<kObjSphere>(z, sub, d, A);
+  else if (obj == kObjRastrigin) epi_strided<kObjRastrigin>(z, sub, d, A);
+  else if (obj == kObjAckley) epi_strided<kObjAckley>(z, sub, d, A);
+  else epi_strided<kObjRosenbrock>(z, sub, d, A);
+}
+
 }  // namespace de
