@@ -12,9 +12,11 @@
 //      |y| straight into the leader's shared memory (distributed shared
 //      memory);
 //   2. cluster barrier; the leader runs the three split products on tcgen05
-//      (M is resident in its shared memory for the whole launch), evaluates
-//      the objective terms from TMEM in FP32 and decides every selection the
-//      split-precision bound allows;
+//      (M is resident in its shared memory for the whole launch) and sends
+//      each accumulator row from TMEM to the CTA that owns the target;
+//      after a second cluster barrier every CTA evaluates the objective terms
+//      of its rows in FP32 and decides every selection the split-precision
+//      bound allows, on the leader's tile state;
 //   3. rows it cannot decide (and trials that could become the best) are
 //      re-evaluated in FP64: their owners publish y to the leader, the other
 //      CTAs of the cluster each compute a block of z = M y and its objective
