@@ -502,10 +502,13 @@ DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d
  *   3  FP64, one cooperative persistent kernel for many generations of
  *      every run of the handle (grid barrier between generations; the same
  *      numbers as path 0; not with islands or a surrogate, and only when
- *      every tile fits on the device at once); the FP64 autotuner chooses it
- *      over path 0 when it times faster on the handle's problem;
- *      DE_GB300_FP64_PERSIST=0 / 1 forces it off / on (where it applies)
- * cluster_size (may be NULL) receives the CTAs per cluster of path 2, else 0;
+ *      every tile fits on the device at once), or, for one run of at most 8
+ *      tiles, the same loop as one thread-block cluster (cluster barrier);
+ *      the FP64 autotuner chooses among path 0 and these when one times
+ *      faster on the handle's problem; DE_GB300_FP64_PERSIST=0 / 1 / 2 forces
+ *      path 0 / the cooperative launch / the cluster (where it applies)
+ * cluster_size (may be NULL) receives the CTAs per cluster of path 2 or of
+ * path 3 launched as one cluster, else 0;
  * each cluster owns up to 128 targets (a multiple of the cluster size, timed
  * at de_init; DE_GB300_PERSIST_ROWS fixes it).
  * Path 2 is chosen at de_init for a single run whose clusters all fit on the

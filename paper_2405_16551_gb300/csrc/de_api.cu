@@ -46,7 +46,8 @@ struct de_handle {
   Surrogate* surr = nullptr;  // surrogate-assisted generations (surrogate_k >= 2)
   bool variants = false;      // some run uses a strategy variant or jDE
   bool suite = false;         // some run uses an objective of the proposed benchmark (5..20)
-  bool fp64_persist = false;  // FP64, one run: every generation of a call in one cooperative launch
+  bool fp64_persist = false;  // FP64: every generation of a call in one cooperative launch
+  bool fp64_cluster = false;  // ... launched as one thread-block cluster (one run of at most 8 tiles)
   PersistCtl* d_ctl64 = nullptr;
   // island model (de_init_islands): the runs are islands on a migration ring
   bool islands = false;
@@ -305,11 +306,17 @@ static de_status enqueue_generations(de_handle* h, int64_t n) {
     return DE_OK;
   }
   if (h->fp64_persist) {
-    // one cooperative launch runs up to 2^20 generations (or stops early)
-    for (int64_t left = n; left > 0; left -= (int64_t)1 << 20)
-      DE_CUDA(h, k_gen_fp64_persist_launch(h->d_run, h->d_items, h->nitems, h->nruns, h->threads, h->smem_gen,
-                                           h->variants, h->suite, h->d_ctl64,
-                                           std::min<int64_t>(left, (int64_t)1 << 20), h->stream));
+    // one cooperative (or one-cluster) launch runs up to 2^20 generations (or
+    // stops early)
+    for (int64_t left = n; left > 0; left -= (int64_t)1 << 20) {
+      const long long g = std::min<int64_t>(left, (int64_t)1 << 20);
+      if (h->fp64_cluster)
+        DE_CUDA(h, k_gen_fp64_cluster_launch(h->d_run, h->d_items, h->nitems, h->threads, h->smem_gen, h->variants,
+                                             h->suite, h->d_ctl64, g, h->stream));
+      else
+        DE_CUDA(h, k_gen_fp64_persist_launch(h->d_run, h->d_items, h->nitems, h->nruns, h->threads, h->smem_gen,
+                                             h->variants, h->suite, h->d_ctl64, g, h->stream));
+    }
     return DE_OK;
   }
   if (h->prec != DE_PREC_FP64 && h->tc.persist.ok) {
@@ -439,7 +446,7 @@ static std::string tune_key(const de_handle* h) {
     sum_d += (long long)R.np * R.d;
   }
   char b[256];
-  snprintf(b, sizeof b, "gen_fp64v3 runs=%d np0=%d d0=%d obj0=%d rot0=%d sumnp=%lld sumnd=%lld", h->nruns, h->run[0].np,
+  snprintf(b, sizeof b, "gen_fp64v4 runs=%d np0=%d d0=%d obj0=%d rot0=%d sumnp=%lld sumnd=%lld", h->nruns, h->run[0].np,
            h->run[0].d, h->run[0].obj, h->run[0].rotate, sum_np, sum_d);
   return b;
 }
@@ -490,6 +497,12 @@ static bool fp64_persist_ok(const de_handle* h) {
   return h->nitems <= k_gen_fp64_persist_capacity(h->threads, h->smem_gen, h->variants, h->suite);
 }
 
+// ... and as one thread-block cluster: one run of at most 8 tiles.
+static bool fp64_cluster_ok(const de_handle* h) {
+  return h->nruns == 1 && fp64_persist_ok(h) &&
+         k_gen_fp64_cluster_fits(h->nitems, h->threads, h->smem_gen, h->variants, h->suite);
+}
+
 static de_status autotune_fp64(de_handle* h, int nsm) {
   const char* env = getenv("DE_GB300_AUTOTUNE");
   const bool enabled = !(env && env[0] == '0');
@@ -498,9 +511,11 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
   const std::string key = tune_key(h);
   int cached = 0;
   if (tune_lookup(key, cached)) {
-    // value: rows per tile, plus 100 when the cooperative persistent kernel won
+    // value: rows per tile, plus 100 x the mode that won (0: one kernel per
+    // generation, 1: cooperative persistent kernel, 2: the same as one cluster)
     h->rows = cached % 100;
-    h->fp64_persist = cached >= 100 && fp64_persist_ok(h);
+    h->fp64_persist = cached >= 100;
+    h->fp64_cluster = cached >= 200;
     return DE_OK;
   }
   // candidates are timed on the freshly initialised problem, which is then
@@ -509,8 +524,7 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
   DE_CUDA(h, cudaEventCreate(&e0));
   DE_CUDA(h, cudaEventCreate(&e1));
   float best_ms = 1e30f;
-  int best_rows = h->rows;
-  bool best_persist = false;
+  int best_rows = h->rows, best_mode = 0;
   std::vector<RunDesc> saved = h->run;
   for (auto& R : h->run) {
     R.target = 0.0;  // no stop rule while timing
@@ -539,15 +553,17 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
     if (ms < best_ms * 0.97f) {
       best_ms = ms;
       best_rows = rows;
-      best_persist = false;
+      best_mode = 0;
     }
-    // the same tiles in one cooperative launch
-    if (fp64_persist_ok(h)) {
+    // the same tiles in one cooperative launch, and as one cluster
+    for (int mode = 1; mode <= 2 && st_all == DE_OK; ++mode) {
+      if (mode == 1 ? !fp64_persist_ok(h) : !fp64_cluster_ok(h)) continue;
       for (int r = 0; r < h->nruns; ++r) {
         int32_t zero = 0;
         DE_CUDA(h, cudaMemcpyAsync(&h->run[r].st->stop, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream));
       }
       h->fp64_persist = true;
+      h->fp64_cluster = mode == 2;
       st_all = enqueue_generations(h, 2);
       if (st_all == DE_OK) {
         DE_CUDA(h, cudaEventRecord(e0, h->stream));
@@ -557,13 +573,14 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
         DE_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
       }
       h->fp64_persist = false;
-      if (st_all != DE_OK) break;
-      if (ms < best_ms * 0.97f) {
+      h->fp64_cluster = false;
+      if (st_all == DE_OK && ms < best_ms * 0.97f) {
         best_ms = ms;
         best_rows = rows;
-        best_persist = true;
+        best_mode = mode;
       }
     }
+    if (st_all != DE_OK) break;
   }
   for (int r = 0; r < h->nruns; ++r) {
     // keep the tile fields, restore the stop rule
@@ -571,12 +588,13 @@ static de_status autotune_fp64(de_handle* h, int nsm) {
     saved[r].ntiles = h->run[r].ntiles;
   }
   h->run = saved;
-  if (st_all != DE_OK) return st_all;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (st_all != DE_OK) return st_all;
   h->rows = best_rows;
-  h->fp64_persist = best_persist;
-  tune_store(key, best_rows + (best_persist ? 100 : 0));
+  h->fp64_persist = best_mode >= 1;
+  h->fp64_cluster = best_mode == 2;
+  tune_store(key, best_rows + 100 * best_mode);
   return DE_OK;
 }
 
@@ -1017,9 +1035,13 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     TRY(build_items(h));
     TRY(upload_desc(h));
     k_configure(h->smem_gen);
-    if (const char* e = getenv("DE_GB300_FP64_PERSIST"))
-      if (e[0] == '1') h->fp64_persist = true;  // forced on where it applies
-    if (h->fp64_persist && !fp64_persist_ok(h)) h->fp64_persist = false;
+    if (const char* e = getenv("DE_GB300_FP64_PERSIST")) {
+      // forced on where it applies: 1 cooperative launch, 2 one cluster
+      if (e[0] == '1' || e[0] == '2') h->fp64_persist = true;
+      h->fp64_cluster = e[0] == '2';
+    }
+    if (h->fp64_cluster && !fp64_cluster_ok(h)) h->fp64_cluster = false;
+    if (h->fp64_persist && !fp64_persist_ok(h)) h->fp64_persist = h->fp64_cluster = false;
     for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
   } else if (h->prec != DE_PREC_FP64) {
     if (h->tc.persist.ok) TRY(autotune_persist(h));
@@ -1106,7 +1128,7 @@ de_status de_init_islands(const de_config* cfg, int32_t nislands, int32_t interv
   h->stage.dp = dp;
   h->isl = IslandCtl{nislands, interval, migrants, 0, -1};
   h->islands = true;
-  h->fp64_persist = false;  // migration runs between generations
+  h->fp64_persist = h->fp64_cluster = false;  // migration runs between generations
   drop_graph(h);
   st = islands_resync(h);
   if (st == DE_OK) {
@@ -1382,7 +1404,8 @@ de_status de_get_plan(de_handle* h, int32_t* kernel_path, int32_t* cluster_size)
   if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
   const bool persist = h->prec != DE_PREC_FP64 && h->tc.persist.ok;
   if (kernel_path) *kernel_path = h->prec == DE_PREC_FP64 ? (h->fp64_persist ? 3 : 0) : (persist ? 2 : 1);
-  if (cluster_size) *cluster_size = persist ? h->tc.persist.C : 0;
+  if (cluster_size)
+    *cluster_size = persist ? h->tc.persist.C : (h->prec == DE_PREC_FP64 && h->fp64_cluster ? h->nitems : 0);
   return DE_OK;
 }
 

@@ -21,6 +21,7 @@
 // M^T is one coalesced read shared by all rows of the tile).  The last CTA of
 // a run to finish (atomic ticket) reduces the per-tile best partials in tile
 // order, so the best record is deterministic.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -31,6 +32,8 @@
 #include "de_device.cuh"
 #include "de_kernels.h"
 #include "de_suite.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace de {
 
@@ -428,12 +431,16 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
 // k + 1).  Runs stopped before the launch are counted in
 // slot 2 (iteration -1).  With one run every CTA takes the stop decision
 // itself and the launch ends at once.
+//
+// clustered = 1: the launch is one thread-block cluster (a single run of at
+// most 8 tiles); the hardware cluster barrier, whose release / acquire covers
+// the global writes of every thread, replaces the counter.
 constexpr long long kFp64Spin = 1LL << 22;
 
 template <bool VAR, bool SUITE>
 __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restrict__ runs,
                                                           const int4* __restrict__ items, int nruns,
-                                                          PersistCtl* ctl, long long gens) {
+                                                          PersistCtl* ctl, long long gens, int clustered) {
   extern __shared__ __align__(16) double sm[];
   __shared__ int s_stop, s_best, s_abort, s_done;
   __shared__ long long s_gen, s_evals;
@@ -481,7 +488,9 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
         pp->idx = bb.i;
       }
     }
-    if (warp == 0) {
+    if (clustered) {
+      cg::this_cluster().sync();
+    } else if (warp == 0) {
       // arrive, then wait for every CTA of this iteration; the whole warp
       // polls the counter (one load per poll, no divergent spin)
       if (lane == 0) {
@@ -587,13 +596,61 @@ cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, in
                                       cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
   if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&runs, (void*)&items, (void*)&nruns, (void*)&ctl, (void*)&gens};
+  int clustered = 0;
+  void* args[] = {(void*)&runs, (void*)&items, (void*)&nruns, (void*)&ctl, (void*)&gens, (void*)&clustered};
   const dim3 grid((unsigned)nitems), block((unsigned)threads);
   if (var && suite) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<true, true>, grid, block, args, smem, s);
   else if (var) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<true, false>, grid, block, args, smem, s);
   else if (suite) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<false, true>, grid, block, args, smem, s);
   else e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<false, false>, grid, block, args, smem, s);
   return e;
+}
+
+// The same kernel as one cluster of nitems CTAs (nitems <= 8, one run).
+template <bool VAR, bool SUITE>
+static cudaError_t fp64_cluster_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
+                                       PersistCtl* ctl, long long gens, cudaStream_t s, bool query_only,
+                                       int* nclusters) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nitems);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)nitems;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (query_only) return cudaOccupancyMaxActiveClusters(nclusters, k_gen_fp64_persist<VAR, SUITE>, &cfg);
+  const int nruns = 1, clustered = 1;
+  return cudaLaunchKernelEx(&cfg, k_gen_fp64_persist<VAR, SUITE>, runs, items, nruns, ctl, gens, clustered);
+}
+
+cudaError_t k_gen_fp64_cluster_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
+                                      bool var, bool suite, PersistCtl* ctl, long long gens, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
+  if (e != cudaSuccess) return e;
+  if (var && suite) return fp64_cluster_launch<true, true>(runs, items, nitems, threads, smem, ctl, gens, s, false, nullptr);
+  if (var) return fp64_cluster_launch<true, false>(runs, items, nitems, threads, smem, ctl, gens, s, false, nullptr);
+  if (suite) return fp64_cluster_launch<false, true>(runs, items, nitems, threads, smem, ctl, gens, s, false, nullptr);
+  return fp64_cluster_launch<false, false>(runs, items, nitems, threads, smem, ctl, gens, s, false, nullptr);
+}
+
+bool k_gen_fp64_cluster_fits(int nitems, int threads, size_t smem, bool var, bool suite) {
+  if (nitems < 1 || nitems > 8) return false;
+  int n = 0;
+  cudaError_t e;
+  if (var && suite) e = fp64_cluster_launch<true, true>(nullptr, nullptr, nitems, threads, smem, nullptr, 0, 0, true, &n);
+  else if (var) e = fp64_cluster_launch<true, false>(nullptr, nullptr, nitems, threads, smem, nullptr, 0, 0, true, &n);
+  else if (suite) e = fp64_cluster_launch<false, true>(nullptr, nullptr, nitems, threads, smem, nullptr, 0, 0, true, &n);
+  else e = fp64_cluster_launch<false, false>(nullptr, nullptr, nitems, threads, smem, nullptr, 0, 0, true, &n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= 1;
 }
 
 int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite) {

@@ -31,6 +31,11 @@ cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, in
                                       size_t smem, bool var, bool suite, PersistCtl* ctl, long long gens,
                                       cudaStream_t s);
 int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite);
+// the same loop as one thread-block cluster of nitems CTAs (one run,
+// nitems <= 8), the cluster barrier between generations
+cudaError_t k_gen_fp64_cluster_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
+                                      bool var, bool suite, PersistCtl* ctl, long long gens, cudaStream_t s);
+bool k_gen_fp64_cluster_fits(int nitems, int threads, size_t smem, bool var, bool suite);
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s);
 // ncomp: row buffers per row (the components of a composition function, else 1)
 void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int ncomp,

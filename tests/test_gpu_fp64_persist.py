@@ -186,3 +186,74 @@ def test_persistent_fp64_batch_runs_like_the_oracle(monkeypatch):
         assert b["generations"] == go and b["evals"] == evo
         assert np.array_equal(x, Xo)
         assert np.allclose(f, fo, rtol=1e-12, atol=0)
+
+
+def _small_cfgs():
+    """Runs of at most 8 tiles: the cooperative loop can run as one
+    thread-block cluster (rows per tile 1 without the autotuner)."""
+    s19 = problems.suite(19, 12, seed=9)
+    return [
+        capi.make_config(8, 10, objective=0, shift=problems.shift(10, seed=1), seed=1, max_generations=10**6,
+                         target_error=0.0),
+        capi.make_config(7, 37, objective=1, shift=problems.shift(37, seed=2), rot=problems.rotation(37, seed=2),
+                         seed=2, max_generations=10**6, target_error=0.0, jde=True, strategy=capi.DE_RAND1EXP),
+        capi.make_config(5, 12, objective=19, shift=s19["shift"], rot=s19["rot"], seed=9, max_generations=10**6,
+                         target_error=0.0, strategy=capi.DE_BEST1BIN),
+    ]
+
+
+@pytest.mark.parametrize("k", range(3))
+def test_one_cluster_fp64_loop_equals_the_per_generation_kernel(k, monkeypatch):
+    """The cooperative FP64 loop launched as one cluster (cluster barrier
+    between generations) gives the populations, records and jDE parameters of
+    the one-kernel-per-generation path."""
+    _need_gpu()
+    monkeypatch.setenv("DE_GB300_AUTOTUNE", "0")
+    out = []
+    for mode in ("2", "0"):
+        monkeypatch.setenv("DE_GB300_FP64_PERSIST", mode)
+        cfg = _small_cfgs()[k]
+        h = capi.de_init(cfg)
+        try:
+            plan = capi.de_get_plan(h)
+            capi.de_step(h, 150)
+            x, f = capi.de_get_population(h)
+            out.append((plan, x, f, capi.de_get_best(h), capi.de_get_adaptive(h) if cfg.jde else None))
+        finally:
+            capi.de_destroy(h)
+    (pa, xa, fa, ba, ada), (pb, xb, fb, bb, adb) = out
+    assert pa == {"kernel_path": 3, "cluster_size": _small_cfgs()[k].np} and pb["kernel_path"] == 0
+    assert np.array_equal(xa, xb) and np.array_equal(fa, fb)
+    for key in ("generations", "evals", "best_index", "best_f", "stop_reason"):
+        assert ba[key] == bb[key], key
+    assert ba["generations"] == 150
+    if ada is not None:
+        assert np.array_equal(ada[0], adb[0]) and np.array_equal(ada[1], adb[1])
+
+
+def test_one_cluster_fp64_run_stops_like_the_oracle(monkeypatch):
+    """A run to 1e-8 as one cluster stops at the oracle's generation with its
+    evaluation count, and its population equals the per-generation path's
+    (near the optimum the GPU and the oracle may settle FP64 near-ties
+    differently, so the oracle's population is not compared)."""
+    _need_gpu()
+    monkeypatch.setenv("DE_GB300_AUTOTUNE", "0")
+    d = 6
+    o = problems.shift(d, seed=3)
+    Xo, fo, go, evo, _ = oracle.run(8, d, 0.5, 0.9, -100, 100, 0, o, None, seed=3, max_generations=3000,
+                                    target_error=1e-8)
+    out = []
+    for mode in ("2", "0"):
+        monkeypatch.setenv("DE_GB300_FP64_PERSIST", mode)
+        h = capi.de_init(capi.make_config(8, d, objective=0, shift=o, seed=3, max_generations=3000,
+                                          target_error=1e-8))
+        try:
+            assert capi.de_get_plan(h)["cluster_size"] == (8 if mode == "2" else 0)
+            res = capi.de_run(h)[0]
+            out.append((res, capi.de_get_population(h)))
+        finally:
+            capi.de_destroy(h)
+    (ra, (xa, fa)), (rb, (xb, fb)) = out
+    assert ra["generations"] == rb["generations"] == go and ra["evals"] == rb["evals"] == evo
+    assert ra["stop_reason"] == rb["stop_reason"]
+    assert np.array_equal(xa, xb) and np.array_equal(fa, fb)
