@@ -46,19 +46,65 @@ __device__ __forceinline__ double schwefel_term(double t, int n) {
   return t * sin(sqrt(fabs(t)));
 }
 
+// The costly part of coordinate l's term of basic function fn (the FP64
+// transcendental functions), at w = w_l and v = w_{next(l)} (the cyclic
+// neighbour, for the pair functions); 0 where fn has none.  The whole CTA
+// computes these for a tile before one warp per row sums the terms.
+__device__ __forceinline__ double basic_costly(int fn, double w, double v, int l, int n) {
+  switch (fn) {
+    case kObjRastrigin:
+    case kObjAckley: return cos2pi_f64_horner(w);
+    case kObjSchwefel: return schwefel_term(w + 420.9687462275036, n);
+    case kObjSchafferF6: {
+      const double s = w * w + v * v;
+      const double sn = sin(sqrt(s));
+      const double den = 1.0 + 0.001 * s;
+      return 0.5 + (sn * sn - 0.5) / (den * den);
+    }
+    case kObjKatsuura: {
+      // 1 + i sum_{j=1}^{32} |2^j w - nearest integer| / 2^j, to the power 10 / n^1.2;
+      // 2^j w, its rounding and the difference are exact
+      double s = 0.0, p2 = 1.0;
+      for (int j = 1; j <= 32; ++j) {
+        p2 *= 2.0;
+        const double t = p2 * w;
+        s += fabs(t - rint(t)) / p2;
+      }
+      return pow(1.0 + (double)(l + 1) * s, 10.0 / pow((double)n, 1.2));
+    }
+    case kObjGriewankRosenbrock: {
+      // Griewank's 1-D term of Rosenbrock's 2-D term of the cyclic pair, at t = w + 1
+      const double u = w + 1.0, vv = v + 1.0;
+      const double a = u * u - vv, b = u - 1.0;
+      const double r = 100.0 * a * a + b * b;
+      return r * r / 4000.0 - cos(r) + 1.0;
+    }
+    case kObjElliptic: return n > 1 ? pow(1e6, (double)l / (double)(n - 1)) : 1.0;
+    case kObjGriewank: return cos(w / sqrt((double)(l + 1)));
+    default: return 0.0;
+  }
+}
+
+__device__ __forceinline__ bool basic_has_costly(int fn) {
+  return fn == kObjRastrigin || fn == kObjAckley || fn == kObjSchwefel || fn == kObjSchafferF6 ||
+         fn == kObjKatsuura || fn == kObjGriewankRosenbrock || fn == kObjElliptic || fn == kObjGriewank;
+}
+
 // g of basic function fn on the n-vector w_l = sc * z[src(l)], src(l) =
-// idx[base + l] (idx != NULL: a hybrid part) or base + l; position i = l + 1.
-// Called by a whole warp; every lane returns g.
-static __device__ __noinline__ double basic_fn_warp(int fn, const double* __restrict__ z, const int32_t* __restrict__ idx, int base,
-                                int n, double sc, int lane) {
+// idx[base + l] (idx != NULL: a hybrid part) or base + l; position i = l + 1;
+// E[l] holds basic_costly of coordinate l.  Called by a whole warp: lane k
+// sums the terms of l = k, k + 32, ... in order, then a fixed xor tree; every
+// lane returns g.
+static __device__ __noinline__ double basic_fn_warp(int fn, const double* __restrict__ z,
+                                                    const int32_t* __restrict__ idx, int base, int n, double sc,
+                                                    const double* __restrict__ E, int lane) {
   auto W = [&](int l) { return sc * z[idx ? idx[base + l] : base + l]; };
   double s1 = 0.0, s2 = 0.0, p = 1.0;
-  const double kex = fn == kObjKatsuura ? 10.0 / pow((double)n, 1.2) : 0.0;
   for (int l = lane; l < n; l += 32) {
     const double w = W(l);
     switch (fn) {
       case kObjSphere: s1 += w * w; break;
-      case kObjRastrigin: s1 += w * w - 10.0 * cos2pi_f64_horner(w) + 10.0; break;
+      case kObjRastrigin: s1 += w * w - 10.0 * E[l] + 10.0; break;
       case kObjRosenbrock:
         if (l + 1 < n) {
           const double t0 = w + 1.0, t1 = W(l + 1) + 1.0;
@@ -68,14 +114,16 @@ static __device__ __noinline__ double basic_fn_warp(int fn, const double* __rest
         break;
       case kObjAckley:
         s1 += w * w;
-        s2 += cos2pi_f64_horner(w);
+        s2 += E[l];
         break;
       case kObjZakharov:
         // sum w^2 + (sum 0.5 i w_i)^2 + (sum 0.5 i w_i)^4
         s1 += w * w;
         s2 += 0.5 * (double)(l + 1) * w;
         break;
-      case kObjSchwefel: s1 += schwefel_term(w + 420.9687462275036, n); break;
+      case kObjSchwefel:
+      case kObjSchafferF6:
+      case kObjGriewankRosenbrock: s1 += E[l]; break;
       case kObjBentCigar: s1 += (l == 0 ? 1.0 : 1e6) * (w * w); break;
       case kObjHGBat:
       case kObjHappyCat: {
@@ -84,43 +132,11 @@ static __device__ __noinline__ double basic_fn_warp(int fn, const double* __rest
         s2 += x;
         break;
       }
-      case kObjSchafferF6: {
-        // pair (w_l, w_{l+1}), cyclic
-        const double v = W(l + 1 < n ? l + 1 : 0);
-        const double s = w * w + v * v;
-        const double sn = sin(sqrt(s));
-        const double den = 1.0 + 0.001 * s;
-        s1 += 0.5 + (sn * sn - 0.5) / (den * den);
-        break;
-      }
-      case kObjKatsuura: {
-        // 1 + i sum_{j=1}^{32} |2^j w - nearest integer| / 2^j, to the power 10 / n^1.2;
-        // 2^j w, its rounding and the difference are exact
-        double s = 0.0, p2 = 1.0;
-        for (int j = 1; j <= 32; ++j) {
-          p2 *= 2.0;
-          const double v = p2 * w;
-          s += fabs(v - rint(v)) / p2;
-        }
-        p *= pow(1.0 + (double)(l + 1) * s, kex);
-        break;
-      }
-      case kObjGriewankRosenbrock: {
-        // Griewank's 1-D term of Rosenbrock's 2-D term of the cyclic pair, at t = w + 1
-        const double u = w + 1.0, v = W(l + 1 < n ? l + 1 : 0) + 1.0;
-        const double a = u * u - v, b = u - 1.0;
-        const double r = 100.0 * a * a + b * b;
-        s1 += r * r / 4000.0 - cos(r) + 1.0;
-        break;
-      }
-      case kObjElliptic: {
-        const double c = n > 1 ? pow(1e6, (double)l / (double)(n - 1)) : 1.0;
-        s1 += c * (w * w);
-        break;
-      }
+      case kObjKatsuura: p *= E[l]; break;
+      case kObjElliptic: s1 += E[l] * (w * w); break;
       case kObjGriewank:
         s1 += w * w / 4000.0;
-        p *= cos(w / sqrt((double)(l + 1)));
+        p *= E[l];
         break;
       default: s1 = CUDART_NAN;
     }
@@ -267,9 +283,19 @@ static __device__ __noinline__ void suite_tile(const RunDesc& R, const double* s
       for (int e = threadIdx.x; e < nc * blk; e += blockDim.x) Z[e] = Y[e];
     }
     __syncthreads();
+    // the costly parts of every (component, row, coordinate) over the whole
+    // CTA, into Y (free after the rotation)
+    for (int e = threadIdx.x; e < nc * blk; e += blockDim.x) {
+      const int c = e / blk, rem = e - c * blk, r = rem / dp, j = rem - r * dp;
+      if (j >= d || !basic_has_costly(R.sfn[c])) continue;
+      const double* zr = Z + (size_t)c * blk + r * dp;
+      Y[e] = basic_costly(R.sfn[c], zr[j], zr[j + 1 < d ? j + 1 : 0], j, d);
+    }
+    __syncthreads();
     for (int p = warp; p < nc * nrows; p += nwarps) {
       const int c = p / nrows, r = p - c * nrows;
-      const double g = basic_fn_warp(R.sfn[c], Z + (size_t)c * blk + r * dp, nullptr, 0, d, 1.0, lane);
+      const double g =
+          basic_fn_warp(R.sfn[c], Z + (size_t)c * blk + r * dp, nullptr, 0, d, 1.0, Y + (size_t)c * blk + r * dp, lane);
       const double* oc = R.o + (size_t)c * dp;
       double dd = 0.0;
       for (int j = lane; j < d; j += 32) {
@@ -316,14 +342,35 @@ static __device__ __noinline__ void suite_tile(const RunDesc& R, const double* s
   else
     for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) Z[e] = Y[e];
   __syncthreads();
+  // the costly parts of every (row, position) over the whole CTA, into Y
+  // (free after the rotation); a hybrid part q takes positions seg_q ..
+  // seg_{q+1} - 1 of the permuted row
+  for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) {
+    const int r = e / dp, j = e - r * dp;
+    if (j >= d) continue;
+    const double* zr = Z + r * dp;
+    if (is_hyb) {
+      int q = 0;
+      while (q + 1 < R.nc && j >= R.seg[q + 1]) ++q;
+      const int fn = R.sfn[q];
+      if (!basic_has_costly(fn)) continue;
+      const int b0 = R.seg[q], n = R.seg[q + 1] - b0, l = j - b0;
+      const double sc = R.sscale[q];
+      Y[e] = basic_costly(fn, sc * zr[R.perm[j]], sc * zr[R.perm[b0 + (l + 1 < n ? l + 1 : 0)]], l, n);
+    } else if (basic_has_costly(R.obj)) {
+      Y[e] = basic_costly(R.obj, zr[j], zr[j + 1 < d ? j + 1 : 0], j, d);
+    }
+  }
+  __syncthreads();
   for (int r = warp; r < nrows; r += nwarps) {
     const double* zr = Z + r * dp;
+    const double* er = Y + r * dp;
     double g = 0.0;
     if (is_hyb) {
       for (int q = 0; q < R.nc; ++q)
-        g += basic_fn_warp(R.sfn[q], zr, R.perm, R.seg[q], R.seg[q + 1] - R.seg[q], R.sscale[q], lane);
+        g += basic_fn_warp(R.sfn[q], zr, R.perm, R.seg[q], R.seg[q + 1] - R.seg[q], R.sscale[q], er + R.seg[q], lane);
     } else {
-      g = basic_fn_warp(R.obj, zr, nullptr, 0, d, 1.0, lane);
+      g = basic_fn_warp(R.obj, zr, nullptr, 0, d, 1.0, er, lane);
     }
     if (lane == 0) f[r] = g;
   }
