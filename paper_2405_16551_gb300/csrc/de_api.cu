@@ -963,6 +963,10 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
         suite_segments(sp, c.d, R.seg);
         R.perm = (const int32_t*)(A + O.perm);
       }
+      for (int q = 0; q < sp.n; ++q) {
+        const int n = sp.kind == 1 ? R.seg[q + 1] - R.seg[q] : c.d;
+        R.skex[q] = 10.0 / std::pow((double)n, 1.2);
+      }
     }
     if (c.jde) {
       R.jF[0] = (double*)(A + O.jF0);

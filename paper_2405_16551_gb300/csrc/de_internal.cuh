@@ -78,6 +78,7 @@ struct RunDesc {
   int32_t sfn[5];          // basic function of each
   int32_t seg[6];          // hybrid: first permuted position of each part, seg[nc] = d
   double sscale[5];        // domain scale of each
+  double skex[5];          // Katsuura's exponent 10 / n^1.2 of each (n: its length)
   double slambda[5], ssigma[5], sbias[5];  // composition: height, coverage, bias
   const int32_t* perm;     // hybrid: d positions of the permutation
   // buffers

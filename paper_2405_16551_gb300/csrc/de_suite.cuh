@@ -49,8 +49,9 @@ __device__ __forceinline__ double schwefel_term(double t, int n) {
 // The costly part of coordinate l's term of basic function fn (the FP64
 // transcendental functions), at w = w_l and v = w_{next(l)} (the cyclic
 // neighbour, for the pair functions); 0 where fn has none.  The whole CTA
-// computes these for a tile before one warp per row sums the terms.
-__device__ __forceinline__ double basic_costly(int fn, double w, double v, int l, int n) {
+// computes these for a tile before one warp per row sums the terms.  kex:
+// Katsuura's exponent 10 / n^1.2 for this n (computed once per part).
+__device__ __forceinline__ double basic_costly(int fn, double w, double v, int l, int n, double kex) {
   switch (fn) {
     case kObjRastrigin:
     case kObjAckley: return cos2pi_f64_horner(w);
@@ -70,7 +71,7 @@ __device__ __forceinline__ double basic_costly(int fn, double w, double v, int l
         const double t = p2 * w;
         s += fabs(t - rint(t)) / p2;
       }
-      return pow(1.0 + (double)(l + 1) * s, 10.0 / pow((double)n, 1.2));
+      return pow(1.0 + (double)(l + 1) * s, kex);
     }
     case kObjGriewankRosenbrock: {
       // Griewank's 1-D term of Rosenbrock's 2-D term of the cyclic pair, at t = w + 1
@@ -289,7 +290,7 @@ static __device__ __noinline__ void suite_tile(const RunDesc& R, const double* s
       const int c = e / blk, rem = e - c * blk, r = rem / dp, j = rem - r * dp;
       if (j >= d || !basic_has_costly(R.sfn[c])) continue;
       const double* zr = Z + (size_t)c * blk + r * dp;
-      Y[e] = basic_costly(R.sfn[c], zr[j], zr[j + 1 < d ? j + 1 : 0], j, d);
+      Y[e] = basic_costly(R.sfn[c], zr[j], zr[j + 1 < d ? j + 1 : 0], j, d, R.skex[c]);
     }
     __syncthreads();
     for (int p = warp; p < nc * nrows; p += nwarps) {
@@ -343,22 +344,35 @@ static __device__ __noinline__ void suite_tile(const RunDesc& R, const double* s
     for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) Z[e] = Y[e];
   __syncthreads();
   // the costly parts of every (row, position) over the whole CTA, into Y
-  // (free after the rotation); a hybrid part q takes positions seg_q ..
-  // seg_{q+1} - 1 of the permuted row
-  for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) {
-    const int r = e / dp, j = e - r * dp;
-    if (j >= d) continue;
-    const double* zr = Z + r * dp;
-    if (is_hyb) {
+  // (free after the rotation)
+  if (is_hyb) {
+    // part q takes positions seg_q .. seg_{q+1} - 1 of the permuted row; its
+    // nrows x n_q terms form chunks of 32, and warps take chunks, so that the
+    // lanes of a warp evaluate one basic function
+    int nch = 0, cst[6];
+    for (int q = 0; q < R.nc; ++q) {
+      cst[q] = nch;
+      nch += basic_has_costly(R.sfn[q]) ? (nrows * (R.seg[q + 1] - R.seg[q]) + 31) / 32 : 0;
+    }
+    cst[R.nc] = nch;
+    for (int ch = warp; ch < nch; ch += nwarps) {
       int q = 0;
-      while (q + 1 < R.nc && j >= R.seg[q + 1]) ++q;
-      const int fn = R.sfn[q];
-      if (!basic_has_costly(fn)) continue;
-      const int b0 = R.seg[q], n = R.seg[q + 1] - b0, l = j - b0;
+      while (ch >= cst[q + 1]) ++q;
+      const int b0 = R.seg[q], n = R.seg[q + 1] - b0;
+      const int k = (ch - cst[q]) * 32 + lane;
+      if (k >= nrows * n) continue;
+      const int r = k / n, l = k - r * n;
+      const double* zr = Z + r * dp;
       const double sc = R.sscale[q];
-      Y[e] = basic_costly(fn, sc * zr[R.perm[j]], sc * zr[R.perm[b0 + (l + 1 < n ? l + 1 : 0)]], l, n);
-    } else if (basic_has_costly(R.obj)) {
-      Y[e] = basic_costly(R.obj, zr[j], zr[j + 1 < d ? j + 1 : 0], j, d);
+      Y[r * dp + b0 + l] =
+          basic_costly(R.sfn[q], sc * zr[R.perm[b0 + l]], sc * zr[R.perm[b0 + (l + 1 < n ? l + 1 : 0)]], l, n, R.skex[q]);
+    }
+  } else if (basic_has_costly(R.obj)) {
+    for (int e = threadIdx.x; e < nrows * dp; e += blockDim.x) {
+      const int r = e / dp, j = e - r * dp;
+      if (j >= d) continue;
+      const double* zr = Z + r * dp;
+      Y[e] = basic_costly(R.obj, zr[j], zr[j + 1 < d ? j + 1 : 0], j, d, R.skex[0]);
     }
   }
   __syncthreads();
