@@ -345,7 +345,9 @@ __global__ void __launch_bounds__(256, 1)
         mma_commit(bar_mma);
       }
       __syncthreads();
-      const bool have = mbar_wait(bar_mma, (uint32_t)(itg & 1));
+      // every thread's bounded wait must have seen the products complete;
+      // otherwise no row is delivered and every target goes to the FP64 band
+      const bool have = __syncthreads_and(mbar_wait(bar_mma, (uint32_t)(itg & 1)) ? 1 : 0) != 0;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int m = 32 * (warp & 3) + lane;
       const int half = R.ntn / 2;
