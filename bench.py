@@ -648,9 +648,9 @@ def run_workload(args, capi, torch, rank, world):
 
 # DRAM traffic of one launch of the dominant kernel, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a 200-generation launch of
-# the BF16x3 persistent kernel on this workload (173,568 + 1,852,416 bytes),
+# the BF16x3 persistent kernel on this workload (205,312 + 1,778,944 bytes),
 # scaled to a launch of 3000 generations (traffic grows with generations)
-TRAFFIC_PER_LAUNCH = {("k_persist", 3000): (173568 + 1852416) * 3000 // 200}
+TRAFFIC_PER_LAUNCH = {("k_persist", 3000): (205312 + 1778944) * 3000 // 200}
 
 
 if __name__ == "__main__":
