@@ -406,10 +406,12 @@ void or_step_ex(int np, int d, double F, double CR, double lo, double hi,
     /* evaluate the trial population (Sec. 7.3.1) */
     or_eval_p(obj, d, o, M, scale, perm, trial, d, np, ft, sa, threads);
 
-    /* greedy selection: the trial replaces the target when it is no worse
-       (ties go to the trial); a NaN trial never replaces */
+    /* greedy selection (Sec. 2, Selection): the trial replaces the target
+       when it is no worse (ties go to the trial).  A NaN objective value has
+       no quality and ranks below every number: a NaN trial never replaces,
+       and any other trial replaces a NaN target. */
     for (int i = 0; i < np; ++i) {
-        int acc = ft[i] <= fX[i];
+        int acc = !isnan(ft[i]) && (isnan(fX[i]) || ft[i] <= fX[i]);
         if (accept_out) accept_out[i] = (uint8_t)acc;
         if (ftrial_out) ftrial_out[i] = ft[i];
         if (sabs_out) sabs_out[i] = sa[i];

@@ -362,6 +362,32 @@ def test_step_selection():
     assert np.array_equal(fo, r["f_trial"])
 
 
+def test_step_selection_ranks_nan_last():
+    """NaN fitness has no quality (Sec. 2, Selection, read with NaN below
+    every number): a NaN trial never replaces its target, and every other
+    trial, +inf included, replaces a NaN target.  Unrotated Rastrigin with
+    o = 0 and scale 1e308 on coordinates in {0, +-100}: y is 0 or +-inf, so f
+    is 0 (all coordinates 0) or NaN; +inf comes from scale 1e154."""
+    rng = np.random.default_rng(3)
+    X = rng.choice([0.0, 100.0, -100.0], size=(64, 2))
+    o = np.zeros(2)
+    f, _ = oracle.evaluate(1, X, o, None, scale=1e308)
+    assert np.isnan(f).any() and (f == 0).any()
+    for g in range(1, 6):
+        r = oracle.step(X, f, 0.5, 0.9, -100, 100, 1, o, None, seed=7, generation=g, scale=1e308)
+        nt, nx = np.isnan(r["f_trial"]), np.isnan(f)
+        want = ~nt & (nx | (r["f_trial"] <= f))
+        assert np.array_equal(r["accept"].astype(bool), want)
+        assert (~nt & nx).any() or g > 1  # the rule that NaN targets are replaced is exercised
+        X, f = r["X_next"], r["f_next"]
+    # +inf against NaN: with scale 1e154 a coordinate of 100 gives z^2 = 1e312 = +inf
+    # and cos(2 pi 1e156) finite, so f = +inf, while the target keeps f = NaN
+    Xi = np.full((8, 1), 100.0)
+    fi = np.full(8, np.nan)
+    r = oracle.step(Xi, fi, 0.5, 0.9, -100, 100, 1, np.zeros(1), None, seed=1, generation=1, scale=1e154)
+    assert np.all(np.isposinf(r["f_trial"])) and r["accept"].all()
+
+
 def test_step_deterministic_and_seeded():
     X, f, o, M = _pop(32, 5, 15)
     a = oracle.step(X, f, 0.5, 0.9, -100, 100, 1, o, M, seed=6, generation=1)
