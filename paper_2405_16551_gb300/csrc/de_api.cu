@@ -55,6 +55,14 @@ struct de_handle {
   IslandStage stage{};
   void* isl_mem = nullptr;
   IslandCtl isl{};
+  // failure-detection test (DE_GB300_TEST_GRID_TIMEOUT=k at de_init): CTA
+  // k - 1 of every cooperative FP64 launch leaves out its first grid-barrier
+  // arrival, and the barrier gives up after a few thousand polls
+  int test_grid_skip = 0;
+  // per run: a hash of the problem (objective, F, CR, bounds, scale, seed,
+  // run_id, precision, strategy, jDE, FP64 band policy, shift, rotation and
+  // permutation), written to checkpoints and checked by de_load
+  std::vector<uint64_t> fingerprint;
   std::string err;
 };
 
@@ -315,7 +323,7 @@ static de_status enqueue_generations(de_handle* h, int64_t n) {
                                              h->suite, h->d_ctl64, g, h->stream));
       else
         DE_CUDA(h, k_gen_fp64_persist_launch(h->d_run, h->d_items, h->nitems, h->nruns, h->threads, h->smem_gen,
-                                             h->variants, h->suite, h->d_ctl64, g, h->stream));
+                                             h->variants, h->suite, h->d_ctl64, g, h->stream, h->test_grid_skip));
     }
     return DE_OK;
   }
@@ -780,6 +788,35 @@ de_status de_destroy(de_handle* h) {
   return DE_OK;
 }
 
+// 64-bit FNV-1a over 8-byte words (the problem data can be 4096^2 doubles).
+static uint64_t fnv_words(uint64_t h, const void* data, size_t bytes) {
+  const uint8_t* p = (const uint8_t*)data;
+  for (size_t i = 0; i < bytes; i += 8) {
+    uint64_t w = 0;
+    memcpy(&w, p + i, std::min<size_t>(8, bytes - i));
+    h = (h ^ w) * 0x100000001B3ull;
+  }
+  return h;
+}
+
+// Identity of a run's problem for checkpoints: everything that fixes its
+// trajectory except the stopping limits (a resumed run may get a new budget).
+static uint64_t problem_fingerprint(const de_config& c) {
+  uint64_t h = 0xCBF29CE484222325ull;
+  const int32_t ints[8] = {c.np, c.d, c.objective, c.precision, c.strategy, c.jde ? 1 : 0, c.fp64_band,
+                           (int32_t)c.run_id};
+  const double reals[6] = {c.f, c.cr, c.lo, c.hi, c.scale, 0.0};
+  h = fnv_words(h, ints, sizeof ints);
+  h = fnv_words(h, reals, sizeof reals);
+  h = fnv_words(h, &c.seed, sizeof c.seed);
+  const int pairs = (c.objective >= DE_OBJ_SPHERE && c.objective <= DE_OBJ_COMPOSITION3) ? suite_pairs(c.objective) : 1;
+  const uint64_t none = 0x9E3779B97F4A7C15ull;
+  h = c.shift ? fnv_words(h, c.shift, (size_t)pairs * c.d * sizeof(double)) : fnv_words(h, &none, 8);
+  h = c.rot ? fnv_words(h, c.rot, (size_t)pairs * c.d * c.d * sizeof(double)) : fnv_words(h, &none, 8);
+  h = c.perm ? fnv_words(h, c.perm, (size_t)c.d * sizeof(int32_t)) : fnv_words(h, &none, 8);
+  return h;
+}
+
 de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream, de_handle** out) {
   g_err.clear();
   if (!out) return fail(nullptr, DE_ERR_INVALID_ARG, "out is NULL");
@@ -814,6 +851,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     h->suite = h->suite || cfgs[r].objective >= DE_OBJ_ZAKHAROV;
   }
   h->cfg.assign(cfgs, cfgs + nruns);
+  for (int r = 0; r < nruns; ++r) h->fingerprint.push_back(problem_fingerprint(cfgs[r]));
   for (auto& c : h->cfg) {
     c.shift = nullptr;
     c.rot = nullptr;
@@ -1046,6 +1084,9 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     }
     if (h->fp64_cluster && !fp64_cluster_ok(h)) h->fp64_cluster = false;
     if (h->fp64_persist && !fp64_persist_ok(h)) h->fp64_persist = h->fp64_cluster = false;
+    // the failure-detection test applies to the generations after set-up
+    // (not to the autotuner's timing launches)
+    if (const char* v = getenv("DE_GB300_TEST_GRID_TIMEOUT")) h->test_grid_skip = std::max(0, atoi(v));
     for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
   } else if (h->prec != DE_PREC_FP64) {
     if (h->tc.persist.ok) TRY(autotune_persist(h));
@@ -1463,6 +1504,7 @@ de_status de_save(de_handle* h, const char* path) {
     const int cur = cur_buf(h, h->h_state[r].gen);
     int32_t shape[5] = {R.np, R.d, R.prec, R.strategy, R.jde};
     put(shape, sizeof shape);
+    put(&h->fingerprint[r], sizeof(uint64_t));
     put(&h->h_state[r], sizeof(RunState));
     std::vector<double> x((size_t)R.np * R.dp), f(R.np);
     std::vector<uint8_t> fx(R.np);
@@ -1489,7 +1531,7 @@ de_status de_save(de_handle* h, const char* path) {
   }
   CkptHeader hd{};
   memcpy(hd.magic, "DEGB300", 8);
-  hd.version = 3;
+  hd.version = 4;
   hd.nruns = h->nruns;
   hd.payload_bytes = payload.size();
   hd.crc = crc32_update(0, payload.data(), payload.size());
@@ -1509,7 +1551,7 @@ de_status de_load(de_handle* h, const char* path) {
   if (!fp) return fail(h, DE_ERR_IO, std::string("cannot open ") + path);
   CkptHeader hd{};
   std::vector<char> payload;
-  bool ok = fread(&hd, sizeof hd, 1, fp) == 1 && memcmp(hd.magic, "DEGB300", 8) == 0 && hd.version == 3 &&
+  bool ok = fread(&hd, sizeof hd, 1, fp) == 1 && memcmp(hd.magic, "DEGB300", 8) == 0 && hd.version == 4 &&
             hd.payload_bytes < (1ull << 40);
   if (ok) {
     payload.resize(hd.payload_bytes);
@@ -1526,44 +1568,64 @@ de_status de_load(de_handle* h, const char* path) {
     off += n;
     return true;
   };
+  // every run is parsed and checked on the host before anything reaches the
+  // device, so that a rejected file leaves the handle as it was
+  struct RunCkpt {
+    RunState st;
+    std::vector<double> x, f, adapt;
+    std::vector<uint8_t> fx;
+    std::vector<float> tau;
+  };
+  std::vector<RunCkpt> rc(h->nruns);
   for (int r = 0; r < h->nruns; ++r) {
     const RunDesc& R = h->run[r];
+    RunCkpt& c = rc[r];
     int32_t shape[5];
-    RunState st;
-    if (!get(shape, sizeof shape) || !get(&st, sizeof st)) return fail(h, DE_ERR_IO, "checkpoint truncated");
-    if (shape[0] != R.np || shape[1] != R.d || shape[2] != R.prec || shape[3] != R.strategy || shape[4] != R.jde)
-      return fail(h, DE_ERR_STATE, "checkpoint shape differs from the handle's");
-    std::vector<double> x((size_t)R.np * R.dp), f(R.np);
-    std::vector<uint8_t> fx(R.np);
-    if (!get(x.data(), x.size() * sizeof(double)) || !get(f.data(), f.size() * sizeof(double)) ||
-        !get(fx.data(), fx.size()))
+    uint64_t fp = 0;
+    if (!get(shape, sizeof shape) || !get(&fp, sizeof fp) || !get(&c.st, sizeof c.st))
       return fail(h, DE_ERR_IO, "checkpoint truncated");
-    std::vector<float> tau;
+    if (shape[0] != R.np || shape[1] != R.d || shape[2] != R.prec || shape[3] != R.strategy || shape[4] != R.jde)
+      return fail(h, DE_ERR_STATE, "checkpoint shape of run " + std::to_string(r) + " differs from the handle's");
+    if (fp != h->fingerprint[r])
+      return fail(h, DE_ERR_STATE, "checkpoint of run " + std::to_string(r) +
+                                       " was written for another problem (objective, F, CR, bounds, seed, shift or "
+                                       "rotation differ)");
+    c.x.resize((size_t)R.np * R.dp);
+    c.f.resize(R.np);
+    c.fx.resize(R.np);
+    if (!get(c.x.data(), c.x.size() * sizeof(double)) || !get(c.f.data(), c.f.size() * sizeof(double)) ||
+        !get(c.fx.data(), c.fx.size()))
+      return fail(h, DE_ERR_IO, "checkpoint truncated");
     if (R.tau) {
-      tau.resize(R.np);
-      if (!get(tau.data(), tau.size() * sizeof(float))) return fail(h, DE_ERR_IO, "checkpoint truncated");
-      DE_CUDA(h, cudaMemcpyAsync(R.tau, tau.data(), tau.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+      c.tau.resize(R.np);
+      if (!get(c.tau.data(), c.tau.size() * sizeof(float))) return fail(h, DE_ERR_IO, "checkpoint truncated");
     }
-    std::vector<double> adapt;
     if (R.jde) {
-      adapt.resize(2 * (size_t)R.np);
-      if (!get(adapt.data(), adapt.size() * sizeof(double))) return fail(h, DE_ERR_IO, "checkpoint truncated");
+      c.adapt.resize(2 * (size_t)R.np);
+      if (!get(c.adapt.data(), c.adapt.size() * sizeof(double))) return fail(h, DE_ERR_IO, "checkpoint truncated");
     }
-    const int cur = cur_buf(h, st.gen);
+  }
+  if (off != payload.size()) return fail(h, DE_ERR_IO, "checkpoint has trailing bytes");
+  for (int r = 0; r < h->nruns; ++r) {
+    const RunDesc& R = h->run[r];
+    RunCkpt& c = rc[r];
+    const int cur = cur_buf(h, c.st.gen);
+    if (R.tau)
+      DE_CUDA(h, cudaMemcpyAsync(R.tau, c.tau.data(), c.tau.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     if (R.jde) {
-      DE_CUDA(h, cudaMemcpyAsync(R.jF[cur], adapt.data(), R.np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-      DE_CUDA(h, cudaMemcpyAsync(R.jCR[cur], adapt.data() + R.np, R.np * sizeof(double), cudaMemcpyHostToDevice,
+      DE_CUDA(h, cudaMemcpyAsync(R.jF[cur], c.adapt.data(), R.np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      DE_CUDA(h, cudaMemcpyAsync(R.jCR[cur], c.adapt.data() + R.np, R.np * sizeof(double), cudaMemcpyHostToDevice,
                                  h->stream));
     }
-    st.ticket = 0;
-    st.band_n = 0;
-    st.band_left = 0;
-    DE_CUDA(h, cudaMemcpyAsync(R.X[cur], x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    DE_CUDA(h, cudaMemcpyAsync(R.f[cur], f.data(), f.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    DE_CUDA(h, cudaMemcpyAsync(R.fx[cur], fx.data(), fx.size(), cudaMemcpyHostToDevice, h->stream));
-    DE_CUDA(h, cudaMemcpyAsync(R.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
-    DE_CUDA(h, cudaStreamSynchronize(h->stream));
+    c.st.ticket = 0;
+    c.st.band_n = 0;
+    c.st.band_left = 0;
+    DE_CUDA(h, cudaMemcpyAsync(R.X[cur], c.x.data(), c.x.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(R.f[cur], c.f.data(), c.f.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(R.fx[cur], c.fx.data(), c.fx.size(), cudaMemcpyHostToDevice, h->stream));
+    DE_CUDA(h, cudaMemcpyAsync(R.st, &c.st, sizeof c.st, cudaMemcpyHostToDevice, h->stream));
   }
+  DE_CUDA(h, cudaStreamSynchronize(h->stream));
   const de_status s = islands_resync(h);
   if (s != DE_OK) return s;
   DE_CUDA(h, cudaStreamSynchronize(h->stream));

@@ -473,6 +473,10 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
   if (nruns == 1 && s_stop) return;
   unsigned nstopped = 0;  // runs known stopped (thread 0)
+  // the failure-detection test (off in normal launches): this CTA may leave
+  // out its first arrival, and the barrier may give up sooner
+  const bool test_skip = ctl->test_skip == (int)blockIdx.x + 1;
+  const long long spin_limit = ctl->test_spin > 0 ? ctl->test_spin : kFp64Spin;
   for (long long itg = 0; itg < gens; ++itg) {
     const bool live = !s_stop;
     const int64_t g = s_gen + 1;
@@ -493,14 +497,14 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
     } else if (warp == 0) {
       // arrive, then wait for every CTA of this iteration; the whole warp
       // polls the counter (one load per poll, no divergent spin)
-      if (lane == 0) {
+      if (lane == 0 && !(test_skip && itg == 0)) {
         __threadfence();
         atomicAdd(&ctl->bar, 1u);
       }
       __syncwarp();
       const unsigned target = (unsigned)(itg + 1) * nct;
       bool ok = false;
-      for (long long k = 0; k < kFp64Spin; ++k) {
+      for (long long k = 0; k < spin_limit; ++k) {
         unsigned v;
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->bar) : "memory");
         if (v >= target) {
@@ -593,9 +597,18 @@ void k_configure(size_t smem_gen) {
 
 cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int nruns, int threads,
                                       size_t smem, bool var, bool suite, PersistCtl* ctl, long long gens,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, int test_skip) {
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
   if (e != cudaSuccess) return e;
+  if (test_skip > 0) {
+    // about 4096 polls instead of 2^22: the test's wait runs out in milliseconds
+    const int skip = test_skip;
+    const long long spin = 4096;
+    e = cudaMemcpyAsync(&ctl->test_skip, &skip, sizeof skip, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl->test_spin, &spin, sizeof spin, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // skip and spin live on this stack frame
+    if (e != cudaSuccess) return e;
+  }
   int clustered = 0;
   void* args[] = {(void*)&runs, (void*)&items, (void*)&nruns, (void*)&ctl, (void*)&gens, (void*)&clustered};
   const dim3 grid((unsigned)nitems), block((unsigned)threads);

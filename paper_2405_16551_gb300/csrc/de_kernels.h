@@ -18,6 +18,11 @@ struct PersistCtl {
   int abort;         // set when a bounded wait expired
   long long gen0;    // generation counter when the launch began
   unsigned int stopped[3];  // runs stopped per iteration mod 3 (batched FP64 launch)
+  // failure-detection test of the cooperative FP64 kernel (0 = off): CTA
+  // test_skip - 1 leaves out its first grid-barrier arrival, and the barrier
+  // gives up after test_spin polls, so that the bounded wait runs out
+  int test_skip;
+  long long test_spin;
 };
 // FP64 path (de_fp64.cu)
 void k_configure(size_t smem_gen);
@@ -27,9 +32,10 @@ void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int t
                        bool suite, cudaStream_t s);
 // the generation loop of FP64 runs in one cooperative launch (every item
 // co-resident: nitems <= k_gen_fp64_persist_capacity; gens <= 2^20)
+// test_skip > 0: the grid-barrier failure test (PersistCtl::test_skip)
 cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int nruns, int threads,
                                       size_t smem, bool var, bool suite, PersistCtl* ctl, long long gens,
-                                      cudaStream_t s);
+                                      cudaStream_t s, int test_skip = 0);
 int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite);
 // the same loop as one thread-block cluster of nitems CTAs (one run,
 // nitems <= 8), the cluster barrier between generations

@@ -113,6 +113,23 @@ __global__ void k_noalloc_pack_b(const double* __restrict__ M, int d, int ntn, i
   }
 }
 
+// Bytes one call needs for d (one 128-row tile), by the geometry rules below.
+static size_t na_one_tile_bytes(int d, int esz) {
+  const int kpad = (int)na_up(d, 16);
+  const int ntn = d <= 256 ? kpad : 256;
+  const int nn = (d + ntn - 1) / ntn;
+  const size_t a_tile = (size_t)2 * kTileM * kpad * esz, b_tile = (size_t)2 * ntn * kpad * esz;
+  return na_layout(1, (d + 3) / 4 * 4, nn * b_tile, a_tile).total;
+}
+
+// Largest d whose split copy of M and one operand tile fit the scratch
+// (1920 for BF16X3, 1280 for TF32X3); the need grows with d.
+static int na_max_d(int esz) {
+  int d = 4096;
+  while (d > 1 && na_one_tile_bytes(d, esz) > kNoallocScratch) --d;
+  return d;
+}
+
 static std::mutex g_na_mu;
 static uint8_t* g_na_base[kNoallocMaxDevices];
 
@@ -165,6 +182,11 @@ de_status noalloc_eval(int prec, int obj, int d, double scale, const double* o, 
 
   const size_t tiles = ((size_t)n + kTileM - 1) / kTileM;
   const NaLayout L = na_layout(tiles, dp, nn * b_tile, a_tile);
+  if (na_layout(1, dp, nn * b_tile, a_tile).total > kNoallocScratch) {
+    err = "de_eval_noalloc: d = " + std::to_string(d) + " does not fit the 16 MiB static scratch even for one " +
+          "128-row tile; the largest d is " + std::to_string(na_max_d(esz)) + (esz == 2 ? " in BF16X3" : " in TF32X3");
+    return DE_ERR_INVALID_ARG;
+  }
   if (L.total > kNoallocScratch) {
     size_t tmax = std::min(tiles, kNoallocScratch / a_tile + 1);
     while (tmax > 0 && na_layout(tmax, dp, nn * b_tile, a_tile).total > kNoallocScratch) --tmax;

@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(256, 1)
           const bool near = fs - tau <= R.near_thr || fif - tif <= R.near_thr;
           const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f;
           l_ft[lr] = (double)fs;
-          if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !have) {
+          if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !(fif == fif) || !have) {
             l_blist[atomicAdd(l_nb, 1)] = lr;
             flag = 4;
           } else if (sure_accept || (ambiguous && fs <= fif)) {

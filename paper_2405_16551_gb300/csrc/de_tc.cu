@@ -387,13 +387,16 @@ __global__ void __launch_bounds__(kFitThreads, 1)
     __syncthreads();
   }
 
-  // ---- error path: wait (bounded) for outstanding copies and MMAs
+  // ---- error path: wait (bounded) for outstanding copies and MMAs; in
+  // evaluation mode the tile's outputs become NaN, so that a caller who
+  // cannot read the run state still sees that these rows were not evaluated
   if (s_err) {
     if (tid == 0) {
       atomicOr(&st->err, kErrTimeout);
       for (int k = 0; k < loads_issued; ++k) mbar_wait(full_bar(k % S), (uint32_t)((k / S) & 1));
       for (int k = 0; k < mmas_committed; ++k) mbar_wait(done_bar(k % S), (uint32_t)((k / S) & 1));
     }
+    if (mode == 1 && tid < nrows) fout[row0 + tid] = __longlong_as_double(0x7FF8000000000000LL);
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
     return;
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(kFitThreads, 1)
       const bool near = fs - tau <= R.near_thr || fif - tif <= R.near_thr;
       const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f;
       s_ftrial[m] = (double)fs;
-      if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs)) {
+      if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !(fif == fif)) {
         // the split values cannot decide (or the trial may become the best):
         // FP64 decision in k_band_fp64
         const uint32_t e = atomicAdd(R.band_cnt, 1u);
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(256) k_band_fp64(const RunDesc* __restrict__ r
         if (lane == 0) {
           const double ft = f2[0];
           const double fi = be.need_target ? f2[1] : R.f[0][i];
-          const bool acc = ft <= fi;  // false for a NaN trial
+          const bool acc = fit_key(ft) <= fit_key(fi) && fit_key(ft) != 0x7FFFFFFFFFFFFFFFLL;  // NaN ranks last
           R.f[0][i] = acc ? ft : fi;
           R.fx[0][i] = 1;
           R.tau[i] = 0.f;
