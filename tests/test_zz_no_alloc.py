@@ -108,6 +108,70 @@ def test_noalloc_size_limit(prec):
         capi.de_destroy(h)
 
 
+# largest n per call at d = 1000 (4 N tiles of M) and largest d per precision
+# for the 16 MiB scratch (stated in de.h)
+MAX_ROWS_D1000 = {capi.DE_PREC_BF16X3: 3072, capi.DE_PREC_TF32X3: 1024}
+MAX_D = {capi.DE_PREC_BF16X3: 1920, capi.DE_PREC_TF32X3: 1280}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_noalloc_d1000_at_the_row_limit_two_calls(prec):
+    """d = 1000: M spans four 256-wide N tiles, which the kernel loops over.
+    The first call takes the largest n that fits, the second a ragged n;
+    both equal de_eval bit for bit."""
+    torch = _need_gpu()
+    d, obj = 1000, 1
+    o, M = problems.shift(d, seed=12), problems.rotation(d, seed=12)
+    cfg = capi.make_config(64, d, objective=obj, shift=o, rot=M, precision=prec, max_generations=1)
+    h = capi.de_init(cfg)
+    try:
+        od = torch.from_numpy(o).cuda()
+        Md = torch.from_numpy(np.ascontiguousarray(M)).cuda()
+        nmax = MAX_ROWS_D1000[prec]
+        for call, (n, seed) in enumerate([(nmax, 13), (nmax - 77, 14)]):
+            X = problems.population(n, d, seed=seed)
+            X[:8] = o + np.random.default_rng(seed).normal(size=(8, d)) * 1e-3
+            f_ref, f_na = _both(torch, h, prec, obj, d, 1.0, od, Md, X, ld=d)
+            assert np.array_equal(f_ref, f_na), f"call {call}"
+            fo, sabs = oracle.evaluate(obj, X[:64], o, M)
+            err = np.abs(f_na[:64] - fo) / (np.abs(fo) + sabs)
+            assert err.max() <= REL_SPLIT[prec], (call, err.max())
+        # one row more than fits is rejected
+        X = torch.zeros((nmax + 1, d), dtype=torch.float64, device="cuda")
+        f = torch.zeros(nmax + 1, dtype=torch.float64, device="cuda")
+        with pytest.raises(capi.DEError) as ei:
+            capi.de_eval_noalloc(prec, obj, d, 1.0, od.data_ptr(), Md.data_ptr(), X.data_ptr(), d, nmax + 1,
+                                 f.data_ptr())
+        assert ei.value.status == capi.DE_ERR_INVALID_ARG and f"at most {nmax} rows" in str(ei.value)
+    finally:
+        capi.de_destroy(h)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_noalloc_largest_d(prec):
+    """The largest d whose split M fits the scratch is accepted (one tile,
+    equal to de_eval); one more is rejected with the limit in the message."""
+    torch = _need_gpu()
+    d, obj, n = MAX_D[prec], 0, 128
+    o, M = problems.shift(d, seed=15), problems.rotation(d, seed=15)
+    od = torch.from_numpy(o).cuda()
+    Md = torch.from_numpy(np.ascontiguousarray(M)).cuda()
+    h = capi.de_init(capi.make_config(8, d, objective=obj, shift=o, rot=M, precision=prec, max_generations=1))
+    try:
+        X = problems.population(n, d, seed=16)
+        f_ref, f_na = _both(torch, h, prec, obj, d, 1.0, od, Md, X, ld=d)
+        assert np.array_equal(f_ref, f_na)
+    finally:
+        capi.de_destroy(h)
+    d1 = d + 1
+    X = torch.zeros((4, d1), dtype=torch.float64, device="cuda")
+    f = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(capi.DEError) as ei:
+        capi.de_eval_noalloc(prec, obj, d1, 1.0, None, None, X.data_ptr(), d1, 4, f.data_ptr())
+    assert ei.value.status == capi.DE_ERR_INVALID_ARG
+    assert f"the largest d is {d}" in str(ei.value)
+
+
 def test_noalloc_allocates_nothing():
     """After the first call (one-time set-up), a call leaves the device's free
     memory unchanged."""
