@@ -195,7 +195,7 @@ DTYPE = {"fp64": "f64", "bf16x3": "bf16x3 products, f32 accumulate, f64 trials a
 
 # de_get_plan's kernel paths
 KERNEL_PATH_NAMES = {0: "fp64 fused", 1: "split three-kernel", 2: "split persistent cluster",
-                     3: "fp64 cooperative persistent"}
+                     3: "fp64 cooperative persistent", 4: "split persistent, CTA-local products (cooperative)"}
 
 
 def launches_per_step(plan, G):
@@ -208,7 +208,7 @@ def launches_per_step(plan, G):
         return 3 + 3 * G      # trial, tensor-core fitness, FP64 band per generation
     if path == 3:
         return 3 + 1          # one cooperative FP64 kernel for all generations
-    return 3 + 2              # one persistent kernel for all generations, then its close-out kernel
+    return 3 + 2              # one persistent split kernel (path 2 or 4) for all generations, then its close-out
 
 
 def measure(capi, torch, prec_name, G, steps, warmup, rank, flush, stream):
@@ -359,13 +359,15 @@ def main():
         # algorithmic bytes per trial: read the target row, write the next
         # generation's row, fitness in and out
         byts = NP * (2 * 8 * D + 16)
-        per_launch = byts * G if path == 2 else byts
-        launch_us = avg_gen_us * G if path == 2 else avg_gen_us
+        persistent = path in (2, 4)
+        kname = {2: "k_persist", 4: "k_persist_cta"}.get(path, "k_trial_split + k_fit_tc + k_band_fp64")
+        per_launch = byts * G if persistent else byts
+        launch_us = avg_gen_us * G if persistent else avg_gen_us
         achieved = per_launch / (launch_us * 1e-6) / 1e9
         pk = float(peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": "hbm", "kernel": "k_persist" if path == 2 else "k_trial_split + k_fit_tc + k_band_fp64",
+        roof = {"bound": "hbm", "kernel": kname,
                 "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
-                "traffic": TRAFFIC_PER_LAUNCH.get(("k_persist", G)) if path == 2 else None,
+                "traffic": TRAFFIC_PER_LAUNCH.get((kname, G)) if persistent else None,
                 "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": launch_us,
                 "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
                                 else "fallback 6.8 TB/s (of fallback)"),

@@ -683,29 +683,51 @@ static de_status autotune_split(de_handle* h) {
   return s;
 }
 
-// Rows per cluster of the persistent cluster kernel: fewer rows give each
-// CTA fewer trials to build but put more clusters at the grid barrier.  Timed
-// on the handle's own problem from 128 rows down (multiples of the cluster
-// size, every tile resident), cached like the other choices; it never changes
-// results.  DE_GB300_PERSIST_ROWS fixes the value instead.
+// The persistent split-precision form and its tile: the cluster kernel with
+// rows per cluster timed from 128 down (multiples of the cluster size), and
+// the CTA-local kernel with targets per CTA timed from the fewest that keep
+// every CTA resident up to 16.  Both are timed on the handle's own problem and
+// the faster is cached like the other choices (value: 1000 x form + rows); the
+// choice never changes results.  DE_GB300_PERSIST_ROWS /
+// DE_GB300_PERSIST_CTA_ROWS fix the tile instead.
 static std::string tune_key_persist(const de_handle* h) {
   const RunDesc& R = h->run[0];
   char b[256];
-  snprintf(b, sizeof b, "persist_v1 prec=%d np=%d d=%d obj=%d rot=%d var=%d", h->prec, R.np, R.d, R.obj, R.rotate,
-           h->tc.persist.var ? 1 : 0);
+  snprintf(b, sizeof b, "persist_v2 prec=%d np=%d d=%d obj=%d rot=%d var=%d cl=%d cta=%d", h->prec, R.np, R.d, R.obj,
+           R.rotate, h->tc.persist.var ? 1 : 0, h->tc.persist.cl_ok ? 1 : 0, h->tc.persist.cta_ok ? 1 : 0);
   return b;
+}
+
+static bool persist_choose(PersistPlan& pp, const RunDesc& R, int mode, int rows) {
+  if (mode == 1) {
+    if (!pp.cta_ok || !persist_cta_set_rows(pp, R, rows)) return false;
+  } else {
+    if (!pp.cl_ok || !persist_set_rows(pp, R, rows)) return false;
+  }
+  pp.mode = mode;
+  return true;
 }
 
 static de_status autotune_persist(de_handle* h) {
   const char* env = getenv("DE_GB300_AUTOTUNE");
   PersistPlan& pp = h->tc.persist;
-  if ((env && env[0] == '0') || !pp.ok || getenv("DE_GB300_PERSIST_ROWS")) return DE_OK;
+  if ((env && env[0] == '0') || !pp.ok || getenv("DE_GB300_PERSIST_ROWS") || getenv("DE_GB300_PERSIST_CTA_ROWS"))
+    return DE_OK;
   const std::string key = tune_key_persist(h);
   int cached = 0;
-  if (tune_lookup(key, cached)) {
-    persist_set_rows(pp, h->run[0], cached);
-    return DE_OK;
+  if (tune_lookup(key, cached) && persist_choose(pp, h->run[0], cached / 1000, cached % 1000)) return DE_OK;
+  // candidates: (form, rows)
+  std::vector<std::pair<int, int>> cand;
+  if (pp.cl_ok)
+    for (int rows = pp.prows; rows >= pp.C; rows -= pp.C) cand.push_back({0, rows});
+  if (pp.cta_ok) {
+    const int first = pp.cta_rows;
+    for (int rows : {first, first + 1, first + 2, 8, 10, 12, 16})
+      if (rows >= first && rows <= 16 &&
+          std::find(cand.begin(), cand.end(), std::make_pair(1, rows)) == cand.end())
+        cand.push_back({1, rows});
   }
+  const PersistPlan keep = pp;
   cudaEvent_t e0, e1;
   DE_CUDA(h, cudaEventCreate(&e0));
   DE_CUDA(h, cudaEventCreate(&e1));
@@ -716,11 +738,11 @@ static de_status autotune_persist(de_handle* h) {
     R.max_gens = INT64_MAX / 4;
   }
   de_status st_all = upload_desc(h);
-  const int first = pp.prows;
   float best_ms = 1e30f;
-  int best = first;
-  for (int rows = first; rows >= pp.C && st_all == DE_OK; rows -= pp.C) {
-    if (!persist_set_rows(pp, h->run[0], rows)) continue;
+  std::pair<int, int> best = {keep.mode, keep.mode == 1 ? keep.cta_rows : keep.prows};
+  for (const auto& c : cand) {
+    if (st_all != DE_OK) break;
+    if (!persist_choose(pp, h->run[0], c.first, c.second)) continue;
     int32_t zero = 0;
     DE_CUDA(h, cudaMemcpyAsync(&h->run[0].st->stop, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream));
     st_all = enqueue_generations(h, 4);
@@ -736,16 +758,17 @@ static de_status autotune_persist(de_handle* h) {
     }
     if (st_all == DE_OK && ms < best_ms * 0.98f) {
       best_ms = ms;
-      best = rows;
+      best = c;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->run = saved;
-  persist_set_rows(pp, h->run[0], best);
+  pp = keep;
+  persist_choose(pp, h->run[0], best.first, best.second);
   if (st_all != DE_OK) return st_all;
   const de_status s = upload_desc(h);
-  if (s == DE_OK) tune_store(key, best);
+  if (s == DE_OK) tune_store(key, 1000 * best.first + best.second);
   return s;
 }
 
@@ -1448,9 +1471,12 @@ de_status de_get_surrogate_stats(de_handle* h, int64_t* trainings, int64_t* scre
 de_status de_get_plan(de_handle* h, int32_t* kernel_path, int32_t* cluster_size) {
   if (!h) return fail(nullptr, DE_ERR_INVALID_ARG, "handle is NULL");
   const bool persist = h->prec != DE_PREC_FP64 && h->tc.persist.ok;
-  if (kernel_path) *kernel_path = h->prec == DE_PREC_FP64 ? (h->fp64_persist ? 3 : 0) : (persist ? 2 : 1);
+  if (kernel_path)
+    *kernel_path = h->prec == DE_PREC_FP64 ? (h->fp64_persist ? 3 : 0)
+                                           : (persist ? (h->tc.persist.mode == 1 ? 4 : 2) : 1);
   if (cluster_size)
-    *cluster_size = persist ? h->tc.persist.C : (h->prec == DE_PREC_FP64 && h->fp64_cluster ? h->nitems : 0);
+    *cluster_size = persist ? (h->tc.persist.mode == 1 ? 0 : h->tc.persist.C)
+                            : (h->prec == DE_PREC_FP64 && h->fp64_cluster ? h->nitems : 0);
   return DE_OK;
 }
 

@@ -75,11 +75,17 @@ void k_island_launch(const RunDesc* runs, IslandCtl* ctl, const IslandStage& sta
 
 // persistent cluster path (de_persist.cu)
 struct PersistPlan {
-  bool ok = false;
+  bool ok = false;   // some persistent form applies (mode says which runs)
+  int mode = 0;      // 0: thread-block clusters (k_persist); 1: CTA-local products (k_persist_cta)
+  bool cl_ok = false;  // the cluster form applies
   int C = 0, ntiles = 0, prec = 0, nch = 1, prows = 128;
   int maxcl = 0;  // clusters that fit on the device at once
   bool var = false;  // the run uses a strategy variant or jDE
   size_t smem = 0;
+  // CTA-local form: targets per CTA, CTAs, resident-CTA capacity, shared memory
+  bool cta_ok = false;
+  int cta_rows = 0, cta_ntiles = 0, cta_cap = 0;
+  size_t cta_smem = 0;
 };
 
 // split-precision tensor-core path (de_tc.cu)
@@ -110,6 +116,14 @@ bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec);
 bool persist_set_rows(PersistPlan& pp, const RunDesc& R, int prows);
 cudaError_t persist_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
                            cudaStream_t s);
+// the CTA-local persistent form (de_persist_cta.cu): one run of at most 128
+// coordinates, at most 16 targets per CTA, every CTA resident
+bool persist_cta_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec);
+bool persist_cta_set_rows(PersistPlan& pp, const RunDesc& R, int rows);
+cudaError_t persist_cta_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
+                               cudaStream_t s);
+// counters after a persistent launch of run 0 (evaluations, trials, tickets)
+void k_persist_close_launch(const RunDesc* runs, const PersistCtl* ctl, cudaStream_t s);
 
 de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* cfgs, int prec, cudaStream_t s,
                         std::string& err);

@@ -37,6 +37,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "de_device.cuh"
 #include "de_kernels.h"
@@ -720,6 +722,10 @@ __global__ void k_persist_close(const RunDesc* __restrict__ runs, int run, const
   st->band_left = 0;
 }
 
+void k_persist_close_launch(const RunDesc* runs, const PersistCtl* ctl, cudaStream_t s) {
+  k_persist_close<<<1, 1, 0, s>>>(runs, 0, ctl);
+}
+
 // ------------------------------------------------------------------ host side
 size_t persist_smem(const RunDesc& R, int C) {
   const size_t lead = (size_t)R.a_tile_bytes + R.b_tile_bytes + (size_t)2 * kPBandMax * R.dp * sizeof(double);
@@ -727,8 +733,24 @@ size_t persist_smem(const RunDesc& R, int C) {
   return std::max(lead, member);
 }
 
+static bool persist_cluster_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec);
+
+// Both persistent forms; the CTA-local one is the first choice where it
+// applies (the autotuner may pick the cluster form instead).  The
+// environment variable DE_GB300_PERSIST_MODE=cluster / cta keeps one form.
 bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
-  pp.ok = false;
+  const char* env = getenv("DE_GB300_PERSIST_MODE");
+  const bool want_cl = !(env && strcmp(env, "cta") == 0), want_cta = !(env && strcmp(env, "cluster") == 0);
+  pp.cl_ok = want_cl && persist_cluster_plan(pp, R, nruns, prec);
+  pp.cta_ok = want_cta && persist_cta_plan(pp, R, nruns, prec);
+  pp.prec = prec;
+  pp.var = R.strategy != 0 || R.jde;
+  pp.mode = pp.cta_ok ? 1 : 0;
+  pp.ok = pp.cl_ok || pp.cta_ok;
+  return pp.ok;
+}
+
+static bool persist_cluster_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
   // one run, one N tile, whole K resident, rows of at most 128 coordinates
   // (the trial and target rows of a warp then stay in registers)
   if (nruns != 1 || R.nn != 1 || R.kc != R.kpad || R.d > 128) return false;
@@ -769,7 +791,6 @@ bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
     if (v >= C && v <= kTileM && v % C == 0) prows = v;
   }
   if (!persist_set_rows(pp, R, prows)) return false;
-  pp.ok = true;
   pp.smem = smem;
   pp.prec = prec;
   pp.nch = 1;
@@ -788,6 +809,7 @@ bool persist_set_rows(PersistPlan& pp, const RunDesc& R, int prows) {
 
 cudaError_t persist_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
                            cudaStream_t s) {
+  if (pp.mode == 1) return persist_cta_launch(pp, runs, ctl, gens, s);
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};

@@ -1,0 +1,691 @@
+// de_persist_cta.cu -- the split-precision generation loop as one cooperative
+// persistent kernel in which every CTA runs the tensor-core products of its
+// own targets.
+//
+// CTA t owns `rows` (at most 16) consecutive targets for the whole launch and
+// keeps the split M (the B operand) resident in shared memory.  One
+// generation:
+//
+//   1. every warp builds the trials of its targets (Eq. 2, Eq. 3, bound
+//      repair; FP64, one target per warp at a time, the same routines as the
+//      other paths), keeps the trial and target rows in registers and writes
+//      the split rows of y = (t - o) s into the CTA's own A operand;
+//   2. one thread issues the three split products on tcgen05 (M = 128, the
+//      whole K resident); A holds 16 rows, and the rows 16..127 the
+//      instruction also reads are other bytes of the CTA's shared memory,
+//      whose products land in tensor-memory lanes nobody reads;
+//   3. warps 0 and 4 (the warps that may read TMEM lanes 0..31) copy the
+//      accumulator rows to shared memory; every target is then evaluated in
+//      FP32 by 16 threads (strided columns, fixed xor tree: the order of the
+//      cluster kernel, so both give the same values) and its selection is
+//      decided where the split error bound allows.  The other targets (and
+//      trials that could stop the run) are re-evaluated in FP64 by the whole
+//      CTA, with M^T read at L2;
+//   4. the CTA writes its next-generation rows to the other population buffer
+//      (double buffering: no CTA overwrites a row another CTA still reads as
+//      a donor), its best partial, and arrives at a grid barrier (bounded
+//      spin on a global counter).  After the barrier every CTA reduces all
+//      partials in the same order, so every CTA takes the same best record
+//      and stop decision (Sec. 7.3.4).
+//
+// There is no cluster and no distributed shared memory: the grid barrier is
+// the only synchronisation between CTAs.  The launch is cooperative, so every
+// CTA is resident.  Every wait is bounded; on expiry the kernel records
+// kErrTimeout, the CTAs agree on an abort through a global flag and leave at
+// the same point of the loop with the population of the last complete
+// generation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "de_device.cuh"
+#include "de_kernels.h"
+#include "de_tcgen05.cuh"
+
+namespace de {
+
+constexpr int kCtaRowsMax = 16;                   // targets per CTA (two A row groups)
+constexpr long long kCtaGridSpin = 1LL << 22;     // polls of the grid barrier (with back-off)
+constexpr uint32_t kCtaAPad = 2048;               // bytes after A that rows 16..127 of the products read
+
+// Bytes of one part (high or low) of the 16-row A operand: k-groups of 16
+// bytes, each holding two 8-row core matrices (k-group stride 256 bytes).
+__host__ __device__ inline uint32_t cta_a_part(const RunDesc& R) { return (uint32_t)(R.kpad * R.esz / 16) * 256u; }
+// Row stride (floats) of the accumulator rows in shared memory.
+__host__ __device__ inline int cta_zstride(const RunDesc& R) { return R.ntn + 4; }
+
+struct CtaLayout {
+  uint32_t a, b, z, y, red, total;
+};
+
+__host__ __device__ inline CtaLayout cta_layout(const RunDesc& R) {
+  CtaLayout L;
+  const uint32_t ap = cta_a_part(R);
+  L.a = 0;
+  L.b = (2u * ap + kCtaAPad + 1023u) / 1024u * 1024u;
+  L.z = L.b + (uint32_t)R.b_tile_bytes;
+  L.y = L.z + (uint32_t)(kCtaRowsMax * cta_zstride(R)) * 4u;  // 16-byte aligned: zstride is a multiple of 4
+  L.y = (L.y + 15u) / 16u * 16u;
+  L.red = L.y + (uint32_t)(2 * R.dp) * 8u;  // FP64 y of a band row's trial and target
+  L.total = L.red + 2u * 256u * 8u;         // FP64 terms of the band evaluation
+  return L;
+}
+
+// y[0..3] (coordinates j0..j0+3 of A row m < 16) as high and low parts.
+template <int ESZ>
+__device__ __forceinline__ void cta_store_split4(uint8_t* A, uint32_t a_part, int m, int j0, const float y[4]) {
+  const int rg = m >> 3, rr = m & 7;
+  if constexpr (ESZ == 2) {
+    __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      hi[q] = __float2bfloat16_rn(y[q]);
+      lo[q] = __float2bfloat16_rn(y[q] - __bfloat162float(hi[q]));  // exact residual, then rounded
+    }
+    const uint32_t off = (uint32_t)(j0 >> 3) * 256u + (uint32_t)rg * 128u + (uint32_t)rr * 16u + (uint32_t)(j0 & 7) * 2u;
+    *reinterpret_cast<uint2*>(A + off) = *reinterpret_cast<const uint2*>(hi);
+    *reinterpret_cast<uint2*>(A + a_part + off) = *reinterpret_cast<const uint2*>(lo);
+  } else {
+    float4 hi, lo;
+    hi.x = to_tf32(y[0]);
+    hi.y = to_tf32(y[1]);
+    hi.z = to_tf32(y[2]);
+    hi.w = to_tf32(y[3]);
+    lo.x = to_tf32(y[0] - hi.x);
+    lo.y = to_tf32(y[1] - hi.y);
+    lo.z = to_tf32(y[2] - hi.z);
+    lo.w = to_tf32(y[3] - hi.w);
+    const uint32_t off = (uint32_t)(j0 >> 2) * 256u + (uint32_t)rg * 128u + (uint32_t)rr * 16u;
+    *reinterpret_cast<float4*>(A + off) = hi;
+    *reinterpret_cast<float4*>(A + a_part + off) = lo;
+  }
+}
+
+// FP64 fitness of the shifted vector y (shared memory, d values) by the
+// whole CTA: z_j = sum_k M_jk y_k (M^T read at L2, two accumulator chains),
+// the objective terms per coordinate, then a fixed-order sum (per warp an
+// xor tree, then the warps in order).  Every thread returns the value.
+__device__ double cta_fitness_fp64(const RunDesc& R, const double* sy, double* red) {
+  const int d = R.d, obj = R.obj, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ double s_zv[129];
+  if (tid < d) {
+    double z;
+    if (R.rotate) {
+      double p0 = 0.0, p1 = 0.0;
+      int k = 0;
+      for (; k + 1 < d; k += 2) {
+        p0 = fma(__ldcg(R.MT + (size_t)k * d + tid), sy[k], p0);
+        p1 = fma(__ldcg(R.MT + (size_t)(k + 1) * d + tid), sy[k + 1], p1);
+      }
+      if (k < d) p0 = fma(__ldcg(R.MT + (size_t)k * d + tid), sy[k], p0);
+      z = p0 + p1;
+    } else {
+      z = sy[tid];
+    }
+    s_zv[tid] = z;
+  }
+  __syncthreads();
+  double t1 = 0.0, t2 = 0.0;
+  if (tid < d) {
+    const double z = s_zv[tid];
+    if (obj == kObjSphere) {
+      t1 = z * z;
+    } else if (obj == kObjRastrigin) {
+      t1 = z * z - 10.0 * cos2pi_f64(z) + 10.0;
+    } else if (obj == kObjAckley) {
+      t1 = z * z;
+      t2 = cos2pi_f64(z);
+    } else if (tid + 1 < d) {  // Rosenbrock at t = z + 1
+      const double t0 = z + 1.0, tn = s_zv[tid + 1] + 1.0;
+      const double a = tn - t0 * t0, b = t0 - 1.0;
+      t1 = 100.0 * a * a + b * b;
+    }
+  }
+  t1 = warp_sum(t1);
+  t2 = warp_sum(t2);
+  if (lane == 0) {
+    red[warp] = t1;
+    red[8 + warp] = t2;
+  }
+  __syncthreads();
+  double s1 = 0.0, s2 = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    s1 += red[w];
+    s2 += red[8 + w];
+  }
+  __syncthreads();  // red and s_zv are reused by the next call
+  return obj == kObjAckley ? 20.0 + 2.718281828459045 - 20.0 * exp(-0.2 * sqrt(s1 / d)) - exp(s2 / d) : s1;
+}
+
+// VAR: the run uses a strategy variant or jDE (a separate instance, so that
+// plain DE/rand/1/bin keeps its register allocation)
+template <int ESZ, bool VAR>
+__global__ void __launch_bounds__(256, 1)
+    k_persist_cta(const RunDesc* __restrict__ runs, int run, PersistCtl* ctl, long long gens, int rows) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cta = (int)blockIdx.x, nct = (int)gridDim.x;
+  // the run descriptor lives in shared memory for the whole launch
+  __shared__ RunDesc sR;
+  static_assert(sizeof(RunDesc) % 8 == 0, "descriptor copied in 8-byte words");
+  for (int q = tid; q < (int)(sizeof(RunDesc) / 8); q += blockDim.x)
+    reinterpret_cast<uint64_t*>(&sR)[q] = reinterpret_cast<const uint64_t*>(runs + run)[q];
+  __syncthreads();
+  const RunDesc& R = sR;
+  RunState* st = R.st;
+  const int d = R.d, dp = R.dp, np = R.np, obj = R.obj;
+  const int row0 = cta * rows;
+
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ double s_f[kCtaRowsMax], s_ft[kCtaRowsMax];
+  __shared__ float s_tau[kCtaRowsMax], s_yn[kCtaRowsMax];
+  __shared__ uint8_t s_fx[kCtaRowsMax], s_flag[kCtaRowsMax];  // flag bit 0 accept, 1 decided in FP64, 2 pending FP64
+  __shared__ int s_blist[kCtaRowsMax];
+  __shared__ int s_nb, s_stop, s_abort, s_bidx, s_have, s_bfail, s_mfail;
+  __shared__ long long s_gen;
+  __shared__ double s_best;
+  __shared__ unsigned long long s_nband_total;
+
+  const CtaLayout L = cta_layout(R);
+  const uint32_t a_part = cta_a_part(R), b_part = (uint32_t)(R.b_tile_bytes / 2);
+  uint8_t* sA = smem + L.a;
+  uint8_t* sB = smem + L.b;
+  const int zs = cta_zstride(R);
+  float* zbuf = reinterpret_cast<float*>(smem + L.z);
+  double* sY = reinterpret_cast<double*>(smem + L.y);  // [2][dp]: FP64 y of a band row's trial and target
+  double* s_red = reinterpret_cast<double*>(smem + L.red);
+
+  const uint32_t bar_b = smem_u32(&s_bar[0]), bar_mma = smem_u32(&s_bar[1]);
+  const uint32_t ncols = R.ntn <= 32 ? 32u : (R.ntn <= 64 ? 64u : 128u);
+  const uint32_t fmt = ESZ == 2 ? 1u : 2u;
+  const uint32_t idesc =
+      (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(R.ntn >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+  const uint32_t bk = (uint32_t)(R.ntn / 8) * 128u;
+
+  // ---------------------------------------------------------------- set-up
+  if (tid == 0) {
+    mbar_init(bar_b, 1);
+    mbar_init(bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_gen = *(volatile int64_t*)&st->gen;
+    s_stop = *(volatile int32_t*)&st->stop;
+    s_best = *(volatile double*)&st->best_f;
+    s_bidx = max(*(volatile int32_t*)&st->best_idx, 0);  // DE/best/1 base (row 0 when none is finite)
+    s_abort = 0;
+    s_bfail = 0;
+    s_mfail = 0;
+    s_nband_total = 0;
+    if (cta == 0) ctl->gen0 = s_gen;  // generation counter at launch, for the trial count
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // the A operand and the bytes the products read past it start at zero
+  for (uint32_t q = tid * 16u; q < L.b; q += blockDim.x * 16u) *reinterpret_cast<uint4*>(smem + q) = make_uint4(0u, 0u, 0u, 0u);
+  {
+    const int cur0 = (int)(*(volatile int64_t*)&st->gen & 1);
+    if (tid < kCtaRowsMax) {
+      const int i = row0 + tid;
+      const bool mine = tid < rows && i < np;
+      s_f[tid] = mine ? R.f[cur0][i] : CUDART_INF;
+      s_fx[tid] = mine ? R.fx[cur0][i] : 1;
+      s_tau[tid] = mine ? R.tau[i] : 0.f;
+      s_yn[tid] = 0.f;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (tid == 0) {
+    // M split stays resident for the whole launch
+    mbar_expect_tx(bar_b, 2 * b_part);
+    bulk_g2s(smem_u32(sB), R.B, b_part, bar_b);
+    bulk_g2s(smem_u32(sB) + b_part, R.B + b_part, b_part, bar_b);
+    if (!mbar_wait(bar_b, 0u)) {
+      atomicOr(&st->err, kErrTimeout);
+      atomicExch(&ctl->abort, 1);
+      s_abort = 1;
+      s_bfail = 1;
+    }
+  }
+  __syncthreads();
+  const uint32_t tmem = s_tmem;
+
+  // per-warp registers: trial and target rows of this warp's targets (local
+  // rows warp and warp + 8), and the lane's coordinates of the shift
+  double tr[2][4], tx[2][4], osh[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int j = 4 * lane + e;
+    osh[e] = j < d ? R.o[j] : 0.0;
+  }
+  long long gen = s_gen;
+  int stop = s_stop;
+  double best_prev = s_best;
+  int best_idx = s_bidx;
+  bool abort = s_abort != 0;
+  uint32_t mma_phase = 0;
+
+  for (long long itg = 0; itg < gens && !stop && !abort; ++itg) {
+    const int64_t g = gen + 1;
+    const int cur = (int)(gen & 1), nxt = cur ^ 1;
+    const double* __restrict__ X = R.X[cur];
+    double* __restrict__ Xn = R.X[nxt];
+    const double* jFc = VAR && R.jde ? R.jF[cur] : nullptr;
+    const double* jCRc = VAR && R.jde ? R.jCR[cur] : nullptr;
+
+    if (tid == 0) {
+      s_nb = 0;
+      s_have = 1;  // cleared by warp 0 or 4 when its wait for the products gives up
+    }
+    // ---- 1. trials of this CTA's targets -> registers and the A operand;
+    // the loads of both of a warp's targets are issued before either is used
+    {
+      TrialSetup ts[2];
+      ChunkIn cin[2];
+      TrialVar tv[2];
+      bool valid[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int lr = warp + 8 * q;
+        const int i = row0 + lr;
+        valid[q] = lr < rows && i < np;
+        if (valid[q]) {
+          if constexpr (VAR) ts[q] = trial_setup_var(R, (uint32_t)i, g, lane, best_idx, jFc, jCRc, tv[q]);
+          else ts[q] = trial_setup(R, (uint32_t)i, g, lane);
+          if (4 * lane < d) trial_load(R, X, ts[q], (uint32_t)i, g, 4 * lane, cin[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (!valid[q]) continue;
+        const int lr = warp + 8 * q;
+        const int i = row0 + lr;
+        const int j0 = 4 * lane;
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        uint32_t bits = 0;
+        if (j0 < d) {
+          if constexpr (VAR) bits = trial_compute(R, ts[q], j0, cin[q], t, tv[q].F, tv[q].thr, tv[q].L);
+          else bits = trial_compute(R, ts[q], j0, cin[q], t);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) tx[q][e] = cin[q].xi[e];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) tr[q][e] = t[e];
+        float yn2 = 0.f;
+        if (j0 < R.kpad) {
+          float y[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            y[e] = (j0 + e < d) ? to_f32_rn(shifted(t[e], osh[e], R)) : 0.f;
+            yn2 += y[e] * y[e];
+          }
+          cta_store_split4<ESZ>(sA, a_part, lr, j0, y);
+        }
+        if (R.dbg_trial) trial_debug(R, (uint32_t)i, j0, lane, bits, t);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) yn2 += __shfl_xor_sync(0xffffffffu, yn2, o);
+        if (lane == 0) s_yn[lr] = sqrtf(yn2);
+      }
+    }
+    // generic-proxy writes of A become visible to the tensor cores' async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+
+    // ---- 2. split products on tcgen05
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int ksteps = R.kpad * ESZ / 32;
+      const uint32_t aa = smem_u32(sA), bb = smem_u32(sB);
+      for (int ks = 0; ks < ksteps; ++ks) {
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass) {
+          const uint32_t a = aa + (pass == 2 ? a_part : 0u) + (uint32_t)ks * 512u;
+          const uint32_t b = bb + (pass == 1 ? b_part : 0u) + (uint32_t)ks * 2u * bk;
+          mma_split<ESZ>(tmem, smem_desc(a, 256u, 128u), smem_desc(b, bk, 128u), idesc, (ks > 0 || pass > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(bar_mma);
+    }
+    // ---- 3a. warps 0 and 4 copy the accumulator rows (TMEM lanes 0..31 ->
+    // shared memory): warp 0 the first half of the columns, warp 4 the rest
+    if ((warp & 3) == 0) {
+      const bool ok = mbar_wait(bar_mma, mma_phase);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const bool have = __all_sync(0xffffffffu, ok);
+      if (have) {
+        const int half = R.ntn / 2;
+        const int cb = (warp >> 2) * half;
+        for (int c = 0; c < half; c += 32) {
+          float v[32];
+          const int w = min(32, half - c);
+          const uint32_t ta = tmem + (uint32_t)(cb + c);
+          if (w == 32) {
+            tmem_ld_cols32(ta, v);
+          } else if (w == 24) {
+            tmem_ld_cols16(ta, v);
+            tmem_ld8(ta + 16u, v + 16);
+          } else if (w == 16) {
+            tmem_ld_cols16(ta, v);
+          } else {
+            tmem_ld8(ta, v);
+          }
+          if (lane < rows) {
+            float* dst = zbuf + (size_t)lane * zs + cb + c;
+#pragma unroll
+            for (int e = 0; e < 32; e += 4)
+              if (e < w) *reinterpret_cast<float4*>(dst + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+          }
+        }
+      } else if (lane == 0) {
+        atomicOr(&st->err, kErrTimeout);
+        atomicExch(&ctl->abort, 1);
+        s_abort = 1;
+        s_have = 0;
+        s_mfail = 1 + (int)mma_phase;  // the phase whose products may still be in flight, plus one
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    mma_phase ^= 1u;
+    __syncthreads();
+
+    // ---- 3b. FP32 objective of every target (16 threads per row) and the
+    // selections the split error bound decides
+    const bool have = s_have != 0;
+    {
+      const int rr = tid >> 4, sub = tid & 15;
+      const int i = row0 + rr;
+      const bool valid = rr < rows && i < np;
+      EpiAcc acc_{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (valid && have) epi_strided_dispatch(obj, zbuf + (size_t)rr * zs, sub, d, acc_);
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        acc_.a1 += __shfl_xor_sync(0xffffffffu, acc_.a1, o);
+        acc_.a2 += __shfl_xor_sync(0xffffffffu, acc_.a2, o);
+        acc_.a3 += __shfl_xor_sync(0xffffffffu, acc_.a3, o);
+        acc_.aS += __shfl_xor_sync(0xffffffffu, acc_.aS, o);
+        acc_.aG += __shfl_xor_sync(0xffffffffu, acc_.aG, o);
+      }
+      if (sub == 0 && rr < kCtaRowsMax) {
+        uint8_t flag = 0;
+        if (valid && have) {
+          const float s1 = acc_.a1, s2 = acc_.a2, s3 = acc_.a3;
+          float S = acc_.aS, G = acc_.aG;
+          float fs;
+          if (obj == kObjAckley) {
+            const float r = sqrtf(s1 / (float)d);
+            const float e1 = expf(-0.2f * r), e2 = expf(s2 / (float)d);
+            fs = 20.f + 2.718281828f - 20.f * e1 - e2;
+            S = 20.f + 2.718281828f + 20.f * e1 + expf(S / (float)d);
+            G = (r > 0.f ? 4.f * e1 * s3 / ((float)d * r) : 3.0e38f) + 6.283185307f * e2;
+          } else {
+            if (obj != kObjRastrigin) S = s1;
+            fs = s1;
+          }
+          const float tau = 2.f * R.band_u * G * R.rownorm * s_yn[rr] + (float)d * 0x1.0p-21f * S + 1e-30f;
+          const double fi = s_f[rr];
+          const float fif = (float)fi;
+          const float tif = s_fx[rr] ? 0.f : s_tau[rr];
+          const float mrg = 0x1.0p-22f * fabsf(fif);
+          const float bp = (float)best_prev;
+          const bool sure_reject = fs - tau > fif + tif + mrg;
+          const bool sure_accept = fs + tau < fif - tif - mrg;
+          const bool ambiguous = !sure_reject && !sure_accept;
+          const bool may_be_best = R.band_all && fs - tau <= bp + 0x1.0p-22f * fabsf(bp);
+          const bool near = fs - tau <= R.near_thr || fif - tif <= R.near_thr;
+          const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f;
+          s_ft[rr] = (double)fs;
+          if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !(fif == fif)) {
+            s_blist[atomicAdd(&s_nb, 1)] = rr;
+            flag = 4;
+          } else if (sure_accept || (ambiguous && fs <= fif)) {
+            // decided on the split values (an undecidable comparison far from
+            // the optimum goes to the smaller split value, ties to the trial)
+            flag = 1;
+            s_f[rr] = (double)fs;
+            s_fx[rr] = 0;
+            s_tau[rr] = tau;
+          }
+        }
+        s_flag[rr] = flag;
+      }
+    }
+    __syncthreads();
+
+    // ---- 3c. FP64 decisions of the listed targets (listing order), by the
+    // whole CTA; the owning warp publishes the FP64 y vectors
+    const int nb = s_nb;
+    for (int b = 0; b < nb; ++b) {
+      const int lr = s_blist[b];
+      const bool need_t = !s_fx[lr];
+      if ((lr & 7) == warp) {
+        const int q = lr >> 3;
+        const int j0 = 4 * lane;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (j0 + e >= d) continue;
+          sY[j0 + e] = shifted(q ? tr[1][e] : tr[0][e], osh[e], R);
+          if (need_t) sY[dp + j0 + e] = shifted(q ? tx[1][e] : tx[0][e], osh[e], R);
+        }
+      }
+      __syncthreads();
+      const double ft = cta_fitness_fp64(R, sY, s_red);
+      const double fi = need_t ? cta_fitness_fp64(R, sY + dp, s_red) : s_f[lr];
+      if (tid == 0) {
+        const bool acc = fit_key(ft) <= fit_key(fi) && fit_key(ft) != 0x7FFFFFFFFFFFFFFFLL;  // NaN ranks last
+        s_ft[lr] = ft;
+        s_f[lr] = acc ? ft : fi;
+        s_fx[lr] = 1;
+        s_tau[lr] = 0.f;
+        s_flag[lr] = (acc ? 1 : 0) | 2;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) s_nband_total += (unsigned long long)nb;  // published once, at the end of the launch
+
+    // ---- 4. next-generation rows, debug capture, best partial
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int lr = warp + 8 * q;
+      const int i = row0 + lr;
+      if (lr >= rows || i >= np) continue;
+      const bool acc = s_flag[lr] & 1;
+      if (VAR && R.jde && lane == 0) {
+        // jDE: an accepted trial passes its F_i and CR_i on
+        double Fi = __ldcg(jFc + i), CRi = __ldcg(jCRc + i);
+        if (acc) jde_params(R, (uint32_t)i, g, jFc, jCRc, Fi, CRi);
+        R.jF[nxt][i] = Fi;
+        R.jCR[nxt][i] = CRi;
+      }
+      const int j0 = 4 * lane;
+      if (j0 < d) {
+        double* dst = Xn + (size_t)i * dp + j0;
+        if (acc) {
+          *reinterpret_cast<double2*>(dst) = make_double2(tr[q][0], tr[q][1]);
+          *reinterpret_cast<double2*>(dst + 2) = make_double2(tr[q][2], tr[q][3]);
+        } else {
+          *reinterpret_cast<double2*>(dst) = make_double2(tx[q][0], tx[q][1]);
+          *reinterpret_cast<double2*>(dst + 2) = make_double2(tx[q][2], tx[q][3]);
+        }
+      }
+    }
+    if (warp == 0) {
+      Best b;
+      b.init();
+      if (lane < rows && row0 + lane < np) {
+        const int i = row0 + lane;
+        b.offer(s_f[lane], i);
+        if (R.dbg_ftrial) {
+          R.dbg_ftrial[i] = s_ft[lane];
+          R.dbg_accept[i] = s_flag[lane] & 1;
+          R.dbg_fp64[i] = (s_flag[lane] >> 1) & 1;
+        }
+      }
+      b.warp_reduce();
+      if (lane == 0) {
+        BestPartial* pp = R.part + (size_t)(g & 1) * nct + cta;
+        pp->f = b.f;
+        pp->idx = b.i;
+      }
+    }
+    __syncthreads();  // every row and the partial are written
+
+    // ---- 5. grid barrier; then every CTA reduces all partials (the same
+    // order everywhere) into the best record and the stop rule
+    if (warp == 0) {
+      bool ok = s_abort == 0;
+      if (ok) {
+        if (lane == 0) {
+          __threadfence();
+          atomicAdd(&ctl->bar, 1u);
+        }
+        __syncwarp();
+        const unsigned target = (unsigned)(itg + 1) * (unsigned)nct;
+        ok = false;
+        for (long long k = 0; k < kCtaGridSpin; ++k) {
+          unsigned v;
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->bar) : "memory");
+          if (v >= target) {
+            ok = true;
+            break;
+          }
+          if (*(volatile int*)&ctl->abort) break;
+          __nanosleep(32);
+        }
+        __syncwarp();
+        if (!ok && lane == 0 && !*(volatile int*)&ctl->abort) {
+          atomicExch(&ctl->abort, 1);
+          atomicOr(&st->err, kErrTimeout);
+        }
+      }
+      if (!ok) {
+        if (lane == 0) s_abort = 1;
+      } else {
+        Best b;
+        b.init();
+        const BestPartial* pp = R.part + (size_t)(g & 1) * nct;
+        for (int t = lane; t < nct; t += 32) b.offer(__ldcg(&pp[t].f), __ldcg(&pp[t].idx));
+        b.warp_reduce();
+        if (lane == 0) {
+          const double bf = b.f;
+          const int bi = b.i;
+          const int64_t evals = (int64_t)np * (1 + g);  // the initial population counts as NP evaluations
+          int sp = 0;
+          if (R.target > 0.0 && bi >= 0 && bf < R.target) sp = 1;
+          else if (R.max_evals > 0 && evals >= R.max_evals) sp = 2;
+          else if (g >= R.max_gens) sp = 3;
+          s_stop = sp;
+          s_best = bf;
+          if (bi >= 0) s_bidx = bi;
+          s_gen = g;
+          if (cta == 0) {
+            // one writer of the run state; evals are published at the end
+            st->best_f = bf;
+            st->best_idx = bi;
+            st->gen = g;
+            st->stop = sp;
+            if (bi < 0) atomicOr(&st->err, kErrNonFinite);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    gen = s_gen;
+    stop = s_stop;
+    best_prev = s_best;
+    best_idx = s_bidx;
+    abort = s_abort != 0;
+  }
+
+  // ---------------------------------------------------------------- teardown
+  if (tid == 0) atomicAdd(&R.stats[0], s_nband_total);
+  {
+    const int curf = (int)(gen & 1);
+    if (tid < rows && row0 + tid < np) {
+      const int i = row0 + tid;
+      R.f[curf][i] = s_f[tid];
+      R.fx[curf][i] = s_fx[tid];
+      R.tau[i] = s_tau[tid];
+    }
+  }
+  // copies and products still in flight after a failed wait must land
+  // before the CTA leaves and frees its tensor memory (bounded waits)
+  if (tid == 0) {
+    if (s_bfail) mbar_wait(bar_b, 0u);
+    if (s_mfail) mbar_wait(bar_mma, (uint32_t)(s_mfail - 1));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+// ------------------------------------------------------------------ host side
+template <int ESZ, bool VAR>
+static const void* cta_kernel() {
+  return (const void*)k_persist_cta<ESZ, VAR>;
+}
+
+static const void* cta_kernel(int prec, bool var) {
+  if (prec == DE_PREC_BF16X3) return var ? cta_kernel<2, true>() : cta_kernel<2, false>();
+  return var ? cta_kernel<4, true>() : cta_kernel<4, false>();
+}
+
+bool persist_cta_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
+  pp.cta_ok = false;
+  // one run, one N tile of at most 128 columns (TMEM: 128 columns), whole K
+  // resident, rows of at most 128 coordinates (one 4-coordinate chunk per lane)
+  if (nruns != 1 || R.nn != 1 || R.kc != R.kpad || R.d > 128 || R.ntn > 128) return false;
+  const size_t smem = cta_layout(R).total;
+  if (smem > 220 * 1024) return false;
+  const bool var = R.strategy != 0 || R.jde;
+  const void* k = cta_kernel(prec, var);
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  pp.cta_cap = per_sm * nsm;
+  pp.cta_smem = smem;
+  // first choice: the fewest targets per CTA that keep every CTA resident
+  int rows = std::max(1, (R.np + pp.cta_cap - 1) / pp.cta_cap);
+  if (rows > kCtaRowsMax) return false;
+  if (const char* env = getenv("DE_GB300_PERSIST_CTA_ROWS")) {
+    const int v = atoi(env);
+    if (v >= 1 && v <= kCtaRowsMax) rows = v;
+  }
+  if (!persist_cta_set_rows(pp, R, rows)) return false;
+  pp.cta_ok = true;
+  pp.prec = prec;
+  pp.var = var;
+  return true;
+}
+
+bool persist_cta_set_rows(PersistPlan& pp, const RunDesc& R, int rows) {
+  if (rows < 1 || rows > kCtaRowsMax) return false;
+  const int ntiles = (R.np + rows - 1) / rows;
+  if (ntiles > pp.cta_cap) return false;
+  pp.cta_rows = rows;
+  pp.cta_ntiles = ntiles;
+  return true;
+}
+
+cudaError_t persist_cta_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
+  if (e != cudaSuccess) return e;
+  int run = 0, rows = pp.cta_rows;
+  void* args[] = {(void*)&runs, (void*)&run, (void*)&ctl, (void*)&gens, (void*)&rows};
+  e = cudaLaunchCooperativeKernel(cta_kernel(pp.prec, pp.var), dim3((unsigned)pp.cta_ntiles), dim3(256), args,
+                                  pp.cta_smem, s);
+  if (e != cudaSuccess) return e;
+  k_persist_close_launch(runs, ctl, s);
+  return cudaGetLastError();
+}
+
+}  // namespace de

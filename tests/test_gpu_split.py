@@ -22,22 +22,33 @@ REL_SPLIT = {capi.DE_PREC_BF16X3: 1e-5, capi.DE_PREC_TF32X3: 1e-6}
 PRECS = [capi.DE_PREC_BF16X3, capi.DE_PREC_TF32X3]
 
 
-@pytest.fixture(params=["persistent", "three-kernel"])
+# the split-precision kernel paths: the persistent kernel as thread-block
+# clusters (path 2) or with CTA-local products (path 4), and the three-kernel
+# path (1); DE_GB300_PERSIST=0 disables both persistent forms,
+# DE_GB300_PERSIST_MODE keeps one of them
+PATH_ENV = {"cluster": ("1", "cluster"), "cta": ("1", "cta"), "three-kernel": ("0", "cta")}
+PATH_NUM = {"cluster": 2, "cta": 4, "three-kernel": 1}
+
+
+def _use_path(monkeypatch, name):
+    persist, mode = PATH_ENV[name]
+    monkeypatch.setenv("DE_GB300_PERSIST", persist)
+    monkeypatch.setenv("DE_GB300_PERSIST_MODE", mode)
+
+
+@pytest.fixture(params=["cluster", "cta", "three-kernel"])
 def split_path(request, monkeypatch):
-    """Run a test on both split-precision kernel paths; the persistent cluster
-    path is chosen at de_init unless DE_GB300_PERSIST=0."""
-    monkeypatch.setenv("DE_GB300_PERSIST", "1" if request.param == "persistent" else "0")
+    """Run a test on every split-precision kernel path."""
+    _use_path(monkeypatch, request.param)
     return request.param
 
 
 def _check_path(h, split_path):
+    """The handle runs the requested path where it applies (a persistent form
+    falls back to the three-kernel path for shapes it does not cover)."""
     plan = capi.de_get_plan(h)
-    if split_path == "three-kernel":
-        assert plan["kernel_path"] == 1
-    else:
-        assert plan["kernel_path"] in (1, 2)
-        return plan["kernel_path"] == 2
-    return False
+    assert plan["kernel_path"] in (1, PATH_NUM[split_path])
+    return plan["kernel_path"] != 1
 
 
 def _need_gpu():
@@ -149,19 +160,26 @@ def test_split_run_follows_the_fp64_trajectory(prec, split_path):
     assert res["best_f"] < 1e-8
 
 
-def test_persistent_path_is_used_for_the_rotated_rastrigin_workload():
-    """NP=1024, D=100 in split precision runs on the persistent cluster kernel."""
+def test_persistent_path_is_used_for_the_rotated_rastrigin_workload(monkeypatch):
+    """NP=1024, D=100 in split precision runs on a persistent kernel: the
+    autotuner's choice of form, or the form DE_GB300_PERSIST_MODE keeps."""
     _need_gpu()
     d = 100
     o, M = problems.shift(d, seed=1), problems.rotation(d, seed=1)
-    for prec in PRECS:
-        h = capi.de_init(capi.make_config(1024, d, objective=1, shift=o, rot=M, precision=prec,
-                                          max_generations=10))
-        try:
-            plan = capi.de_get_plan(h)
-        finally:
-            capi.de_destroy(h)
-        assert plan["kernel_path"] == 2 and plan["cluster_size"] == 8, plan
+    for mode, want in ((None, (2, 4)), ("cluster", (2,)), ("cta", (4,))):
+        if mode is None:
+            monkeypatch.delenv("DE_GB300_PERSIST_MODE", raising=False)
+        else:
+            monkeypatch.setenv("DE_GB300_PERSIST_MODE", mode)
+        for prec in PRECS:
+            h = capi.de_init(capi.make_config(1024, d, objective=1, shift=o, rot=M, precision=prec,
+                                              max_generations=10))
+            try:
+                plan = capi.de_get_plan(h)
+            finally:
+                capi.de_destroy(h)
+            assert plan["kernel_path"] in want, (mode, plan)
+            assert plan["cluster_size"] == (8 if plan["kernel_path"] == 2 else 0), plan
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -173,16 +191,17 @@ def test_split_paths_agree_over_many_generations(prec, monkeypatch):
     d = 30
     o, M = problems.shift(d, seed=4), problems.rotation(d, seed=4)
     pops = []
-    for flag in ("1", "0"):
-        monkeypatch.setenv("DE_GB300_PERSIST", flag)
+    for name in ("cluster", "cta", "three-kernel"):
+        _use_path(monkeypatch, name)
         h = capi.de_init(capi.make_config(300, d, objective=1, shift=o, rot=M, seed=3, precision=prec,
                                           max_generations=200, target_error=0.0, fp64_band=capi.DE_BAND_ALL))
         try:
+            assert capi.de_get_plan(h)["kernel_path"] == PATH_NUM[name]
             capi.de_run(h)
             pops.append(capi.de_get_population(h))
         finally:
             capi.de_destroy(h)
-    assert np.array_equal(pops[0][0], pops[1][0])
+    assert np.array_equal(pops[0][0], pops[1][0]) and np.array_equal(pops[0][0], pops[2][0])
 
 
 def test_persistent_rows_per_cluster_do_not_change_results(monkeypatch):
@@ -199,6 +218,7 @@ def test_persistent_rows_per_cluster_do_not_change_results(monkeypatch):
 
     def run(persist, rows):
         monkeypatch.setenv("DE_GB300_PERSIST", "1" if persist else "0")
+        monkeypatch.setenv("DE_GB300_PERSIST_MODE", "cluster")
         monkeypatch.setenv("DE_GB300_PERSIST_ROWS", rows)
         h = capi.de_init(capi.make_config(120, d, objective=3, shift=o, rot=M, seed=5, precision=capi.DE_PREC_BF16X3,
                                           max_generations=150, target_error=0.0, fp64_band=capi.DE_BAND_ALL))
@@ -222,6 +242,43 @@ def test_persistent_rows_per_cluster_do_not_change_results(monkeypatch):
         for key in keys:
             assert b[key] == tiled[0][2][key] == ref[2][key], key
         assert st["trials"] == ref[3]["trials"] == 120 * 150  # trials evaluated since de_init
+
+
+def test_cta_local_rows_per_cta_do_not_change_results(monkeypatch):
+    """The CTA-local persistent kernel's targets per CTA only change the
+    tiling (NP = 120: 8 to 120 CTAs): after 150 generations every tiling
+    gives the same populations, fitness, counters and best records, and the
+    populations equal the cluster kernel's (both evaluate a row's FP32 terms
+    in the same order and take every undecidable comparison in FP64; FP64
+    values agree within 1e-12 of the term scale)."""
+    _need_gpu()
+    d = 40
+    o, M = problems.shift(d, seed=6), problems.rotation(d, seed=6)
+
+    def run(mode, rows):
+        monkeypatch.setenv("DE_GB300_PERSIST", "1")
+        monkeypatch.setenv("DE_GB300_PERSIST_MODE", mode)
+        monkeypatch.setenv("DE_GB300_PERSIST_ROWS" if mode == "cluster" else "DE_GB300_PERSIST_CTA_ROWS", rows)
+        h = capi.de_init(capi.make_config(120, d, objective=3, shift=o, rot=M, seed=5, precision=capi.DE_PREC_BF16X3,
+                                          max_generations=150, target_error=0.0, fp64_band=capi.DE_BAND_ALL))
+        try:
+            assert capi.de_get_plan(h)["kernel_path"] == PATH_NUM[mode]
+            capi.de_run(h)
+            x, f = capi.de_get_population(h)
+            return x, f, capi.de_get_best(h), capi.de_get_stats(h)
+        finally:
+            capi.de_destroy(h)
+
+    ref = run("cluster", "40")
+    tiled = [run("cta", rows) for rows in ("1", "5", "8", "16")]
+    for x, f, b, st in tiled:
+        assert np.array_equal(x, tiled[0][0]) and np.array_equal(f, tiled[0][1])
+        assert b == tiled[0][2] and st == tiled[0][3]
+        assert np.array_equal(x, ref[0])
+        assert np.allclose(f, ref[1], rtol=1e-10, atol=0)
+        for key in ("generations", "evals", "best_index", "stop_reason"):
+            assert b[key] == ref[2][key], key
+        assert st["trials"] == ref[3]["trials"] == 120 * 150
 
 
 @pytest.mark.parametrize("prec", PRECS)

@@ -233,9 +233,19 @@ def test_adaptive_getters_reject_plain_runs_and_bad_values():
 REL_SPLIT = {capi.DE_PREC_BF16X3: 1e-5, capi.DE_PREC_TF32X3: 1e-6}
 
 
-@pytest.fixture(params=["persistent", "three-kernel"])
+# split-precision kernel paths: persistent clusters (2), persistent with
+# CTA-local products (4), three kernels (1)
+PATH_ENV = {"cluster": ("1", "cluster"), "cta": ("1", "cta"), "three-kernel": ("0", "cta")}
+
+
+def _use_path(monkeypatch, name):
+    monkeypatch.setenv("DE_GB300_PERSIST", PATH_ENV[name][0])
+    monkeypatch.setenv("DE_GB300_PERSIST_MODE", PATH_ENV[name][1])
+
+
+@pytest.fixture(params=["cluster", "cta", "three-kernel"])
 def split_path(request, monkeypatch):
-    monkeypatch.setenv("DE_GB300_PERSIST", "1" if request.param == "persistent" else "0")
+    _use_path(monkeypatch, request.param)
     return request.param
 
 
@@ -258,7 +268,7 @@ def test_split_variants_one_generation_match_oracle(prec, strategy, jde, np_, d,
     h = capi.de_init(cfg)
     try:
         plan = capi.de_get_plan(h)["kernel_path"]
-        assert plan == (1 if split_path == "three-kernel" else plan)
+        assert plan in {"cluster": (1, 2), "cta": (1, 4), "three-kernel": (1,)}[split_path]
         capi.de_set_population(h, 0, X, fX)
         capi.de_set_generation(h, 0, 8)
         if jde:
@@ -294,8 +304,8 @@ def test_split_variant_paths_agree_over_many_generations(strategy, jde, monkeypa
     d = 30
     o, M = problems.shift(d, seed=4), problems.rotation(d, seed=4)
     out = []
-    for flag in ("1", "0"):
-        monkeypatch.setenv("DE_GB300_PERSIST", flag)
+    for name in ("cluster", "cta", "three-kernel"):
+        _use_path(monkeypatch, name)
         h = capi.de_init(capi.make_config(300, d, objective=1, shift=o, rot=M, seed=3, precision=capi.DE_PREC_BF16X3,
                                           max_generations=150, target_error=0.0, fp64_band=capi.DE_BAND_ALL,
                                           strategy=strategy, jde=jde))
@@ -304,9 +314,10 @@ def test_split_variant_paths_agree_over_many_generations(strategy, jde, monkeypa
             out.append((capi.de_get_population(h), capi.de_get_adaptive(h) if jde else None))
         finally:
             capi.de_destroy(h)
-    assert np.array_equal(out[0][0][0], out[1][0][0])
-    if jde:
-        assert np.array_equal(out[0][1][0], out[1][1][0]) and np.array_equal(out[0][1][1], out[1][1][1])
+    for k in (1, 2):
+        assert np.array_equal(out[0][0][0], out[k][0][0])
+        if jde:
+            assert np.array_equal(out[0][1][0], out[k][1][0]) and np.array_equal(out[0][1][1], out[k][1][1])
 
 
 def test_split_batch_with_variants_equals_single_runs(monkeypatch):
