@@ -273,7 +273,8 @@ def test_cta_local_rows_per_cta_do_not_change_results(monkeypatch):
     tiled = [run("cta", rows) for rows in ("1", "5", "8", "16")]
     for x, f, b, st in tiled:
         assert np.array_equal(x, tiled[0][0]) and np.array_equal(f, tiled[0][1])
-        assert b == tiled[0][2] and st == tiled[0][3]
+        assert np.array_equal(b["best_x"], tiled[0][2]["best_x"]) and b["best_f"] == tiled[0][2]["best_f"]
+        assert st == tiled[0][3]
         assert np.array_equal(x, ref[0])
         assert np.allclose(f, ref[1], rtol=1e-10, atol=0)
         for key in ("generations", "evals", "best_index", "stop_reason"):
