@@ -693,8 +693,11 @@ static de_status autotune_split(de_handle* h) {
 static std::string tune_key_persist(const de_handle* h) {
   const RunDesc& R = h->run[0];
   char b[256];
-  snprintf(b, sizeof b, "persist_v2 prec=%d np=%d d=%d obj=%d rot=%d var=%d cl=%d cta=%d", h->prec, R.np, R.d, R.obj,
-           R.rotate, h->tc.persist.var ? 1 : 0, h->tc.persist.cl_ok ? 1 : 0, h->tc.persist.cta_ok ? 1 : 0);
+  // the debug capture and the band policy change the kernel's timing (the
+  // capture orders the stop decision before the trials)
+  snprintf(b, sizeof b, "persist_v3 prec=%d np=%d d=%d obj=%d rot=%d var=%d cl=%d cta=%d dbg=%d band=%d", h->prec,
+           R.np, R.d, R.obj, R.rotate, h->tc.persist.var ? 1 : 0, h->tc.persist.cl_ok ? 1 : 0,
+           h->tc.persist.cta_ok ? 1 : 0, R.dbg_trial ? 1 : 0, R.band_all);
   return b;
 }
 

@@ -23,6 +23,9 @@ struct PersistCtl {
   // gives up after test_spin polls, so that the bounded wait runs out
   int test_skip;
   long long test_spin;
+  // grid-barrier arrivals of the CTA-local split kernel: CTA c counts on
+  // sbar[c % 8][0], each counter on its own 128-byte line
+  unsigned int sbar[8][32];
 };
 // FP64 path (de_fp64.cu)
 void k_configure(size_t smem_gen);

@@ -254,8 +254,12 @@ __global__ void __launch_bounds__(256, 1)
   __syncthreads();
   const uint32_t tmem = s_tmem;
 
-  // per-warp registers: trial and target rows of this warp's targets (local
-  // rows warp and warp + 8), and the lane's coordinates of the shift
+  // Targets of this warp: local rows (warp - shift) + 8 q.  With at most 7
+  // targets per CTA (plain DE/rand/1/bin) warp 0 has none: it reduces the
+  // previous generation's best partials while the other warps build trials.
+  const int shift = (!VAR && rows <= 7) ? 1 : 0;
+  // per-warp registers: trial and current rows of this warp's targets, and the
+  // lane's coordinates of the shift
   double tr[2][4], tx[2][4], osh[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -263,24 +267,67 @@ __global__ void __launch_bounds__(256, 1)
     osh[e] = j < d ? R.o[j] : 0.0;
   }
   long long gen = s_gen;
-  int stop = s_stop;
-  double best_prev = s_best;
-  int best_idx = s_bidx;
   bool abort = s_abort != 0;
+  bool reduce_pending = false;  // partials of generation gen still to reduce
+  bool rows_in_regs = false;    // tx holds the current rows (after the first generation of a launch)
+  bool have_next = false;       // nts / nu hold the draws of generation gen + 1
+  TrialSetup nts[2];            // plain DE: r1, r2, r3, j_rand of the next generation
+  U32x4 nu[2];                  // ... and the lane's crossover block
+  unsigned nbar = 0;            // grid barriers passed in this launch
   uint32_t mma_phase = 0;
 
-  for (long long itg = 0; itg < gens && !stop && !abort; ++itg) {
+  for (long long itg = 0;; ++itg) {
     const int64_t g = gen + 1;
     const int cur = (int)(gen & 1), nxt = cur ^ 1;
     const double* __restrict__ X = R.X[cur];
     double* __restrict__ Xn = R.X[nxt];
     const double* jFc = VAR && R.jde ? R.jF[cur] : nullptr;
     const double* jCRc = VAR && R.jde ? R.jCR[cur] : nullptr;
+    const bool more = itg < gens && !abort;
 
+    // ---- 0. best record and stop rule of generation gen, whose partials are
+    // complete (the grid barrier passed): warp 0, the same order in every CTA
+    if (reduce_pending && warp == 0) {
+      Best b;
+      b.init();
+      const BestPartial* pp = R.part + (size_t)(gen & 1) * nct;
+      for (int t = lane; t < nct; t += 32) b.offer(__ldcg(&pp[t].f), __ldcg(&pp[t].idx));
+      b.warp_reduce();
+      if (lane == 0) {
+        const double bf = b.f;
+        const int bi = b.i;
+        const int64_t evals = (int64_t)np * (1 + gen);  // the initial population counts as NP evaluations
+        int sp = 0;
+        if (R.target > 0.0 && bi >= 0 && bf < R.target) sp = 1;
+        else if (R.max_evals > 0 && evals >= R.max_evals) sp = 2;
+        else if (gen >= R.max_gens) sp = 3;
+        s_stop = sp;
+        s_best = bf;
+        if (bi >= 0) s_bidx = bi;
+        s_gen = gen;
+        if (cta == 0) {
+          // one writer of the run state; evals are published at the end
+          st->best_f = bf;
+          st->best_idx = bi;
+          st->gen = gen;
+          st->stop = sp;
+          if (bi < 0) atomicOr(&st->err, kErrNonFinite);
+        }
+      }
+    }
+    reduce_pending = false;
+    // the variants need the best record before their trials (DE/best/1
+    // base), and a debug capture must not record trials of a generation that
+    // the stop rule cancels: both take the stop decision first
+    const bool ordered = VAR || R.dbg_trial != nullptr;
+    if (ordered || !more) __syncthreads();
+    if (!more) break;
+    if (ordered && s_stop) break;
     if (tid == 0) {
       s_nb = 0;
       s_have = 1;  // cleared by warp 0 or 4 when its wait for the products gives up
     }
+
     // ---- 1. trials of this CTA's targets -> registers and the A operand;
     // the loads of both of a warp's targets are issued before either is used
     {
@@ -288,23 +335,60 @@ __global__ void __launch_bounds__(256, 1)
       ChunkIn cin[2];
       TrialVar tv[2];
       bool valid[2];
+      const int j0 = 4 * lane;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const int lr = warp + 8 * q;
+        const int lr = warp - shift + 8 * q;
         const int i = row0 + lr;
-        valid[q] = lr < rows && i < np;
-        if (valid[q]) {
-          if constexpr (VAR) ts[q] = trial_setup_var(R, (uint32_t)i, g, lane, best_idx, jFc, jCRc, tv[q]);
-          else ts[q] = trial_setup(R, (uint32_t)i, g, lane);
-          if (4 * lane < d) trial_load(R, X, ts[q], (uint32_t)i, g, 4 * lane, cin[q]);
+        valid[q] = warp >= shift && lr < rows && i < np;
+        if (!valid[q]) continue;
+        if constexpr (VAR) {
+          ts[q] = trial_setup_var(R, (uint32_t)i, g, lane, s_bidx, jFc, jCRc, tv[q]);
+          if (j0 < d) trial_load(R, X, ts[q], (uint32_t)i, g, j0, cin[q]);
+        } else {
+          // the draws were made while this CTA waited at the last grid barrier
+          ts[q] = have_next ? nts[q] : trial_setup(R, (uint32_t)i, g, lane, 0u, false);
+          if (R.dbg_idx && lane == 0) {
+            R.dbg_idx[3 * i + 0] = (int32_t)ts[q].r1;
+            R.dbg_idx[3 * i + 1] = (int32_t)ts[q].r2;
+            R.dbg_idx[3 * i + 2] = (int32_t)ts[q].r3;
+            R.dbg_jrand[i] = (int32_t)ts[q].jr;
+          }
+          if (j0 < d) {
+            cin[q].u = have_next ? nu[q]
+                                 : draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)g, (uint32_t)i, 1u + lane);
+            const double* rows3[3] = {X + (size_t)ts[q].r1 * dp + j0, X + (size_t)ts[q].r2 * dp + j0,
+                                      X + (size_t)ts[q].r3 * dp + j0};
+            double* dst[3] = {cin[q].x1, cin[q].x2, cin[q].x3};
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              const double2 a = __ldcg(reinterpret_cast<const double2*>(rows3[r]));
+              const double2 b2 = __ldcg(reinterpret_cast<const double2*>(rows3[r] + 2));
+              dst[r][0] = a.x;
+              dst[r][1] = a.y;
+              dst[r][2] = b2.x;
+              dst[r][3] = b2.y;
+            }
+            if (rows_in_regs) {
+              // the target is the row this warp wrote in the last generation
+#pragma unroll
+              for (int e = 0; e < 4; ++e) cin[q].xi[e] = tx[q][e];
+            } else {
+              const double2 a = __ldcg(reinterpret_cast<const double2*>(X + (size_t)i * dp + j0));
+              const double2 b2 = __ldcg(reinterpret_cast<const double2*>(X + (size_t)i * dp + j0 + 2));
+              cin[q].xi[0] = a.x;
+              cin[q].xi[1] = a.y;
+              cin[q].xi[2] = b2.x;
+              cin[q].xi[3] = b2.y;
+            }
+          }
         }
       }
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (!valid[q]) continue;
-        const int lr = warp + 8 * q;
+        const int lr = warp - shift + 8 * q;
         const int i = row0 + lr;
-        const int j0 = 4 * lane;
         double t[4] = {0.0, 0.0, 0.0, 0.0};
         uint32_t bits = 0;
         if (j0 < d) {
@@ -334,6 +418,10 @@ __global__ void __launch_bounds__(256, 1)
     // generic-proxy writes of A become visible to the tensor cores' async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    // otherwise the stop rule of generation gen was reduced meanwhile; a
+    // stopped run leaves before anything of generation g is written
+    if (!ordered && s_stop) break;
+    const double best_prev = s_best;
 
     // ---- 2. split products on tcgen05
     if (tid == 0) {
@@ -409,7 +497,7 @@ __global__ void __launch_bounds__(256, 1)
         acc_.aS += __shfl_xor_sync(0xffffffffu, acc_.aS, o);
         acc_.aG += __shfl_xor_sync(0xffffffffu, acc_.aG, o);
       }
-      if (sub == 0 && rr < kCtaRowsMax) {
+      if (sub == 0) {
         uint8_t flag = 0;
         if (valid && have) {
           const float s1 = acc_.a1, s2 = acc_.a2, s3 = acc_.a3;
@@ -461,14 +549,14 @@ __global__ void __launch_bounds__(256, 1)
     for (int b = 0; b < nb; ++b) {
       const int lr = s_blist[b];
       const bool need_t = !s_fx[lr];
-      if ((lr & 7) == warp) {
+      if ((lr & 7) + shift == warp) {
         const int q = lr >> 3;
-        const int j0 = 4 * lane;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          if (j0 + e >= d) continue;
-          sY[j0 + e] = shifted(q ? tr[1][e] : tr[0][e], osh[e], R);
-          if (need_t) sY[dp + j0 + e] = shifted(q ? tx[1][e] : tx[0][e], osh[e], R);
+          const int j = 4 * lane + e;
+          if (j >= d) continue;
+          sY[j] = shifted(q ? tr[1][e] : tr[0][e], osh[e], R);
+          if (need_t) sY[dp + j] = shifted(q ? tx[1][e] : tx[0][e], osh[e], R);
         }
       }
       __syncthreads();
@@ -486,12 +574,13 @@ __global__ void __launch_bounds__(256, 1)
     }
     if (tid == 0) s_nband_total += (unsigned long long)nb;  // published once, at the end of the launch
 
-    // ---- 4. next-generation rows, debug capture, best partial
+    // ---- 4. next-generation rows (they stay in registers as the next
+    // targets), debug capture, best partial
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const int lr = warp + 8 * q;
+      const int lr = warp - shift + 8 * q;
       const int i = row0 + lr;
-      if (lr >= rows || i >= np) continue;
+      if (warp < shift || lr >= rows || i >= np) continue;
       const bool acc = s_flag[lr] & 1;
       if (VAR && R.jde && lane == 0) {
         // jDE: an accepted trial passes its F_i and CR_i on
@@ -500,18 +589,18 @@ __global__ void __launch_bounds__(256, 1)
         R.jF[nxt][i] = Fi;
         R.jCR[nxt][i] = CRi;
       }
+      if (acc) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) tx[q][e] = tr[q][e];
+      }
       const int j0 = 4 * lane;
       if (j0 < d) {
         double* dst = Xn + (size_t)i * dp + j0;
-        if (acc) {
-          *reinterpret_cast<double2*>(dst) = make_double2(tr[q][0], tr[q][1]);
-          *reinterpret_cast<double2*>(dst + 2) = make_double2(tr[q][2], tr[q][3]);
-        } else {
-          *reinterpret_cast<double2*>(dst) = make_double2(tx[q][0], tx[q][1]);
-          *reinterpret_cast<double2*>(dst + 2) = make_double2(tx[q][2], tx[q][3]);
-        }
+        *reinterpret_cast<double2*>(dst) = make_double2(tx[q][0], tx[q][1]);
+        *reinterpret_cast<double2*>(dst + 2) = make_double2(tx[q][2], tx[q][3]);
       }
     }
+    rows_in_regs = true;
     if (warp == 0) {
       Best b;
       b.init();
@@ -533,22 +622,26 @@ __global__ void __launch_bounds__(256, 1)
     }
     __syncthreads();  // every row and the partial are written
 
-    // ---- 5. grid barrier; then every CTA reduces all partials (the same
-    // order everywhere) into the best record and the stop rule
+    // ---- 5. grid barrier (arrivals spread over 8 counters on their own
+    // cache lines; lanes 0..7 of warp 0 poll one each).  Meanwhile the other
+    // warps draw the next generation's indices, j_rand and crossover blocks,
+    // which depend on (seed, generation, target) only.
     if (warp == 0) {
       bool ok = s_abort == 0;
       if (ok) {
         if (lane == 0) {
           __threadfence();
-          atomicAdd(&ctl->bar, 1u);
+          atomicAdd(&ctl->sbar[cta & 7][0], 1u);
         }
         __syncwarp();
-        const unsigned target = (unsigned)(itg + 1) * (unsigned)nct;
+        const unsigned mine = lane < 8 ? (unsigned)((nct - lane + 7) / 8) : 0u;  // CTAs counted by counter `lane`
+        const unsigned target = (nbar + 1u) * mine;
         ok = false;
         for (long long k = 0; k < kCtaGridSpin; ++k) {
-          unsigned v;
-          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->bar) : "memory");
-          if (v >= target) {
+          unsigned v = 0u;
+          if (lane < 8)
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->sbar[lane][0]) : "memory");
+          if (__all_sync(0xffffffffu, v >= target)) {
             ok = true;
             break;
           }
@@ -561,43 +654,35 @@ __global__ void __launch_bounds__(256, 1)
           atomicOr(&st->err, kErrTimeout);
         }
       }
-      if (!ok) {
-        if (lane == 0) s_abort = 1;
-      } else {
-        Best b;
-        b.init();
-        const BestPartial* pp = R.part + (size_t)(g & 1) * nct;
-        for (int t = lane; t < nct; t += 32) b.offer(__ldcg(&pp[t].f), __ldcg(&pp[t].idx));
-        b.warp_reduce();
-        if (lane == 0) {
-          const double bf = b.f;
-          const int bi = b.i;
-          const int64_t evals = (int64_t)np * (1 + g);  // the initial population counts as NP evaluations
-          int sp = 0;
-          if (R.target > 0.0 && bi >= 0 && bf < R.target) sp = 1;
-          else if (R.max_evals > 0 && evals >= R.max_evals) sp = 2;
-          else if (g >= R.max_gens) sp = 3;
-          s_stop = sp;
-          s_best = bf;
-          if (bi >= 0) s_bidx = bi;
-          s_gen = g;
-          if (cta == 0) {
-            // one writer of the run state; evals are published at the end
-            st->best_f = bf;
-            st->best_idx = bi;
-            st->gen = g;
-            st->stop = sp;
-            if (bi < 0) atomicOr(&st->err, kErrNonFinite);
-          }
-        }
+      if (!ok && lane == 0) s_abort = 1;
+    } else if (!VAR) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int lr = warp - shift + 8 * q;
+        const int i = row0 + lr;
+        if (lr >= rows || i >= np) continue;
+        nts[q] = trial_setup(R, (uint32_t)i, g + 1, lane, 0u, false);
+        nu[q] = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)(g + 1), (uint32_t)i, 1u + lane);
       }
     }
+    if (!VAR && warp == 0 && shift == 0) {
+      // warp 0 has targets only with more than 7 per CTA: its draws come last
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int lr = 8 * q;
+        const int i = row0 + lr;
+        if (lr >= rows || i >= np) continue;
+        nts[q] = trial_setup(R, (uint32_t)i, g + 1, lane, 0u, false);
+        nu[q] = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)(g + 1), (uint32_t)i, 1u + lane);
+      }
+    }
+    have_next = !VAR;
+    ++nbar;
     __syncthreads();
-    gen = s_gen;
-    stop = s_stop;
-    best_prev = s_best;
-    best_idx = s_bidx;
     abort = s_abort != 0;
+    if (abort) break;
+    gen = g;
+    reduce_pending = true;
   }
 
   // ---------------------------------------------------------------- teardown

@@ -935,7 +935,7 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
   bytes += cap * sizeof(uint32_t);
   bytes = round_up(bytes, 256);
   const size_t off_ctl = bytes;
-  bytes += 256;
+  bytes += round_up(sizeof(PersistCtl), 256);
   p.nch_max = nch_max;
   p.smem_band = 0;
   for (auto& R : runs)
