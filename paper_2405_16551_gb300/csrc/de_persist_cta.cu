@@ -10,12 +10,13 @@
 //      repair; FP64, one target per warp at a time, the same routines as the
 //      other paths), keeps the trial and target rows in registers and writes
 //      the split rows of y = (t - o) s into the CTA's own A operand;
-//   2. one thread issues the three split products on tcgen05 (M = 128, the
-//      whole K resident); A holds 16 rows, and the rows 16..127 the
-//      instruction also reads are other bytes of the CTA's shared memory,
-//      whose products land in tensor-memory lanes nobody reads;
-//   3. warps 0 and 4 (the warps that may read TMEM lanes 0..31) copy the
-//      accumulator rows to shared memory; every target is then evaluated in
+//   2. one thread issues the three split products on tcgen05 with the roles
+//      of the operands exchanged: A is M (128 rows, one per output
+//      coordinate z_j, zero past D; resident for the whole launch), B the
+//      16-row y tile (N = 16), so that TMEM lane j, column r holds z_j of
+//      target r and the tensor work scales with 16 targets, not 128;
+//   3. the eight warps copy the accumulator (lanes 32 (w mod 4) .., columns
+//      8 (w / 4) ..) to shared memory as rows of z; every target is then evaluated in
 //      FP32 by 16 threads (strided columns, fixed xor tree: the order of the
 //      cluster kernel, so both give the same values) and its selection is
 //      decided where the split error bound allows.  The other targets (and
@@ -46,24 +47,24 @@ namespace de {
 
 constexpr int kCtaRowsMax = 16;                   // targets per CTA (two A row groups)
 constexpr long long kCtaGridSpin = 1LL << 22;     // polls of the grid barrier (with back-off)
-constexpr uint32_t kCtaAPad = 2048;               // bytes after A that rows 16..127 of the products read
 
-// Bytes of one part (high or low) of the 16-row A operand: k-groups of 16
+// Bytes of one part (high or low) of the 16-row y operand: k-groups of 16
 // bytes, each holding two 8-row core matrices (k-group stride 256 bytes).
-__host__ __device__ inline uint32_t cta_a_part(const RunDesc& R) { return (uint32_t)(R.kpad * R.esz / 16) * 256u; }
+__host__ __device__ inline uint32_t cta_y_part(const RunDesc& R) { return (uint32_t)(R.kpad * R.esz / 16) * 256u; }
+// ... and of the 128-row M operand (k-group stride 16 x 128 = 2048 bytes).
+__host__ __device__ inline uint32_t cta_m_part(const RunDesc& R) { return (uint32_t)(R.kpad * R.esz / 16) * 2048u; }
 // Row stride (floats) of the accumulator rows in shared memory.
 __host__ __device__ inline int cta_zstride(const RunDesc& R) { return R.ntn + 4; }
 
 struct CtaLayout {
-  uint32_t a, b, z, y, red, total;
+  uint32_t yop, mop, z, y, red, total;
 };
 
 __host__ __device__ inline CtaLayout cta_layout(const RunDesc& R) {
   CtaLayout L;
-  const uint32_t ap = cta_a_part(R);
-  L.a = 0;
-  L.b = (2u * ap + kCtaAPad + 1023u) / 1024u * 1024u;
-  L.z = L.b + (uint32_t)R.b_tile_bytes;
+  L.yop = 0;
+  L.mop = (2u * cta_y_part(R) + 1023u) / 1024u * 1024u;
+  L.z = L.mop + 2u * cta_m_part(R);
   L.y = L.z + (uint32_t)(kCtaRowsMax * cta_zstride(R)) * 4u;  // 16-byte aligned: zstride is a multiple of 4
   L.y = (L.y + 15u) / 16u * 16u;
   L.red = L.y + (uint32_t)(2 * R.dp) * 8u;  // FP64 y of a band row's trial and target
@@ -71,7 +72,8 @@ __host__ __device__ inline CtaLayout cta_layout(const RunDesc& R) {
   return L;
 }
 
-// y[0..3] (coordinates j0..j0+3 of A row m < 16) as high and low parts.
+// y[0..3] (coordinates j0..j0+3 of row m < 16 of the y operand) as high and
+// low parts.
 template <int ESZ>
 __device__ __forceinline__ void cta_store_split4(uint8_t* A, uint32_t a_part, int m, int j0, const float y[4]) {
   const int rg = m >> 3, rr = m & 7;
@@ -182,30 +184,28 @@ __global__ void __launch_bounds__(256, 1)
   __shared__ float s_tau[kCtaRowsMax], s_yn[kCtaRowsMax];
   __shared__ uint8_t s_fx[kCtaRowsMax], s_flag[kCtaRowsMax];  // flag bit 0 accept, 1 decided in FP64, 2 pending FP64
   __shared__ int s_blist[kCtaRowsMax];
-  __shared__ int s_nb, s_stop, s_abort, s_bidx, s_have, s_bfail, s_mfail;
+  __shared__ int s_nb, s_stop, s_abort, s_bidx, s_have, s_mfail;
   __shared__ long long s_gen;
   __shared__ double s_best;
   __shared__ unsigned long long s_nband_total;
 
   const CtaLayout L = cta_layout(R);
-  const uint32_t a_part = cta_a_part(R), b_part = (uint32_t)(R.b_tile_bytes / 2);
-  uint8_t* sA = smem + L.a;
-  uint8_t* sB = smem + L.b;
+  const uint32_t y_part = cta_y_part(R), m_part = cta_m_part(R);
+  uint8_t* sYop = smem + L.yop;  // B operand: split y of this CTA's targets
+  uint8_t* sMop = smem + L.mop;  // A operand: split M
   const int zs = cta_zstride(R);
   float* zbuf = reinterpret_cast<float*>(smem + L.z);
   double* sY = reinterpret_cast<double*>(smem + L.y);  // [2][dp]: FP64 y of a band row's trial and target
   double* s_red = reinterpret_cast<double*>(smem + L.red);
 
-  const uint32_t bar_b = smem_u32(&s_bar[0]), bar_mma = smem_u32(&s_bar[1]);
-  const uint32_t ncols = R.ntn <= 32 ? 32u : (R.ntn <= 64 ? 64u : 128u);
+  const uint32_t bar_mma = smem_u32(&s_bar[1]);
+  const uint32_t ncols = 32u;  // the accumulator: 128 lanes x 16 columns (the smallest allocation)
   const uint32_t fmt = ESZ == 2 ? 1u : 2u;
-  const uint32_t idesc =
-      (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(R.ntn >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
-  const uint32_t bk = (uint32_t)(R.ntn / 8) * 128u;
+  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kCtaRowsMax >> 3) << 17) |
+                         ((uint32_t)(kTileM >> 4) << 24);
 
   // ---------------------------------------------------------------- set-up
   if (tid == 0) {
-    mbar_init(bar_b, 1);
     mbar_init(bar_mma, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_gen = *(volatile int64_t*)&st->gen;
@@ -213,7 +213,6 @@ __global__ void __launch_bounds__(256, 1)
     s_best = *(volatile double*)&st->best_f;
     s_bidx = max(*(volatile int32_t*)&st->best_idx, 0);  // DE/best/1 base (row 0 when none is finite)
     s_abort = 0;
-    s_bfail = 0;
     s_mfail = 0;
     s_nband_total = 0;
     if (cta == 0) ctl->gen0 = s_gen;  // generation counter at launch, for the trial count
@@ -223,8 +222,21 @@ __global__ void __launch_bounds__(256, 1)
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // the A operand and the bytes the products read past it start at zero
-  for (uint32_t q = tid * 16u; q < L.b; q += blockDim.x * 16u) *reinterpret_cast<uint4*>(smem + q) = make_uint4(0u, 0u, 0u, 0u);
+  // the y operand starts at zero (rows past this CTA's targets stay zero)
+  for (uint32_t q = tid * 16u; q < L.mop; q += blockDim.x * 16u) *reinterpret_cast<uint4*>(smem + q) = make_uint4(0u, 0u, 0u, 0u);
+  // the split M as the A operand: 128 rows (rows past ntn zero); the global
+  // copy holds ntn rows, k-group stride ntn / 8 x 128 bytes
+  {
+    const int nkg = R.kpad * ESZ / 16, rgs = R.ntn / 8;
+    const size_t gpart = (size_t)R.b_tile_bytes / 2;
+    for (int u = tid; u < 2 * nkg * 128; u += blockDim.x) {
+      const int part = u / (nkg * 128), rem = u % (nkg * 128);
+      const int kg = rem / 128, rg = (rem / 8) % 16, rr = rem % 8;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (rg < rgs) v = __ldg(reinterpret_cast<const uint4*>(R.B + part * gpart + (size_t)(kg * rgs + rg) * 128 + rr * 16));
+      *reinterpret_cast<uint4*>(sMop + part * m_part + (uint32_t)kg * 2048u + (uint32_t)rg * 128u + (uint32_t)rr * 16u) = v;
+    }
+  }
   {
     const int cur0 = (int)(*(volatile int64_t*)&st->gen & 1);
     if (tid < kCtaRowsMax) {
@@ -239,18 +251,6 @@ __global__ void __launch_bounds__(256, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (tid == 0) {
-    // M split stays resident for the whole launch
-    mbar_expect_tx(bar_b, 2 * b_part);
-    bulk_g2s(smem_u32(sB), R.B, b_part, bar_b);
-    bulk_g2s(smem_u32(sB) + b_part, R.B + b_part, b_part, bar_b);
-    if (!mbar_wait(bar_b, 0u)) {
-      atomicOr(&st->err, kErrTimeout);
-      atomicExch(&ctl->abort, 1);
-      s_abort = 1;
-      s_bfail = 1;
-    }
-  }
   __syncthreads();
   const uint32_t tmem = s_tmem;
 
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(256, 1)
             y[e] = (j0 + e < d) ? to_f32_rn(shifted(t[e], osh[e], R)) : 0.f;
             yn2 += y[e] * y[e];
           }
-          cta_store_split4<ESZ>(sA, a_part, lr, j0, y);
+          cta_store_split4<ESZ>(sYop, y_part, lr, j0, y);
         }
         if (R.dbg_trial) trial_debug(R, (uint32_t)i, j0, lane, bits, t);
 #pragma unroll
@@ -423,50 +423,39 @@ __global__ void __launch_bounds__(256, 1)
     if (!ordered && s_stop) break;
     const double best_prev = s_best;
 
-    // ---- 2. split products on tcgen05
+    // ---- 2. split products on tcgen05: z = Mh yh + Ml yh + Mh yl, M as the
+    // 128-row A operand and the targets' y as the 16-row B operand
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int ksteps = R.kpad * ESZ / 32;
-      const uint32_t aa = smem_u32(sA), bb = smem_u32(sB);
+      const uint32_t mm = smem_u32(sMop), yy = smem_u32(sYop);
       for (int ks = 0; ks < ksteps; ++ks) {
 #pragma unroll
         for (int pass = 0; pass < 3; ++pass) {
-          const uint32_t a = aa + (pass == 2 ? a_part : 0u) + (uint32_t)ks * 512u;
-          const uint32_t b = bb + (pass == 1 ? b_part : 0u) + (uint32_t)ks * 2u * bk;
-          mma_split<ESZ>(tmem, smem_desc(a, 256u, 128u), smem_desc(b, bk, 128u), idesc, (ks > 0 || pass > 0) ? 1u : 0u);
+          const uint32_t a = mm + (pass == 1 ? m_part : 0u) + (uint32_t)ks * 4096u;
+          const uint32_t b = yy + (pass == 2 ? y_part : 0u) + (uint32_t)ks * 512u;
+          mma_split<ESZ>(tmem, smem_desc(a, 2048u, 128u), smem_desc(b, 256u, 128u), idesc,
+                         (ks > 0 || pass > 0) ? 1u : 0u);
         }
       }
       mma_commit(bar_mma);
     }
-    // ---- 3a. warps 0 and 4 copy the accumulator rows (TMEM lanes 0..31 ->
-    // shared memory): warp 0 the first half of the columns, warp 4 the rest
-    if ((warp & 3) == 0) {
+    // ---- 3a. every warp copies one block of the accumulator (TMEM lanes
+    // 32 (w mod 4) .. + 31 = coordinates j, columns 8 (w / 4) .. + 7 = targets)
+    // to shared memory as rows of z
+    {
       const bool ok = mbar_wait(bar_mma, mma_phase);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const bool have = __all_sync(0xffffffffu, ok);
-      if (have) {
-        const int half = R.ntn / 2;
-        const int cb = (warp >> 2) * half;
-        for (int c = 0; c < half; c += 32) {
-          float v[32];
-          const int w = min(32, half - c);
-          const uint32_t ta = tmem + (uint32_t)(cb + c);
-          if (w == 32) {
-            tmem_ld_cols32(ta, v);
-          } else if (w == 24) {
-            tmem_ld_cols16(ta, v);
-            tmem_ld8(ta + 16u, v + 16);
-          } else if (w == 16) {
-            tmem_ld_cols16(ta, v);
-          } else {
-            tmem_ld8(ta, v);
-          }
-          if (lane < rows) {
-            float* dst = zbuf + (size_t)lane * zs + cb + c;
+      const bool have_w = __all_sync(0xffffffffu, ok);
+      if (have_w) {
+        float v[8];
+        const int q = warp & 3, cb = (warp >> 2) * 8;
+        tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cb, v);
+        const int j = 32 * q + lane;
+        if (j < d) {
 #pragma unroll
-            for (int e = 0; e < 32; e += 4)
-              if (e < w) *reinterpret_cast<float4*>(dst + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-          }
+          for (int e = 0; e < 8; ++e)
+            if (cb + e < rows) zbuf[(size_t)(cb + e) * zs + j] = v[e];
         }
       } else if (lane == 0) {
         atomicOr(&st->err, kErrTimeout);
@@ -698,10 +687,7 @@ __global__ void __launch_bounds__(256, 1)
   }
   // copies and products still in flight after a failed wait must land
   // before the CTA leaves and frees its tensor memory (bounded waits)
-  if (tid == 0) {
-    if (s_bfail) mbar_wait(bar_b, 0u);
-    if (s_mfail) mbar_wait(bar_mma, (uint32_t)(s_mfail - 1));
-  }
+  if (tid == 0 && s_mfail) mbar_wait(bar_mma, (uint32_t)(s_mfail - 1));
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));

@@ -247,10 +247,11 @@ def test_persistent_rows_per_cluster_do_not_change_results(monkeypatch):
 def test_cta_local_rows_per_cta_do_not_change_results(monkeypatch):
     """The CTA-local persistent kernel's targets per CTA only change the
     tiling (NP = 120: 8 to 120 CTAs): after 150 generations every tiling
-    gives the same populations, fitness, counters and best records, and the
-    populations equal the cluster kernel's (both evaluate a row's FP32 terms
-    in the same order and take every undecidable comparison in FP64; FP64
-    values agree within 1e-12 of the term scale)."""
+    gives the same populations, fitness, counters and best records.  The
+    populations also equal the cluster kernel's: both take every undecidable
+    comparison in FP64.  Fitness kept from split-precision decisions agrees
+    within the split tolerance (the two kernels group the tensor-core
+    products of a coordinate differently)."""
     _need_gpu()
     d = 40
     o, M = problems.shift(d, seed=6), problems.rotation(d, seed=6)
@@ -276,7 +277,7 @@ def test_cta_local_rows_per_cta_do_not_change_results(monkeypatch):
         assert np.array_equal(b["best_x"], tiled[0][2]["best_x"]) and b["best_f"] == tiled[0][2]["best_f"]
         assert st == tiled[0][3]
         assert np.array_equal(x, ref[0])
-        assert np.allclose(f, ref[1], rtol=1e-10, atol=0)
+        assert np.allclose(f, ref[1], rtol=1e-5, atol=0)
         for key in ("generations", "evals", "best_index", "stop_reason"):
             assert b[key] == ref[2][key], key
         assert st["trials"] == ref[3]["trials"] == 120 * 150
