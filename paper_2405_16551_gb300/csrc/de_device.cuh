@@ -341,20 +341,63 @@ __host__ __device__ __forceinline__ long long ordered_key(double x) {
 
 // FP64 -> FP32 rounding to nearest, ties to even, on the integer pipe (the
 // conversion instruction occupies the FP64 pipe, which bounds the trial
-// kernels on this part): the 29 dropped significand bits decide the
-// increment, whose carry runs into the exponent field (and to infinity past
-// the largest float).  Zero, subnormal, infinite and NaN inputs and results
-// below the normal float range take the hardware conversion.
+// kernels on this part).  Normal results: the 29 dropped significand bits
+// decide the increment, whose carry runs into the exponent field (and to
+// infinity past the largest float).  Results below the normal range: the
+// 53-bit significand shifted to units of 2^-149 with the same rounding (a
+// carry gives the smallest normal).  Infinities and NaNs stay so; finite
+// inputs beyond the float range round to infinity.
 __device__ __forceinline__ float to_f32_rn(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
-  if (e < 1 || e > 254) return (float)x;
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const int e = ex - 1023 + 127;
   const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
-  const unsigned int mant = (unsigned int)(m >> 29);
-  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFULL);
-  unsigned int r = ((unsigned int)(b >> 63) << 31) | ((unsigned int)e << 23) | mant;
-  if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) r += 1u;
+  unsigned int r;
+  if (e >= 1 && e <= 254) {
+    const unsigned int mant = (unsigned int)(m >> 29);
+    const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFULL);
+    r = sign | ((unsigned int)e << 23) | mant;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) r += 1u;
+  } else if (ex == 0x7FF) {
+    r = sign | 0x7F800000u | (m ? 0x400000u | (unsigned int)(m >> 29) : 0u);
+  } else if (e > 254) {
+    r = sign | 0x7F800000u;
+  } else {
+    // x = (2^52 + m) 2^(ex - 1075); in units of 2^-149 that is a right shift
+    // by sh = 926 - ex >= 30 bits (double subnormals are far below 2^-150)
+    const int sh = 926 - ex;
+    unsigned int k = 0u;
+    if (ex != 0 && sh < 64) {
+      const unsigned long long sig = (1ULL << 52) | m;
+      const unsigned long long rem = sig & ((1ULL << sh) - 1ULL), half = 1ULL << (sh - 1);
+      k = (unsigned int)(sig >> sh);
+      if (rem > half || (rem == half && (k & 1u))) k += 1u;
+    }
+    r = sign | k;
+  }
   return __uint_as_float(r);
+}
+
+// FP32 -> FP64 (exact) on the integer pipe.
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int ex = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long m = u & 0x7FFFFFu;
+  unsigned long long r;
+  if (ex != 0u && ex != 0xFFu) {
+    r = sign | ((unsigned long long)(ex + 896u) << 52) | (m << 29);
+  } else if (ex == 0xFFu) {
+    r = sign | (0x7FFULL << 52) | (m << 29);
+  } else if (m == 0u) {
+    r = sign;
+  } else {
+    // subnormal: m 2^-149 with the leading one at bit p
+    const int p = 31 - __clz((unsigned int)m);
+    r = sign | ((unsigned long long)(p - 149 + 1023) << 52) | ((m << (52 - p)) & 0xFFFFFFFFFFFFFULL);
+  }
+  return __longlong_as_double((long long)r);
 }
 
 // y = (t - o) s, rounded once per operation as written

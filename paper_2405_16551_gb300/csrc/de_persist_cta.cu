@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(256, 1)
   RunState* st = R.st;
   const int d = R.d, dp = R.dp, np = R.np, obj = R.obj;
   const int row0 = cta * rows;
+  const bool has_target = R.target > 0.0;
+  const float target_f = (float)R.target * 1.001f;
 
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_bar[2];
@@ -187,6 +189,8 @@ __global__ void __launch_bounds__(256, 1)
   __shared__ int s_nb, s_stop, s_abort, s_bidx, s_have, s_mfail;
   __shared__ long long s_gen;
   __shared__ double s_best;
+  __shared__ float s_bestf;                 // s_best rounded to FP32 (the decisions run in FP32)
+  __shared__ long long s_key[kCtaRowsMax];  // ordered key of s_f (best-partial scan)
   __shared__ unsigned long long s_nband_total;
 
   const CtaLayout L = cta_layout(R);
@@ -199,18 +203,22 @@ __global__ void __launch_bounds__(256, 1)
   double* s_red = reinterpret_cast<double*>(smem + L.red);
 
   const uint32_t bar_mma = smem_u32(&s_bar[1]);
-  const uint32_t ncols = 32u;  // the accumulator: 128 lanes x 16 columns (the smallest allocation)
+  // three accumulators of 128 lanes x 16 columns, one per split pass: warps
+  // 0, 1 and 2 issue the passes at the same time (one thread issues a product
+  // only every several tens of cycles); z is their sum in pass order
+  const uint32_t ncols = 64u;
   const uint32_t fmt = ESZ == 2 ? 1u : 2u;
   const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kCtaRowsMax >> 3) << 17) |
                          ((uint32_t)(kTileM >> 4) << 24);
 
   // ---------------------------------------------------------------- set-up
   if (tid == 0) {
-    mbar_init(bar_mma, 1);
+    mbar_init(bar_mma, 3);  // one commit per issuing warp
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_gen = *(volatile int64_t*)&st->gen;
     s_stop = *(volatile int32_t*)&st->stop;
     s_best = *(volatile double*)&st->best_f;
+    s_bestf = to_f32_rn(s_best);
     s_bidx = max(*(volatile int32_t*)&st->best_idx, 0);  // DE/best/1 base (row 0 when none is finite)
     s_abort = 0;
     s_mfail = 0;
@@ -246,6 +254,7 @@ __global__ void __launch_bounds__(256, 1)
       s_fx[tid] = mine ? R.fx[cur0][i] : 1;
       s_tau[tid] = mine ? R.tau[i] : 0.f;
       s_yn[tid] = 0.f;
+      s_key[tid] = fit_key(s_f[tid]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -303,6 +312,7 @@ __global__ void __launch_bounds__(256, 1)
         else if (gen >= R.max_gens) sp = 3;
         s_stop = sp;
         s_best = bf;
+        s_bestf = to_f32_rn(bf);
         if (bi >= 0) s_bidx = bi;
         s_gen = gen;
         if (cta == 0) {
@@ -421,23 +431,21 @@ __global__ void __launch_bounds__(256, 1)
     // otherwise the stop rule of generation gen was reduced meanwhile; a
     // stopped run leaves before anything of generation g is written
     if (!ordered && s_stop) break;
-    const double best_prev = s_best;
+    const float bp = s_bestf;
 
     // ---- 2. split products on tcgen05: z = Mh yh + Ml yh + Mh yl, M as the
     // 128-row A operand and the targets' y as the 16-row B operand
-    if (tid == 0) {
+    if (warp < 3 && lane == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int ksteps = R.kpad * ESZ / 32;
-      const uint32_t mm = smem_u32(sMop), yy = smem_u32(sYop);
-      for (int ks = 0; ks < ksteps; ++ks) {
-#pragma unroll
-        for (int pass = 0; pass < 3; ++pass) {
-          const uint32_t a = mm + (pass == 1 ? m_part : 0u) + (uint32_t)ks * 4096u;
-          const uint32_t b = yy + (pass == 2 ? y_part : 0u) + (uint32_t)ks * 512u;
-          mma_split<ESZ>(tmem, smem_desc(a, 2048u, 128u), smem_desc(b, 256u, 128u), idesc,
-                         (ks > 0 || pass > 0) ? 1u : 0u);
-        }
-      }
+      const int pass = warp;
+      // descriptors of the operands' first K step; a byte offset enters the
+      // 14-bit address field (16-byte units) and never carries out of it
+      const uint64_t dm = smem_desc(smem_u32(sMop) + (pass == 1 ? m_part : 0u), 2048u, 128u);
+      const uint64_t dy = smem_desc(smem_u32(sYop) + (pass == 2 ? y_part : 0u), 256u, 128u);
+      for (int ks = 0; ks < ksteps; ++ks)
+        mma_split<ESZ>(tmem + 16u * (uint32_t)pass, dm + (uint64_t)(ks * 256), dy + (uint64_t)(ks * 32), idesc,
+                       ks > 0 ? 1u : 0u);
       mma_commit(bar_mma);
     }
     // ---- 3a. every warp copies one block of the accumulator (TMEM lanes
@@ -448,9 +456,14 @@ __global__ void __launch_bounds__(256, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const bool have_w = __all_sync(0xffffffffu, ok);
       if (have_w) {
-        float v[8];
+        float v[8], w1[8], w2[8];
         const int q = warp & 3, cb = (warp >> 2) * 8;
-        tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cb, v);
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cb;
+        tmem_ld8(ta, v);
+        tmem_ld8(ta + 16u, w1);
+        tmem_ld8(ta + 32u, w2);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (v[e] + w1[e]) + w2[e];
         const int j = 32 * q + lane;
         if (j < d) {
 #pragma unroll
@@ -481,10 +494,15 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
         acc_.a1 += __shfl_xor_sync(0xffffffffu, acc_.a1, o);
-        acc_.a2 += __shfl_xor_sync(0xffffffffu, acc_.a2, o);
-        acc_.a3 += __shfl_xor_sync(0xffffffffu, acc_.a3, o);
         acc_.aS += __shfl_xor_sync(0xffffffffu, acc_.aS, o);
         acc_.aG += __shfl_xor_sync(0xffffffffu, acc_.aG, o);
+      }
+      if (obj == kObjAckley) {  // the other objectives leave these two at zero
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          acc_.a2 += __shfl_xor_sync(0xffffffffu, acc_.a2, o);
+          acc_.a3 += __shfl_xor_sync(0xffffffffu, acc_.a3, o);
+        }
       }
       if (sub == 0) {
         uint8_t flag = 0;
@@ -502,19 +520,20 @@ __global__ void __launch_bounds__(256, 1)
             if (obj != kObjRastrigin) S = s1;
             fs = s1;
           }
+          // FP32 throughout; the FP64 values are converted on the integer
+          // pipe (the FP64 pipe is the trial construction's bottleneck)
           const float tau = 2.f * R.band_u * G * R.rownorm * s_yn[rr] + (float)d * 0x1.0p-21f * S + 1e-30f;
-          const double fi = s_f[rr];
-          const float fif = (float)fi;
+          const float fif = to_f32_rn(s_f[rr]);
           const float tif = s_fx[rr] ? 0.f : s_tau[rr];
           const float mrg = 0x1.0p-22f * fabsf(fif);
-          const float bp = (float)best_prev;
           const bool sure_reject = fs - tau > fif + tif + mrg;
           const bool sure_accept = fs + tau < fif - tif - mrg;
           const bool ambiguous = !sure_reject && !sure_accept;
           const bool may_be_best = R.band_all && fs - tau <= bp + 0x1.0p-22f * fabsf(bp);
           const bool near = fs - tau <= R.near_thr || fif - tif <= R.near_thr;
-          const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f;
-          s_ft[rr] = (double)fs;
+          const bool may_stop = has_target && fs - tau < target_f;
+          const double fsd = f64_of_f32(fs);
+          s_ft[rr] = fsd;
           if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !(fif == fif)) {
             s_blist[atomicAdd(&s_nb, 1)] = rr;
             flag = 4;
@@ -522,7 +541,8 @@ __global__ void __launch_bounds__(256, 1)
             // decided on the split values (an undecidable comparison far from
             // the optimum goes to the smaller split value, ties to the trial)
             flag = 1;
-            s_f[rr] = (double)fs;
+            s_f[rr] = fsd;
+            s_key[rr] = fit_key(fsd);
             s_fx[rr] = 0;
             s_tau[rr] = tau;
           }
@@ -555,6 +575,7 @@ __global__ void __launch_bounds__(256, 1)
         const bool acc = fit_key(ft) <= fit_key(fi) && fit_key(ft) != 0x7FFFFFFFFFFFFFFFLL;  // NaN ranks last
         s_ft[lr] = ft;
         s_f[lr] = acc ? ft : fi;
+        s_key[lr] = fit_key(acc ? ft : fi);
         s_fx[lr] = 1;
         s_tau[lr] = 0.f;
         s_flag[lr] = (acc ? 1 : 0) | 2;
@@ -590,24 +611,25 @@ __global__ void __launch_bounds__(256, 1)
       }
     }
     rows_in_regs = true;
-    if (warp == 0) {
-      Best b;
-      b.init();
-      if (lane < rows && row0 + lane < np) {
-        const int i = row0 + lane;
-        b.offer(s_f[lane], i);
-        if (R.dbg_ftrial) {
-          R.dbg_ftrial[i] = s_ft[lane];
-          R.dbg_accept[i] = s_flag[lane] & 1;
-          R.dbg_fp64[i] = (s_flag[lane] >> 1) & 1;
+    if (tid == 0) {
+      // the CTA's best (lowest key, then lowest index; NaN never): a scan of
+      // at most 16 precomputed keys
+      long long bk = 0x7FFFFFFFFFFFFFFFLL;
+      int bi = -1;
+      for (int r = 0; r < rows && row0 + r < np; ++r)
+        if (s_key[r] != 0x7FFFFFFFFFFFFFFFLL && (bi < 0 || s_key[r] < bk)) {
+          bk = s_key[r];
+          bi = r;
         }
-      }
-      b.warp_reduce();
-      if (lane == 0) {
-        BestPartial* pp = R.part + (size_t)(g & 1) * nct + cta;
-        pp->f = b.f;
-        pp->idx = b.i;
-      }
+      BestPartial* pp = R.part + (size_t)(g & 1) * nct + cta;
+      pp->f = bi >= 0 ? s_f[bi] : CUDART_INF;
+      pp->idx = bi >= 0 ? row0 + bi : -1;
+    }
+    if (R.dbg_ftrial && warp == 0 && lane < rows && row0 + lane < np) {
+      const int i = row0 + lane;
+      R.dbg_ftrial[i] = s_ft[lane];
+      R.dbg_accept[i] = s_flag[lane] & 1;
+      R.dbg_fp64[i] = (s_flag[lane] >> 1) & 1;
     }
     __syncthreads();  // every row and the partial are written
 
@@ -619,8 +641,9 @@ __global__ void __launch_bounds__(256, 1)
       bool ok = s_abort == 0;
       if (ok) {
         if (lane == 0) {
-          __threadfence();
-          atomicAdd(&ctl->sbar[cta & 7][0], 1u);
+          // release: this CTA's rows and partial (ordered before by the CTA
+          // barrier) are visible to every CTA that observes the count
+          asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&ctl->sbar[cta & 7][0]), "r"(1u) : "memory");
         }
         __syncwarp();
         const unsigned mine = lane < 8 ? (unsigned)((nct - lane + 7) / 8) : 0u;  // CTAs counted by counter `lane`
