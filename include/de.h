@@ -151,10 +151,13 @@ typedef enum {
  *   FP64     DFMA on CUDA cores, FP64 terms.
  *   BF16X3   tcgen05 tensor cores: y and M split into bf16 high and low parts,
  *            z = yh Mh + yh Ml + yl Mh accumulated in FP32 (TMEM); FP32 terms.
- *   TF32X3   the same with tf32 parts.
- * In BF16X3/TF32X3 the selection comparison is redone in FP64 as de_fp64_band
- * says, and the best-so-far record returned by de_get_best / de_run is the
- * FP64 fitness of the best individual. */
+ *            About 16 bits of y and M take part (2^-16 relative per product).
+ *   TF32X3   the same with tf32 parts (22 bits, 2^-22 per product).
+ * The split forms are the library's FP32-class arithmetic: there is no plain
+ * FP32 form, because the rotation is a dense contraction that runs on the
+ * tensor cores.  In BF16X3/TF32X3 the selection comparison is redone in FP64
+ * as de_fp64_band says, and the best-so-far record returned by de_get_best /
+ * de_run is the FP64 fitness of the best individual. */
 typedef enum {
     DE_PREC_FP64 = 0,
     DE_PREC_BF16X3 = 1,
@@ -178,7 +181,10 @@ typedef struct {
     int32_t objective;        /* de_objective */
     double scale;             /* y = (x - o) * scale; 1.0 keeps the search range (Sec. 7.3.1) */
     const double* shift;      /* host, d values of o (composition functions: n*d, one row per
-                                 component), or NULL for o = 0; copied by de_init */
+                                 component), or NULL for o = 0; copied by de_init.  The problem
+                                 data of Sec. 7.3.1 is the caller's: it is passed, not drawn
+                                 by the library, so that any other program (a CPU reference,
+                                 another run) can be given the very same arrays */
     const double* rot;        /* host, d*d row-major M (z = M y; composition functions: n such
                                  matrices), or NULL for no rotation; copied */
     uint64_t seed;            /* Philox key */
@@ -305,25 +311,43 @@ DE_API de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_
 DE_API de_status de_init_islands(const de_config* cfg, int32_t nislands, int32_t interval, int32_t migrants,
                                  void* cuda_stream, de_handle** out);
 
-/* Re-initialise run `run` (or every run when run == -1) as de_init did:
- * population from the INIT stream, evaluation, counters and best record
- * reset.  Enqueued on the handle's stream; allocates nothing. */
+/* Re-initialise run `run` (or every run when run == -1) as de_init did
+ * (Sec. 2, initialisation): population from the INIT stream, evaluation,
+ * counters and best record reset.  Enqueued on the handle's stream;
+ * allocates nothing. */
 DE_API de_status de_reset(de_handle* h, int32_t run);
 
 /* Enqueue `generations` generations (>= 0) on the handle's stream, with no
  * stop test other than the per-run stop flags the device sets itself.
- * Generation g builds every trial from the generation g-1 population
- * (synchronous replacement).  Returns once the work is enqueued. */
+ * One generation is the loop of Sec. 2: per target the mutant of Eq. 2, the
+ * crossover of Eq. 3, bound repair, the objective of Sec. 7.3.1 and greedy
+ * selection (Sec. 2, Selection; Sec. 6.2.5), then the best-so-far record and
+ * the stopping rule of Sec. 7.3.4.  Generation g builds every trial from the
+ * generation g-1 population (synchronous replacement, as the kernel-per-
+ * operation GPU designs of Sec. 5.3 and Sec. 6.1 do).  A trial whose
+ * objective is NaN never replaces its target, and any trial replaces a
+ * target whose objective is NaN (NaN ranks below every number).
+ * Returns once the work is enqueued; a device-side error shows at the next
+ * synchronising call (DE_ERR_TIMEOUT, DE_ERR_NONFINITE). */
 DE_API de_status de_step(de_handle* h, int64_t generations);
 
-/* Run until every run has stopped (target, evaluation budget or
- * max_generations), checking the stop flags between CUDA-graph launches.
- * out: host array of nruns results (may be NULL).  Synchronises. */
+/* Run until every run has stopped under the stopping rule of Sec. 7.3.4
+ * (best f below target_error, or the evaluation budget max_evals, counting
+ * the initial population) or after max_generations, checking the stop flags
+ * between launches.  out: host array of nruns results (may be NULL).
+ * Synchronises.
+ * Errors: DE_ERR_TIMEOUT (a bounded device-side wait gave up; the run's
+ * population is then undefined until de_reset), DE_ERR_NONFINITE (every
+ * fitness of a run is NaN), DE_ERR_CUDA. */
 DE_API de_status de_run(de_handle* h, de_result* out);
 
-/* Evaluate n rows with run `run`'s objective, shift, rotation and precision.
- * x_dev: device, n rows of d doubles with row stride ld (>= d) doubles.
- * f_dev: device, n doubles.  Both caller-owned; enqueued on the stream. */
+/* Evaluate n rows with run `run`'s objective, shift, rotation and precision:
+ * the function evaluation of Sec. 6.2.2 on the objectives of Sec. 7.3.1
+ * (y = (x - o) scale, z = M y, then the basic, hybrid or composition
+ * function).  x_dev: device, n rows of d doubles with row stride ld (>= d)
+ * doubles.  f_dev: device, n doubles.  Both caller-owned; enqueued on the
+ * stream.  In a split precision, a row whose bounded device-side wait gave up
+ * (it should not on a healthy device) comes back as NaN. */
 DE_API de_status de_eval(de_handle* h, int32_t run, const double* x_dev, int64_t ld, int32_t n, double* f_dev);
 
 /* ---- evaluation without a handle and without allocation ----------------
@@ -347,16 +371,22 @@ DE_API de_status de_eval(de_handle* h, int32_t run, const double* x_dev, int64_t
  * each call writes every part it uses before reading it.  Rows past n in the
  * last 128-row tile are computed on but never reach f_dev.
  *
- * Limit: the scratch bounds n per call.  A call needs about 1 KiB, plus
- * 2 e npad kpad bytes for M, plus 256 e kpad + 520 bytes per 128 rows, where:
+ * Limit: the scratch bounds d and n per call.  A call needs about 1 KiB,
+ * plus 2 e npad kpad bytes for M, plus 256 e kpad + 520 bytes per 128 rows,
+ * where:
  *   e = 2 for BF16X3, 4 for TF32X3;
  *   kpad = d rounded up to 16;
  *   npad = kpad for d <= 256, else d rounded up to 256.
- * The largest n per call (BF16X3 / TF32X3):
+ * The largest d is 1920 (BF16X3) / 1280 (TF32X3); a larger d returns
+ * DE_ERR_INVALID_ARG naming that limit.  The largest n per call
+ * (BF16X3 / TF32X3):
  *   d = 10: 246,400 / 126,976     d = 30: 126,976 / 64,384
  *   d = 100: 36,992 / 18,432      d = 1000: 3,072 / 1,024
  * A larger n returns DE_ERR_INVALID_ARG, naming the largest n for that d and
  * precision, and launches nothing.
+ * A bounded device-side wait that gives up (it should not on a healthy
+ * device) cannot be reported by the call, which has returned by then: the
+ * rows of the affected 128-row tiles come back as NaN.
  *
  * First call: the first call on each device looks up the scratch's address
  * (cudaGetSymbolAddress), with that device current.  This may also load the
@@ -372,7 +402,8 @@ DE_API de_status de_eval(de_handle* h, int32_t run, const double* x_dev, int64_t
  * precision: DE_PREC_BF16X3 or DE_PREC_TF32X3.  DE_PREC_FP64 returns
  *   DE_ERR_UNSUPPORTED (use de_eval, which needs no scratch for FP64).
  * objective: DE_OBJ_SPHERE .. DE_OBJ_ACKLEY.  Rosenbrock needs d <= 256.
- * d: 1..4096.  scale: finite and nonzero (y = (x - o) scale).
+ * d: 1..1920 (BF16X3) or 1..1280 (TF32X3).  scale: finite and nonzero
+ *   (y = (x - o) scale).
  * shift_dev: device, d doubles, or NULL for o = 0.
  * rot_dev: device, d*d doubles row-major (z_j = sum_k M[j][k] y_k), or NULL
  *   for M = I.
@@ -453,16 +484,20 @@ DE_API de_status de_get_surrogate_stats(de_handle* h, int64_t* trainings, int64_
                                         double* last_rho, int32_t* k_now);
 
 /* Copy run `run`'s current population (np*d, host) and fitness (np, host)
- * out; either pointer may be NULL.  Synchronises. */
+ * out (the population and objective values of Sec. 2); either pointer may be
+ * NULL.  Synchronises. */
 DE_API de_status de_get_population(de_handle* h, int32_t run, double* x_host, double* f_host);
 
-/* Replace run `run`'s population and fitness with host arrays (np*d, np).
- * f_host may be NULL, in which case the population is evaluated on the
- * device.  Resets that run's stop flag and recomputes its best record; the
- * generation counter is kept. */
+/* Replace run `run`'s population and fitness with host arrays (np*d, np)
+ * (the population of Sec. 2).  x_host must be finite (DE_ERR_NONFINITE
+ * otherwise); f_host may hold NaN, and may be NULL, in which case the
+ * population is evaluated on the device.  Resets that run's stop flag and
+ * recomputes its best record (Sec. 7.3.4); the generation counter is kept. */
 DE_API de_status de_set_population(de_handle* h, int32_t run, const double* x_host, const double* f_host);
 
-/* Set the generation counter of run `run` (the next de_step runs g + 1). */
+/* Set the generation counter of run `run` (the next de_step runs g + 1).
+ * The counter selects the random numbers of a generation (Philox counter) and
+ * the evaluation count NP (1 + g) of the stopping rule (Sec. 7.3.4). */
 DE_API de_status de_set_generation(de_handle* h, int32_t run, int64_t generation);
 
 /* jDE state of run `run` (cfg.jde set): the per-individual F_i and CR_i of
@@ -482,13 +517,17 @@ DE_API de_status de_set_adaptive(de_handle* h, int32_t run, const double* f_host
  * current device. */
 DE_API int64_t de_selftest_f32_rounding(const double* x_host, int64_t n);
 
-/* Best record of run `run`: best_f, its index, a copy of its vector
- * (host, d doubles, may be NULL), and generation/evaluation counters. */
+/* Best record of run `run` (the best-so-far solution that the stopping rule
+ * of Sec. 7.3.4 tests): best_f, its index (lowest index on ties), a copy of
+ * its vector (host, d doubles, may be NULL), and generation/evaluation
+ * counters. */
 DE_API de_status de_get_best(de_handle* h, int32_t run, double* best_f, int32_t* best_index, double* best_x,
                       int64_t* generations, int64_t* evals, int32_t* stop_reason);
 
 /* Copy the last generation's debug capture of run `run` (cfg.debug_capture
- * must have been set).  Synchronises. */
+ * must have been set): the mutant indices r1, r2, r3 of Eq. 2, j_rand and the
+ * crossover mask of Eq. 3, the repaired trials, their fitness and the
+ * selection decisions (Sec. 2, Selection).  Synchronises. */
 DE_API de_status de_get_debug(de_handle* h, int32_t run, const de_debug* out);
 
 /* Number of runs in the handle, and run `run`'s np and d. */
@@ -499,6 +538,10 @@ DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d
  *   1  split precision, three kernels per generation (trial, tensor-core
  *      fitness and selection, FP64 band), in CUDA graphs
  *   2  split precision, one persistent cluster kernel for many generations
+ *   4  split precision, one cooperative persistent kernel for many
+ *      generations in which every CTA owns at most 16 targets and runs their
+ *      tensor-core products itself (a grid barrier between generations, no
+ *      clusters); single runs of d <= 128 whose CTAs all fit at once
  *   3  FP64, one cooperative persistent kernel for many generations of
  *      every run of the handle (grid barrier between generations; the same
  *      numbers as path 0; not with islands or a surrogate, and only when
@@ -511,8 +554,14 @@ DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d
  * path 3 launched as one cluster, else 0;
  * each cluster owns up to 128 targets (a multiple of the cluster size, timed
  * at de_init; DE_GB300_PERSIST_ROWS fixes it).
- * Path 2 is chosen at de_init for a single run whose clusters all fit on the
- * device at once; the environment variable DE_GB300_PERSIST=0 disables it. */
+ * Paths 2 and 4 apply to a single run of d <= 128; de_init times both and
+ * keeps the faster (DE_GB300_PERSIST_MODE=cluster / cta keeps one form,
+ * DE_GB300_PERSIST_CTA_ROWS fixes the targets per CTA of path 4); the
+ * environment variable DE_GB300_PERSIST=0 disables both.
+ * Test switch (failure detection, off by default): DE_GB300_TEST_GRID_TIMEOUT=k
+ * at de_init makes CTA k - 1 of every path-3 launch leave out its first
+ * grid-barrier arrival and the barrier give up after a few thousand polls, so
+ * that the bounded wait runs out and de_run returns DE_ERR_TIMEOUT. */
 DE_API de_status de_get_plan(de_handle* h, int32_t* kernel_path, int32_t* cluster_size);
 
 /* Counters of the split-precision selection of run `run` since de_init:
@@ -521,11 +570,19 @@ DE_API de_status de_get_plan(de_handle* h, int32_t* kernel_path, int32_t* cluste
  * precision, where every comparison is FP64. */
 DE_API de_status de_get_stats(de_handle* h, int32_t run, int64_t* fp64_reevals, int64_t* trials);
 
-/* Write the full state of every run (population, fitness, counters, best
- * records, problem data) to `path`, with a CRC32 over the payload; de_load
- * restores it into a handle created with the same configurations.
- * Errors: DE_ERR_IO (open/write/read failure, bad magic, CRC mismatch),
- * DE_ERR_STATE (shapes differ from the handle's). */
+/* Write the state of every run (population, fitness, jDE parameters,
+ * counters, best record: the state of the loop of Sec. 2 at a generation
+ * boundary) to `path`, with a CRC32 over the payload and, per run, a 64-bit
+ * hash of the problem (objective, F, CR, bounds, scale, seed, run_id,
+ * precision, strategy, jDE, FP64 band policy, shift, rotation and
+ * permutation).  de_load restores it into a handle created with the same
+ * configurations; the stopping limits (target_error, max_evals,
+ * max_generations) may differ.  de_load parses and checks the whole file on
+ * the host before it copies anything to the device, so a refused file leaves
+ * the handle unchanged.
+ * Errors: DE_ERR_IO (open/write/read failure, bad magic, CRC mismatch,
+ * truncation), DE_ERR_STATE (a run's shape or problem differs from the
+ * handle's). */
 DE_API de_status de_save(de_handle* h, const char* path);
 DE_API de_status de_load(de_handle* h, const char* path);
 
