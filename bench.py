@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     p.add_argument("--workload", default="rastrigin",
                    choices=["rastrigin", "sphere_small", "batch512", "ode_surrogate", "stress", "stress_batch",
-                            "variants", "suite", "islands"],
+                            "variants", "suite", "islands", "accuracy"],
                    help="rastrigin: the headline configuration (default); the others measure the batched, "
                         "surrogate and large-dimension configurations with the same harness")
     return p.parse_args()
@@ -617,6 +617,8 @@ def run_workload(args, capi, torch, rank, world):
                     config={"workload": f"F03 D=30, {G} generations, 3 seeds; islands vs no migration vs one "
                                         "population of 1024", "l2": "working set in L2"},
                     forms=forms, gpu_launches=None)
+    elif args.workload == "accuracy":
+        line.update(accuracy_workload(capi, torch, stream, problems))
     elif args.workload == "stress_batch":
         # 64 runs of the large-dimension shape in one handle (working set far above L2)
         G = min(args.generations, 10)
@@ -653,6 +655,121 @@ def run_workload(args, capi, torch, rank, world):
                     tensor_tflops=flops / (ms / 1e3) / 1e12, gpu_launches=steps * (3 + 3 * G))
     line["clocks"] = clocks.stop()
     return line
+
+
+def accuracy_workload(capi, torch, stream, problems):
+    """The mixed-precision and batched forms against plain FP64 GPU DE at a
+    stated final error (the stopping rule of Sec. 7.3.4): wall time and true
+    objective evaluations to reach it.
+
+    * rotated sphere, NP = 1024, D = 100, F = 0.5, CR = 0.9, run to f < 1e-8
+      in FP64, BF16x3 and TF32x3 (5 seeds);
+    * rotated Rastrigin, the same shape: FP64 runs 3000 generations; each
+      split form then runs (up to 9000 generations) until its best is below
+      the FP64 run's final error (3 seeds);
+    * the 512-run batch (first 32 runs, FP64, 200 generations) in one handle
+      against the same runs one handle at a time: the final errors are equal
+      (checked, run by run), so the comparison is the time alone.
+    Times are device time (CUDA events around de_reset + de_run) and wall
+    time of de_run; evaluations are NP (1 + generations), plus the split
+    forms' FP64 re-evaluations, reported separately."""
+    n, d = 1024, 100
+
+    def run_to(obj, seed, prec, target, gens):
+        o, M = problems.shift(d, seed=seed), problems.rotation(d, seed=seed)
+        c = capi.make_config(n, d, objective=obj, shift=o, rot=M, seed=seed, precision=prec, target_error=target,
+                             max_generations=gens)
+        h = capi.de_init(c, stream=stream.cuda_stream)
+        try:
+            capi.de_run(h)  # warm-up (kernel load, autotuner cache)
+            torch.cuda.synchronize()
+            st0 = capi.de_get_stats(h)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            capi.de_reset(h)
+            t0 = time.perf_counter()
+            r = capi.de_run(h)[0]
+            wall = time.perf_counter() - t0
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = capi.de_get_stats(h)
+            return {"seconds": e0.elapsed_time(e1) / 1e3, "wall_s": wall, "generations": r["generations"],
+                    "evals": r["evals"], "fp64_reevals": st["fp64_reevals"] - st0["fp64_reevals"], "best_f": r["best_f"],
+                    "reached": r["stop_reason"] == capi.DE_STOP_TARGET, "kernel_path": capi.de_get_plan(h)["kernel_path"]}
+        finally:
+            capi.de_destroy(h)
+
+    def summary(runs):
+        t = [r["seconds"] for r in runs]
+        ev = [r["evals"] for r in runs]
+        return {"runs": runs, "median_s": float(np.median(t)), "median_evals": float(np.median(ev)),
+                "all_reached": all(r["reached"] for r in runs)}
+
+    out = {}
+    # 1. rotated sphere to 1e-8
+    sph = {}
+    for name in ("fp64", "bf16x3", "tf32x3"):
+        sph[name] = summary([run_to(0, seed, PREC_NAMES[name], 1e-8, 20000) for seed in (1, 2, 3, 4, 5)])
+    for name in sph:
+        sph[name]["speedup_time_vs_fp64"] = sph["fp64"]["median_s"] / sph[name]["median_s"]
+        sph[name]["evals_ratio_vs_fp64"] = sph[name]["median_evals"] / sph["fp64"]["median_evals"]
+    out["rotated_sphere_to_1e-8"] = sph
+    # 2. rotated Rastrigin to the FP64 run's final error after 3000 generations
+    ras = {"fp64_3000_generations": [], "bf16x3": [], "tf32x3": []}
+    for seed in (1, 2, 3):
+        ref = run_to(1, seed, 0, 0.0, 3000)
+        ras["fp64_3000_generations"].append(ref)
+        for name in ("bf16x3", "tf32x3"):
+            r = run_to(1, seed, PREC_NAMES[name], ref["best_f"], 9000)
+            r["target"] = ref["best_f"]
+            r["speedup_time_vs_fp64"] = ref["seconds"] / r["seconds"]
+            r["evals_ratio_vs_fp64"] = r["evals"] / ref["evals"]
+            ras[name].append(r)
+    for name in ("bf16x3", "tf32x3"):
+        ras[name + "_median_speedup_time"] = float(np.median([r["speedup_time_vs_fp64"] for r in ras[name]]))
+        ras[name + "_median_evals_ratio"] = float(np.median([r["evals_ratio_vs_fp64"] for r in ras[name]]))
+        ras[name + "_all_reached"] = all(r["reached"] for r in ras[name])
+    out["rotated_rastrigin_to_fp64_final_error"] = ras
+    # 3. batch vs one run at a time, equal final errors
+    shapes = problems.batch_shapes(512, seed=1)[:32]
+    G = 200
+    cfgs = [capi.make_config(nn, dd, objective=obj, shift=problems.shift(dd, seed=1, run_id=r),
+                             rot=problems.rotation(dd, seed=1, run_id=r), seed=1, run_id=r, target_error=0.0,
+                             max_generations=G) for r, (nn, dd, obj) in enumerate(shapes)]
+    hb = capi.de_init_batch(cfgs, stream=stream.cuda_stream)
+    capi.de_run(hb, len(cfgs))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    capi.de_reset(hb, -1)
+    rb = capi.de_run(hb, len(cfgs))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    capi.de_destroy(hb)
+    t_seq, same = 0.0, True
+    for r, c in enumerate(cfgs):
+        h = capi.de_init(c, stream=stream.cuda_stream)
+        capi.de_run(h)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        capi.de_reset(h)
+        rs = capi.de_run(h)[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_seq += e0.elapsed_time(e1) / 1e3
+        same = same and rs["best_f"] == rb[r]["best_f"] and rs["generations"] == rb[r]["generations"]
+        capi.de_destroy(h)
+    out["batch_vs_one_at_a_time"] = {"runs": len(cfgs), "generations": G, "batched_s": t_batch,
+                                     "one_at_a_time_s": t_seq, "speedup_time": t_seq / t_batch,
+                                     "final_errors_identical": same,
+                                     "trials": sum(nn for nn, _, _ in shapes) * G}
+    return dict(metric="wall-time speedup over plain FP64 GPU DE to f < 1e-8, rotated sphere NP=1024 D=100 (BF16x3)",
+                value=sph["bf16x3"]["speedup_time_vs_fp64"], unit="x", ms_per_step=1e3 * sph["bf16x3"]["median_s"],
+                dtype="f64 / bf16x3 / tf32x3 forms compared",
+                config={"workload": "rotated sphere and rotated Rastrigin NP=1024 D=100 F=0.5 CR=0.9 to a stated "
+                                    "error; 32 batch runs FP64 200 generations", "l2": "working set in L2"},
+                forms=out, gpu_launches=None)
 
 
 # DRAM traffic of one launch of the dominant kernel, from an ncu capture

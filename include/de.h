@@ -233,9 +233,12 @@ typedef enum {
 /* When the split precisions redo a selection comparison in FP64.
  *   DE_BAND_NEAR (default)  the split values cannot decide it within their
  *                           error bound and one of the two values is near the
- *                           optimum (below target_error / (8 u), u the unit
- *                           error of the split product), or the trial could
- *                           meet the stop target; elsewhere the split values
+ *                           optimum (below min(target_error, 1e-8) / (8 u), u
+ *                           the unit error of the split product), or the
+ *                           trial's error bound straddles the stop target
+ *                           (the stop rule of Sec. 7.3.4 is then decided in
+ *                           FP64; a trial surely below or above the target
+ *                           decides it on its split value); elsewhere the split values
  *                           decide, and a decision may then differ from the
  *                           FP64 one only inside the split error bound
  *   DE_BAND_ALL             every comparison the split values cannot decide,

@@ -437,7 +437,10 @@ __global__ void __launch_bounds__(256, 1)
           const bool ambiguous = !sure_reject && !sure_accept;
           const bool may_be_best = R.band_all && fs - tau <= bp + 0x1.0p-22f * fabsf(bp);
           const bool near = fs - tau <= R.near_thr || fif - tif <= R.near_thr;
-          const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f;
+          // only a trial the split bound cannot place on one side of the stop target
+          // needs FP64 for the stop rule: surely below (or above) decides it as well
+          const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f &&
+                                !(fs + tau < (float)R.target * 0.999f);
           l_ft[lr] = (double)fs;
           if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !(fif == fif) || !have) {
             l_blist[atomicAdd(l_nb, 1)] = lr;

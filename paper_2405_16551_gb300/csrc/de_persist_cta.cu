@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256, 1)
   const int d = R.d, dp = R.dp, np = R.np, obj = R.obj;
   const int row0 = cta * rows;
   const bool has_target = R.target > 0.0;
-  const float target_f = (float)R.target * 1.001f;
+  const float target_f = (float)R.target * 1.001f, target_lo = (float)R.target * 0.999f;
 
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_bar[2];
@@ -531,7 +531,10 @@ __global__ void __launch_bounds__(256, 1)
           const bool ambiguous = !sure_reject && !sure_accept;
           const bool may_be_best = R.band_all && fs - tau <= bp + 0x1.0p-22f * fabsf(bp);
           const bool near = fs - tau <= R.near_thr || fif - tif <= R.near_thr;
-          const bool may_stop = has_target && fs - tau < target_f;
+          // only a trial the split bound cannot place on one side of the stop
+          // target needs FP64 for the stop rule: surely below (or above)
+          // decides it as well
+          const bool may_stop = has_target && fs - tau < target_f && !(fs + tau < target_lo);
           const double fsd = f64_of_f32(fs);
           s_ft[rr] = fsd;
           if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !(fif == fif)) {

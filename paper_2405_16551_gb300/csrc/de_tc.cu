@@ -489,7 +489,10 @@ __global__ void __launch_bounds__(kFitThreads, 1)
       const bool ambiguous = !sure_reject && !sure_accept;
       const bool may_be_best = R.band_all && fs - tau <= bp + 0x1.0p-22f * fabsf(bp);
       const bool near = fs - tau <= R.near_thr || fif - tif <= R.near_thr;
-      const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f;
+      // only a trial the split bound cannot place on one side of the stop target
+          // needs FP64 for the stop rule: surely below (or above) decides it as well
+          const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f &&
+                                !(fs + tau < (float)R.target * 0.999f);
       s_ftrial[m] = (double)fs;
       if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !(fif == fif)) {
         // the split values cannot decide (or the trial may become the best):
@@ -868,8 +871,12 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
     R.band_cw = std::max(1, std::min(8, (int)(kBandSmem / (8 * (size_t)R.d)) - 1));
     R.nch = (R.d + R.band_cw - 1) / R.band_cw;
     // near the optimum: where the split bound (about 4 u f) reaches an eighth
-    // of the target, comparisons are redone in FP64
-    R.near_thr = R.target > 0.0 ? (float)(R.target / (8.0 * R.band_u)) : 0.f;
+    // of the stopping accuracy, comparisons are redone in FP64.  The accuracy
+    // is the target, capped at the paper's 1e-8 (Sec. 7.3.4): a larger target
+    // (a run stopped at some other error) must not make every value "near";
+    // its stop decision is exact on its own (only trials the split bound
+    // cannot place on one side of the target are redone in FP64)
+    R.near_thr = R.target > 0.0 ? (float)(std::min(R.target, 1e-8) / (8.0 * R.band_u)) : 0.f;
     smem = std::max(smem, plan_smem(R, esz));
     bytes = round_up(bytes, 1024);
     offA[r] = bytes;
