@@ -291,7 +291,6 @@ def main():
     if dist is not None:
         dist.barrier()
     t_wall = time.perf_counter() - t_wall0
-    clk = clocks.stop()
     dev_ms, gen_ms = replicas.max_over_ranks([head["dev_ms"], head["gen_ms"]], dist, device="cuda")
     trials_per_step = NP * G
     value = replicas.job_rate(trials_per_step * args.steps, world, dev_ms / 1e3)
@@ -340,6 +339,16 @@ def main():
         e2e = {"value": replicas.job_rate(trials_per_step * args.steps, world, tot), "unit": "trial evals/s",
                "h2d_bytes_per_step": 8 * (D + D * D), "d2h_bytes_per_step": 8 * (D + 1) + 48}
 
+    # the device's measured FP64 rate (DFMA chains on every SM), the peak of
+    # the FP64 kernels
+    fp64_peak = capi.de_selftest_fp64_rate()
+    if forms:
+        f64 = forms["fp64"]
+        f64["fp64_tflops"] = NP * (2.0 * D * D + 9.0 * D) / (f64["us_per_generation"] * 1e-6) / 1e12
+        f64["fp64_frac_of_measured_rate"] = f64["fp64_tflops"] / fp64_peak
+
+    clk = clocks.stop()
+
     # roofline of the dominant kernel
     peaks = {}
     try:
@@ -352,9 +361,10 @@ def main():
         flops = NP * (2.0 * D * D + 9.0 * D)
         achieved = flops / (avg_gen_us * 1e-6) / 1e12
         roof = {"bound": "alu", "kernel": "k_gen_fp64" if path == 0 else "k_gen_fp64_persist",
-                "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25, "traffic": None,
-                "peak_source": "nominal GB300 FP64 rate 1.25 TFLOP/s (a DFMA loop measured 1.20 on this part)"}
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "de_selftest_fp64_rate: independent DFMA chains on every SM of this device, "
+                               "measured in this run (of measured)"}
     else:
         # algorithmic bytes per trial: read the target row, write the next
         # generation's row, fitness in and out
@@ -382,6 +392,7 @@ def main():
                        "l2": "flushed between runs (512 MiB write)", "parallelism": f"replicas x{world}"},
             "generations_per_s": world * G * args.steps / (dev_ms / 1e3), "best_f_last_run": head["best_f"],
             "forms": forms, "wall_s": t_wall, "e2e": e2e, "roofline": roof, "clocks": clk,
+            "fp64_rate_tflops_measured": fp64_peak,
             "gpu_launches": args.steps * launches_per_step(head["plan"], G)}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(*make_problem())
@@ -631,11 +642,22 @@ def run_workload(args, capi, torch, rank, world):
         ms = _timed(torch, stream, flush, steps, warmup, lambda: (capi.de_reset(h, -1), capi.de_step(h, G)))
         capi.de_destroy(h)
         value = R * n * G * steps / (ms / 1e3)
+        # the trial construction's FP64 work: x_r2 - x_r3, the fused
+        # multiply-add of Eq. 2 and t - o per coordinate (4 flops); its rate
+        # over the whole step against the measured FP64 rate is a lower bound
+        # on the trial kernel's own FP64-pipe fraction
+        fp64_peak = capi.de_selftest_fp64_rate()
+        trial_fp64_tflops = 4.0 * R * n * d * G * steps / (ms / 1e3) / 1e12
         line.update(metric=f"trial evals/sec, {R} runs of NP=8192 D=1000 rotated-shifted Rastrigin, BF16x3",
                     value=value, ms_per_step=ms / steps, dtype="bf16x3 products, f32 accumulate",
                     config={"workload": f"{R} x (NP=8192 D=1000), {G} generations per step, one handle",
                             "l2": f"working set about {R / 4:.0f} GB, far above L2"},
                     tensor_tflops=3 * 2.0 * R * n * d * d * G * steps / (ms / 1e3) / 1e12,
+                    trial_fp64_tflops_over_step=trial_fp64_tflops, fp64_rate_tflops_measured=fp64_peak,
+                    trial_fp64_frac_over_step=trial_fp64_tflops / fp64_peak,
+                    hbm_frac_over_step=R * n * (2 * 8 * d + 16) * G * steps / (ms / 1e3) / 1e9 /
+                    float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+                    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None,
                     gpu_launches=steps * (3 * R + 3 * G))
     else:  # stress
         G = min(args.generations, 100)

@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
             "de_get_surrogate_stats": ([H, _i64p, _i64p, _dp, _i32p], ctypes.c_int),
             "de_get_adaptive": ([H, ctypes.c_int32, _dp, _dp], ctypes.c_int),
             "de_selftest_f32_rounding": ([_dp, ctypes.c_int64], ctypes.c_int64),
+            "de_selftest_fp64_rate": ([], ctypes.c_double),
             "de_init_islands": ([ctypes.POINTER(de_config), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                  ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
             "de_set_adaptive": ([H, ctypes.c_int32, _dp, _dp], ctypes.c_int),
@@ -144,7 +145,7 @@ def exported_symbols():
             "de_get_debug", "de_get_shape", "de_get_stats", "de_get_plan", "de_save", "de_load", "de_destroy",
             "de_eval_noalloc", "de_mlp_create", "de_mlp_destroy", "de_mlp_set_params", "de_mlp_get_params",
             "de_mlp_forward", "de_mlp_grad", "de_mlp_train", "de_get_surrogate_stats", "de_get_adaptive",
-            "de_set_adaptive", "de_init_islands", "de_selftest_f32_rounding"]
+            "de_set_adaptive", "de_init_islands", "de_selftest_f32_rounding", "de_selftest_fp64_rate"]
 
 
 def _status_name(s):
@@ -339,6 +340,14 @@ def de_selftest_f32_rounding(x) -> int:
     """Mismatches between the library's FP64 -> FP32 rounding and the GPU's."""
     a = np.ascontiguousarray(x, dtype=np.float64)
     return int(load().de_selftest_f32_rounding(_p(a), a.size))
+
+
+def de_selftest_fp64_rate() -> float:
+    """Measured FP64 fused multiply-add throughput of the current device (TFLOP/s)."""
+    r = float(load().de_selftest_fp64_rate())
+    if r <= 0:
+        raise DEError(DE_ERR_CUDA, "FP64 rate self-test failed")
+    return r
 
 
 def de_get_adaptive(h, run: int = 0):

@@ -75,3 +75,13 @@ def test_empty_evaluation_is_a_no_op(prec):
         assert torch.all(fd == 7.0)
     finally:
         capi.de_destroy(h)
+
+
+def test_fp64_rate_self_test():
+    """The measured FP64 fused multiply-add rate is positive and of the order
+    of the part's FP64 rate (GB300: about 1.25 TFLOP/s nominal)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    r = capi.de_selftest_fp64_rate()
+    assert 0.2 < r < 5.0, r
