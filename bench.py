@@ -796,9 +796,11 @@ def accuracy_workload(capi, torch, stream, problems):
 
 # DRAM traffic of one launch of the dominant kernel, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a 200-generation launch of
-# the BF16x3 persistent kernel on this workload (205,312 + 1,778,944 bytes),
-# scaled to a launch of 3000 generations (traffic grows with generations)
-TRAFFIC_PER_LAUNCH = {("k_persist", 3000): (205312 + 1778944) * 3000 // 200}
+# the BF16x3 persistent kernel on this workload, scaled to a launch of 3000
+# generations (traffic grows with generations)
+TRAFFIC_PER_LAUNCH = {("k_persist", 3000): (205312 + 1778944) * 3000 // 200,
+                      # k_persist_cta, 7 targets per CTA: 982,528 + 523,776 bytes per 200 generations
+                      ("k_persist_cta", 3000): (982528 + 523776) * 3000 // 200}
 
 
 if __name__ == "__main__":

@@ -523,7 +523,7 @@ DE_API int64_t de_selftest_f32_rounding(const double* x_host, int64_t n);
 /* Self-test (no counterpart in the paper): the current device's FP64
  * fused multiply-add throughput in TFLOP/s (2 flops per DFMA), measured by a
  * kernel of independent DFMA chains on every SM (4 CTAs of 256 threads per
- * SM, 8 chains per thread, 4096 steps; CUDA events, best of 3).  This is the
+ * SM, 8 chains per thread, 1024 steps; CUDA events, best of 3).  This is the
  * measured peak the FP64 kernels' throughput is reported against.  Returns
  * -1 on a CUDA error.  Allocates and synchronises the current device. */
 DE_API double de_selftest_fp64_rate(void);

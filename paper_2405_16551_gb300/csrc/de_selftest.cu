@@ -52,7 +52,7 @@ extern "C" DE_API double de_selftest_fp64_rate(void) {
   double* sink = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   double best = -1.0;
-  const int iters = 4096, threads = 256, blocks = nsm * 4;
+  const int iters = 1024, threads = 256, blocks = nsm * 4;
   if (cudaMalloc(&sink, sizeof(double)) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
       cudaEventCreate(&e1) == cudaSuccess) {
     de::k_dfma_rate<<<blocks, threads>>>(iters, sink);  // warm-up
