@@ -195,7 +195,8 @@ DTYPE = {"fp64": "f64", "bf16x3": "bf16x3 products, f32 accumulate, f64 trials a
 
 # de_get_plan's kernel paths
 KERNEL_PATH_NAMES = {0: "fp64 fused", 1: "split three-kernel", 2: "split persistent cluster",
-                     3: "fp64 cooperative persistent", 4: "split persistent, CTA-local products (cooperative)"}
+                     3: "fp64 cooperative persistent", 4: "split persistent, CTA-local products (cooperative)",
+                     5: "split persistent batch, per-run arrival counters (cooperative)"}
 
 
 def launches_per_step(plan, G):
@@ -208,6 +209,8 @@ def launches_per_step(plan, G):
         return 3 + 3 * G      # trial, tensor-core fitness, FP64 band per generation
     if path == 3:
         return 3 + 1          # one cooperative FP64 kernel for all generations
+    if path == 5:
+        return 3 + 1          # one persistent batch kernel for all generations
     return 3 + 2              # one persistent split kernel (path 2 or 4) for all generations, then its close-out
 
 

@@ -59,6 +59,9 @@ struct de_handle {
   // k - 1 of every cooperative FP64 launch leaves out its first grid-barrier
   // arrival, and the barrier gives up after a few thousand polls
   int test_grid_skip = 0;
+  // split precision, several runs: every generation of a call in one
+  // cooperative launch of the persistent batch kernel (kernel path 5)
+  bool pbatch_on = false;
   // per run: a hash of the problem (objective, F, CR, bounds, scale, seed,
   // run_id, precision, strategy, jDE, FP64 band policy, shift, rotation and
   // permutation), written to checkpoints and checked by de_load
@@ -325,6 +328,14 @@ static de_status enqueue_generations(de_handle* h, int64_t n) {
         DE_CUDA(h, k_gen_fp64_persist_launch(h->d_run, h->d_items, h->nitems, h->nruns, h->threads, h->smem_gen,
                                              h->variants, h->suite, h->d_ctl64, g, h->stream, h->test_grid_skip));
     }
+    return DE_OK;
+  }
+  if (h->prec != DE_PREC_FP64 && h->pbatch_on) {
+    // one launch of the persistent batch kernel runs up to 2^20 generations
+    // of every run (a run's arrival count stays below 2^32)
+    for (int64_t left = n; left > 0; left -= (int64_t)1 << 20)
+      DE_CUDA(h, pbatch_launch(h->tc.pbatch, h->d_run, h->tc.d_ctl, std::min<int64_t>(left, (int64_t)1 << 20),
+                               h->stream));
     return DE_OK;
   }
   if (h->prec != DE_PREC_FP64 && h->tc.persist.ok) {
@@ -775,6 +786,73 @@ static de_status autotune_persist(de_handle* h) {
   return s;
 }
 
+// Batches in split precision: the persistent batch kernel (kernel path 5,
+// double-buffered population) against the three-kernel path in CUDA graphs
+// (path 1, population updated in place), timed on the handle's own problem
+// after the three-kernel geometry is tuned; the faster is kept and cached.
+// DE_GB300_PERSIST_BATCH=1 forces path 5 where it applies, =0 disables it.
+static void set_dbuf(de_handle* h, bool on) {
+  h->dbuf = on;
+  for (auto& R : h->run) R.dbuf = on ? 1 : 0;
+}
+
+static de_status choose_pbatch(de_handle* h) {
+  if (!h->tc.pbatch.ok) return DE_OK;
+  const char* force = getenv("DE_GB300_PERSIST_BATCH");
+  const char* env = getenv("DE_GB300_AUTOTUNE");
+  bool on = false;
+  if (force && force[0] == '1') {
+    on = true;
+  } else if (!(env && env[0] == '0')) {
+    const std::string key = "pbatch_v1 " + tune_key_split(h);
+    int cached = 0;
+    if (tune_lookup(key, cached)) {
+      on = cached == 1;
+    } else {
+      cudaEvent_t e0, e1;
+      DE_CUDA(h, cudaEventCreate(&e0));
+      DE_CUDA(h, cudaEventCreate(&e1));
+      std::vector<RunDesc> saved = h->run;
+      for (auto& R : h->run) {
+        R.target = 0.0;  // no stop rule while timing
+        R.max_evals = 0;
+        R.max_gens = INT64_MAX / 4;
+      }
+      auto time_gens = [&](bool pb, float& ms_per_gen) -> de_status {
+        set_dbuf(h, pb);
+        h->pbatch_on = pb;
+        de_status s = upload_desc(h);
+        for (int r = 0; r < h->nruns && s == DE_OK; ++r) {
+          int32_t zero = 0;
+          DE_CUDA(h, cudaMemcpyAsync(&h->run[r].st->stop, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream));
+        }
+        const int G = 12;
+        if (s == DE_OK) s = enqueue_generations(h, 2);
+        DE_CUDA(h, cudaEventRecord(e0, h->stream));
+        if (s == DE_OK) s = enqueue_generations(h, G);
+        DE_CUDA(h, cudaEventRecord(e1, h->stream));
+        DE_CUDA(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        DE_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+        ms_per_gen = ms / G;
+        return s;
+      };
+      float ms_graph = 0.f, ms_pb = 0.f;
+      de_status s = time_gens(false, ms_graph);
+      if (s == DE_OK) s = time_gens(true, ms_pb);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      h->run = saved;
+      if (s != DE_OK) return s;
+      on = ms_pb < ms_graph * 0.98f;
+      tune_store(key, on ? 1 : 2);
+    }
+  }
+  h->pbatch_on = on;
+  set_dbuf(h, on);
+  return upload_desc(h);
+}
+
 // ---------------------------------------------------------------- C ABI
 extern "C" {
 
@@ -1115,8 +1193,12 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     if (const char* v = getenv("DE_GB300_TEST_GRID_TIMEOUT")) h->test_grid_skip = std::max(0, atoi(v));
     for (int r = 0; r < nruns; ++r) TRY(init_run(h, r));
   } else if (h->prec != DE_PREC_FP64) {
-    if (h->tc.persist.ok) TRY(autotune_persist(h));
-    else TRY(autotune_split(h));
+    if (h->tc.persist.ok) {
+      TRY(autotune_persist(h));
+    } else {
+      TRY(autotune_split(h));
+      TRY(choose_pbatch(h));
+    }
     for (int r = 0; r < nruns; ++r) {
       TRY(init_run(h, r));
       // the counters start after the timing generations
@@ -1240,7 +1322,7 @@ de_status de_run(de_handle* h, de_result* out) {
       }
     if (all) break;
     // the persistent kernels stop the run themselves: one launch
-    const bool persistent = h->fp64_persist || (h->prec != DE_PREC_FP64 && h->tc.persist.ok);
+    const bool persistent = h->fp64_persist || (h->prec != DE_PREC_FP64 && (h->tc.persist.ok || h->pbatch_on));
     s = enqueue_generations(h, std::max<int64_t>(1, persistent ? left : std::min<int64_t>(chunk, left)));
     if (s != DE_OK) return s;
     s = read_states(h);
@@ -1476,6 +1558,7 @@ de_status de_get_plan(de_handle* h, int32_t* kernel_path, int32_t* cluster_size)
   const bool persist = h->prec != DE_PREC_FP64 && h->tc.persist.ok;
   if (kernel_path)
     *kernel_path = h->prec == DE_PREC_FP64 ? (h->fp64_persist ? 3 : 0)
+                   : h->pbatch_on         ? 5
                                            : (persist ? (h->tc.persist.mode == 1 ? 4 : 2) : 1);
   if (cluster_size)
     *cluster_size = persist ? (h->tc.persist.mode == 1 ? 0 : h->tc.persist.C)

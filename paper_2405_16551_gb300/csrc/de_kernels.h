@@ -91,6 +91,21 @@ struct PersistPlan {
   size_t cta_smem = 0;
 };
 
+// the persistent batch kernel (de_persist_batch.cu): work items of at most 8
+// targets of one run, a fixed contiguous slice of items per CTA, per-run
+// arrival counters
+struct PbPlan {
+  bool ok = false;
+  int nct = 0, nruns = 0, prec = 0, kpad_max = 0, dp_max = 0;
+  size_t smem = 0;
+  int4* d_items = nullptr;   // (run, tile, first row, rows)
+  int2* d_slices = nullptr;  // per CTA: [first item, last item + 1)
+  unsigned* d_cnt = nullptr; // per run: items done in this launch
+};
+bool pbatch_plan(PbPlan& pp, const std::vector<RunDesc>& runs, int prec);
+void pbatch_free(PbPlan& pp);
+cudaError_t pbatch_launch(const PbPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens, cudaStream_t s);
+
 // split-precision tensor-core path (de_tc.cu)
 struct TcPlan {
   int prec = 0;
@@ -111,6 +126,7 @@ struct TcPlan {
   int nruns = 0;
   bool var = false;            // some run uses a strategy variant or jDE
   PersistPlan persist;         // the persistent cluster kernel, when it applies
+  PbPlan pbatch;               // the persistent batch kernel, when it applies
   PersistCtl* d_ctl = nullptr;
 };
 bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec);

@@ -39,22 +39,14 @@
 
 #include <algorithm>
 
+#include "de_cta_tile.cuh"
 #include "de_device.cuh"
 #include "de_kernels.h"
 #include "de_tcgen05.cuh"
 
 namespace de {
 
-constexpr int kCtaRowsMax = 16;                   // targets per CTA (two A row groups)
 constexpr long long kCtaGridSpin = 1LL << 22;     // polls of the grid barrier (with back-off)
-
-// Bytes of one part (high or low) of the 16-row y operand: k-groups of 16
-// bytes, each holding two 8-row core matrices (k-group stride 256 bytes).
-__host__ __device__ inline uint32_t cta_y_part(const RunDesc& R) { return (uint32_t)(R.kpad * R.esz / 16) * 256u; }
-// ... and of the 128-row M operand (k-group stride 16 x 128 = 2048 bytes).
-__host__ __device__ inline uint32_t cta_m_part(const RunDesc& R) { return (uint32_t)(R.kpad * R.esz / 16) * 2048u; }
-// Row stride (floats) of the accumulator rows in shared memory.
-__host__ __device__ inline int cta_zstride(const RunDesc& R) { return R.ntn + 4; }
 
 struct CtaLayout {
   uint32_t yop, mop, z, y, red, total;
@@ -70,93 +62,6 @@ __host__ __device__ inline CtaLayout cta_layout(const RunDesc& R) {
   L.red = L.y + (uint32_t)(2 * R.dp) * 8u;  // FP64 y of a band row's trial and target
   L.total = L.red + 2u * 256u * 8u;         // FP64 terms of the band evaluation
   return L;
-}
-
-// y[0..3] (coordinates j0..j0+3 of row m < 16 of the y operand) as high and
-// low parts.
-template <int ESZ>
-__device__ __forceinline__ void cta_store_split4(uint8_t* A, uint32_t a_part, int m, int j0, const float y[4]) {
-  const int rg = m >> 3, rr = m & 7;
-  if constexpr (ESZ == 2) {
-    __nv_bfloat16 hi[4], lo[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      hi[q] = __float2bfloat16_rn(y[q]);
-      lo[q] = __float2bfloat16_rn(y[q] - __bfloat162float(hi[q]));  // exact residual, then rounded
-    }
-    const uint32_t off = (uint32_t)(j0 >> 3) * 256u + (uint32_t)rg * 128u + (uint32_t)rr * 16u + (uint32_t)(j0 & 7) * 2u;
-    *reinterpret_cast<uint2*>(A + off) = *reinterpret_cast<const uint2*>(hi);
-    *reinterpret_cast<uint2*>(A + a_part + off) = *reinterpret_cast<const uint2*>(lo);
-  } else {
-    float4 hi, lo;
-    hi.x = to_tf32(y[0]);
-    hi.y = to_tf32(y[1]);
-    hi.z = to_tf32(y[2]);
-    hi.w = to_tf32(y[3]);
-    lo.x = to_tf32(y[0] - hi.x);
-    lo.y = to_tf32(y[1] - hi.y);
-    lo.z = to_tf32(y[2] - hi.z);
-    lo.w = to_tf32(y[3] - hi.w);
-    const uint32_t off = (uint32_t)(j0 >> 2) * 256u + (uint32_t)rg * 128u + (uint32_t)rr * 16u;
-    *reinterpret_cast<float4*>(A + off) = hi;
-    *reinterpret_cast<float4*>(A + a_part + off) = lo;
-  }
-}
-
-// FP64 fitness of the shifted vector y (shared memory, d values) by the
-// whole CTA: z_j = sum_k M_jk y_k (M^T read at L2, two accumulator chains),
-// the objective terms per coordinate, then a fixed-order sum (per warp an
-// xor tree, then the warps in order).  Every thread returns the value.
-__device__ double cta_fitness_fp64(const RunDesc& R, const double* sy, double* red) {
-  const int d = R.d, obj = R.obj, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  __shared__ double s_zv[129];
-  if (tid < d) {
-    double z;
-    if (R.rotate) {
-      double p0 = 0.0, p1 = 0.0;
-      int k = 0;
-      for (; k + 1 < d; k += 2) {
-        p0 = fma(__ldcg(R.MT + (size_t)k * d + tid), sy[k], p0);
-        p1 = fma(__ldcg(R.MT + (size_t)(k + 1) * d + tid), sy[k + 1], p1);
-      }
-      if (k < d) p0 = fma(__ldcg(R.MT + (size_t)k * d + tid), sy[k], p0);
-      z = p0 + p1;
-    } else {
-      z = sy[tid];
-    }
-    s_zv[tid] = z;
-  }
-  __syncthreads();
-  double t1 = 0.0, t2 = 0.0;
-  if (tid < d) {
-    const double z = s_zv[tid];
-    if (obj == kObjSphere) {
-      t1 = z * z;
-    } else if (obj == kObjRastrigin) {
-      t1 = z * z - 10.0 * cos2pi_f64(z) + 10.0;
-    } else if (obj == kObjAckley) {
-      t1 = z * z;
-      t2 = cos2pi_f64(z);
-    } else if (tid + 1 < d) {  // Rosenbrock at t = z + 1
-      const double t0 = z + 1.0, tn = s_zv[tid + 1] + 1.0;
-      const double a = tn - t0 * t0, b = t0 - 1.0;
-      t1 = 100.0 * a * a + b * b;
-    }
-  }
-  t1 = warp_sum(t1);
-  t2 = warp_sum(t2);
-  if (lane == 0) {
-    red[warp] = t1;
-    red[8 + warp] = t2;
-  }
-  __syncthreads();
-  double s1 = 0.0, s2 = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-    s1 += red[w];
-    s2 += red[8 + w];
-  }
-  __syncthreads();  // red and s_zv are reused by the next call
-  return obj == kObjAckley ? 20.0 + 2.718281828459045 - 20.0 * exp(-0.2 * sqrt(s1 / d)) - exp(s2 / d) : s1;
 }
 
 // VAR: the run uses a strategy variant or jDE (a separate instance, so that
@@ -232,19 +137,8 @@ __global__ void __launch_bounds__(256, 1)
   }
   // the y operand starts at zero (rows past this CTA's targets stay zero)
   for (uint32_t q = tid * 16u; q < L.mop; q += blockDim.x * 16u) *reinterpret_cast<uint4*>(smem + q) = make_uint4(0u, 0u, 0u, 0u);
-  // the split M as the A operand: 128 rows (rows past ntn zero); the global
-  // copy holds ntn rows, k-group stride ntn / 8 x 128 bytes
-  {
-    const int nkg = R.kpad * ESZ / 16, rgs = R.ntn / 8;
-    const size_t gpart = (size_t)R.b_tile_bytes / 2;
-    for (int u = tid; u < 2 * nkg * 128; u += blockDim.x) {
-      const int part = u / (nkg * 128), rem = u % (nkg * 128);
-      const int kg = rem / 128, rg = (rem / 8) % 16, rr = rem % 8;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (rg < rgs) v = __ldg(reinterpret_cast<const uint4*>(R.B + part * gpart + (size_t)(kg * rgs + rg) * 128 + rr * 16));
-      *reinterpret_cast<uint4*>(sMop + part * m_part + (uint32_t)kg * 2048u + (uint32_t)rg * 128u + (uint32_t)rr * 16u) = v;
-    }
-  }
+  // the split M as the A operand: 128 rows (rows past ntn zero)
+  cta_load_m<ESZ>(R, sMop, m_part);
   {
     const int cur0 = (int)(*(volatile int64_t*)&st->gen & 1);
     if (tid < kCtaRowsMax) {
@@ -732,9 +626,10 @@ static const void* cta_kernel(int prec, bool var) {
 
 bool persist_cta_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
   pp.cta_ok = false;
-  // one run, one N tile of at most 128 columns (TMEM: 128 columns), whole K
-  // resident, rows of at most 128 coordinates (one 4-coordinate chunk per lane)
-  if (nruns != 1 || R.nn != 1 || R.kc != R.kpad || R.d > 128 || R.ntn > 128) return false;
+  // one run, one N tile of at most 128 columns, rows of at most 128
+  // coordinates (one 4-coordinate chunk per lane); the whole split M is
+  // copied into shared memory (the three-kernel path's K chunking does not apply)
+  if (nruns != 1 || R.nn != 1 || R.d > 128 || R.ntn > 128) return false;
   const size_t smem = cta_layout(R).total;
   if (smem > 220 * 1024) return false;
   const bool var = R.strategy != 0 || R.jde;

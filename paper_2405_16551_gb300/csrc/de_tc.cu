@@ -989,6 +989,11 @@ de_status tc_plan_build(TcPlan& p, std::vector<RunDesc>& runs, const de_config* 
     // the persistent cluster kernel runs a single run whose clusters all fit at once
     const char* env = getenv("DE_GB300_PERSIST");
     if (!(env && env[0] == '0') && e == cudaSuccess) persist_plan(p.persist, runs[0], (int)runs.size(), prec);
+    // ... and the persistent batch kernel a batch of runs of at most 128
+    // coordinates (DE_GB300_PERSIST_BATCH=0 disables it)
+    const char* envb = getenv("DE_GB300_PERSIST_BATCH");
+    if (!(env && env[0] == '0') && !(envb && envb[0] == '0') && e == cudaSuccess && runs.size() >= 2)
+      pbatch_plan(p.pbatch, runs, prec);
     cudaGetLastError();
   }
   p.d_band_cnt = (uint32_t*)((uint8_t*)p.arena + off_bcnt);
@@ -1044,6 +1049,7 @@ de_status tc_set_geometry(TcPlan& p, std::vector<RunDesc>& runs, int trial_rows,
 }
 
 void tc_plan_free(TcPlan& p) {
+  pbatch_free(p.pbatch);
   if (p.arena) cudaFree(p.arena);
   if (p.d_trial_items) cudaFree(p.d_trial_items);
   if (p.d_fit_items) cudaFree(p.d_fit_items);

@@ -1,0 +1,152 @@
+"""The persistent batch kernel (kernel path 5): every generation of a batch of
+independent split-precision runs in one cooperative launch, work items of at
+most 8 targets, per-run arrival counters.  Through the C ABI only.
+
+* one generation of a batch of uneven runs equals the oracle's: indices,
+  crossover masks and trials bit for bit, fitness within the split bound,
+  decisions outside the FP64 band;
+* a batch equals the same runs one handle at a time (same populations,
+  fitness, stop generations and best records), with runs that stop at
+  different generations and runs that reach the target;
+* the autotuner's choice between this path and the three-kernel path never
+  changes results.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_16551_gb300 import capi, problems
+
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-12
+REL_SPLIT = {capi.DE_PREC_BF16X3: 1e-5, capi.DE_PREC_TF32X3: 1e-6}
+PRECS = [capi.DE_PREC_BF16X3, capi.DE_PREC_TF32X3]
+
+
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _cfgs(shapes, prec, seed=9):
+    """(config, shift, rotation) per run; run r draws from run_id r."""
+    out = []
+    for r, (n, d, obj) in enumerate(shapes):
+        o = problems.shift(d, seed=seed, run_id=r)
+        M = problems.rotation(d, seed=seed, run_id=r)
+        out.append((capi.make_config(n, d, objective=obj, shift=o, rot=M, seed=seed, run_id=r, precision=prec,
+                                     target_error=0.0, max_generations=10**6), o, M))
+    return out
+
+
+SHAPES = [(150, 100, 1), (9, 1, 0), (70, 37, 3), (200, 128, 2), (33, 10, 1), (64, 64, 0), (4, 3, 3)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_generation_matches_oracle(prec, monkeypatch):
+    _need_gpu()
+    monkeypatch.setenv("DE_GB300_PERSIST_BATCH", "1")
+    cf = _cfgs(SHAPES, prec)
+    cfgs = [c for c, _, _ in cf]
+    for c in cfgs:
+        c.debug_capture = 1
+        c.fp64_band = capi.DE_BAND_ALL
+    pops = [problems.population(n, d, seed=40 + r) for r, (n, d, _) in enumerate(SHAPES)]
+    h = capi.de_init_batch(cfgs)
+    try:
+        assert capi.de_get_plan(h)["kernel_path"] == 5
+        fits = []
+        for r, ((c, o, M), X) in enumerate(zip(cf, pops)):
+            obj = SHAPES[r][2]
+            fX, _ = oracle.evaluate(obj, X, o, M)
+            fits.append(fX)
+            capi.de_set_population(h, r, X, fX)
+            capi.de_set_generation(h, r, 6)
+        capi.de_step(h, 1)
+        for r, ((c, o, M), X, fX) in enumerate(zip(cf, pops, fits)):
+            n, d, obj = SHAPES[r]
+            g = capi.de_get_debug(h, r)
+            xn, fn = capi.de_get_population(h, r)
+            ref = oracle.step(X, fX, 0.5, 0.9, -100, 100, obj, o, M, seed=9, generation=7, run_id=r)
+            assert np.array_equal(g["idx"], ref["idx"]), r
+            assert np.array_equal(g["mask"], ref["mask"]), r
+            assert np.array_equal(g["trial"], ref["trial"]), r
+            fp64 = g["fp64_checked"].astype(bool)
+            scale = np.abs(ref["f_trial"]) + ref["sabs_trial"]
+            tol = np.where(fp64, REL64, REL_SPLIT[prec]) * scale
+            assert np.all(np.abs(g["f_trial"] - ref["f_trial"]) <= tol), r
+            inband = np.abs(ref["f_trial"] - fX) <= REL64 * scale
+            assert np.array_equal(g["accept"][~inband], ref["accept"][~inband]), r
+            acc = g["accept"].astype(bool)
+            assert np.array_equal(xn[acc], ref["trial"][acc]) and np.array_equal(xn[~acc], X[~acc]), r
+    finally:
+        capi.de_destroy(h)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_equals_single_runs_with_different_stops(prec, monkeypatch):
+    """Runs with their own generation limits and a sphere run that meets the
+    1e-8 target: the batch on path 5 gives every run the population, fitness,
+    stop generation and best record of its own handle (every undecidable
+    comparison in FP64, so the single runs' kernel path does not matter)."""
+    _need_gpu()
+    shapes = [(120, 30, 1), (48, 10, 0), (90, 100, 3), (33, 50, 2), (64, 10, 0)]
+    limits = [40, 25, 60, 17, 500]
+    cf = _cfgs(shapes, prec)
+    cfgs = []
+    for r, (c, _, _) in enumerate(cf):
+        c.max_generations = limits[r]
+        c.fp64_band = capi.DE_BAND_ALL
+        if r == 4:  # small sphere: stops at the 1e-8 target
+            c.target_error = 1e-8
+        cfgs.append(c)
+    monkeypatch.setenv("DE_GB300_PERSIST_BATCH", "1")
+    h = capi.de_init_batch(cfgs)
+    try:
+        assert capi.de_get_plan(h)["kernel_path"] == 5
+        res = capi.de_run(h, len(cfgs))
+        batch = [capi.de_get_population(h, r) for r in range(len(cfgs))]
+        bests = [capi.de_get_best(h, r) for r in range(len(cfgs))]
+    finally:
+        capi.de_destroy(h)
+    assert res[4]["stop_reason"] == capi.DE_STOP_TARGET and res[4]["generations"] < 500
+    for r, c in enumerate(cfgs):
+        assert res[r]["generations"] == (limits[r] if r < 4 else res[4]["generations"])
+        hs = capi.de_init(c)
+        try:
+            rs = capi.de_run(hs)[0]
+            xs, fs = capi.de_get_population(hs)
+            bs = capi.de_get_best(hs)
+        finally:
+            capi.de_destroy(hs)
+        assert np.array_equal(batch[r][0], xs), r
+        assert np.allclose(batch[r][1], fs, rtol=REL_SPLIT[prec], atol=0), r
+        assert rs["generations"] == res[r]["generations"] and rs["stop_reason"] == res[r]["stop_reason"], r
+        assert bs["best_index"] == bests[r]["best_index"], r
+        assert abs(bs["best_f"] - bests[r]["best_f"]) <= REL64 * (abs(bs["best_f"]) + 1e-300) + 1e-300, r
+
+
+def test_batch_path_choice_does_not_change_results(monkeypatch):
+    """Path 5 and the three-kernel path give a batch the same populations when
+    every undecidable comparison is redone in FP64."""
+    _need_gpu()
+    shapes = [(100, 20, 1), (57, 100, 3), (80, 40, 0)]
+    pops = []
+    for flag, want in (("1", 5), ("0", 1)):
+        monkeypatch.setenv("DE_GB300_PERSIST_BATCH", flag)
+        cfgs = [c for c, _, _ in _cfgs(shapes, capi.DE_PREC_BF16X3)]
+        for c in cfgs:
+            c.fp64_band = capi.DE_BAND_ALL
+            c.max_generations = 60
+        h = capi.de_init_batch(cfgs)
+        try:
+            assert capi.de_get_plan(h)["kernel_path"] == want
+            capi.de_run(h, len(cfgs))
+            pops.append([capi.de_get_population(h, r)[0] for r in range(len(cfgs))])
+        finally:
+            capi.de_destroy(h)
+    for a, b in zip(*pops):
+        assert np.array_equal(a, b)
