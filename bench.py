@@ -474,10 +474,12 @@ def run_workload(args, capi, torch, rank, world):
                                              rot=problems.rotation(d, seed=1, run_id=r), seed=1, run_id=r,
                                              precision=PREC_NAMES[name], target_error=0.0, max_generations=G))
             h = capi.de_init_batch(cfgs, stream=stream.cuda_stream)
+            path = capi.de_get_plan(h)["kernel_path"]
             ms = _timed(torch, stream, flush, steps, warmup, lambda: (capi.de_reset(h, -1), capi.de_step(h, G)))
             capi.de_destroy(h)
             tot = sum(n for n, _, _ in shapes) * G * steps
-            forms[name] = {"trial_evals_per_s": tot / (ms / 1e3), "ms_per_step": ms / steps}
+            forms[name] = {"trial_evals_per_s": tot / (ms / 1e3), "ms_per_step": ms / steps,
+                           "kernel_path": KERNEL_PATH_NAMES[path]}
         # the same runs one handle at a time in plain FP64 (first 16 runs, scaled by their share of the trials)
         ms_seq, tr_seq = 0.0, 0
         for r, (n, d, obj) in enumerate(shapes[:16]):
@@ -497,7 +499,9 @@ def run_workload(args, capi, torch, rank, world):
                     dtype="bf16x3 products, f32 accumulate, f64 trials and selection band",
                     config={"workload": f"512-run batch, {G} generations per step, one handle, CUDA graphs",
                             "l2": "flushed between steps (512 MiB write)"},
-                    forms=forms, gpu_launches=steps * (3 * 512 + 3 * G))
+                    forms=forms,
+                    gpu_launches=steps * (3 * 512 + (1 if forms["bf16x3"]["kernel_path"] == KERNEL_PATH_NAMES[5]
+                                                     else 3 * G)))
     elif args.workload == "ode_surrogate":
         # time and true evaluations to reach f < 1e-8, plain DE vs 8 screened candidates
         res = {}

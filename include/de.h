@@ -553,13 +553,14 @@ DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d
  *      generations in which every CTA owns at most 16 targets and runs their
  *      tensor-core products itself (a grid barrier between generations, no
  *      clusters); single runs of d <= 128 whose CTAs all fit at once
- *   5  split precision, one cooperative persistent kernel for many
- *      generations of a batch of runs: work items of consecutive targets of
- *      one run, a fixed slice of items per CTA, and in place of a grid
- *      barrier one arrival counter per run (a run's next generation starts
- *      when every item of its previous one is done; the stop rule of
- *      Sec. 7.3.4 applies per run); batches of at least two runs, each with
- *      d <= 128 and DE/rand/1/bin; de_init times it against path 1 and keeps
+ *   5  split precision, one cooperative persistent kernel (one CTA per SM)
+ *      for many generations of a batch of runs: work items are the runs'
+ *      128-target tiles, each CTA owns a fixed slice of them, and in place of
+ *      a grid barrier each run has an arrival counter (a run's next
+ *      generation starts when every tile of its previous one is done; the
+ *      stop rule of Sec. 7.3.4 applies per run); batches of at least two
+ *      DE/rand/1/bin runs of d <= 128 whose operands fit one CTA's shared
+ *      memory (TF32x3: d <= 112); de_init times it against path 1 and keeps
  *      the faster (DE_GB300_PERSIST_BATCH=1 / 0 forces path 5 / path 1)
  *   3  FP64, one cooperative persistent kernel for many generations of
  *      every run of the handle (grid barrier between generations; the same

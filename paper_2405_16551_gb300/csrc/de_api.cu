@@ -804,7 +804,7 @@ static de_status choose_pbatch(de_handle* h) {
   if (force && force[0] == '1') {
     on = true;
   } else if (!(env && env[0] == '0')) {
-    const std::string key = "pbatch_v1 " + tune_key_split(h);
+    const std::string key = "pbatch_v2 " + tune_key_split(h);
     int cached = 0;
     if (tune_lookup(key, cached)) {
       on = cached == 1;

@@ -97,8 +97,9 @@ struct PersistPlan {
 struct PbPlan {
   bool ok = false;
   int nct = 0, nruns = 0, prec = 0, kpad_max = 0, dp_max = 0;
+  uint32_t ncols = 32;       // tensor-memory columns of a CTA
   size_t smem = 0;
-  int4* d_items = nullptr;   // (run, tile, first row, rows)
+  int4* d_items = nullptr;   // (run, 128-row tile, first row, rows)
   int2* d_slices = nullptr;  // per CTA: [first item, last item + 1)
   unsigned* d_cnt = nullptr; // per run: items done in this launch
 };

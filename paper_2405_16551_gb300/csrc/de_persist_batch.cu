@@ -1,28 +1,41 @@
 // de_persist_batch.cu -- the split-precision generation loop of a batch of
 // independent runs (uneven NP, D and objective) as one cooperative persistent
-// kernel with CTA-local tensor-core products.
+// kernel, one CTA per SM.
 //
-// The batch is cut into work items: tiles of at most 8 consecutive targets of
-// one run, in run order.  CTA c owns a fixed, contiguous slice of items for
-// the whole launch and, for every generation, processes its items in order.
-// One item is one DE generation of its targets (Eq. 2, Eq. 3, bound repair,
-// the objective of Sec. 7.3.1 and greedy selection, Sec. 2), computed the way
-// k_persist_cta computes it: one target per warp, the split y of the tile as
-// the 16-row B operand, the run's split M (loaded into shared memory when the
-// run changes) as the 128-row A operand, three split passes issued by three
-// warps, the FP32 objective by 16 threads per target, the rows the split
-// error bound cannot decide re-evaluated in FP64 by the whole CTA.
+// The batch is cut into work items: the 128-target tiles of every run, in run
+// order.  CTA c owns a fixed, contiguous slice of items for the whole launch
+// (slices balanced by an estimate of each item's time) and, for every
+// generation, processes its items in order.  One item is one DE generation of
+// its targets (Eq. 2, Eq. 3, bound repair, the objective of Sec. 7.3.1 and
+// greedy selection, Sec. 2), the work of the three-kernel path's trial and
+// fitness tiles done in one place:
+//
+//   trials     the whole CTA, R.lpt lanes per target: FP64 trial rows to the
+//              next generation's rows, their shifted vectors rounded to FP32
+//              and split into high and low parts straight into the A operand
+//              in shared memory (the 128 targets are the products' M
+//              dimension);
+//   products   z = M y as Y M^T, three split passes accumulated in FP32 in
+//              tensor memory; the run's split M (the B operand, N = its padded
+//              D) is copied into shared memory by one bulk asynchronous copy
+//              when the CTA's run changes, while that item's trials are built;
+//   epilogue   the objective terms from TMEM (two threads per target, one per
+//              column half), the split error bound and the selection decisions
+//              it allows; the targets it cannot decide are re-evaluated in
+//              FP64 by the whole CTA;
+//   rows       rejected trials' rows overwritten by their targets, fitness
+//              values and the tile's best partial.
 //
 // There is no grid barrier.  Each run has an arrival counter: an item adds
-// one after its rows, fitness and best partial are written (release order).
-// Before a CTA builds trials of generation g of run r it waits (bounded)
-// until the counter shows every tile of r done with generation g - 1, then
-// reduces r's tile partials itself (the same order in every CTA) into the best
-// record and the stop rule of Sec. 7.3.4; the CTA that owns tile 0 of r
-// publishes them.  Items of a stopped run are skipped.  Every CTA processes
-// generation g - 1 of all its items before generation g, and the launch is
-// cooperative (every CTA resident), so the waits always end.  The population,
-// fitness and FP64 flags are double buffered by generation parity.
+// one after its rows, fitness and partial are written (release order).  Before
+// a CTA builds trials of generation g of run r it waits (bounded) until the
+// counter shows every tile of r done with generation g - 1, then reduces r's
+// tile partials itself (the same order in every CTA) into the best record and
+// the stop rule of Sec. 7.3.4; the CTA that owns tile 0 of r publishes them.
+// Items of a stopped run are skipped.  Every CTA processes generation g - 1 of
+// all its items before generation g, and the launch is cooperative (every CTA
+// resident), so the waits always end.  The population, fitness and FP64 flags
+// are double buffered by generation parity.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,33 +48,32 @@
 
 namespace de {
 
-constexpr int kPbRows = 8;                 // targets per item: one per warp
+constexpr int kPbThreads = 256;
 constexpr int kPbSliceRuns = 64;           // runs one CTA's slice may touch
 constexpr long long kPbSpin = 1LL << 22;   // polls of a run's arrival counter (with back-off)
 
 struct PbLayout {
-  uint32_t yop, mop, z, y, red, total;
+  uint32_t a, b, y, red, total;
 };
 
-// shared memory of a CTA for runs of at most kpad_max padded K and dp_max
-// padded row length
+// shared memory of a CTA for runs of at most kpad_max padded K (= padded N)
+// and dp_max row length: A (128 target rows, two parts), B (the split M, two
+// parts), two FP64 vectors for the FP64 decisions, their reduction slots
 __host__ __device__ inline PbLayout pb_layout(int kpad_max, int dp_max, int esz) {
   PbLayout L;
-  const uint32_t y_part = (uint32_t)(kpad_max * esz / 16) * 256u, m_part = (uint32_t)(kpad_max * esz / 16) * 2048u;
-  L.yop = 0;
-  L.mop = (2u * y_part + 1023u) / 1024u * 1024u;
-  L.z = L.mop + 2u * m_part;
-  L.y = L.z + (uint32_t)kPbRows * (uint32_t)(kpad_max + 4) * 4u;
-  L.y = (L.y + 15u) / 16u * 16u;
+  L.a = 0;
+  L.b = 2u * (uint32_t)kTileM * (uint32_t)(kpad_max * esz);  // a multiple of 4096
+  L.y = L.b + 2u * (uint32_t)kpad_max * (uint32_t)(kpad_max * esz);
   L.red = L.y + (uint32_t)(2 * dp_max) * 8u;
-  L.total = L.red + 2u * 256u * 8u;
+  L.total = L.red + 16u * 8u;
   return L;
 }
 
 template <int ESZ>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(kPbThreads, 1)
     k_persist_batch(const RunDesc* __restrict__ runs, const int4* __restrict__ items, const int2* __restrict__ slices,
-                    PersistCtl* ctl, unsigned* __restrict__ cnt, long long gens, int kpad_max, int dp_max) {
+                    PersistCtl* ctl, unsigned* __restrict__ cnt, long long gens, int kpad_max, int dp_max,
+                    uint32_t ncols) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = (int)blockIdx.x;
   const int2 sl = slices[cta];
@@ -70,37 +82,37 @@ __global__ void __launch_bounds__(256, 2)
 
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ RunDesc sR;
-  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_bar[2];  // [0] products done, [1] split M copied
   __shared__ uint32_t s_tmem;
-  __shared__ double s_f[kPbRows], s_ft[kPbRows];
-  __shared__ float s_tau[kPbRows], s_yn[kPbRows];
-  __shared__ uint8_t s_fx[kPbRows], s_flag[kPbRows];  // flag bit 0 accept, 1 decided in FP64, 2 pending FP64
-  __shared__ long long s_key[kPbRows];
-  __shared__ int s_blist[kPbRows];
-  __shared__ int s_nb, s_abort, s_have, s_mfail;
+  __shared__ float s_part[5][kTileM];
+  __shared__ double s_fi[kTileM], s_fnew[kTileM], s_ftrial[kTileM];
+  __shared__ float s_taunew[kTileM], s_yn[kTileM];
+  __shared__ uint8_t s_fx0[kTileM], s_fxnew[kTileM];
+  __shared__ uint8_t s_flag[kTileM];  // bit 0 accept, 1 decided in FP64, 2 pending FP64
+  __shared__ int s_blist[kTileM];
+  __shared__ double s_bf[kPbThreads / 32];
+  __shared__ long long s_bk[kPbThreads / 32];
+  __shared__ int s_bi[kPbThreads / 32];
+  __shared__ int s_nb, s_abort, s_issued, s_mfail;
   // per run of the slice: stopped, generation at launch, last generation
   // observed complete (loop index), owner of tile 0, best f of the last
-  // complete generation (FP32, for the FP64-band policy)
+  // complete generation (FP32, for the FP64-decision policy)
   __shared__ int s_rstop[kPbSliceRuns], s_rdone[kPbSliceRuns], s_rpub[kPbSliceRuns];
   __shared__ long long s_rgen0[kPbSliceRuns];
   __shared__ float s_rbest[kPbSliceRuns];
   static_assert(sizeof(RunDesc) % 8 == 0, "descriptor copied in 8-byte words");
 
   const PbLayout L = pb_layout(kpad_max, dp_max, ESZ);
-  uint8_t* sYop = smem + L.yop;
-  uint8_t* sMop = smem + L.mop;
-  float* zbuf = reinterpret_cast<float*>(smem + L.z);
+  uint8_t* sA = smem + L.a;
   double* sY = reinterpret_cast<double*>(smem + L.y);
   double* s_red = reinterpret_cast<double*>(smem + L.red);
-  const uint32_t bar_mma = smem_u32(&s_bar);
-  const uint32_t ncols = 64u;  // three accumulators of 128 lanes x 16 columns
+  const uint32_t bar_mma = smem_u32(&s_bar[0]), bar_b = smem_u32(&s_bar[1]);
   const uint32_t fmt = ESZ == 2 ? 1u : 2u;
-  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kCtaRowsMax >> 3) << 17) |
-                         ((uint32_t)(kTileM >> 4) << 24);
 
   // ---------------------------------------------------------------- set-up
   if (tid == 0) {
-    mbar_init(bar_mma, 3);  // one commit per issuing warp
+    mbar_init(bar_mma, 1);
+    mbar_init(bar_b, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
     s_mfail = 0;
@@ -120,24 +132,21 @@ __global__ void __launch_bounds__(256, 2)
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // the y operand starts at zero (rows past a tile's targets stay zero or
-  // stale; their products land in columns nobody reads)
-  for (uint32_t q = tid * 16u; q < L.mop; q += blockDim.x * 16u) *reinterpret_cast<uint4*>(smem + q) = make_uint4(0u, 0u, 0u, 0u);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
 
   int cur_run = -1;
-  double tr[4], tx[4], osh[4];
-  uint32_t mma_phase = 0;
+  uint32_t mma_phase = 0, b_phase = 0;
+  bool b_wait = false;  // (thread 0) a copy of the split M is in flight
   bool abort = false;
 
   // the stop rule of run r (slice index q) after its generation g, from the
   // tile partials of g: warp 0 reduces, lane 0 decides and, for the owner of
   // tile 0, publishes
   auto reduce_run = [&](const RunDesc& R, int q, int64_t g) {
-    const int nt = (R.np + kPbRows - 1) / kPbRows;
+    const int nt = R.ntiles_tc;
     Best b;
     b.init();
     const BestPartial* pp = R.part + (size_t)(g & 1) * nt;
@@ -166,8 +175,7 @@ __global__ void __launch_bounds__(256, 2)
   // wait (warp 0, bounded) until every tile of run r finished generation
   // number `k` of this launch (k >= 1)
   auto wait_run = [&](const RunDesc& R, int r, int k) -> bool {
-    const int nt = (R.np + kPbRows - 1) / kPbRows;
-    const unsigned target = (unsigned)k * (unsigned)nt;
+    const unsigned target = (unsigned)k * (unsigned)R.ntiles_tc;
     for (long long p = 0; p < kPbSpin; ++p) {
       unsigned v;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt + r) : "memory");
@@ -188,14 +196,31 @@ __global__ void __launch_bounds__(256, 2)
       const int r = w.x, q = r - run_lo;
       if (s_rstop[q]) continue;  // uniform: written before the last barrier
       if (r != cur_run) {
-        // the run's descriptor, shift and split M
+        // the run's descriptor; its split M follows asynchronously (the
+        // products of the previous item, which read the old one, are done)
         __syncthreads();
         for (int k = tid; k < (int)(sizeof(RunDesc) / 8); k += blockDim.x)
           reinterpret_cast<uint64_t*>(&sR)[k] = reinterpret_cast<const uint64_t*>(runs + r)[k];
         __syncthreads();
-        cta_load_m<ESZ>(sR, sMop, cta_m_part(sR));
-#pragma unroll
-        for (int e = 0; e < 4; ++e) osh[e] = 4 * lane + e < sR.d ? sR.o[4 * lane + e] : 0.0;
+        if (tid == 0) {
+          bool ok = true;
+          if (b_wait) {  // the previous copy (of a run whose items were all skipped) lands first
+            ok = mbar_wait(bar_b, b_phase);
+            if (ok) {
+              b_phase ^= 1u;
+              b_wait = false;
+            } else {
+              atomicOr(&sR.st->err, kErrTimeout);
+              atomicExch(&ctl->abort, 1);
+              s_abort = 1;
+            }
+          }
+          if (ok) {
+            mbar_expect_tx(bar_b, (uint32_t)sR.b_tile_bytes);
+            bulk_g2s(smem_u32(smem + L.b), sR.B, (uint32_t)sR.b_tile_bytes, bar_b);
+            b_wait = true;
+          }
+        }
         cur_run = r;
       }
       const RunDesc& R = sR;
@@ -210,7 +235,6 @@ __global__ void __launch_bounds__(256, 2)
       }
       if (tid == 0) {
         s_nb = 0;
-        s_have = 1;
         if (*(volatile int*)&ctl->abort) s_abort = 1;
       }
       __syncthreads();
@@ -223,226 +247,310 @@ __global__ void __launch_bounds__(256, 2)
       const int cur = (int)((g - 1) & 1), nxt = cur ^ 1;
       const double* __restrict__ X = R.X[cur];
       double* __restrict__ Xn = R.X[nxt];
-      const uint32_t y_part = cta_y_part(R), m_part = cta_m_part(R);
-      const int zs = cta_zstride(R);
-      if (tid < nrows) {
-        const int i = row0 + tid;
-        s_f[tid] = R.f[cur][i];
-        s_fx[tid] = R.fx[cur][i];
-        s_tau[tid] = R.tau[i];
+      const uint32_t a_part = (uint32_t)(R.a_tile_bytes / 2), b_part = (uint32_t)(R.b_tile_bytes / 2);
+
+      // the selection inputs of row m (TMEM lane), fetched while the trials
+      // are built; column half h of the epilogue
+      const int m = 32 * (warp & 3) + lane, h = warp >> 2;
+      double pf_fi = 0.0;
+      float pf_tau = 0.f;
+      uint8_t pf_fx = 1;
+      if (h == 0 && m < nrows) {
+        const int i = row0 + m;
+        pf_fi = __ldcg(&R.f[cur][i]);
+        pf_fx = __ldcg(&R.fx[cur][i]);
+        pf_tau = __ldcg(&R.tau[i]);
       }
 
-      // ---- 1. trials (one target per warp) -> registers and the y operand
-      if (warp < nrows) {
-        const int i = row0 + warp;
-        const int j0 = 4 * lane;
-        const TrialSetup ts = trial_setup(R, (uint32_t)i, g, lane);
-        ChunkIn cin;
-        double t[4] = {0.0, 0.0, 0.0, 0.0};
-        uint32_t bits = 0;
-        if (j0 < d) {
-          trial_load(R, X, ts, (uint32_t)i, g, j0, cin);
-          bits = trial_compute(R, ts, j0, cin, t);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) tx[e] = cin.xi[e];
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) tr[e] = t[e];
-        float yn2 = 0.f;
-        if (j0 < R.kpad) {
-          float y[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            y[e] = (j0 + e < d) ? to_f32_rn(shifted(t[e], osh[e], R)) : 0.f;
-            yn2 += y[e] * y[e];
+      // ---- 1. trials, R.lpt lanes per target (one 4-coordinate chunk per
+      // lane covers the padded row: d <= 128), round rd of warp w holding
+      // targets (8 rd + w) tpw ..; the trial rows go straight to the next
+      // generation's rows (a rejected trial is overwritten by its target in
+      // step 6).  The loads of round rd + 1 are in flight while round rd is
+      // computed (two register sets).
+      {
+        const int lpt = R.lpt, tpw = 32 / lpt, sub = lane & (lpt - 1), j0 = 4 * sub;
+        const int per_round = (kPbThreads / 32) * tpw;
+        const int rounds = (nrows + per_round - 1) / per_round;
+        struct Unit {
+          TrialSetup s;
+          ChunkIn c;
+          int m;
+          bool v;
+        };
+        auto prep = [&](int rd, Unit& U) {
+          if (rd >= rounds) return;
+          const int mm = (rd * (kPbThreads / 32) + warp) * tpw + lane / lpt;
+          U.v = mm < nrows;
+          U.m = U.v ? mm : nrows - 1;  // idle segments repeat a valid target without writing
+          U.s = trial_setup(R, (uint32_t)(row0 + U.m), g, sub, 0u, U.v);
+          if (j0 < d) trial_load(R, X, U.s, (uint32_t)(row0 + U.m), g, j0, U.c);
+        };
+        auto finish = [&](int rd, const Unit& U) {
+          if (rd >= rounds) return;  // uniform
+          const int i = row0 + U.m;
+          double t[4] = {0.0, 0.0, 0.0, 0.0};
+          uint32_t bits = 0;
+          if (j0 < d) {
+            bits = trial_compute(R, U.s, j0, U.c, t);
+            if (U.v) {
+              double* row = Xn + (size_t)i * dp + j0;
+              *reinterpret_cast<double2*>(row) = make_double2(t[0], t[1]);
+              *reinterpret_cast<double2*>(row + 2) = make_double2(t[2], t[3]);
+            }
           }
-          cta_store_split4<ESZ>(sYop, y_part, warp, j0, y);
-        }
-        if (R.dbg_trial) trial_debug(R, (uint32_t)i, j0, lane, bits, t);
+          float yn2 = 0.f;
+          if (j0 < R.kpad) {
+            float y[4];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) yn2 += __shfl_xor_sync(0xffffffffu, yn2, o);
-        if (lane == 0) s_yn[warp] = sqrtf(yn2);
+            for (int e = 0; e < 4; ++e) {
+              y[e] = (j0 + e < d) ? to_f32_rn(shifted(t[e], __ldg(R.o + j0 + e), R)) : 0.f;
+              yn2 += y[e] * y[e];
+            }
+            if (U.v) store_split4<ESZ>(sA, a_part, U.m, j0, y);
+          }
+          if (R.dbg_trial) trial_debug(R, (uint32_t)i, j0, lane, bits, t, lpt, U.v);
+          for (int o = lpt >> 1; o > 0; o >>= 1) yn2 += __shfl_xor_sync(0xffffffffu, yn2, o);
+          if (U.v && sub == 0) s_yn[U.m] = sqrtf(yn2);
+        };
+        Unit ua, ub;
+        prep(0, ua);
+        prep(1, ub);
+        for (int rd = 0; rd < rounds; rd += 2) {
+          finish(rd, ua);
+          prep(rd + 2, ua);
+          finish(rd + 1, ub);
+          prep(rd + 3, ub);
+        }
       }
-      // generic-proxy writes of the operands become visible to the tensor
-      // cores' async proxy
+      // generic-proxy writes of A become visible to the tensor cores' async proxy
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
 
-      // ---- 2. split products: warps 0, 1, 2 issue one pass each
-      if (warp < 3 && lane == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int ksteps = R.kpad * ESZ / 32;
-        const int pass = warp;
-        const uint64_t dm = smem_desc(smem_u32(sMop) + (pass == 1 ? m_part : 0u), 2048u, 128u);
-        const uint64_t dy = smem_desc(smem_u32(sYop) + (pass == 2 ? y_part : 0u), 256u, 128u);
-        for (int ks = 0; ks < ksteps; ++ks)
-          mma_split<ESZ>(tmem + 16u * (uint32_t)pass, dm + (uint64_t)(ks * 256), dy + (uint64_t)(ks * 32), idesc,
-                         ks > 0 ? 1u : 0u);
-        mma_commit(bar_mma);
-      }
-      // ---- 3a. warps 0..3 copy the accumulators' columns 0..7 (targets) of
-      // lanes 32 w .. 32 w + 31 (coordinates) to shared memory as rows of z
-      if (warp < 4) {
-        const bool ok = mbar_wait(bar_mma, mma_phase);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (__all_sync(0xffffffffu, ok)) {
-          float v[8], w1[8], w2[8];
-          const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
-          tmem_ld8(ta, v);
-          tmem_ld8(ta + 16u, w1);
-          tmem_ld8(ta + 32u, w2);
-          const int j = 32 * warp + lane;
-          if (j < d) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-              if (e < nrows) zbuf[(size_t)e * zs + j] = (v[e] + w1[e]) + w2[e];
+      // ---- 2. split products Z = Y M^T (thread 0 issues all three passes)
+      if (tid == 0) {
+        bool ok = !s_abort;
+        if (ok && b_wait) {
+          ok = mbar_wait(bar_b, b_phase);
+          if (ok) {
+            b_phase ^= 1u;
+            b_wait = false;
           }
-        } else if (lane == 0) {
+        }
+        if (ok) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int ksteps = R.kpad * ESZ / 32;
+          const uint32_t a0 = smem_u32(sA), b0 = smem_u32(smem + L.b), bk = (uint32_t)(R.ntn / 8) * 128u;
+          const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(R.ntn >> 3) << 17) |
+                                 ((uint32_t)(kTileM >> 4) << 24);
+          for (int ks = 0; ks < ksteps; ++ks) {
+#pragma unroll
+            for (int pass = 0; pass < 3; ++pass) {
+              const uint32_t a = a0 + (pass == 2 ? a_part : 0u) + (uint32_t)ks * 2u * 2048u;
+              const uint32_t b = b0 + (pass == 1 ? b_part : 0u) + (uint32_t)ks * 2u * bk;
+              mma_split<ESZ>(tmem, smem_desc(a, 2048u, 128u), smem_desc(b, bk, 128u), idesc,
+                             (ks > 0 || pass > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(bar_mma);
+        } else {
           atomicOr(&R.st->err, kErrTimeout);
           atomicExch(&ctl->abort, 1);
           s_abort = 1;
-          s_have = 0;
+        }
+        s_issued = ok ? 1 : 0;
+      }
+      __syncthreads();
+
+      // ---- 3. epilogue: objective terms of row m, column half h, from TMEM
+      const bool issued = s_issued != 0;
+      bool have = false;
+      if (issued) {
+        have = mbar_wait(bar_mma, mma_phase);
+        if (!have && lane == 0) {
+          atomicOr(&R.st->err, kErrTimeout);
+          atomicExch(&ctl->abort, 1);
+          s_abort = 1;
           s_mfail = 1 + (int)mma_phase;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mma_phase ^= 1u;
       }
-      mma_phase ^= 1u;
+      have = __all_sync(0xffffffffu, have);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      EpiAcc acc_{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const int half = R.ntn / 2, cb = h * half;
+      const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+      if (have) {
+        for (int c = 0; c < half; c += 32) {
+          float v[32];
+          const int wc = min(32, half - c);  // a multiple of 8
+          const uint32_t ta = tmem + lane_base + (uint32_t)(cb + c);
+          if (wc == 32) {
+            tmem_ld_cols32(ta, v);
+          } else if (wc == 24) {
+            tmem_ld_cols16(ta, v);
+            tmem_ld8(ta + 16u, v + 16);
+          } else if (wc == 16) {
+            tmem_ld_cols16(ta, v);
+          } else {
+            tmem_ld8(ta, v);
+          }
+          epi_dispatch(obj, v, wc, cb + c, d, c == 0, acc_);
+        }
+        if (obj == kObjRosenbrock && h == 0 && half < d) {
+          // the term of the last column of this half needs the next column
+          const float tn = tmem_ld1(tmem + lane_base + (uint32_t)half) + 1.f;
+          const float aa = tn - acc_.prev_t * acc_.prev_t, bb = acc_.prev_t - 1.f;
+          acc_.a1 += fmaf(100.f * aa, aa, bb * bb);
+          acc_.aG += 400.f * fabsf(acc_.prev_t) * fabsf(aa) + 2.f * fabsf(bb) + 200.f * fabsf(aa);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      if (h == 1) {
+        s_part[0][m] = acc_.a1;
+        s_part[1][m] = acc_.a2;
+        s_part[2][m] = acc_.a3;
+        s_part[3][m] = acc_.aS;
+        s_part[4][m] = acc_.aG;
+      }
       __syncthreads();
 
-      // ---- 3b. FP32 objective (16 threads per target) and the decisions the
-      // split error bound allows
-      const bool have = s_have != 0;
-      {
-        const int rr = tid >> 4, sub = tid & 15;
-        const bool valid = rr < nrows;
-        EpiAcc acc_{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (valid && have) epi_strided_dispatch(obj, zbuf + (size_t)rr * zs, sub, d, acc_);
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-          acc_.a1 += __shfl_xor_sync(0xffffffffu, acc_.a1, o);
-          acc_.aS += __shfl_xor_sync(0xffffffffu, acc_.aS, o);
-          acc_.aG += __shfl_xor_sync(0xffffffffu, acc_.aG, o);
-        }
+      // ---- 4. the decisions the split error bound allows (Sec. 2, selection)
+      if (h == 0 && m < nrows) {
+        const float s1 = acc_.a1 + s_part[0][m], s2 = acc_.a2 + s_part[1][m], s3 = acc_.a3 + s_part[2][m];
+        float S = acc_.aS + s_part[3][m], G = acc_.aG + s_part[4][m];
+        float fs;
         if (obj == kObjAckley) {
-#pragma unroll
-          for (int o = 8; o > 0; o >>= 1) {
-            acc_.a2 += __shfl_xor_sync(0xffffffffu, acc_.a2, o);
-            acc_.a3 += __shfl_xor_sync(0xffffffffu, acc_.a3, o);
-          }
+          const float rq = sqrtf(s1 / (float)d);
+          const float e1 = expf(-0.2f * rq), e2 = expf(s2 / (float)d);
+          fs = 20.f + 2.718281828f - 20.f * e1 - e2;
+          S = 20.f + 2.718281828f + 20.f * e1 + expf(S / (float)d);
+          G = (rq > 0.f ? 4.f * e1 * s3 / ((float)d * rq) : 3.0e38f) + 6.283185307f * e2;
+        } else {
+          if (obj != kObjRastrigin) S = s1;
+          fs = s1;
         }
-        if (sub == 0 && valid) {
-          uint8_t flag = 0;
-          if (have) {
-            const float s1 = acc_.a1, s2 = acc_.a2, s3 = acc_.a3;
-            float S = acc_.aS, G = acc_.aG;
-            float fs;
-            if (obj == kObjAckley) {
-              const float rq = sqrtf(s1 / (float)d);
-              const float e1 = expf(-0.2f * rq), e2 = expf(s2 / (float)d);
-              fs = 20.f + 2.718281828f - 20.f * e1 - e2;
-              S = 20.f + 2.718281828f + 20.f * e1 + expf(S / (float)d);
-              G = (rq > 0.f ? 4.f * e1 * s3 / ((float)d * rq) : 3.0e38f) + 6.283185307f * e2;
-            } else {
-              if (obj != kObjRastrigin) S = s1;
-              fs = s1;
-            }
-            const float tau = 2.f * R.band_u * G * R.rownorm * s_yn[rr] + (float)d * 0x1.0p-21f * S + 1e-30f;
-            const float fif = to_f32_rn(s_f[rr]);
-            const float tif = s_fx[rr] ? 0.f : s_tau[rr];
-            const float mrg = 0x1.0p-22f * fabsf(fif);
-            const float bp = s_rbest[q];
-            const bool sure_reject = fs - tau > fif + tif + mrg;
-            const bool sure_accept = fs + tau < fif - tif - mrg;
-            const bool ambiguous = !sure_reject && !sure_accept;
-            const bool may_be_best = R.band_all && fs - tau <= bp + 0x1.0p-22f * fabsf(bp);
-            const bool near = fs - tau <= R.near_thr || fif - tif <= R.near_thr;
-            // only a trial the split bound cannot place on one side of the
-            // stop target needs FP64 for the stop rule
-            const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f &&
-                                  !(fs + tau < (float)R.target * 0.999f);
-            const double fsd = f64_of_f32(fs);
-            s_ft[rr] = fsd;
-            if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !(fif == fif)) {
-              s_blist[atomicAdd(&s_nb, 1)] = rr;
-              flag = 4;
-            } else if (sure_accept || (ambiguous && fs <= fif)) {
-              flag = 1;
-              s_f[rr] = fsd;
-              s_fx[rr] = 0;
-              s_tau[rr] = tau;
-            }
-          }
-          s_flag[rr] = flag;
+        // error bound of fs: split products (relative to |M||y|) through the
+        // derivative bound G, plus FP32 rounding of the terms and their sum
+        const float tau = 2.f * R.band_u * G * R.rownorm * s_yn[m] + (float)d * 0x1.0p-21f * S + 1e-30f;
+        const float fif = to_f32_rn(pf_fi);
+        const float tif = pf_fx ? 0.f : pf_tau;
+        const float mrg = 0x1.0p-22f * fabsf(fif);
+        const float bp = s_rbest[q];
+        const bool sure_reject = fs - tau > fif + tif + mrg;
+        const bool sure_accept = fs + tau < fif - tif - mrg;
+        const bool ambiguous = !sure_reject && !sure_accept;
+        const bool may_be_best = R.band_all && fs - tau <= bp + 0x1.0p-22f * fabsf(bp);
+        const bool near = fs - tau <= R.near_thr || fif - tif <= R.near_thr;
+        // only a trial the split bound cannot place on one side of the stop
+        // target needs FP64 for the stop rule
+        const bool may_stop = R.target > 0.0 && fs - tau < (float)R.target * 1.001f &&
+                              !(fs + tau < (float)R.target * 0.999f);
+        const double fsd = f64_of_f32(fs);
+        s_ftrial[m] = fsd;
+        s_fi[m] = pf_fi;
+        s_fx0[m] = pf_fx;
+        if (!have) {
+          s_flag[m] = 0;  // the launch is abandoned; keep the target
+          s_fnew[m] = pf_fi;
+          s_fxnew[m] = pf_fx;
+          s_taunew[m] = pf_tau;
+        } else if ((ambiguous && (R.band_all || near)) || may_be_best || may_stop || !(fs == fs) || !(fif == fif)) {
+          s_blist[atomicAdd(&s_nb, 1)] = m;
+          s_flag[m] = 4;
+        } else {
+          // decided on the split values (an undecidable comparison far from the
+          // optimum goes to the smaller split value, ties to the trial)
+          const bool acc = sure_accept || (ambiguous && fs <= fif);
+          s_flag[m] = acc ? 1 : 0;
+          s_fnew[m] = acc ? fsd : pf_fi;
+          s_fxnew[m] = acc ? 0 : pf_fx;
+          s_taunew[m] = acc ? tau : pf_tau;
         }
       }
       __syncthreads();
 
-      // ---- 3c. FP64 decisions of the listed targets, by the whole CTA
+      // ---- 5. FP64 decisions of the listed targets, by the whole CTA, in
+      // list order (the order does not change any value)
       const int nb = s_nb;
       for (int b = 0; b < nb; ++b) {
-        const int lr = s_blist[b];
-        const bool need_t = !s_fx[lr];
-        if (lr == warp) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int j = 4 * lane + e;
-            if (j >= d) continue;
-            sY[j] = shifted(tr[e], osh[e], R);
-            if (need_t) sY[dp + j] = shifted(tx[e], osh[e], R);
-          }
+        const int lm = s_blist[b], i = row0 + lm;
+        const bool need_t = !s_fx0[lm];
+        for (int j = tid; j < d; j += blockDim.x) {
+          const double oj = __ldg(R.o + j);
+          sY[j] = shifted(__ldcg(Xn + (size_t)i * dp + j), oj, R);
+          if (need_t) sY[dp + j] = shifted(__ldcg(X + (size_t)i * dp + j), oj, R);
         }
         __syncthreads();
         const double ft = cta_fitness_fp64(R, sY, s_red);
-        const double fi = need_t ? cta_fitness_fp64(R, sY + dp, s_red) : s_f[lr];
+        const double fi = need_t ? cta_fitness_fp64(R, sY + dp, s_red) : s_fi[lm];
         if (tid == 0) {
           const bool acc = fit_key(ft) <= fit_key(fi) && fit_key(ft) != 0x7FFFFFFFFFFFFFFFLL;  // NaN ranks last
-          s_ft[lr] = ft;
-          s_f[lr] = acc ? ft : fi;
-          s_fx[lr] = 1;
-          s_tau[lr] = 0.f;
-          s_flag[lr] = (acc ? 1 : 0) | 2;
+          s_ftrial[lm] = ft;
+          s_fnew[lm] = acc ? ft : fi;
+          s_fxnew[lm] = 1;
+          s_taunew[lm] = 0.f;
+          s_flag[lm] = (acc ? 1 : 0) | 2;
         }
         __syncthreads();
       }
 
-      // ---- 4. next-generation rows, fitness, debug capture, best partial
-      if (warp < nrows) {
-        const int i = row0 + warp;
-        const bool acc = s_flag[warp] & 1;
-        const int j0 = 4 * lane;
-        if (j0 < d) {
-          double* dst = Xn + (size_t)i * dp + j0;
-          const double* src = acc ? tr : tx;
-          *reinterpret_cast<double2*>(dst) = make_double2(src[0], src[1]);
-          *reinterpret_cast<double2*>(dst + 2) = make_double2(src[2], src[3]);
-        }
-      }
+      // ---- 6. next-generation fitness, rows, debug capture, best partial
+      Best bb;
+      bb.init();
       if (tid < nrows) {
         const int i = row0 + tid;
-        R.f[nxt][i] = s_f[tid];
-        R.fx[nxt][i] = s_fx[tid];
-        R.tau[i] = s_tau[tid];
-        s_key[tid] = fit_key(s_f[tid]);
+        const uint8_t fl = s_flag[tid];
+        R.f[nxt][i] = s_fnew[tid];
+        R.fx[nxt][i] = s_fxnew[tid];
+        R.tau[i] = s_taunew[tid];
         if (R.dbg_ftrial) {
-          R.dbg_ftrial[i] = s_ft[tid];
-          R.dbg_accept[i] = s_flag[tid] & 1;
-          R.dbg_fp64[i] = (s_flag[tid] >> 1) & 1;
+          R.dbg_ftrial[i] = s_ftrial[tid];
+          R.dbg_accept[i] = fl & 1;
+          R.dbg_fp64[i] = (fl >> 1) & 1;
         }
+        bb.offer(s_fnew[tid], i);
+      }
+      {
+        // a rejected trial's row becomes its target's again: warp w copies
+        // rows w, w + 8, .. (dp / 2 <= 64 double2 each, two per lane), the
+        // loads of eight rows issued before their stores
+        const int dp2 = dp / 2;
+        for (int e0 = warp; e0 < nrows; e0 += 8 * (kPbThreads / 32)) {
+          double2 v[8][2];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int e = e0 + k * (kPbThreads / 32);
+            const bool cp = e < nrows && !(s_flag[e] & 1);
+            const double2* src = reinterpret_cast<const double2*>(X + (size_t)(row0 + e) * dp);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh)
+              if (cp && lane + 32 * hh < dp2) v[k][hh] = __ldcg(src + lane + 32 * hh);
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int e = e0 + k * (kPbThreads / 32);
+            const bool cp = e < nrows && !(s_flag[e] & 1);
+            double2* dst = reinterpret_cast<double2*>(Xn + (size_t)(row0 + e) * dp);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh)
+              if (cp && lane + 32 * hh < dp2) dst[lane + 32 * hh] = v[k][hh];
+          }
+        }
+      }
+      bb.warp_reduce();
+      if (lane == 0) {
+        s_bf[warp] = bb.f;
+        s_bk[warp] = bb.k;
+        s_bi[warp] = bb.i;
       }
       __syncthreads();
       if (tid == 0) {
-        // the tile's best (lowest key, then lowest index; NaN never)
-        long long bk = 0x7FFFFFFFFFFFFFFFLL;
-        int bi = -1;
-        for (int k = 0; k < nrows; ++k)
-          if (s_key[k] != 0x7FFFFFFFFFFFFFFFLL && (bi < 0 || s_key[k] < bk)) {
-            bk = s_key[k];
-            bi = k;
-          }
-        const int nt = (R.np + kPbRows - 1) / kPbRows;
-        BestPartial* pp = R.part + (size_t)(g & 1) * nt + tile;
-        pp->f = bi >= 0 ? s_f[bi] : CUDART_INF;
-        pp->idx = bi >= 0 ? row0 + bi : -1;
+        bb.init();
+        for (int k = 0; k < kPbThreads / 32; ++k) bb.take(s_bf[k], s_bk[k], s_bi[k]);
+        BestPartial* pp = R.part + (size_t)(g & 1) * R.ntiles_tc + tile;
+        pp->f = bb.f;
+        pp->idx = bb.i;
         atomicAdd(&R.stats[0], (unsigned long long)nb);
         atomicAdd(&R.stats[1], (unsigned long long)nrows);
         // release: the item's rows, fitness and partial (ordered before by the
@@ -465,8 +573,11 @@ __global__ void __launch_bounds__(256, 2)
       reduce_run(R, q, s_rgen0[q] + gens);
     }
   }
-  // products still in flight after a failed wait must land before TMEM is freed
-  if (tid == 0 && s_mfail) mbar_wait(bar_mma, (uint32_t)(s_mfail - 1));
+  // copies and products still in flight land before the CTA leaves and frees TMEM
+  if (tid == 0) {
+    if (b_wait) mbar_wait(bar_b, b_phase);
+    if (s_mfail) mbar_wait(bar_mma, (uint32_t)(s_mfail - 1));
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
@@ -477,43 +588,73 @@ static const void* pb_kernel(int prec) {
   return prec == DE_PREC_BF16X3 ? (const void*)k_persist_batch<2> : (const void*)k_persist_batch<4>;
 }
 
+// Estimated time of one item (arbitrary units): a fixed part (wait, products,
+// barriers, release), trial rounds of R.lpt lanes per target, the rows written
+// and the epilogue columns.  Used only to balance the slices.
+static long long item_cost(const RunDesc& R, int nrows) {
+  const long long rounds = ((long long)nrows * R.lpt + kPbThreads - 1) / kPbThreads;
+  return 400 + 100 * rounds + (long long)nrows * R.dp / 64 + 4 * R.ntn;
+}
+
 bool pbatch_plan(PbPlan& pp, const std::vector<RunDesc>& runs, int prec) {
   pp.ok = false;
   const int nruns = (int)runs.size();
   if (nruns < 2) return false;
   int kpad_max = 16, dp_max = 4;
   for (const RunDesc& R : runs) {
-    // (the three-kernel path's K chunking does not apply: the whole split M
-    // is copied into shared memory)
-    if (R.nn != 1 || R.d > 128 || R.ntn > 128 || R.strategy != 0 || R.jde || R.obj > kObjAckley)
-      return false;
+    // one N tile (N = the padded D), the whole split M resident in shared
+    // memory (the three-kernel path's K chunking does not apply)
+    if (R.nn != 1 || R.d > 128 || R.ntn != R.kpad || R.strategy != 0 || R.jde || R.obj > kObjAckley) return false;
     kpad_max = std::max(kpad_max, R.kpad);
     dp_max = std::max(dp_max, R.dp);
   }
-  const size_t smem = pb_layout(kpad_max, dp_max, prec == DE_PREC_BF16X3 ? 2 : 4).total;
-  if (smem > 220 * 1024) return false;
+  const int esz = prec == DE_PREC_BF16X3 ? 2 : 4;
+  const size_t smem = pb_layout(kpad_max, dp_max, esz).total;
   const void* k = pb_kernel(prec);
-  int per_sm = 0, dev = 0, nsm = 0;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      cudaGetDevice(&dev) != cudaSuccess ||
+  int per_sm = 0, dev = 0, nsm = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1) {
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  // items: tiles of at most kPbRows targets, in run order
+  if (smem + fa.sharedSizeBytes > (size_t)optin) return false;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kPbThreads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  uint32_t ncols = 32;
+  while ((int)ncols < kpad_max) ncols *= 2;
+  // items: the 128-target tiles of every run, in run order
   std::vector<int4> items;
+  std::vector<long long> cost;
   for (int r = 0; r < nruns; ++r)
-    for (int t = 0, row = 0; row < runs[r].np; ++t, row += kPbRows)
-      items.push_back(make_int4(r, t, row, std::min(kPbRows, runs[r].np - row)));
+    for (int t = 0, row = 0; row < runs[r].np; ++t, row += kTileM) {
+      const int n = std::min(kTileM, runs[r].np - row);
+      items.push_back(make_int4(r, t, row, n));
+      cost.push_back(item_cost(runs[r], n));
+    }
   const int nitems = (int)items.size();
   const int nct = std::min(per_sm * nsm, nitems);
-  // contiguous slices of nearly equal item counts
+  // contiguous slices of nearly equal estimated time: CTA c takes the items
+  // whose cost midpoint falls in [W c / nct, W (c + 1) / nct)
+  long long W = 0;
+  for (long long c : cost) W += c;
   std::vector<int2> slices(nct);
-  for (int c = 0; c < nct; ++c) {
-    const int lo = (int)((long long)nitems * c / nct), hi = (int)((long long)nitems * (c + 1) / nct);
-    slices[c] = make_int2(lo, hi);
-    if (hi > lo && items[hi - 1].x - items[lo].x + 1 > kPbSliceRuns) return false;
+  {
+    int lo = 0;
+    long long acc = 0;
+    for (int c = 0; c < nct; ++c) {
+      int hi = lo;
+      const long long lim = W * (c + 1) / nct;
+      while (hi < nitems && (c == nct - 1 || acc + cost[hi] / 2 < lim)) acc += cost[hi++];
+      slices[c] = make_int2(lo, hi);
+      if (hi > lo && items[hi - 1].x - items[lo].x + 1 > kPbSliceRuns) return false;
+      lo = hi;
+    }
   }
   if (cudaMalloc(&pp.d_items, items.size() * sizeof(int4)) != cudaSuccess ||
       cudaMalloc(&pp.d_slices, slices.size() * sizeof(int2)) != cudaSuccess ||
@@ -530,6 +671,7 @@ bool pbatch_plan(PbPlan& pp, const std::vector<RunDesc>& runs, int prec) {
   pp.prec = prec;
   pp.kpad_max = kpad_max;
   pp.dp_max = dp_max;
+  pp.ncols = ncols;
   pp.ok = true;
   return true;
 }
@@ -552,9 +694,10 @@ cudaError_t pbatch_launch(const PbPlan& pp, const RunDesc* runs, PersistCtl* ctl
   const int2* slices = pp.d_slices;
   unsigned* cnt = pp.d_cnt;
   int kpad_max = pp.kpad_max, dp_max = pp.dp_max;
+  uint32_t ncols = pp.ncols;
   void* args[] = {(void*)&runs, (void*)&items, (void*)&slices, (void*)&ctl, (void*)&cnt, (void*)&gens,
-                  (void*)&kpad_max, (void*)&dp_max};
-  return cudaLaunchCooperativeKernel(pb_kernel(pp.prec), dim3((unsigned)pp.nct), dim3(256), args, pp.smem, s);
+                  (void*)&kpad_max, (void*)&dp_max, (void*)&ncols};
+  return cudaLaunchCooperativeKernel(pb_kernel(pp.prec), dim3((unsigned)pp.nct), dim3(kPbThreads), args, pp.smem, s);
 }
 
 }  // namespace de
