@@ -89,7 +89,7 @@ def _load():
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, _dp, _dp, _i32p, ctypes.c_double, ctypes.c_uint64,
                                        ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
-                                       ctypes.c_double, _dp, _dp, _dp, _dp, _i64p, ctypes.c_int]
+                                       ctypes.c_double, _dp, _dp, _dp, _dp, _i64p, ctypes.c_int, ctypes.c_int]
         lib.or_run_islands.restype = ctypes.c_int64
         lib.or_init_population.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_uint64, ctypes.c_uint32, _dp]
@@ -383,9 +383,12 @@ def island_ranked(f, n, worst=False):
 
 
 def run_islands(m, interval, nmig, np_, d, F, CR, lo, hi, obj, o, M, seed, max_generations, max_evals=0,
-                target_error=1e-8, run_id=0, scale=1.0, perm=None, strategy=0, jde=False, threads=1):
+                target_error=1e-8, run_id=0, scale=1.0, perm=None, strategy=0, jde=False, threads=1,
+                asynchronous=False):
     """The island model: returns (X [m, np, d], f [m, np], generations,
-    evaluations of one island, F_i [m, np], CR_i [m, np])."""
+    evaluations of one island, F_i [m, np], CR_i [m, np]).  asynchronous:
+    migrants arrive one migration interval late (posted at the previous
+    migration point)."""
     X = np.zeros((m, np_, d))
     f = np.zeros((m, np_))
     jF = np.zeros((m, np_))
@@ -394,5 +397,5 @@ def run_islands(m, interval, nmig, np_, d, F, CR, lo, hi, obj, o, M, seed, max_g
     g = _load().or_run_islands(m, interval, nmig, np_, d, F, CR, lo, hi, obj, _p(_f64(o)), _p(_f64(M)),
                                _p(_i32(perm), _i32p), scale, seed, run_id, int(strategy), 1 if jde else 0,
                                max_generations, max_evals, target_error, _p(X), _p(f), _p(jF), _p(jCR),
-                               ctypes.byref(ev), threads)
+                               ctypes.byref(ev), threads, 1 if asynchronous else 0)
     return X, f, int(g), int(ev.value), jF, jCR

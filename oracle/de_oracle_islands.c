@@ -18,6 +18,16 @@
  *     (descending f, NaN first, higher index first), the q-th best into the
  *     q-th worst; all migrants are taken from the populations before any
  *     replacement.  A migrant keeps its fitness (and, with jDE, its F and CR);
+ *   - asynchronous migration (Sec. 3.2 names synchronous and asynchronous
+ *     strategies; in the GPU form of Sec. 5.4 the asynchronous one migrates
+ *     inside the generation kernel, so an island may receive migrants of
+ *     another island that is ahead or behind it, which the paper notes makes
+ *     runs irreproducible).  Read here with that staleness fixed to one
+ *     interval: at every migration point each island posts its nmig best
+ *     (the order above) to a mailbox, and takes, into its nmig worst, the
+ *     migrants its ring predecessor posted at the previous migration point
+ *     (none at the first).  No island then needs another island's state of
+ *     the same generation, and the result does not depend on timing;
  *   - the model stops, all islands together, once the best f over all islands
  *     is below the target, or the per-island evaluations reach max_evals, or
  *     max_generations have run (tested before every generation, as a single
@@ -72,7 +82,8 @@ int64_t or_run_islands(int m, int interval, int nmig, int np, int d, double F, d
                        int obj, const double* o, const double* M, const int32_t* perm, double scale,
                        uint64_t seed, uint32_t run_id0, int strategy, int jde,
                        int64_t max_generations, int64_t max_evals, double target_error,
-                       double* X, double* fX, double* jF, double* jCR, int64_t* evals_out, int threads)
+                       double* X, double* fX, double* jF, double* jCR, int64_t* evals_out, int threads,
+                       int async_mig)
 {
     const size_t P = (size_t)np * d;
     double* Xn = (double*)malloc(sizeof(double) * P);
@@ -83,6 +94,12 @@ int64_t or_run_islands(int m, int interval, int nmig, int np, int d, double F, d
     double* mf = (double*)malloc(sizeof(double) * (size_t)m * nmig);
     double* mF = (double*)malloc(sizeof(double) * (size_t)m * nmig);
     double* mC = (double*)malloc(sizeof(double) * (size_t)m * nmig);
+    /* asynchronous migration: the migrants posted at the previous migration point */
+    double* px = (double*)malloc(sizeof(double) * (size_t)m * nmig * d);
+    double* pf = (double*)malloc(sizeof(double) * (size_t)m * nmig);
+    double* pF = (double*)malloc(sizeof(double) * (size_t)m * nmig);
+    double* pC = (double*)malloc(sizeof(double) * (size_t)m * nmig);
+    int posted = 0;
     int32_t* best = (int32_t*)malloc(sizeof(int32_t) * (size_t)nmig);
     int32_t* worst = (int32_t*)malloc(sizeof(int32_t) * (size_t)nmig);
     for (int k = 0; k < m; ++k) {
@@ -134,19 +151,36 @@ int64_t or_run_islands(int m, int interval, int nmig, int np, int d, double F, d
                     }
                 }
             }
-            /* ... then island (k + 1) % m takes island k's in place of its worst */
-            for (int k = 0; k < m; ++k) {
+            /* ... then island (k + 1) % m takes island k's in place of its
+               worst: this point's migrants (synchronous), or those posted at
+               the previous point (asynchronous; none at the first point) */
+            const double *ux = mx, *uf = mf, *uF = mF, *uC = mC;
+            if (async_mig) {
+                ux = px;
+                uf = pf;
+                uF = pF;
+                uC = pC;
+            }
+            for (int k = 0; k < m && (!async_mig || posted); ++k) {
                 int dst = (k + 1) % m;
                 or_island_ranked(np, fX + (size_t)dst * np, nmig, 1, worst);
                 for (int q = 0; q < nmig; ++q) {
                     size_t s = (size_t)k * nmig + q;
-                    memcpy(X + dst * P + (size_t)worst[q] * d, mx + s * d, sizeof(double) * (size_t)d);
-                    fX[(size_t)dst * np + worst[q]] = mf[s];
+                    memcpy(X + dst * P + (size_t)worst[q] * d, ux + s * d, sizeof(double) * (size_t)d);
+                    fX[(size_t)dst * np + worst[q]] = uf[s];
                     if (jde) {
-                        jF[(size_t)dst * np + worst[q]] = mF[s];
-                        jCR[(size_t)dst * np + worst[q]] = mC[s];
+                        jF[(size_t)dst * np + worst[q]] = uF[s];
+                        jCR[(size_t)dst * np + worst[q]] = uC[s];
                     }
                 }
+            }
+            if (async_mig) {
+                /* this point's migrants become the posted ones */
+                memcpy(px, mx, sizeof(double) * (size_t)m * nmig * d);
+                memcpy(pf, mf, sizeof(double) * (size_t)m * nmig);
+                memcpy(pF, mF, sizeof(double) * (size_t)m * nmig);
+                memcpy(pC, mC, sizeof(double) * (size_t)m * nmig);
+                posted = 1;
             }
         }
     }
@@ -158,6 +192,10 @@ int64_t or_run_islands(int m, int interval, int nmig, int np, int d, double F, d
     free(mf);
     free(mF);
     free(mC);
+    free(px);
+    free(pf);
+    free(pF);
+    free(pC);
     free(best);
     free(worst);
     if (evals_out) *evals_out = evals;
