@@ -603,8 +603,8 @@ def run_workload(args, capi, torch, rank, world):
         obj = problems.SUITE[3]
         data = problems.suite(obj, d, seed=1)
         forms = {}
-        for name, kind in (("islands_ring_k20_m2", "ring"), ("islands_no_migration", "none"),
-                           ("one_population_np1024", "single")):
+        for name, kind in (("islands_ring_k20_m2", "ring"), ("islands_async_ring_k20_m2", "async"),
+                           ("islands_no_migration", "none"), ("one_population_np1024", "single")):
             bests, secs = [], []
             for seed in (1, 2, 3):
                 c = capi.make_config(npi if kind != "single" else m * npi, d, objective=obj, shift=data["shift"],
@@ -614,7 +614,9 @@ def run_workload(args, capi, torch, rank, world):
                     h = capi.de_init(c, stream=stream.cuda_stream)
                     nr = 1
                 else:
-                    h = capi.de_init_islands(c, m, 20 if kind == "ring" else 1 << 30, 2, stream=stream.cuda_stream)
+                    h = capi.de_init_islands_ex(c, m, 1 << 30 if kind == "none" else 20, 2,
+                                                capi.DE_MIGRATE_ASYNC if kind == "async" else capi.DE_MIGRATE_SYNC,
+                                                stream=stream.cuda_stream)
                     nr = m
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -632,8 +634,9 @@ def run_workload(args, capi, torch, rank, world):
                            f"2 migrants) on the 30-D rotated Rastrigin function F03, FP64",
                     value=forms["islands_ring_k20_m2"]["trial_evals_per_s"],
                     ms_per_step=1e3 * forms["islands_ring_k20_m2"]["seconds_per_run"], dtype="f64",
-                    config={"workload": f"F03 D=30, {G} generations, 3 seeds; islands vs no migration vs one "
-                                        "population of 1024", "l2": "working set in L2"},
+                    config={"workload": f"F03 D=30, {G} generations, 3 seeds; islands (synchronous and "
+                                        "asynchronous migration) vs no migration vs one population of 1024",
+                            "l2": "working set in L2"},
                     forms=forms, gpu_launches=None)
     elif args.workload == "accuracy":
         line.update(accuracy_workload(capi, torch, stream, problems))

@@ -314,6 +314,28 @@ DE_API de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_
 DE_API de_status de_init_islands(const de_config* cfg, int32_t nislands, int32_t interval, int32_t migrants,
                                  void* cuda_stream, de_handle** out);
 
+/* Migration strategies of the island model (Sec. 3.2 names synchronous and
+ * asynchronous migration). */
+typedef enum {
+  DE_MIGRATE_SYNC = 0,  /* as de_init_islands */
+  DE_MIGRATE_ASYNC = 1  /* one interval late, through a mailbox (below) */
+} de_migration;
+
+/* de_init_islands with a migration strategy.  DE_MIGRATE_ASYNC: in the GPU
+ * form of Sec. 5.4 asynchronous migration happens inside the generation
+ * kernel, so an island may receive migrants of an island that is ahead of it
+ * or behind it and runs cannot be repeated; here the staleness is fixed to one
+ * interval.  At every migration point (generation g, g % interval == 0) island
+ * k posts its `migrants` best (the order above) to a device mailbox and takes,
+ * into its `migrants` worst, the migrants island k - 1 posted at the previous
+ * migration point (none at the first point after de_init, de_reset,
+ * de_set_population or de_load, which empty the mailbox).  One kernel per
+ * migration, no ordering among the islands, reproducible results.  Same
+ * errors as de_init_islands, plus DE_ERR_INVALID_ARG for another `migration`
+ * value. */
+DE_API de_status de_init_islands_ex(const de_config* cfg, int32_t nislands, int32_t interval, int32_t migrants,
+                                    int32_t migration, void* cuda_stream, de_handle** out);
+
 /* Re-initialise run `run` (or every run when run == -1) as de_init did
  * (Sec. 2, initialisation): population from the INIT stream, evaluation,
  * counters and best record reset.  Enqueued on the handle's stream;

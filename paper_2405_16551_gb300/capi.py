@@ -27,6 +27,7 @@ DE_PREC_FP64, DE_PREC_BF16X3, DE_PREC_TF32X3 = 0, 1, 2
 DE_STOP_NONE, DE_STOP_TARGET, DE_STOP_EVALS, DE_STOP_GENERATIONS = 0, 1, 2, 3
 DE_BAND_NEAR, DE_BAND_ALL = 0, 1
 DE_RAND1BIN, DE_BEST1BIN, DE_RAND1EXP = 0, 1, 2
+DE_MIGRATE_SYNC, DE_MIGRATE_ASYNC = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -118,6 +119,8 @@ def load(build_if_missing: bool = True):
             "de_selftest_fp64_rate": ([], ctypes.c_double),
             "de_init_islands": ([ctypes.POINTER(de_config), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                  ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
+            "de_init_islands_ex": ([ctypes.POINTER(de_config), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
             "de_set_adaptive": ([H, ctypes.c_int32, _dp, _dp], ctypes.c_int),
             "de_mlp_create": ([ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
             "de_mlp_destroy": ([H], ctypes.c_int),
@@ -145,7 +148,8 @@ def exported_symbols():
             "de_get_debug", "de_get_shape", "de_get_stats", "de_get_plan", "de_save", "de_load", "de_destroy",
             "de_eval_noalloc", "de_mlp_create", "de_mlp_destroy", "de_mlp_set_params", "de_mlp_get_params",
             "de_mlp_forward", "de_mlp_grad", "de_mlp_train", "de_get_surrogate_stats", "de_get_adaptive",
-            "de_set_adaptive", "de_init_islands", "de_selftest_f32_rounding", "de_selftest_fp64_rate"]
+            "de_set_adaptive", "de_init_islands", "de_init_islands_ex", "de_selftest_f32_rounding",
+            "de_selftest_fp64_rate"]
 
 
 def _status_name(s):
@@ -333,6 +337,15 @@ def de_init_islands(cfg, nislands: int, interval: int, migrants: int, stream=Non
     h = ctypes.c_void_p()
     _check(load().de_init_islands(ctypes.byref(cfg), nislands, interval, migrants, ctypes.c_void_p(stream or 0),
                                   ctypes.byref(h)), None)
+    return h.value
+
+
+def de_init_islands_ex(cfg, nislands: int, interval: int, migrants: int, migration: int, stream=None):
+    """de_init_islands with a migration strategy (DE_MIGRATE_SYNC or
+    DE_MIGRATE_ASYNC: migrants one interval late, through a mailbox)."""
+    h = ctypes.c_void_p()
+    _check(load().de_init_islands_ex(ctypes.byref(cfg), nislands, interval, migrants, migration,
+                                     ctypes.c_void_p(stream or 0), ctypes.byref(h)), None)
     return h.value
 
 

@@ -278,13 +278,15 @@ static void drop_graph(de_handle* h) {
   h->graph_gens = 0;
 }
 
-// Island model: forget the last migration and apply the model's group stop
-// to the current state (after (re)initialisation or a population change).
+// Island model: forget the last migration (and the mailbox of asynchronous
+// migration) and apply the model's group stop to the current state (after
+// (re)initialisation, a population change or a restore).
 static de_status islands_resync(de_handle* h) {
   if (!h->islands) return DE_OK;
   h->isl.mig_gen = -1;
+  h->isl.post_gen = -1;
   DE_CUDA(h, cudaMemcpyAsync(h->d_isl, &h->isl, sizeof(IslandCtl), cudaMemcpyHostToDevice, h->stream));
-  k_island_launch(h->d_run, h->d_isl, h->stage, h->nruns, false, h->stream);
+  k_island_launch(h->d_run, h->d_isl, h->stage, h->nruns, false, false, h->stream);
   DE_CUDA(h, cudaGetLastError());
   return DE_OK;
 }
@@ -293,7 +295,7 @@ static de_status islands_resync(de_handle* h) {
 static de_status launch_generation(de_handle* h, cudaStream_t s) {
   if (h->prec == DE_PREC_FP64) {
     k_gen_fp64_launch(h->d_run, h->d_items, h->nitems, h->threads, h->smem_gen, h->variants, h->suite, s);
-    if (h->islands) k_island_launch(h->d_run, h->d_isl, h->stage, h->nruns, true, s);
+    if (h->islands) k_island_launch(h->d_run, h->d_isl, h->stage, h->nruns, true, h->isl.async != 0, s);
   } else {
     tc_generation_launch(h->tc, h->d_run, s);
   }
@@ -1241,8 +1243,15 @@ de_status de_reset(de_handle* h, int32_t run) {
 
 de_status de_init_islands(const de_config* cfg, int32_t nislands, int32_t interval, int32_t migrants,
                           void* cuda_stream, de_handle** out) {
+  return de_init_islands_ex(cfg, nislands, interval, migrants, DE_MIGRATE_SYNC, cuda_stream, out);
+}
+
+de_status de_init_islands_ex(const de_config* cfg, int32_t nislands, int32_t interval, int32_t migrants,
+                             int32_t migration, void* cuda_stream, de_handle** out) {
   g_err.clear();
   if (!cfg || !out) return fail(nullptr, DE_ERR_INVALID_ARG, "cfg or out is NULL");
+  if (migration != DE_MIGRATE_SYNC && migration != DE_MIGRATE_ASYNC)
+    return fail(nullptr, DE_ERR_INVALID_ARG, "migration must be DE_MIGRATE_SYNC or DE_MIGRATE_ASYNC");
   if (nislands < 2 || nislands > 4096) return fail(nullptr, DE_ERR_INVALID_ARG, "nislands must be in [2, 4096]");
   if (interval < 1) return fail(nullptr, DE_ERR_INVALID_ARG, "interval must be >= 1");
   if (migrants < 1 || migrants > kIslandMaxMigrants || 2 * migrants > cfg->np)
@@ -1257,7 +1266,8 @@ de_status de_init_islands(const de_config* cfg, int32_t nislands, int32_t interv
   de_status st = de_init_batch(cfgs.data(), nislands, cuda_stream, &h);
   if (st != DE_OK) return st;
   const int dp = h->run[0].dp;
-  const size_t n = (size_t)nislands * migrants;
+  // two mailbox slots of nislands x migrants (synchronous migration uses the first)
+  const size_t n = 2 * (size_t)nislands * migrants;
   const size_t bytes = n * (dp * sizeof(double) + 3 * sizeof(double) + sizeof(int32_t) + 1) + 1024;
   cudaError_t e = cudaMalloc(&h->isl_mem, bytes + sizeof(IslandCtl));
   if (e != cudaSuccess) {
@@ -1279,7 +1289,8 @@ de_status de_init_islands(const de_config* cfg, int32_t nislands, int32_t interv
   p += n * sizeof(int32_t);
   h->stage.fx = (uint8_t*)p;
   h->stage.dp = dp;
-  h->isl = IslandCtl{nislands, interval, migrants, 0, -1};
+  h->stage.slot = nislands * migrants;
+  h->isl = IslandCtl{nislands, interval, migrants, migration == DE_MIGRATE_ASYNC ? 1 : 0, -1, -1};
   h->islands = true;
   h->fp64_persist = h->fp64_cluster = false;  // migration runs between generations
   drop_graph(h);

@@ -19,6 +19,21 @@
 // which CTAs run: every migrant is read before any island is written.  The
 // three kernels run after every generation and return at once when no
 // migration is due, so a CUDA graph of generations can hold them.
+//
+// Asynchronous migration (Sec. 3.2 names both strategies; in the GPU form of
+// Sec. 5.4 the asynchronous one migrates inside the generation kernel, so an
+// island may receive migrants of an island that is ahead of it or behind it,
+// and runs cannot be repeated).  Here the staleness is fixed to one migration
+// interval, through a mailbox of two slots:
+//   k_island_async   one CTA per island, one kernel: at migration point g the
+//                    island posts its nmig best to slot (g / interval) & 1 and
+//                    takes, into its nmig worst, the migrants its ring
+//                    predecessor posted at the previous migration point (from
+//                    the other slot; none at the first point).  No CTA reads a
+//                    slot that a CTA of the same launch writes, so the islands
+//                    need no ordering among themselves and the results do not
+//                    depend on it;
+//   k_island_group   as above, and it records the post.
 #include <cuda_runtime.h>
 
 #include "de_common.cuh"
@@ -85,6 +100,32 @@ __device__ int island_pick(const double* __restrict__ f, int np, const int* take
   return r;
 }
 
+// the island's best record after an exchange (the whole CTA)
+__device__ void island_best_record(const RunDesc& R, int cur) {
+  __shared__ double sf[32];
+  __shared__ long long sk[32];
+  __shared__ int si[32];
+  Best b;
+  b.init();
+  for (int i = threadIdx.x; i < R.np; i += blockDim.x) b.offer(R.f[cur][i], i);
+  b.warp_reduce();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sf[warp] = b.f;
+    sk[warp] = b.k;
+    si[warp] = b.i;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    b.init();
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b.take(sf[w], sk[w], si[w]);
+    if (b.i >= 0) {
+      R.st->best_f = b.f;
+      R.st->best_idx = b.i;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_island_select(const RunDesc* __restrict__ runs, const IslandCtl* ctl,
                                                        IslandStage stage) {
   const int k = blockIdx.x;
@@ -143,32 +184,70 @@ __global__ void __launch_bounds__(256) k_island_apply(const RunDesc* __restrict_
     }
   }
   __syncthreads();
-  // the island's best record after the exchange
-  __shared__ double sf[32];
-  __shared__ long long sk[32];
-  __shared__ int si[32];
-  Best b;
-  b.init();
-  for (int i = threadIdx.x; i < R.np; i += blockDim.x) b.offer(R.f[cur][i], i);
-  b.warp_reduce();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    sf[warp] = b.f;
-    sk[warp] = b.k;
-    si[warp] = b.i;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    b.init();
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b.take(sf[w], sk[w], si[w]);
-    if (b.i >= 0) {
-      R.st->best_f = b.f;
-      R.st->best_idx = b.i;
-    }
-  }
+  island_best_record(R, cur);
 }
 
-__global__ void __launch_bounds__(256) k_island_group(const RunDesc* __restrict__ runs, IslandCtl* ctl) {
+__global__ void __launch_bounds__(256) k_island_async(const RunDesc* __restrict__ runs, const IslandCtl* ctl,
+                                                      IslandStage stage) {
+  const int k = blockIdx.x, m = ctl->m;
+  const RunDesc& R = runs[k];
+  const int64_t gen = *(volatile int64_t*)&R.st->gen;
+  if (!island_due(ctl, gen)) return;
+  const int cur = (int)(gen & 1), nmig = ctl->nmig;
+  const int64_t ep = gen / ctl->interval;
+  const size_t wslot = (size_t)(ep & 1) * stage.slot, rslot = (size_t)((ep & 1) ^ 1) * stage.slot;
+  // the previous migration point posted (not so after a reset or a population change)
+  const bool take = ctl->post_gen >= 0 && ctl->post_gen == gen - ctl->interval;
+  const double* f = R.f[cur];
+  __shared__ int best[kIslandMaxMigrants], worst[kIslandMaxMigrants];
+  for (int q = 0; q < nmig; ++q) {
+    const int b = island_pick(f, R.np, best, q, false);
+    if (threadIdx.x == 0) best[q] = b;
+    __syncthreads();
+  }
+  for (int q = 0; q < nmig && take; ++q) {
+    const int w = island_pick(f, R.np, worst, q, true);
+    if (threadIdx.x == 0) worst[q] = w;
+    __syncthreads();
+  }
+  // post this island's best (rows disjoint from its worst: nmig <= np / 2 and
+  // both orders are total)
+  for (int q = 0; q < nmig; ++q) {
+    const size_t s = wslot + (size_t)k * nmig + q;
+    const double* src = R.X[cur] + (size_t)best[q] * R.dp;
+    for (int j = threadIdx.x; j < R.dp; j += blockDim.x) stage.x[s * stage.dp + j] = src[j];
+    if (threadIdx.x == 0) {
+      stage.f[s] = f[best[q]];
+      stage.fx[s] = R.fx[cur][best[q]];
+      if (R.jde) {
+        stage.F[s] = R.jF[cur][best[q]];
+        stage.CR[s] = R.jCR[cur][best[q]];
+      }
+    }
+  }
+  if (!take) return;
+  // take the predecessor's posts of the previous migration point
+  const int from = (k + m - 1) % m;
+  for (int q = 0; q < nmig; ++q) {
+    const size_t s = rslot + (size_t)from * nmig + q;
+    const int w = worst[q];
+    double* dst = R.X[cur] + (size_t)w * R.dp;
+    for (int j = threadIdx.x; j < R.dp; j += blockDim.x) dst[j] = stage.x[s * stage.dp + j];
+    if (threadIdx.x == 0) {
+      R.f[cur][w] = stage.f[s];
+      R.fx[cur][w] = stage.fx[s];
+      if (R.jde) {
+        R.jF[cur][w] = stage.F[s];
+        R.jCR[cur][w] = stage.CR[s];
+      }
+    }
+  }
+  __syncthreads();
+  island_best_record(R, cur);
+}
+
+// posted: this launch follows k_island_async (a due migration posted)
+__global__ void __launch_bounds__(256) k_island_group(const RunDesc* __restrict__ runs, IslandCtl* ctl, int posted) {
   const int m = ctl->m;
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
@@ -183,17 +262,22 @@ __global__ void __launch_bounds__(256) k_island_group(const RunDesc* __restrict_
     for (int k = threadIdx.x; k < m; k += blockDim.x) runs[k].st->stop = 1;
   if (threadIdx.x == 0) {
     const int64_t gen = runs[0].st->gen;
-    if (island_due(ctl, gen)) ctl->mig_gen = gen;
+    if (island_due(ctl, gen)) {
+      ctl->mig_gen = gen;
+      if (posted) ctl->post_gen = gen;
+    }
   }
 }
 
 void k_island_launch(const RunDesc* runs, IslandCtl* ctl, const IslandStage& stage, int m, bool migrate,
-                     cudaStream_t s) {
-  if (migrate) {
+                     bool async, cudaStream_t s) {
+  if (migrate && async) {
+    k_island_async<<<m, 256, 0, s>>>(runs, ctl, stage);
+  } else if (migrate) {
     k_island_select<<<m, 256, 0, s>>>(runs, ctl, stage);
     k_island_apply<<<m, 256, 0, s>>>(runs, ctl, stage);
   }
-  k_island_group<<<1, 256, 0, s>>>(runs, ctl);
+  k_island_group<<<1, 256, 0, s>>>(runs, ctl, migrate && async ? 1 : 0);
 }
 
 }  // namespace de

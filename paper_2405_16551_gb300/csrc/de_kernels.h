@@ -60,21 +60,27 @@ struct IslandCtl {
   int32_t m;         // islands (the runs of the handle)
   int32_t interval;  // generations between migrations
   int32_t nmig;      // migrants per island and migration
-  int32_t pad;
+  int32_t async;     // 1: asynchronous migration through the mailbox
   int64_t mig_gen;   // generation of the last migration (-1: none)
+  int64_t post_gen;  // asynchronous: generation of the mailbox's last post (-1: none)
 };
-struct IslandStage {  // m x nmig migrants between the select and apply kernels
+// Two slots of m x nmig migrants: synchronous migration stages through slot 0
+// between its select and apply kernels; asynchronous migration posts to slot
+// (g / interval) & 1 at migration point g and reads the other one.
+struct IslandStage {
   double* x;          // rows of dp doubles
   double* f;
   uint8_t* fx;
   double* F;          // jDE parameters
   double* CR;
-  int32_t* widx;      // the receiving island's worst slots
+  int32_t* widx;      // the receiving island's worst slots (synchronous)
   int32_t dp;
+  int32_t slot;       // migrants per slot (m x nmig)
 };
-// migrate: also run the exchange kernels (else only the group stop test)
+// migrate: also run the exchange kernels (else only the group stop test);
+// async: the asynchronous exchange kernel instead of the synchronous pair
 void k_island_launch(const RunDesc* runs, IslandCtl* ctl, const IslandStage& stage, int m, bool migrate,
-                     cudaStream_t s);
+                     bool async, cudaStream_t s);
 
 // persistent cluster path (de_persist.cu)
 struct PersistPlan {

@@ -157,3 +157,19 @@ def test_islands_outside_the_fp64_path_are_unsupported_on_host():
     with pytest.raises(capi.DEError) as ei:
         capi.de_init_islands(cfg, 4, 5, 1)
     assert ei.value.status == capi.DE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("migration", [-1, 2, 7])
+def test_unknown_migration_strategy_rejected_on_host(migration):
+    cfg = capi.make_config(64, 10)
+    with pytest.raises(capi.DEError) as ei:
+        capi.de_init_islands_ex(cfg, 4, 5, 1, migration)
+    assert ei.value.status == capi.DE_ERR_INVALID_ARG and "migration" in str(ei.value)
+
+
+def test_async_island_arguments_checked_like_sync_on_host():
+    cfg = capi.make_config(64, 10)
+    for args in ((1, 5, 1), (4, 0, 1), (4, 5, 33)):
+        with pytest.raises(capi.DEError) as ei:
+            capi.de_init_islands_ex(cfg, *args, capi.DE_MIGRATE_ASYNC)
+        assert ei.value.status == capi.DE_ERR_INVALID_ARG

@@ -1,6 +1,7 @@
 """GPU parity of the island model (Sec. 3.2, Sec. 5.4) against the CPU
 oracle, through the C ABI: island populations after ring migrations, jDE
-parameters carried by migrants, and the model's common stop."""
+parameters carried by migrants, and the model's common stop; the same for
+asynchronous migration (migrants one interval late, through a mailbox)."""
 import numpy as np
 import pytest
 
@@ -17,12 +18,13 @@ def _need_gpu():
     return torch
 
 
-def _run(m, interval, nmig, np_, d, obj, G, target=0.0, rotate=True, seed=3, **kw):
+def _run(m, interval, nmig, np_, d, obj, G, target=0.0, rotate=True, seed=3, asynchronous=False, **kw):
     o = problems.shift(d, seed=seed)
     M = problems.rotation(d, seed=seed) if rotate else None
     cfg = capi.make_config(np_, d, objective=obj, shift=o, rot=M, seed=seed, run_id=5, max_generations=G,
                            target_error=target, **kw)
-    h = capi.de_init_islands(cfg, m, interval, nmig)
+    h = capi.de_init_islands_ex(cfg, m, interval, nmig,
+                                capi.DE_MIGRATE_ASYNC if asynchronous else capi.DE_MIGRATE_SYNC)
     try:
         res = capi.de_run(h, m)
         pops = [capi.de_get_population(h, k) for k in range(m)]
@@ -31,7 +33,8 @@ def _run(m, interval, nmig, np_, d, obj, G, target=0.0, rotate=True, seed=3, **k
         capi.de_destroy(h)
     Xo, fo, go, evo, Fo, Co = oracle.run_islands(m, interval, nmig, np_, d, 0.5, 0.9, -100, 100, obj, o, M,
                                                  seed=seed, max_generations=G, target_error=target, run_id=5,
-                                                 strategy=kw.get("strategy", 0), jde=kw.get("jde", False))
+                                                 strategy=kw.get("strategy", 0), jde=kw.get("jde", False),
+                                                 asynchronous=asynchronous)
     return res, pops, ad, (Xo, fo, go, evo, Fo, Co), (o, M)
 
 
@@ -83,3 +86,70 @@ def test_reset_replays_the_same_island_run():
         capi.de_destroy(h)
     for k in range(3):
         assert np.array_equal(a[k][0], b[k][0]) and np.array_equal(a[k][1], b[k][1])
+
+
+# ----------------------------------------------------------------- asynchronous
+@pytest.mark.parametrize("m,interval,nmig,np_,d,obj", [(4, 5, 2, 32, 10, 1), (3, 1, 1, 20, 7, 3), (8, 7, 3, 50, 30, 2),
+                                                       (2, 3, 4, 16, 5, 0)])
+def test_async_island_populations_match_oracle(m, interval, nmig, np_, d, obj):
+    _need_gpu()
+    G = 40
+    res, pops, _, (Xo, fo, go, evo, _, _), (o, M) = _run(m, interval, nmig, np_, d, obj, G, asynchronous=True)
+    assert all(r["generations"] == G for r in res)
+    for k in range(m):
+        x, f = pops[k]
+        assert np.array_equal(x, Xo[k])
+        _, sabs = oracle.evaluate(obj, x, o, M)
+        assert np.all(np.abs(f - fo[k]) <= 1e-12 * (np.abs(fo[k]) + sabs))
+
+
+def test_async_differs_from_sync_on_the_gpu_as_in_the_oracle():
+    _need_gpu()
+    a = _run(4, 4, 2, 24, 8, 1, 20, asynchronous=True)
+    b = _run(4, 4, 2, 24, 8, 1, 20)
+    assert any(not np.array_equal(a[1][k][0], b[1][k][0]) for k in range(4))
+    for k in range(4):
+        assert np.array_equal(a[1][k][0], a[3][0][k]) and np.array_equal(b[1][k][0], b[3][0][k])
+
+
+def test_async_jde_islands_carry_parameters_like_the_oracle():
+    _need_gpu()
+    m, G = 4, 30
+    res, pops, ad, (Xo, fo, go, evo, Fo, Co), _ = _run(m, 3, 2, 24, 12, 1, G, jde=True, strategy=capi.DE_RAND1EXP,
+                                                      asynchronous=True)
+    for k in range(m):
+        assert np.array_equal(pops[k][0], Xo[k])
+        assert np.array_equal(ad[k][0], Fo[k]) and np.array_equal(ad[k][1], Co[k])
+
+
+def test_async_model_stops_together_at_the_oracles_generation():
+    _need_gpu()
+    m = 4
+    res, pops, _, (Xo, fo, go, evo, _, _), _ = _run(m, 10, 1, 32, 5, 0, 3000, target=1e-8, rotate=False,
+                                                   asynchronous=True)
+    assert all(r["generations"] == go for r in res)
+    assert all(r["stop_reason"] == capi.DE_STOP_TARGET for r in res)
+    for k in range(m):
+        assert np.array_equal(pops[k][0], Xo[k])
+
+
+def test_async_reset_empties_the_mailbox_and_replays_the_run():
+    """de_reset forgets the posts: the replay takes no migrants at the first
+    migration point after it, exactly as the first run did."""
+    _need_gpu()
+    o = problems.shift(10, seed=1)
+    cfg = capi.make_config(24, 10, objective=1, shift=o, seed=2, max_generations=25, target_error=0.0)
+    h = capi.de_init_islands_ex(cfg, 3, 4, 2, capi.DE_MIGRATE_ASYNC)
+    try:
+        capi.de_run(h, 3)
+        a = [capi.de_get_population(h, k) for k in range(3)]
+        capi.de_reset(h)
+        capi.de_run(h, 3)
+        b = [capi.de_get_population(h, k) for k in range(3)]
+    finally:
+        capi.de_destroy(h)
+    Xo = oracle.run_islands(3, 4, 2, 24, 10, 0.5, 0.9, -100, 100, 1, o, None, seed=2, max_generations=25,
+                            target_error=0.0, asynchronous=True)[0]
+    for k in range(3):
+        assert np.array_equal(a[k][0], b[k][0]) and np.array_equal(a[k][1], b[k][1])
+        assert np.array_equal(a[k][0], Xo[k])
