@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     p.add_argument("--workload", default="rastrigin",
                    choices=["rastrigin", "sphere_small", "batch512", "ode_surrogate", "stress", "stress_batch",
-                            "variants", "suite", "islands", "accuracy"],
+                            "variants", "suite", "islands", "accuracy", "split_error"],
                    help="rastrigin: the headline configuration (default); the others measure the batched, "
                         "surrogate and large-dimension configurations with the same harness")
     return p.parse_args()
@@ -640,6 +640,8 @@ def run_workload(args, capi, torch, rank, world):
                     forms=forms, gpu_launches=None)
     elif args.workload == "accuracy":
         line.update(accuracy_workload(capi, torch, stream, problems))
+    elif args.workload == "split_error":
+        line.update(split_error_workload(capi, torch, problems))
     elif args.workload == "stress_batch":
         # 64 runs of the large-dimension shape in one handle (working set far above L2)
         G = min(args.generations, 10)
@@ -687,6 +689,71 @@ def run_workload(args, capi, torch, rank, world):
                     tensor_tflops=flops / (ms / 1e3) / 1e12, gpu_launches=steps * (3 + 3 * G))
     line["clocks"] = clocks.stop()
     return line
+
+
+def split_error_workload(capi, torch, problems):
+    """Fitness error of each precision form against the FP64 oracle, per
+    objective (Sec. 7.3.1: sphere, Rastrigin, Rosenbrock, Ackley) x D in
+    {10, 100, 1000} x {64 random points in [-100, 100]^D, 64 points where the
+    oracle's f is 1e-8 (x = o + delta v, v a random unit vector, delta by
+    bisection on the oracle)}, all rotated and shifted, evaluated through
+    de_eval.  Reported per cell: the largest and median |f_gpu - f| / (|f| + S)
+    (the parity tolerance's scale) and the largest plain |f_gpu - f| / |f|.
+    Split precision takes Rosenbrock up to D = 256 only."""
+    import oracle
+
+    oracle.build()
+    n = 64
+    names = {0: "sphere", 1: "rastrigin", 2: "rosenbrock", 3: "ackley"}
+    forms = {"fp64": {}, "bf16x3": {}, "tf32x3": {}}
+    for obj in range(4):
+        for d in (10, 100, 1000):
+            o, M = problems.shift(d, seed=5), problems.rotation(d, seed=5)
+            rng = np.random.default_rng(1000 * obj + d)
+            V = rng.normal(size=(n, d))
+            V /= np.linalg.norm(V, axis=1, keepdims=True)
+            lo_d, hi_d = np.zeros(n), np.ones(n)  # f(o + v) > 1e-8 for every objective here
+            for _ in range(45):
+                mid = 0.5 * (lo_d + hi_d)
+                fm, _ = oracle.evaluate(obj, o + mid[:, None] * V, o, M)
+                above = fm > 1e-8
+                hi_d = np.where(above, mid, hi_d)
+                lo_d = np.where(above, lo_d, mid)
+            sets = {"random": problems.population(n, d, seed=11), "f_1e-8": o + hi_d[:, None] * V}
+            ref = {k: oracle.evaluate(obj, X, o, M) for k, X in sets.items()}
+            for form, prec in (("fp64", capi.DE_PREC_FP64), ("bf16x3", capi.DE_PREC_BF16X3),
+                               ("tf32x3", capi.DE_PREC_TF32X3)):
+                cell = forms[form].setdefault(names[obj], {})
+                if prec != capi.DE_PREC_FP64 and obj == 2 and d > 256:
+                    cell[str(d)] = "unsupported (split Rosenbrock up to D = 256)"
+                    continue
+                h = capi.de_init(capi.make_config(n, d, objective=obj, shift=o, rot=M, precision=prec,
+                                                  max_generations=1))
+                res = {}
+                try:
+                    for k, X in sets.items():
+                        xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+                        fd = torch.zeros(n, dtype=torch.float64, device="cuda")
+                        capi.de_eval(h, 0, xd.data_ptr(), d, n, fd.data_ptr())
+                        torch.cuda.synchronize()
+                        f = fd.cpu().numpy()
+                        fo, sabs = ref[k]
+                        e_tol = np.abs(f - fo) / (np.abs(fo) + sabs)
+                        e_rel = np.abs(f - fo) / np.abs(fo)
+                        res[k] = {"max_err_tol_scale": float(e_tol.max()), "median_err_tol_scale": float(np.median(e_tol)),
+                                  "max_err_plain_relative": float(e_rel.max()), "f_median": float(np.median(fo))}
+                finally:
+                    capi.de_destroy(h)
+                cell[str(d)] = res
+    worst = {form: max(v["max_err_tol_scale"] for ob in forms[form].values() for c in ob.values()
+                       if isinstance(c, dict) for v in c.values()) for form in forms}
+    return dict(metric="largest fitness error of the split precisions against the FP64 oracle, |f_s - f| / (|f| + S), "
+                       "objectives 0-3 x D 10/100/1000 x {random points, f = 1e-8 above the optimum}",
+                value=worst["bf16x3"], unit="relative error", higher_is_better=False, ms_per_step=None,
+                dtype="bf16x3 / tf32x3 products, f32 accumulate (fp64 for reference)",
+                config={"workload": "64 random points and 64 points with f = 1e-8 per objective and D, "
+                                    "rotated and shifted, through de_eval"},
+                forms=forms, worst_err_tol_scale=worst, gpu_launches=None)
 
 
 def accuracy_workload(capi, torch, stream, problems):
