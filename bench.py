@@ -503,26 +503,61 @@ def run_workload(args, capi, torch, rank, world):
                     gpu_launches=steps * (3 * 512 + (1 if forms["bf16x3"]["kernel_path"] == KERNEL_PATH_NAMES[5]
                                                      else 3 * G)))
     elif args.workload == "ode_surrogate":
-        # time and true evaluations to reach f < 1e-8, plain DE vs 8 screened candidates
+        # wall time and true evaluations to reach f < 1e-8: plain DE (k = 1)
+        # against 8 screened candidates (25 Adam steps per retraining, the
+        # default, and 100), 5 seeds each; then the objective cost at which
+        # the surrogate would break even
+        seeds = (1, 2, 3, 4, 5)
         res = {}
-        for k in (0, 8):
+        for name, k, steps_tr in (("plain_k1", 0, 0), ("surrogate_k8", 8, 0), ("surrogate_k8_steps100", 8, 100)):
             runs = []
-            for seed in (1, 2, 3):
+            for seed in seeds:
                 c = capi.make_config(256, 20, objective=4, shift=problems.ode_hidden(seed), seed=seed,
-                                     max_evals=200000, max_generations=10**6, target_error=1e-8, surrogate_k=k)
+                                     max_evals=200000, max_generations=10**6, target_error=1e-8, surrogate_k=k,
+                                     surrogate_steps=steps_tr)
                 h = capi.de_init(c, stream=stream.cuda_stream)
                 t0 = time.perf_counter()
                 r = capi.de_run(h)[0]
                 runs.append({"seconds": time.perf_counter() - t0, "true_evals": r["evals"],
                              "generations": r["generations"], "best_f": r["best_f"], "stop": r["stop_reason"]})
                 capi.de_destroy(h)
-            res["plain" if k == 0 else "surrogate_k8"] = runs
-        ev = sum(r["true_evals"] for r in res["plain"])
-        tm = sum(r["seconds"] for r in res["plain"])
+            res[name] = {"runs": runs, "mean_seconds": float(np.mean([r["seconds"] for r in runs])),
+                         "mean_true_evals": float(np.mean([r["true_evals"] for r in runs])),
+                         "mean_generations": float(np.mean([r["generations"] for r in runs]))}
+        # the objective's own time per generation: NP = 256 rows through de_eval
+        c = capi.make_config(256, 20, objective=4, shift=problems.ode_hidden(1), seed=1, max_generations=1)
+        h = capi.de_init(c, stream=stream.cuda_stream)
+        xd = torch.from_numpy(problems.population(256, 20, seed=2)).cuda()
+        fd = torch.zeros(256, dtype=torch.float64, device="cuda")
+        capi.de_eval(h, 0, xd.data_ptr(), 20, 256, fd.data_ptr())
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            capi.de_eval(h, 0, xd.data_ptr(), 20, 256, fd.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_obj = e0.elapsed_time(e1) / 10 / 1e3
+        capi.de_destroy(h)
+        gp, wp = res["plain_k1"]["mean_generations"], res["plain_k1"]["mean_seconds"]
+        for name in ("surrogate_k8", "surrogate_k8_steps100"):
+            gs, ws = res[name]["mean_generations"], res[name]["mean_seconds"]
+            cp, cs = wp / gp - t_obj, ws / gs - t_obj  # per-generation cost besides the objective
+            res[name]["overhead_per_generation_s"] = cs - cp
+            if gs < gp:
+                tb = (gs * cs - gp * cp) / (gp - gs)
+                res[name]["break_even_objective_s_per_generation"] = tb
+                res[name]["break_even_objective_s_per_evaluation"] = tb / 256
+                res[name]["break_even_vs_this_objective"] = tb / t_obj
+            else:
+                res[name]["break_even_objective_s_per_generation"] = None  # saves no generations
+        ev = sum(r["true_evals"] for r in res["plain_k1"]["runs"])
+        tm = sum(r["seconds"] for r in res["plain_k1"]["runs"])
         line.update(metric="true evaluations/sec to f < 1e-8, ODE fit (D=20, NP=256, RK4 2000 steps FP64)",
-                    value=ev / tm, ms_per_step=1e3 * tm / 3, dtype="f64 objective, bf16 surrogate",
-                    config={"workload": "ODE fit, 3 seeds, plain DE and surrogate k = 8, budget 2e5 true evaluations"},
-                    runs=res, gpu_launches=None)
+                    value=ev / tm, ms_per_step=1e3 * tm / len(seeds), dtype="f64 objective, bf16 surrogate",
+                    config={"workload": "ODE fit, 5 seeds, plain DE (k = 1) and 8 screened candidates (25 or 100 "
+                                        "Adam steps per retraining), budget 2e5 true evaluations"},
+                    runs=res, objective_seconds_per_generation=t_obj, gpu_launches=None)
     elif args.workload == "variants":
         # the strategy variants and jDE on the FP64 path: rotated Rastrigin
         # NP = 1024, D = 100, reset + G generations per step, and the best f

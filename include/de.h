@@ -198,7 +198,7 @@ typedef struct {
     int32_t surrogate_k;      /* 0 or 1: plain DE.  2..32: surrogate-assisted generations with this many
                                  candidate trials per target (FP64, d == 20, one run per handle; see
                                  de_get_surrogate_stats) */
-    int32_t surrogate_steps;  /* Adam steps per retraining of the surrogate; 0 = 100 */
+    int32_t surrogate_steps;  /* Adam steps per retraining of the surrogate; 0 = 25 */
     int32_t strategy;         /* de_strategy: base vector and crossover of the trial (Sec. 2); not with a
                                  surrogate */
     int32_t jde;              /* nonzero: jDE self-adaptive F and CR per individual (Sec. 2, the adaptive

@@ -412,7 +412,7 @@ static de_status init_run(de_handle* h, int r) {
   k_init_population_launch(h->d_run, r, R.np, R.dp, h->stream);
   if (R.jde) k_jde_init_launch(h->d_run, r, R.np, h->stream);
   if (h->prec == DE_PREC_FP64) {
-    k_eval_rows_launch(h->d_run, r, R.X[0], R.dp, R.np, R.dp, suite_comps(R), R.f[0], R.fx[0], h->stream);
+    k_eval_rows_launch(h->d_run, r, R, R.X[0], R.dp, R.np, R.f[0], R.fx[0], h->stream);
   } else {
     // split precisions evaluate the initial population in their own precision
     // (values with error bounds, like accepted trials); the best record is
@@ -438,7 +438,7 @@ static de_status exact_best(de_handle* h, int r) {
   DE_CUDA(h, cudaStreamSynchronize(h->stream));
   if (fx) return DE_OK;
   double* fb = R.f[cur] + st.best_idx;
-  k_eval_rows_launch(h->d_run, r, R.X[cur] + (size_t)st.best_idx * R.dp, R.dp, 1, R.dp, suite_comps(R), fb,
+  k_eval_rows_launch(h->d_run, r, R, R.X[cur] + (size_t)st.best_idx * R.dp, R.dp, 1, fb,
                      R.fx[cur] + st.best_idx, h->stream);
   DE_CUDA(h, cudaGetLastError());
   DE_CUDA(h, cudaMemcpyAsync(&st.best_f, fb, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1377,7 +1377,7 @@ de_status de_eval(de_handle* h, int32_t run, const double* x_dev, int64_t ld, in
     return fail(h, DE_ERR_INVALID_ARG, "f_dev is not device memory");
   }
   if (h->prec == DE_PREC_FP64) {
-    k_eval_rows_launch(h->d_run, run, x_dev, ld, n, R.dp, suite_comps(R), f_dev, nullptr, h->stream);
+    k_eval_rows_launch(h->d_run, run, R, x_dev, ld, n, f_dev, nullptr, h->stream);
   } else {
     de_status s = tc_eval_launch(h->tc, h->d_run, run, R, x_dev, ld, n, f_dev, h->stream, h->err);
     if (s != DE_OK) return s;
@@ -1428,7 +1428,7 @@ de_status de_set_population(de_handle* h, int32_t run, const double* x_host, con
     DE_CUDA(h, cudaMemcpyAsync(R.f[cur], f_host, R.np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     DE_CUDA(h, cudaMemsetAsync(R.fx[cur], 1, R.np, h->stream));
   } else {
-    k_eval_rows_launch(h->d_run, run, R.X[cur], R.dp, R.np, R.dp, suite_comps(R), R.f[cur], R.fx[cur], h->stream);
+    k_eval_rows_launch(h->d_run, run, R, R.X[cur], R.dp, R.np, R.f[cur], R.fx[cur], h->stream);
   }
   k_best_init_launch(h->d_run, run, h->stream);
   DE_CUDA(h, cudaGetLastError());

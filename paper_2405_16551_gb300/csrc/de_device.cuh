@@ -141,8 +141,11 @@ static __device__ __forceinline__ double ode_chain(const double* __restrict__ x,
   const double nk2 = -__dadd_rn(k, 2.0), nc = -c;
   const double h = kOdeDt, hh = kOdeDt * 0.5, h6 = kOdeDt / 6.0;
   double q = lane == 0 ? 1.0 : 0.0, p = 0.0, acc = 0.0;
+  // the reference position of step s is loaded one step ahead, off the
+  // integration's dependency chain
+  double rv = (ref && on) ? __ldg(ref + lane) : 0.0;
   for (int s = 0; s < kOdeSteps; ++s) {
-    const double rv = (ref && on) ? __ldg(ref + s * kOdeN + lane) : 0.0;
+    const double rv_next = (ref && on && s + 1 < kOdeSteps) ? __ldg(ref + (s + 1) * kOdeN + lane) : 0.0;
     const double a1 = __fma_rn(nc, p, __fma_rn(nk2, q, ode_neighbours(q, lane)));
     const double q2 = __fma_rn(hh, p, q), p2 = __fma_rn(hh, a1, p);
     const double a2 = __fma_rn(nc, p2, __fma_rn(nk2, q2, ode_neighbours(q2, lane)));
@@ -160,6 +163,7 @@ static __device__ __forceinline__ double ode_chain(const double* __restrict__ x,
       }
       if (out) out[s * kOdeN + lane] = q;
     }
+    rv = rv_next;
   }
   return acc;
 }

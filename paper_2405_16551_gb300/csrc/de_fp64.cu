@@ -708,8 +708,20 @@ void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cuda
   k_init_population<<<blocks, threads, 0, s>>>(runs, run);
 }
 
-void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int ncomp,
+void k_eval_rows_launch(const RunDesc* runs, int run, const RunDesc& Rh, const double* x, int64_t ld, int n,
                         double* f, uint8_t* fx, cudaStream_t s) {
+  if (n <= 0) return;
+  if (Rh.obj == kObjOde) {
+    // a warp per row, few rows per CTA: the rows spread over every SM (an
+    // SM's FP64 pipe, not the latency of one chain, bounds a CTA of 8 chains)
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int rows = std::max(1, std::min(8, (n + nsm - 1) / std::max(nsm, 1)));
+    k_eval_rows<<<(n + rows - 1) / rows, 32 * rows, 0, s>>>(runs, run, x, ld, n, rows, f, fx);
+    return;
+  }
+  const int dp = Rh.dp, ncomp = suite_comps(Rh);
   int rows = 8;
   while (rows > 1 && (size_t)2 * ncomp * rows * dp * sizeof(double) > 200 * 1024) rows >>= 1;
   const size_t smem = (size_t)2 * ncomp * rows * dp * sizeof(double);

@@ -46,8 +46,9 @@ cudaError_t k_gen_fp64_cluster_launch(const RunDesc* runs, const int4* items, in
                                       bool var, bool suite, PersistCtl* ctl, long long gens, cudaStream_t s);
 bool k_gen_fp64_cluster_fits(int nitems, int threads, size_t smem, bool var, bool suite);
 void k_init_population_launch(const RunDesc* runs, int run, int np, int dp, cudaStream_t s);
-// ncomp: row buffers per row (the components of a composition function, else 1)
-void k_eval_rows_launch(const RunDesc* runs, int run, const double* x, int64_t ld, int n, int dp, int ncomp,
+// f (and, when fx is not NULL, the FP64 flags) of n rows of x; Rh is the
+// host copy of run `run`'s descriptor
+void k_eval_rows_launch(const RunDesc* runs, int run, const RunDesc& Rh, const double* x, int64_t ld, int n,
                         double* f, uint8_t* fx, cudaStream_t s);
 inline int suite_comps(const RunDesc& R) { return R.obj >= DE_OBJ_COMPOSITION1 ? R.nc : 1; }
 void k_best_init_launch(const RunDesc* runs, int run, cudaStream_t s);
@@ -97,8 +98,8 @@ struct PersistPlan {
   size_t cta_smem = 0;
 };
 
-// the persistent batch kernel (de_persist_batch.cu): work items of at most 8
-// targets of one run, a fixed contiguous slice of items per CTA, per-run
+// the persistent batch kernel (de_persist_batch.cu): work items are the runs'
+// 128-target tiles, a fixed contiguous slice of items per CTA, per-run
 // arrival counters
 struct PbPlan {
   bool ok = false;

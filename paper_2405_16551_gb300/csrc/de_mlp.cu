@@ -15,9 +15,11 @@
 //                   128-row half of a 256-row minibatch: dZ2 = dy w3 relu',
 //                   dH1 = dZ2 W2 on the tensor cores, dZ1 = dH1 relu'; writes
 //                   the transposed operands of the weight gradients
-//   k_mlp_update    weight gradients as products over the batch
-//                   (dW2 = dZ2^T H1 with a ones row for db2, dW1 = dZ1^T A1),
-//                   then Adam on the FP32 masters and the BF16 operand copies
+//   k_mlp_wgrad     weight gradients as products over the batch
+//                   (dW2 = dZ2^T H1 with a ones row for db2, dW1 = dZ1^T A1)
+//                   into the raw gradient vector
+//   k_mlp_adam      Adam on every FP32 master (one thread per parameter,
+//                   coalesced) and the BF16 operand copies of W1 | b1 and W2
 //
 // Operand layout in shared and global memory: the canonical K-major, no
 // swizzle layout of de_tcgen05.cuh (core matrices of 8 rows x 16 bytes).
@@ -325,7 +327,6 @@ __global__ void __launch_bounds__(256, 1) k_mlp_pass(MlpDev P, MlpStepArgs a, co
 struct AdamArgs {
   float lr, c1, c2, eps, beta1, beta2;  // c1 = 1 - beta1^t, c2 = 1 - beta2^t
   float omb1, omb2;                     // 1 - beta1, 1 - beta2 (rounded once from FP64)
-  int apply;                            // 0: write raw gradients to P.grad instead
 };
 
 __device__ __forceinline__ float adam_step(float w, float g, float* m, float* v, const AdamArgs& A) {
@@ -336,8 +337,9 @@ __device__ __forceinline__ float adam_step(float w, float g, float* m, float* v,
   return w - A.lr * (mn / A.c1) / (sqrtf(vn / A.c2) + A.eps);
 }
 
-// Blocks 0, 1: rows [128 b, 128 b + 128) of W2 and b2; block 2: W1, b1, w3, b3.
-__global__ void __launch_bounds__(256, 1) k_mlp_update(MlpDev P, AdamArgs A) {
+// Raw weight gradients of one step into P.grad.  Blocks 0, 1: rows
+// [128 b, 128 b + 128) of W2 and b2; block 2: W1, b1, w3, b3 and the loss.
+__global__ void __launch_bounds__(256, 1) k_mlp_wgrad(MlpDev P) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ uint32_t s_tmem;
@@ -401,67 +403,23 @@ __global__ void __launch_bounds__(256, 1) k_mlp_update(MlpDev P, AdamArgs A) {
       const int c0 = 128 * h + 32 * j;
       float g[32];
       tmem_ld_cols32(tmem + lane_base + (uint32_t)c0, g);
-      float wn[32];
+      float4* dst = reinterpret_cast<float4*>(P.grad + kMlpOffW2 + (size_t)o * kMlpH + c0);
 #pragma unroll
-      for (int e = 0; e < 32; ++e) {
-        const size_t k = (size_t)o * kMlpH + c0 + e;
-        if (A.apply) {
-          wn[e] = adam_step(P.W2[k], g[e], P.mW2 + k, P.vW2 + k, A);
-          P.W2[k] = wn[e];
-        } else {
-          P.grad[kMlpOffW2 + k] = g[e];
-          wn[e] = P.W2[k];
-        }
-        // W2^T halves (row = input unit, k = output unit), 16 row groups
-        st_bf16(P.w2t + (size_t)((c0 + e) >> 7) * (kMlpW2Bytes / 2), toff((c0 + e) & 127, o, 16), wn[e]);
-      }
-#pragma unroll
-      for (int e = 0; e < 32; e += 8) st_bf16x8(P.w2k, o, c0 + e, 32, wn + e);
+      for (int e = 0; e < 8; ++e) dst[e] = make_float4(g[4 * e], g[4 * e + 1], g[4 * e + 2], g[4 * e + 3]);
     }
-    if (h == 0) {
-      const float gb = tmem_ld1(tmem + lane_base + 256u);
-      if (A.apply) P.b2[o] = adam_step(P.b2[o], gb, P.mb2 + o, P.vb2 + o, A);
-      else P.grad[kMlpOffB2 + o] = gb;
-    }
+    if (h == 0) P.grad[kMlpOffB2 + o] = tmem_ld1(tmem + lane_base + 256u);
   } else {
     // W1 (and b1 in column 20): thread row o of half h
     const int o = 128 * h + 32 * q + lane;
     float g[32];
     tmem_ld_cols32(tmem + lane_base + 32u * (uint32_t)h, g);
-    float wn[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      if (c < kMlpIn) {
-        const size_t k = (size_t)o * kMlpIn + c;
-        if (A.apply) {
-          wn[c] = adam_step(P.W1[k], g[c], P.mW1 + k, P.vW1 + k, A);
-          P.W1[k] = wn[c];
-        } else {
-          P.grad[kMlpOffW1 + k] = g[c];
-          wn[c] = P.W1[k];
-        }
-      } else if (c == kMlpIn) {
-        if (A.apply) {
-          wn[c] = adam_step(P.b1[o], g[c], P.mb1 + o, P.vb1 + o, A);
-          P.b1[o] = wn[c];
-        } else {
-          P.grad[kMlpOffB1 + o] = g[c];
-          wn[c] = P.b1[o];
-        }
-      } else {
-        wn[c] = 0.f;
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 32; c += 8) st_bf16x8(P.w1k, o, c, 32, wn + c);
+    for (int c = 0; c < kMlpIn; ++c) P.grad[kMlpOffW1 + (size_t)o * kMlpIn + c] = g[c];
+    P.grad[kMlpOffB1 + o] = g[kMlpIn];
     // w3 and b3 from the two halves' partial sums, in a fixed order
-    const float gw = P.part[tid] + P.part[kMlpPart + tid];
-    if (A.apply) P.w3[tid] = adam_step(P.w3[tid], gw, P.mw3 + tid, P.vw3 + tid, A);
-    else P.grad[kMlpOffW3 + tid] = gw;
+    P.grad[kMlpOffW3 + tid] = P.part[tid] + P.part[kMlpPart + tid];
     if (tid == 0) {
-      const float gb = P.part[kMlpH] + P.part[kMlpPart + kMlpH];
-      if (A.apply) P.b3[0] = adam_step(P.b3[0], gb, P.mb3, P.vb3, A);
-      else P.grad[kMlpOffB3] = gb;
+      P.grad[kMlpOffB3] = P.part[kMlpH] + P.part[kMlpPart + kMlpH];
       P.loss[0] = (P.part[kMlpH + 1] + P.part[kMlpPart + kMlpH + 1]) / (float)kMlpBatch;
     }
   }
@@ -469,6 +427,26 @@ __global__ void __launch_bounds__(256, 1) k_mlp_update(MlpDev P, AdamArgs A) {
   __syncthreads();
   if (s_err && tid == 0) atomicOr(P.err, 1);
   if (warp == 0) tmem_free(tmem, ncols);
+}
+
+// Adam on parameter k of the FP32 vector (masters, moments and gradients are
+// laid out alike), then its BF16 operand copies (W1 | b1 and W2; b2, w3 and
+// b3 are read as FP32).
+__global__ void __launch_bounds__(256) k_mlp_adam(MlpDev P, AdamArgs A) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kMlpParams) return;
+  float* W = P.W1;  // the parameter vector starts at W1
+  const float w = adam_step(W[k], P.grad[k], P.mW1 + k, P.vW1 + k, A);
+  W[k] = w;
+  if (k < kMlpOffB1) {
+    st_bf16(P.w1k, toff(k / kMlpIn, k % kMlpIn, 32), w);
+  } else if (k < kMlpOffW2) {
+    st_bf16(P.w1k, toff(k - kMlpOffB1, kMlpIn, 32), w);
+  } else if (k < kMlpOffB2) {
+    const int e = k - kMlpOffW2, o = e / kMlpH, i = e % kMlpH;
+    st_bf16(P.w2k, toff(o, i, 32), w);
+    st_bf16(P.w2t + (size_t)(i >> 7) * (kMlpW2Bytes / 2), toff(i & 127, o, 16), w);
+  }
 }
 
 // BF16 operand copies from the FP32 masters (after set-up or a parameter load).
@@ -491,7 +469,7 @@ __global__ void k_mlp_pack(MlpDev P) {
 void mlp_configure() {
   cudaFuncSetAttribute(k_mlp_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
   cudaFuncSetAttribute(k_mlp_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
-  cudaFuncSetAttribute(k_mlp_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 void mlp_pack_launch(const MlpDev& P, cudaStream_t s) { k_mlp_pack<<<64, 256, 0, s>>>(P); }
@@ -515,8 +493,8 @@ void mlp_step_launch(const MlpDev& P, const MlpStepArgs& a, const double* x, int
   A.eps = 1e-8f;
   A.omb1 = (float)(1.0 - b1);
   A.omb2 = (float)(1.0 - b2);
-  A.apply = apply ? 1 : 0;
-  k_mlp_update<<<3, 256, 200 * 1024, s>>>(P, A);
+  k_mlp_wgrad<<<3, 256, 200 * 1024, s>>>(P);
+  if (apply) k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, s>>>(P, A);
 }
 
 }  // namespace de

@@ -334,7 +334,7 @@ de_status surr_generation(Surrogate& S, const RunDesc* d_run, const RunDesc& R, 
       predicted = true;
     }
   }
-  k_eval_rows_launch(d_run, 0, S.T, dp, np, dp, suite_comps(R), S.ftrial, nullptr, s);
+  k_eval_rows_launch(d_run, 0, R, S.T, dp, np, S.ftrial, nullptr, s);
   k_surr_select<<<(np + 7) / 8, 256, 0, s>>>(d_run, 0, S.T, S.ftrial, S.cand_sel, S.arch_x, S.arch_f, S.head, S.cap);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(S.h_f.data(), S.ftrial, np * sizeof(double), cudaMemcpyDeviceToHost, s);

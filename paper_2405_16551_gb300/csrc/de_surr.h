@@ -31,7 +31,7 @@ de_status mlp_train_rows(::de_mlp* m, const double* x, int64_t ld, const float* 
 //   least rho_min (otherwise one candidate, i.e. plain DE).
 struct Surrogate {
   int k = 8;
-  int steps = 100;
+  int steps = 25;  // Adam steps per retraining (the default of surrogate_steps)
   float lr = 1e-3f;
   int warmup = 5, retrain = 10, window = 20000, cap = 200000;
   double rho_min = 0.3;
