@@ -601,9 +601,10 @@ DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d
  * DE_GB300_PERSIST_CTA_ROWS fixes the targets per CTA of path 4); the
  * environment variable DE_GB300_PERSIST=0 disables both.
  * Test switch (failure detection, off by default): DE_GB300_TEST_GRID_TIMEOUT=k
- * at de_init makes CTA k - 1 of every path-3 launch leave out its first
- * grid-barrier arrival and the barrier give up after a few thousand polls, so
- * that the bounded wait runs out and de_run returns DE_ERR_TIMEOUT. */
+ * at de_init makes CTA k - 1 of every persistent launch (paths 2, 3, 4 and 5)
+ * leave out its first grid-barrier arrival (path 5: the arrival of its first
+ * item's first generation) and the waits give up after a few thousand polls,
+ * so that the bounded wait runs out and de_run returns DE_ERR_TIMEOUT. */
 DE_API de_status de_get_plan(de_handle* h, int32_t* kernel_path, int32_t* cluster_size);
 
 /* Counters of the split-precision selection of run `run` since de_init:

@@ -598,17 +598,8 @@ void k_configure(size_t smem_gen) {
 cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int nruns, int threads,
                                       size_t smem, bool var, bool suite, PersistCtl* ctl, long long gens,
                                       cudaStream_t s, int test_skip) {
-  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
+  cudaError_t e = persist_ctl_reset(ctl, test_skip, s);
   if (e != cudaSuccess) return e;
-  if (test_skip > 0) {
-    // about 4096 polls instead of 2^22: the test's wait runs out in milliseconds
-    const int skip = test_skip;
-    const long long spin = 4096;
-    e = cudaMemcpyAsync(&ctl->test_skip, &skip, sizeof skip, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl->test_spin, &spin, sizeof spin, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // skip and spin live on this stack frame
-    if (e != cudaSuccess) return e;
-  }
   int clustered = 0;
   void* args[] = {(void*)&runs, (void*)&items, (void*)&nruns, (void*)&ctl, (void*)&gens, (void*)&clustered};
   const dim3 grid((unsigned)nitems), block((unsigned)threads);

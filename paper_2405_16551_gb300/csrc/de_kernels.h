@@ -27,6 +27,9 @@ struct PersistCtl {
   // sbar[c % 8][0], each counter on its own 128-byte line
   unsigned int sbar[8][32];
 };
+// zero the control block of a persistent launch; test_skip > 0 also arms the
+// failure-detection test (test_skip, and test_spin = 4096 polls)
+cudaError_t persist_ctl_reset(PersistCtl* ctl, int test_skip, cudaStream_t s);
 // FP64 path (de_fp64.cu)
 void k_configure(size_t smem_gen);
 // var: some run uses a strategy variant or jDE; suite: some run uses an
@@ -112,7 +115,8 @@ struct PbPlan {
 };
 bool pbatch_plan(PbPlan& pp, const std::vector<RunDesc>& runs, int prec);
 void pbatch_free(PbPlan& pp);
-cudaError_t pbatch_launch(const PbPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens, cudaStream_t s);
+cudaError_t pbatch_launch(const PbPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens, cudaStream_t s,
+                          int test_skip = 0);
 
 // split-precision tensor-core path (de_tc.cu)
 struct TcPlan {
@@ -142,13 +146,13 @@ bool persist_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec);
 // 128, with every tile resident); false leaves the plan unchanged
 bool persist_set_rows(PersistPlan& pp, const RunDesc& R, int prows);
 cudaError_t persist_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
-                           cudaStream_t s);
+                           cudaStream_t s, int test_skip = 0);
 // the CTA-local persistent form (de_persist_cta.cu): one run of at most 128
 // coordinates, at most 16 targets per CTA, every CTA resident
 bool persist_cta_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec);
 bool persist_cta_set_rows(PersistPlan& pp, const RunDesc& R, int rows);
 cudaError_t persist_cta_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
-                               cudaStream_t s);
+                               cudaStream_t s, int test_skip = 0);
 // counters after a persistent launch of run 0 (evaluations, trials, tickets)
 void k_persist_close_launch(const RunDesc* runs, const PersistCtl* ctl, cudaStream_t s);
 

@@ -68,9 +68,9 @@ __device__ __forceinline__ void grid_arrive(PersistCtl* ctl) {
 
 // Wait until `target` CTAs have arrived at the grid barrier (called by a
 // whole warp: every lane reads the same counter in the same instruction, so
-// all of them leave the loop together).
-__device__ bool grid_wait(PersistCtl* ctl, unsigned target) {
-  for (long long k = 0; k < kGridSpin; ++k) {
+// all of them leave the loop together); at most `spin` polls.
+__device__ bool grid_wait(PersistCtl* ctl, unsigned target, long long spin) {
+  for (long long k = 0; k < spin; ++k) {
     if (ld_acquire_u32(&ctl->bar) >= target) return true;
     if (*(volatile int*)&ctl->abort) return false;
     __nanosleep(32);
@@ -109,6 +109,10 @@ __global__ void __launch_bounds__(256, 1)
   const int tile = (int)blockIdx.x / C;
   const int nclusters = (int)gridDim.x / C;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // failure-detection test (off unless set by the launcher): this CTA leaves
+  // out its first grid-barrier arrival and the waits give up after test_spin polls
+  const bool test_skip = ctl->test_skip == (int)blockIdx.x + 1;
+  const long long spin_limit = ctl->test_spin > 0 ? ctl->test_spin : kGridSpin;
   // the run descriptor lives in shared memory for the whole launch: its fields
   // are read in every phase, after barriers that would force global reloads
   __shared__ RunDesc sR;
@@ -642,16 +646,16 @@ __global__ void __launch_bounds__(256, 1)
     // every CTA arrives at the grid barrier once its rows are written; the
     // leader waits for all of them
     __syncthreads();
-    if (!leader && tid == 0) grid_arrive(ctl);
+    if (!leader && tid == 0 && !(test_skip && itg == 0)) grid_arrive(ctl);
 
     // ---- 5. grid barrier (thread 0 of each leader); best record and stop
     // rule (the leader's warp 0 reduces the clusters' partials)
     if (leader && warp == 0) {
       if (!s_abort) {
         // the whole warp polls (one load per poll, no divergent spin)
-        if (lane == 0) grid_arrive(ctl);
+        if (lane == 0 && !(test_skip && itg == 0)) grid_arrive(ctl);
         __syncwarp();
-        if (!grid_wait(ctl, (unsigned)(itg + 1) * (unsigned)(nclusters * C)) && lane == 0) {
+        if (!grid_wait(ctl, (unsigned)(itg + 1) * (unsigned)(nclusters * C), spin_limit) && lane == 0) {
           atomicOr(&st->err, kErrTimeout);
           s_abort = 1;
         }
@@ -810,10 +814,22 @@ bool persist_set_rows(PersistPlan& pp, const RunDesc& R, int prows) {
   return true;
 }
 
-cudaError_t persist_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
-                           cudaStream_t s) {
-  if (pp.mode == 1) return persist_cta_launch(pp, runs, ctl, gens, s);
+cudaError_t persist_ctl_reset(PersistCtl* ctl, int test_skip, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
+  if (e != cudaSuccess || test_skip <= 0) return e;
+  // about 4096 polls instead of 2^22: the test's wait runs out in milliseconds
+  const int skip = test_skip;
+  const long long spin = 4096;
+  e = cudaMemcpyAsync(&ctl->test_skip, &skip, sizeof skip, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl->test_spin, &spin, sizeof spin, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // skip and spin live on this stack frame
+  return e;
+}
+
+cudaError_t persist_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
+                           cudaStream_t s, int test_skip) {
+  if (pp.mode == 1) return persist_cta_launch(pp, runs, ctl, gens, s, test_skip);
+  cudaError_t e = persist_ctl_reset(ctl, test_skip, s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(pp.ntiles * pp.C));

@@ -77,6 +77,11 @@ __global__ void __launch_bounds__(kPbThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = (int)blockIdx.x;
   const int2 sl = slices[cta];
+  // failure-detection test (off unless set by the launcher): this CTA leaves
+  // out the arrival of its first item's first generation, and the waits give
+  // up after test_spin polls
+  const bool test_skip = ctl->test_skip == cta + 1;
+  const long long spin_limit = ctl->test_spin > 0 ? ctl->test_spin : kPbSpin;
   const int run_lo = sl.x < sl.y ? items[sl.x].x : 0;
   const int nsr = sl.x < sl.y ? items[sl.y - 1].x - run_lo + 1 : 0;  // runs of the slice (<= kPbSliceRuns)
 
@@ -176,7 +181,7 @@ __global__ void __launch_bounds__(kPbThreads, 1)
   // number `k` of this launch (k >= 1)
   auto wait_run = [&](const RunDesc& R, int r, int k) -> bool {
     const unsigned target = (unsigned)k * (unsigned)R.ntiles_tc;
-    for (long long p = 0; p < kPbSpin; ++p) {
+    for (long long p = 0; p < spin_limit; ++p) {
       unsigned v;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt + r) : "memory");
       if (v >= target) return true;
@@ -555,7 +560,8 @@ __global__ void __launch_bounds__(kPbThreads, 1)
         atomicAdd(&R.stats[1], (unsigned long long)nrows);
         // release: the item's rows, fitness and partial (ordered before by the
         // CTA barrier) are visible to every CTA that observes the count
-        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(cnt + r), "r"(1u) : "memory");
+        if (!(test_skip && itg == 0 && it == sl.x))
+          asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(cnt + r), "r"(1u) : "memory");
       }
     }
     __syncthreads();
@@ -686,8 +692,9 @@ void pbatch_free(PbPlan& pp) {
   pp.ok = false;
 }
 
-cudaError_t pbatch_launch(const PbPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
+cudaError_t pbatch_launch(const PbPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens, cudaStream_t s,
+                          int test_skip) {
+  cudaError_t e = persist_ctl_reset(ctl, test_skip, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(pp.d_cnt, 0, (size_t)pp.nruns * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   const int4* items = pp.d_items;

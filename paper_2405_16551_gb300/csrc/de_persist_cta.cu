@@ -71,6 +71,10 @@ __global__ void __launch_bounds__(256, 1)
     k_persist_cta(const RunDesc* __restrict__ runs, int run, PersistCtl* ctl, long long gens, int rows) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = (int)blockIdx.x, nct = (int)gridDim.x;
+  // failure-detection test (off unless set by the launcher): this CTA leaves
+  // out its first grid-barrier arrival and the barrier gives up after test_spin polls
+  const bool test_skip = ctl->test_skip == cta + 1;
+  const long long spin_limit = ctl->test_spin > 0 ? ctl->test_spin : kCtaGridSpin;
   // the run descriptor lives in shared memory for the whole launch
   __shared__ RunDesc sR;
   static_assert(sizeof(RunDesc) % 8 == 0, "descriptor copied in 8-byte words");
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0) {
       bool ok = s_abort == 0;
       if (ok) {
-        if (lane == 0) {
+        if (lane == 0 && !(test_skip && nbar == 0)) {
           // release: this CTA's rows and partial (ordered before by the CTA
           // barrier) are visible to every CTA that observes the count
           asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&ctl->sbar[cta & 7][0]), "r"(1u) : "memory");
@@ -546,7 +550,7 @@ __global__ void __launch_bounds__(256, 1)
         const unsigned mine = lane < 8 ? (unsigned)((nct - lane + 7) / 8) : 0u;  // CTAs counted by counter `lane`
         const unsigned target = (nbar + 1u) * mine;
         ok = false;
-        for (long long k = 0; k < kCtaGridSpin; ++k) {
+        for (long long k = 0; k < spin_limit; ++k) {
           unsigned v = 0u;
           if (lane < 8)
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->sbar[lane][0]) : "memory");
@@ -668,8 +672,8 @@ bool persist_cta_set_rows(PersistPlan& pp, const RunDesc& R, int rows) {
 }
 
 cudaError_t persist_cta_launch(const PersistPlan& pp, const RunDesc* runs, PersistCtl* ctl, long long gens,
-                               cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PersistCtl), s);
+                               cudaStream_t s, int test_skip) {
+  cudaError_t e = persist_ctl_reset(ctl, test_skip, s);
   if (e != cudaSuccess) return e;
   int run = 0, rows = pp.cta_rows;
   void* args[] = {(void*)&runs, (void*)&run, (void*)&ctl, (void*)&gens, (void*)&rows};

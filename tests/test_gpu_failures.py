@@ -67,6 +67,69 @@ def test_grid_barrier_timeout_is_reported_and_the_device_stays_usable(monkeypatc
     assert r["generations"] == 50 and r["stop_reason"] == capi.DE_STOP_GENERATIONS
 
 
+@pytest.mark.parametrize("mode,path", [("cta", 4), ("cluster", 2)])
+def test_split_persistent_grid_barrier_timeout_is_reported(mode, path, monkeypatch):
+    """The split persistent kernels (the CTA-local one of the NP = 1024,
+    D = 100 configuration, and the cluster form): CTA 0 leaves out its first
+    grid-barrier arrival, every CTA's bounded wait gives up, the run reports
+    DE_ERR_TIMEOUT with no generation completed, and the device stays usable."""
+    _need_gpu()
+    np_, d, obj = 1024, 100, 1
+    o, M = problems.shift(d, seed=23), problems.rotation(d, seed=23)
+    monkeypatch.setenv("DE_GB300_PERSIST_MODE", mode)
+    monkeypatch.setenv("DE_GB300_AUTOTUNE", "0")
+    monkeypatch.setenv("DE_GB300_TEST_GRID_TIMEOUT", "1")
+    cfg = capi.make_config(np_, d, objective=obj, shift=o, rot=M, seed=4, precision=capi.DE_PREC_BF16X3,
+                           max_generations=50, target_error=0.0)
+    h = capi.de_init(cfg)
+    try:
+        assert capi.de_get_plan(h)["kernel_path"] == path
+        with pytest.raises(capi.DEError) as ei:
+            capi.de_run(h)
+        assert ei.value.status == capi.DE_ERR_TIMEOUT
+        assert capi.de_get_best(h)["generations"] == 0
+    finally:
+        capi.de_destroy(h)
+    monkeypatch.delenv("DE_GB300_TEST_GRID_TIMEOUT")
+    h = capi.de_init(cfg)
+    try:
+        assert capi.de_get_plan(h)["kernel_path"] == path
+        r = capi.de_run(h)[0]
+    finally:
+        capi.de_destroy(h)
+    assert r["generations"] == 50 and r["stop_reason"] == capi.DE_STOP_GENERATIONS
+
+
+def test_batch_arrival_counter_timeout_is_reported(monkeypatch):
+    """The persistent batch kernel: CTA 0 leaves out the arrival of its first
+    item's first generation, the CTAs waiting for that run give up, the batch
+    reports DE_ERR_TIMEOUT, and a new handle on the same device runs."""
+    _need_gpu()
+    shapes = [(150, 30, 1), (200, 20, 0), (90, 10, 3), (300, 50, 2)]
+    cfgs = [capi.make_config(n, dd, objective=ob, shift=problems.shift(dd, seed=5, run_id=r),
+                             rot=problems.rotation(dd, seed=5, run_id=r), seed=5, run_id=r,
+                             precision=capi.DE_PREC_BF16X3, max_generations=40, target_error=0.0)
+            for r, (n, dd, ob) in enumerate(shapes)]
+    monkeypatch.setenv("DE_GB300_PERSIST_BATCH", "1")
+    monkeypatch.setenv("DE_GB300_TEST_GRID_TIMEOUT", "1")
+    h = capi.de_init_batch(cfgs)
+    try:
+        assert capi.de_get_plan(h)["kernel_path"] == 5
+        with pytest.raises(capi.DEError) as ei:
+            capi.de_run(h, len(cfgs))
+        assert ei.value.status == capi.DE_ERR_TIMEOUT
+    finally:
+        capi.de_destroy(h)
+    monkeypatch.delenv("DE_GB300_TEST_GRID_TIMEOUT")
+    h = capi.de_init_batch(cfgs)
+    try:
+        assert capi.de_get_plan(h)["kernel_path"] == 5
+        res = capi.de_run(h, len(cfgs))
+    finally:
+        capi.de_destroy(h)
+    assert all(r["generations"] == 40 for r in res)
+
+
 # ----------------------------------------------------------------------------- NaN fitness
 def _nan_problem(np_, d, seed, values):
     """Unrotated Rastrigin with o = 0 and scale 1e308 on a population whose
