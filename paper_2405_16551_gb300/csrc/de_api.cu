@@ -1063,6 +1063,8 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     R.hi = c.hi;
     R.scale = c.scale;
     R.lo_key = ordered_key(c.lo);
+    R.lo_half = 0.5 * c.lo;
+    R.hi_half = 0.5 * c.hi;
     R.hi_key = ordered_key(c.hi);
     R.unit_scale = c.scale == 1.0;
     R.cr_thr = cr_threshold(c.cr);

@@ -497,15 +497,17 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
   }
   // bound repair: a crossed coordinate outside [lo, hi] goes half way from
   // the target's coordinate to the violated bound (the paper leaves bounds
-  // handling open); the FP64 work runs only when some lane of the warp needs it
-  if (__any_sync(__activemask(), oob != 0u)) {
+  // handling open).  (x_i + b) / 2 rounded once equals fma(0.5, x_i, b / 2):
+  // halving commutes with rounding away from the subnormal range, and b / 2 is
+  // exact.  An FP64 instruction costs the same however few lanes use it, so
+  // each coordinate slot is repaired only when some lane of the warp needs it.
+  const unsigned act = __activemask();
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
-      if ((oob >> m) & 1u) {
-        const double bound = ordered_key(t[m]) < R.lo_key ? R.lo : R.hi;
-        t[m] = __dmul_rn(__dadd_rn(c.xi[m], bound), 0.5);
-      }
-  }
+  for (int m = 0; m < 4; ++m)
+    if (__any_sync(act, (oob >> m) & 1u) && ((oob >> m) & 1u)) {
+      const double half = ordered_key(t[m]) < R.lo_key ? R.lo_half : R.hi_half;
+      t[m] = __fma_rn(0.5, c.xi[m], half);
+    }
   return bits;
 }
 

@@ -56,6 +56,7 @@ struct RunDesc {
   int32_t np, d, dp, obj;
   double F, CR, lo, hi, scale;
   long long lo_key, hi_key;  // ordered integer keys of lo and hi
+  double lo_half, hi_half;   // lo / 2 and hi / 2 (bound repair as one fma)
   int32_t unit_scale;        // scale == 1: the shift needs no multiplication
   int32_t pad0;
   uint64_t cr_thr;
