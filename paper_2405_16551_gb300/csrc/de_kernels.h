@@ -23,9 +23,9 @@ struct PersistCtl {
   // gives up after test_spin polls, so that the bounded wait runs out
   int test_skip;
   long long test_spin;
-  // grid-barrier arrivals of the CTA-local split kernel: CTA c counts on
-  // sbar[c % 8][0], each counter on its own 128-byte line
-  unsigned int sbar[8][32];
+  // grid-barrier arrivals of the CTA-local split kernel in sbar[0] (the rest
+  // of the 128 bytes keeps other fields off its line)
+  unsigned int sbar[32];
 };
 // zero the control block of a persistent launch; test_skip > 0 also arms the
 // failure-detection test (test_skip, and test_spin = 4096 polls)

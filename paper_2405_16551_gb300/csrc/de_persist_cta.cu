@@ -534,26 +534,25 @@ __global__ void __launch_bounds__(256, 1)
     }
     __syncthreads();  // every row and the partial are written
 
-    // ---- 5. grid barrier (arrivals spread over 8 counters on their own
-    // cache lines; lanes 0..7 of warp 0 poll one each).  Meanwhile the other
-    // warps draw the next generation's indices, j_rand and crossover blocks,
-    // which depend on (seed, generation, target) only.
+    // ---- 5. grid barrier (one arrival counter, polled by the whole of warp
+    // 0 in one load; one counter measured about 0.1 us faster per barrier
+    // than arrivals spread over 8).  Meanwhile the other warps draw the next
+    // generation's indices, j_rand and crossover blocks, which depend on
+    // (seed, generation, target) only.
     if (warp == 0) {
       bool ok = s_abort == 0;
       if (ok) {
         if (lane == 0 && !(test_skip && nbar == 0)) {
           // release: this CTA's rows and partial (ordered before by the CTA
           // barrier) are visible to every CTA that observes the count
-          asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&ctl->sbar[cta & 7][0]), "r"(1u) : "memory");
+          asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&ctl->sbar[0]), "r"(1u) : "memory");
         }
         __syncwarp();
-        const unsigned mine = lane < 8 ? (unsigned)((nct - lane + 7) / 8) : 0u;  // CTAs counted by counter `lane`
-        const unsigned target = (nbar + 1u) * mine;
+        const unsigned target = (nbar + 1u) * (unsigned)nct;
         ok = false;
         for (long long k = 0; k < spin_limit; ++k) {
-          unsigned v = 0u;
-          if (lane < 8)
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->sbar[lane][0]) : "memory");
+          unsigned v;
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->sbar[0]) : "memory");
           if (__all_sync(0xffffffffu, v >= target)) {
             ok = true;
             break;

@@ -209,7 +209,9 @@ def test_device_allocation_failure_returns_oom_and_frees_everything():
         capi.de_init_batch(big)
     assert ei.value.status == capi.DE_ERR_OOM
     torch.cuda.synchronize()
-    assert torch.cuda.mem_get_info()[0] == free0
+    # nothing of the failed set-up stays allocated (free memory may only have
+    # grown, by a deferred release of an earlier test's handle)
+    assert torch.cuda.mem_get_info()[0] >= free0
     # the device still serves a normal handle
     h = capi.de_init(capi.make_config(16, 4, max_generations=3, target_error=0.0))
     try:
