@@ -653,6 +653,7 @@ def run_workload(args, capi, torch, rank, world):
                                                 capi.DE_MIGRATE_ASYNC if kind == "async" else capi.DE_MIGRATE_SYNC,
                                                 stream=stream.cuda_stream)
                     nr = m
+                path = KERNEL_PATH_NAMES[capi.de_get_plan(h)["kernel_path"]]
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -662,7 +663,7 @@ def run_workload(args, capi, torch, rank, world):
                 secs.append(e0.elapsed_time(e1) / 1e3)
                 bests.append(min(r["best_f"] for r in res))
                 capi.de_destroy(h)
-            forms[name] = {"best_f_per_seed": bests, "median_best_f": float(np.median(bests)),
+            forms[name] = {"best_f_per_seed": bests, "median_best_f": float(np.median(bests)), "kernel_path": path,
                            "seconds_per_run": float(np.mean(secs)),
                            "trial_evals_per_s": m * npi * G / float(np.mean(secs))}
         line.update(metric=f"trial evals/sec, island model (16 x NP=64, ring migration every 20 generations, "

@@ -586,8 +586,11 @@ DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d
  *      the faster (DE_GB300_PERSIST_BATCH=1 / 0 forces path 5 / path 1)
  *   3  FP64, one cooperative persistent kernel for many generations of
  *      every run of the handle (grid barrier between generations; the same
- *      numbers as path 0; not with islands or a surrogate, and only when
- *      every tile fits on the device at once), or, for one run of at most 8
+ *      numbers as path 0; not with a surrogate, and only when every tile
+ *      fits on the device at once; an island model's migrations and common
+ *      stop run inside the loop, an extra grid barrier after each migration,
+ *      except for the benchmark suite's objectives 5..20, whose islands run
+ *      on path 0), or, for one run of at most 8
  *      tiles, the same loop as one thread-block cluster (cluster barrier);
  *      the FP64 autotuner chooses among path 0 and these when one times
  *      faster on the handle's problem; DE_GB300_FP64_PERSIST=0 / 1 / 2 forces

@@ -328,7 +328,8 @@ static de_status enqueue_generations(de_handle* h, int64_t n) {
                                              h->suite, h->d_ctl64, g, h->stream));
       else
         DE_CUDA(h, k_gen_fp64_persist_launch(h->d_run, h->d_items, h->nitems, h->nruns, h->threads, h->smem_gen,
-                                             h->variants, h->suite, h->d_ctl64, g, h->stream, h->test_grid_skip));
+                                             h->variants, h->suite, h->d_ctl64, g, h->stream, h->test_grid_skip,
+                                             h->islands ? h->d_isl : nullptr, h->islands ? &h->stage : nullptr));
     }
     return DE_OK;
   }
@@ -512,7 +513,7 @@ static int heuristic_rows(const de_handle* h, int nsm) {
 // count, tiles x 2^20 generations per launch, stays below 2^32);
 // DE_GB300_FP64_PERSIST=0 disables it, =1 forces it where it applies.
 static bool fp64_persist_ok(const de_handle* h) {
-  if (h->prec != DE_PREC_FP64 || h->surr || h->islands || !h->d_ctl64 || h->nitems >= 4096) return false;
+  if (h->prec != DE_PREC_FP64 || h->surr || (h->islands && h->suite) || !h->d_ctl64 || h->nitems >= 4096) return false;
   if (const char* e = getenv("DE_GB300_FP64_PERSIST"))
     if (e[0] == '0') return false;
   return h->nitems <= k_gen_fp64_persist_capacity(h->threads, h->smem_gen, h->variants, h->suite);
@@ -1296,7 +1297,11 @@ de_status de_init_islands_ex(const de_config* cfg, int32_t nislands, int32_t int
   h->stage.slot = nislands * migrants;
   h->isl = IslandCtl{nislands, interval, migrants, migration == DE_MIGRATE_ASYNC ? 1 : 0, -1, -1};
   h->islands = true;
-  h->fp64_persist = h->fp64_cluster = false;  // migration runs between generations
+  // the cooperative FP64 kernel migrates inside its generation loop (not
+  // for the benchmark suite's objectives, and never as one cluster: islands
+  // are at least two runs); otherwise migration runs between generations
+  h->fp64_cluster = false;
+  h->fp64_persist = h->fp64_persist && fp64_persist_ok(h);
   drop_graph(h);
   st = islands_resync(h);
   if (st == DE_OK) {

@@ -30,6 +30,7 @@
 #include "de_common.cuh"
 #include "de_internal.cuh"
 #include "de_device.cuh"
+#include "de_island_dev.cuh"
 #include "de_kernels.h"
 #include "de_suite.cuh"
 
@@ -437,12 +438,16 @@ __global__ void __launch_bounds__(256) k_gen_fp64(const RunDesc* __restrict__ ru
 // the global writes of every thread, replaces the counter.
 constexpr long long kFp64Spin = 1LL << 22;
 
-template <bool VAR, bool SUITE>
+// ISL: the runs are islands (an instance of its own, so that the other
+// instances keep their register allocation)
+template <bool VAR, bool SUITE, bool ISL>
 __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restrict__ runs,
                                                           const int4* __restrict__ items, int nruns,
-                                                          PersistCtl* ctl, long long gens, int clustered) {
+                                                          PersistCtl* ctl, long long gens, int clustered,
+                                                          IslandCtl* isl, IslandStage stage) {
   extern __shared__ __align__(16) double sm[];
   __shared__ int s_stop, s_best, s_abort, s_done;
+  __shared__ unsigned s_below;
   __shared__ long long s_gen, s_evals;
   __shared__ double s_bestf;
   __shared__ double s_bf[8];
@@ -466,6 +471,7 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
     s_best = st->best_idx;
     s_abort = 0;
     s_done = 0;
+    s_below = 0u;
     if (blockIdx.x == 0) ctl->gen0 = s_gen;
     if (s_stop && it.y == 0 && nruns > 1) atomicAdd(&ctl->stopped[2], 1u);
   }
@@ -477,6 +483,43 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
   // out its first arrival, and the barrier may give up sooner
   const bool test_skip = ctl->test_skip == (int)blockIdx.x + 1;
   const long long spin_limit = ctl->test_spin > 0 ? ctl->test_spin : kFp64Spin;
+  // grid barrier number nbar + 1 (warp 0; the whole warp polls the counter,
+  // one load per poll, no divergent spin)
+  unsigned nbar = 0;
+  auto grid_sync = [&]() -> bool {
+    if (lane == 0 && !(test_skip && nbar == 0)) {
+      __threadfence();
+      atomicAdd(&ctl->bar, 1u);
+    }
+    __syncwarp();
+    const unsigned target = (nbar + 1u) * nct;
+    bool ok = false;
+    for (long long k = 0; k < spin_limit; ++k) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->bar) : "memory");
+      if (v >= target) {
+        ok = true;
+        break;
+      }
+      if (*(volatile int*)&ctl->abort) break;
+      __nanosleep(32);
+    }
+    __syncwarp();
+    ++nbar;
+    return ok;
+  };
+  // a grid barrier of the whole CTA (island migration steps)
+  auto full_sync = [&]() {
+    if (warp == 0) {
+      const bool ok = grid_sync();
+      if (!ok && lane == 0) {
+        atomicExch(&ctl->abort, 1);
+        atomicOr(&st->err, kErrTimeout);
+        s_abort = 1;
+      }
+    }
+    __syncthreads();
+  };
   for (long long itg = 0; itg < gens; ++itg) {
     const bool live = !s_stop;
     const int64_t g = s_gen + 1;
@@ -490,31 +533,16 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
         BestPartial* pp = R.part + (size_t)(g & 1) * ntiles + it.y;
         pp->f = bb.f;
         pp->idx = bb.i;
+        // island model: the model stops as a whole once any island's best is
+        // below the target (counted before the barrier, read after it)
+        if (ISL && R.target > 0.0 && bb.i >= 0 && bb.f < R.target) atomicAdd(&ctl->below[itg % 3], 1u);
       }
     }
     if (clustered) {
       cg::this_cluster().sync();
     } else if (warp == 0) {
-      // arrive, then wait for every CTA of this iteration; the whole warp
-      // polls the counter (one load per poll, no divergent spin)
-      if (lane == 0 && !(test_skip && itg == 0)) {
-        __threadfence();
-        atomicAdd(&ctl->bar, 1u);
-      }
-      __syncwarp();
-      const unsigned target = (unsigned)(itg + 1) * nct;
-      bool ok = false;
-      for (long long k = 0; k < spin_limit; ++k) {
-        unsigned v;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->bar) : "memory");
-        if (v >= target) {
-          ok = true;
-          break;
-        }
-        if (*(volatile int*)&ctl->abort) break;
-        __nanosleep(32);
-      }
-      __syncwarp();
+      // arrive, then wait for every CTA of this iteration
+      const bool ok = grid_sync();
       if (lane == 0) {
         if (!ok) {
           atomicExch(&ctl->abort, 1);
@@ -527,6 +555,12 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
           // next written at iteration itg + 1, after the next barrier
           if (blockIdx.x == 0) ctl->stopped[(itg + 1) % 3] = 0u;
           if (nstopped >= (unsigned)nruns) s_done = 1;
+        }
+        if (ISL && ok) {
+          s_below = __ldcg(&ctl->below[itg % 3]);
+          // every CTA read slot (itg + 2) % 3 before arriving at this barrier;
+          // it is next counted at iteration itg + 2
+          if (blockIdx.x == 0) ctl->below[(itg + 2) % 3] = 0u;
         }
       }
     }
@@ -552,7 +586,8 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
         }
         const int64_t evals = s_evals + R.np;
         int stop = 0;
-        if (R.target > 0.0 && s_best >= 0 && s_bestf < R.target) stop = 1;
+        if (ISL && s_below > 0u) stop = 1;  // some island is below the target
+        else if (R.target > 0.0 && s_best >= 0 && s_bestf < R.target) stop = 1;
         else if (R.max_evals > 0 && evals >= R.max_evals) stop = 2;
         else if (g >= R.max_gens) stop = 3;
         s_evals = evals;
@@ -574,6 +609,43 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
       __syncthreads();
       if (nruns == 1 && s_stop) break;
     }
+    if constexpr (ISL) {
+      if (!(live && isl->interval > 0 && g % isl->interval == 0)) continue;
+      // island model: migration after generation g (the islands advance
+      // together, so every CTA takes this branch).  The CTA of each island's
+      // tile 0 exchanges; a grid barrier then keeps every tile from building
+      // generation g + 1 before the migrants are in place.
+      const int cur = (int)(g & 1);
+      const bool owner = it.y == 0;
+      if (isl->async) {
+        // one interval late, through the mailbox (k_island_async's rule)
+        const int64_t ep = g / isl->interval;
+        // post_gen is written by CTA 0 after an earlier migration's barrier: read at L2
+        const long long pg = *(volatile long long*)&isl->post_gen;
+        const bool take = pg >= 0 && pg == g - isl->interval;
+        if (owner)
+          island_exchange(R, it.x, isl->m, isl->nmig, cur, stage, true, (size_t)(ep & 1) * stage.slot, take,
+                          (size_t)((ep & 1) ^ 1) * stage.slot);
+      } else {
+        // every island posts before any island takes
+        if (owner) island_exchange(R, it.x, isl->m, isl->nmig, cur, stage, true, 0, false, 0);
+        full_sync();
+        if (s_abort) break;
+        if (owner) island_exchange(R, it.x, isl->m, isl->nmig, cur, stage, false, 0, true, 0);
+      }
+      full_sync();
+      if (s_abort) break;
+      if (tid == 0) {
+        // the island's best record after the exchange (DE/best/1's base)
+        s_best = *(volatile int32_t*)&st->best_idx;
+        s_bestf = *(volatile double*)&st->best_f;
+        if (blockIdx.x == 0) {
+          isl->mig_gen = g;
+          if (isl->async) isl->post_gen = g;
+        }
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -588,26 +660,34 @@ void k_configure(size_t smem_gen) {
   cudaFuncSetAttribute(k_gen_fp64<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_gen_fp64<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_gen_fp64<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_gen_fp64_persist<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_gen_fp64_persist<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_gen_fp64_persist<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_gen_fp64_persist<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64_persist<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64_persist<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64_persist<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64_persist<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64_persist<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_gen_fp64_persist<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_eval_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int nruns, int threads,
                                       size_t smem, bool var, bool suite, PersistCtl* ctl, long long gens,
-                                      cudaStream_t s, int test_skip) {
+                                      cudaStream_t s, int test_skip, IslandCtl* isl, const IslandStage* stage) {
   cudaError_t e = persist_ctl_reset(ctl, test_skip, s);
   if (e != cudaSuccess) return e;
   int clustered = 0;
-  void* args[] = {(void*)&runs, (void*)&items, (void*)&nruns, (void*)&ctl, (void*)&gens, (void*)&clustered};
+  IslandStage st{};
+  if (stage) st = *stage;
+  void* args[] = {(void*)&runs, (void*)&items, (void*)&nruns, (void*)&ctl, (void*)&gens, (void*)&clustered,
+                  (void*)&isl, (void*)&st};
   const dim3 grid((unsigned)nitems), block((unsigned)threads);
-  if (var && suite) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<true, true>, grid, block, args, smem, s);
-  else if (var) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<true, false>, grid, block, args, smem, s);
-  else if (suite) e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<false, true>, grid, block, args, smem, s);
-  else e = cudaLaunchCooperativeKernel((const void*)k_gen_fp64_persist<false, false>, grid, block, args, smem, s);
-  return e;
+  if (isl && suite) return cudaErrorInvalidValue;  // islands of the suite's objectives run generation by generation
+  const void* k = isl ? (var ? (const void*)k_gen_fp64_persist<true, false, true>
+                             : (const void*)k_gen_fp64_persist<false, false, true>)
+                  : var && suite ? (const void*)k_gen_fp64_persist<true, true, false>
+                  : var          ? (const void*)k_gen_fp64_persist<true, false, false>
+                  : suite        ? (const void*)k_gen_fp64_persist<false, true, false>
+                                 : (const void*)k_gen_fp64_persist<false, false, false>;
+  return cudaLaunchCooperativeKernel(k, grid, block, args, smem, s);
 }
 
 // The same kernel as one cluster of nitems CTAs (nitems <= 8, one run).
@@ -627,9 +707,12 @@ static cudaError_t fp64_cluster_launch(const RunDesc* runs, const int4* items, i
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (query_only) return cudaOccupancyMaxActiveClusters(nclusters, k_gen_fp64_persist<VAR, SUITE>, &cfg);
+  if (query_only) return cudaOccupancyMaxActiveClusters(nclusters, k_gen_fp64_persist<VAR, SUITE, false>, &cfg);
   const int nruns = 1, clustered = 1;
-  return cudaLaunchKernelEx(&cfg, k_gen_fp64_persist<VAR, SUITE>, runs, items, nruns, ctl, gens, clustered);
+  IslandCtl* isl = nullptr;
+  const IslandStage stage{};
+  return cudaLaunchKernelEx(&cfg, k_gen_fp64_persist<VAR, SUITE, false>, runs, items, nruns, ctl, gens, clustered, isl,
+                            stage);
 }
 
 cudaError_t k_gen_fp64_cluster_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,
@@ -661,10 +744,10 @@ int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite) 
   int per_sm = 0, dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const void* f = var && suite ? (const void*)k_gen_fp64_persist<true, true>
-                  : var        ? (const void*)k_gen_fp64_persist<true, false>
-                  : suite      ? (const void*)k_gen_fp64_persist<false, true>
-                               : (const void*)k_gen_fp64_persist<false, false>;
+  const void* f = var && suite ? (const void*)k_gen_fp64_persist<true, true, false>
+                  : var        ? (const void*)k_gen_fp64_persist<true, false, false>
+                  : suite      ? (const void*)k_gen_fp64_persist<false, true, false>
+                               : (const void*)k_gen_fp64_persist<false, false, false>;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -39,6 +39,7 @@
 #include "de_common.cuh"
 #include "de_device.cuh"
 #include "de_internal.cuh"
+#include "de_island_dev.cuh"
 #include "de_kernels.h"
 
 namespace de {
@@ -46,84 +47,6 @@ namespace de {
 // a migration is due after generation gen
 __device__ __forceinline__ bool island_due(const IslandCtl* ctl, int64_t gen) {
   return ctl->interval > 0 && gen > 0 && gen % ctl->interval == 0 && gen > ctl->mig_gen;
-}
-
-// CTA-wide arg-extremum of (key, index) over i in [0, np) minus the `ntaken`
-// indices already chosen; worst = largest (key, index), else smallest.
-__device__ int island_pick(const double* __restrict__ f, int np, const int* taken, int ntaken, bool worst) {
-  __shared__ long long sk[32];
-  __shared__ int si[32];
-  long long bk = worst ? (long long)0x8000000000000000LL : 0x7FFFFFFFFFFFFFFFLL;
-  int bi = -1;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    bool t = false;
-    for (int q = 0; q < ntaken; ++q) t |= taken[q] == i;
-    if (t) continue;
-    const long long k = fit_key(f[i]);
-    const bool take = bi < 0 || (worst ? (k > bk || (k == bk && i > bi)) : (k < bk || (k == bk && i < bi)));
-    if (take) {
-      bk = k;
-      bi = i;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    const bool take = oi >= 0 && (bi < 0 || (worst ? (ok > bk || (ok == bk && oi > bi)) : (ok < bk || (ok == bk && oi < bi))));
-    if (take) {
-      bk = ok;
-      bi = oi;
-    }
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    sk[warp] = bk;
-    si[warp] = bi;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      const long long ok = sk[w];
-      const int oi = si[w];
-      const bool take = oi >= 0 && (bi < 0 || (worst ? (ok > bk || (ok == bk && oi > bi)) : (ok < bk || (ok == bk && oi < bi))));
-      if (take) {
-        bk = ok;
-        bi = oi;
-      }
-    }
-    si[0] = bi;
-  }
-  __syncthreads();
-  const int r = si[0];
-  __syncthreads();
-  return r;
-}
-
-// the island's best record after an exchange (the whole CTA)
-__device__ void island_best_record(const RunDesc& R, int cur) {
-  __shared__ double sf[32];
-  __shared__ long long sk[32];
-  __shared__ int si[32];
-  Best b;
-  b.init();
-  for (int i = threadIdx.x; i < R.np; i += blockDim.x) b.offer(R.f[cur][i], i);
-  b.warp_reduce();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    sf[warp] = b.f;
-    sk[warp] = b.k;
-    si[warp] = b.i;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    b.init();
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b.take(sf[w], sk[w], si[w]);
-    if (b.i >= 0) {
-      R.st->best_f = b.f;
-      R.st->best_idx = b.i;
-    }
-  }
 }
 
 __global__ void __launch_bounds__(256) k_island_select(const RunDesc* __restrict__ runs, const IslandCtl* ctl,
@@ -189,61 +112,15 @@ __global__ void __launch_bounds__(256) k_island_apply(const RunDesc* __restrict_
 
 __global__ void __launch_bounds__(256) k_island_async(const RunDesc* __restrict__ runs, const IslandCtl* ctl,
                                                       IslandStage stage) {
-  const int k = blockIdx.x, m = ctl->m;
+  const int k = blockIdx.x;
   const RunDesc& R = runs[k];
   const int64_t gen = *(volatile int64_t*)&R.st->gen;
   if (!island_due(ctl, gen)) return;
-  const int cur = (int)(gen & 1), nmig = ctl->nmig;
   const int64_t ep = gen / ctl->interval;
   const size_t wslot = (size_t)(ep & 1) * stage.slot, rslot = (size_t)((ep & 1) ^ 1) * stage.slot;
   // the previous migration point posted (not so after a reset or a population change)
   const bool take = ctl->post_gen >= 0 && ctl->post_gen == gen - ctl->interval;
-  const double* f = R.f[cur];
-  __shared__ int best[kIslandMaxMigrants], worst[kIslandMaxMigrants];
-  for (int q = 0; q < nmig; ++q) {
-    const int b = island_pick(f, R.np, best, q, false);
-    if (threadIdx.x == 0) best[q] = b;
-    __syncthreads();
-  }
-  for (int q = 0; q < nmig && take; ++q) {
-    const int w = island_pick(f, R.np, worst, q, true);
-    if (threadIdx.x == 0) worst[q] = w;
-    __syncthreads();
-  }
-  // post this island's best (rows disjoint from its worst: nmig <= np / 2 and
-  // both orders are total)
-  for (int q = 0; q < nmig; ++q) {
-    const size_t s = wslot + (size_t)k * nmig + q;
-    const double* src = R.X[cur] + (size_t)best[q] * R.dp;
-    for (int j = threadIdx.x; j < R.dp; j += blockDim.x) stage.x[s * stage.dp + j] = src[j];
-    if (threadIdx.x == 0) {
-      stage.f[s] = f[best[q]];
-      stage.fx[s] = R.fx[cur][best[q]];
-      if (R.jde) {
-        stage.F[s] = R.jF[cur][best[q]];
-        stage.CR[s] = R.jCR[cur][best[q]];
-      }
-    }
-  }
-  if (!take) return;
-  // take the predecessor's posts of the previous migration point
-  const int from = (k + m - 1) % m;
-  for (int q = 0; q < nmig; ++q) {
-    const size_t s = rslot + (size_t)from * nmig + q;
-    const int w = worst[q];
-    double* dst = R.X[cur] + (size_t)w * R.dp;
-    for (int j = threadIdx.x; j < R.dp; j += blockDim.x) dst[j] = stage.x[s * stage.dp + j];
-    if (threadIdx.x == 0) {
-      R.f[cur][w] = stage.f[s];
-      R.fx[cur][w] = stage.fx[s];
-      if (R.jde) {
-        R.jF[cur][w] = stage.F[s];
-        R.jCR[cur][w] = stage.CR[s];
-      }
-    }
-  }
-  __syncthreads();
-  island_best_record(R, cur);
+  island_exchange(R, k, ctl->m, ctl->nmig, (int)(gen & 1), stage, true, wslot, take, rslot);
 }
 
 // posted: this launch follows k_island_async (a due migration posted)

@@ -23,6 +23,9 @@ struct PersistCtl {
   // gives up after test_spin polls, so that the bounded wait runs out
   int test_skip;
   long long test_spin;
+  // island model in the cooperative FP64 kernel: tiles whose best is below
+  // the target, per iteration mod 3 (the model's common stop)
+  unsigned int below[3];
   // grid-barrier arrivals of the CTA-local split kernel in sbar[0] (the rest
   // of the 128 bytes keeps other fields off its line)
   unsigned int sbar[32];
@@ -39,9 +42,14 @@ void k_gen_fp64_launch(const RunDesc* runs, const int4* items, int nitems, int t
 // the generation loop of FP64 runs in one cooperative launch (every item
 // co-resident: nitems <= k_gen_fp64_persist_capacity; gens <= 2^20)
 // test_skip > 0: the grid-barrier failure test (PersistCtl::test_skip)
+// isl (NULL without islands): the runs are islands (de_init_islands_ex) whose
+// migrations and common stop run inside the launch
+struct IslandCtl;
+struct IslandStage;
 cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, int nitems, int nruns, int threads,
                                       size_t smem, bool var, bool suite, PersistCtl* ctl, long long gens,
-                                      cudaStream_t s, int test_skip = 0);
+                                      cudaStream_t s, int test_skip = 0, IslandCtl* isl = nullptr,
+                                      const IslandStage* stage = nullptr);
 int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite);
 // the same loop as one thread-block cluster of nitems CTAs (one run,
 // nitems <= 8), the cluster barrier between generations
