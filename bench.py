@@ -912,8 +912,8 @@ def accuracy_workload(capi, torch, stream, problems):
 # the BF16x3 persistent kernel on this workload, scaled to a launch of 3000
 # generations (traffic grows with generations)
 TRAFFIC_PER_LAUNCH = {("k_persist", 3000): (205312 + 1778944) * 3000 // 200,
-                      # k_persist_cta, 7 targets per CTA: 975,872 + 377,088 bytes per 200 generations
-                      ("k_persist_cta", 3000): (975872 + 377088) * 3000 // 200}
+                      # k_persist_cta, 7 targets per CTA: 988,416 + 419,840 bytes per 200 generations
+                      ("k_persist_cta", 3000): (988416 + 419840) * 3000 // 200}
 
 
 if __name__ == "__main__":

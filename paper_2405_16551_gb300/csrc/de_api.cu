@@ -516,7 +516,7 @@ static bool fp64_persist_ok(const de_handle* h) {
   if (h->prec != DE_PREC_FP64 || h->surr || (h->islands && h->suite) || !h->d_ctl64 || h->nitems >= 4096) return false;
   if (const char* e = getenv("DE_GB300_FP64_PERSIST"))
     if (e[0] == '0') return false;
-  return h->nitems <= k_gen_fp64_persist_capacity(h->threads, h->smem_gen, h->variants, h->suite);
+  return h->nitems <= k_gen_fp64_persist_capacity(h->threads, h->smem_gen, h->variants, h->suite, h->islands);
 }
 
 // ... and as one thread-block cluster: one run of at most 8 tiles.

@@ -404,6 +404,14 @@ __device__ __forceinline__ double f64_of_f32(float f) {
   return __longlong_as_double((long long)r);
 }
 
+// y = (t - o) s with the scale known at compile time to be 1 (UNIT: no
+// multiplication on the FP64 pipe, which bounds the trial kernels) or not
+template <bool UNIT>
+__device__ __forceinline__ double shifted_as(double t, double o, double s) {
+  const double y = __dsub_rn(t, o);
+  return UNIT ? y : __dmul_rn(y, s);
+}
+
 // y = (t - o) s, rounded once per operation as written
 __device__ __forceinline__ double shifted(double t, double o, const RunDesc& R) {
   const double y = __dsub_rn(t, o);
@@ -499,15 +507,17 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
   // the target's coordinate to the violated bound (the paper leaves bounds
   // handling open).  (x_i + b) / 2 rounded once equals fma(0.5, x_i, b / 2):
   // halving commutes with rounding away from the subnormal range, and b / 2 is
-  // exact.  An FP64 instruction costs the same however few lanes use it, so
-  // each coordinate slot is repaired only when some lane of the warp needs it.
-  const unsigned act = __activemask();
+  // exact, so the repair is one FP64 instruction per slot; it runs only when
+  // some lane of the warp needs it (one vote per chunk: a vote per slot cost
+  // the FP64 generation kernel more than the instructions it saved)
+  if (__any_sync(__activemask(), oob != 0u)) {
 #pragma unroll
-  for (int m = 0; m < 4; ++m)
-    if (__any_sync(act, (oob >> m) & 1u) && ((oob >> m) & 1u)) {
-      const double half = ordered_key(t[m]) < R.lo_key ? R.lo_half : R.hi_half;
-      t[m] = __fma_rn(0.5, c.xi[m], half);
-    }
+    for (int m = 0; m < 4; ++m)
+      if ((oob >> m) & 1u) {
+        const double half = ordered_key(t[m]) < R.lo_key ? R.lo_half : R.hi_half;
+        t[m] = __fma_rn(0.5, c.xi[m], half);
+      }
+  }
   return bits;
 }
 

@@ -740,14 +740,17 @@ bool k_gen_fp64_cluster_fits(int nitems, int threads, size_t smem, bool var, boo
   return n >= 1;
 }
 
-int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite) {
+int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite, bool isl) {
   int per_sm = 0, dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const void* f = var && suite ? (const void*)k_gen_fp64_persist<true, true, false>
-                  : var        ? (const void*)k_gen_fp64_persist<true, false, false>
-                  : suite      ? (const void*)k_gen_fp64_persist<false, true, false>
-                               : (const void*)k_gen_fp64_persist<false, false, false>;
+  if (isl && suite) return 0;  // islands of the suite's objectives run generation by generation
+  const void* f = isl ? (var ? (const void*)k_gen_fp64_persist<true, false, true>
+                             : (const void*)k_gen_fp64_persist<false, false, true>)
+                  : var && suite ? (const void*)k_gen_fp64_persist<true, true, false>
+                  : var          ? (const void*)k_gen_fp64_persist<true, false, false>
+                  : suite        ? (const void*)k_gen_fp64_persist<false, true, false>
+                                 : (const void*)k_gen_fp64_persist<false, false, false>;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;

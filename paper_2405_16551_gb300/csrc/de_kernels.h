@@ -50,7 +50,8 @@ cudaError_t k_gen_fp64_persist_launch(const RunDesc* runs, const int4* items, in
                                       size_t smem, bool var, bool suite, PersistCtl* ctl, long long gens,
                                       cudaStream_t s, int test_skip = 0, IslandCtl* isl = nullptr,
                                       const IslandStage* stage = nullptr);
-int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite);
+// CTAs of the cooperative FP64 kernel that fit at once (isl: the island instance)
+int k_gen_fp64_persist_capacity(int threads, size_t smem, bool var, bool suite, bool isl = false);
 // the same loop as one thread-block cluster of nitems CTAs (one run,
 // nitems <= 8), the cluster barrier between generations
 cudaError_t k_gen_fp64_cluster_launch(const RunDesc* runs, const int4* items, int nitems, int threads, size_t smem,

@@ -37,6 +37,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 #include <cstring>
 
@@ -293,6 +294,10 @@ __global__ void __launch_bounds__(256, 1)
           }
         }
       }
+      // compiled twice, for a unit domain scale (no multiplication on the
+      // FP64 pipe) and any other
+      auto build = [&](auto unit) {
+      constexpr bool UNIT = decltype(unit)::value;
 #pragma unroll
       for (int q = qb; q < qb + QB; ++q) {
         if (!valid[q]) continue;
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(256, 1)
             float y[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              y[e] = (j0 + e < d) ? to_f32_rn(shifted(t[e], osh[c][e], R)) : 0.f;
+              y[e] = (j0 + e < d) ? to_f32_rn(shifted_as<UNIT>(t[e], osh[c][e], R.scale)) : 0.f;
               yn2 += y[e] * y[e];
             }
             store_split4<ESZ>(lA, a_part, lr, j0, y);
@@ -327,6 +332,9 @@ __global__ void __launch_bounds__(256, 1)
         for (int o = 16; o > 0; o >>= 1) yn2 += __shfl_xor_sync(0xffffffffu, yn2, o);
         if (lane == 0) l_yn[lr] = sqrtf(yn2);
       }
+      };
+      if (R.unit_scale) build(std::true_type{});
+      else build(std::false_type{});
     }
     cluster.sync();  // operands complete
 

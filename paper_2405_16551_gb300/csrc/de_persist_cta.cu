@@ -38,6 +38,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "de_cta_tile.cuh"
 #include "de_device.cuh"
@@ -292,6 +293,10 @@ __global__ void __launch_bounds__(256, 1)
           }
         }
       }
+      // compiled twice, for a unit domain scale (no multiplication on the
+      // FP64 pipe) and any other
+      auto build = [&](auto unit) {
+      constexpr bool UNIT = decltype(unit)::value;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (!valid[q]) continue;
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(256, 1)
           float y[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            y[e] = (j0 + e < d) ? to_f32_rn(shifted(t[e], osh[e], R)) : 0.f;
+            y[e] = (j0 + e < d) ? to_f32_rn(shifted_as<UNIT>(t[e], osh[e], R.scale)) : 0.f;
             yn2 += y[e] * y[e];
           }
           cta_store_split4<ESZ>(sYop, y_part, lr, j0, y);
@@ -322,6 +327,9 @@ __global__ void __launch_bounds__(256, 1)
         for (int o = 16; o > 0; o >>= 1) yn2 += __shfl_xor_sync(0xffffffffu, yn2, o);
         if (lane == 0) s_yn[lr] = sqrtf(yn2);
       }
+      };
+      if (R.unit_scale) build(std::true_type{});
+      else build(std::false_type{});
     }
     // generic-proxy writes of A become visible to the tensor cores' async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -48,6 +48,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -102,9 +103,12 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
   const bool dbg = R.dbg_trial != nullptr;
   const int cw = 4 * lpt;  // coordinates per chunk
   const int nchunks = (R.kpad + cw - 1) / cw;
-  // the loads of chunk c + 1 are issued before chunk c is computed
+  // the loads of chunk c + 1 are issued before chunk c is computed; the loop
+  // is compiled twice, for a unit domain scale (no multiplication) and any other
   ChunkIn cur, nxt;
   if (4 * sub < R.d) trial_load(R, X, s, (uint32_t)i, g, 4 * sub, cur);
+  auto chunks = [&](auto unit) {
+  constexpr bool UNIT = decltype(unit)::value;
   for (int c = 0; c < nchunks; ++c) {
     const int j0 = cw * c + 4 * sub;
     if (c + 1 < nchunks && j0 + cw < R.d) trial_load(R, X, s, (uint32_t)i, g, j0 + cw, nxt);
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
       float y[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        y[q] = (j0 + q < R.d) ? to_f32_rn(shifted(t[q], R.o[j0 + q], R)) : 0.f;
+        y[q] = (j0 + q < R.d) ? to_f32_rn(shifted_as<UNIT>(t[q], R.o[j0 + q], R.scale)) : 0.f;
         yn2 += y[q] * y[q];
       }
       if (valid) store_split4<ESZ>(Ahi, a_part, m, j0, y);
@@ -131,6 +135,9 @@ __global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__
     if (dbg) trial_debug(R, (uint32_t)i, j0, lane, bits, t, lpt, valid);
     cur = nxt;
   }
+  };
+  if (R.unit_scale) chunks(std::true_type{});
+  else chunks(std::false_type{});
   for (int o = lpt >> 1; o > 0; o >>= 1) yn2 += __shfl_xor_sync(0xffffffffu, yn2, o);
   if (valid && sub == 0) R.ynorm[i] = sqrtf(yn2);
 }

@@ -28,6 +28,9 @@ FP64_FORMS = [("0", 0), ("1", 3)]
 def fp64_form(request, monkeypatch):
     env, path = request.param
     monkeypatch.setenv("DE_GB300_FP64_PERSIST", env)
+    # the heuristic tile size (no timed choice from an earlier test's cache),
+    # with which every tile of these shapes is resident at once
+    monkeypatch.setenv("DE_GB300_AUTOTUNE", "0")
     return path
 
 
