@@ -631,7 +631,7 @@ static std::string tune_key_split(const de_handle* h) {
     sum_d += (long long)R.np * R.d;
   }
   char b[256];
-  snprintf(b, sizeof b, "split_v2 prec=%d runs=%d np0=%d d0=%d obj0=%d sumnp=%lld sumnd=%lld", h->prec, h->nruns,
+  snprintf(b, sizeof b, "split_v4 prec=%d runs=%d np0=%d d0=%d obj0=%d sumnp=%lld sumnd=%lld", h->prec, h->nruns,
            h->run[0].np, h->run[0].d, h->run[0].obj, sum_np, sum_d);
   return b;
 }
@@ -640,10 +640,12 @@ static de_status autotune_split(de_handle* h) {
   const char* env = getenv("DE_GB300_AUTOTUNE");
   if ((env && env[0] == '0') || h->tc.persist.ok) return DE_OK;
   const std::string key = tune_key_split(h);
-  // cached value: 100 x targets per trial CTA + 10 x K-chunk divisor + pipeline stages
+  // cached value: 1000 x trial-kernel instance (1: held to 85 registers) + 100
+  // x targets per trial CTA + 10 x K-chunk divisor + pipeline stages
   int code = 0;
   if (tune_lookup(key, code)) {
-    de_status s = tc_set_geometry(h->tc, h->run, code / 100, (code / 10) % 10, code % 10, h->stream, h->err);
+    h->tc.trial_occ = code / 1000;
+    de_status s = tc_set_geometry(h->tc, h->run, (code / 100) % 10, (code / 10) % 10, code % 10, h->stream, h->err);
     if (s == DE_OK) s = upload_desc(h);
     return s;
   }
@@ -659,7 +661,9 @@ static de_status autotune_split(de_handle* h) {
   float best_ms = 1e30f;
   int best = 0;
   de_status st_all = DE_OK;
+  for (int oc = 0; oc < 2 && st_all == DE_OK; ++oc)
   for (int tr : {2, 4, 8}) {
+    h->tc.trial_occ = oc;
     for (int kd : {1, 2, 4})
       for (int ns : {2, 4}) {
       st_all = tc_set_geometry(h->tc, h->run, tr, kd, ns, h->stream, h->err);
@@ -671,14 +675,14 @@ static de_status autotune_split(de_handle* h) {
       }
       launch_generation(h);
       DE_CUDA(h, cudaEventRecord(e0, h->stream));
-      for (int k = 0; k < 3; ++k) launch_generation(h);
+      for (int k = 0; k < 6; ++k) launch_generation(h);
       DE_CUDA(h, cudaEventRecord(e1, h->stream));
       DE_CUDA(h, cudaEventSynchronize(e1));
       float ms = 0.f;
       DE_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best_ms * 0.97f) {
         best_ms = ms;
-        best = tr * 100 + kd * 10 + ns;
+        best = oc * 1000 + tr * 100 + kd * 10 + ns;
       }
       }
     if (st_all != DE_OK) break;
@@ -691,7 +695,8 @@ static de_status autotune_split(de_handle* h) {
   }
   h->run = saved;
   if (st_all != DE_OK) return st_all;
-  de_status s = tc_set_geometry(h->tc, h->run, best / 100, (best / 10) % 10, best % 10, h->stream, h->err);
+  h->tc.trial_occ = best / 1000;
+  de_status s = tc_set_geometry(h->tc, h->run, (best / 100) % 10, (best / 10) % 10, best % 10, h->stream, h->err);
   if (s == DE_OK) s = upload_desc(h);
   if (s == DE_OK) tune_store(key, best);
   return s;

@@ -143,6 +143,7 @@ struct TcPlan {
   size_t smem_band = 0;
   int grid_band = 0;
   int trial_rows = 8;          // targets (warps) per trial CTA
+  int trial_occ = 0;           // 1: the trial kernel instance held to 85 registers (more warps per SM)
   int nsplit = 1;              // N tiles spread over CTAs of the fitness kernel (the largest N-tile count)
   int nruns = 0;
   bool var = false;            // some run uses a strategy variant or jDE

@@ -65,8 +65,12 @@ namespace de {
 // short rows do not leave most lanes of the FP64 instructions idle; warp w of
 // the CTA takes targets (group * warps + w) * (32 / lpt) + L / lpt.
 // VAR: some run uses a strategy variant or jDE (a separate instance).
-template <int ESZ, bool VAR>
-__global__ void __launch_bounds__(256) k_trial_split(const RunDesc* __restrict__ runs, const int2* __restrict__ items) {
+// OCC: an instance held to 85 registers a thread (three 256-thread CTAs' worth
+// of warps per SM), which spills a little but keeps more loads in flight; the
+// autotuner times both on the handle's problem.
+template <int ESZ, bool VAR, bool OCC>
+__global__ void __launch_bounds__(256, OCC ? 3 : 1)
+    k_trial_split(const RunDesc* __restrict__ runs, const int2* __restrict__ items) {
   __shared__ int s_stop, s_best;
   __shared__ long long s_gen;
   const int2 it = items[blockIdx.x];
@@ -1085,14 +1089,20 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int block, si
 
 void tc_generation_launch(const TcPlan& p, const RunDesc* runs, cudaStream_t s) {
   const int tb = 32 * p.trial_rows;
+  const dim3 gt(p.nitems_trial);
+  const int2* ti = p.d_trial_items;
   if (p.prec == DE_PREC_BF16X3) {
-    if (p.var) launch_pdl(k_trial_split<2, true>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
-    else launch_pdl(k_trial_split<2, false>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
+    if (p.var && p.trial_occ) launch_pdl(k_trial_split<2, true, true>, gt, tb, 0, s, runs, ti);
+    else if (p.var) launch_pdl(k_trial_split<2, true, false>, gt, tb, 0, s, runs, ti);
+    else if (p.trial_occ) launch_pdl(k_trial_split<2, false, true>, gt, tb, 0, s, runs, ti);
+    else launch_pdl(k_trial_split<2, false, false>, gt, tb, 0, s, runs, ti);
     launch_pdl(k_fit_tc<2>, dim3(p.nitems_fit, p.nsplit), kFitThreads, p.smem_fit, s, runs,
                (const int2*)p.d_fit_items, 0, (double*)nullptr, 0);
   } else {
-    if (p.var) launch_pdl(k_trial_split<4, true>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
-    else launch_pdl(k_trial_split<4, false>, dim3(p.nitems_trial), tb, 0, s, runs, (const int2*)p.d_trial_items);
+    if (p.var && p.trial_occ) launch_pdl(k_trial_split<4, true, true>, gt, tb, 0, s, runs, ti);
+    else if (p.var) launch_pdl(k_trial_split<4, true, false>, gt, tb, 0, s, runs, ti);
+    else if (p.trial_occ) launch_pdl(k_trial_split<4, false, true>, gt, tb, 0, s, runs, ti);
+    else launch_pdl(k_trial_split<4, false, false>, gt, tb, 0, s, runs, ti);
     launch_pdl(k_fit_tc<4>, dim3(p.nitems_fit, p.nsplit), kFitThreads, p.smem_fit, s, runs,
                (const int2*)p.d_fit_items, 0, (double*)nullptr, 0);
   }
