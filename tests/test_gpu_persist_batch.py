@@ -163,3 +163,39 @@ def test_batch_path_choice_does_not_change_results(monkeypatch):
             capi.de_destroy(h)
     for a, b in zip(*pops):
         assert np.array_equal(a, b)
+
+
+def test_batch_generation_with_a_domain_scale_matches_oracle(monkeypatch):
+    """Runs with a domain scale other than 1 on path 5 (one generation,
+    every undecidable comparison in FP64)."""
+    _need_gpu()
+    monkeypatch.setenv("DE_GB300_PERSIST_BATCH", "1")
+    shapes, s = [(150, 100, 1), (70, 37, 3), (40, 10, 0)], 0.0512
+    cf = []
+    for r, (n, d, obj) in enumerate(shapes):
+        o, M = problems.shift(d, seed=4, run_id=r), problems.rotation(d, seed=4, run_id=r)
+        c = capi.make_config(n, d, objective=obj, scale=s, shift=o, rot=M, seed=4, run_id=r,
+                             precision=capi.DE_PREC_BF16X3, target_error=0.0, max_generations=10**6,
+                             debug_capture=True, fp64_band=capi.DE_BAND_ALL)
+        cf.append((c, o, M))
+    pops = [problems.population(n, d, seed=60 + r) for r, (n, d, _) in enumerate(shapes)]
+    h = capi.de_init_batch([c for c, _, _ in cf])
+    try:
+        assert capi.de_get_plan(h)["kernel_path"] == 5
+        fits = []
+        for r, ((c, o, M), X) in enumerate(zip(cf, pops)):
+            fX, _ = oracle.evaluate(shapes[r][2], X, o, M, scale=s)
+            fits.append(fX)
+            capi.de_set_population(h, r, X, fX)
+            capi.de_set_generation(h, r, 1)
+        capi.de_step(h, 1)
+        for r, ((c, o, M), X, fX) in enumerate(zip(cf, pops, fits)):
+            obj = shapes[r][2]
+            g = capi.de_get_debug(h, r)
+            ref = oracle.step(X, fX, 0.5, 0.9, -100, 100, obj, o, M, seed=4, generation=2, run_id=r, scale=s)
+            assert np.array_equal(g["trial"], ref["trial"]), r
+            fp64 = g["fp64_checked"].astype(bool)
+            tol = np.where(fp64, REL64, REL_SPLIT[capi.DE_PREC_BF16X3]) * (np.abs(ref["f_trial"]) + ref["sabs_trial"])
+            assert np.all(np.abs(g["f_trial"] - ref["f_trial"]) <= tol), r
+    finally:
+        capi.de_destroy(h)

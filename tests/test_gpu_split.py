@@ -351,3 +351,38 @@ def test_integer_fp32_rounding_equals_the_hardware_conversion():
                       5e-324, 1e300, -1e300, 0.1, 1 / 3], dtype=np.float64)
     for arr in (x, ties, rng.uniform(-200, 200, 300_000), edges):
         assert capi.de_selftest_f32_rounding(arr) == 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("obj,d", [(1, 100), (3, 37)])
+def test_split_generation_with_a_domain_scale_matches_oracle(prec, obj, d, split_path):
+    """A domain scale other than 1 (y = (t - o) s, Sec. 7.3.1's folding of
+    [-100, 100] onto the function's domain: 0.0512 for Rastrigin's +-5.12):
+    the trial loops are compiled separately for a unit scale, so this case
+    runs the other instance of each."""
+    _need_gpu()
+    np_, F, CR, s = 300, 0.5, 0.9, 0.0512
+    o, M = problems.shift(d, seed=8), problems.rotation(d, seed=8)
+    X = problems.population(np_, d, seed=8)
+    fX, _ = oracle.evaluate(obj, X, o, M, scale=s)
+    cfg = capi.make_config(np_, d, f=F, cr=CR, objective=obj, scale=s, shift=o, rot=M, seed=8, precision=prec,
+                           max_generations=10**6, target_error=0.0, debug_capture=True, fp64_band=capi.DE_BAND_ALL)
+    h = capi.de_init(cfg)
+    try:
+        _check_path(h, split_path)
+        capi.de_set_population(h, 0, X, fX)
+        capi.de_set_generation(h, 0, 2)
+        capi.de_step(h, 1)
+        g = capi.de_get_debug(h)
+        xn, _ = capi.de_get_population(h)
+    finally:
+        capi.de_destroy(h)
+    r = oracle.step(X, fX, F, CR, -100, 100, obj, o, M, seed=8, generation=3, scale=s)
+    assert np.array_equal(g["trial"], r["trial"])
+    fp64 = g["fp64_checked"].astype(bool)
+    tol_scale = np.abs(r["f_trial"]) + r["sabs_trial"]
+    assert np.all(np.abs(g["f_trial"] - r["f_trial"]) <= np.where(fp64, REL64, REL_SPLIT[prec]) * tol_scale)
+    inband = np.abs(r["f_trial"] - fX) <= REL64 * tol_scale
+    assert np.array_equal(g["accept"][~inband], r["accept"][~inband])
+    acc = g["accept"].astype(bool)
+    assert np.array_equal(xn[acc], r["trial"][acc]) and np.array_equal(xn[~acc], X[~acc])
