@@ -640,7 +640,8 @@ __device__ __forceinline__ void trial_debug(const RunDesc& R, uint32_t i, int j0
 // FP64 path: build the trial row into T and Y = (T - o) s (rows of length dp).
 // VAR: the run may use a strategy variant or jDE (best: the current best row;
 // jF, jCR: the current jDE parameters).
-template <bool VAR>
+// UNIT: the run's domain scale is 1 (the shift without a multiplication)
+template <bool VAR, bool UNIT = false>
 __device__ __forceinline__ void build_trial_row(const RunDesc& R, const double* X, uint32_t i,
                                                 int64_t g, int lane, double* __restrict__ Trow,
                                                 double* __restrict__ Yrow, int best = 0,
@@ -663,7 +664,8 @@ __device__ __forceinline__ void build_trial_row(const RunDesc& R, const double* 
       }
       double y[4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) y[m] = (j0 + m < R.d) ? shifted(t[m], R.o[j0 + m], R) : 0.0;
+      for (int m = 0; m < 4; ++m)
+        y[m] = (j0 + m < R.d) ? (UNIT ? shifted_as<true>(t[m], R.o[j0 + m], 1.0) : shifted(t[m], R.o[j0 + m], R)) : 0.0;
       *reinterpret_cast<double2*>(Trow + j0) = make_double2(t[0], t[1]);
       *reinterpret_cast<double2*>(Trow + j0 + 2) = make_double2(t[2], t[3]);
       *reinterpret_cast<double2*>(Yrow + j0) = make_double2(y[0], y[1]);

@@ -236,6 +236,11 @@ __device__ __forceinline__ Best gen_tile(const RunDesc& R, int64_t g, int row0, 
   if (var) {
     for (int rl = warp; rl < nrows; rl += nwarps)
       build_trial_row<true>(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp, best, jFc, jCRc);
+  } else if (R.unit_scale) {
+    // a unit domain scale: no multiplication on the FP64 pipe (the compiler
+    // would otherwise run it speculatively)
+    for (int rl = warp; rl < nrows; rl += nwarps)
+      build_trial_row<false, true>(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp);
   } else {
     for (int rl = warp; rl < nrows; rl += nwarps)
       build_trial_row<false>(R, X, (uint32_t)(row0 + rl), g, lane, T + rl * dp, Y + rl * dp);
