@@ -67,9 +67,10 @@ namespace de {
 // VAR: some run uses a strategy variant or jDE (a separate instance).
 // OCC: an instance held to 85 registers a thread (three 256-thread CTAs' worth
 // of warps per SM), which spills a little but keeps more loads in flight; the
-// autotuner times both on the handle's problem.
+// other is held to 128 (no spills; left unbounded the compiler takes ~150 and
+// a quarter of the warps).  The autotuner times both on the handle's problem.
 template <int ESZ, bool VAR, bool OCC>
-__global__ void __launch_bounds__(256, OCC ? 3 : 1)
+__global__ void __launch_bounds__(256, OCC ? 3 : 2)
     k_trial_split(const RunDesc* __restrict__ runs, const int2* __restrict__ items) {
   __shared__ int s_stop, s_best;
   __shared__ long long s_gen;
