@@ -1072,6 +1072,8 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
     R.lo_half = 0.5 * c.lo;
     R.hi_half = 0.5 * c.hi;
     R.hi_key = ordered_key(c.hi);
+    R.lo_hk = hi_key32(c.lo);
+    R.hi_hk = hi_key32(c.hi);
     R.unit_scale = c.scale == 1.0;
     R.cr_thr = cr_threshold(c.cr);
     R.seed = c.seed;

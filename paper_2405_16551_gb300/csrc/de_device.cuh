@@ -343,6 +343,26 @@ __host__ __device__ __forceinline__ long long ordered_key(double x) {
   return k >= 0 ? k : -(k & 0x7FFFFFFFFFFFFFFFLL);
 }
 
+// The same order on the high 32 bits alone: a <= b implies
+// hi_key32(a) <= hi_key32(b) for finite a, b (the high word of a
+// magnitude is monotone in it, and -0, +0 and the tiniest values of either
+// sign map to 0).  So hi_key32(x) < hi_key32(lo) proves x < lo, and
+// hi_key32(lo) < hi_key32(x) < hi_key32(hi) proves lo < x < hi; only equal
+// high words need the 64-bit keys.  The trial kernels test bounds with it:
+// the 64-bit key and its compare cost one FP64-pipe instruction per
+// coordinate on this part (counted with sm__inst_executed_pipe_fp64), the
+// 32-bit form none.
+__host__ __device__ __forceinline__ int hi_key32(double x) {
+#if defined(__CUDA_ARCH__)
+  const int h = __double2hiint(x);
+#else
+  long long k;
+  memcpy(&k, &x, sizeof k);
+  const int h = (int)(k >> 32);
+#endif
+  return h >= 0 ? h : -(h & 0x7FFFFFFF);
+}
+
 // FP64 -> FP32 rounding to nearest, ties to even, on the integer pipe (the
 // conversion instruction occupies the FP64 pipe, which bounds the trial
 // kernels on this part).  Normal results: the 29 dropped significand bits
@@ -477,7 +497,10 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
                                                   double t[4], double F, uint64_t thr, int L) {
   const int d = R.d;
   const uint32_t u[4] = {c.u.x, c.u.y, c.u.z, c.u.w};
-  uint32_t bits = 0, oob = 0;
+  // u <= thr on 32 bits (thr = 2^32, CR = 1, crosses every coordinate, as
+  // does the largest 32-bit value)
+  const uint32_t thr32 = thr > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)thr;
+  uint32_t bits = 0, near = 0;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     const int j = j0 + m;
@@ -489,15 +512,17 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
         if (off < 0) off += d;
         crossed = off < L;
       } else {
-        crossed = ((uint32_t)j == s.jr) || ((uint64_t)u[m] <= thr);
+        crossed = ((uint32_t)j == s.jr) || (u[m] <= thr32);
       }
       if (crossed) {
         // Eq. 2: y = x_r1 + F (x_r2 - x_r3), one rounding for the product-sum
         const double v = __fma_rn(F, __dsub_rn(c.x2[m], c.x3[m]), c.x1[m]);
         t[m] = v;
         bits |= 1u << m;
-        const long long kv = ordered_key(v);
-        if (kv < R.lo_key || kv > R.hi_key) oob |= 1u << m;
+        // strictly inside by the high words, else decided below on 64 bits
+        // (non-finite values land there too)
+        const int hk = hi_key32(v);
+        if (hk <= R.lo_hk || hk >= R.hi_hk) near |= 1u << m;
       } else {
         t[m] = c.xi[m];
       }
@@ -507,15 +532,16 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
   // the target's coordinate to the violated bound (the paper leaves bounds
   // handling open).  (x_i + b) / 2 rounded once equals fma(0.5, x_i, b / 2):
   // halving commutes with rounding away from the subnormal range, and b / 2 is
-  // exact, so the repair is one FP64 instruction per slot; it runs only when
-  // some lane of the warp needs it (one vote per chunk: a vote per slot cost
-  // the FP64 generation kernel more than the instructions it saved)
-  if (__any_sync(__activemask(), oob != 0u)) {
+  // exact, so the repair is one FP64 instruction per slot.  It runs only when
+  // some lane of the warp has a coordinate at or past a bound's high word
+  // (one vote per chunk: a vote per slot cost the FP64 generation kernel more
+  // than the instructions it saved).
+  if (__any_sync(__activemask(), near != 0u)) {
 #pragma unroll
     for (int m = 0; m < 4; ++m)
-      if ((oob >> m) & 1u) {
-        const double half = ordered_key(t[m]) < R.lo_key ? R.lo_half : R.hi_half;
-        t[m] = __fma_rn(0.5, c.xi[m], half);
+      if ((near >> m) & 1u) {
+        const long long kv = ordered_key(t[m]);
+        if (kv < R.lo_key || kv > R.hi_key) t[m] = __fma_rn(0.5, c.xi[m], kv < R.lo_key ? R.lo_half : R.hi_half);
       }
   }
   return bits;

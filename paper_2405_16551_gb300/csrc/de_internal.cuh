@@ -58,6 +58,7 @@ struct RunDesc {
   long long lo_key, hi_key;  // ordered integer keys of lo and hi
   double lo_half, hi_half;   // lo / 2 and hi / 2 (bound repair as one fma)
   int32_t unit_scale;        // scale == 1: the shift needs no multiplication
+  int32_t lo_hk, hi_hk;      // ordered keys of the high words of lo and hi (hi_key32)
   int32_t pad0;
   uint64_t cr_thr;
   uint64_t seed;

@@ -135,6 +135,23 @@ def test_one_generation_matches_oracle(np_, d, obj, F, CR, rotate):
     assert np.all(m.sum(axis=1) >= 1)
 
 
+@pytest.mark.parametrize("lo,hi", [(-5.12, 5.12), (0.0, 1.0), (-100.0, 100.0)])
+@pytest.mark.parametrize("F", [0.0, 0.5, 1.0])
+def test_trials_on_and_next_to_the_bounds_match_oracle(lo, hi, F):
+    """Mutants on a bound, one ulp either side of it, at signed zeros and
+    subnormals: the kernels decide "inside" on the high 32 bits of the keys
+    and only equal high words on all 64, so these are the cases where a
+    wrong shortcut would show.  With F = 0 the mutant is x_r1 exactly."""
+    _need_gpu()
+    vals = [lo, hi, np.nextafter(lo, np.inf), np.nextafter(hi, -np.inf), np.nextafter(lo, -np.inf),
+            np.nextafter(hi, np.inf), 0.0, -0.0, 5e-324, -5e-324, 1e-310, -1e-310, 0.5 * (lo + hi),
+            hi + 2.0 ** -20 * abs(hi), lo - 2.0 ** -20 * max(abs(lo), 1.0), hi - 1e-12, lo + 1e-12]
+    rng = np.random.default_rng(11)
+    np_, d = 64, 24
+    X = rng.choice(np.array(vals, dtype=np.float64), size=(np_, d))
+    _step_compare(np_, d, 0, F, 1.0, seed=3, gen=2, rotate=True, lo=lo, hi=hi, X=X)
+
+
 def test_trajectory_small_sphere_matches_oracle_run():
     """The FP64 sphere run (NP=64, D=10, F=0.5, CR=0.9, seed 1, up to 1000
     generations, stop at 1e-8): same stop generation, evaluations and best."""
