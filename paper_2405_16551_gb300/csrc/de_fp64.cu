@@ -493,8 +493,9 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
   unsigned nbar = 0;
   auto grid_sync = [&]() -> bool {
     if (lane == 0 && !(test_skip && nbar == 0)) {
-      __threadfence();
-      atomicAdd(&ctl->bar, 1u);
+      // release: the CTA's writes before the barrier are visible to every
+      // CTA that observes the count
+      asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&ctl->bar), "r"(1u) : "memory");
     }
     __syncwarp();
     const unsigned target = (nbar + 1u) * nct;
@@ -506,15 +507,19 @@ __global__ void __launch_bounds__(256) k_gen_fp64_persist(const RunDesc* __restr
         ok = true;
         break;
       }
-      if (*(volatile int*)&ctl->abort) break;
-      __nanosleep(32);
+      // the abort flag every 16th poll (a read after every poll doubles
+      // the round trips per poll)
+      if ((k & 15) == 15 && *(volatile int*)&ctl->abort) break;
     }
     __syncwarp();
     ++nbar;
     return ok;
   };
-  // a grid barrier of the whole CTA (island migration steps)
+  // a grid barrier of the whole CTA (island migration steps); the CTA
+  // barrier first orders every warp's writes (the posted migrants) before
+  // warp 0's release
   auto full_sync = [&]() {
+    __syncthreads();
     if (warp == 0) {
       const bool ok = grid_sync();
       if (!ok && lane == 0) {

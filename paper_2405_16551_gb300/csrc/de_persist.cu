@@ -52,7 +52,7 @@ namespace de {
 constexpr int kPBandMax = 4;              // band rows per exchange round
 constexpr int kPC = 8;                    // CTAs per cluster
 constexpr int kPMaxC = 16;                // largest cluster
-constexpr long long kGridSpin = 1LL << 22;  // polls of the grid barrier (with back-off)
+constexpr long long kGridSpin = 1LL << 22;  // polls of the grid barrier (each a round trip to L2: seconds in all)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -69,12 +69,13 @@ __device__ __forceinline__ void grid_arrive(PersistCtl* ctl) {
 
 // Wait until `target` CTAs have arrived at the grid barrier (called by a
 // whole warp: every lane reads the same counter in the same instruction, so
-// all of them leave the loop together); at most `spin` polls.
+// all of them leave the loop together); at most `spin` polls, each a round
+// trip to L2 with no pause (the abort flag is read every 16th: a read after
+// every poll doubled the round trips per poll).
 __device__ bool grid_wait(PersistCtl* ctl, unsigned target, long long spin) {
   for (long long k = 0; k < spin; ++k) {
     if (ld_acquire_u32(&ctl->bar) >= target) return true;
-    if (*(volatile int*)&ctl->abort) return false;
-    __nanosleep(32);
+    if ((k & 15) == 15 && *(volatile int*)&ctl->abort) return false;
   }
   atomicExch(&ctl->abort, 1);
   return false;

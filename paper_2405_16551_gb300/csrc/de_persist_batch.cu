@@ -50,7 +50,7 @@ namespace de {
 
 constexpr int kPbThreads = 256;
 constexpr int kPbSliceRuns = 64;           // runs one CTA's slice may touch
-constexpr long long kPbSpin = 1LL << 22;   // polls of a run's arrival counter (with back-off)
+constexpr long long kPbSpin = 1LL << 22;   // polls of a run's arrival counter (each a round trip to L2: seconds in all)
 
 struct PbLayout {
   uint32_t a, b, y, red, total;
@@ -185,8 +185,9 @@ __global__ void __launch_bounds__(kPbThreads, 1)
       unsigned v;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt + r) : "memory");
       if (v >= target) return true;
-      if (*(volatile int*)&ctl->abort) return false;
-      __nanosleep(64);
+      // the abort flag every 16th poll (a read after every poll doubles
+      // the round trips per poll)
+      if ((p & 15) == 15 && *(volatile int*)&ctl->abort) return false;
     }
     if (lane == 0) {
       atomicExch(&ctl->abort, 1);

@@ -47,7 +47,7 @@
 
 namespace de {
 
-constexpr long long kCtaGridSpin = 1LL << 22;     // polls of the grid barrier (with back-off)
+constexpr long long kCtaGridSpin = 1LL << 22;     // polls of the grid barrier (each a round trip to L2: seconds in all)
 
 struct CtaLayout {
   uint32_t yop, mop, z, y, red, total;
@@ -542,56 +542,45 @@ __global__ void __launch_bounds__(256, 1)
     }
     __syncthreads();  // every row and the partial are written
 
-    // ---- 5. grid barrier (one arrival counter, polled by the whole of warp
-    // 0 in one load; one counter measured about 0.1 us faster per barrier
-    // than arrivals spread over 8).  Meanwhile the other warps draw the next
-    // generation's indices, j_rand and crossover blocks, which depend on
-    // (seed, generation, target) only.
-    if (warp == 0) {
-      bool ok = s_abort == 0;
-      if (ok) {
-        if (lane == 0 && !(test_skip && nbar == 0)) {
-          // release: this CTA's rows and partial (ordered before by the CTA
-          // barrier) are visible to every CTA that observes the count
-          asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&ctl->sbar[0]), "r"(1u) : "memory");
+    // ---- 5. grid barrier on one arrival counter.  Warp 0 arrives and polls
+    // the count with one load in flight and no pause; the other warps draw
+    // the next generation's indices, j_rand and crossover blocks meanwhile
+    // (they depend on (seed, generation, target) only).  Measured: reading
+    // the abort flag after every poll doubled the round trips per poll (it
+    // is read every 16th), more polling warps crowd the counter's L2 slice,
+    // which also takes the arrivals, and relaxed polls with one acquire fence
+    // after them cost more than acquire polls.
+    if (warp == 0 && s_abort == 0) {
+      if (lane == 0 && !(test_skip && nbar == 0)) {
+        // release: this CTA's rows and partial (ordered before by the CTA
+        // barrier) are visible to every CTA that observes the count
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&ctl->sbar[0]), "r"(1u) : "memory");
+      }
+      const unsigned target = (nbar + 1u) * (unsigned)nct;
+      bool ok = false;
+      for (long long k = 0; k < spin_limit; ++k) {
+        unsigned v = 0u;
+        if (lane == 0) asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->sbar[0]) : "memory");
+        if (__shfl_sync(0xffffffffu, v, 0) >= target) {
+          ok = true;
+          break;
         }
-        __syncwarp();
-        const unsigned target = (nbar + 1u) * (unsigned)nct;
-        ok = false;
-        for (long long k = 0; k < spin_limit; ++k) {
-          unsigned v;
-          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->sbar[0]) : "memory");
-          if (__all_sync(0xffffffffu, v >= target)) {
-            ok = true;
-            break;
-          }
-          if (*(volatile int*)&ctl->abort) break;
-          __nanosleep(32);
-        }
-        __syncwarp();
-        if (!ok && lane == 0 && !*(volatile int*)&ctl->abort) {
+        if ((k & 15) == 15 && *(volatile int*)&ctl->abort) break;
+      }
+      if (!ok && lane == 0) {
+        if (!*(volatile int*)&ctl->abort) {
           atomicExch(&ctl->abort, 1);
           atomicOr(&st->err, kErrTimeout);
         }
+        s_abort = 1;
       }
-      if (!ok && lane == 0) s_abort = 1;
-    } else if (!VAR) {
+    }
+    if (!VAR) {
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int lr = warp - shift + 8 * q;
         const int i = row0 + lr;
-        if (lr >= rows || i >= np) continue;
-        nts[q] = trial_setup(R, (uint32_t)i, g + 1, lane, 0u, false);
-        nu[q] = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)(g + 1), (uint32_t)i, 1u + lane);
-      }
-    }
-    if (!VAR && warp == 0 && shift == 0) {
-      // warp 0 has targets only with more than 7 per CTA: its draws come last
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int lr = 8 * q;
-        const int i = row0 + lr;
-        if (lr >= rows || i >= np) continue;
+        if (warp < shift || lr >= rows || i >= np) continue;
         nts[q] = trial_setup(R, (uint32_t)i, g + 1, lane, 0u, false);
         nu[q] = draw_block(R.seed, kPurposeStep, R.run_id, 0u, (uint32_t)(g + 1), (uint32_t)i, 1u + lane);
       }
