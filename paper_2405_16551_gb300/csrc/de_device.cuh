@@ -500,7 +500,9 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
   // u <= thr on 32 bits (thr = 2^32, CR = 1, crosses every coordinate, as
   // does the largest 32-bit value)
   const uint32_t thr32 = thr > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)thr;
-  uint32_t bits = 0, near = 0;
+  // per slot: below lo / above hi by the high words alone, or a high word
+  // equal to a bound's (decided on all 64 bits below)
+  uint32_t bits = 0, lowm = 0, highm = 0, eqm = 0;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     const int j = j0 + m;
@@ -519,10 +521,11 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
         const double v = __fma_rn(F, __dsub_rn(c.x2[m], c.x3[m]), c.x1[m]);
         t[m] = v;
         bits |= 1u << m;
-        // strictly inside by the high words, else decided below on 64 bits
-        // (non-finite values land there too)
+        // non-finite values land above hi (+NaN, +inf) or below lo
         const int hk = hi_key32(v);
-        if (hk <= R.lo_hk || hk >= R.hi_hk) near |= 1u << m;
+        lowm |= (uint32_t)(hk < R.lo_hk) << m;
+        highm |= (uint32_t)(hk > R.hi_hk) << m;
+        eqm |= (uint32_t)(hk == R.lo_hk || hk == R.hi_hk) << m;
       } else {
         t[m] = c.xi[m];
       }
@@ -533,16 +536,23 @@ __device__ __forceinline__ uint32_t trial_compute(const RunDesc& R, const TrialS
   // handling open).  (x_i + b) / 2 rounded once equals fma(0.5, x_i, b / 2):
   // halving commutes with rounding away from the subnormal range, and b / 2 is
   // exact, so the repair is one FP64 instruction per slot.  It runs only when
-  // some lane of the warp has a coordinate at or past a bound's high word
-  // (one vote per chunk: a vote per slot cost the FP64 generation kernel more
-  // than the instructions it saved).
-  if (__any_sync(__activemask(), near != 0u)) {
+  // some lane of the warp needs it (one vote per chunk: a vote per slot cost
+  // the FP64 generation kernel more than the instructions it saved), and the
+  // 64-bit keys only when some lane has a high word equal to a bound's (their
+  // compare costs an FP64-pipe instruction per slot).
+  if (__any_sync(__activemask(), (lowm | highm | eqm) != 0u)) {
+    if (__any_sync(__activemask(), eqm != 0u)) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        if ((eqm >> m) & 1u) {
+          const long long kv = ordered_key(t[m]);
+          lowm |= (uint32_t)(kv < R.lo_key) << m;
+          highm |= (uint32_t)(kv > R.hi_key) << m;
+        }
+    }
 #pragma unroll
     for (int m = 0; m < 4; ++m)
-      if ((near >> m) & 1u) {
-        const long long kv = ordered_key(t[m]);
-        if (kv < R.lo_key || kv > R.hi_key) t[m] = __fma_rn(0.5, c.xi[m], kv < R.lo_key ? R.lo_half : R.hi_half);
-      }
+      if (((lowm | highm) >> m) & 1u) t[m] = __fma_rn(0.5, c.xi[m], ((lowm >> m) & 1u) ? R.lo_half : R.hi_half);
   }
   return bits;
 }
