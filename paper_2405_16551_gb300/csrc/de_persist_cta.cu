@@ -115,8 +115,13 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t bar_mma = smem_u32(&s_bar[1]);
   // three accumulators of 128 lanes x 16 columns, one per split pass: warps
   // 0, 1 and 2 issue the passes at the same time (one thread issues a product
-  // only every several tens of cycles); z is their sum in pass order
-  const uint32_t ncols = 64u;
+  // only every several tens of cycles); z is their sum in pass order.  The
+  // split M, the A operand of every product of the launch, lives in tensor
+  // memory from column kColA on (high part, then low part), so that a product
+  // reads only its 512-byte B operand from shared memory instead of also the
+  // 4 KB of A, which bounded the products at about 45 cycles each.
+  constexpr uint32_t kColA = 64u, kColPart = ESZ == 2 ? 64u : 128u;
+  constexpr uint32_t ncols = ESZ == 2 ? 256u : 512u;
   const uint32_t fmt = ESZ == 2 ? 1u : 2u;
   const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kCtaRowsMax >> 3) << 17) |
                          ((uint32_t)(kTileM >> 4) << 24);
@@ -161,6 +166,26 @@ __global__ void __launch_bounds__(256, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
   const uint32_t tmem = s_tmem;
+  {
+    // split M into tensor memory: row r of A (lane r) from the shared-memory
+    // copy, one 16-byte k-group (4 columns) per store; warps w and w + 4
+    // share lanes 32 (w mod 4) .. + 31 and take alternate k-groups
+    const int q4 = warp & 3, r = 32 * q4 + lane;
+    const int nkg = R.kpad * ESZ / 16;
+    for (int part = 0; part < 2; ++part)
+      for (int kg = warp >> 2; kg < nkg; kg += 2) {
+        const uint4 v = *reinterpret_cast<const uint4*>(sMop + (uint32_t)part * m_part + (uint32_t)kg * 2048u +
+                                                        (uint32_t)(r >> 3) * 128u + (uint32_t)(r & 7) * 16u);
+        const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + kColA + (uint32_t)part * kColPart + 4u * (uint32_t)kg;
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta), "r"(v.x), "r"(v.y),
+                     "r"(v.z), "r"(v.w)
+                     : "memory");
+      }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
 
   // Targets of this warp: local rows (warp - shift) + 8 q.  With at most 7
   // targets per CTA (plain DE/rand/1/bin) warp 0 has none: it reduces the
@@ -347,11 +372,12 @@ __global__ void __launch_bounds__(256, 1)
       const int pass = warp;
       // descriptors of the operands' first K step; a byte offset enters the
       // 14-bit address field (16-byte units) and never carries out of it
-      const uint64_t dm = smem_desc(smem_u32(sMop) + (pass == 1 ? m_part : 0u), 2048u, 128u);
+      // A in tensor memory: a K step (two k-groups) is 8 columns
+      const uint32_t ta = tmem + kColA + (pass == 1 ? kColPart : 0u);
       const uint64_t dy = smem_desc(smem_u32(sYop) + (pass == 2 ? y_part : 0u), 256u, 128u);
       for (int ks = 0; ks < ksteps; ++ks)
-        mma_split<ESZ>(tmem + 16u * (uint32_t)pass, dm + (uint64_t)(ks * 256), dy + (uint64_t)(ks * 32), idesc,
-                       ks > 0 ? 1u : 0u);
+        mma_split_ta<ESZ>(tmem + 16u * (uint32_t)pass, ta + 8u * (uint32_t)ks, dy + (uint64_t)(ks * 32), idesc,
+                          ks > 0 ? 1u : 0u);
       mma_commit(bar_mma);
     }
     // ---- 3a. every warp copies one block of the accumulator (TMEM lanes
@@ -642,6 +668,9 @@ bool persist_cta_plan(PersistPlan& pp, const RunDesc& R, int nruns, int prec) {
     cudaGetLastError();
     return false;
   }
+  // tensor memory: 256 columns a CTA (BF16x3: accumulators and the split M)
+  // or 512 (TF32x3) of the SM's 512, so at most 2 or 1 resident CTAs
+  per_sm = std::min(per_sm, prec == DE_PREC_BF16X3 ? 2 : 1);
   pp.cta_cap = per_sm * nsm;
   pp.cta_smem = smem;
   // first choice: the fewest targets per CTA that keep every CTA resident
