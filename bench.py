@@ -913,8 +913,8 @@ def accuracy_workload(capi, torch, stream, problems):
 # generations (traffic grows with generations); a kernel changed since its
 # last capture has no entry
 TRAFFIC_PER_LAUNCH = {
-    # k_persist_cta, 7 targets per CTA: 986,624 + 421,120 bytes per 200 generations
-    ("k_persist_cta", 3000): (986624 + 421120) * 3000 // 200}
+    # k_persist_cta, 7 targets per CTA: 986,112 + 448,000 bytes per 200 generations
+    ("k_persist_cta", 3000): (986112 + 448000) * 3000 // 200}
 
 
 if __name__ == "__main__":
