@@ -599,8 +599,9 @@ DE_API de_status de_get_shape(de_handle* h, int32_t run, int32_t* np, int32_t* d
  * path 3 launched as one cluster, else 0;
  * each cluster owns up to 128 targets (a multiple of the cluster size, timed
  * at de_init; DE_GB300_PERSIST_ROWS fixes it).
- * Paths 2 and 4 apply to a single run of d <= 128; de_init times both and
- * keeps the faster (DE_GB300_PERSIST_MODE=cluster / cta keeps one form,
+ * Paths 2 and 4 apply to a single run, path 2 of d <= 105 (its FP64 band
+ * gives each of the 7 member CTAs at most 15 outputs), path 4 of d <= 128;
+ * de_init times both where both apply and keeps the faster (DE_GB300_PERSIST_MODE=cluster / cta keeps one form,
  * DE_GB300_PERSIST_CTA_ROWS fixes the targets per CTA of path 4); the
  * environment variable DE_GB300_PERSIST=0 disables both.
  * Test switch (failure detection, off by default): DE_GB300_TEST_GRID_TIMEOUT=k

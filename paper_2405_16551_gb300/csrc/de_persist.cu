@@ -771,6 +771,10 @@ static bool persist_cluster_plan(PersistPlan& pp, const RunDesc& R, int nruns, i
   // (the trial and target rows of a warp then stay in registers)
   if (nruns != 1 || R.nn != 1 || R.kc != R.kpad || R.d > 128) return false;
   const int C = kPC;
+  // the FP64 band gives each of the C - 1 member CTAs a block of cwp + 1
+  // outputs (the last one Rosenbrock's neighbour term), computed by 16
+  // threads: cwp <= 15, so d <= 15 (C - 1) = 105
+  if ((R.d + C - 2) / (C - 1) > 15) return false;
   const size_t smem = persist_smem(R, C);
   if (smem > 220 * 1024) return false;
   // first choice: tiles of 128 rows (smaller populations take one tile of

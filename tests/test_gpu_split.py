@@ -90,6 +90,8 @@ def test_split_eval_within_tolerance(prec, obj, d):
     "np_,d,obj,F,CR",
     [(1024, 100, 1, 0.5, 0.9), (64, 10, 0, 0.5, 0.9), (300, 37, 2, 0.8, 0.3), (130, 64, 3, 0.5, 1.0),
      (4, 1, 1, 0.5, 0.9),
+     (200, 128, 1, 0.5, 0.9),    # the largest D of the CTA-local kernel: K fills the A operand's columns
+     (96, 120, 0, 0.5, 0.9),     # K of 128 (BF16x3) and 120 (TF32x3)
      (256, 1000, 1, 0.5, 0.9),   # the large-dimension workload's D: four N tiles, K staged in chunks
      (130, 300, 3, 0.5, 0.9)],   # two N tiles, the second ragged
 )
