@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -473,25 +475,54 @@ static std::string tune_key(const de_handle* h) {
   return b;
 }
 
-static bool tune_lookup(const std::string& key, int& rows) {
-  FILE* f = fopen(tune_cache_path().c_str(), "r");
-  if (!f) return false;
+// The cache file's entries, parsed once per change of the file (path, size
+// and modification time): a de_init then costs one stat, not a read and a
+// parse of the whole file.  The last line of a key wins.
+struct TuneCache {
+  std::mutex mu;
+  std::string path;
+  long long size = -1, mtime_ns = -1;
+  std::map<std::string, int> entries;
+};
+static TuneCache g_tune;
+
+static void tune_refresh(const std::string& path) {
+  struct stat sb;
+  if (stat(path.c_str(), &sb) != 0) {
+    g_tune.path = path;
+    g_tune.size = g_tune.mtime_ns = -1;
+    g_tune.entries.clear();
+    return;
+  }
+  const long long mt = (long long)sb.st_mtim.tv_sec * 1000000000LL + sb.st_mtim.tv_nsec;
+  if (path == g_tune.path && (long long)sb.st_size == g_tune.size && mt == g_tune.mtime_ns) return;
+  g_tune.path = path;
+  g_tune.size = (long long)sb.st_size;
+  g_tune.mtime_ns = mt;
+  g_tune.entries.clear();
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return;
   char line[512];
-  bool found = false;
   while (fgets(line, sizeof line, f)) {
     char* bar = strchr(line, '|');
     if (!bar) continue;
     *bar = 0;
-    if (key == line) {
-      rows = atoi(bar + 1);
-      found = rows > 0;
-    }
+    g_tune.entries[line] = atoi(bar + 1);
   }
   fclose(f);
-  return found;
+}
+
+static bool tune_lookup(const std::string& key, int& rows) {
+  std::lock_guard<std::mutex> lk(g_tune.mu);
+  tune_refresh(tune_cache_path());
+  const auto it = g_tune.entries.find(key);
+  if (it == g_tune.entries.end() || it->second <= 0) return false;
+  rows = it->second;
+  return true;
 }
 
 static void tune_store(const std::string& key, int rows) {
+  std::lock_guard<std::mutex> lk(g_tune.mu);
   std::string p = tune_cache_path();
   const size_t slash = p.find_last_of('/');
   if (slash != std::string::npos && slash > 0) mkdir(p.substr(0, slash).c_str(), 0755);
@@ -499,6 +530,7 @@ static void tune_store(const std::string& key, int rows) {
   if (!f) return;
   fprintf(f, "%s|%d\n", key.c_str(), rows);
   fclose(f);
+  g_tune.size = g_tune.mtime_ns = -1;  // re-read on the next lookup (other processes may append too)
 }
 
 static int heuristic_rows(const de_handle* h, int nsm) {
@@ -947,10 +979,14 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(nullptr, DE_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  cudaDeviceProp prop;
-  e = cudaGetDeviceProperties(&prop, dev);
-  if (e != cudaSuccess) return fail(nullptr, DE_ERR_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
-  if (!(prop.major == 10 && prop.minor == 3))
+  // three attributes (cudaGetDeviceProperties fills the whole structure and
+  // costs a good part of a de_init)
+  int cc_major = 0, cc_minor = 0, nsm = 0;
+  e = cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return fail(nullptr, DE_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+  if (!(cc_major == 10 && cc_minor == 3))
     return fail(nullptr, DE_ERR_UNSUPPORTED, "this library is built for compute capability 10.3 (sm_103a)");
 
   de_handle* h = new de_handle();
@@ -1189,7 +1225,7 @@ de_status de_init_batch(const de_config* cfgs, int32_t nruns, void* cuda_stream,
   if (h->prec == DE_PREC_FP64 && cfgs[0].surrogate_k < 2) {
     ce = cudaMalloc(&h->d_ctl64, sizeof(PersistCtl));
     if (ce != cudaSuccess) return fin(fail(h, DE_ERR_OOM, "cudaMalloc(persistent control) failed"));
-    TRY(autotune_fp64(h, prop.multiProcessorCount));
+    TRY(autotune_fp64(h, nsm));
     TRY(build_items(h));
     TRY(upload_desc(h));
     k_configure(h->smem_gen);
